@@ -1,0 +1,99 @@
+"""Seeded synthetic charge sets shaped like the paper's test problems.
+
+These generators hold none of the method's arithmetic: they only draw points,
+layer ids and charges.  Both the tests and the benchmark use them, for the GPU
+library and for the CPU oracle alike.
+
+* :func:`config1` -- three-layer medium (interfaces z=0, z=-1.2, eps=(1,5,10)),
+  N charges uniform in [-0.5,0.5]^2 x [-1.1,-0.1] (middle layer).
+* :func:`config2` -- same medium, N split equally between the three layers
+  (remainder to the middle one): top z in [0.1,1.1], middle [-1.1,-0.1],
+  bottom [-2.3,-1.3], x, y uniform in [-0.5,0.5].
+* :func:`paper_p4` -- the irregular domains of Section 4: charges uniform in
+  r(theta) = 0.5 - a + a P_4(cos theta), a = (0.1, 0.15, 0.05), centred at
+  z = 0.6, -0.6, -1.8, eps = (21.2, 47.5, 62.8), by rejection from the
+  bounding cube.
+Charges are uniform in [-1, 1].  Every generator uses numpy's PCG64 with
+seed 20190829 + config index unless a seed is given.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+D_CONFIG = (0.0, -1.2)
+EPS_CONFIG = (1.0, 5.0, 10.0)
+EPS_HIGH_CONTRAST = (1.0, 80.0, 2.0)
+EPS_PAPER = (21.2, 47.5, 62.8)
+SEED_BASE = 20190829
+
+
+@dataclass
+class Workload:
+    name: str
+    d: np.ndarray        # interface z positions, strictly decreasing
+    eps: np.ndarray      # permittivity per layer, layer 0 on top
+    xyz: np.ndarray      # [N, 3] float64
+    layer: np.ndarray    # [N] int32
+    q: np.ndarray        # [N] float64
+
+    @property
+    def n(self) -> int:
+        return int(self.xyz.shape[0])
+
+
+def _box(rng, n, zlo, zhi):
+    xy = rng.uniform(-0.5, 0.5, size=(n, 2))
+    z = rng.uniform(zlo, zhi, size=n)
+    return np.column_stack([xy, z])
+
+
+def config1(n: int = 1000, seed: int | None = None, eps=EPS_CONFIG) -> Workload:
+    rng = np.random.Generator(np.random.PCG64(SEED_BASE + 1 if seed is None else seed))
+    xyz = _box(rng, n, -1.1, -0.1)
+    q = rng.uniform(-1.0, 1.0, size=n)
+    return Workload("config1_n%d" % n, np.array(D_CONFIG), np.array(eps, dtype=np.float64), xyz,
+                    np.ones(n, dtype=np.int32), q)
+
+
+def config2(n: int = 1 << 20, seed: int | None = None, eps=EPS_CONFIG) -> Workload:
+    rng = np.random.Generator(np.random.PCG64(SEED_BASE + 2 if seed is None else seed))
+    n0 = n // 3
+    n2 = n // 3
+    n1 = n - n0 - n2
+    parts = [(_box(rng, n0, 0.1, 1.1), 0), (_box(rng, n1, -1.1, -0.1), 1), (_box(rng, n2, -2.3, -1.3), 2)]
+    xyz = np.concatenate([p for p, _ in parts])
+    layer = np.concatenate([np.full(p.shape[0], l, dtype=np.int32) for p, l in parts])
+    q = rng.uniform(-1.0, 1.0, size=n)
+    return Workload("config2_n%d" % n, np.array(D_CONFIG), np.array(eps, dtype=np.float64), xyz, layer, q)
+
+
+def paper_p4(counts=(912, 640, 1296), seed: int | None = None) -> Workload:
+    rng = np.random.Generator(np.random.PCG64(SEED_BASE + 6 if seed is None else seed))
+    avals = (0.1, 0.15, 0.05)
+    centres = (0.6, -0.6, -1.8)
+    pts, lay = [], []
+    for l, (cnt, a, zc) in enumerate(zip(counts, avals, centres)):
+        got = []
+        while sum(g.shape[0] for g in got) < cnt:
+            c = rng.uniform(-0.5, 0.5, size=(4 * cnt, 3))
+            r = np.linalg.norm(c, axis=1)
+            ct = np.divide(c[:, 2], r, out=np.zeros_like(r), where=r > 0)
+            p4 = (35 * ct ** 4 - 30 * ct ** 2 + 3) / 8.0
+            keep = r < 0.5 - a + a * p4
+            got.append(c[keep])
+        g = np.concatenate(got)[:cnt]
+        g[:, 2] += zc
+        pts.append(g)
+        lay.append(np.full(cnt, l, dtype=np.int32))
+    xyz = np.concatenate(pts)
+    layer = np.concatenate(lay)
+    q = rng.uniform(-1.0, 1.0, size=xyz.shape[0])
+    return Workload("paper_p4_%d" % xyz.shape[0], np.array(D_CONFIG), np.array(EPS_PAPER), xyz, layer, q)
+
+
+def subsample(n: int, count: int, seed: int = SEED_BASE + 3) -> np.ndarray:
+    """The first ``count`` indices of a seeded permutation of range(n)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.sort(rng.permutation(n)[:count]).astype(np.int64)
