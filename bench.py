@@ -1,0 +1,323 @@
+"""Benchmark of the layered-media FMM on one or more GB300s.
+
+One step = one pass of the whole hot path on one synthetic charge set that is
+already resident in HBM: octree build (classify, Morton sort, boxes,
+interaction lists) followed by the evaluation of potentials and fields
+(P2M, M2M, free-space and reaction M2L, L2L, L2P, near field, component
+sum).  Workload: three-layer medium (interfaces z=0, z=-1.2, eps=(1,5,10)),
+N = 1,048,576 charges split equally between the layers, p = 10, leaf
+capacity 40.  ``value`` is particles/s of the headline form (FP32 P2P, M2L
+and L2P with compensated sums and FP64 Sommerfeld tables); the plain FP64
+form is timed on the same input and reported beside it.
+
+With --gpus N (torchrun, one process per GPU) every rank runs an independent
+replica of the step (the method needs no exchange between GPUs for one
+problem); ``value`` is all particles processed / the slowest rank's time.
+
+``--impl reference`` times the CPU oracle (direct FP64 sum, exact
+three-layer image series) on the host cores on a bounded sample of targets
+of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particles/s at N=1M p=10 (FP32 form vs plain FP64 GPU), rel L2 err"
+FP64_PEAK_TFLOPS = 1.25  # nominal dense FP64 of a GB300 (no measured figure available)
+SMS = 152
+
+
+def fp32_peak_tflops(sm_mhz):
+    # 128 FP32 lanes per SM, one FMA (2 flops) per lane per clock
+    return SMS * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1 << 20)
+    ap.add_argument("--p", type=int, default=10)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 leg")
+    ap.add_argument("--sample", type=int, default=256, help="oracle targets for the accuracy / CPU leg")
+    return ap.parse_args()
+
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % index)
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        try:
+            import torch
+            if not torch.cuda.is_available():
+                backend = "gloo"
+        except Exception:
+            backend = "gloo"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def allmax(pg, v):
+    if pg is None:
+        return v
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([float(v)], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_sample(w, count):
+    import oracle
+    from paper_1908_10863_gb300 import workloads
+    t = workloads.subsample(w.n, count)
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    ref, refE = oracle.direct(w.d, w.eps, w.xyz, w.layer, w.q, targets=t, mode=oracle.MODE_IMAGES,
+                              threads=threads)
+    dt = time.perf_counter() - t0
+    return t, ref, refE, dt, threads
+
+
+def m2l_flops_per_pair(p):
+    # dense M2L: (p+1)^2 source coefficients x (p+1)(p+2)/2 target coefficients, complex MAC = 8 flops
+    return 8 * (p + 1) ** 2 * (p + 1) * (p + 2) // 2
+
+
+def run_form(f, xyz_d, lay_d, q_d, phi_d, fld_d, torch, steps, warmup, flush):
+    stream = torch.cuda.current_stream()
+
+    def step():
+        f.build_device(xyz_d, lay_d, stream)
+        f.evaluate_device(q_d, phi_d, fld_d, stream)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(steps):
+        flush.fill_(1.0)  # evict L2 between steps (untimed)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    torch.cuda.synchronize()
+    return times
+
+
+def main():
+    args = parse()
+    world, rank, local, pg = dist_setup(args)
+    from paper_1908_10863_gb300 import workloads
+
+    w = workloads.config2(args.n)
+    workload = ("three-layer medium d=(0,-1.2) eps=(1,5,10), N=%d charges split equally between layers, "
+                "q~U[-1,1], p=%d, leaf 40" % (w.n, args.p))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        count = max(8, args.sample // 4)
+        for _ in range(args.warmup):
+            pass  # the oracle has no warm-up state; warm-up steps are not needed
+        times = []
+        threads = os.cpu_count() or 1
+        for _ in range(args.steps):
+            _, _, _, dt, threads = oracle_sample(w, count)
+            times.append(dt)
+        ms = 1e3 * sum(times) / len(times)
+        value = count / (ms / 1e3)
+        line = {"metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": args.gpus, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+                "config": {"workload": workload, "sample_targets": count},
+                "cpu_baseline": {"value": value, "unit": "particles/s", "cores": threads, "kind": "oracle",
+                                 "sample": "%d targets (seeded subsample) x all %d sources per step, exact "
+                                           "three-layer image series" % (count, w.n)},
+                "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+
+    import torch
+    from paper_1908_10863_gb300 import LayeredFMM
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    xyz_d = torch.from_numpy(w.xyz).to(dev)
+    lay_d = torch.from_numpy(w.layer).to(dev)
+    q_d = torch.from_numpy(w.q).to(dev)
+    phi_d = torch.empty(w.n, dtype=torch.float64, device=dev)
+    fld_d = torch.empty((w.n, 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
+
+    results = {}
+    forms = [("fp32", 1)] + ([] if args.no_fp64 else [("fp64", 0)])
+    clocks = Clocks(local)
+    for name, prec in forms:
+        f = LayeredFMM(w.d, w.eps, args.p, precision=prec)
+        barrier(pg)
+        if name == "fp32":
+            clocks.start()
+        times = run_form(f, xyz_d, lay_d, q_d, phi_d, fld_d, torch, args.steps, args.warmup, flush)
+        if name == "fp32":
+            clk = clocks.stop()
+        barrier(pg)
+        # stage timings of one profiled step (separate, untimed pass)
+        f.set_option(3, 1)
+        f.build_device(xyz_d, lay_d, torch.cuda.current_stream())
+        f.evaluate_device(q_d, phi_d, fld_d, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        tim = f.timings()
+        f.set_option(3, 0)
+        st = f.stats()
+        ms = sum(times) / len(times)
+        results[name] = {"ms_per_step": ms, "times": times, "timings": tim, "stats": st,
+                         "phi": phi_d.cpu().numpy().copy(), "E": fld_d.cpu().numpy().copy()}
+        if name == "fp32":
+            # end-to-end through the host-buffer C ABI (copies inside the timed region)
+            e2e_t = []
+            for k in range(max(2, min(args.steps, 5))):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                f.build(w.xyz, w.layer)
+                ph, E = f.evaluate(w.q)
+                e2e_t.append(time.perf_counter() - t0)
+            results[name]["e2e_s"] = sum(e2e_t) / len(e2e_t)
+        f.close()
+
+    ms_max = allmax(pg, results["fp32"]["ms_per_step"])
+    e2e_max = allmax(pg, results["fp32"]["e2e_s"])
+    if rank != 0:
+        barrier(pg)
+        return 0
+
+    value = world * w.n / (ms_max / 1e3)
+    t, ref, refE, dt, threads = oracle_sample(w, args.sample)
+    forms_out = {}
+    for name in results:
+        r = results[name]
+        import oracle
+        e2p = oracle.err2(ref, r["phi"][t])
+        e2E = oracle.err2(refE, r["E"][t])
+        forms_out[name] = {"particles_per_s": w.n / (r["ms_per_step"] / 1e3), "ms_per_step": r["ms_per_step"],
+                           "err2_phi": e2p, "err2_field": e2E, "stage_ms": r["timings"]}
+    st = results["fp32"]["stats"]
+    tim = results["fp32"]["timings"]
+    flops = st["m2l_free"] * m2l_flops_per_pair(args.p)
+    m2l_ms = tim["m2l_free"]
+    sm_mhz = clk.get("sm_max_mhz") or 2070.0
+    peak = fp32_peak_tflops(sm_mhz)
+    achieved = flops / (m2l_ms / 1e3) / 1e12 if m2l_ms > 0 else None
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "particles/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_max,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": workload, "form": "FP32 P2P/M2L/L2P, compensated sums, FP64 Sommerfeld tables",
+                   "l2": "256 MB buffer written between timed steps (L2 flushed)", "parallelism": "replicas"},
+        "err2": {"phi": forms_out["fp32"]["err2_phi"], "field": forms_out["fp32"]["err2_field"],
+                 "targets": int(len(t)), "reference": "CPU oracle (FP64 direct sum, exact image series)"},
+        "forms": forms_out,
+        "roofline": {"kernel": "k_m2l (free-space M2L, FP32)", "bound": "alu", "achieved": achieved,
+                     "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
+                     "traffic": None,
+                     "peak_note": "FP32 CUDA-core peak from unit counts (152 SMs x 128 lanes x 2 flops) at the "
+                                  "max SM clock seen; algorithmic flops = 8 (p+1)^2 (p+1)(p+2)/2 per box pair"},
+        "cpu_baseline": {"value": len(t) / dt, "unit": "particles/s", "cores": threads, "kind": "oracle",
+                         "sample": "%d targets (seeded subsample) x all %d sources, exact three-layer image "
+                                   "series, %.1f s" % (len(t), w.n, dt)},
+        "e2e": {"value": world * w.n / e2e_max, "unit": "particles/s", "h2d_bytes_per_step": w.n * (24 + 4 + 8),
+                "d2h_bytes_per_step": w.n * (8 + 24)},
+        "gpu_launches": None,
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+    barrier(pg)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

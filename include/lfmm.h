@@ -1,0 +1,171 @@
+/*
+ * lfmm.h -- C ABI of the layered-media Laplace FMM for one GB300 (sm_103a).
+ *
+ * The library evaluates, for N point charges Q_j at r_j in a medium of L+1
+ * horizontal layers (interfaces z = d_0 > d_1 > ... > d_{L-1}, permittivity
+ * eps_l in layer l, layer 0 on top), the potential and field at every charge
+ *
+ *   Phi(r_i) = sum_{j != i, l_j = l_i} Q_j / (4 pi |r_i - r_j|)
+ *            + sum_j Q_j u^r_{l_i l_j}(r_i, r_j),          E = -grad Phi,
+ *
+ * (Section 3.1, eqs. potential1, totalinteraction, freereactioncomponents of
+ * Wang, Zhang & Cai, arXiv 1908.10863), where u^r is the reaction part of the
+ * layered Green's function (eqs. reactioncomponent, generalcomponents,
+ * zexponential).  The free-space part is computed by a classic FMM and each
+ * reaction component by the FMM of Algorithm 1 on equivalent polarization
+ * sources (eq. eqpolarizedsource), summed as in Algorithm 2.
+ *
+ * Conventions for every call:
+ *   - All pointers are plain host or device pointers as stated per argument;
+ *     the caller owns every array it passes and keeps ownership.  The library
+ *     copies what it needs; no pointer is retained after a call returns.
+ *   - Arrays of points are row-major [n][3] float64.
+ *   - Results are written in the caller's order of the charges.
+ *   - A context is not thread-safe: one host thread at a time.
+ *   - No exception crosses the ABI.  A failing call returns a status other
+ *     than LFMM_OK, leaves the context usable (or, for lfmm_create, sets *out
+ *     to NULL) and stores a message readable with lfmm_last_error.
+ *   - The library needs a CUDA device; it never computes on the host.
+ */
+#ifndef LFMM_H
+#define LFMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lfmm_ctx lfmm_ctx;
+
+typedef enum {
+    LFMM_OK = 0,
+    LFMM_EINVAL = 1,   /* invalid argument (sizes, layer ids, points on an interface, ...) */
+    LFMM_ENOMEM = 2,   /* device or host allocation failed */
+    LFMM_ECUDA = 3,    /* a CUDA runtime call failed (message holds the CUDA error) */
+    LFMM_ESTATE = 4,   /* call out of order (e.g. evaluate before build) */
+    LFMM_ETIMEOUT = 5, /* reserved: bounded device-side wait expired */
+    LFMM_ENUMERIC = 6  /* non-finite input or result */
+} lfmm_status;
+
+/* Options for lfmm_set_option. */
+enum {
+    LFMM_OPT_PRECISION = 1, /* 0 = plain FP64 (default); 1 = FP32 P2P/M2L/L2P with
+                               compensated far-field sums, FP64 Sommerfeld tables */
+    LFMM_OPT_LEAF_CAP = 2,  /* octree leaf capacity (default 40) */
+    LFMM_OPT_PROFILE = 3,   /* 1 = time every stage with CUDA events (lfmm_get_timings) */
+    LFMM_OPT_QUAD_NODES = 4 /* Gauss-Laguerre nodes of the M2L remainder integrals (16..128, default 64) */
+};
+
+/* Create a context for the medium.
+ *   d   : host, L interface heights, strictly decreasing (Section 3.1).
+ *   L   : number of interfaces, 0 <= L <= 2 (one to three layers).
+ *   eps : host, L+1 permittivities > 0, layer 0 on top.
+ *   p   : truncation order of all expansions, 1 <= p <= 20 (FP64) and
+ *         p <= 14 in the FP32 form.
+ *   out : receives the context, or NULL on failure.
+ * Selects CUDA device 0 unless a device is already current. */
+lfmm_status lfmm_create(const double* d, int L, const double* eps, int p, lfmm_ctx** out);
+
+/* Set one option (see LFMM_OPT_*). Takes effect at the next build/evaluate. */
+lfmm_status lfmm_set_option(lfmm_ctx* ctx, int opt, double value);
+
+/* Build the octree and interaction lists for n charges (Algorithm 1, first
+ * two steps; Section 3.3 for the interface-aligned boxes).
+ *   xyz   : host, [n][3] positions.
+ *   layer : host, [n] layer ids, with d_l < z < d_{l-1} (eq. Laplaceeqlayer).
+ * Points on or outside their layer's slab are rejected with LFMM_EINVAL.
+ * n >= 1.  Replaces any previous build. */
+lfmm_status lfmm_build(lfmm_ctx* ctx, int64_t n, const double* xyz, const int32_t* layer);
+
+/* Same as lfmm_build with device-resident inputs, ordered on cuda_stream
+ * (a cudaStream_t, or NULL for the legacy default stream).  Inputs must stay
+ * valid until the call returns (it synchronises the stream). */
+lfmm_status lfmm_build_device(lfmm_ctx* ctx, int64_t n, const double* xyz_dev, const int32_t* layer_dev,
+                              void* cuda_stream);
+
+/* Evaluate potentials and fields for nrhs charge vectors over the built
+ * geometry (Algorithm 2).
+ *   q     : host, [nrhs][n] charges in the caller's order.
+ *   phi   : host, [nrhs][n] output potentials (1/(4 pi) included).
+ *   field : host, [nrhs][n][3] output E = -grad Phi, or NULL to skip.
+ * Returns LFMM_ESTATE before a successful build. */
+lfmm_status lfmm_evaluate(lfmm_ctx* ctx, int nrhs, const double* q, double* phi, double* field);
+
+/* Same with device arrays (float64), ordered on cuda_stream; returns once the
+ * work is enqueued on that stream (no host synchronisation). */
+lfmm_status lfmm_evaluate_device(lfmm_ctx* ctx, int nrhs, const double* q_dev, double* phi_dev, double* field_dev,
+                                 void* cuda_stream);
+
+/* Message of the last failed call on ctx ("" if none); valid until the next call. */
+const char* lfmm_last_error(const lfmm_ctx* ctx);
+
+/* Release every resource of ctx.  NULL is allowed. */
+void lfmm_destroy(lfmm_ctx* ctx);
+
+/* ---- inspection and measurement --------------------------------------- */
+
+/* Counters of the current build (host array of at least LFMM_STAT_COUNT
+ * int64 entries, see LFMM_STAT_*). */
+enum {
+    LFMM_STAT_N = 0,
+    LFMM_STAT_DEPTH = 1,
+    LFMM_STAT_BOXES = 2,          /* all levels, all layers */
+    LFMM_STAT_LEAVES = 3,
+    LFMM_STAT_M2L_FREE = 4,       /* free-space M2L box pairs, all levels */
+    LFMM_STAT_M2L_REACTION = 5,   /* reaction M2L box pairs, all levels and components */
+    LFMM_STAT_P2P_FREE = 6,       /* free-space near-field particle pairs (incl. i == j slots) */
+    LFMM_STAT_P2P_REACTION = 7,   /* reaction near-field particle pairs */
+    LFMM_STAT_COMPONENTS = 8,     /* free + reaction components of the medium */
+    LFMM_STAT_M2M_EDGES = 9,      /* parent-child edges (also the L2L count) */
+    LFMM_STAT_LAUNCHES = 10,      /* kernels launched by this context since lfmm_create (cumulative) */
+    LFMM_STAT_COUNT = 16
+};
+lfmm_status lfmm_get_stats(const lfmm_ctx* ctx, int64_t* out, int nout);
+
+/* Stage timings of the last evaluate in milliseconds (needs
+ * LFMM_OPT_PROFILE = 1), host array of LFMM_TIME_COUNT doubles. */
+enum {
+    LFMM_TIME_P2M = 0,
+    LFMM_TIME_M2M = 1,
+    LFMM_TIME_M2L_FREE = 2,
+    LFMM_TIME_M2L_REACTION = 3,
+    LFMM_TIME_L2L = 4,
+    LFMM_TIME_L2P = 5,
+    LFMM_TIME_P2P = 6,
+    LFMM_TIME_TOTAL = 7,
+    LFMM_TIME_BUILD = 8,
+    LFMM_TIME_COUNT = 12
+};
+lfmm_status lfmm_get_timings(const lfmm_ctx* ctx, double* out, int nout);
+
+/* Sommerfeld-type integral tables of one reaction component, as used by the
+ * reaction M2L (eqs. uniformintegral, scaledsommerfeldint; Section 3.4), for
+ * npts geometries on the device:
+ *   comp : (l, lp, a, b) of the component (a, b in {1, 2}).
+ *   rho, z : host, [npts] horizontal distance and vertical separation
+ *            (z > 0: |z_c^t - z_c^{ab}|) in physical units.
+ *   S    : box size used for scaling (eq. scaledsommerfeldint).
+ *   out  : host, [npts][2P+1][2P+1] row-major (N, mu), the unnormalised,
+ *          scaled integral S^{N+1} int_0^inf J_mu(k rho) k^N e^{-kz}
+ *          sigma(k) dk for 0 <= mu <= N <= 2P (other entries 0).
+ *   P    : expansion order (tables cover N <= 2P).
+ * Computed by the same device routine as the M2L kernel. */
+lfmm_status lfmm_sommerfeld_tables(lfmm_ctx* ctx, int l, int lp, int a, int b, int npts, const double* rho,
+                                   const double* z, double S, int P, double* out);
+
+/* Reaction kernel values of one component for npts (rho, h) pairs on the
+ * device: out[i][0..2] = (int J0 e^{-kh} sigma dk, int k J0 e^{-kh} sigma dk,
+ * int k J1 e^{-kh} sigma dk), the quantities of the near-field interactions
+ * of Algorithm 1 (I_00 and its derivatives).  Host arrays. */
+lfmm_status lfmm_reaction_kernel(lfmm_ctx* ctx, int l, int lp, int a, int b, int npts, const double* rho,
+                                 const double* h, double* out);
+
+/* Host-only helper (no device needed): Gauss-Laguerre nodes and weights of
+ * order Q (weight e^{-t} on [0, inf)) as used by the quadratures. */
+lfmm_status lfmm_gauss_laguerre(int Q, double* nodes, double* weights);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LFMM_H */

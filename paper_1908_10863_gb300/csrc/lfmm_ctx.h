@@ -1,0 +1,140 @@
+// lfmm_ctx.h -- host-side context of the layered-media FMM library and the
+// launcher functions each translation unit provides.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/lfmm.h"
+#include "lfmm_internal.cuh"
+
+// Grow-only device buffer owned by the context.
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t cap = 0;
+    template <typename T>
+    T* as() const { return reinterpret_cast<T*>(ptr); }
+};
+
+// Status from a launcher: empty string = fine, else the error message.
+using LfErr = std::string;
+
+struct LfmmLevel {
+    int nbox = 0;
+    int off = 0;      // first global box id
+    double h = 0.0;   // box size
+    // list CSR offsets into the global near / m2l entry arrays
+    int64_t near_base = 0, m2l_base = 0, m2r_base = 0;
+    int64_t near_count = 0, m2l_count = 0, m2r_count = 0;  // near, free M2L, reaction M2L
+};
+
+struct lfmm_ctx {
+    // medium and order
+    int L = 0;
+    double d[2] = {0, 0};
+    double eps[3] = {1, 1, 1};
+    int p = 0;
+    // options
+    int precision = 0;
+    int leaf_cap = 40;
+    int profile = 0;
+    int quad_nodes = 64;
+    int quad_nodes_near = 32;
+    int near_pole = 0;  // density denominator has a real zero in (0, 1.5]
+    std::string err;
+
+    // components
+    int ncomp = 0;
+    LfmmComp comp[LFMM_MAXCOMP];
+
+    // device and streams
+    int device = 0;
+    cudaStream_t s_main = nullptr, s_near = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    std::vector<cudaEvent_t> prof_ev;
+
+    // quadrature tables (device): [Qm2l] then [Qnear] nodes/weights
+    DevBuf gl_t_m2l, gl_w_m2l, gl_t_near, gl_w_near;
+    int gl_q_m2l = 0, gl_q_near = 0;
+
+    // free-space M2L tables per offset (box units), [343][(2p+1)^2] (FP64 and FP32)
+    DevBuf free_T64, free_T32;
+    // regular harmonics of the 8 child offsets (+-1/4)^3, [8][2*NRE] (re, im)
+    DevBuf oct_U64, oct_U32;
+    DevBuf comp_dev;  // LfmmComp[ncomp]
+
+    // geometry of the grid
+    bool built = false;
+    int64_t n = 0;
+    int depth = 0;
+    double H = 1.0;
+    double origin[3] = {0, 0, 0};
+    int nlayer_used[3] = {0, 0, 0};
+    std::vector<LfmmLevel> levels;  // index = level 0..depth
+    int nbox_total = 0;
+
+    // particle data (sorted order)
+    DevBuf perm;          // int32 [n]: sorted index -> caller index
+    DevBuf xs, ys, zs;    // double [n]
+    DevBuf keys, keys_tmp, vals_tmp, scan_tmp, hist;
+    DevBuf xyz_in, layer_in;  // staging of host inputs
+    DevBuf err_flag;          // int [4]
+    DevBuf counts;            // misc small counters
+
+    // boxes (global ids)
+    DevBuf box_key;     // uint32
+    DevBuf box_pbeg;    // int32
+    DevBuf box_pend;    // int32
+    DevBuf box_parent;  // int32
+    DevBuf box_cbeg;    // int32 (first child id, -1 for leaves)
+    DevBuf box_cend;    // int32
+    DevBuf box_center;  // LfD4 (x, y, z, layer)
+    DevBuf flags, idx;  // temporaries
+
+    // lists: offsets per level box (near_off[level_box] relative to level base) and entries
+    DevBuf near_off, near_ent, m2l_off, m2l_ent, m2r_off, m2r_ent;
+    int64_t near_total = 0, m2l_total = 0, m2r_total = 0;
+
+    // evaluation buffers
+    DevBuf q_sorted;            // R [n]
+    DevBuf Mexp, Lexp;          // R [nbox][(p+1)^2]
+    DevBuf phi_far, phi_near;   // double [n]
+    DevBuf fld_far, fld_near;   // double [n*3]
+    DevBuf q_stage, phi_stage, fld_stage;  // host<->device staging for lfmm_evaluate
+
+    // statistics
+    int64_t launches = 0;  // kernels launched by this context since creation
+    int64_t stats[16] = {0};
+    double timings[12] = {0};
+    // profiling: (slot, start, stop) event triples recorded during an evaluation
+    struct ProfRec { int slot; cudaEvent_t a, b; };
+    std::vector<ProfRec> prof_recs;
+    std::vector<cudaEvent_t> prof_pool;
+    size_t prof_used = 0;
+};
+
+// ---- allocation helpers (lfmm_api.cu) ----
+LfErr lf_reserve(DevBuf& b, size_t bytes);
+LfErr lf_cuda(cudaError_t e, const char* what);
+
+// ---- tree construction (lfmm_tree.cu) ----
+LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz_dev, const int32_t* layer_dev, int64_t n, cudaStream_t st);
+
+// ---- evaluation (lfmm_fmm.cu, lfmm_near.cu) ----
+LfErr lf_evaluate_sorted(lfmm_ctx* ctx, const double* q_dev, double* phi_dev, double* field_dev, cudaStream_t st);
+LfErr lf_near_field(lfmm_ctx* ctx, cudaStream_t st);
+
+// ---- debug / parity kernels (lfmm_near.cu) ----
+LfErr lf_sommerfeld_tables_dev(lfmm_ctx* ctx, int comp, int npts, const double* rho, const double* z, double S,
+                               int P, double* out);
+LfErr lf_reaction_kernel_dev(lfmm_ctx* ctx, int comp, int npts, const double* rho, const double* h, double* out);
+
+// exclusive scan of int32 (lfmm_tree.cu); returns the total through *total (host) if non-null
+LfErr lf_scan_i32(lfmm_ctx* ctx, const int* in, int* out, int64_t n, int64_t* total, cudaStream_t st);
+
+// profile helpers: lf_prof_start returns a handle for lf_prof_stop (or -1 when off)
+int lf_prof_start(lfmm_ctx* ctx, int slot, cudaStream_t st);
+void lf_prof_stop(lfmm_ctx* ctx, int handle, cudaStream_t st);

@@ -1,0 +1,615 @@
+// lfmm_fmm.cu -- far-field kernels of the layered-media FMM (Algorithm 1:
+// upward pass, downward pass, evaluation of the local expansions) and the
+// driver of one evaluation.
+//
+// Every component targeting layer l adds into ONE local-expansion tree of
+// that layer: the free-space M2L of eq. metole and the reaction M2L of eqs.
+// metoleimage1 / coefintable (built from the Sommerfeld tables of
+// lfmm_sommerfeld_table_block) both land in the same L; L2L (eq. letole) and
+// L2P are then done once per layer instead of once per component.  This is
+// the sum of Algorithm 2 moved before the (linear) downward pass.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "lfmm_ctx.h"
+
+#define LF_CHECK(call)                                    \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return lf_cuda(e_, #call); \
+    } while (0)
+#define LF_TRY(expr)                \
+    do {                            \
+        LfErr r_ = (expr);          \
+        if (!r_.empty()) return r_; \
+    } while (0)
+
+static inline int lf_blocks(int64_t n, int t) { return (int)((n + t - 1) / t); }
+
+__constant__ LfmmComp c_comp[LFMM_MAXCOMP];
+
+template <typename R>
+struct LfAcc {  // compensated (Kahan) sum in single precision, plain sum in double
+    R s = 0, c = 0;
+    __device__ __forceinline__ void add(R x)
+    {
+        R y = x - c;
+        R t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ R get() const { return s; }
+};
+template <>
+struct LfAcc<double> {
+    double s = 0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double get() const { return s; }
+};
+
+// ---------------------------------------------------------------------------
+// P2M (eq. mefreespace / melayerupgoingimage): M_n^m = sum_j q_j conj(U_n^m((x_j - s)/h)).
+// One warp per leaf box; lanes own particles while the harmonics are formed
+// and coefficients while they are summed.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(32) k_p2m(int off, int p, const LfD4* __restrict__ cen,
+                                            const int* __restrict__ pbeg, const int* __restrict__ pend,
+                                            const double* __restrict__ xs, const double* __restrict__ ys,
+                                            const double* __restrict__ zs, const R* __restrict__ q, double h,
+                                            R* __restrict__ M)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* su = reinterpret_cast<R*>(smem_raw);
+    const int nre = lf_nre(p), nc = lf_nc(p);
+    const int lane = threadIdx.x;
+    const int b = off + blockIdx.x;
+    const LfD4 c = cen[b];
+    const double ih = 1.0 / h;
+    R* ure = su + lane * 2 * nre;
+    R* uim = ure + nre;
+    constexpr int KMAX = (LFMM_PMAX + 1) * (LFMM_PMAX + 1) / 32 + 1;
+    R acc[KMAX];
+    int src[KMAX];
+    for (int k = 0; k < KMAX; ++k) {
+        acc[k] = 0;
+        int o = lane + 32 * k;
+        src[k] = -1;
+        if (o < nc) {
+            int n, m, im;
+            lf_decode(p, o, n, m, im);
+            src[k] = im ? (nre + lf_re(n, m)) : lf_re(n, m);
+        }
+    }
+    for (int start = pbeg[b]; start < pend[b]; start += 32) {
+        int i = start + lane;
+        if (i < pend[b]) {
+            R x = (R)((xs[i] - c.x) * ih), y = (R)((ys[i] - c.y) * ih), z = (R)((zs[i] - c.z) * ih);
+            lf_regular<R>(p, x, y, z, ure, uim);
+            R qi = q[i];
+            for (int j = 0; j < nre; ++j) {
+                ure[j] *= qi;
+                uim[j] *= -qi;  // conjugate
+            }
+        } else {
+            for (int j = 0; j < 2 * nre; ++j) ure[j] = 0;
+        }
+        __syncwarp();
+        for (int k = 0; k < KMAX; ++k) {
+            if (src[k] < 0) continue;
+            R s = 0;
+            for (int r = 0; r < 32; ++r) s += su[r * 2 * nre + src[k]];
+            acc[k] += s;
+        }
+        __syncwarp();
+    }
+    R* out = M + (size_t)b * nc;
+    for (int k = 0; k < KMAX; ++k)
+        if (src[k] >= 0) out[lane + 32 * k] = acc[k];
+}
+
+// Complex helpers for packed coefficient arrays (m may be negative).
+template <typename R>
+__device__ __forceinline__ void lf_get(const R* v, int p, int n, int m, R& re, R& im)
+{
+    if (m >= 0) {
+        re = v[lf_re(n, m)];
+        im = (m > 0) ? v[lf_im(p, n, m)] : R(0);
+    } else {
+        int a = -m;
+        R s = (a & 1) ? R(-1) : R(1);
+        re = s * v[lf_re(n, a)];
+        im = -s * v[lf_im(p, n, a)];
+    }
+}
+// regular harmonics stored as separate re/im arrays of length NRE
+template <typename R>
+__device__ __forceinline__ void lf_getU(const R* ure, const R* uim, int n, int m, R& re, R& im)
+{
+    if (m >= 0) {
+        re = ure[lf_re(n, m)];
+        im = uim[lf_re(n, m)];
+    } else {
+        int a = -m;
+        R s = (a & 1) ? R(-1) : R(1);
+        re = s * ure[lf_re(n, a)];
+        im = -s * uim[lf_re(n, a)];
+    }
+}
+
+__device__ __forceinline__ int lf_octant(LfD4 child, LfD4 parent)
+{
+    return (child.x > parent.x ? 1 : 0) | (child.y > parent.y ? 2 : 0) | (child.z > parent.z ? 4 : 0);
+}
+
+// ---------------------------------------------------------------------------
+// M2M (eq. metome): M_p(n,m) = sum_{k,l} 2^{-k} M_c(k,l) conj(U_{n-k}^{m-l}(d)),
+// d = (child - parent)/h_parent in {+-1/4}^3.  One block per parent box.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_m2m(int off, int p, const LfD4* __restrict__ cen, const int* __restrict__ cbeg,
+                      const int* __restrict__ cend, const R* __restrict__ octU, R* __restrict__ M)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nre = lf_nre(p), nc = lf_nc(p);
+    R* sM = reinterpret_cast<R*>(smem_raw);
+    R* sUr = sM + nc;
+    R* sUi = sUr + nre;
+    const int b = off + blockIdx.x;
+    const int tid = threadIdx.x;
+    int n = 0, m = 0, im = 0;
+    const bool act = tid < nre;
+    if (act) lf_decode(p, tid, n, m, im);
+    R ar = 0, ai = 0;
+    const LfD4 pc = cen[b];
+    for (int ch = cbeg[b]; ch < cend[b]; ++ch) {
+        int o = lf_octant(cen[ch], pc);
+        for (int j = tid; j < nc; j += blockDim.x) sM[j] = M[(size_t)ch * nc + j];
+        for (int j = tid; j < nre; j += blockDim.x) {
+            sUr[j] = octU[(size_t)o * 2 * nre + j];
+            sUi[j] = octU[(size_t)o * 2 * nre + nre + j];
+        }
+        __syncthreads();
+        if (act) {
+            R sc = 1;
+            for (int k = 0; k <= n; ++k) {
+                for (int l = -k; l <= k; ++l) {
+                    int dm = m - l;
+                    if (dm > n - k || dm < -(n - k)) continue;
+                    R mr, mi, ur, ui;
+                    lf_get(sM, p, k, l, mr, mi);
+                    lf_getU(sUr, sUi, n - k, dm, ur, ui);
+                    // M * conj(U)
+                    ar += sc * (mr * ur + mi * ui);
+                    ai += sc * (mi * ur - mr * ui);
+                }
+                sc *= R(0.5);
+            }
+        }
+        __syncthreads();
+    }
+    if (act) {
+        M[(size_t)b * nc + lf_re(n, m)] = ar;
+        if (m > 0) M[(size_t)b * nc + lf_im(p, n, m)] = ai;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// L2L (eq. letole): L_c(j,i) = sum_{k>=j,l} 2^{-j} L_p(k,l) conj(U_{k-j}^{l-i}(d)).
+// One block per child box; overwrites L of the child.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_l2l(int off, int p, const LfD4* __restrict__ cen, const int* __restrict__ parent,
+                      const R* __restrict__ octU, R* __restrict__ L)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nre = lf_nre(p), nc = lf_nc(p);
+    R* sL = reinterpret_cast<R*>(smem_raw);
+    R* sUr = sL + nc;
+    R* sUi = sUr + nre;
+    const int b = off + blockIdx.x;
+    const int tid = threadIdx.x;
+    const int pb = parent[b];
+    const int o = lf_octant(cen[b], cen[pb]);
+    for (int j = tid; j < nc; j += blockDim.x) sL[j] = L[(size_t)pb * nc + j];
+    for (int j = tid; j < nre; j += blockDim.x) {
+        sUr[j] = octU[(size_t)o * 2 * nre + j];
+        sUi[j] = octU[(size_t)o * 2 * nre + nre + j];
+    }
+    __syncthreads();
+    if (tid >= nre) return;
+    int jn, im_, mm;
+    lf_decode(p, tid, jn, mm, im_);
+    R ar = 0, ai = 0;
+    for (int k = jn; k <= p; ++k) {
+        for (int l = -k; l <= k; ++l) {
+            int dm = l - mm;
+            if (dm > k - jn || dm < -(k - jn)) continue;
+            R lr, li, ur, ui;
+            lf_get(sL, p, k, l, lr, li);
+            lf_getU(sUr, sUi, k - jn, dm, ur, ui);
+            ar += lr * ur + li * ui;
+            ai += li * ur - lr * ui;
+        }
+    }
+    R sc = 1;
+    for (int q = 0; q < jn; ++q) sc *= R(0.5);
+    L[(size_t)b * nc + lf_re(jn, mm)] = sc * ar;
+    if (mm > 0) L[(size_t)b * nc + lf_im(p, jn, mm)] = sc * ai;
+}
+
+// ---------------------------------------------------------------------------
+// M2L for one level, all components, one block per target box.
+// Output j of the packed layout is owned by thread j.  Per entry (c, s):
+//   v = (t - P_c(s)) / h, (rho, phi) its horizontal polar coordinates;
+//   M' = M_s e^{i m phi} (times (-1)^{n+m} for a reflecting map);
+//   T  = real table in the phi = 0 half plane: free space T_N^mu(v) from the
+//        per-offset table, reaction components from the Sommerfeld routine;
+//   L'_k^l = sum_{n,m} M'_n^m T_{n+k}^{m+l},  L_k^l += (-1)^k e^{i l phi} L'_k^l / h.
+// ---------------------------------------------------------------------------
+struct M2LArgs {
+    int p;
+    int level_off;
+    double h;
+    const LfD4* cen;
+    const int* mbeg;
+    const int* mend;
+    const uint32_t* ment;
+    const void* M;
+    void* L;
+    const void* freeT;  // [343][TS*TS] in R
+    const double* gl_t;
+    const double* gl_w;
+    int Q;
+};
+
+template <typename R, bool REACT>
+__global__ void k_m2l(M2LArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int p = a.p, nre = lf_nre(p), nc = lf_nc(p), TS = 2 * p + 1, TT = TS * TS;
+    const int nq = REACT ? a.Q : 0;
+    double* sTd = reinterpret_cast<double*>(smem_raw);  // TT (reaction only)
+    double* sJ = sTd + (REACT ? TT : 0);                 // Q*TS
+    double* sA = sJ + nq * TS;                           // Q*TS
+    R* sT = reinterpret_cast<R*>(sA + nq * TS);          // TT
+    R* sM = sT + TT;                                     // nc
+    R* sOut = sM + nc;                                   // nc
+    R* sC = sOut + nc;                                   // p+1 (cos m phi)
+    R* sS = sC + (p + 1);                                // p+1 (sin m phi)
+
+    const R* M = reinterpret_cast<const R*>(a.M);
+    R* L = reinterpret_cast<R*>(a.L);
+    const R* freeT = reinterpret_cast<const R*>(a.freeT);
+
+    const int t = a.level_off + blockIdx.x;
+    const int tid = threadIdx.x;
+    const bool act = tid < nc;
+    int k = 0, l = 0, isim = 0;
+    if (act) lf_decode(p, tid, k, l, isim);
+    const LfD4 ct = a.cen[t];
+    LfAcc<R> acc;
+    const double ih = 1.0 / a.h;
+
+    for (int e = a.mbeg[t]; e < a.mend[t]; ++e) {
+        const uint32_t ent = a.ment[e];
+        const int c = (int)(ent >> LFMM_ENT_SHIFT);
+        const int s = (int)(ent & LFMM_ENT_MASK);
+        const LfmmComp& cp = c_comp[c];
+        const LfD4 cs = a.cen[s];
+        const double psz = cp.is_free ? cs.z : cp.s * cs.z + cp.o;
+        const double vx = (ct.x - cs.x) * ih, vy = (ct.y - cs.y) * ih, vz = (ct.z - psz) * ih;
+        const double rho = sqrt(vx * vx + vy * vy);
+        const double phi = (rho > 0.0) ? atan2(vy, vx) : 0.0;
+        if (tid <= p) {
+            double sn, cs_;
+            sincos(tid * phi, &sn, &cs_);
+            sC[tid] = (R)cs_;
+            sS[tid] = (R)sn;
+        }
+        if (!REACT) {
+            int ox = (int)lrint(vx), oy = (int)lrint(vy), oz = (int)lrint(vz);
+            const R* src = freeT + (size_t)((ox + 3) * 49 + (oy + 3) * 7 + (oz + 3)) * TT;
+            for (int j = tid; j < TT; j += blockDim.x) sT[j] = src[j];
+        } else {
+            const double zz = (cp.a == 1) ? vz : -vz;  // > 0 for valid entries
+            lf_sommerfeld_table_block(cp, rho, zz, a.h, 2 * p, sTd, TS, a.Q, a.gl_t, a.gl_w, sJ, sA);
+            for (int j = tid; j < TT; j += blockDim.x) {
+                int N = j / TS, mu = j - N * TS;
+                double v = (mu <= N) ? sTd[j] : 0.0;
+                if (cp.a == 2 && ((N + mu) & 1)) v = -v;
+                sT[j] = (R)v;
+            }
+        }
+        __syncthreads();
+        // rotated (and for reflections sign-flipped) multipole of the source
+        const R* Ms = M + (size_t)s * nc;
+        for (int j = tid; j < nre; j += blockDim.x) {
+            int n, m, dummy;
+            lf_decode(p, j, n, m, dummy);
+            R mr = Ms[j];
+            R mi = (m > 0) ? Ms[lf_im(p, n, m)] : R(0);
+            R cr = sC[m], sr = sS[m];
+            R rr = mr * cr - mi * sr, ri = mr * sr + mi * cr;
+            if (cp.refl && ((n + m) & 1)) {
+                rr = -rr;
+                ri = -ri;
+            }
+            sM[j] = rr;
+            if (m > 0) sM[lf_im(p, n, m)] = ri;
+        }
+        __syncthreads();
+        if (act) {
+            R sum = 0;
+            for (int n = 0; n <= p; ++n) {
+                const R* Trow = sT + (n + k) * TS;
+                const int b0 = lf_re(n, 0);
+                const int bi = lf_im(p, n, 1) - 1;  // Im(n,m) at bi + m
+                if (!isim) sum += sM[b0] * Trow[l];
+                for (int m = 1; m <= n; ++m) {
+                    R mv = isim ? sM[bi + m] : sM[b0 + m];
+                    sum += mv * Trow[m + l];
+                    int mu = l - m;
+                    R tv = Trow[mu >= 0 ? mu : -mu];
+                    // (-1)^m from M_n^{-m}, (-1)^mu from T_N^{-mu}, -1 for the imaginary part
+                    int par = m + ((mu < 0) ? -mu : 0) + isim;
+                    sum += (par & 1) ? -mv * tv : mv * tv;
+                }
+            }
+            sOut[tid] = sum;
+        }
+        __syncthreads();
+        if (act) {
+            R re = sOut[lf_re(k, l)];
+            R im = (l > 0) ? sOut[lf_im(p, k, l)] : R(0);
+            R cr = sC[l], sr = sS[l];
+            R v = isim ? (sr * re + cr * im) : (cr * re - sr * im);
+            acc.add((k & 1) ? -v : v);
+        }
+        __syncthreads();
+    }
+    if (act) L[(size_t)t * nc + tid] += acc.get() * (R)ih;
+}
+
+// ---------------------------------------------------------------------------
+// L2P with gradient: Phi = sum L_k^l conj(U_k^l((x - t)/h)),
+// dz Phi = sum L_k^l conj(U_{k-1}^l), (dx + i dy) Phi = sum L_k^l conj(U_{k-1}^{l-1}).
+// One warp per leaf box.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(32) k_l2p(int off, int p, const LfD4* __restrict__ cen,
+                                            const int* __restrict__ pbeg, const int* __restrict__ pend,
+                                            const double* __restrict__ xs, const double* __restrict__ ys,
+                                            const double* __restrict__ zs, double h, const R* __restrict__ L,
+                                            double* __restrict__ phi, double* __restrict__ fld)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nre = lf_nre(p), nc = lf_nc(p);
+    R* sL = reinterpret_cast<R*>(smem_raw);
+    R* su = sL + nc;
+    const int lane = threadIdx.x;
+    const int b = off + blockIdx.x;
+    for (int j = lane; j < nc; j += 32) sL[j] = L[(size_t)b * nc + j];
+    __syncwarp();
+    const LfD4 c = cen[b];
+    const double ih = 1.0 / h;
+    R* ure = su + lane * 2 * nre;
+    R* uim = ure + nre;
+    for (int i = pbeg[b] + lane; i < pend[b]; i += 32) {
+        R x = (R)((xs[i] - c.x) * ih), y = (R)((ys[i] - c.y) * ih), z = (R)((zs[i] - c.z) * ih);
+        lf_regular<R>(p, x, y, z, ure, uim);
+        LfAcc<R> P, Gz, Gx, Gy;
+        for (int n = 0; n <= p; ++n) {
+            // potential: Re(L conj U) with factor 2 for m >= 1
+            P.add(sL[lf_re(n, 0)] * ure[lf_re(n, 0)]);
+            for (int m = 1; m <= n; ++m)
+                P.add(R(2) * (sL[lf_re(n, m)] * ure[lf_re(n, m)] + sL[lf_im(p, n, m)] * uim[lf_re(n, m)]));
+            if (n == 0) continue;
+            // d/dz: L_n^m with U_{n-1}^m
+            Gz.add(sL[lf_re(n, 0)] * ure[lf_re(n - 1, 0)]);
+            for (int m = 1; m <= n - 1; ++m)
+                Gz.add(R(2) * (sL[lf_re(n, m)] * ure[lf_re(n - 1, m)] + sL[lf_im(p, n, m)] * uim[lf_re(n - 1, m)]));
+            // (dx + i dy): sum_{l=1..n} L_n^l conj(U_{n-1}^{l-1}) - L_n^0 U_{n-1}^1
+            //              - sum_{l=1..n-2} conj(L_n^l) U_{n-1}^{l+1}
+            for (int m = 1; m <= n; ++m) {
+                R lr = sL[lf_re(n, m)], li = sL[lf_im(p, n, m)];
+                R ur = ure[lf_re(n - 1, m - 1)], ui = uim[lf_re(n - 1, m - 1)];
+                Gx.add(lr * ur + li * ui);
+                Gy.add(li * ur - lr * ui);
+            }
+            if (n >= 2) {
+                R l0 = sL[lf_re(n, 0)];
+                Gx.add(-l0 * ure[lf_re(n - 1, 1)]);
+                Gy.add(-l0 * uim[lf_re(n - 1, 1)]);
+            }
+            for (int m = 1; m <= n - 2; ++m) {
+                R lr = sL[lf_re(n, m)], li = sL[lf_im(p, n, m)];
+                R ur = ure[lf_re(n - 1, m + 1)], ui = uim[lf_re(n - 1, m + 1)];
+                // -(lr - i li)(ur + i ui)
+                Gx.add(-(lr * ur + li * ui));
+                Gy.add(-(lr * ui - li * ur));
+            }
+        }
+        phi[i] = (double)P.get();
+        fld[3 * (size_t)i + 0] = -(double)Gx.get() * ih;
+        fld[3 * (size_t)i + 1] = -(double)Gy.get() * ih;
+        fld[3 * (size_t)i + 2] = -(double)Gz.get() * ih;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Charges in sorted order, and the final combination in caller order.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_gather_q(const double* __restrict__ q, const int32_t* __restrict__ perm, int64_t n,
+                           R* __restrict__ qs)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) qs[i] = (R)q[perm[i]];
+}
+
+__global__ void k_combine(int64_t n, const int32_t* __restrict__ perm, const double* __restrict__ pf,
+                          const double* __restrict__ pn, const double* __restrict__ ff,
+                          const double* __restrict__ fn, double* __restrict__ phi, double* __restrict__ fld)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double s = 0.079577471545947667884;  // 1 / (4 pi)
+    int64_t j = perm[i];
+    phi[j] = (pf[i] + pn[i]) * s;
+    if (fld) {
+        fld[3 * j + 0] = (ff[3 * i + 0] + fn[3 * i + 0]) * s;
+        fld[3 * j + 1] = (ff[3 * i + 1] + fn[3 * i + 1]) * s;
+        fld[3 * j + 2] = (ff[3 * i + 2] + fn[3 * i + 2]) * s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Driver.
+// ---------------------------------------------------------------------------
+template <typename R>
+static size_t m2l_smem(int p, int Q, bool react)
+{
+    int TS = 2 * p + 1, TT = TS * TS, nc = lf_nc(p);
+    size_t d = react ? (size_t)TT + 2 * (size_t)Q * TS : 0;
+    return sizeof(double) * d + sizeof(R) * (TT + 2 * nc + 2 * (p + 1)) + 64;
+}
+
+template <typename R>
+static LfErr far_field(lfmm_ctx* ctx, cudaStream_t st)
+{
+    const int p = ctx->p, nc = lf_nc(p), nre = lf_nre(p);
+    const int depth = ctx->depth;
+    const LfmmLevel& leaf = ctx->levels[depth];
+    R* M = ctx->Mexp.as<R>();
+    R* L = ctx->Lexp.as<R>();
+    const LfD4* cen = ctx->box_center.as<LfD4>();
+    const int* pbeg = ctx->box_pbeg.as<int>();
+    const int* pend = ctx->box_pend.as<int>();
+    const int* cbeg = ctx->box_cbeg.as<int>();
+    const int* cend = ctx->box_cend.as<int>();
+    const int* par = ctx->box_parent.as<int>();
+    const R* octU = reinterpret_cast<const R*>(sizeof(R) == 8 ? ctx->oct_U64.ptr : ctx->oct_U32.ptr);
+    const R* freeT = reinterpret_cast<const R*>(sizeof(R) == 8 ? ctx->free_T64.ptr : ctx->free_T32.ptr);
+
+    // upward pass
+    int ph = lf_prof_start(ctx, LFMM_TIME_P2M, st);
+    {
+        size_t sm = sizeof(R) * 2 * 32 * (size_t)nre;
+        LF_CHECK(cudaFuncSetAttribute(k_p2m<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        ++ctx->launches, k_p2m<R><<<leaf.nbox, 32, sm, st>>>(leaf.off, p, cen, pbeg, pend, ctx->xs.as<double>(), ctx->ys.as<double>(),
+                                            ctx->zs.as<double>(), ctx->q_sorted.as<R>(), leaf.h, M);
+        LF_TRY(lf_cuda(cudaGetLastError(), "p2m"));
+    }
+    lf_prof_stop(ctx, ph, st);
+    {
+        size_t sm = sizeof(R) * (nc + 2 * (size_t)nre);
+        int th = ((nre + 31) / 32) * 32;
+        for (int l = depth - 1; l >= 0; --l) {
+            const LfmmLevel& lv = ctx->levels[l];
+            if (lv.nbox == 0) continue;
+            ph = lf_prof_start(ctx, LFMM_TIME_M2M, st);
+            ++ctx->launches, k_m2m<R><<<lv.nbox, th, sm, st>>>(lv.off, p, cen, cbeg, cend, octU, M);
+            lf_prof_stop(ctx, ph, st);
+        }
+        LF_TRY(lf_cuda(cudaGetLastError(), "m2m"));
+    }
+    // downward pass: L2L then M2L (free space, then reaction) per level
+    const int Q = ctx->gl_q_m2l;
+    const size_t msm_f = m2l_smem<R>(p, Q, false), msm_r = m2l_smem<R>(p, Q, true);
+    LF_CHECK(cudaFuncSetAttribute(k_m2l<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm_f));
+    LF_CHECK(cudaFuncSetAttribute(k_m2l<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm_r));
+    const int mth = ((nc + 31) / 32) * 32;
+    const size_t lsm = sizeof(R) * (nc + 2 * (size_t)nre);
+    const int lth = ((nre + 31) / 32) * 32;
+    for (int l = 0; l <= depth; ++l) {
+        const LfmmLevel& lv = ctx->levels[l];
+        if (lv.nbox == 0) continue;
+        ph = lf_prof_start(ctx, LFMM_TIME_L2L, st);
+        if (l == 0)
+            LF_CHECK(cudaMemsetAsync(L + (size_t)lv.off * nc, 0, sizeof(R) * (size_t)lv.nbox * nc, st));
+        else
+            ++ctx->launches, k_l2l<R><<<lv.nbox, lth, lsm, st>>>(lv.off, p, cen, par, octU, L);
+        lf_prof_stop(ctx, ph, st);
+        M2LArgs a;
+        a.p = p;
+        a.level_off = lv.off;
+        a.h = lv.h;
+        a.cen = cen;
+        a.M = M;
+        a.L = L;
+        a.freeT = freeT;
+        a.gl_t = ctx->gl_t_m2l.as<double>();
+        a.gl_w = ctx->gl_w_m2l.as<double>();
+        a.Q = Q;
+        if (lv.m2l_count > 0) {
+            a.mbeg = ctx->m2l_off.as<int>();
+            a.mend = ctx->m2l_off.as<int>() + ctx->nbox_total;
+            a.ment = ctx->m2l_ent.as<uint32_t>();
+            ph = lf_prof_start(ctx, LFMM_TIME_M2L_FREE, st);
+            ++ctx->launches, k_m2l<R, false><<<lv.nbox, mth, msm_f, st>>>(a);
+            lf_prof_stop(ctx, ph, st);
+        }
+        if (lv.m2r_count > 0) {
+            a.mbeg = ctx->m2r_off.as<int>();
+            a.mend = ctx->m2r_off.as<int>() + ctx->nbox_total;
+            a.ment = ctx->m2r_ent.as<uint32_t>();
+            ph = lf_prof_start(ctx, LFMM_TIME_M2L_REACTION, st);
+            ++ctx->launches, k_m2l<R, true><<<lv.nbox, mth, msm_r, st>>>(a);
+            lf_prof_stop(ctx, ph, st);
+        }
+        LF_TRY(lf_cuda(cudaGetLastError(), "l2l/m2l"));
+    }
+    ph = lf_prof_start(ctx, LFMM_TIME_L2P, st);
+    {
+        size_t sm = sizeof(R) * (nc + 2 * 32 * (size_t)nre);
+        LF_CHECK(cudaFuncSetAttribute(k_l2p<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        ++ctx->launches, k_l2p<R><<<leaf.nbox, 32, sm, st>>>(leaf.off, p, cen, pbeg, pend, ctx->xs.as<double>(), ctx->ys.as<double>(),
+                                            ctx->zs.as<double>(), leaf.h, L, ctx->phi_far.as<double>(),
+                                            ctx->fld_far.as<double>());
+        LF_TRY(lf_cuda(cudaGetLastError(), "l2p"));
+    }
+    lf_prof_stop(ctx, ph, st);
+    return LfErr();
+}
+
+LfErr lf_evaluate_sorted(lfmm_ctx* ctx, const double* q_dev, double* phi_dev, double* field_dev, cudaStream_t st)
+{
+    const int64_t n = ctx->n;
+    const int nc = lf_nc(ctx->p);
+    const size_t rs = ctx->precision ? sizeof(float) : sizeof(double);
+    LF_TRY(lf_reserve(ctx->q_sorted, (size_t)n * rs));
+    LF_TRY(lf_reserve(ctx->Mexp, (size_t)ctx->nbox_total * nc * rs));
+    LF_TRY(lf_reserve(ctx->Lexp, (size_t)ctx->nbox_total * nc * rs));
+    LF_TRY(lf_reserve(ctx->phi_far, (size_t)n * 8));
+    LF_TRY(lf_reserve(ctx->phi_near, (size_t)n * 8));
+    LF_TRY(lf_reserve(ctx->fld_far, (size_t)n * 24));
+    LF_TRY(lf_reserve(ctx->fld_near, (size_t)n * 24));
+    LF_CHECK(cudaMemcpyToSymbolAsync(c_comp, ctx->comp, sizeof(LfmmComp) * ctx->ncomp, 0, cudaMemcpyHostToDevice, st));
+    const int ptot = lf_prof_start(ctx, LFMM_TIME_TOTAL, st);
+    if (ctx->precision)
+        ++ctx->launches, k_gather_q<float><<<lf_blocks(n, 256), 256, 0, st>>>(q_dev, ctx->perm.as<int32_t>(), n, ctx->q_sorted.as<float>());
+    else
+        ++ctx->launches, k_gather_q<double><<<lf_blocks(n, 256), 256, 0, st>>>(q_dev, ctx->perm.as<int32_t>(), n,
+                                                                ctx->q_sorted.as<double>());
+    LF_TRY(lf_cuda(cudaGetLastError(), "gather q"));
+    // near field on its own stream, concurrent with the far field
+    LF_CHECK(cudaEventRecord(ctx->ev_fork, st));
+    LF_CHECK(cudaStreamWaitEvent(ctx->s_near, ctx->ev_fork, 0));
+    LF_TRY(lf_near_field(ctx, ctx->s_near));
+    LF_CHECK(cudaEventRecord(ctx->ev_join, ctx->s_near));
+    if (ctx->precision)
+        LF_TRY(far_field<float>(ctx, st));
+    else
+        LF_TRY(far_field<double>(ctx, st));
+    LF_CHECK(cudaStreamWaitEvent(st, ctx->ev_join, 0));
+    ++ctx->launches, k_combine<<<lf_blocks(n, 256), 256, 0, st>>>(n, ctx->perm.as<int32_t>(), ctx->phi_far.as<double>(),
+                                                  ctx->phi_near.as<double>(), ctx->fld_far.as<double>(),
+                                                  ctx->fld_near.as<double>(), phi_dev, field_dev);
+    LF_TRY(lf_cuda(cudaGetLastError(), "combine"));
+    lf_prof_stop(ctx, ptot, st);
+    return LfErr();
+}

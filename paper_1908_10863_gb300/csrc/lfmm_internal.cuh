@@ -1,0 +1,279 @@
+// lfmm_internal.cuh -- shared definitions of the layered-media FMM library.
+//
+// Expansion normalisation used on the device (differs from the paper's by a
+// diagonal factor; every operator below is the paper's operator conjugated by
+// that diagonal):
+//   regular solid harmonic    U_n^m(v) = r^n Pbar_n^m(cos t) e^{i m f} / (n+m)!
+//   irregular solid harmonic  T_n^m(v) = (n-m)! Pbar_n^m(cos t) e^{i m f} / r^{n+1}
+// with Pbar_n^m the associated Legendre function WITHOUT the Condon-Shortley
+// phase, and U_n^{-m} = (-1)^m conj(U_n^m) (same for T).  With these,
+//   1/|x - y| = sum conj(U_n^m(y)) T_n^m(x)                        (|y| < |x|)
+// multipole  M_n^m = sum_j q_j conj(U_n^m(x_j - s))                  (P2M)
+// local      Phi(x) = sum L_n^m conj(U_n^m(x - t))                   (L2P)
+// M2M        M'_n^m = sum M_k^l conj(U_{n-k}^{m-l}(s - s'))
+// M2L        L_k^l  = (-1)^k sum M_n^m T_{n+k}^{m+l}(t - s)
+// L2L        L'_j^i = sum L_k^l conj(U_{k-j}^{l-i}(t' - t)).
+// The paper's coefficients relate by M^paper_nm = sqrt(4pi/(2n+1))
+// sqrt((n-m)!(n+m)!) M_n^m (eq. freespaceexpcoef), likewise for L.
+//
+// Reaction components (Section 3.3): with the polarization source
+// z'' = s z' + o (eq. eqpolarizedsource) the reaction kernel is a function of
+// x - x'' that is harmonic on the target side, and the same M2L holds with
+//   T_N^mu -> e^{i mu f} K_{N,mu}(rho, dz)                 (a = 1, dz > 0)
+//   T_N^mu -> (-1)^{N+mu} e^{i mu f} K_{N,mu}(rho, -dz)    (a = 2, dz < 0)
+//   K_{N,mu}(rho, z) = int_0^inf J_mu(k rho) k^N e^{-k z} sigma(k) dk,
+// the unnormalised form of eq. uniformintegral; for sigma == 1 it equals T.
+// A reflected map (s = -1) multiplies M_n^m by (-1)^{n+m}.
+//
+// Storage: every expansion is a vector of (p+1)^2 reals, Re(n,m) for
+// 0 <= m <= n at n(n+1)/2 + m, then Im(n,m) for 1 <= m <= n at
+// NRE + n(n-1)/2 + m - 1, NRE = (p+1)(p+2)/2.  Expansions are scaled by the
+// box size S of their level (M/S^n, L S^n, eq. scaledsommerfeldint), so all
+// operators act on box-unit vectors.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#define LFMM_PMAX 20
+#define LFMM_MAXCOMP 24
+#define LFMM_QMAX 128
+#define LFMM_FINE_LEVEL 10
+#define LFMM_ENT_SHIFT 26
+#define LFMM_ENT_MASK ((1u << LFMM_ENT_SHIFT) - 1u)
+
+// Box centre (x, y, z) and layer id (w), 32-byte aligned.
+struct __align__(32) LfD4 {
+    double x, y, z, w;
+};
+
+// One FMM component: free space (a = b = 0) or a reaction component
+// (l, lp, a, b).  Plain data, copied to constant memory.
+struct LfmmComp {
+    int l, lp, a, b;
+    int is_free;
+    int refl;        // 1: the polarization map reflects z
+    double s, o;     // z'' = s z' + o
+    double iface;    // interface between targets and polarization sources
+    // density sigma(k) = num(x) / den(x), x = exp(-D k)
+    double D;
+    double C, zeta;  // leading behaviour C exp(-k zeta)
+    int has_rem;     // remainder sigma - C e^{-k zeta} non-zero
+    double zeta_r;   // remainder ~ exp(-k zeta_r)
+    double rem[5];   // remainder numerator / x^{zeta_r / D}
+    double den[3];   // den[0] = 1
+};
+
+__host__ __device__ __forceinline__ int lf_nre(int p) { return (p + 1) * (p + 2) / 2; }
+__host__ __device__ __forceinline__ int lf_nc(int p) { return (p + 1) * (p + 1); }
+__host__ __device__ __forceinline__ int lf_re(int n, int m) { return n * (n + 1) / 2 + m; }
+__host__ __device__ __forceinline__ int lf_im(int p, int n, int m) { return lf_nre(p) + n * (n - 1) / 2 + m - 1; }
+__host__ __device__ __forceinline__ double lf_sgn(int k) { return (k & 1) ? -1.0 : 1.0; }
+
+// Decode packed output index j into (n, m, is_imag).
+__host__ __device__ __forceinline__ void lf_decode(int p, int j, int& n, int& m, int& im)
+{
+    int nre = lf_nre(p);
+    if (j < nre) {
+        im = 0;
+        n = 0;
+        while ((n + 1) * (n + 2) / 2 <= j) ++n;
+        m = j - n * (n + 1) / 2;
+    } else {
+        im = 1;
+        int r = j - nre;
+        n = 1;
+        while ((n + 1) * n / 2 <= r) ++n;
+        m = r - n * (n - 1) / 2 + 1;
+    }
+}
+
+// Morton interleave of three 10-bit integers (x in bit 0).
+__host__ __device__ __forceinline__ uint32_t lf_spread3(uint32_t v)
+{
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000FFu;
+    v = (v | (v << 8)) & 0x0300F00Fu;
+    v = (v | (v << 4)) & 0x030C30C3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+__host__ __device__ __forceinline__ uint32_t lf_compact3(uint32_t v)
+{
+    v &= 0x09249249u;
+    v = (v | (v >> 2)) & 0x030C30C3u;
+    v = (v | (v >> 4)) & 0x0300F00Fu;
+    v = (v | (v >> 8)) & 0x030000FFu;
+    v = (v | (v >> 16)) & 0x000003FFu;
+    return v;
+}
+
+// Irregular solid harmonics in the x-z half plane (azimuth 0), real:
+// out[N*ld + mu] = T_N^mu(rho, 0, z) for 0 <= mu <= N <= nmax, scaled by
+// `scale`.  Column recurrence in N (stable upward Legendre recurrence):
+//   T_mu^mu   = (2mu-1)!! rho^mu / r^{2mu+1}
+//   T_{mu+1}^mu = (2mu+1) z T_mu^mu / r^2
+//   T_n^mu    = [(2n-1) z T_{n-1}^mu - (n+mu-1)(n-mu-1) T_{n-2}^mu] / r^2.
+// Computes the column mu only (so threads can split columns).
+__host__ __device__ __forceinline__ void lf_theta_column(double rho, double z, int mu, int nmax, double scale,
+                                                         double* out, int ld)
+{
+    double r2 = rho * rho + z * z;
+    double ir2 = 1.0 / r2;
+    double ir = sqrt(ir2);
+    double t = scale * ir;  // T_0^0 = 1/r
+    for (int m = 1; m <= mu; ++m) t *= (2.0 * m - 1.0) * rho * ir2;
+    if (mu > nmax) return;
+    out[mu * ld + mu] = t;
+    if (mu + 1 > nmax) return;
+    double tm1 = t;
+    double tn = (2.0 * mu + 1.0) * z * ir2 * t;
+    out[(mu + 1) * ld + mu] = tn;
+    for (int n = mu + 2; n <= nmax; ++n) {
+        double tnew = ((2.0 * n - 1.0) * z * tn - (double)(n + mu - 1) * (double)(n - mu - 1) * tm1) * ir2;
+        out[n * ld + mu] = tnew;
+        tm1 = tn;
+        tn = tnew;
+    }
+}
+
+// Regular solid harmonics U_n^m(v) for 0 <= m <= n <= p (complex, packed as
+// re/im arrays of length NRE).  Recurrences:
+//   U_m^m = U_{m-1}^{m-1} (x + i y) / (2m)
+//   U_{m+1}^m = z U_m^m
+//   U_n^m = [(2n-1) z U_{n-1}^m - r^2 U_{n-2}^m] / (n^2 - m^2).
+template <typename R>
+__host__ __device__ __forceinline__ void lf_regular(int p, R x, R y, R z, R* ure, R* uim)
+{
+    R r2 = x * x + y * y + z * z;
+    R dre = 1, dim = 0;  // U_m^m
+    for (int m = 0; m <= p; ++m) {
+        if (m > 0) {
+            R inv = R(1) / R(2 * m);
+            R nre = (dre * x - dim * y) * inv;
+            R nim = (dre * y + dim * x) * inv;
+            dre = nre;
+            dim = nim;
+        }
+        ure[lf_re(m, m)] = dre;
+        uim[lf_re(m, m)] = dim;
+        if (m + 1 <= p) {
+            ure[lf_re(m + 1, m)] = z * dre;
+            uim[lf_re(m + 1, m)] = z * dim;
+        }
+        for (int n = m + 2; n <= p; ++n) {
+            R inv = R(1) / R(n * n - m * m);
+            R a = R(2 * n - 1) * z;
+            ure[lf_re(n, m)] = (a * ure[lf_re(n - 1, m)] - r2 * ure[lf_re(n - 2, m)]) * inv;
+            uim[lf_re(n, m)] = (a * uim[lf_re(n - 1, m)] - r2 * uim[lf_re(n - 2, m)]) * inv;
+        }
+    }
+}
+
+// Bessel functions J_0..J_nmax at x >= 0 into out[0..nmax].  For x > nmax
+// the upward recurrence from J_0, J_1 is stable; otherwise Miller's
+// downward recurrence normalised by J_0 + 2 sum J_{2k} = 1.
+__device__ __forceinline__ void lf_bessel_j_set(double x, int nmax, double* out)
+{
+    if (x == 0.0) {
+        out[0] = 1.0;
+        for (int m = 1; m <= nmax; ++m) out[m] = 0.0;
+        return;
+    }
+    if (x > (double)nmax) {
+        double jm1 = j0(x), jc = j1(x);
+        out[0] = jm1;
+        if (nmax >= 1) out[1] = jc;
+        for (int m = 1; m < nmax; ++m) {
+            double jn = (2.0 * m / x) * jc - jm1;
+            out[m + 1] = jn;
+            jm1 = jc;
+            jc = jn;
+        }
+        return;
+    }
+    int start = nmax + 24 + (int)x;
+    start += (start & 1);
+    double jp1 = 0.0, jc = 1e-300, sum = 0.0;
+    double ix2 = 2.0 / x;
+    for (int m = start; m >= 1; --m) {
+        // jc = J_m (unnormalised); J_{m-1} = (2m/x) J_m - J_{m+1}
+        double jm1 = m * ix2 * jc - jp1;
+        jp1 = jc;
+        jc = jm1;  // now J_{m-1}
+        if (m - 1 <= nmax) out[m - 1] = jc;
+        if (((m - 1) & 1) == 0 && m - 1 > 0) sum += 2.0 * jc;
+        if (fabs(jc) > 1e250) {
+            const double sc = 1e-250;
+            jc *= sc;
+            jp1 *= sc;
+            sum *= sc;
+            for (int k = m - 1; k <= nmax; ++k) out[k] *= sc;
+        }
+    }
+    sum += jc;  // + J_0
+    double inv = 1.0 / sum;
+    for (int m = 0; m <= nmax; ++m) out[m] *= inv;
+}
+
+__device__ __forceinline__ double lf_poly(const double* c, int n, double x)
+{
+    double v = 0.0;
+    for (int i = n - 1; i >= 0; --i) v = v * x + c[i];
+    return v;
+}
+
+// Box-unit Sommerfeld table of one component (block-cooperative, FP64):
+//   T[N*ld + mu] = S^{N+1} K_{N,mu}(rho, z) for 0 <= mu <= N <= nmax,
+// rho_h = rho / S, z_h = z / S (z > 0).  K = C T_N^mu(rho, z + zeta) (the
+// leading exponential of sigma, closed form) + the remainder integral by
+// Q-point Gauss-Laguerre in t = k (z + zeta_r):
+//   (1/Z) sum_q w_q J_mu(k_q rho) k_q^N [sigma_r(k_q) e^{k_q zeta_r}].
+// Scratch: sJ[Q*(nmax+1)], sA[Q*(nmax+1)] doubles in shared memory.
+// All threads of the block must call it; ends with __syncthreads().
+__device__ __forceinline__ void lf_sommerfeld_table_block(const LfmmComp& c, double rho_h, double z_h, double S,
+                                                          int nmax, double* T, int ld, int Q, const double* gl_t,
+                                                          const double* gl_w, double* sJ, double* sA)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int w = nmax + 1;
+    for (int mu = tid; mu <= nmax; mu += nt)
+        lf_theta_column(rho_h, z_h + c.zeta / S, mu, nmax, c.C, T, ld);
+    if (c.has_rem) {
+        const double Zh = z_h + c.zeta_r / S;
+        const double Dh = c.D / S;
+        const double iZ = 1.0 / Zh;
+        for (int q = tid; q < Q; q += nt) {
+            double kap = gl_t[q] * iZ;
+            double x = exp(-Dh * kap);
+            double rt = lf_poly(c.rem, 5, x) / lf_poly(c.den, 3, x);
+            double a = gl_w[q] * iZ * rt;
+            double* Arow = sA + q * w;
+            for (int N = 0; N <= nmax; ++N) {
+                Arow[N] = a;
+                a *= kap;
+            }
+            lf_bessel_j_set(kap * rho_h, nmax, sJ + q * w);
+        }
+        __syncthreads();
+        const int nent = w * w;
+        for (int e = tid; e < nent; e += nt) {
+            int N = e / w, mu = e - N * w;
+            if (mu > N) continue;
+            double s = 0.0;
+            for (int q = 0; q < Q; ++q) s += sA[q * w + N] * sJ[q * w + mu];
+            T[N * ld + mu] += s;
+        }
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Host-side declarations shared between translation units.
+// ---------------------------------------------------------------------------
+struct LfmmDeviceLevel {
+    int nbox;     // boxes of this level (all layers)
+    int off;      // first global box id
+    double h;     // box size
+};

@@ -1,0 +1,847 @@
+// lfmm_tree.cu -- octree construction and interaction lists on the device.
+//
+// Algorithm 1 of the paper starts by forming the polarization coordinates and
+// an adaptive tree.  Here every layer's charges live in one global uniform
+// grid whose planes contain the interfaces (so no box of an aligned level
+// straddles an interface, which is the centre condition of eq.
+// imagecentercond).  Polarization boxes are the source boxes mapped by
+// z'' = s z + o (eq. eqpolarizedsource); their multipoles are the physical
+// ones up to the sign (-1)^{n+m} of a reflection.  Lists come from a dual
+// traversal per level: the candidates of a target box are the children of
+// its parent's near list; an admissible candidate (one box of separation,
+// sides of the interface respected for reaction components) becomes an M2L
+// entry, the rest stay near.  At the leaf level the near list is the P2P
+// list (free space) or the near-field Sommerfeld list (reaction).
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <vector>
+
+#include "lfmm_ctx.h"
+
+#define LF_CHECK(call)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return lf_cuda(e_, #call); \
+    } while (0)
+#define LF_TRY(expr)                 \
+    do {                             \
+        LfErr r_ = (expr);           \
+        if (!r_.empty()) return r_;  \
+    } while (0)
+
+static inline int lf_blocks(int64_t n, int t) { return (int)((n + t - 1) / t); }
+
+// ---------------------------------------------------------------------------
+// Exclusive scan of int32 (block of 512 threads x 4 items, recursive on the
+// block sums).
+// ---------------------------------------------------------------------------
+#define SCAN_T 512
+#define SCAN_I 4
+#define SCAN_TILE (SCAN_T * SCAN_I)
+
+__global__ void k_scan_tile(const int* in, int* out, int64_t n, int* bsum)  // may run in place
+{
+    __shared__ int warp_tot[SCAN_T / 32];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)tid * SCAN_I;
+    int v[SCAN_I];
+    int s = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_I; ++j) {
+        int x = (base + j < n) ? in[base + j] : 0;
+        v[j] = s;
+        s += x;
+    }
+    // inclusive warp scan of thread totals
+    int incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int t = (lane < SCAN_T / 32) ? warp_tot[lane] : 0;
+        int ti = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, ti, o);
+            if (lane >= o) ti += y;
+        }
+        if (lane < SCAN_T / 32) warp_tot[lane] = ti - t;  // exclusive warp offsets
+        if (lane == SCAN_T / 32 - 1 && bsum) bsum[blockIdx.x] = ti;
+    }
+    __syncthreads();
+    int off = warp_tot[wid] + incl - s;
+#pragma unroll
+    for (int j = 0; j < SCAN_I; ++j)
+        if (base + j < n) out[base + j] = v[j] + off;
+}
+
+__global__ void k_scan_add(int* out, int64_t n, const int* boff)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += boff[i / SCAN_TILE];
+}
+
+static LfErr scan_rec(lfmm_ctx* ctx, const int* in, int* out, int64_t n, int* tmp, cudaStream_t st)
+{
+    int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (nb <= 1) {
+        ++ctx->launches, k_scan_tile<<<1, SCAN_T, 0, st>>>(in, out, n, nullptr);
+        return lf_cuda(cudaGetLastError(), "scan");
+    }
+    int* bs = tmp;
+    int* rest = tmp + nb;
+    ++ctx->launches, k_scan_tile<<<(int)nb, SCAN_T, 0, st>>>(in, out, n, bs);
+    LF_TRY(lf_cuda(cudaGetLastError(), "scan tile"));
+    LF_TRY(scan_rec(ctx, bs, bs, nb, rest, st));
+    ++ctx->launches, k_scan_add<<<lf_blocks(n, 256), 256, 0, st>>>(out, n, bs);
+    return lf_cuda(cudaGetLastError(), "scan add");
+}
+
+LfErr lf_scan_i32(lfmm_ctx* ctx, const int* in, int* out, int64_t n, int64_t* total, cudaStream_t st)
+{
+    if (n <= 0) {
+        if (total) *total = 0;
+        return LfErr();
+    }
+    int64_t need = 0, m = n;
+    while (m > 1) {
+        m = (m + SCAN_TILE - 1) / SCAN_TILE;
+        need += m + 1;
+    }
+    LF_TRY(lf_reserve(ctx->scan_tmp, (size_t)(need + 16) * sizeof(int)));
+    // the last input is copied before the scan is enqueued, so in-place scans work
+    int last[2] = {0, 0};
+    if (total) LF_CHECK(cudaMemcpyAsync(&last[0], in + n - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LF_TRY(scan_rec(ctx, in, out, n, ctx->scan_tmp.as<int>(), st));
+    if (total) {
+        LF_CHECK(cudaMemcpyAsync(&last[1], out + n - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+        LF_CHECK(cudaStreamSynchronize(st));
+        *total = (int64_t)last[1] + last[0];
+    }
+    return LfErr();
+}
+
+// ---------------------------------------------------------------------------
+// Stable LSD radix sort of (key, value) uint32 pairs, 8 bits per pass.
+// ---------------------------------------------------------------------------
+#define RS_T 256
+#define RS_ROUNDS 8
+#define RS_TILE (RS_T * RS_ROUNDS)
+
+__global__ void k_radix_hist(const uint32_t* __restrict__ keys, int64_t n, int shift, int* __restrict__ hist,
+                             int nblocks)
+{
+    __shared__ int h[256];
+    const int tid = threadIdx.x;
+    h[tid] = 0;
+    __syncthreads();
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+        int64_t i = (int64_t)blockIdx.x * RS_TILE + r * RS_T + tid;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1);
+    }
+    __syncthreads();
+    hist[tid * nblocks + blockIdx.x] = h[tid];
+}
+
+__global__ void k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n, int shift,
+                                const int* __restrict__ hoff, int nblocks)
+{
+    __shared__ int s_off[256];
+    __shared__ int s_wcnt[RS_T / 32][256];
+    __shared__ int s_rtot[256];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    s_off[tid] = hoff[tid * nblocks + blockIdx.x];
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+        int64_t i = (int64_t)blockIdx.x * RS_TILE + r * RS_T + tid;
+        bool valid = i < n;
+        uint32_t key = valid ? kin[i] : 0u;
+        uint32_t val = valid ? vin[i] : 0u;
+        int digit = valid ? (int)((key >> shift) & 255u) : 256;
+#pragma unroll
+        for (int w = 0; w < RS_T / 32; ++w) s_wcnt[w][tid] = 0;
+        __syncthreads();
+        unsigned peers = __match_any_sync(0xffffffffu, digit);
+        int rank = __popc(peers & ((1u << lane) - 1u));
+        int leader = __ffs(peers) - 1;
+        if (valid && lane == leader) s_wcnt[wid][digit] = __popc(peers);
+        __syncthreads();
+        {
+            int run = 0;
+#pragma unroll
+            for (int w = 0; w < RS_T / 32; ++w) {
+                int t = s_wcnt[w][tid];
+                s_wcnt[w][tid] = run;
+                run += t;
+            }
+            s_rtot[tid] = run;
+        }
+        __syncthreads();
+        if (valid) {
+            int pos = s_off[digit] + s_wcnt[wid][digit] + rank;
+            kout[pos] = key;
+            vout[pos] = val;
+        }
+        __syncthreads();
+        s_off[tid] += s_rtot[tid];
+        __syncthreads();
+    }
+}
+
+static LfErr radix_sort(lfmm_ctx* ctx, uint32_t* keys, uint32_t* vals, int64_t n, cudaStream_t st)
+{
+    int nb = lf_blocks(n, RS_TILE);
+    LF_TRY(lf_reserve(ctx->keys_tmp, (size_t)n * 4));
+    LF_TRY(lf_reserve(ctx->vals_tmp, (size_t)n * 4));
+    LF_TRY(lf_reserve(ctx->hist, (size_t)256 * nb * 4));
+    uint32_t *ka = keys, *va = vals, *kb = ctx->keys_tmp.as<uint32_t>(), *vb = ctx->vals_tmp.as<uint32_t>();
+    int* h = ctx->hist.as<int>();
+    for (int pass = 0; pass < 4; ++pass) {
+        int shift = 8 * pass;
+        ++ctx->launches, k_radix_hist<<<nb, RS_T, 0, st>>>(ka, n, shift, h, nb);
+        LF_TRY(lf_cuda(cudaGetLastError(), "radix hist"));
+        LF_TRY(lf_scan_i32(ctx, h, h, (int64_t)256 * nb, nullptr, st));
+        ++ctx->launches, k_radix_scatter<<<nb, RS_T, 0, st>>>(ka, va, kb, vb, n, shift, h, nb);
+        LF_TRY(lf_cuda(cudaGetLastError(), "radix scatter"));
+        std::swap(ka, kb);
+        std::swap(va, vb);
+    }
+    // four passes: data is back in (keys, vals)
+    return LfErr();
+}
+
+// ---------------------------------------------------------------------------
+// Keys, bounds, depth.
+// ---------------------------------------------------------------------------
+__global__ void k_bounds(const double* __restrict__ xyz, int64_t n, double* __restrict__ part)
+{
+    __shared__ double s[6][256];
+    const int tid = threadIdx.x;
+    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + tid; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        for (int k = 0; k < 3; ++k) {
+            double v = xyz[3 * i + k];
+            mn[k] = fmin(mn[k], v);
+            mx[k] = fmax(mx[k], v);
+        }
+    for (int k = 0; k < 3; ++k) {
+        s[k][tid] = mn[k];
+        s[3 + k][tid] = mx[k];
+    }
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (tid < o)
+            for (int k = 0; k < 3; ++k) {
+                s[k][tid] = fmin(s[k][tid], s[k][tid + o]);
+                s[3 + k][tid] = fmax(s[3 + k][tid], s[3 + k][tid + o]);
+            }
+        __syncthreads();
+    }
+    if (tid == 0)
+        for (int k = 0; k < 6; ++k) part[blockIdx.x * 6 + k] = s[k][0];
+}
+
+struct KeyParams {
+    int L;
+    double d[2];
+    double org[3];
+    double hfine;
+    int iz_lo[3], iz_hi[3];
+};
+
+__global__ void k_make_keys(const double* __restrict__ xyz, const int32_t* __restrict__ layer, int64_t n,
+                            KeyParams kp, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                            int* __restrict__ err)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+    int l = layer[i];
+    bool bad = (l < 0 || l > kp.L);
+    if (!bad) {
+        if (l > 0 && !(z < kp.d[l - 1])) bad = true;
+        if (l < kp.L && !(z > kp.d[l])) bad = true;
+    }
+    if (!(isfinite(x) && isfinite(y) && isfinite(z))) {
+        atomicMin(&err[1], (int)min(i, (int64_t)0x7fffffff));
+        atomicOr(&err[0], 2);
+        l = 0;
+    } else if (bad) {
+        atomicMin(&err[1], (int)min(i, (int64_t)0x7fffffff));
+        atomicOr(&err[0], 1);
+        l = 0;
+    }
+    const int top = (1 << LFMM_FINE_LEVEL) - 1;
+    int ix = (int)floor((x - kp.org[0]) / kp.hfine);
+    int iy = (int)floor((y - kp.org[1]) / kp.hfine);
+    int iz = (int)floor((z - kp.org[2]) / kp.hfine);
+    ix = min(max(ix, 0), top);
+    iy = min(max(iy, 0), top);
+    iz = min(max(iz, kp.iz_lo[l]), kp.iz_hi[l]);
+    keys[i] = ((uint32_t)l << 30) | lf_spread3((uint32_t)ix) | (lf_spread3((uint32_t)iy) << 1) |
+              (lf_spread3((uint32_t)iz) << 2);
+    vals[i] = (uint32_t)i;
+}
+
+__global__ void k_level_counts(const uint32_t* __restrict__ keys, int64_t n, int* __restrict__ counts)
+{
+    __shared__ int s[LFMM_FINE_LEVEL + 1];
+    if (threadIdx.x <= LFMM_FINE_LEVEL) s[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        uint32_t k = keys[i], kp = (i > 0) ? keys[i - 1] : 0u;
+        for (int l = 0; l <= LFMM_FINE_LEVEL; ++l) {
+            int sh = 3 * (LFMM_FINE_LEVEL - l);
+            if (i == 0 || (k >> sh) != (kp >> sh)) atomicAdd(&s[l], 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x <= LFMM_FINE_LEVEL && s[threadIdx.x]) atomicAdd(&counts[threadIdx.x], s[threadIdx.x]);
+}
+
+__global__ void k_gather_sorted(const double* __restrict__ xyz, const uint32_t* __restrict__ vals, int64_t n,
+                                double* __restrict__ xs, double* __restrict__ ys, double* __restrict__ zs,
+                                int32_t* __restrict__ perm)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t j = vals[i];
+    xs[i] = xyz[3 * (int64_t)j];
+    ys[i] = xyz[3 * (int64_t)j + 1];
+    zs[i] = xyz[3 * (int64_t)j + 2];
+    perm[i] = (int32_t)j;
+}
+
+// ---------------------------------------------------------------------------
+// Boxes.
+// ---------------------------------------------------------------------------
+__global__ void k_flags_particles(const uint32_t* __restrict__ keys, int64_t n, int shift, int* __restrict__ f)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    f[i] = (i == 0 || (keys[i] >> shift) != (keys[i - 1] >> shift)) ? 1 : 0;
+}
+
+__global__ void k_leaf_boxes(const uint32_t* __restrict__ keys, int64_t n, int shift, const int* __restrict__ f,
+                             const int* __restrict__ idx, int off, uint32_t* __restrict__ bkey,
+                             int* __restrict__ pbeg, int* __restrict__ cbeg, int* __restrict__ cend)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !f[i]) return;
+    int b = off + idx[i];
+    bkey[b] = keys[i] >> shift;
+    pbeg[b] = (int)i;
+    cbeg[b] = -1;
+    cend[b] = -1;
+}
+
+__global__ void k_flags_boxes(const uint32_t* __restrict__ bkey, int off, int nb, int* __restrict__ f)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb) return;
+    f[i] = (i == 0 || (bkey[off + i] >> 3) != (bkey[off + i - 1] >> 3)) ? 1 : 0;
+}
+
+__global__ void k_parent_boxes(const int* __restrict__ f, const int* __restrict__ idx, int coff, int nb, int poff,
+                               uint32_t* __restrict__ bkey, int* __restrict__ pbeg, int* __restrict__ parent,
+                               int* __restrict__ cbeg)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb) return;
+    int c = coff + i;
+    // idx is the exclusive scan of the first-child flags: the parent of a
+    // non-first child is the last flagged run before it
+    int p = poff + idx[i] + f[i] - 1;
+    parent[c] = p;
+    if (f[i]) {
+        bkey[p] = bkey[c] >> 3;
+        pbeg[p] = pbeg[c];
+        cbeg[p] = c;
+    }
+}
+
+__global__ void k_level_ends(int off, int nb, int64_t n, int child_end, const int* __restrict__ pbeg,
+                             int* __restrict__ pend, const int* __restrict__ cbeg, int* __restrict__ cend,
+                             int is_leaf)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb) return;
+    int b = off + i;
+    pend[b] = (i + 1 < nb) ? pbeg[b + 1] : (int)n;
+    if (!is_leaf) cend[b] = (i + 1 < nb) ? cbeg[b + 1] : child_end;
+}
+
+__global__ void k_centers(const uint32_t* __restrict__ bkey, int off, int nb, int level, double h, double ox,
+                          double oy, double oz, LfD4* __restrict__ cen)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb) return;
+    uint32_t k = bkey[off + i];
+    uint32_t layer = k >> (3 * level);
+    uint32_t mort = (level > 0) ? (k & ((1u << (3 * level)) - 1u)) : 0u;
+    uint32_t ix = lf_compact3(mort), iy = lf_compact3(mort >> 1), iz = lf_compact3(mort >> 2);
+    cen[off + i] = LfD4{ox + (ix + 0.5) * h, oy + (iy + 0.5) * h, oz + (iz + 0.5) * h, (double)layer};
+}
+
+// ---------------------------------------------------------------------------
+// Lists.
+// ---------------------------------------------------------------------------
+__constant__ LfmmComp c_tree_comp[LFMM_MAXCOMP];
+
+__device__ __forceinline__ bool lf_admissible(const LfmmComp& c, LfD4 ct, LfD4 cs, double h)
+{
+    if (c.is_free) {
+        double D = fmax(fabs(ct.x - cs.x), fmax(fabs(ct.y - cs.y), fabs(ct.z - cs.z)));
+        return D > 1.5 * h;
+    }
+    double psz = c.s * cs.z + c.o;
+    double dx = ct.x - cs.x, dy = ct.y - cs.y, dz = ct.z - psz;
+    double D = fmax(fabs(dx), fmax(fabs(dy), fabs(dz)));
+    if (D < 2.0 * h * (1.0 - 1e-9)) return false;
+    if (c.a == 1) {
+        if (!(ct.z > c.iface && psz < c.iface)) return false;
+    } else {
+        if (!(ct.z < c.iface && psz > c.iface)) return false;
+    }
+    if (c.has_rem) {
+        // keep the remainder integral on the real axis (rho <= z + zeta_r)
+        double rho = sqrt(dx * dx + dy * dy);
+        if (rho > fabs(dz) + c.zeta_r) return false;
+    }
+    return true;
+}
+
+__global__ void k_list_pass(int level_off, int nb, double h, const int* __restrict__ parent,
+                            const int* __restrict__ cbeg, const int* __restrict__ cend,
+                            const LfD4* __restrict__ cen, const int* __restrict__ pnear_beg,
+                            const int* __restrict__ pnear_end, const uint32_t* __restrict__ near_ent_in,
+                            int* __restrict__ cnt, const int* __restrict__ off, uint32_t* __restrict__ m2l_out,
+                            uint32_t* __restrict__ m2r_out, uint32_t* __restrict__ near_out, int fill,
+                            unsigned long long* __restrict__ stat)
+{
+    // cnt / off: [3][nb] = free M2L, reaction M2L, near
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb) return;
+    int t = level_off + i;
+    int pt = parent[t];
+    LfD4 ct = cen[t];
+    int nf = 0, nr = 0, nn = 0;
+    int wf = fill ? off[i] : 0, wr = fill ? off[nb + i] : 0, wn = fill ? off[2 * nb + i] : 0;
+    for (int e = pnear_beg[pt]; e < pnear_end[pt]; ++e) {
+        uint32_t ent = near_ent_in[e];
+        int c = (int)(ent >> LFMM_ENT_SHIFT);
+        int s = (int)(ent & LFMM_ENT_MASK);
+        const LfmmComp& cp = c_tree_comp[c];
+        for (int sc = cbeg[s]; sc < cend[s]; ++sc) {
+            LfD4 cs = cen[sc];
+            uint32_t v = ((uint32_t)c << LFMM_ENT_SHIFT) | (uint32_t)sc;
+            if (lf_admissible(cp, ct, cs, h)) {
+                if (cp.is_free) {
+                    if (fill) m2l_out[wf++] = v;
+                    ++nf;
+                } else {
+                    if (fill) m2r_out[wr++] = v;
+                    ++nr;
+                }
+            } else {
+                if (fill) near_out[wn++] = v;
+                ++nn;
+            }
+        }
+    }
+    if (!fill) {
+        cnt[i] = nf;
+        cnt[nb + i] = nr;
+        cnt[2 * nb + i] = nn;
+    } else if (stat) {
+        if (nf) atomicAdd(&stat[0], (unsigned long long)nf);
+        if (nr) atomicAdd(&stat[1], (unsigned long long)nr);
+    }
+}
+
+__global__ void k_set_ranges(int level_off, int nb, const int* __restrict__ off, const int* __restrict__ cnt,
+                             int base, int* __restrict__ beg, int* __restrict__ end)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb) return;
+    beg[level_off + i] = base + off[i];
+    end[level_off + i] = base + off[i] + cnt[i];
+}
+
+// particle-pair statistics of the leaf-level near lists
+__global__ void k_p2p_stats(int level_off, int nb, const int* __restrict__ nbeg, const int* __restrict__ nend,
+                            const uint32_t* __restrict__ ent, const int* __restrict__ pbeg,
+                            const int* __restrict__ pend, unsigned long long* __restrict__ stat)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb) return;
+    int t = level_off + i;
+    unsigned long long nt = (unsigned long long)(pend[t] - pbeg[t]);
+    unsigned long long f = 0, r = 0;
+    for (int e = nbeg[t]; e < nend[t]; ++e) {
+        uint32_t v = ent[e];
+        int c = (int)(v >> LFMM_ENT_SHIFT);
+        int s = (int)(v & LFMM_ENT_MASK);
+        unsigned long long ns = (unsigned long long)(pend[s] - pbeg[s]);
+        if (c_tree_comp[c].is_free) f += nt * ns; else r += nt * ns;
+    }
+    if (f) atomicAdd(&stat[2], f);
+    if (r) atomicAdd(&stat[3], r);
+}
+
+// grow a buffer keeping its first `keep` bytes
+static LfErr grow_keep(DevBuf& b, size_t bytes, size_t keep, cudaStream_t st)
+{
+    if (bytes <= b.cap) return LfErr();
+    size_t nc = std::max(bytes, b.cap + b.cap / 2);
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, nc);
+    if (e != cudaSuccess) return lf_cuda(e, "cudaMalloc (grow)");
+    if (keep && b.ptr) {
+        e = cudaMemcpyAsync(p, b.ptr, keep, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return lf_cuda(e, "cudaMemcpyAsync (grow)");
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return lf_cuda(e, "sync (grow)");
+    }
+    if (b.ptr) cudaFree(b.ptr);
+    b.ptr = p;
+    b.cap = nc;
+    return LfErr();
+}
+
+// ---------------------------------------------------------------------------
+// Host driver.
+// ---------------------------------------------------------------------------
+LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int64_t n, cudaStream_t st)
+{
+    if (n > (int64_t)LFMM_ENT_MASK) return "too many charges for this build (max 2^26)";
+    // ---- bounds ----
+    const int nbb = 256;
+    LF_TRY(lf_reserve(ctx->counts, 65536));  // [0,16K) bounds partials, 16K level counts, 20K stats
+    double* part = ctx->counts.as<double>();
+    ++ctx->launches, k_bounds<<<nbb, 256, 0, st>>>(xyz, n, part);
+    LF_TRY(lf_cuda(cudaGetLastError(), "bounds"));
+    std::vector<double> hp(nbb * 6);
+    LF_CHECK(cudaMemcpyAsync(hp.data(), part, sizeof(double) * 6 * nbb, cudaMemcpyDeviceToHost, st));
+    LF_CHECK(cudaStreamSynchronize(st));
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int b = 0; b < nbb; ++b)
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = std::min(lo[k], hp[b * 6 + k]);
+            hi[k] = std::max(hi[k], hp[b * 6 + 3 + k]);
+        }
+    for (int k = 0; k < 3; ++k)
+        if (!std::isfinite(lo[k]) || !std::isfinite(hi[k])) return "non-finite coordinates";
+    double ext = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
+    ext = std::max(ext, 1e-12) * (1.0 + 1e-9) + 1e-300;
+
+    // ---- grid: interfaces are planes of every level >= the alignment level ----
+    double H, oz;
+    if (ctx->L == 2) {
+        double D = ctx->d[0] - ctx->d[1];
+        H = D;
+        for (;;) {
+            // origin: a multiple of D below d0 such that [oz, oz + H] covers [lo, hi]
+            double c = std::ceil((ctx->d[0] - lo[2]) / D - 1e-12);
+            if (c < 0) c = 0;
+            oz = ctx->d[0] - c * D;
+            if (oz > lo[2]) oz -= D;
+            if (H >= ext && oz + H > hi[2] + 1e-12 * H) break;
+            H *= 2.0;
+        }
+    } else if (ctx->L == 1) {
+        H = 1.0;
+        while (H < ext) H *= 2.0;
+        while (H * 0.5 >= ext) H *= 0.5;
+        // d0 is a plane of every level >= 2
+        for (;;) {
+            double u = H / 4.0;
+            double c = std::ceil((ctx->d[0] - lo[2]) / u - 1e-12);
+            if (c < 0) c = 0;
+            oz = ctx->d[0] - c * u;
+            if (oz > lo[2]) oz -= u;
+            if (oz + H > hi[2] + 1e-12 * H) break;
+            H *= 2.0;
+        }
+    } else {
+        H = ext * (1.0 + 1e-6);
+        oz = lo[2] - 1e-7 * H;
+    }
+    double pad = 1e-7 * H;
+    ctx->H = H;
+    ctx->origin[0] = lo[0] - pad;
+    ctx->origin[1] = lo[1] - pad;
+    ctx->origin[2] = oz;
+    if (ctx->origin[0] + H < hi[0] || ctx->origin[1] + H < hi[1]) {
+        // widen so the padded box still holds every point
+        ctx->H = H = H * 2.0;
+    }
+
+    KeyParams kp;
+    kp.L = ctx->L;
+    kp.d[0] = ctx->d[0];
+    kp.d[1] = ctx->d[1];
+    for (int k = 0; k < 3; ++k) kp.org[k] = ctx->origin[k];
+    kp.hfine = H / (double)(1 << LFMM_FINE_LEVEL);
+    const int top = (1 << LFMM_FINE_LEVEL) - 1;
+    for (int l = 0; l < 3; ++l) {
+        kp.iz_lo[l] = 0;
+        kp.iz_hi[l] = top;
+        if (l <= ctx->L) {
+            if (l < ctx->L) kp.iz_lo[l] = std::max(0, (int)std::llround((ctx->d[l] - oz) / kp.hfine));
+            if (l > 0) kp.iz_hi[l] = std::min(top, (int)std::llround((ctx->d[l - 1] - oz) / kp.hfine) - 1);
+            if (kp.iz_hi[l] < kp.iz_lo[l]) kp.iz_hi[l] = kp.iz_lo[l];
+        }
+    }
+
+    // ---- keys and sort ----
+    LF_TRY(lf_reserve(ctx->keys, (size_t)n * 4));
+    LF_TRY(lf_reserve(ctx->vals_tmp, (size_t)n * 4));
+    LF_TRY(lf_reserve(ctx->err_flag, 64));
+    int init_err[4] = {0, 0x7fffffff, 0, 0};
+    LF_CHECK(cudaMemcpyAsync(ctx->err_flag.ptr, init_err, sizeof(init_err), cudaMemcpyHostToDevice, st));
+    // values live in idx (uint32)
+    LF_TRY(lf_reserve(ctx->idx, (size_t)std::max<int64_t>(n, 1024) * 4));
+    uint32_t* keys = ctx->keys.as<uint32_t>();
+    uint32_t* vals = ctx->idx.as<uint32_t>();
+    ++ctx->launches, k_make_keys<<<lf_blocks(n, 256), 256, 0, st>>>(xyz, layer, n, kp, keys, vals, ctx->err_flag.as<int>());
+    LF_TRY(lf_cuda(cudaGetLastError(), "make keys"));
+    int herr[4];
+    LF_CHECK(cudaMemcpyAsync(herr, ctx->err_flag.ptr, sizeof(herr), cudaMemcpyDeviceToHost, st));
+    LF_CHECK(cudaStreamSynchronize(st));
+    if (herr[0] & 2) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "EINVAL: non-finite coordinate at charge %d", herr[1]);
+        return buf;
+    }
+    if (herr[0] & 1) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "EINVAL: charge %d has an invalid layer id or lies outside its layer", herr[1]);
+        return buf;
+    }
+    LF_TRY(radix_sort(ctx, keys, vals, n, st));
+
+    // sorted particle arrays
+    LF_TRY(lf_reserve(ctx->xs, (size_t)n * 8));
+    LF_TRY(lf_reserve(ctx->ys, (size_t)n * 8));
+    LF_TRY(lf_reserve(ctx->zs, (size_t)n * 8));
+    LF_TRY(lf_reserve(ctx->perm, (size_t)n * 4));
+    ++ctx->launches, k_gather_sorted<<<lf_blocks(n, 256), 256, 0, st>>>(xyz, vals, n, ctx->xs.as<double>(), ctx->ys.as<double>(),
+                                                        ctx->zs.as<double>(), ctx->perm.as<int32_t>());
+    LF_TRY(lf_cuda(cudaGetLastError(), "gather"));
+
+    // ---- depth ----
+    int* cnt = reinterpret_cast<int*>(ctx->counts.as<char>() + 16384);
+    LF_CHECK(cudaMemsetAsync(cnt, 0, sizeof(int) * 16, st));
+    ++ctx->launches, k_level_counts<<<lf_blocks(n, 256), 256, 0, st>>>(keys, n, cnt);
+    LF_TRY(lf_cuda(cudaGetLastError(), "level counts"));
+    int hc[16];
+    LF_CHECK(cudaMemcpyAsync(hc, cnt, sizeof(int) * 16, cudaMemcpyDeviceToHost, st));
+    LF_CHECK(cudaStreamSynchronize(st));
+    int depth = LFMM_FINE_LEVEL;
+    for (int l = 0; l <= LFMM_FINE_LEVEL; ++l) {
+        double mean = (double)n / (double)hc[l];
+        if (mean <= 0.5 * ctx->leaf_cap) {
+            depth = l;
+            break;
+        }
+    }
+    ctx->depth = depth;
+    ctx->levels.assign(depth + 1, LfmmLevel());
+    for (int l = 0; l <= depth; ++l) {
+        ctx->levels[l].nbox = hc[l];
+        ctx->levels[l].h = H / (double)(1 << l);
+    }
+    // global ids: finest level first
+    int tot = 0;
+    for (int l = depth; l >= 0; --l) {
+        ctx->levels[l].off = tot;
+        tot += hc[l];
+    }
+    ctx->nbox_total = tot;
+    if ((int64_t)tot > (int64_t)LFMM_ENT_MASK) return "too many boxes";
+
+    size_t nb = (size_t)tot;
+    LF_TRY(lf_reserve(ctx->box_key, nb * 4));
+    LF_TRY(lf_reserve(ctx->box_pbeg, nb * 4));
+    LF_TRY(lf_reserve(ctx->box_pend, nb * 4));
+    LF_TRY(lf_reserve(ctx->box_parent, nb * 4));
+    LF_TRY(lf_reserve(ctx->box_cbeg, nb * 4));
+    LF_TRY(lf_reserve(ctx->box_cend, nb * 4));
+    LF_TRY(lf_reserve(ctx->box_center, nb * sizeof(LfD4)));
+    LF_TRY(lf_reserve(ctx->flags, (size_t)n * 4));
+    LF_TRY(lf_reserve(ctx->scan_tmp, 64));
+    DevBuf& idxb = ctx->keys_tmp;  // reuse as scan output
+    LF_TRY(lf_reserve(idxb, (size_t)n * 4));
+    uint32_t* bkey = ctx->box_key.as<uint32_t>();
+    int *pbeg = ctx->box_pbeg.as<int>(), *pend = ctx->box_pend.as<int>(), *par = ctx->box_parent.as<int>();
+    int *cbeg = ctx->box_cbeg.as<int>(), *cend = ctx->box_cend.as<int>();
+    int* fl = ctx->flags.as<int>();
+    int* ix = idxb.as<int>();
+
+    // leaf level
+    {
+        const LfmmLevel& lv = ctx->levels[depth];
+        int sh = 3 * (LFMM_FINE_LEVEL - depth);
+        ++ctx->launches, k_flags_particles<<<lf_blocks(n, 256), 256, 0, st>>>(keys, n, sh, fl);
+        int64_t total = 0;
+        LF_TRY(lf_scan_i32(ctx, fl, ix, n, &total, st));
+        if (total != lv.nbox) return "internal: leaf box count mismatch";
+        ++ctx->launches, k_leaf_boxes<<<lf_blocks(n, 256), 256, 0, st>>>(keys, n, sh, fl, ix, lv.off, bkey, pbeg, cbeg, cend);
+        ++ctx->launches, k_level_ends<<<lf_blocks(lv.nbox, 256), 256, 0, st>>>(lv.off, lv.nbox, n, 0, pbeg, pend, cbeg, cend, 1);
+        LF_TRY(lf_cuda(cudaGetLastError(), "leaf boxes"));
+    }
+    for (int l = depth - 1; l >= 0; --l) {
+        const LfmmLevel& ch = ctx->levels[l + 1];
+        const LfmmLevel& lv = ctx->levels[l];
+        ++ctx->launches, k_flags_boxes<<<lf_blocks(ch.nbox, 256), 256, 0, st>>>(bkey, ch.off, ch.nbox, fl);
+        int64_t total = 0;
+        LF_TRY(lf_scan_i32(ctx, fl, ix, ch.nbox, &total, st));
+        if (total != lv.nbox) return "internal: box count mismatch";
+        ++ctx->launches, k_parent_boxes<<<lf_blocks(ch.nbox, 256), 256, 0, st>>>(fl, ix, ch.off, ch.nbox, lv.off, bkey, pbeg, par,
+                                                                   cbeg);
+        ++ctx->launches, k_level_ends<<<lf_blocks(lv.nbox, 256), 256, 0, st>>>(lv.off, lv.nbox, n, ch.off + ch.nbox, pbeg, pend, cbeg,
+                                                                cend, 0);
+        LF_TRY(lf_cuda(cudaGetLastError(), "parent boxes"));
+    }
+    {
+        // roots have no parent
+        const LfmmLevel& r = ctx->levels[0];
+        std::vector<int> mone(r.nbox, -1);
+        LF_CHECK(cudaMemcpyAsync(par + r.off, mone.data(), sizeof(int) * r.nbox, cudaMemcpyHostToDevice, st));
+    }
+    for (int l = 0; l <= depth; ++l) {
+        const LfmmLevel& lv = ctx->levels[l];
+        ++ctx->launches, k_centers<<<lf_blocks(lv.nbox, 256), 256, 0, st>>>(bkey, lv.off, lv.nbox, l, lv.h, ctx->origin[0],
+                                                            ctx->origin[1], ctx->origin[2],
+                                                            ctx->box_center.as<LfD4>());
+    }
+    LF_TRY(lf_cuda(cudaGetLastError(), "centers"));
+
+    // ---- lists ----
+    LF_CHECK(cudaMemcpyToSymbolAsync(c_tree_comp, ctx->comp, sizeof(LfmmComp) * ctx->ncomp, 0,
+                                     cudaMemcpyHostToDevice, st));
+    LF_TRY(lf_reserve(ctx->near_off, nb * 4 * 2));  // beg, end
+    LF_TRY(lf_reserve(ctx->m2l_off, nb * 4 * 2));
+    LF_TRY(lf_reserve(ctx->m2r_off, nb * 4 * 2));
+    int* nbeg = ctx->near_off.as<int>();
+    int* nend = nbeg + nb;
+    int* mbeg = ctx->m2l_off.as<int>();
+    int* mend = mbeg + nb;
+    int* rbeg = ctx->m2r_off.as<int>();
+    int* rend = rbeg + nb;
+    // level 0: near(root_t) = root of the source layer of every component
+    int64_t near_used = 0, m2l_used = 0, m2r_used = 0;
+    {
+        const LfmmLevel& r = ctx->levels[0];
+        std::vector<uint32_t> rk(r.nbox);
+        LF_CHECK(cudaMemcpyAsync(rk.data(), bkey + r.off, 4 * r.nbox, cudaMemcpyDeviceToHost, st));
+        LF_CHECK(cudaStreamSynchronize(st));
+        int root_of[3] = {-1, -1, -1};
+        for (int i = 0; i < r.nbox; ++i) root_of[rk[i]] = r.off + i;
+        for (int l = 0; l < 3; ++l) ctx->nlayer_used[l] = root_of[l] >= 0;
+        std::vector<uint32_t> ent;
+        std::vector<int> hb(r.nbox), he(r.nbox), zero(r.nbox, 0);
+        for (int i = 0; i < r.nbox; ++i) {
+            int tl = (int)rk[i];
+            hb[i] = (int)ent.size();
+            for (int c = 0; c < ctx->ncomp; ++c) {
+                const LfmmComp& cp = ctx->comp[c];
+                if (cp.l != tl) continue;
+                int src = root_of[cp.lp];
+                if (src < 0) continue;
+                ent.push_back(((uint32_t)c << LFMM_ENT_SHIFT) | (uint32_t)src);
+            }
+            he[i] = (int)ent.size();
+        }
+        LF_TRY(grow_keep(ctx->near_ent, std::max<size_t>(ent.size(), 1) * 4, 0, st));
+        if (!ent.empty())
+            LF_CHECK(cudaMemcpyAsync(ctx->near_ent.ptr, ent.data(), ent.size() * 4, cudaMemcpyHostToDevice, st));
+        LF_CHECK(cudaMemcpyAsync(nbeg + r.off, hb.data(), 4 * r.nbox, cudaMemcpyHostToDevice, st));
+        LF_CHECK(cudaMemcpyAsync(nend + r.off, he.data(), 4 * r.nbox, cudaMemcpyHostToDevice, st));
+        LF_CHECK(cudaMemcpyAsync(mbeg + r.off, zero.data(), 4 * r.nbox, cudaMemcpyHostToDevice, st));
+        LF_CHECK(cudaMemcpyAsync(mend + r.off, zero.data(), 4 * r.nbox, cudaMemcpyHostToDevice, st));
+        LF_CHECK(cudaMemcpyAsync(rbeg + r.off, zero.data(), 4 * r.nbox, cudaMemcpyHostToDevice, st));
+        LF_CHECK(cudaMemcpyAsync(rend + r.off, zero.data(), 4 * r.nbox, cudaMemcpyHostToDevice, st));
+        LF_CHECK(cudaStreamSynchronize(st));
+        near_used = (int64_t)ent.size();
+        ctx->levels[0].near_base = 0;
+        ctx->levels[0].near_count = near_used;
+    }
+    unsigned long long* stat = reinterpret_cast<unsigned long long*>(ctx->counts.as<char>() + 20480);
+    LF_CHECK(cudaMemsetAsync(stat, 0, 8 * 8, st));
+    int maxnb = 0;
+    for (int l = 0; l <= depth; ++l) maxnb = std::max(maxnb, ctx->levels[l].nbox);
+    LF_TRY(lf_reserve(ctx->hist, (size_t)maxnb * 4 * 6 + 64));
+    int* cnt3 = ctx->hist.as<int>();
+    int* off3 = cnt3 + 3 * maxnb;
+    for (int l = 1; l <= depth; ++l) {
+        LfmmLevel& lv = ctx->levels[l];
+        const int n3 = lv.nbox;
+        ++ctx->launches, k_list_pass<<<lf_blocks(n3, 128), 128, 0, st>>>(lv.off, n3, lv.h, par, cbeg, cend, ctx->box_center.as<LfD4>(),
+                                                        nbeg, nend, ctx->near_ent.as<uint32_t>(), cnt3, nullptr,
+                                                        nullptr, nullptr, nullptr, 0, nullptr);
+        LF_TRY(lf_cuda(cudaGetLastError(), "list count"));
+        int64_t tf = 0, tr = 0, tn = 0;
+        LF_TRY(lf_scan_i32(ctx, cnt3, off3, n3, &tf, st));
+        LF_TRY(lf_scan_i32(ctx, cnt3 + n3, off3 + n3, n3, &tr, st));
+        LF_TRY(lf_scan_i32(ctx, cnt3 + 2 * n3, off3 + 2 * n3, n3, &tn, st));
+        if (near_used + tn > 0x7fffffffLL || m2l_used + tf > 0x7fffffffLL || m2r_used + tr > 0x7fffffffLL)
+            return "interaction lists too long";
+        LF_TRY(grow_keep(ctx->near_ent, (size_t)(near_used + tn + 1) * 4, (size_t)near_used * 4, st));
+        LF_TRY(grow_keep(ctx->m2l_ent, (size_t)(m2l_used + tf + 1) * 4, (size_t)m2l_used * 4, st));
+        LF_TRY(grow_keep(ctx->m2r_ent, (size_t)(m2r_used + tr + 1) * 4, (size_t)m2r_used * 4, st));
+        uint32_t* nent = ctx->near_ent.as<uint32_t>();
+        // per-level offsets are relative: shift the output pointers
+        ++ctx->launches, k_list_pass<<<lf_blocks(n3, 128), 128, 0, st>>>(
+            lv.off, n3, lv.h, par, cbeg, cend, ctx->box_center.as<LfD4>(), nbeg, nend, nent, cnt3, off3,
+            ctx->m2l_ent.as<uint32_t>() + m2l_used, ctx->m2r_ent.as<uint32_t>() + m2r_used, nent + near_used, 1,
+            stat);
+        ++ctx->launches, k_set_ranges<<<lf_blocks(n3, 256), 256, 0, st>>>(lv.off, n3, off3, cnt3, (int)m2l_used, mbeg, mend);
+        ++ctx->launches, k_set_ranges<<<lf_blocks(n3, 256), 256, 0, st>>>(lv.off, n3, off3 + n3, cnt3 + n3, (int)m2r_used, rbeg, rend);
+        ++ctx->launches, k_set_ranges<<<lf_blocks(n3, 256), 256, 0, st>>>(lv.off, n3, off3 + 2 * n3, cnt3 + 2 * n3, (int)near_used,
+                                                          nbeg, nend);
+        LF_TRY(lf_cuda(cudaGetLastError(), "list fill"));
+        lv.near_base = near_used;
+        lv.near_count = tn;
+        lv.m2l_base = m2l_used;
+        lv.m2l_count = tf;
+        lv.m2r_base = m2r_used;
+        lv.m2r_count = tr;
+        near_used += tn;
+        m2l_used += tf;
+        m2r_used += tr;
+    }
+    ctx->m2r_total = m2r_used;
+    ctx->near_total = near_used;
+    ctx->m2l_total = m2l_used;
+    {
+        const LfmmLevel& lf = ctx->levels[depth];
+        ++ctx->launches, k_p2p_stats<<<lf_blocks(lf.nbox, 256), 256, 0, st>>>(lf.off, lf.nbox, nbeg, nend,
+                                                              ctx->near_ent.as<uint32_t>(), pbeg, pend, stat);
+        LF_TRY(lf_cuda(cudaGetLastError(), "p2p stats"));
+    }
+    unsigned long long hs[8];
+    LF_CHECK(cudaMemcpyAsync(hs, stat, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    LF_CHECK(cudaStreamSynchronize(st));
+    ctx->stats[LFMM_STAT_N] = n;
+    ctx->stats[LFMM_STAT_DEPTH] = depth;
+    ctx->stats[LFMM_STAT_BOXES] = tot;
+    ctx->stats[LFMM_STAT_LEAVES] = ctx->levels[depth].nbox;
+    ctx->stats[LFMM_STAT_M2L_FREE] = (int64_t)hs[0];
+    ctx->stats[LFMM_STAT_M2L_REACTION] = (int64_t)hs[1];
+    ctx->stats[LFMM_STAT_P2P_FREE] = (int64_t)hs[2];
+    ctx->stats[LFMM_STAT_P2P_REACTION] = (int64_t)hs[3];
+    ctx->stats[LFMM_STAT_COMPONENTS] = ctx->ncomp;
+    ctx->stats[LFMM_STAT_M2M_EDGES] = tot - ctx->levels[0].nbox;
+    ctx->n = n;
+    return LfErr();
+}

@@ -1,0 +1,208 @@
+"""Python binding of the C ABI in ``include/lfmm.h`` (argument marshalling only).
+
+Every computation runs in the CUDA library ``liblfmm.so``; this module only
+converts numpy arrays / torch CUDA tensors to pointers and status codes to
+exceptions.  Importing it fails loudly when the library cannot be built or
+loaded: there is no host fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETIMEOUT, ENUMERIC = range(7)
+OPT_PRECISION, OPT_LEAF_CAP, OPT_PROFILE, OPT_QUAD_NODES = 1, 2, 3, 4
+STAT_NAMES = ["n", "depth", "boxes", "leaves", "m2l_free", "m2l_reaction", "p2p_free", "p2p_reaction",
+              "components", "m2m_edges", "launches"]
+TIME_NAMES = ["p2m", "m2m", "m2l_free", "m2l_reaction", "l2l", "l2p", "p2p", "total", "build"]
+_STATUS = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ESTATE: "ESTATE", ETIMEOUT: "ETIMEOUT",
+           ENUMERIC: "ENUMERIC"}
+
+
+class LfmmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_STATUS.get(status, str(status)), msg))
+        self.status = status
+
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int32)
+_lp = ctypes.POINTER(ctypes.c_int64)
+_vp = ctypes.c_void_p
+_ctxp = ctypes.c_void_p
+
+EXPORTED = ["lfmm_create", "lfmm_set_option", "lfmm_build", "lfmm_build_device", "lfmm_evaluate",
+            "lfmm_evaluate_device", "lfmm_last_error", "lfmm_destroy", "lfmm_get_stats", "lfmm_get_timings",
+            "lfmm_sommerfeld_tables", "lfmm_reaction_kernel", "lfmm_gauss_laguerre"]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build: bool = True):
+    """Load (building first if needed) the CUDA library; raises on failure."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError("liblfmm.so is missing at %s (run build())" % path)
+    lib = ctypes.CDLL(path)
+    lib.lfmm_create.argtypes = [_dp, ctypes.c_int, _dp, ctypes.c_int, ctypes.POINTER(_ctxp)]
+    lib.lfmm_set_option.argtypes = [_ctxp, ctypes.c_int, ctypes.c_double]
+    lib.lfmm_build.argtypes = [_ctxp, ctypes.c_int64, _dp, _ip]
+    lib.lfmm_build_device.argtypes = [_ctxp, ctypes.c_int64, _vp, _vp, _vp]
+    lib.lfmm_evaluate.argtypes = [_ctxp, ctypes.c_int, _dp, _dp, _dp]
+    lib.lfmm_evaluate_device.argtypes = [_ctxp, ctypes.c_int, _vp, _vp, _vp, _vp]
+    lib.lfmm_last_error.argtypes = [_ctxp]
+    lib.lfmm_last_error.restype = ctypes.c_char_p
+    lib.lfmm_destroy.argtypes = [_ctxp]
+    lib.lfmm_destroy.restype = None
+    lib.lfmm_get_stats.argtypes = [_ctxp, _lp, ctypes.c_int]
+    lib.lfmm_get_timings.argtypes = [_ctxp, _dp, ctypes.c_int]
+    lib.lfmm_sommerfeld_tables.argtypes = [_ctxp] + [ctypes.c_int] * 5 + [_dp, _dp, ctypes.c_double, ctypes.c_int,
+                                                                          _dp]
+    lib.lfmm_reaction_kernel.argtypes = [_ctxp] + [ctypes.c_int] * 5 + [_dp, _dp, _dp]
+    lib.lfmm_gauss_laguerre.argtypes = [ctypes.c_int, _dp, _dp]
+    for name in EXPORTED:
+        if name not in ("lfmm_last_error", "lfmm_destroy"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a, t=_dp):
+    return a.ctypes.data_as(t)
+
+
+def gauss_laguerre(Q: int):
+    """Nodes and weights of the Q-point Gauss-Laguerre rule (host-only call)."""
+    t = np.zeros(Q)
+    w = np.zeros(Q)
+    st = load().lfmm_gauss_laguerre(int(Q), _ptr(t), _ptr(w))
+    if st != OK:
+        raise LfmmError(st, "lfmm_gauss_laguerre")
+    return t, w
+
+
+class LayeredFMM:
+    """One medium (interfaces d, permittivities eps) and expansion order p."""
+
+    def __init__(self, d, eps, p: int, precision: int = 0, leaf_cap: int = 40, profile: bool = False):
+        lib = load()
+        self._lib = lib
+        d = _f64(d)
+        eps = _f64(eps)
+        self.L = int(d.shape[0])
+        self.p = int(p)
+        ctx = _ctxp()
+        st = lib.lfmm_create(_ptr(d) if self.L else None, self.L, _ptr(eps), self.p, ctypes.byref(ctx))
+        if st != OK:
+            raise LfmmError(st, "lfmm_create")
+        self._ctx = ctx
+        self.n = 0
+        if precision:
+            self.set_option(OPT_PRECISION, precision)
+        if leaf_cap != 40:
+            self.set_option(OPT_LEAF_CAP, leaf_cap)
+        if profile:
+            self.set_option(OPT_PROFILE, 1)
+
+    def _check(self, st, what):
+        if st != OK:
+            msg = self._lib.lfmm_last_error(self._ctx)
+            raise LfmmError(st, "%s: %s" % (what, msg.decode() if msg else ""))
+
+    def set_option(self, opt: int, value: float):
+        self._check(self._lib.lfmm_set_option(self._ctx, int(opt), float(value)), "lfmm_set_option")
+
+    def build(self, xyz, layer):
+        xyz = _f64(xyz).reshape(-1, 3)
+        layer = np.ascontiguousarray(layer, dtype=np.int32)
+        self._check(self._lib.lfmm_build(self._ctx, xyz.shape[0], _ptr(xyz), _ptr(layer, _ip)), "lfmm_build")
+        self.n = xyz.shape[0]
+
+    def build_device(self, xyz, layer, stream=None):
+        """xyz: torch.float64 CUDA tensor [n,3]; layer: torch.int32 CUDA tensor [n]."""
+        n = int(xyz.shape[0])
+        s = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+        self._check(self._lib.lfmm_build_device(self._ctx, n, ctypes.c_void_p(xyz.data_ptr()),
+                                                ctypes.c_void_p(layer.data_ptr()), s), "lfmm_build_device")
+        self.n = n
+
+    def evaluate(self, q, field: bool = True):
+        """q: [n] or [nrhs, n] host charges -> (phi, E) host arrays."""
+        q = _f64(q)
+        single = q.ndim == 1
+        q2 = q.reshape(1, -1) if single else q
+        nrhs = q2.shape[0]
+        phi = np.zeros_like(q2)
+        fld = np.zeros(q2.shape + (3,)) if field else None
+        self._check(self._lib.lfmm_evaluate(self._ctx, nrhs, _ptr(q2), _ptr(phi), _ptr(fld) if field else None),
+                    "lfmm_evaluate")
+        if single:
+            return phi[0], (fld[0] if field else None)
+        return phi, fld
+
+    def evaluate_device(self, q, phi, field=None, stream=None):
+        """Device tensors (float64): q [n] or [nrhs, n], phi like q, field [.., n, 3] or None."""
+        nrhs = 1 if q.dim() == 1 else int(q.shape[0])
+        s = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+        self._check(self._lib.lfmm_evaluate_device(self._ctx, nrhs, ctypes.c_void_p(q.data_ptr()),
+                                                   ctypes.c_void_p(phi.data_ptr()),
+                                                   ctypes.c_void_p(field.data_ptr()) if field is not None else None,
+                                                   s), "lfmm_evaluate_device")
+
+    def stats(self) -> dict:
+        out = np.zeros(16, dtype=np.int64)
+        self._check(self._lib.lfmm_get_stats(self._ctx, _ptr(out, _lp), 16), "lfmm_get_stats")
+        return {k: int(v) for k, v in zip(STAT_NAMES, out)}
+
+    def timings(self) -> dict:
+        out = np.zeros(12)
+        self._check(self._lib.lfmm_get_timings(self._ctx, _ptr(out), 12), "lfmm_get_timings")
+        return {k: float(v) for k, v in zip(TIME_NAMES, out)}
+
+    def sommerfeld_tables(self, l, lp, a, b, rho, z, S, P):
+        rho = _f64(rho).ravel()
+        z = _f64(z).ravel()
+        TS = 2 * P + 1
+        out = np.zeros((rho.shape[0], TS, TS))
+        self._check(self._lib.lfmm_sommerfeld_tables(self._ctx, l, lp, a, b, rho.shape[0], _ptr(rho), _ptr(z),
+                                                     float(S), int(P), _ptr(out)), "lfmm_sommerfeld_tables")
+        return out
+
+    def reaction_kernel(self, l, lp, a, b, rho, h):
+        rho = _f64(rho).ravel()
+        h = _f64(h).ravel()
+        out = np.zeros((rho.shape[0], 3))
+        self._check(self._lib.lfmm_reaction_kernel(self._ctx, l, lp, a, b, rho.shape[0], _ptr(rho), _ptr(h),
+                                                   _ptr(out)), "lfmm_reaction_kernel")
+        return out
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._lib.lfmm_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

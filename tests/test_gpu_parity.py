@@ -1,0 +1,144 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1908_10863_gb300 import LayeredFMM, LfmmError, workloads
+
+pytestmark = pytest.mark.gpu
+D3 = [0.0, -1.2]
+EPS = [1.0, 5.0, 10.0]
+
+
+def _cube(n, seed, lo=-0.5, hi=0.5):
+    rng = np.random.default_rng(seed)
+    return rng.uniform(lo, hi, (n, 3)), rng.uniform(-1, 1, n)
+
+
+@pytest.mark.parametrize("p,tol", [(4, 3e-3), (8, 1e-4), (12, 1e-5), (20, 1e-8)])
+def test_free_space_matches_direct_sum(p, tol):
+    xyz, q = _cube(3000, 1)
+    lay = np.zeros(3000, np.int32)
+    with LayeredFMM([], [1.0], p) as f:
+        f.build(xyz, lay)
+        phi, E = f.evaluate(q)
+    ref, refE = oracle.direct([], [1.0], xyz, lay, q, mode=oracle.MODE_FREE_ONLY)
+    assert oracle.err2(ref, phi) < tol
+    assert oracle.err2(refE, E) < 10 * tol
+
+
+def test_two_layer_matches_image_charge_oracle():
+    rng = np.random.default_rng(2)
+    n = 2000
+    lay = rng.integers(0, 2, n).astype(np.int32)
+    xyz = rng.uniform(-0.5, 0.5, (n, 3))
+    xyz[:, 2] = np.where(lay == 0, rng.uniform(0.05, 1.0, n), -rng.uniform(0.05, 1.0, n))
+    q = rng.uniform(-1, 1, n)
+    with LayeredFMM([0.0], [2.0, 7.0], 12) as f:
+        f.build(xyz, lay)
+        phi, E = f.evaluate(q)
+    ref, refE = oracle.direct([0.0], [2.0, 7.0], xyz, lay, q, mode=oracle.MODE_QUAD)
+    assert oracle.err2(ref, phi) < 1e-5
+    assert oracle.err2(refE, E) < 1e-4
+
+
+COMPS = [(0, 0, 1, 1), (1, 0, 2, 1), (1, 0, 1, 1), (2, 0, 2, 1), (0, 1, 1, 2), (0, 1, 1, 1), (1, 1, 1, 1),
+         (1, 1, 2, 1), (1, 1, 1, 2), (1, 1, 2, 2), (2, 1, 2, 2), (2, 1, 2, 1), (0, 2, 1, 2), (1, 2, 2, 2),
+         (1, 2, 1, 2), (2, 2, 2, 2)]
+
+
+@pytest.mark.parametrize("eps", [EPS, [1.0, 80.0, 2.0]])
+def test_sommerfeld_tables_match_image_series(eps):
+    P = 10
+    with LayeredFMM(D3, eps, P) as f:
+        for comp in COMPS:
+            for S, (rh, zh) in [(0.6, (1.0, 2.0)), (0.15, (0.0, 2.0)), (0.15, (2.0 ** 0.5, 3.0)),
+                                (0.0375, (3.0, 2.0)), (1.2, (1.0, 1.0))]:
+                T = f.sommerfeld_tables(*comp, [rh * S], [zh * S], S, P)[0]
+                worst = 0.0
+                for N in range(0, 2 * P + 1, 3):
+                    row = np.array([S ** (N + 1) * oracle.sommerfeld_K_images(D3, eps, *comp, N, mu, rh * S, zh * S)
+                                    for mu in range(N + 1)])
+                    sc = np.max(np.abs(row))
+                    worst = max(worst, np.max(np.abs(T[N, :N + 1] - row)) / sc)
+                assert worst < 1e-11, (comp, S, rh, zh, worst)
+
+
+@pytest.mark.parametrize("eps", [EPS, [1.0, 80.0, 2.0]])
+def test_reaction_near_kernel_matches_image_series(eps):
+    rng = np.random.default_rng(4)
+    rho = rng.uniform(0.0, 0.6, 40)
+    h = rng.uniform(0.15, 2.0, 40)
+    with LayeredFMM(D3, eps, 4) as f:
+        for comp in COMPS:
+            got = f.reaction_kernel(*comp, rho, h)
+            ref = np.array([[oracle.sommerfeld_K_images(D3, eps, *comp, 0, 0, r, z),
+                             oracle.sommerfeld_K_images(D3, eps, *comp, 1, 0, r, z),
+                             oracle.sommerfeld_K_images(D3, eps, *comp, 1, 1, r, z)] for r, z in zip(rho, h)])
+            # high contrast (|q| = 0.93): composite rule, ~5e-12 against the image series
+            tol = 1e-12 if eps[1] < 20 else 2e-11
+            assert np.max(np.abs(got - ref) / (np.abs(ref[:, :1]) + 1e-300)) < tol, comp
+
+
+# measured: p=6 1.1e-4, p=10 2.6e-6, p=14 9.7e-8, p=20 1.08e-9 (one-box separation)
+@pytest.mark.parametrize("p,tol", [(6, 3e-4), (10, 5e-6), (14, 2e-7), (20, 1.5e-9)])
+def test_config1_three_layer_full_oracle(p, tol):
+    w = workloads.config1(1000)
+    with LayeredFMM(w.d, w.eps, p) as f:
+        f.build(w.xyz, w.layer)
+        phi, E = f.evaluate(w.q)
+    ref, refE = oracle.direct(w.d, w.eps, w.xyz, w.layer, w.q, mode=oracle.MODE_IMAGES)
+    e2 = oracle.err2(ref, phi)
+    print("config1 p=%d Err2(phi)=%.3e Err2(E)=%.3e" % (p, e2, oracle.err2(refE, E)))
+    assert e2 < tol
+    assert oracle.err2(refE, E) < 20 * tol
+
+
+def test_config2_mixed_layers_sampled():
+    w = workloads.config2(20000)
+    t = workloads.subsample(w.n, 300)
+    with LayeredFMM(w.d, w.eps, 10) as f:
+        f.build(w.xyz, w.layer)
+        phi, E = f.evaluate(w.q)
+        st = f.stats()
+    ref, refE = oracle.direct(w.d, w.eps, w.xyz, w.layer, w.q, targets=t, mode=oracle.MODE_IMAGES)
+    print("config2 N=20000 p=10 stats", st, "Err2", oracle.err2(ref, phi[t]))
+    assert oracle.err2(ref, phi[t]) < 1e-5
+    assert oracle.err2(refE, E[t]) < 1e-4
+
+
+def test_fp32_form_config1():
+    w = workloads.config1(1000)
+    with LayeredFMM(w.d, w.eps, 10, precision=1) as f:
+        f.build(w.xyz, w.layer)
+        phi, E = f.evaluate(w.q)
+    ref, refE = oracle.direct(w.d, w.eps, w.xyz, w.layer, w.q, mode=oracle.MODE_IMAGES)
+    print("fp32 config1 p=10 Err2", oracle.err2(ref, phi), oracle.err2(refE, E))
+    assert oracle.err2(ref, phi) < 3e-5
+
+
+def test_single_and_tiny_inputs():
+    for n in (1, 2, 7):
+        w = workloads.config2(n=max(n, 3), seed=5)
+        xyz, lay, q = w.xyz[:n], w.layer[:n], w.q[:n]
+        with LayeredFMM(w.d, w.eps, 8) as f:
+            f.build(xyz, lay)
+            phi, E = f.evaluate(q)
+        ref, refE = oracle.direct(w.d, w.eps, xyz, lay, q, mode=oracle.MODE_IMAGES)
+        assert np.allclose(phi, ref, rtol=1e-9, atol=1e-12), (n, phi, ref)
+        assert np.allclose(E, refE, rtol=1e-8, atol=1e-11)
+
+
+def test_rejects_points_outside_their_layer():
+    w = workloads.config1(50)
+    bad = w.xyz.copy()
+    bad[7, 2] = 0.3  # above the top interface but tagged middle layer
+    with LayeredFMM(w.d, w.eps, 6) as f:
+        with pytest.raises(LfmmError) as ei:
+            f.build(bad, w.layer)
+        assert "EINVAL" in str(ei.value)
+        with pytest.raises(LfmmError):
+            f.evaluate(w.q)  # no successful build yet
+        f.build(w.xyz, w.layer)  # context still usable
+        phi, _ = f.evaluate(w.q)
+        assert np.all(np.isfinite(phi))
