@@ -166,6 +166,7 @@ def run_form(f, xyz_d, lay_d, q_d, phi_d, fld_d, torch, steps, warmup, flush):
     for _ in range(warmup):
         step()
     torch.cuda.synchronize()
+    launches0 = f.stats()["launches"]
     times = []
     for _ in range(steps):
         flush.fill_(1.0)  # evict L2 between steps (untimed)
@@ -177,7 +178,7 @@ def run_form(f, xyz_d, lay_d, q_d, phi_d, fld_d, torch, steps, warmup, flush):
         b.synchronize()
         times.append(a.elapsed_time(b))
     torch.cuda.synchronize()
-    return times
+    return times, f.stats()["launches"] - launches0
 
 
 def main():
@@ -233,7 +234,7 @@ def main():
         barrier(pg)
         if name == "fp32":
             clocks.start()
-        times = run_form(f, xyz_d, lay_d, q_d, phi_d, fld_d, torch, args.steps, args.warmup, flush)
+        times, launches = run_form(f, xyz_d, lay_d, q_d, phi_d, fld_d, torch, args.steps, args.warmup, flush)
         if name == "fp32":
             clk = clocks.stop()
         barrier(pg)
@@ -246,7 +247,7 @@ def main():
         f.set_option(3, 0)
         st = f.stats()
         ms = sum(times) / len(times)
-        results[name] = {"ms_per_step": ms, "times": times, "timings": tim, "stats": st,
+        results[name] = {"ms_per_step": ms, "times": times, "timings": tim, "stats": st, "launches": launches,
                          "phi": phi_d.cpu().numpy().copy(), "E": fld_d.cpu().numpy().copy()}
         if name == "fp32":
             # end-to-end through the host-buffer C ABI (copies inside the timed region)
@@ -311,7 +312,7 @@ def main():
                                    "series, %.1f s" % (len(t), w.n, dt)},
         "e2e": {"value": world * w.n / e2e_max, "unit": "particles/s", "h2d_bytes_per_step": w.n * (24 + 4 + 8),
                 "d2h_bytes_per_step": w.n * (8 + 24)},
-        "gpu_launches": None,
+        "gpu_launches": results["fp32"]["launches"],
         "clocks": clk,
     }
     print(json.dumps(line))
