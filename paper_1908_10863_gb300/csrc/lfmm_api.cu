@@ -221,7 +221,7 @@ static LfErr setup_rules(lfmm_ctx* ctx)
     LF_TRY(make_rule(ctx->near_pole, 32, ctx->near_pole ? 48 : ctx->quad_nodes, T, W));
     LF_TRY(upload_rule(ctx->gl_t_m2l, ctx->gl_w_m2l, T, W));
     ctx->gl_q_m2l = (int)T.size();
-    LF_TRY(make_rule(ctx->near_pole, 32, 32, T, W));
+    LF_TRY(make_rule(ctx->near_pole, 32, ctx->near_pole ? 48 : 32, T, W));
     LF_TRY(upload_rule(ctx->gl_t_near, ctx->gl_w_near, T, W));
     ctx->gl_q_near = (int)T.size();
     return LfErr();
@@ -470,6 +470,15 @@ static lfmm_status fail(lfmm_ctx* ctx, const LfErr& e)
     return status_of(e);
 }
 
+int lf_find_comp(const lfmm_ctx* ctx, int l, int lp, int a, int b)
+{
+    for (int c = 0; c < ctx->ncomp; ++c) {
+        const LfmmComp& cp = ctx->comp[c];
+        if (!cp.is_free && cp.l == l && cp.lp == lp && cp.a == a && cp.b == b) return c;
+    }
+    return -1;
+}
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
@@ -706,21 +715,12 @@ lfmm_status lfmm_get_timings(const lfmm_ctx* ctx, double* out, int nout)
     return LFMM_OK;
 }
 
-static int find_comp(const lfmm_ctx* ctx, int l, int lp, int a, int b)
-{
-    for (int c = 0; c < ctx->ncomp; ++c) {
-        const LfmmComp& cp = ctx->comp[c];
-        if (!cp.is_free && cp.l == l && cp.lp == lp && cp.a == a && cp.b == b) return c;
-    }
-    return -1;
-}
-
 lfmm_status lfmm_sommerfeld_tables(lfmm_ctx* ctx, int l, int lp, int a, int b, int npts, const double* rho,
                                    const double* z, double S, int P, double* out)
 {
     if (!ctx) return LFMM_EINVAL;
     ctx->err.clear();
-    int c = find_comp(ctx, l, lp, a, b);
+    int c = lf_find_comp(ctx, l, lp, a, b);
     if (c < 0) return fail(ctx, "EINVAL: no such reaction component");
     if (npts < 1 || !rho || !z || !out || P < 0 || P > LFMM_PMAX || !(S > 0.0))
         return fail(ctx, "EINVAL: bad table request");
@@ -748,7 +748,7 @@ lfmm_status lfmm_reaction_kernel(lfmm_ctx* ctx, int l, int lp, int a, int b, int
 {
     if (!ctx) return LFMM_EINVAL;
     ctx->err.clear();
-    int c = find_comp(ctx, l, lp, a, b);
+    int c = lf_find_comp(ctx, l, lp, a, b);
     if (c < 0) return fail(ctx, "EINVAL: no such reaction component");
     if (npts < 1 || !rho || !h || !out) return fail(ctx, "EINVAL: bad kernel request");
     for (int i = 0; i < npts; ++i)

@@ -132,6 +132,9 @@ LfErr lf_sommerfeld_tables_dev(lfmm_ctx* ctx, int comp, int npts, const double* 
                                int P, double* out);
 LfErr lf_reaction_kernel_dev(lfmm_ctx* ctx, int comp, int npts, const double* rho, const double* h, double* out);
 
+// index of the reaction component (l, lp, a, b), or -1 (lfmm_api.cu)
+int lf_find_comp(const lfmm_ctx* ctx, int l, int lp, int a, int b);
+
 // exclusive scan of int32 (lfmm_tree.cu); returns the total through *total (host) if non-null
 LfErr lf_scan_i32(lfmm_ctx* ctx, const int* in, int* out, int64_t n, int64_t* total, cudaStream_t st);
 

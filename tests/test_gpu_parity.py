@@ -75,8 +75,8 @@ def test_reaction_near_kernel_matches_image_series(eps):
             ref = np.array([[oracle.sommerfeld_K_images(D3, eps, *comp, 0, 0, r, z),
                              oracle.sommerfeld_K_images(D3, eps, *comp, 1, 0, r, z),
                              oracle.sommerfeld_K_images(D3, eps, *comp, 1, 1, r, z)] for r, z in zip(rho, h)])
-            # high contrast (|q| = 0.93): composite rule, ~5e-12 against the image series
-            tol = 1e-12 if eps[1] < 20 else 2e-11
+            # high contrast (|q| = 0.93): composite Legendre/Laguerre rule, ~3e-13
+            tol = 1e-12
             assert np.max(np.abs(got - ref) / (np.abs(ref[:, :1]) + 1e-300)) < tol, comp
 
 
