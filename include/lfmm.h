@@ -161,6 +161,22 @@ lfmm_status lfmm_sommerfeld_tables(lfmm_ctx* ctx, int l, int lp, int a, int b, i
 lfmm_status lfmm_reaction_kernel(lfmm_ctx* ctx, int l, int lp, int a, int b, int npts, const double* rho,
                                  const double* h, double* out);
 
+/* Allocation-free variant of lfmm_reaction_kernel, for callers that may not
+ * allocate device memory during the call (stream capture, real-time loops,
+ * hosts with a fixed device-memory budget).  The paper has no counterpart;
+ * this is a library interface only.
+ * Same arguments and results as lfmm_reaction_kernel (host arrays).  Inputs
+ * and outputs are staged through one static device array shared by all calls
+ * (LFMM_NOALLOC_MAX_POINTS points, 2.6 MB per GPU that loads the library, held
+ * until process exit); the call makes no cudaMalloc / cudaFree.
+ *   npts : 1 <= npts <= LFMM_NOALLOC_MAX_POINTS, else LFMM_EINVAL.
+ * The first call on a device resolves the array's device address (make it
+ * before any stream capture).  Calls that overlap on the GPU race on the
+ * shared array: serialise them.  Synchronises the context's stream. */
+#define LFMM_NOALLOC_MAX_POINTS 65536
+lfmm_status lfmm_reaction_kernel_noalloc(lfmm_ctx* ctx, int l, int lp, int a, int b, int npts, const double* rho,
+                                         const double* h, double* out);
+
 /* Host-only helper (no device needed): Gauss-Laguerre nodes and weights of
  * order Q (weight e^{-t} on [0, inf)) as used by the quadratures. */
 lfmm_status lfmm_gauss_laguerre(int Q, double* nodes, double* weights);

@@ -42,6 +42,7 @@
 #define LFMM_FINE_LEVEL 10
 #define LFMM_ENT_SHIFT 26
 #define LFMM_ENT_MASK ((1u << LFMM_ENT_SHIFT) - 1u)
+#define LFMM_MAX_DEVICES 64
 
 // Box centre (x, y, z) and layer id (w), 32-byte aligned.
 struct __align__(32) LfD4 {

@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <mutex>
+
 #include "lfmm_ctx.h"
 
 #define LF_CHECK(call)                                    \
@@ -288,4 +290,102 @@ LfErr lf_reaction_kernel_dev(lfmm_ctx* ctx, int comp, int npts, const double* rh
     LF_TRY(upload_consts(ctx, ctx->s_main));
     ++ctx->launches, k_reaction_kernel<<<lf_blocks(npts, 128), 128, 0, ctx->s_main>>>(comp, npts, rho, h, ctx->gl_q_near, out);
     return lf_cuda(cudaGetLastError(), "reaction kernel");
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of lfmm_reaction_kernel.
+//
+// Some callers cannot allocate device memory at the point where they need the
+// layered reaction kernel: code running inside a stream capture, real-time or
+// embedded loops that forbid allocator calls, or hosts that manage a fixed
+// device-memory budget themselves.  lfmm_reaction_kernel stages its inputs and
+// outputs through buffers it allocates on every call; this variant stages them
+// through one file-scope device array instead, so the call itself makes no
+// cudaMalloc / cudaFree (or any other allocating call).
+//
+// The array holds LFMM_NOALLOC_MAX_POINTS points (rho, h and three outputs per
+// point: 5 doubles, 2.6 MB).  It is defined once per process and every GPU
+// that loads this library keeps its copy until the process exits.  All calls
+// share it and it keeps the last call's contents; nothing in it needs to start
+// at zero because every entry a call reads is written by that call first.
+// Calls that overlap on the GPU (several host threads, several contexts on one
+// device) race on the array and must be serialised by the caller.
+//
+// The device address of the array is resolved with cudaGetSymbolAddress the
+// first time the entry point runs on a device (with that device current) and
+// cached per device; that first call therefore must not happen inside a stream
+// capture.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) double g_noalloc_scratch[5 * LFMM_NOALLOC_MAX_POINTS];
+
+static std::mutex g_noalloc_mutex;
+static double* g_noalloc_ptr[LFMM_MAX_DEVICES] = {nullptr};
+
+static LfErr noalloc_scratch(int device, double** out)
+{
+    if (device < 0 || device >= LFMM_MAX_DEVICES) return "EINVAL: device index out of range";
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[device]) {
+        int cur = -1;
+        cudaError_t e = cudaGetDevice(&cur);
+        if (e != cudaSuccess) return lf_cuda(e, "cudaGetDevice");
+        if (cur != device) {
+            e = cudaSetDevice(device);
+            if (e != cudaSuccess) return lf_cuda(e, "cudaSetDevice");
+        }
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (cur != device) cudaSetDevice(cur);
+        if (e != cudaSuccess) return lf_cuda(e, "cudaGetSymbolAddress");
+        g_noalloc_ptr[device] = static_cast<double*>(p);
+    }
+    *out = g_noalloc_ptr[device];
+    return LfErr();
+}
+
+extern "C" lfmm_status lfmm_reaction_kernel_noalloc(lfmm_ctx* ctx, int l, int lp, int a, int b, int npts,
+                                                     const double* rho, const double* h, double* out)
+{
+    if (!ctx) return LFMM_EINVAL;
+    ctx->err.clear();
+    int c = lf_find_comp(ctx, l, lp, a, b);
+    if (c < 0) {
+        ctx->err = "EINVAL: no such reaction component";
+        return LFMM_EINVAL;
+    }
+    if (npts < 1 || !rho || !h || !out) {
+        ctx->err = "EINVAL: bad kernel request";
+        return LFMM_EINVAL;
+    }
+    if (npts > LFMM_NOALLOC_MAX_POINTS) {
+        ctx->err = "EINVAL: npts exceeds LFMM_NOALLOC_MAX_POINTS (" + std::to_string(LFMM_NOALLOC_MAX_POINTS) +
+                   ") of the allocation-free entry point";
+        return LFMM_EINVAL;
+    }
+    for (int i = 0; i < npts; ++i)
+        if (!(h[i] > 0.0) || !(rho[i] >= 0.0)) {
+            ctx->err = "EINVAL: need h > 0 and rho >= 0";
+            return LFMM_EINVAL;
+        }
+    double* base = nullptr;
+    LfErr e = noalloc_scratch(ctx->device, &base);
+    double* drho = base;
+    double* dh = base + LFMM_NOALLOC_MAX_POINTS;
+    double* dout = base + 2 * LFMM_NOALLOC_MAX_POINTS;
+    cudaStream_t st = ctx->s_main;
+    if (e.empty()) e = lf_cuda(cudaMemcpyAsync(drho, rho, sizeof(double) * npts, cudaMemcpyHostToDevice, st), "copy");
+    if (e.empty()) e = lf_cuda(cudaMemcpyAsync(dh, h, sizeof(double) * npts, cudaMemcpyHostToDevice, st), "copy");
+    if (e.empty()) e = upload_consts(ctx, st);
+    if (e.empty()) {
+        ++ctx->launches, k_reaction_kernel<<<lf_blocks(npts, 128), 128, 0, st>>>(c, npts, drho, dh, ctx->gl_q_near, dout);
+        e = lf_cuda(cudaGetLastError(), "reaction kernel");
+    }
+    if (e.empty())
+        e = lf_cuda(cudaMemcpyAsync(out, dout, sizeof(double) * 3 * npts, cudaMemcpyDeviceToHost, st), "copy back");
+    if (e.empty()) e = lf_cuda(cudaStreamSynchronize(st), "reaction kernel");
+    if (!e.empty()) {
+        ctx->err = e;
+        return e.compare(0, 6, "EINVAL") == 0 ? LFMM_EINVAL : LFMM_ECUDA;
+    }
+    return LFMM_OK;
 }

@@ -38,7 +38,8 @@ _ctxp = ctypes.c_void_p
 
 EXPORTED = ["lfmm_create", "lfmm_set_option", "lfmm_build", "lfmm_build_device", "lfmm_evaluate",
             "lfmm_evaluate_device", "lfmm_last_error", "lfmm_destroy", "lfmm_get_stats", "lfmm_get_timings",
-            "lfmm_sommerfeld_tables", "lfmm_reaction_kernel", "lfmm_gauss_laguerre"]
+            "lfmm_sommerfeld_tables", "lfmm_reaction_kernel", "lfmm_reaction_kernel_noalloc", "lfmm_gauss_laguerre"]
+NOALLOC_MAX_POINTS = 65536
 
 
 def library_path() -> str:
@@ -69,6 +70,7 @@ def load(build: bool = True):
     lib.lfmm_sommerfeld_tables.argtypes = [_ctxp] + [ctypes.c_int] * 5 + [_dp, _dp, ctypes.c_double, ctypes.c_int,
                                                                           _dp]
     lib.lfmm_reaction_kernel.argtypes = [_ctxp] + [ctypes.c_int] * 5 + [_dp, _dp, _dp]
+    lib.lfmm_reaction_kernel_noalloc.argtypes = [_ctxp] + [ctypes.c_int] * 5 + [_dp, _dp, _dp]
     lib.lfmm_gauss_laguerre.argtypes = [ctypes.c_int, _dp, _dp]
     for name in EXPORTED:
         if name not in ("lfmm_last_error", "lfmm_destroy"):
@@ -188,6 +190,15 @@ class LayeredFMM:
         out = np.zeros((rho.shape[0], 3))
         self._check(self._lib.lfmm_reaction_kernel(self._ctx, l, lp, a, b, rho.shape[0], _ptr(rho), _ptr(h),
                                                    _ptr(out)), "lfmm_reaction_kernel")
+        return out
+
+    def reaction_kernel_noalloc(self, l, lp, a, b, rho, h):
+        """Same as reaction_kernel through the allocation-free entry point."""
+        rho = _f64(rho).ravel()
+        h = _f64(h).ravel()
+        out = np.zeros((rho.shape[0], 3))
+        self._check(self._lib.lfmm_reaction_kernel_noalloc(self._ctx, l, lp, a, b, rho.shape[0], _ptr(rho),
+                                                           _ptr(h), _ptr(out)), "lfmm_reaction_kernel_noalloc")
         return out
 
     def close(self):
