@@ -119,6 +119,7 @@ enum {
     LFMM_STAT_COMPONENTS = 8,     /* free + reaction components of the medium */
     LFMM_STAT_M2M_EDGES = 9,      /* parent-child edges (also the L2L count) */
     LFMM_STAT_LAUNCHES = 10,      /* kernels launched by this context since lfmm_create (cumulative) */
+    LFMM_STAT_REACTION_KEYS = 11, /* distinct (component, level, offset) reaction M2L operators */
     LFMM_STAT_COUNT = 16
 };
 lfmm_status lfmm_get_stats(const lfmm_ctx* ctx, int64_t* out, int nout);

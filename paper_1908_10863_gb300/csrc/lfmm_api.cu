@@ -515,6 +515,7 @@ lfmm_status lfmm_create(const double* d, int L, const double* eps, int p, lfmm_c
     if (e.empty()) e = lf_cuda(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming), "event");
     if (e.empty()) e = setup_rules(ctx);
     if (e.empty()) e = setup_tables(ctx);
+    if (e.empty()) e = lf_setup_m2l_ops(ctx);
     if (!e.empty()) {
         lfmm_status s = status_of(e);
         lfmm_destroy(ctx);
@@ -690,7 +691,11 @@ void lfmm_destroy(lfmm_ctx* ctx)
                       &ctx->box_parent, &ctx->box_cbeg, &ctx->box_cend, &ctx->box_center, &ctx->flags, &ctx->idx,
                       &ctx->near_off, &ctx->near_ent, &ctx->m2l_off, &ctx->m2l_ent, &ctx->m2r_off, &ctx->m2r_ent,
                       &ctx->q_sorted, &ctx->Mexp, &ctx->Lexp, &ctx->phi_far, &ctx->phi_near, &ctx->fld_far,
-                      &ctx->fld_near, &ctx->q_stage, &ctx->phi_stage, &ctx->fld_stage};
+                      &ctx->fld_near, &ctx->q_stage, &ctx->phi_stage, &ctx->fld_stage, &ctx->m2l_A64, &ctx->m2l_A32,
+                      &ctx->m2l_cls, &ctx->m2l_inv, &ctx->m2l_slots, &ctx->m2l_keys, &ctx->m2l_sorted,
+                      &ctx->m2l_tiles, &ctx->m2l_levelh, &ctx->m2r_keys, &ctx->m2r_order,
+                      &ctx->m2r_tgt, &ctx->m2r_kstart, &ctx->m2r_kval, &ctx->m2r_tables, &ctx->m2r_levelh,
+                      &ctx->m2r_batches};
     for (DevBuf* b : bufs) lf_free(*b);
     for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);

@@ -98,6 +98,13 @@ struct lfmm_ctx {
     DevBuf near_off, near_ent, m2l_off, m2l_ent, m2r_off, m2r_ent;
     int64_t near_total = 0, m2l_total = 0, m2r_total = 0;
 
+    // free-space M2L as per-offset GEMMs (p <= 15)
+    DevBuf m2l_A64, m2l_A32, m2l_cls, m2l_inv, m2l_slots, m2l_keys, m2l_sorted, m2l_tiles, m2l_levelh;
+    int m2l_rm = 0, m2l_rp = 0, m2l_ntiles = 0;
+    // reaction M2L grouped by geometry key on interface-aligned levels
+    DevBuf m2r_keys, m2r_order, m2r_tgt, m2r_kstart, m2r_kval, m2r_tables, m2r_levelh, m2r_batches;
+    int m2r_nkeys = 0, m2r_nbatch = 0, m2r_keyed_from = 0;
+
     // evaluation buffers
     DevBuf q_sorted;            // R [n]
     DevBuf Mexp, Lexp;          // R [nbox][(p+1)^2]
@@ -122,6 +129,16 @@ LfErr lf_cuda(cudaError_t e, const char* what);
 
 // ---- tree construction (lfmm_tree.cu) ----
 LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz_dev, const int32_t* layer_dev, int64_t n, cudaStream_t st);
+
+// ---- free-space M2L GEMM (lfmm_m2l.cu) ----
+LfErr lf_setup_m2l_ops(lfmm_ctx* ctx);
+LfErr lf_prepare_m2l(lfmm_ctx* ctx, cudaStream_t st);
+LfErr lf_m2l_gemm(lfmm_ctx* ctx, cudaStream_t st);
+// ---- reaction M2L by geometry key (lfmm_m2r.cu) ----
+LfErr lf_prepare_m2r(lfmm_ctx* ctx, cudaStream_t st);
+LfErr lf_m2r_apply(lfmm_ctx* ctx, cudaStream_t st);
+// stable LSD radix sort of uint32 (key, value) pairs (lfmm_tree.cu); uses keys_tmp, vals_tmp, hist
+LfErr lf_radix_sort(lfmm_ctx* ctx, uint32_t* keys, uint32_t* vals, int64_t n, cudaStream_t st);
 
 // ---- evaluation (lfmm_fmm.cu, lfmm_near.cu) ----
 LfErr lf_evaluate_sorted(lfmm_ctx* ctx, const double* q_dev, double* phi_dev, double* field_dev, cudaStream_t st);

@@ -199,7 +199,7 @@ __global__ void k_m2m(int off, int p, const LfD4* __restrict__ cen, const int* _
 
 // ---------------------------------------------------------------------------
 // L2L (eq. letole): L_c(j,i) = sum_{k>=j,l} 2^{-j} L_p(k,l) conj(U_{k-j}^{l-i}(d)).
-// One block per child box; overwrites L of the child.
+// One block per child box; adds into L of the child (which holds its M2L).
 // ---------------------------------------------------------------------------
 template <typename R>
 __global__ void k_l2l(int off, int p, const LfD4* __restrict__ cen, const int* __restrict__ parent,
@@ -237,8 +237,8 @@ __global__ void k_l2l(int off, int p, const LfD4* __restrict__ cen, const int* _
     }
     R sc = 1;
     for (int q = 0; q < jn; ++q) sc *= R(0.5);
-    L[(size_t)b * nc + lf_re(jn, mm)] = sc * ar;
-    if (mm > 0) L[(size_t)b * nc + lf_im(p, jn, mm)] = sc * ai;
+    L[(size_t)b * nc + lf_re(jn, mm)] += sc * ar;
+    if (mm > 0) L[(size_t)b * nc + lf_im(p, jn, mm)] += sc * ai;
 }
 
 // ---------------------------------------------------------------------------
@@ -517,7 +517,7 @@ static LfErr far_field(lfmm_ctx* ctx, cudaStream_t st)
         }
         LF_TRY(lf_cuda(cudaGetLastError(), "m2m"));
     }
-    // downward pass: L2L then M2L (free space, then reaction) per level
+    // downward pass: all M2L into zeroed L, then L2L top-down (child += shifted parent)
     const int Q = ctx->gl_q_m2l;
     const size_t msm_f = m2l_smem<R>(p, Q, false), msm_r = m2l_smem<R>(p, Q, true);
     LF_CHECK(cudaFuncSetAttribute(k_m2l<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm_f));
@@ -525,15 +525,21 @@ static LfErr far_field(lfmm_ctx* ctx, cudaStream_t st)
     const int mth = ((nc + 31) / 32) * 32;
     const size_t lsm = sizeof(R) * (nc + 2 * (size_t)nre);
     const int lth = ((nre + 31) / 32) * 32;
+    LF_CHECK(cudaMemsetAsync(L, 0, sizeof(R) * (size_t)ctx->nbox_total * nc, st));
+    const bool gemm = ctx->m2l_ntiles > 0;
+    if (gemm) {
+        ph = lf_prof_start(ctx, LFMM_TIME_M2L_FREE, st);
+        LF_TRY(lf_m2l_gemm(ctx, st));
+        lf_prof_stop(ctx, ph, st);
+    }
+    if (ctx->m2r_nbatch > 0) {
+        ph = lf_prof_start(ctx, LFMM_TIME_M2L_REACTION, st);
+        LF_TRY(lf_m2r_apply(ctx, st));
+        lf_prof_stop(ctx, ph, st);
+    }
     for (int l = 0; l <= depth; ++l) {
         const LfmmLevel& lv = ctx->levels[l];
         if (lv.nbox == 0) continue;
-        ph = lf_prof_start(ctx, LFMM_TIME_L2L, st);
-        if (l == 0)
-            LF_CHECK(cudaMemsetAsync(L + (size_t)lv.off * nc, 0, sizeof(R) * (size_t)lv.nbox * nc, st));
-        else
-            ++ctx->launches, k_l2l<R><<<lv.nbox, lth, lsm, st>>>(lv.off, p, cen, par, octU, L);
-        lf_prof_stop(ctx, ph, st);
         M2LArgs a;
         a.p = p;
         a.level_off = lv.off;
@@ -545,7 +551,7 @@ static LfErr far_field(lfmm_ctx* ctx, cudaStream_t st)
         a.gl_t = ctx->gl_t_m2l.as<double>();
         a.gl_w = ctx->gl_w_m2l.as<double>();
         a.Q = Q;
-        if (lv.m2l_count > 0) {
+        if (!gemm && lv.m2l_count > 0) {
             a.mbeg = ctx->m2l_off.as<int>();
             a.mend = ctx->m2l_off.as<int>() + ctx->nbox_total;
             a.ment = ctx->m2l_ent.as<uint32_t>();
@@ -553,7 +559,7 @@ static LfErr far_field(lfmm_ctx* ctx, cudaStream_t st)
             ++ctx->launches, k_m2l<R, false><<<lv.nbox, mth, msm_f, st>>>(a);
             lf_prof_stop(ctx, ph, st);
         }
-        if (lv.m2r_count > 0) {
+        if (lv.m2r_count > 0 && l < ctx->m2r_keyed_from) {
             a.mbeg = ctx->m2r_off.as<int>();
             a.mend = ctx->m2r_off.as<int>() + ctx->nbox_total;
             a.ment = ctx->m2r_ent.as<uint32_t>();
@@ -561,7 +567,15 @@ static LfErr far_field(lfmm_ctx* ctx, cudaStream_t st)
             ++ctx->launches, k_m2l<R, true><<<lv.nbox, mth, msm_r, st>>>(a);
             lf_prof_stop(ctx, ph, st);
         }
-        LF_TRY(lf_cuda(cudaGetLastError(), "l2l/m2l"));
+        LF_TRY(lf_cuda(cudaGetLastError(), "m2l"));
+    }
+    for (int l = 1; l <= depth; ++l) {
+        const LfmmLevel& lv = ctx->levels[l];
+        if (lv.nbox == 0) continue;
+        ph = lf_prof_start(ctx, LFMM_TIME_L2L, st);
+        ++ctx->launches, k_l2l<R><<<lv.nbox, lth, lsm, st>>>(lv.off, p, cen, par, octU, L);
+        lf_prof_stop(ctx, ph, st);
+        LF_TRY(lf_cuda(cudaGetLastError(), "l2l"));
     }
     ph = lf_prof_start(ctx, LFMM_TIME_L2P, st);
     {

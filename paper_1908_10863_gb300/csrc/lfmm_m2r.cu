@@ -1,0 +1,410 @@
+// lfmm_m2r.cu -- reaction-component M2L (eqs. metoleimage1, coefintable)
+// grouped by geometry key.
+//
+// On a level whose grid planes contain the interfaces, every polarization
+// box is a grid box, so the offset o = (t - P(s))/h of a reaction M2L pair is
+// an integer vector in [-3,3]^3.  The translation operator then depends only
+// on the key (component, level, offset): the Sommerfeld table of the pair
+// (leading image in closed form + Gauss-Laguerre remainder, all (N, mu)) is
+// computed once per key at build time, and at evaluation time the pairs of
+// one key are applied as batched GEMMs Y = A_key X (X = 64 gathered source
+// multipoles), added atomically into the targets' local expansions.  The
+// reflection sign (-1)^{n+m} of the multipole (s = -1 maps) and the
+// (-1)^{N+mu} of an a = 2 component are folded into A_key.
+// Pairs on coarser, non-aligned levels keep the per-pair kernel.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "lfmm_ctx.h"
+
+#define LF_CHECK(call)                                    \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return lf_cuda(e_, #call); \
+    } while (0)
+#define LF_TRY(expr)                \
+    do {                            \
+        LfErr r_ = (expr);          \
+        if (!r_.empty()) return r_; \
+    } while (0)
+
+static inline int lf_blocks(int64_t n, int t) { return (int)((n + t - 1) / t); }
+
+#define R_TB 64   // pairs per batch
+#define R_T 256   // threads: 16 row groups x 16 column groups
+#define KEY_NONE 0xffffffffu
+
+__constant__ LfmmComp c_rcomp[LFMM_MAXCOMP];
+
+// key = comp (5 bits) | level (4 bits) | offset index (12 bits, offsets in [-7, 7]^3)
+#define R_OR 7
+#define R_OW (2 * R_OR + 1)
+__host__ __device__ __forceinline__ uint32_t rkey(int c, int l, int ox, int oy, int oz)
+{
+    return ((uint32_t)c << 16) | ((uint32_t)l << 12) | (uint32_t)(((ox + R_OR) * R_OW + (oy + R_OR)) * R_OW + (oz + R_OR));
+}
+__host__ __device__ __forceinline__ void rkey_decode(uint32_t key, int& c, int& l, int& ox, int& oy, int& oz)
+{
+    c = (int)(key >> 16);
+    l = (int)((key >> 12) & 15u);
+    int oi = (int)(key & 4095u);
+    ox = oi / (R_OW * R_OW) - R_OR;
+    oy = (oi / R_OW) % R_OW - R_OR;
+    oz = oi % R_OW - R_OR;
+}
+
+__global__ void k_m2r_keys(int off, int nb, double h, const LfD4* __restrict__ cen, const int* __restrict__ rbeg,
+                           const int* __restrict__ rend, const uint32_t* __restrict__ rent, int level,
+                           uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, int* __restrict__ tgt,
+                           int* __restrict__ bad)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb) return;
+    int t = off + i;
+    LfD4 ct = cen[t];
+    double ih = 1.0 / h;
+    for (int e = rbeg[t]; e < rend[t]; ++e) {
+        uint32_t v = rent[e];
+        int c = (int)(v >> LFMM_ENT_SHIFT);
+        int s = (int)(v & LFMM_ENT_MASK);
+        const LfmmComp& cp = c_rcomp[c];
+        LfD4 cs = cen[s];
+        double vx = (ct.x - cs.x) * ih, vy = (ct.y - cs.y) * ih, vz = (ct.z - (cp.s * cs.z + cp.o)) * ih;
+        int ox = (int)lrint(vx), oy = (int)lrint(vy), oz = (int)lrint(vz);
+        bool ok = fabs(vx - ox) < 1e-6 && fabs(vy - oy) < 1e-6 && fabs(vz - oz) < 1e-6 && ox >= -R_OR &&
+                  ox <= R_OR && oy >= -R_OR && oy <= R_OR && oz >= -R_OR && oz <= R_OR;
+        if (!ok) atomicAdd(bad, 1);
+        keys[e] = ok ? rkey(c, level, ox, oy, oz) : KEY_NONE;
+        vals[e] = (uint32_t)e;
+        tgt[e] = t;
+    }
+}
+
+__global__ void k_key_flags(const uint32_t* __restrict__ keys, int n, int* __restrict__ f)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    f[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1 : 0;
+}
+
+__global__ void k_key_starts(const uint32_t* __restrict__ keys, int n, const int* __restrict__ f,
+                             const int* __restrict__ idx, int* __restrict__ kstart, uint32_t* __restrict__ kval)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !f[i]) return;
+    kstart[idx[i]] = i;
+    kval[idx[i]] = keys[i];
+}
+
+// One block per key: the box-unit table (lead + remainder) with the a = 2 sign.
+__global__ void k_m2r_tables(const uint32_t* __restrict__ kval, int nkeys, const double* __restrict__ levelh, int P,
+                             const double* __restrict__ gt, const double* __restrict__ gw, int Q,
+                             double* __restrict__ tables)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int TS = 2 * P + 1, TT = TS * TS;
+    double* sT = reinterpret_cast<double*>(smem_raw);
+    double* sJ = sT + TT;
+    double* sA = sJ + Q * TS;
+    const int k = blockIdx.x;
+    int c, l, ox, oy, oz;
+    rkey_decode(kval[k], c, l, ox, oy, oz);
+    const LfmmComp& cp = c_rcomp[c];
+    const double rho = sqrt((double)(ox * ox + oy * oy));
+    const double zz = (cp.a == 1) ? (double)oz : (double)(-oz);
+    for (int j = threadIdx.x; j < TT; j += blockDim.x) sT[j] = 0.0;
+    __syncthreads();
+    lf_sommerfeld_table_block(cp, rho, zz, levelh[l], 2 * P, sT, TS, Q, gt, gw, sJ, sA);
+    double* out = tables + (size_t)k * TT;
+    for (int j = threadIdx.x; j < TT; j += blockDim.x) {
+        int N = j / TS, mu = j - N * TS;
+        double v = (mu <= N) ? sT[j] : 0.0;
+        if (cp.a == 2 && ((N + mu) & 1)) v = -v;
+        out[j] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Build-time preparation.
+// ---------------------------------------------------------------------------
+LfErr lf_prepare_m2r(lfmm_ctx* ctx, cudaStream_t st)
+{
+    ctx->m2r_nkeys = 0;
+    ctx->m2r_nbatch = 0;
+    ctx->m2r_keyed_from = ctx->depth + 1;
+    // the keyed GEMM holds a whole operator in shared memory: p <= 10
+    if (ctx->m2l_rm == 0 || ctx->m2l_rm > 8 || ctx->m2r_total == 0) return LfErr();
+    // first level whose grid planes contain the interfaces
+    int la = ctx->depth + 1;
+    for (int l = 0; l <= ctx->depth; ++l) {
+        const double h = ctx->levels[l].h;
+        bool ok = true;
+        for (int i = 0; i < ctx->L; ++i) {
+            double r = (ctx->d[i] - ctx->origin[2]) / h;
+            if (fabs(r - llround(r)) > 1e-9 * std::max(1.0, fabs(r))) ok = false;
+        }
+        if (ok) {
+            la = l;
+            break;
+        }
+    }
+    ctx->m2r_keyed_from = la;
+    int64_t first = -1, last = -1;
+    for (int l = la; l <= ctx->depth; ++l) {
+        const LfmmLevel& lv = ctx->levels[l];
+        if (lv.m2r_count == 0) continue;
+        if (first < 0) first = lv.m2r_base;
+        last = lv.m2r_base + lv.m2r_count;
+    }
+    if (first < 0) return LfErr();
+    const int ne = (int)(last - first);
+    LF_CHECK(cudaMemcpyToSymbolAsync(c_rcomp, ctx->comp, sizeof(LfmmComp) * ctx->ncomp, 0, cudaMemcpyHostToDevice, st));
+    LF_TRY(lf_reserve(ctx->m2r_keys, (size_t)ne * 4 + 16));
+    LF_TRY(lf_reserve(ctx->m2r_order, (size_t)ne * 4 + 16));
+    LF_TRY(lf_reserve(ctx->m2r_tgt, (size_t)ctx->m2r_total * 4 + 16));
+    int* bad = reinterpret_cast<int*>(ctx->counts.as<char>() + 32768);
+    LF_CHECK(cudaMemsetAsync(bad, 0, 16, st));
+    // entries of aligned levels are contiguous: index them relative to `first`
+    uint32_t* keys = ctx->m2r_keys.as<uint32_t>();
+    uint32_t* vals = ctx->m2r_order.as<uint32_t>();
+    for (int l = la; l <= ctx->depth; ++l) {
+        const LfmmLevel& lv = ctx->levels[l];
+        if (lv.nbox == 0 || lv.m2r_count == 0) continue;
+        ++ctx->launches, k_m2r_keys<<<lf_blocks(lv.nbox, 128), 128, 0, st>>>(
+            lv.off, lv.nbox, lv.h, ctx->box_center.as<LfD4>(), ctx->m2r_off.as<int>(),
+            ctx->m2r_off.as<int>() + ctx->nbox_total, ctx->m2r_ent.as<uint32_t>(), l, keys - first, vals - first,
+            ctx->m2r_tgt.as<int>(), bad);
+    }
+    LF_TRY(lf_cuda(cudaGetLastError(), "m2r keys"));
+    int hbad = 0;
+    LF_CHECK(cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, st));
+    LF_CHECK(cudaStreamSynchronize(st));
+    if (hbad) return "internal: reaction M2L pair with a non-integer or too distant offset on an aligned level";
+    // vals hold absolute entry indices (e), keys sorted ascending
+    LF_TRY(lf_radix_sort(ctx, keys, vals, ne, st));
+    LF_TRY(lf_reserve(ctx->flags, (size_t)ne * 4 + 16));
+    LF_TRY(lf_reserve(ctx->idx, (size_t)ne * 4 + 16));
+    int* fl = ctx->flags.as<int>();
+    int* ix = ctx->idx.as<int>();
+    ++ctx->launches, k_key_flags<<<lf_blocks(ne, 256), 256, 0, st>>>(keys, ne, fl);
+    int64_t nk = 0;
+    LF_TRY(lf_scan_i32(ctx, fl, ix, ne, &nk, st));
+    LF_TRY(lf_reserve(ctx->m2r_kstart, (size_t)(nk + 1) * 4));
+    LF_TRY(lf_reserve(ctx->m2r_kval, (size_t)(nk + 1) * 4));
+    ++ctx->launches, k_key_starts<<<lf_blocks(ne, 256), 256, 0, st>>>(keys, ne, fl, ix, ctx->m2r_kstart.as<int>(),
+                                                                       ctx->m2r_kval.as<uint32_t>());
+    LF_TRY(lf_cuda(cudaGetLastError(), "m2r key starts"));
+    std::vector<int> kstart(nk + 1);
+    LF_CHECK(cudaMemcpyAsync(kstart.data(), ctx->m2r_kstart.ptr, sizeof(int) * nk, cudaMemcpyDeviceToHost, st));
+    LF_CHECK(cudaStreamSynchronize(st));
+    kstart[nk] = ne;
+    // tables, one per key
+    const int P = ctx->p, TS = 2 * P + 1, TT = TS * TS, Q = ctx->gl_q_m2l;
+    LF_TRY(lf_reserve(ctx->m2r_tables, (size_t)nk * TT * 8 + 16));
+    double hl[16] = {0};
+    for (int l = 0; l <= ctx->depth && l < 16; ++l) hl[l] = ctx->levels[l].h;
+    LF_TRY(lf_reserve(ctx->m2r_levelh, sizeof(hl)));
+    LF_CHECK(cudaMemcpyAsync(ctx->m2r_levelh.ptr, hl, sizeof(hl), cudaMemcpyHostToDevice, st));
+    size_t sm = sizeof(double) * ((size_t)TT + 2 * (size_t)Q * TS);
+    LF_CHECK(cudaFuncSetAttribute(k_m2r_tables, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    ++ctx->launches, k_m2r_tables<<<(int)nk, 128, sm, st>>>(ctx->m2r_kval.as<uint32_t>(), (int)nk,
+                                                            ctx->m2r_levelh.as<double>(), P,
+                                                            ctx->gl_t_m2l.as<double>(), ctx->gl_w_m2l.as<double>(), Q,
+                                                            ctx->m2r_tables.as<double>());
+    LF_TRY(lf_cuda(cudaGetLastError(), "m2r tables"));
+    // batches of R_TB pairs of one key
+    std::vector<int4> batches;
+    for (int k = 0; k < nk; ++k)
+        for (int s = kstart[k]; s < kstart[k + 1]; s += R_TB)
+            batches.push_back(make_int4(k, s, std::min(R_TB, kstart[k + 1] - s), 0));
+    ctx->m2r_nkeys = (int)nk;
+    ctx->m2r_nbatch = (int)batches.size();
+    LF_TRY(lf_reserve(ctx->m2r_batches, batches.size() * sizeof(int4) + 16));
+    LF_CHECK(cudaMemcpyAsync(ctx->m2r_batches.ptr, batches.data(), batches.size() * sizeof(int4),
+                             cudaMemcpyHostToDevice, st));
+    LF_CHECK(cudaStreamSynchronize(st));
+    ctx->stats[LFMM_STAT_REACTION_KEYS] = nk;
+    return LfErr();
+}
+
+// ---------------------------------------------------------------------------
+// Evaluation: batched GEMM per key with atomic accumulation.
+// ---------------------------------------------------------------------------
+struct RGemmArgs {
+    int p, nc;
+    const int4* batches;
+    const uint32_t* kval;
+    const double* tables;
+    const uint32_t* order;  // sorted entry indices
+    const uint32_t* ent;    // m2r entries (component | source box)
+    const int* tgt;         // target box per entry
+    const double* levelh;
+    const void* M;
+    void* L;
+};
+
+template <typename R>
+__device__ __forceinline__ void atomic_add_r(R* a, R v)
+{
+    atomicAdd(a, v);
+}
+
+template <typename R, int RM>
+__global__ void __launch_bounds__(R_T) k_m2r_gemm(RGemmArgs g)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int RP = 16 * RM;
+    constexpr int KP = RP;
+    constexpr int XS = KP + 1;
+    const int p = g.p, nc = g.nc, nre = lf_nre(p), TS = 2 * p + 1;
+    R* sA = reinterpret_cast<R*>(smem_raw);  // [KP][RP]
+    R* sX = sA + KP * RP;                    // [R_TB][XS]
+    R* sT = sX + R_TB * XS;                  // [TS*TS]
+    R* sC = sT + TS * TS;                    // cos(m phi), m <= 2p
+    R* sS = sC + TS;
+    __shared__ int s_src[R_TB], s_tgt[R_TB];
+    const int tid = threadIdx.x;
+    const int cg = tid & 15, rg = tid >> 4;
+    const int4 b = g.batches[blockIdx.x];
+    const int kidx = b.x, start = b.y, cnt = b.z;
+    int c, lev, ox, oy, oz;
+    rkey_decode(g.kval[kidx], c, lev, ox, oy, oz);
+    (void)oz;
+    const LfmmComp& cp = c_rcomp[c];
+    const double phi = (ox == 0 && oy == 0) ? 0.0 : atan2((double)oy, (double)ox);
+    if (tid < TS) {
+        double sn, cs;
+        sincos(tid * phi, &sn, &cs);
+        sC[tid] = (R)cs;
+        sS[tid] = (R)sn;
+    }
+    const double* Tk = g.tables + (size_t)kidx * TS * TS;
+    for (int j = tid; j < TS * TS; j += R_T) sT[j] = (R)Tk[j];
+    if (tid < R_TB) {
+        if (tid < cnt) {
+            uint32_t e = g.order[start + tid];
+            s_src[tid] = (int)(g.ent[e] & LFMM_ENT_MASK);
+            s_tgt[tid] = g.tgt[e];
+        } else {
+            s_src[tid] = -1;
+            s_tgt[tid] = -1;
+        }
+    }
+    __syncthreads();
+    // operator A[k_in][r_out] from the table, the phases and the signs
+    for (int idx = tid; idx < KP * RP; idx += R_T) {
+        int kin = idx / RP, rout = idx - kin * RP;
+        R v = 0;
+        if (kin < nc && rout < nc) {
+            int n, mp, bim, k, l, aim;
+            lf_decode(p, kin, n, mp, bim);
+            lf_decode(p, rout, k, l, aim);
+            // T_N^mu (complex) = e^{i mu phi} T(N, |mu|) with T_N^{-mu} = (-1)^mu conj
+            int N = n + k;
+            int mu1 = mp + l;
+            R c1 = sT[N * TS + mu1] * sC[mu1], d1 = sT[N * TS + mu1] * sS[mu1];
+            R c2 = 0, d2 = 0, s = 0;
+            if (mp > 0) {
+                int mu2 = l - mp, a2 = mu2 < 0 ? -mu2 : mu2;
+                R tv = sT[N * TS + a2];
+                c2 = tv * sC[a2];
+                d2 = tv * sS[a2];
+                if (mu2 < 0) {
+                    if (a2 & 1) c2 = -c2; else d2 = -d2;
+                }
+                s = (mp & 1) ? R(-1) : R(1);
+            }
+            R sk = (k & 1) ? R(-1) : R(1);
+            if (!aim && !bim) v = sk * (c1 + s * c2);
+            else if (!aim && bim) v = sk * (-d1 + s * d2);
+            else if (aim && !bim) v = sk * (d1 + s * d2);
+            else v = sk * (c1 - s * c2);
+            if (cp.refl && ((n + mp) & 1)) v = -v;
+        }
+        sA[idx] = v;
+    }
+    // gather the sources' multipoles
+    const R* M = reinterpret_cast<const R*>(g.M);
+    for (int idx = tid; idx < R_TB * KP; idx += R_T) {
+        int j = idx / KP, k = idx - j * KP;
+        int s = s_src[j];
+        sX[j * XS + k] = (s >= 0 && k < nc) ? M[(size_t)s * nc + k] : R(0);
+    }
+    __syncthreads();
+    R acc[RM][4];
+#pragma unroll
+    for (int r = 0; r < RM; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[r][q] = 0;
+#pragma unroll 4
+    for (int kk = 0; kk < KP; ++kk) {
+        R a[RM];
+#pragma unroll
+        for (int r = 0; r < RM; ++r) a[r] = sA[kk * RP + rg * RM + r];
+        R x[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) x[q] = sX[(4 * cg + q) * XS + kk];
+#pragma unroll
+        for (int r = 0; r < RM; ++r)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[r][q] += a[r] * x[q];
+    }
+    const R ih = (R)(1.0 / g.levelh[lev]);
+    R* L = reinterpret_cast<R*>(g.L);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        int j = 4 * cg + q;
+        if (j >= cnt) continue;
+        R* Lt = L + (size_t)s_tgt[j] * nc;
+#pragma unroll
+        for (int r = 0; r < RM; ++r) {
+            int row = rg * RM + r;
+            if (row < nc) atomic_add_r(Lt + row, acc[r][q] * ih);
+        }
+    }
+    (void)nre;
+}
+
+template <typename R, int RM>
+static LfErr launch_rgemm(lfmm_ctx* ctx, cudaStream_t st, const RGemmArgs& g)
+{
+    constexpr int RP = 16 * RM;
+    const int TS = 2 * ctx->p + 1;
+    size_t sm = sizeof(R) * ((size_t)RP * RP + (size_t)R_TB * (RP + 1) + (size_t)TS * TS + 2 * (size_t)TS) + 64;
+    LF_CHECK(cudaFuncSetAttribute(k_m2r_gemm<R, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    ++ctx->launches, k_m2r_gemm<R, RM><<<ctx->m2r_nbatch, R_T, sm, st>>>(g);
+    return lf_cuda(cudaGetLastError(), "m2r gemm");
+}
+
+template <typename R>
+static LfErr m2r_apply_t(lfmm_ctx* ctx, cudaStream_t st)
+{
+    RGemmArgs g;
+    g.p = ctx->p;
+    g.nc = lf_nc(ctx->p);
+    g.batches = ctx->m2r_batches.as<int4>();
+    g.kval = ctx->m2r_kval.as<uint32_t>();
+    g.tables = ctx->m2r_tables.as<double>();
+    g.order = ctx->m2r_order.as<uint32_t>();
+    g.ent = ctx->m2r_ent.as<uint32_t>();
+    g.tgt = ctx->m2r_tgt.as<int>();
+    g.levelh = ctx->m2r_levelh.as<double>();
+    g.M = ctx->Mexp.ptr;
+    g.L = ctx->Lexp.ptr;
+    LF_CHECK(cudaMemcpyToSymbolAsync(c_rcomp, ctx->comp, sizeof(LfmmComp) * ctx->ncomp, 0, cudaMemcpyHostToDevice, st));
+    switch (ctx->m2l_rm) {
+    case 2: return launch_rgemm<R, 2>(ctx, st, g);
+    case 4: return launch_rgemm<R, 4>(ctx, st, g);
+    case 8: return launch_rgemm<R, 8>(ctx, st, g);
+    default: return "internal: reaction GEMM supports p <= 10";
+    }
+}
+
+LfErr lf_m2r_apply(lfmm_ctx* ctx, cudaStream_t st)
+{
+    if (ctx->m2r_nbatch == 0) return LfErr();
+    return ctx->precision ? m2r_apply_t<float>(ctx, st) : m2r_apply_t<double>(ctx, st);
+}

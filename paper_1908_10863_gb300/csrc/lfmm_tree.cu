@@ -195,7 +195,7 @@ __global__ void k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t
     }
 }
 
-static LfErr radix_sort(lfmm_ctx* ctx, uint32_t* keys, uint32_t* vals, int64_t n, cudaStream_t st)
+LfErr lf_radix_sort(lfmm_ctx* ctx, uint32_t* keys, uint32_t* vals, int64_t n, cudaStream_t st)
 {
     int nb = lf_blocks(n, RS_TILE);
     LF_TRY(lf_reserve(ctx->keys_tmp, (size_t)n * 4));
@@ -627,7 +627,7 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
         snprintf(buf, sizeof buf, "EINVAL: charge %d has an invalid layer id or lies outside its layer", herr[1]);
         return buf;
     }
-    LF_TRY(radix_sort(ctx, keys, vals, n, st));
+    LF_TRY(lf_radix_sort(ctx, keys, vals, n, st));
 
     // sorted particle arrays
     LF_TRY(lf_reserve(ctx->xs, (size_t)n * 8));
@@ -843,5 +843,7 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
     ctx->stats[LFMM_STAT_COMPONENTS] = ctx->ncomp;
     ctx->stats[LFMM_STAT_M2M_EDGES] = tot - ctx->levels[0].nbox;
     ctx->n = n;
-    return LfErr();
+    ctx->stats[LFMM_STAT_REACTION_KEYS] = 0;
+    LF_TRY(lf_prepare_m2l(ctx, st));
+    return lf_prepare_m2r(ctx, st);
 }

@@ -17,7 +17,7 @@ from . import build as _build
 OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETIMEOUT, ENUMERIC = range(7)
 OPT_PRECISION, OPT_LEAF_CAP, OPT_PROFILE, OPT_QUAD_NODES = 1, 2, 3, 4
 STAT_NAMES = ["n", "depth", "boxes", "leaves", "m2l_free", "m2l_reaction", "p2p_free", "p2p_reaction",
-              "components", "m2m_edges", "launches"]
+              "components", "m2m_edges", "launches", "reaction_keys"]
 TIME_NAMES = ["p2m", "m2m", "m2l_free", "m2l_reaction", "l2l", "l2p", "p2p", "total", "build"]
 _STATUS = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ESTATE: "ESTATE", ETIMEOUT: "ETIMEOUT",
            ENUMERIC: "ENUMERIC"}
