@@ -54,7 +54,9 @@ enum {
                                compensated far-field sums, FP64 Sommerfeld tables */
     LFMM_OPT_LEAF_CAP = 2,  /* octree leaf capacity (default 40) */
     LFMM_OPT_PROFILE = 3,   /* 1 = time every stage with CUDA events (lfmm_get_timings) */
-    LFMM_OPT_QUAD_NODES = 4 /* Gauss-Laguerre nodes of the M2L remainder integrals (16..128, default 64) */
+    LFMM_OPT_QUAD_NODES = 4, /* Gauss-Laguerre nodes of the M2L remainder integrals (16..128, default 64) */
+    LFMM_OPT_SURROGATE = 5,  /* 1 = near-field reaction kernels by the trained network (default 0) */
+    LFMM_OPT_SURROGATE_TOL = 6 /* error estimate above which a pair falls back to quadrature (default 1e-6) */
 };
 
 /* Create a context for the medium.
@@ -120,6 +122,8 @@ enum {
     LFMM_STAT_M2M_EDGES = 9,      /* parent-child edges (also the L2L count) */
     LFMM_STAT_LAUNCHES = 10,      /* kernels launched by this context since lfmm_create (cumulative) */
     LFMM_STAT_REACTION_KEYS = 11, /* distinct (component, level, offset) reaction M2L operators */
+    LFMM_STAT_SURR_NET = 12,      /* near-field reaction pairs of the last evaluate done by the network */
+    LFMM_STAT_SURR_QUAD = 13,     /* ... and by the quadrature */
     LFMM_STAT_COUNT = 16
 };
 lfmm_status lfmm_get_stats(const lfmm_ctx* ctx, int64_t* out, int nout);
@@ -161,6 +165,60 @@ lfmm_status lfmm_sommerfeld_tables(lfmm_ctx* ctx, int l, int lp, int a, int b, i
  * of Algorithm 1 (I_00 and its derivatives).  Host arrays. */
 lfmm_status lfmm_reaction_kernel(lfmm_ctx* ctx, int l, int lp, int a, int b, int npts, const double* rho,
                                  const double* h, double* out);
+
+/* ---- learned surrogate of the near-field reaction kernels --------------
+ * Not in the paper: a small network per reaction component (4 inputs, three
+ * hidden layers of 64 with SiLU, 3 outputs; bfloat16 weights, float32
+ * accumulation) replaces the quadrature of the near-field integrals I_00,
+ * I_10, I_11 (Algorithm 1, local direct interactions) where its validated
+ * error is below LFMM_OPT_SURROGATE_TOL; elsewhere the quadrature is kept. */
+
+/* Train the networks of every reaction component of a three-layer medium on
+ * the device: nsamples (rho, h_t, h_s) samples per component (1000 .. 2^26),
+ * rho log-uniform in [1e-3, 3], the depths below/above the interfaces
+ * uniform in [0, d0 - d1] for half the samples and log-uniform in
+ * [1e-4, d0 - d1] for the rest, labelled by the FP64 quadrature; epochs
+ * passes of Adam over them; a tenth as many held-out samples (at least
+ * 4096) fill the per-cell error table (32 x 32 cells of log10 rho by
+ * log10 h).  Deterministic for a given seed.  Replaces earlier networks. */
+lfmm_status lfmm_surrogate_train(lfmm_ctx* ctx, int64_t nsamples, int epochs, uint64_t seed);
+
+/* Training summary of component (l, lp, a, b): out[0] trained (0/1), out[1]
+ * maximum validation error (relative to the kernel scale below), out[2] fraction of
+ * error-table cells at or below the tolerance, out[3] final training loss,
+ * out[4] training samples, out[5] validation samples, out[6] fraction of the
+ * validation samples that fall in accepted cells.  Errors are measured
+ * against the pair's kernel scale |C| / R + |c_r| / R_r (I_00; squared
+ * distances for I_10, I_11), C e^{-k zeta} the density's leading image and
+ * c_r e^{-k zeta_r} its remainder's.  Host array of 8. */
+lfmm_status lfmm_surrogate_info(const lfmm_ctx* ctx, int l, int lp, int a, int b, double* out);
+
+/* Network values for npts pairs (host arrays): rho, target depth ht and
+ * source depth hs (h = ht + hs); out[i][0..3] = (I_00, I_10, I_11 by the
+ * network, 1 if the error table accepts the pair else 0). */
+lfmm_status lfmm_surrogate_eval(lfmm_ctx* ctx, int l, int lp, int a, int b, int npts, const double* rho,
+                                const double* ht, const double* hs, double* out);
+
+/* Master (float32) parameters of one component's network, LFMM_SURR_NPARAM
+ * floats in the order W1[64][4], b1[64], W2[64][64], b2[64], W3[64][64],
+ * b3[64], W4[3][64], b4[3].  get reads them, set replaces them and re-derives
+ * that network's bfloat16 inference weights (allocating the network state on
+ * first use; the error table and standardisation are left as they are). */
+#define LFMM_SURR_NPARAM 8835
+lfmm_status lfmm_surrogate_get_params(const lfmm_ctx* ctx, int l, int lp, int a, int b, float* theta);
+lfmm_status lfmm_surrogate_set_params(lfmm_ctx* ctx, int l, int lp, int a, int b, const float* theta);
+
+/* Raw network outputs y[n][3] (standardised remainders) for features
+ * x[n][4] (host arrays), by the same warp-level bfloat16 tensor-core kernel
+ * the near field uses. */
+lfmm_status lfmm_surrogate_forward(lfmm_ctx* ctx, int l, int lp, int a, int b, int n, const float* x, float* y);
+
+/* Loss (1/n) sum (out - y)^2 and its gradient with respect to the master
+ * parameters for n samples (host arrays x[n][4], y[n][3]; n a multiple of
+ * 64), computed by the training kernels with the current parameters
+ * (forward with bfloat16-rounded weights). */
+lfmm_status lfmm_surrogate_loss_grad(lfmm_ctx* ctx, int l, int lp, int a, int b, int n, const float* x,
+                                     const float* y, double* loss, float* grad);
 
 /* Allocation-free variant of lfmm_reaction_kernel, for callers that may not
  * allocate device memory during the call (stream capture, real-time loops,

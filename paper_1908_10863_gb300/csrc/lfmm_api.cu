@@ -516,6 +516,9 @@ lfmm_status lfmm_create(const double* d, int L, const double* eps, int p, lfmm_c
     if (e.empty()) e = setup_rules(ctx);
     if (e.empty()) e = setup_tables(ctx);
     if (e.empty()) e = lf_setup_m2l_ops(ctx);
+    // the setup tables travel by pageable copies on the legacy stream, which
+    // the context's non-blocking streams do not wait for
+    if (e.empty()) e = lf_cuda(cudaDeviceSynchronize(), "setup copies");
     if (!e.empty()) {
         lfmm_status s = status_of(e);
         lfmm_destroy(ctx);
@@ -548,6 +551,14 @@ lfmm_status lfmm_set_option(lfmm_ctx* ctx, int opt, double v)
         ctx->quad_nodes = Q;
         return fail(ctx, setup_rules(ctx));
     }
+    case LFMM_OPT_SURROGATE:
+        if (v != 0.0 && !ctx->surr_ready) return fail(ctx, "ESTATE: train the surrogate first"), LFMM_ESTATE;
+        ctx->use_surr = (v != 0.0);
+        return LFMM_OK;
+    case LFMM_OPT_SURROGATE_TOL:
+        if (!(v > 0.0)) return fail(ctx, "EINVAL: tolerance must be positive");
+        ctx->surr_tol = v;
+        return LFMM_OK;
     default:
         return fail(ctx, "EINVAL: unknown option");
     }
@@ -695,7 +706,9 @@ void lfmm_destroy(lfmm_ctx* ctx)
                       &ctx->m2l_cls, &ctx->m2l_inv, &ctx->m2l_slots, &ctx->m2l_keys, &ctx->m2l_sorted,
                       &ctx->m2l_tiles, &ctx->m2l_levelh, &ctx->m2r_keys, &ctx->m2r_order,
                       &ctx->m2r_tgt, &ctx->m2r_kstart, &ctx->m2r_kval, &ctx->m2r_tables, &ctx->m2r_levelh,
-                      &ctx->m2r_batches};
+                      &ctx->m2r_batches, &ctx->surr_theta, &ctx->surr_grad, &ctx->surr_m1,
+                      &ctx->surr_m2, &ctx->surr_w, &ctx->surr_b, &ctx->surr_meta, &ctx->surr_err, &ctx->surr_comps,
+                      &ctx->surr_xoff, &ctx->surr_counters};
     for (DevBuf* b : bufs) lf_free(*b);
     for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
@@ -710,6 +723,14 @@ lfmm_status lfmm_get_stats(const lfmm_ctx* ctx, int64_t* out, int nout)
     if (!ctx || !out || nout < 1) return LFMM_EINVAL;
     for (int i = 0; i < nout && i < LFMM_STAT_COUNT; ++i) out[i] = ctx->stats[i];
     if (nout > LFMM_STAT_LAUNCHES) out[LFMM_STAT_LAUNCHES] = ctx->launches;
+    if (nout > LFMM_STAT_SURR_QUAD && ctx->surr_counters.ptr) {
+        unsigned long long c[2] = {0, 0};
+        cudaStreamSynchronize(ctx->s_near);
+        if (lf_d2h(c, ctx->surr_counters.ptr, sizeof(c), ctx->s_main) == cudaSuccess) {
+            out[LFMM_STAT_SURR_NET] = (int64_t)c[0];
+            out[LFMM_STAT_SURR_QUAD] = (int64_t)c[1];
+        }
+    }
     return ctx->built ? LFMM_OK : LFMM_ESTATE;
 }
 
@@ -736,12 +757,12 @@ lfmm_status lfmm_sommerfeld_tables(lfmm_ctx* ctx, int l, int lp, int a, int b, i
     LfErr e = lf_reserve(drho, (size_t)npts * 8);
     if (e.empty()) e = lf_reserve(dz, (size_t)npts * 8);
     if (e.empty()) e = lf_reserve(dout, (size_t)npts * TS * TS * 8);
-    if (e.empty()) e = lf_cuda(cudaMemcpy(drho.ptr, rho, (size_t)npts * 8, cudaMemcpyHostToDevice), "copy");
-    if (e.empty()) e = lf_cuda(cudaMemcpy(dz.ptr, z, (size_t)npts * 8, cudaMemcpyHostToDevice), "copy");
+    if (e.empty()) e = lf_cuda(cudaMemcpyAsync(drho.ptr, rho, (size_t)npts * 8, cudaMemcpyHostToDevice, ctx->s_main), "copy");
+    if (e.empty()) e = lf_cuda(cudaMemcpyAsync(dz.ptr, z, (size_t)npts * 8, cudaMemcpyHostToDevice, ctx->s_main), "copy");
     if (e.empty()) e = lf_sommerfeld_tables_dev(ctx, c, npts, drho.as<double>(), dz.as<double>(), S, P, dout.as<double>());
     if (e.empty()) e = lf_cuda(cudaStreamSynchronize(ctx->s_main), "tables");
     if (e.empty())
-        e = lf_cuda(cudaMemcpy(out, dout.ptr, (size_t)npts * TS * TS * 8, cudaMemcpyDeviceToHost), "copy back");
+        e = lf_cuda(lf_d2h(out, dout.ptr, (size_t)npts * TS * TS * 8, ctx->s_main), "copy back");
     lf_free(drho);
     lf_free(dz);
     lf_free(dout);
@@ -762,14 +783,125 @@ lfmm_status lfmm_reaction_kernel(lfmm_ctx* ctx, int l, int lp, int a, int b, int
     LfErr e = lf_reserve(drho, (size_t)npts * 8);
     if (e.empty()) e = lf_reserve(dh, (size_t)npts * 8);
     if (e.empty()) e = lf_reserve(dout, (size_t)npts * 24);
-    if (e.empty()) e = lf_cuda(cudaMemcpy(drho.ptr, rho, (size_t)npts * 8, cudaMemcpyHostToDevice), "copy");
-    if (e.empty()) e = lf_cuda(cudaMemcpy(dh.ptr, h, (size_t)npts * 8, cudaMemcpyHostToDevice), "copy");
+    if (e.empty()) e = lf_cuda(cudaMemcpyAsync(drho.ptr, rho, (size_t)npts * 8, cudaMemcpyHostToDevice, ctx->s_main), "copy");
+    if (e.empty()) e = lf_cuda(cudaMemcpyAsync(dh.ptr, h, (size_t)npts * 8, cudaMemcpyHostToDevice, ctx->s_main), "copy");
     if (e.empty()) e = lf_reaction_kernel_dev(ctx, c, npts, drho.as<double>(), dh.as<double>(), dout.as<double>());
     if (e.empty()) e = lf_cuda(cudaStreamSynchronize(ctx->s_main), "kernel");
-    if (e.empty()) e = lf_cuda(cudaMemcpy(out, dout.ptr, (size_t)npts * 24, cudaMemcpyDeviceToHost), "copy back");
+    if (e.empty()) e = lf_cuda(lf_d2h(out, dout.ptr, (size_t)npts * 24, ctx->s_main), "copy back");
     lf_free(drho);
     lf_free(dh);
     lf_free(dout);
+    return fail(ctx, e);
+}
+
+lfmm_status lfmm_surrogate_train(lfmm_ctx* ctx, int64_t nsamples, int epochs, uint64_t seed)
+{
+    if (!ctx) return LFMM_EINVAL;
+    ctx->err.clear();
+    prof_reset(ctx);
+    LfErr e = lf_surrogate_train(ctx, nsamples, epochs, seed);
+    if (!e.empty()) {
+        cudaStreamSynchronize(ctx->s_main);
+        return fail(ctx, e);
+    }
+    return LFMM_OK;
+}
+
+lfmm_status lfmm_surrogate_info(const lfmm_ctx* ctx, int l, int lp, int a, int b, double* out)
+{
+    if (!ctx || !out) return LFMM_EINVAL;
+    int c = lf_find_comp(ctx, l, lp, a, b);
+    if (c < 0) return LFMM_EINVAL;
+    for (int q = 0; q < 8; ++q) out[q] = ctx->surr_info[c][q];
+    return LFMM_OK;
+}
+
+lfmm_status lfmm_surrogate_eval(lfmm_ctx* ctx, int l, int lp, int a, int b, int npts, const double* rho,
+                                const double* ht, const double* hs, double* out)
+{
+    if (!ctx) return LFMM_EINVAL;
+    ctx->err.clear();
+    int c = lf_find_comp(ctx, l, lp, a, b);
+    if (c < 0) return fail(ctx, "EINVAL: no such reaction component");
+    if (npts < 1 || !rho || !ht || !hs || !out) return fail(ctx, "EINVAL: bad request");
+    if (!ctx->surr_ready || !ctx->surr_meta_h[c].trained) return fail(ctx, "ESTATE: surrogate not trained"), LFMM_ESTATE;
+    DevBuf dr, dt, ds, dout;
+    LfErr e = lf_reserve(dr, (size_t)npts * 8);
+    if (e.empty()) e = lf_reserve(dt, (size_t)npts * 8);
+    if (e.empty()) e = lf_reserve(ds, (size_t)npts * 8);
+    if (e.empty()) e = lf_reserve(dout, (size_t)npts * 32);
+    if (e.empty()) e = lf_cuda(cudaMemcpyAsync(dr.ptr, rho, (size_t)npts * 8, cudaMemcpyHostToDevice, ctx->s_main), "copy");
+    if (e.empty()) e = lf_cuda(cudaMemcpyAsync(dt.ptr, ht, (size_t)npts * 8, cudaMemcpyHostToDevice, ctx->s_main), "copy");
+    if (e.empty()) e = lf_cuda(cudaMemcpyAsync(ds.ptr, hs, (size_t)npts * 8, cudaMemcpyHostToDevice, ctx->s_main), "copy");
+    if (e.empty()) e = lf_surrogate_eval_dev(ctx, c, npts, dr.as<double>(), dt.as<double>(), ds.as<double>(), dout.as<double>());
+    if (e.empty()) e = lf_cuda(cudaStreamSynchronize(ctx->s_main), "eval");
+    if (e.empty()) e = lf_cuda(lf_d2h(out, dout.ptr, (size_t)npts * 32, ctx->s_main), "copy back");
+    lf_free(dr);
+    lf_free(dt);
+    lf_free(ds);
+    lf_free(dout);
+    return fail(ctx, e);
+}
+
+lfmm_status lfmm_surrogate_get_params(const lfmm_ctx* ctx, int l, int lp, int a, int b, float* theta)
+{
+    if (!ctx || !theta) return LFMM_EINVAL;
+    int c = lf_find_comp(ctx, l, lp, a, b);
+    if (c < 0 || !ctx->surr_theta.ptr) return LFMM_EINVAL;
+    cudaError_t e = lf_d2h(theta, ctx->surr_theta.as<float>() + (size_t)c * LFMM_SURR_NP, LFMM_SURR_NP * 4, ctx->s_main);
+    return e == cudaSuccess ? LFMM_OK : LFMM_ECUDA;
+}
+
+lfmm_status lfmm_surrogate_set_params(lfmm_ctx* ctx, int l, int lp, int a, int b, const float* theta)
+{
+    if (!ctx || !theta) return LFMM_EINVAL;
+    ctx->err.clear();
+    int c = lf_find_comp(ctx, l, lp, a, b);
+    if (c < 0) return fail(ctx, "EINVAL: no such reaction component");
+    LfErr e = lf_surrogate_alloc(ctx);
+    if (e.empty())
+        e = lf_cuda(cudaMemcpyAsync(ctx->surr_theta.as<float>() + (size_t)c * LFMM_SURR_NP, theta, LFMM_SURR_NP * 4, cudaMemcpyHostToDevice, ctx->s_main), "copy params");
+    if (e.empty()) e = lf_surrogate_pack(ctx, c);
+    if (e.empty()) e = lf_cuda(cudaStreamSynchronize(ctx->s_main), "pack");
+    return fail(ctx, e);
+}
+
+lfmm_status lfmm_surrogate_forward(lfmm_ctx* ctx, int l, int lp, int a, int b, int n, const float* x, float* y)
+{
+    if (!ctx) return LFMM_EINVAL;
+    ctx->err.clear();
+    int c = lf_find_comp(ctx, l, lp, a, b);
+    if (c < 0) return fail(ctx, "EINVAL: no such reaction component");
+    if (n < 1 || !x || !y) return fail(ctx, "EINVAL: bad request");
+    DevBuf dx, dy;
+    LfErr e = lf_reserve(dx, (size_t)n * 16);
+    if (e.empty()) e = lf_reserve(dy, (size_t)n * 12);
+    if (e.empty()) e = lf_cuda(cudaMemcpyAsync(dx.ptr, x, (size_t)n * 16, cudaMemcpyHostToDevice, ctx->s_main), "copy");
+    if (e.empty()) e = lf_surrogate_forward_dev(ctx, c, n, dx.as<float>(), dy.as<float>());
+    if (e.empty()) e = lf_cuda(cudaStreamSynchronize(ctx->s_main), "forward");
+    if (e.empty()) e = lf_cuda(lf_d2h(y, dy.ptr, (size_t)n * 12, ctx->s_main), "copy back");
+    lf_free(dx);
+    lf_free(dy);
+    return fail(ctx, e);
+}
+
+lfmm_status lfmm_surrogate_loss_grad(lfmm_ctx* ctx, int l, int lp, int a, int b, int n, const float* x,
+                                     const float* y, double* loss, float* grad)
+{
+    if (!ctx) return LFMM_EINVAL;
+    ctx->err.clear();
+    int c = lf_find_comp(ctx, l, lp, a, b);
+    if (c < 0) return fail(ctx, "EINVAL: no such reaction component");
+    if (n < 64 || (n % 64) || !x || !y || !loss || !grad) return fail(ctx, "EINVAL: need n a multiple of 64");
+    DevBuf dx, dy;
+    LfErr e = lf_surrogate_alloc(ctx);
+    if (e.empty()) e = lf_reserve(dx, (size_t)n * 16);
+    if (e.empty()) e = lf_reserve(dy, (size_t)n * 12);
+    if (e.empty()) e = lf_cuda(cudaMemcpyAsync(dx.ptr, x, (size_t)n * 16, cudaMemcpyHostToDevice, ctx->s_main), "copy");
+    if (e.empty()) e = lf_cuda(cudaMemcpyAsync(dy.ptr, y, (size_t)n * 12, cudaMemcpyHostToDevice, ctx->s_main), "copy");
+    if (e.empty()) e = lf_surrogate_grad_dev(ctx, c, n, dx.as<float>(), dy.as<float>(), loss, grad);
+    lf_free(dx);
+    lf_free(dy);
     return fail(ctx, e);
 }
 

@@ -105,6 +105,14 @@ struct lfmm_ctx {
     DevBuf m2r_keys, m2r_order, m2r_tgt, m2r_kstart, m2r_kval, m2r_tables, m2r_levelh, m2r_batches;
     int m2r_nkeys = 0, m2r_nbatch = 0, m2r_keyed_from = 0;
 
+    // learned surrogate of the near-field reaction kernels
+    DevBuf surr_theta, surr_grad, surr_m1, surr_m2, surr_w, surr_b, surr_meta, surr_err, surr_comps, surr_xoff,
+        surr_counters;
+    int surr_ready = 0, use_surr = 0;
+    double surr_tol = 1e-6;
+    float surr_info[LFMM_MAXCOMP][8] = {{0}};
+    LfmmSurrMeta surr_meta_h[LFMM_MAXCOMP] = {};
+
     // evaluation buffers
     DevBuf q_sorted;            // R [n]
     DevBuf Mexp, Lexp;          // R [nbox][(p+1)^2]
@@ -126,6 +134,12 @@ struct lfmm_ctx {
 // ---- allocation helpers (lfmm_api.cu) ----
 LfErr lf_reserve(DevBuf& b, size_t bytes);
 LfErr lf_cuda(cudaError_t e, const char* what);
+// device-to-host copy ordered after the work queued on st, complete on return
+inline cudaError_t lf_d2h(void* dst, const void* src, size_t bytes, cudaStream_t st)
+{
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st);
+    return e == cudaSuccess ? cudaStreamSynchronize(st) : e;
+}
 
 // ---- tree construction (lfmm_tree.cu) ----
 LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz_dev, const int32_t* layer_dev, int64_t n, cudaStream_t st);
@@ -143,6 +157,17 @@ LfErr lf_radix_sort(lfmm_ctx* ctx, uint32_t* keys, uint32_t* vals, int64_t n, cu
 // ---- evaluation (lfmm_fmm.cu, lfmm_near.cu) ----
 LfErr lf_evaluate_sorted(lfmm_ctx* ctx, const double* q_dev, double* phi_dev, double* field_dev, cudaStream_t st);
 LfErr lf_near_field(lfmm_ctx* ctx, cudaStream_t st);
+
+// ---- surrogate (lfmm_surrogate.cu) ----
+LfErr lf_surrogate_train(lfmm_ctx* ctx, int64_t nsamples, int epochs, uint64_t seed);
+LfErr lf_surrogate_eval_dev(lfmm_ctx* ctx, int comp, int n, const double* rho, const double* ht, const double* hs,
+                            double* out);
+LfErr lf_surrogate_grad_dev(lfmm_ctx* ctx, int comp, int n, const float* x, const float* ystd, double* loss,
+                            float* grad);
+LfErr lf_surrogate_device_view(lfmm_ctx* ctx, LfmmSurrView* v);
+LfErr lf_surrogate_alloc(lfmm_ctx* ctx);
+LfErr lf_surrogate_pack(lfmm_ctx* ctx, int comp);
+LfErr lf_surrogate_forward_dev(lfmm_ctx* ctx, int comp, int n, const float* x, float* y);
 
 // ---- debug / parity kernels (lfmm_near.cu) ----
 LfErr lf_sommerfeld_tables_dev(lfmm_ctx* ctx, int comp, int npts, const double* rho, const double* z, double S,

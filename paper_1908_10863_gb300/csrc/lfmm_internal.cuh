@@ -49,6 +49,24 @@ struct __align__(32) LfD4 {
     double x, y, z, w;
 };
 
+// Surrogate network of one reaction component: sizes and per-component data.
+#define LFMM_SURR_NP 8835   // 4-64-64-64-3 parameters
+#define LFMM_SURR_CELLS 32  // error table: cells in log10(rho) and in h
+struct LfmmSurrMeta {
+    float mu[3], sd[3];  // output standardisation
+    float Tt, Ts;        // trained target / source depth ranges
+    int trained;
+};
+struct LfmmSurrView {  // what the near-field kernel needs
+    int ready;
+    const void* W;       // bf16 weights [ncomp][9728]
+    const float* B;      // biases [ncomp][200]
+    const float* err;    // [ncomp][CELLS*CELLS]
+    const LfmmSurrMeta* meta;
+    float tol;
+    unsigned long long* counters;  // [2]: pairs by network, pairs by quadrature
+};
+
 // One FMM component: free space (a = b = 0) or a reaction component
 // (l, lp, a, b).  Plain data, copied to constant memory.
 struct LfmmComp {
@@ -268,6 +286,79 @@ __device__ __forceinline__ void lf_sommerfeld_table_block(const LfmmComp& c, dou
         }
     }
     __syncthreads();
+}
+
+// Near-field reaction kernel of one component (Algorithm 1, local direct
+// interactions): (I_00, I_10, I_11') = int (J0, k J0, k J1)(k rho) e^{-kh} sigma dk
+// as the closed-form leading image plus the remainder by the quadrature rule
+// (gl_t, gl_w) in t = k (h + zeta_r).
+template <typename R>
+struct LfMath;
+template <>
+struct LfMath<double> {
+    static __device__ __forceinline__ double J0(double x) { return j0(x); }
+    static __device__ __forceinline__ double J1(double x) { return j1(x); }
+    static __device__ __forceinline__ double Exp(double x) { return exp(x); }
+    static __device__ __forceinline__ double Sqrt(double x) { return sqrt(x); }
+    static __device__ __forceinline__ double Rsqrt(double x) { return rsqrt(x); }
+};
+template <>
+struct LfMath<float> {
+    static __device__ __forceinline__ float J0(float x) { return j0f(x); }
+    static __device__ __forceinline__ float J1(float x) { return j1f(x); }
+    static __device__ __forceinline__ float Exp(float x) { return expf(x); }
+    static __device__ __forceinline__ float Sqrt(float x) { return sqrtf(x); }
+    static __device__ __forceinline__ float Rsqrt(float x) { return rsqrtf(x); }
+};
+
+template <typename R>
+struct LfSum {
+    R s = 0, c = 0;
+    __device__ __forceinline__ void add(R x)
+    {
+        R y = x - c;
+        R t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
+template <>
+struct LfSum<double> {
+    double s = 0, c = 0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+};
+
+// Reaction pair kernel: (I_00, I_10, I_11') of one component at (rho, h).
+template <typename R>
+__device__ __forceinline__ void lf_reaction_pair(const LfmmComp& c, R rho, R h, int Q, const double* gl_t,
+                                                 const double* gl_w, R& k00, R& k10, R& k11)
+{
+    typedef LfMath<R> F;
+    R H = h + (R)c.zeta;
+    R r2 = rho * rho + H * H;
+    R ir = F::Rsqrt(r2);
+    R ir3 = ir * ir * ir;
+    R C = (R)c.C;
+    k00 = C * ir;
+    k10 = C * H * ir3;
+    k11 = C * rho * ir3;
+    if (!c.has_rem) return;
+    R Z = h + (R)c.zeta_r;
+    R iZ = R(1) / Z;
+    R D = (R)c.D;
+    for (int q = 0; q < Q; ++q) {
+        R kap = (R)gl_t[q] * iZ;
+        R x = F::Exp(-D * kap);
+        R num = (R)c.rem[4];
+        for (int i = 3; i >= 0; --i) num = num * x + (R)c.rem[i];
+        R den = ((R)c.den[2] * x + (R)c.den[1]) * x + (R)c.den[0];
+        R w = (R)gl_w[q] * iZ * num / den;
+        R a = kap * rho;
+        R j0v = F::J0(a), j1v = F::J1(a);
+        k00 += w * j0v;
+        k10 += w * kap * j0v;
+        k11 += w * kap * j1v;
+    }
 }
 
 // ---------------------------------------------------------------------------

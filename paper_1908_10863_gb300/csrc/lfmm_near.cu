@@ -16,6 +16,7 @@
 #include <mutex>
 
 #include "lfmm_ctx.h"
+#include "lfmm_surrogate.cuh"
 
 #define LF_CHECK(call)                                    \
     do {                                                  \
@@ -34,74 +35,6 @@ __constant__ LfmmComp c_ncomp[LFMM_MAXCOMP];
 __constant__ double c_gl_t[LFMM_QMAX];
 __constant__ double c_gl_w[LFMM_QMAX];
 
-template <typename R>
-struct LfMath;
-template <>
-struct LfMath<double> {
-    static __device__ __forceinline__ double J0(double x) { return j0(x); }
-    static __device__ __forceinline__ double J1(double x) { return j1(x); }
-    static __device__ __forceinline__ double Exp(double x) { return exp(x); }
-    static __device__ __forceinline__ double Sqrt(double x) { return sqrt(x); }
-    static __device__ __forceinline__ double Rsqrt(double x) { return rsqrt(x); }
-};
-template <>
-struct LfMath<float> {
-    static __device__ __forceinline__ float J0(float x) { return j0f(x); }
-    static __device__ __forceinline__ float J1(float x) { return j1f(x); }
-    static __device__ __forceinline__ float Exp(float x) { return expf(x); }
-    static __device__ __forceinline__ float Sqrt(float x) { return sqrtf(x); }
-    static __device__ __forceinline__ float Rsqrt(float x) { return rsqrtf(x); }
-};
-
-template <typename R>
-struct LfSum {
-    R s = 0, c = 0;
-    __device__ __forceinline__ void add(R x)
-    {
-        R y = x - c;
-        R t = s + y;
-        c = (t - s) - y;
-        s = t;
-    }
-};
-template <>
-struct LfSum<double> {
-    double s = 0, c = 0;
-    __device__ __forceinline__ void add(double x) { s += x; }
-};
-
-// Reaction pair kernel: (I_00, I_10, I_11') of one component at (rho, h).
-template <typename R>
-__device__ __forceinline__ void lf_reaction_pair(const LfmmComp& c, R rho, R h, int Q, R& k00, R& k10, R& k11)
-{
-    typedef LfMath<R> F;
-    R H = h + (R)c.zeta;
-    R r2 = rho * rho + H * H;
-    R ir = F::Rsqrt(r2);
-    R ir3 = ir * ir * ir;
-    R C = (R)c.C;
-    k00 = C * ir;
-    k10 = C * H * ir3;
-    k11 = C * rho * ir3;
-    if (!c.has_rem) return;
-    R Z = h + (R)c.zeta_r;
-    R iZ = R(1) / Z;
-    R D = (R)c.D;
-    for (int q = 0; q < Q; ++q) {
-        R kap = (R)c_gl_t[q] * iZ;
-        R x = F::Exp(-D * kap);
-        R num = (R)c.rem[4];
-        for (int i = 3; i >= 0; --i) num = num * x + (R)c.rem[i];
-        R den = ((R)c.den[2] * x + (R)c.den[1]) * x + (R)c.den[0];
-        R w = (R)c_gl_w[q] * iZ * num / den;
-        R a = kap * rho;
-        R j0v = F::J0(a), j1v = F::J1(a);
-        k00 += w * j0v;
-        k10 += w * kap * j0v;
-        k11 += w * kap * j1v;
-    }
-}
-
 struct P2PArgs {
     int leaf_off;
     const LfD4* cen;
@@ -117,14 +50,50 @@ struct P2PArgs {
     double* phi;
     double* fld;
     int Qn;
+    LfmmSurrView sv;  // learned near-field kernels (sv.ready = 0: quadrature only)
 };
 
 #define P2P_T 128
 
+// Reaction kernels of one pair by the quadrature, accumulated into the sums.
+template <typename R>
+__device__ __forceinline__ void p2p_reaction_add(const LfmmComp& cp, R dx, R dy, R dz, R qs, int Qn, LfSum<R>& P,
+                                                 LfSum<R>& Ex, LfSum<R>& Ey, LfSum<R>& Ez)
+{
+    typedef LfMath<R> F;
+    R h = (cp.a == 1) ? dz : -dz;
+    R rho = F::Sqrt(dx * dx + dy * dy);
+    R k00, k10, k11;
+    lf_reaction_pair<R>(cp, rho, h, Qn, c_gl_t, c_gl_w, k00, k10, k11);
+    P.add(qs * k00);
+    Ez.add((cp.a == 1) ? qs * k10 : -qs * k10);
+    if (rho > R(0)) {
+        R g = qs * k11 / rho;
+        Ex.add(g * dx);
+        Ey.add(g * dy);
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void p2p_free_add(R dx, R dy, R dz, R qs, LfSum<R>& P, LfSum<R>& Ex, LfSum<R>& Ey,
+                                             LfSum<R>& Ez)
+{
+    typedef LfMath<R> F;
+    R r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 > R(0)) {
+        R ir = F::Rsqrt(r2);
+        R qi = qs * ir;
+        R q3 = qi * ir * ir;
+        P.add(qi);
+        Ex.add(q3 * dx);
+        Ey.add(q3 * dy);
+        Ez.add(q3 * dz);
+    }
+}
+
 template <typename R>
 __global__ void __launch_bounds__(P2P_T) k_p2p(P2PArgs a)
 {
-    typedef LfMath<R> F;
     __shared__ R sx[P2P_T], sy[P2P_T], sz[P2P_T], sq[P2P_T];
     const R* q = reinterpret_cast<const R*>(a.q);
     const int t = a.leaf_off + blockIdx.x;
@@ -161,36 +130,10 @@ __global__ void __launch_bounds__(P2P_T) k_p2p(P2PArgs a)
                 if (!valid) continue;
                 const int cnt = min(P2P_T, se - cb);
                 if (cp.is_free) {
-                    for (int u = 0; u < cnt; ++u) {
-                        R dx = xi - sx[u], dy = yi - sy[u], dz = zi - sz[u];
-                        R r2 = dx * dx + dy * dy + dz * dz;
-                        if (r2 > R(0)) {
-                            R ir = F::Rsqrt(r2);
-                            R qi = sq[u] * ir;
-                            R q3 = qi * ir * ir;
-                            P.add(qi);
-                            Ex.add(q3 * dx);
-                            Ey.add(q3 * dy);
-                            Ez.add(q3 * dz);
-                        }
-                    }
+                    for (int u = 0; u < cnt; ++u) p2p_free_add<R>(xi - sx[u], yi - sy[u], zi - sz[u], sq[u], P, Ex, Ey, Ez);
                 } else {
-                    for (int u = 0; u < cnt; ++u) {
-                        R dx = xi - sx[u], dy = yi - sy[u];
-                        R dz = zi - sz[u];
-                        R h = (cp.a == 1) ? dz : -dz;
-                        R rho = F::Sqrt(dx * dx + dy * dy);
-                        R k00, k10, k11;
-                        lf_reaction_pair<R>(cp, rho, h, a.Qn, k00, k10, k11);
-                        R qs = sq[u];
-                        P.add(qs * k00);
-                        Ez.add((cp.a == 1) ? qs * k10 : -qs * k10);
-                        if (rho > R(0)) {
-                            R g = qs * k11 / rho;
-                            Ex.add(g * dx);
-                            Ey.add(g * dy);
-                        }
-                    }
+                    for (int u = 0; u < cnt; ++u)
+                        p2p_reaction_add<R>(cp, xi - sx[u], yi - sy[u], zi - sz[u], sq[u], a.Qn, P, Ex, Ey, Ez);
                 }
             }
         }
@@ -200,6 +143,180 @@ __global__ void __launch_bounds__(P2P_T) k_p2p(P2PArgs a)
             a.fld[3 * (size_t)i + 1] = (double)Ey.s;
             a.fld[3 * (size_t)i + 2] = (double)Ez.s;
         }
+    }
+}
+
+// Near field with the learned reaction kernels.  For a trained component each
+// warp first looks its 32 pairs (one source against the warp's 32 targets) up
+// in the error table; if any lane accepts, the warp evaluates the network for
+// all 32 (tensor-core MMAs need the whole warp).  Rejected pairs are not
+// integrated in place (that would stall the warp on the slowest lane):
+// they go to a per-warp queue of (target lane, source) entries that is drained
+// 32 at a time, one pair per lane, the results added into per-target
+// shared-memory accumulators.
+#define P2P_W (P2P_T / 32)
+#define P2P_QCAP 64
+
+template <typename R>
+__device__ __forceinline__ void p2p_drain(const LfmmComp& cp, const uint16_t* qe, int count, int lane, int wbase,
+                                          const R* tx, const R* ty, const R* tz, const R* sx, const R* sy,
+                                          const R* sz, const R* sq, R (*acc)[4], int Qn)
+{
+    typedef LfMath<R> F;
+    if (lane >= count) return;
+    const int ent = qe[lane];
+    const int o = wbase + (ent >> 7), u = ent & 127;
+    R dx = tx[o] - sx[u], dy = ty[o] - sy[u], dz = tz[o] - sz[u];
+    R h = (cp.a == 1) ? dz : -dz;
+    R rho = F::Sqrt(dx * dx + dy * dy);
+    R k00, k10, k11;
+    lf_reaction_pair<R>(cp, rho, h, Qn, c_gl_t, c_gl_w, k00, k10, k11);
+    R qs = sq[u];
+    atomicAdd(&acc[o][0], qs * k00);
+    atomicAdd(&acc[o][3], (cp.a == 1) ? qs * k10 : -qs * k10);
+    if (rho > R(0)) {
+        R g = qs * k11 / rho;
+        atomicAdd(&acc[o][1], g * dx);
+        atomicAdd(&acc[o][2], g * dy);
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(P2P_T) k_p2p_net(P2PArgs a)
+{
+    typedef LfMath<R> F;
+    __shared__ R sx[P2P_T], sy[P2P_T], sz[P2P_T], sq[P2P_T];
+    __shared__ R tx[P2P_T], ty[P2P_T], tz[P2P_T];
+    __shared__ R acc[P2P_T][4];  // deferred (phi, Ex, Ey, Ez) per target
+    __shared__ uint16_t qbuf[P2P_W][P2P_QCAP];
+    const R* q = reinterpret_cast<const R*>(a.q);
+    const int t = a.leaf_off + blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, wbase = tid & ~31;
+    const LfD4 ct = a.cen[t];
+    const int tb = a.pbeg[t], te = a.pend[t];
+    unsigned long long n_net = 0, n_quad = 0;
+    for (int base = tb; base < te; base += P2P_T) {
+        const int i = base + tid;
+        const bool valid = i < te;
+        R xi = 0, yi = 0, zi = 0;
+        if (valid) {
+            xi = (R)(a.xs[i] - ct.x);
+            yi = (R)(a.ys[i] - ct.y);
+            zi = (R)(a.zs[i] - ct.z);
+        }
+        tx[tid] = xi;
+        ty[tid] = yi;
+        tz[tid] = zi;
+        acc[tid][0] = acc[tid][1] = acc[tid][2] = acc[tid][3] = R(0);
+        __syncwarp();
+        LfSum<R> P, Ex, Ey, Ez;
+        for (int e = a.nbeg[t]; e < a.nend[t]; ++e) {
+            const uint32_t ent = a.nent[e];
+            const int c = (int)(ent >> LFMM_ENT_SHIFT);
+            const int s = (int)(ent & LFMM_ENT_MASK);
+            const LfmmComp& cp = c_ncomp[c];
+            const int sb = a.pbeg[s], se = a.pend[s];
+            const bool use_net = !cp.is_free && a.sv.meta[c].trained;
+            LfmmSurrMeta sm;
+            const __nv_bfloat16* sW = nullptr;
+            const float *sB = nullptr, *serr = nullptr;
+            float ht = 0.f;
+            if (use_net) {
+                sm = a.sv.meta[c];
+                sW = reinterpret_cast<const __nv_bfloat16*>(a.sv.W) + (size_t)c * SW_N;
+                sB = a.sv.B + (size_t)c * SB_N;
+                serr = a.sv.err + (size_t)c * LFMM_SURR_CELLS * LFMM_SURR_CELLS;
+                // depth of the target below (a = 1) or above (a = 2) its interface
+                const double zt = valid ? a.zs[i] : ct.z;
+                ht = (float)((cp.a == 1) ? zt - cp.iface : cp.iface - zt);
+            }
+            for (int cb = sb; cb < se; cb += P2P_T) {
+                const int j = cb + tid;
+                __syncthreads();
+                if (j < se) {
+                    sx[tid] = (R)(a.xs[j] - ct.x);
+                    sy[tid] = (R)(a.ys[j] - ct.y);
+                    double zj = cp.is_free ? a.zs[j] : cp.s * a.zs[j] + cp.o;
+                    sz[tid] = (R)(zj - ct.z);
+                    sq[tid] = q[j];
+                }
+                __syncthreads();
+                const int cnt = min(P2P_T, se - cb);
+                if (!use_net) {
+                    if (!valid) continue;
+                    if (cp.is_free) {
+                        for (int u = 0; u < cnt; ++u)
+                            p2p_free_add<R>(xi - sx[u], yi - sy[u], zi - sz[u], sq[u], P, Ex, Ey, Ez);
+                    } else {
+                        for (int u = 0; u < cnt; ++u)
+                            p2p_reaction_add<R>(cp, xi - sx[u], yi - sy[u], zi - sz[u], sq[u], a.Qn, P, Ex, Ey, Ez);
+                        n_quad += cnt;
+                    }
+                    continue;
+                }
+                // every lane of the warp runs this loop (valid or not)
+                int qn = 0;
+                for (int u = 0; u < cnt; ++u) {
+                    R dx = xi - sx[u], dy = yi - sy[u], dz = zi - sz[u];
+                    R h = (cp.a == 1) ? dz : -dz;
+                    R rho = F::Sqrt(dx * dx + dy * dy);
+                    const float hs = (float)h - ht;
+                    const bool net = valid && lf_surr_cell_ok(sm, serr, (float)rho, ht, hs, a.sv.tol);
+                    if (__any_sync(0xffffffffu, net)) {
+                        float f[4], y[3];
+                        surr_features(sm, (float)rho, ht, hs, f);
+                        __syncwarp();
+                        lf_surr_warp(sW, sB, f, y);
+                        if (net) {
+                            R K[3];
+                            lf_surr_kernels<R>(cp, sm, rho, h, y, K);
+                            R qs = sq[u];
+                            P.add(qs * K[0]);
+                            Ez.add((cp.a == 1) ? qs * K[1] : -qs * K[1]);
+                            if (rho > R(0)) {
+                                R g = qs * K[2] / rho;
+                                Ex.add(g * dx);
+                                Ey.add(g * dy);
+                            }
+                            ++n_net;
+                        }
+                    }
+                    const bool rej = valid && !net;
+                    n_quad += rej;
+                    const unsigned m = __ballot_sync(0xffffffffu, rej);
+                    if (m) {
+                        if (rej) qbuf[wid][qn + __popc(m & ((1u << lane) - 1u))] = (uint16_t)((lane << 7) | u);
+                        qn += __popc(m);
+                        if (qn >= 32) {
+                            __syncwarp();
+                            qn -= 32;
+                            p2p_drain<R>(cp, &qbuf[wid][qn], 32, lane, wbase, tx, ty, tz, sx, sy, sz, sq, acc, a.Qn);
+                            __syncwarp();
+                        }
+                    }
+                }
+                if (qn > 0) {
+                    __syncwarp();
+                    p2p_drain<R>(cp, &qbuf[wid][0], qn, lane, wbase, tx, ty, tz, sx, sy, sz, sq, acc, a.Qn);
+                    __syncwarp();
+                }
+            }
+        }
+        __syncwarp();
+        if (valid) {
+            P.add(acc[tid][0]);
+            Ex.add(acc[tid][1]);
+            Ey.add(acc[tid][2]);
+            Ez.add(acc[tid][3]);
+            a.phi[i] = (double)P.s;
+            a.fld[3 * (size_t)i + 0] = (double)Ex.s;
+            a.fld[3 * (size_t)i + 1] = (double)Ey.s;
+            a.fld[3 * (size_t)i + 2] = (double)Ez.s;
+        }
+    }
+    if (n_net | n_quad) {
+        atomicAdd(&a.sv.counters[0], n_net);
+        atomicAdd(&a.sv.counters[1], n_quad);
     }
 }
 
@@ -232,11 +349,22 @@ LfErr lf_near_field(lfmm_ctx* ctx, cudaStream_t st)
     a.phi = ctx->phi_near.as<double>();
     a.fld = ctx->fld_near.as<double>();
     a.Qn = ctx->gl_q_near;
+    LF_TRY(lf_reserve(ctx->surr_counters, 64));
+    LF_CHECK(cudaMemsetAsync(ctx->surr_counters.ptr, 0, 16, st));
+    LF_TRY(lf_surrogate_device_view(ctx, &a.sv));
     const int ph = lf_prof_start(ctx, LFMM_TIME_P2P, st);
-    if (ctx->precision)
-        ++ctx->launches, k_p2p<float><<<leaf.nbox, P2P_T, 0, st>>>(a);
-    else
-        ++ctx->launches, k_p2p<double><<<leaf.nbox, P2P_T, 0, st>>>(a);
+    const bool net = a.sv.ready != 0;
+    if (ctx->precision) {
+        if (net)
+            ++ctx->launches, k_p2p_net<float><<<leaf.nbox, P2P_T, 0, st>>>(a);
+        else
+            ++ctx->launches, k_p2p<float><<<leaf.nbox, P2P_T, 0, st>>>(a);
+    } else {
+        if (net)
+            ++ctx->launches, k_p2p_net<double><<<leaf.nbox, P2P_T, 0, st>>>(a);
+        else
+            ++ctx->launches, k_p2p<double><<<leaf.nbox, P2P_T, 0, st>>>(a);
+    }
     LF_TRY(lf_cuda(cudaGetLastError(), "p2p"));
     lf_prof_stop(ctx, ph, st);
     return LfErr();
@@ -279,7 +407,7 @@ __global__ void k_reaction_kernel(int comp, int npts, const double* __restrict__
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= npts) return;
     double k00, k10, k11;
-    lf_reaction_pair<double>(c_ncomp[comp], rho[i], h[i], Q, k00, k10, k11);
+    lf_reaction_pair<double>(c_ncomp[comp], rho[i], h[i], Q, c_gl_t, c_gl_w, k00, k10, k11);
     out[3 * (size_t)i] = k00;
     out[3 * (size_t)i + 1] = k10;
     out[3 * (size_t)i + 2] = k11;

@@ -15,9 +15,11 @@ import numpy as np
 from . import build as _build
 
 OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETIMEOUT, ENUMERIC = range(7)
-OPT_PRECISION, OPT_LEAF_CAP, OPT_PROFILE, OPT_QUAD_NODES = 1, 2, 3, 4
+OPT_PRECISION, OPT_LEAF_CAP, OPT_PROFILE, OPT_QUAD_NODES, OPT_SURROGATE, OPT_SURROGATE_TOL = 1, 2, 3, 4, 5, 6
 STAT_NAMES = ["n", "depth", "boxes", "leaves", "m2l_free", "m2l_reaction", "p2p_free", "p2p_reaction",
-              "components", "m2m_edges", "launches", "reaction_keys"]
+              "components", "m2m_edges", "launches", "reaction_keys", "surr_net_pairs", "surr_quad_pairs"]
+SURR_NPARAM = 8835
+SURR_INFO = ["trained", "max_err", "cells_ok", "loss", "n_train", "n_val", "samples_ok"]
 TIME_NAMES = ["p2m", "m2m", "m2l_free", "m2l_reaction", "l2l", "l2p", "p2p", "total", "build"]
 _STATUS = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ESTATE: "ESTATE", ETIMEOUT: "ETIMEOUT",
            ENUMERIC: "ENUMERIC"}
@@ -38,7 +40,9 @@ _ctxp = ctypes.c_void_p
 
 EXPORTED = ["lfmm_create", "lfmm_set_option", "lfmm_build", "lfmm_build_device", "lfmm_evaluate",
             "lfmm_evaluate_device", "lfmm_last_error", "lfmm_destroy", "lfmm_get_stats", "lfmm_get_timings",
-            "lfmm_sommerfeld_tables", "lfmm_reaction_kernel", "lfmm_reaction_kernel_noalloc", "lfmm_gauss_laguerre"]
+            "lfmm_sommerfeld_tables", "lfmm_reaction_kernel", "lfmm_reaction_kernel_noalloc", "lfmm_gauss_laguerre",
+            "lfmm_surrogate_train", "lfmm_surrogate_info", "lfmm_surrogate_eval", "lfmm_surrogate_get_params",
+            "lfmm_surrogate_set_params", "lfmm_surrogate_forward", "lfmm_surrogate_loss_grad"]
 NOALLOC_MAX_POINTS = 65536
 
 
@@ -72,6 +76,15 @@ def load(build: bool = True):
     lib.lfmm_reaction_kernel.argtypes = [_ctxp] + [ctypes.c_int] * 5 + [_dp, _dp, _dp]
     lib.lfmm_reaction_kernel_noalloc.argtypes = [_ctxp] + [ctypes.c_int] * 5 + [_dp, _dp, _dp]
     lib.lfmm_gauss_laguerre.argtypes = [ctypes.c_int, _dp, _dp]
+    _fp = ctypes.POINTER(ctypes.c_float)
+    comp = [ctypes.c_int] * 4
+    lib.lfmm_surrogate_train.argtypes = [_ctxp, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64]
+    lib.lfmm_surrogate_info.argtypes = [_ctxp] + comp + [_dp]
+    lib.lfmm_surrogate_eval.argtypes = [_ctxp] + comp + [ctypes.c_int, _dp, _dp, _dp, _dp]
+    lib.lfmm_surrogate_get_params.argtypes = [_ctxp] + comp + [_fp]
+    lib.lfmm_surrogate_set_params.argtypes = [_ctxp] + comp + [_fp]
+    lib.lfmm_surrogate_forward.argtypes = [_ctxp] + comp + [ctypes.c_int, _fp, _fp]
+    lib.lfmm_surrogate_loss_grad.argtypes = [_ctxp] + comp + [ctypes.c_int, _fp, _fp, _dp, _fp]
     for name in EXPORTED:
         if name not in ("lfmm_last_error", "lfmm_destroy"):
             getattr(lib, name).restype = ctypes.c_int
@@ -200,6 +213,60 @@ class LayeredFMM:
         self._check(self._lib.lfmm_reaction_kernel_noalloc(self._ctx, l, lp, a, b, rho.shape[0], _ptr(rho),
                                                            _ptr(h), _ptr(out)), "lfmm_reaction_kernel_noalloc")
         return out
+
+    # ---- learned near-field reaction kernels ------------------------------
+    def surrogate_train(self, nsamples: int = 1 << 20, epochs: int = 4, seed: int = 1):
+        self._check(self._lib.lfmm_surrogate_train(self._ctx, int(nsamples), int(epochs), int(seed)),
+                    "lfmm_surrogate_train")
+
+    def surrogate_info(self, l, lp, a, b) -> dict:
+        out = np.zeros(8)
+        self._check(self._lib.lfmm_surrogate_info(self._ctx, l, lp, a, b, _ptr(out)), "lfmm_surrogate_info")
+        return {k: float(v) for k, v in zip(SURR_INFO, out)}
+
+    def surrogate_eval(self, l, lp, a, b, rho, ht, hs):
+        """-> [n, 4]: network I_00, I_10, I_11 and the error-table acceptance flag."""
+        rho, ht, hs = (_f64(v).ravel() for v in (rho, ht, hs))
+        out = np.zeros((rho.shape[0], 4))
+        self._check(self._lib.lfmm_surrogate_eval(self._ctx, l, lp, a, b, rho.shape[0], _ptr(rho), _ptr(ht),
+                                                  _ptr(hs), _ptr(out)), "lfmm_surrogate_eval")
+        return out
+
+    def surrogate_params(self, l, lp, a, b):
+        th = np.zeros(SURR_NPARAM, dtype=np.float32)
+        fp = ctypes.POINTER(ctypes.c_float)
+        self._check(self._lib.lfmm_surrogate_get_params(self._ctx, l, lp, a, b, _ptr(th, fp)),
+                    "lfmm_surrogate_get_params")
+        return th
+
+    def surrogate_set_params(self, l, lp, a, b, theta):
+        th = np.ascontiguousarray(theta, dtype=np.float32).ravel()
+        if th.shape[0] != SURR_NPARAM:
+            raise ValueError("need %d parameters" % SURR_NPARAM)
+        fp = ctypes.POINTER(ctypes.c_float)
+        self._check(self._lib.lfmm_surrogate_set_params(self._ctx, l, lp, a, b, _ptr(th, fp)),
+                    "lfmm_surrogate_set_params")
+
+    def surrogate_forward(self, l, lp, a, b, x):
+        """Raw (standardised) network outputs [n, 3] for features x [n, 4] by the inference kernel."""
+        x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, 4)
+        y = np.zeros((x.shape[0], 3), dtype=np.float32)
+        fp = ctypes.POINTER(ctypes.c_float)
+        self._check(self._lib.lfmm_surrogate_forward(self._ctx, l, lp, a, b, x.shape[0], _ptr(x, fp), _ptr(y, fp)),
+                    "lfmm_surrogate_forward")
+        return y
+
+    def surrogate_loss_grad(self, l, lp, a, b, x, y):
+        """Loss and parameter gradient on the device for x [n,4], y [n,3] (n a multiple of 64)."""
+        x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, 4)
+        y = np.ascontiguousarray(y, dtype=np.float32).reshape(-1, 3)
+        fp = ctypes.POINTER(ctypes.c_float)
+        loss = ctypes.c_double(0.0)
+        g = np.zeros(SURR_NPARAM, dtype=np.float32)
+        self._check(self._lib.lfmm_surrogate_loss_grad(self._ctx, l, lp, a, b, x.shape[0], _ptr(x, fp),
+                                                       _ptr(y, fp), ctypes.byref(loss), _ptr(g, fp)),
+                    "lfmm_surrogate_loss_grad")
+        return loss.value, g
 
     def close(self):
         if getattr(self, "_ctx", None):

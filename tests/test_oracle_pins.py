@@ -345,3 +345,45 @@ def test_polarization_coordinates():
     for (a, b, zz) in [(1, 1, z11), (2, 2, z22), (1, 2, d[l] - (d[lp - 1] - zp)), (2, 1, d[l - 1] + (zp - d[lp]))]:
         parts += oracle.sommerfeld_K_images(d, MEDIA[0], 1, 1, a, b, 0, 0, 0.1, abs(r[2] - zz))
     assert u == pytest.approx(parts, rel=1e-13)
+
+
+def test_mlp_reference_gradient_matches_finite_differences_and_autograd():
+    # the surrogate network's reference backward pass (oracle/mlp.py)
+    from oracle import mlp
+    rng = np.random.default_rng(3)
+    theta = rng.normal(0, 0.3, mlp.NPARAM)
+    x = rng.uniform(-1, 1, (17, 4))
+    y = rng.normal(0, 1, (17, 3))
+    loss, grad = mlp.loss_and_grad(theta, x, y, quantize=False)
+    idx = rng.choice(mlp.NPARAM, 40, replace=False)
+    h = 1e-6
+    for i in idx:
+        tp = theta.copy(); tp[i] += h
+        tm = theta.copy(); tm[i] -= h
+        fd = (mlp.loss_and_grad(tp, x, y, quantize=False)[0] - mlp.loss_and_grad(tm, x, y, quantize=False)[0]) / (2 * h)
+        assert abs(fd - grad[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, grad[i])
+    torch = pytest.importorskip("torch")
+    t = torch.tensor(theta, dtype=torch.float64, requires_grad=True)
+    parts, o = {}, 0
+    for name, shp in mlp.SHAPES:
+        n = int(np.prod(shp))
+        parts[name] = t[o:o + n].reshape(shp)
+        o += n
+    X = torch.tensor(x)
+    a = X
+    for k in ("1", "2", "3"):
+        a = torch.nn.functional.silu(a @ parts["W" + k].T + parts["b" + k])
+    out = a @ parts["W4"].T + parts["b4"]
+    L = ((out - torch.tensor(y)) ** 2).sum() / x.shape[0]
+    L.backward()
+    assert abs(float(L) - loss) < 1e-12
+    assert np.max(np.abs(t.grad.numpy() - grad)) < 1e-12
+
+
+def test_bf16_rounding_reference():
+    from oracle import mlp
+    v = np.array([1.0, 1.00390625, 1.001953125, 3.14159, -2.5e-3], dtype=np.float32)
+    r = mlp.bf16_round(v)
+    torch = pytest.importorskip("torch")
+    ref = torch.tensor(v).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(r, ref)
