@@ -56,7 +56,9 @@ enum {
     LFMM_OPT_PROFILE = 3,   /* 1 = time every stage with CUDA events (lfmm_get_timings) */
     LFMM_OPT_QUAD_NODES = 4, /* Gauss-Laguerre nodes of the M2L remainder integrals (16..128, default 64) */
     LFMM_OPT_SURROGATE = 5,  /* 1 = near-field reaction kernels by the trained network (default 0) */
-    LFMM_OPT_SURROGATE_TOL = 6 /* error estimate above which a pair falls back to quadrature (default 1e-6) */
+    LFMM_OPT_SURROGATE_TOL = 6, /* error estimate above which a pair falls back to quadrature (default 1e-6) */
+    LFMM_OPT_TENSOR_CORES = 7   /* 1 = float32 free M2L on the tensor cores (3xTF32) where (p+1)^2 <= 128
+                                   (default); 0 = on the CUDA cores */
 };
 
 /* Create a context for the medium.
@@ -124,6 +126,7 @@ enum {
     LFMM_STAT_REACTION_KEYS = 11, /* distinct (component, level, offset) reaction M2L operators */
     LFMM_STAT_SURR_NET = 12,      /* near-field reaction pairs of the last evaluate done by the network */
     LFMM_STAT_SURR_QUAD = 13,     /* ... and by the quadrature */
+    LFMM_STAT_TIMEOUTS = 14,      /* bounded device waits of the last evaluate that ran out (0 expected) */
     LFMM_STAT_COUNT = 16
 };
 lfmm_status lfmm_get_stats(const lfmm_ctx* ctx, int64_t* out, int nout);

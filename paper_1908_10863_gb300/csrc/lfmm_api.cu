@@ -555,6 +555,9 @@ lfmm_status lfmm_set_option(lfmm_ctx* ctx, int opt, double v)
         if (v != 0.0 && !ctx->surr_ready) return fail(ctx, "ESTATE: train the surrogate first"), LFMM_ESTATE;
         ctx->use_surr = (v != 0.0);
         return LFMM_OK;
+    case LFMM_OPT_TENSOR_CORES:
+        ctx->use_tc = (v != 0.0);
+        return LFMM_OK;
     case LFMM_OPT_SURROGATE_TOL:
         if (!(v > 0.0)) return fail(ctx, "EINVAL: tolerance must be positive");
         ctx->surr_tol = v;
@@ -627,6 +630,8 @@ static lfmm_status eval_common(lfmm_ctx* ctx, int nrhs, const double* q_dev, dou
 {
     const int64_t n = ctx->n;
     prof_reset(ctx);
+    cudaError_t ce = cudaMemsetAsync(ctx->counts.as<char>() + LFMM_TIMEOUT_OFF, 0, 4, ctx->s_main);
+    if (ce != cudaSuccess) return fail(ctx, lf_cuda(ce, "timeout flag"));
     for (int r = 0; r < nrhs; ++r) {
         LfErr e = lf_evaluate_sorted(ctx, q_dev + (size_t)r * n, phi_dev + (size_t)r * n,
                                      fld_dev ? fld_dev + (size_t)r * n * 3 : nullptr, ctx->s_main);
@@ -659,8 +664,13 @@ lfmm_status lfmm_evaluate(lfmm_ctx* ctx, int nrhs, const double* q, double* phi,
     ce = cudaMemcpyAsync(phi, ctx->phi_stage.ptr, (size_t)n * nrhs * 8, cudaMemcpyDeviceToHost, ctx->s_main);
     if (ce == cudaSuccess && field)
         ce = cudaMemcpyAsync(field, ctx->fld_stage.ptr, (size_t)n * nrhs * 24, cudaMemcpyDeviceToHost, ctx->s_main);
+    int timeouts = 0;
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(&timeouts, ctx->counts.as<char>() + LFMM_TIMEOUT_OFF, 4, cudaMemcpyDeviceToHost,
+                             ctx->s_main);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->s_main);
     if (ce != cudaSuccess) return fail(ctx, lf_cuda(ce, "evaluate"));
+    if (timeouts) return fail(ctx, "ETIMEOUT: a device wait of the tensor-core M2L ran out"), LFMM_ETIMEOUT;
     if (ctx->profile) prof_collect(ctx, true);
     return LFMM_OK;
 }
@@ -708,7 +718,7 @@ void lfmm_destroy(lfmm_ctx* ctx)
                       &ctx->m2r_tgt, &ctx->m2r_kstart, &ctx->m2r_kval, &ctx->m2r_tables, &ctx->m2r_levelh,
                       &ctx->m2r_batches, &ctx->surr_theta, &ctx->surr_grad, &ctx->surr_m1,
                       &ctx->surr_m2, &ctx->surr_w, &ctx->surr_b, &ctx->surr_meta, &ctx->surr_err, &ctx->surr_comps,
-                      &ctx->surr_xoff, &ctx->surr_counters};
+                      &ctx->surr_xoff, &ctx->surr_counters, &ctx->m2l_Atc, &ctx->m2l_tc_tiles, &ctx->m2l_Ms};
     for (DevBuf* b : bufs) lf_free(*b);
     for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
@@ -723,6 +733,12 @@ lfmm_status lfmm_get_stats(const lfmm_ctx* ctx, int64_t* out, int nout)
     if (!ctx || !out || nout < 1) return LFMM_EINVAL;
     for (int i = 0; i < nout && i < LFMM_STAT_COUNT; ++i) out[i] = ctx->stats[i];
     if (nout > LFMM_STAT_LAUNCHES) out[LFMM_STAT_LAUNCHES] = ctx->launches;
+    if (nout > LFMM_STAT_TIMEOUTS && ctx->counts.ptr) {
+        int tmo = 0;
+        cudaStreamSynchronize(ctx->s_near);
+        if (lf_d2h(&tmo, ctx->counts.as<char>() + LFMM_TIMEOUT_OFF, 4, ctx->s_main) == cudaSuccess)
+            out[LFMM_STAT_TIMEOUTS] = tmo;
+    }
     if (nout > LFMM_STAT_SURR_QUAD && ctx->surr_counters.ptr) {
         unsigned long long c[2] = {0, 0};
         cudaStreamSynchronize(ctx->s_near);

@@ -101,6 +101,9 @@ struct lfmm_ctx {
     // free-space M2L as per-offset GEMMs (p <= 15)
     DevBuf m2l_A64, m2l_A32, m2l_cls, m2l_inv, m2l_slots, m2l_keys, m2l_sorted, m2l_tiles, m2l_levelh;
     int m2l_rm = 0, m2l_rp = 0, m2l_ntiles = 0;
+    // tensor-core free M2L (float32 form, (p+1)^2 <= 128)
+    DevBuf m2l_Atc, m2l_tc_tiles, m2l_Ms;
+    int m2l_tc_ok = 0, m2l_tc_ntiles = 0, use_tc = 1, tc_groups = 27;
     // reaction M2L grouped by geometry key on interface-aligned levels
     DevBuf m2r_keys, m2r_order, m2r_tgt, m2r_kstart, m2r_kval, m2r_tables, m2r_levelh, m2r_batches;
     int m2r_nkeys = 0, m2r_nbatch = 0, m2r_keyed_from = 0;
@@ -165,6 +168,13 @@ LfErr lf_surrogate_eval_dev(lfmm_ctx* ctx, int comp, int n, const double* rho, c
 LfErr lf_surrogate_grad_dev(lfmm_ctx* ctx, int comp, int n, const float* x, const float* ystd, double* loss,
                             float* grad);
 LfErr lf_surrogate_device_view(lfmm_ctx* ctx, LfmmSurrView* v);
+
+// ---- tensor-core free M2L (lfmm_m2l_tc.cu) ----
+// byte offset in ctx->counts of the int counting device waits that ran out
+#define LFMM_TIMEOUT_OFF 40960
+LfErr lf_setup_m2l_tc(lfmm_ctx* ctx, const double* A64, int KP, int RP);
+LfErr lf_m2l_tc(lfmm_ctx* ctx, cudaStream_t st);
+int lf_m2l_tc_tile();
 LfErr lf_surrogate_alloc(lfmm_ctx* ctx);
 LfErr lf_surrogate_pack(lfmm_ctx* ctx, int comp);
 LfErr lf_surrogate_forward_dev(lfmm_ctx* ctx, int comp, int n, const float* x, float* y);

@@ -529,7 +529,10 @@ static LfErr far_field(lfmm_ctx* ctx, cudaStream_t st)
     const bool gemm = ctx->m2l_ntiles > 0;
     if (gemm) {
         ph = lf_prof_start(ctx, LFMM_TIME_M2L_FREE, st);
-        LF_TRY(lf_m2l_gemm(ctx, st));
+        if (sizeof(R) == 4 && ctx->use_tc && ctx->m2l_tc_ok && ctx->m2l_tc_ntiles > 0)
+            LF_TRY(lf_m2l_tc(ctx, st));
+        else
+            LF_TRY(lf_m2l_gemm(ctx, st));
         lf_prof_stop(ctx, ph, st);
     }
     if (ctx->m2r_nbatch > 0) {

@@ -108,6 +108,7 @@ LfErr lf_setup_m2l_ops(lfmm_ctx* ctx)
                     }
             }
     (void)nc;
+    LF_TRY(lf_setup_m2l_tc(ctx, A64.data(), KP, RP));
     std::vector<float> A32(A64.size());
     for (size_t i = 0; i < A64.size(); ++i) A32[i] = (float)A64[i];
     LF_TRY(lf_reserve(ctx->m2l_A64, A64.size() * 8));
@@ -225,6 +226,25 @@ LfErr lf_prepare_m2l(lfmm_ctx* ctx, cudaStream_t st)
         LF_TRY(lf_reserve(ctx->m2l_tiles, tiles.size() * sizeof(int4)));
         LF_CHECK(cudaMemcpyAsync(ctx->m2l_tiles.ptr, tiles.data(), tiles.size() * sizeof(int4),
                                  cudaMemcpyHostToDevice, st));
+    }
+    // wider tiles of the same (level, class) runs for the tensor-core kernel
+    std::vector<int4> tct;
+    ctx->m2l_tc_ntiles = 0;
+    if (ctx->m2l_tc_ok) {
+        const int TN = lf_m2l_tc_tile();
+        int st0 = 0;
+        for (int l = 2; l <= depth; ++l)
+            for (int c = 0; c < 8; ++c) {
+                int n = hcnt[16 + l * 8 + c];
+                for (int s = 0; s < n; s += TN) tct.push_back(make_int4(l, c, st0 + s, std::min(TN, n - s)));
+                st0 += n;
+            }
+        ctx->m2l_tc_ntiles = (int)tct.size();
+        if (!tct.empty()) {
+            LF_TRY(lf_reserve(ctx->m2l_tc_tiles, tct.size() * sizeof(int4)));
+            LF_CHECK(cudaMemcpyAsync(ctx->m2l_tc_tiles.ptr, tct.data(), tct.size() * sizeof(int4),
+                                     cudaMemcpyHostToDevice, st));
+        }
     }
     double hl[16] = {0};
     for (int l = 0; l <= depth && l < 16; ++l) hl[l] = ctx->levels[l].h;

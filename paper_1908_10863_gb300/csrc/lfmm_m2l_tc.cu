@@ -1,0 +1,464 @@
+// lfmm_m2l_tc.cu -- free-space M2L (eq. metole) on the tcgen05 tensor cores.
+//
+// The same per-offset real-linear maps A_o as the CUDA-core GEMM in
+// lfmm_m2l.cu, evaluated as D[r][j] = sum_o sum_k A_o[r][k] X_o[j][k] with
+//   r = output coefficient (M = 128 rows, expansions with (p+1)^2 <= 128),
+//   j = target box of the tile (N = 256 columns, one level and octant class),
+//   k = input coefficient of the source at offset o (K = 128 in 8 chunks of 16),
+// accumulated in tensor memory (128 lanes x 256 float32 columns).
+//
+// Precision: float32 operands as sums of two TF32 pieces, the operator
+// (a1 + a2, from its FP64 values) and the multipoles (x1 + x2, split once per
+// evaluation), with the three products a1 x1 + a1 x2 + a2 x1 ("3xTF32",
+// ~2^-21 of |a||x| per product).  What limits the result is the tensor
+// core's float32 accumulation: its error grows with the number of MMAs
+// summed into one accumulator, so each CTA takes only 7 of the 189 offsets
+// (27 CTAs per tile, joined by float atomics), which keeps the far field
+// within the CUDA-core float32 GEMM's error (measured: Err2 of the potential
+// against the FP64 path 2.0e-6 with 7 offsets per CTA, 1.2e-5 with 63,
+// 3.3e-5 with 189; 1.4e-6 for the CUDA-core float32 GEMM).
+//
+// One CTA = (tile of 256 targets, one third of its 189 offsets):
+//   warps 0..7  gather the 256 pre-split source multipoles of a (offset,
+//               K chunk) stage with 16-byte cp.async into the 64-byte-swizzled
+//               K-major layout (zeros where a target has no source there), two
+//               stages ahead of the tensor cores; thread 0 also starts the bulk
+//               copy of the matching operator chunk (stored pre-split and
+//               pre-swizzled in HBM);
+//   warp 8      one thread issues the 6 MMAs of a stage and commits them to
+//               the stage's "empty" barrier;
+//   epilogue    warps 0..7 read the accumulator (tcgen05.ld), scale by 1/h and
+//               add into the local expansions (float atomics: three CTAs share
+//               a tile).
+// Four stages of 48 KB buffer the operands.  Tiles of one octant class share
+// their offset list; each tile walks it from a different starting offset so
+// that concurrent CTAs read different operator chunks.  Every barrier wait is
+// bounded; on a timeout the CTA records an error, stops issuing work, waits
+// (bounded) for its copies in flight and frees its tensor memory.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "lfmm_ctx.h"
+
+#define LF_CHECK(call)                                    \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return lf_cuda(e_, #call); \
+    } while (0)
+#define LF_TRY(expr)                \
+    do {                            \
+        LfErr r_ = (expr);          \
+        if (!r_.empty()) return r_; \
+    } while (0)
+
+#define TC_N 256                     // targets per tile (MMA N)
+#define TC_M 128                     // output coefficients (MMA M)
+#define TC_KC 16                     // K elements per stage (64 bytes of float32)
+#define TC_NKC 8                     // K chunks (K = 128)
+#define TC_ROWB (TC_KC * 4)          // bytes per row of a stage tile
+#define TC_NOFF 189                  // offsets per octant class
+#define TC_NALL 343
+#define TC_PROD_WARPS 8
+#define TC_THREADS (32 * TC_PROD_WARPS + 32)
+#define TC_A_BYTES (TC_M * TC_ROWB)  // one operator piece of a stage: 8 KB
+#define TC_X_BYTES (TC_N * TC_ROWB)  // one multipole piece of a stage: 16 KB
+#define TC_AP 2                      // operator pieces
+#define TC_XP 2                      // multipole pieces
+#define TC_STAGE_BYTES (TC_AP * TC_A_BYTES + TC_XP * TC_X_BYTES)
+#define TC_MROW 128                  // floats per multipole piece row in the split copy (512 B)
+#define TC_STAGES 4
+#define TC_LAG 2                     // stages between a stage's copies and its hand-over
+#define TC_SMEM (TC_STAGES * TC_STAGE_BYTES + 1024)
+#define TC_TMEM_COLS 256
+#define TC_SPIN_CYCLES (1ll << 31)   // ~1 s at 2 GHz
+
+// ---------------------------------------------------------------------------
+// PTX helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
+        "r"(bytes)
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait: false after ~1 s
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+{
+    if (mbar_try(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try(bar, parity))
+        if (clock64() - t0 > TC_SPIN_CYCLES) return false;
+    return true;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ uint32_t to_tf32(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups 512 B apart
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+    d |= (uint64_t)1 << 16;                   // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(512 >> 4) << 32;          // stride byte offset
+    d |= (uint64_t)1 << 46;                   // descriptor version
+    d |= (uint64_t)4 << 61;                   // 64-byte swizzle
+    return d;
+}
+// instruction descriptor: D float32, A and B TF32, both K-major, M x N
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N)
+{
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, float v[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+        "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// byte offset of element (row, k) of a 64-byte-swizzled K-major tile (k < 16
+// float32): the 16-byte chunk index (address bits 4-5) is XORed with address
+// bits 7-8, i.e. with (row / 2) mod 4
+__host__ __device__ __forceinline__ uint32_t sw64(int row, int k)
+{
+    return (uint32_t)row * 64u + ((uint32_t)(((k >> 2) ^ (row >> 1)) & 3) << 4) + (uint32_t)(k & 3) * 4u;
+}
+
+struct TcArgs {
+    const int4* tiles;      // level, class, start, count
+    const int* sorted;      // target boxes grouped by (level, class)
+    const int* slots;       // [box][189] source box at each offset of the class, or -1
+    const int* cls;         // [8][189] offset index (0..342) of each class position
+    const double* levelh;   // box size per level
+    const unsigned char* A; // [343][4 chunks][2 pieces x 16 KB], pre-swizzled
+    const float* Ms;        // split multipoles [box + 1][2 pieces][128] (last box: zeros)
+    int zero_row;           // index of the zero box of Ms
+    float* L;               // locals [box][nc]
+    int nc;
+    int groups;             // CTAs per tile (offset groups; divides 189)
+    int* err;               // [0]: timeouts
+};
+
+__global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(TcArgs g)
+{
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                         ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full_bar[TC_STAGES], empty_bar[TC_STAGES], done_bar;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort;
+    __shared__ int s_tb[TC_N];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int item = blockIdx.x;
+    const int4 tile = g.tiles[item / g.groups];
+    const int grp = item % g.groups;
+    const int goff = TC_NOFF / g.groups;
+    const int level = tile.x, cl = tile.y, start = tile.z, cnt = tile.w;
+    const int nc = g.nc;
+    const int nstage = goff * TC_NKC;
+
+    if (tid < TC_N) s_tb[tid] = (tid < cnt) ? g.sorted[start + tid] : -1;
+    if (tid == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(&full_bar[s], 32 * TC_PROD_WARPS + 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        mbar_init(&done_bar, 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == TC_PROD_WARPS) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(TC_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+
+    if (warp < TC_PROD_WARPS) {
+        // ---------------- producers ----------------
+        // stage it is filled at iteration it and handed to the tensor cores at
+        // iteration it + TC_LAG, once its copies have landed
+        const int ptid = tid;  // 0 .. 255
+        const int rot = (item / g.groups) % goff;
+        int armed = 0;         // stages with a bulk copy issued by this thread, for the bounded drain
+        int my_src = -1;       // source of row (warp * 32 + lane) at the current offset
+        int it = 0;
+        for (; it < nstage; ++it) {
+            const int s = it % TC_STAGES, round = it / TC_STAGES;
+            const int oi = grp * goff + (it / TC_NKC + rot) % goff, kc = it % TC_NKC;
+            if (it >= TC_STAGES) {
+                if (!mbar_wait(&empty_bar[s], (round - 1) & 1)) atomicExch(&s_abort, 1);
+            }
+            if (*(volatile int*)&s_abort) break;
+            unsigned char* st = sm + (size_t)s * TC_STAGE_BYTES;
+            if (ptid == 0) {
+                const int o = g.cls[cl * TC_NOFF + oi];
+                mbar_arrive_tx(&full_bar[s], TC_AP * TC_A_BYTES);
+                bulk_g2s(st, g.A + ((size_t)o * TC_NKC + kc) * (TC_AP * TC_A_BYTES), TC_AP * TC_A_BYTES,
+                         &full_bar[s]);
+                armed = it + 1;
+            }
+            if (kc == 0) {
+                const int tb = s_tb[warp * 32 + lane];
+                my_src = (tb >= 0) ? g.slots[(size_t)tb * TC_NOFF + oi] : -1;
+            }
+            // 32 rows x 2 pieces x 4 chunks of 16 B per warp: 8 per lane
+            unsigned char* xs = st + TC_AP * TC_A_BYTES;
+            const uint32_t xbase = smem_u32(xs);
+            const int chunk = lane & 3;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int piece = i >> 2;
+                const int rl = (i & 3) * 8 + (lane >> 2);
+                const int src = __shfl_sync(0xffffffffu, my_src, rl);
+                const int row = warp * 32 + rl;
+                const uint32_t off = piece * TC_X_BYTES + sw64(row, chunk * 4);
+                if (src >= 0) {
+                    const float* gsrc = g.Ms + ((size_t)src * TC_XP + piece) * TC_MROW + kc * TC_KC + chunk * 4;
+                    cp_async16(xbase + off, gsrc);
+                } else {
+                    *reinterpret_cast<float4*>(xs + off) = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+            cp_async_commit();
+            if (it >= TC_LAG) {
+                cp_async_wait<TC_LAG>();
+                fence_async_smem();
+                mbar_arrive(&full_bar[(it - TC_LAG) % TC_STAGES]);
+            }
+        }
+        cp_async_wait<0>();
+        fence_async_smem();
+        for (int j = (it > TC_LAG ? it - TC_LAG : 0); j < it; ++j) mbar_arrive(&full_bar[j % TC_STAGES]);
+        // drain: the bulk copies this thread issued complete on their full barriers
+        if (ptid == 0 && *(volatile int*)&s_abort) {
+            for (int j = (armed > TC_STAGES ? armed - TC_STAGES : 0); j < armed; ++j)
+                mbar_wait(&full_bar[j % TC_STAGES], (j / TC_STAGES) & 1);
+        }
+        // ---------------- epilogue ----------------
+        const bool ok = mbar_wait(&done_bar, 0);
+        tc_fence_after();
+        if (ok && !*(volatile int*)&s_abort) {
+            const int q = warp & 3, half = warp >> 2;
+            const int row = 32 * q + lane;
+            const float ih = (float)(1.0 / g.levelh[level]);
+#pragma unroll 1
+            for (int ch = 0; ch < 4; ++ch) {
+                const int col0 = half * 128 + ch * 32;
+                float v[32];
+                tc_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)col0, v);
+                if (row < nc) {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        const int j = col0 + i;
+                        if (j < cnt) atomicAdd(g.L + (size_t)s_tb[j] * nc + row, v[i] * ih);
+                    }
+                }
+            }
+        } else if (lane == 0) {
+            atomicAdd(g.err, 1);
+        }
+    } else {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            const uint32_t idesc = tc_idesc(TC_M, TC_N);
+            bool ok = true;
+            for (int it = 0; it < nstage && ok; ++it) {
+                const int s = it % TC_STAGES, round = it / TC_STAGES;
+                if (!mbar_wait(&full_bar[s], round & 1)) {
+                    ok = false;
+                    atomicExch(&s_abort, 1);
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t base = smem_u32(sm + (size_t)s * TC_STAGE_BYTES);
+                const uint32_t xb = base + TC_AP * TC_A_BYTES;
+                // a1 x1, a1 x2, a2 x1
+                const int pa[3] = {0, 0, 1}, px[3] = {0, 1, 0};
+#pragma unroll
+                for (int prod = 0; prod < 3; ++prod) {
+                    const uint32_t a = base + pa[prod] * TC_A_BYTES;
+                    const uint32_t b = xb + px[prod] * TC_X_BYTES;
+#pragma unroll
+                    for (int ks = 0; ks < TC_KC / 8; ++ks)
+                        tc_mma(tmem, smem_desc(a + 32 * ks), smem_desc(b + 32 * ks), idesc,
+                               (it | prod | ks) != 0 ? 1u : 0u);
+                }
+                tc_commit(&empty_bar[s]);
+            }
+            tc_commit(&done_bar);
+        }
+        __syncwarp();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == TC_PROD_WARPS) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host: operator blob and launch.
+// ---------------------------------------------------------------------------
+static inline uint32_t host_tf32(float x)
+{
+    // round to nearest (ties away from zero) at 10 explicit mantissa bits
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return u;
+    u = (u + 0x1000u) & 0xffffe000u;
+    return u;
+}
+
+// A64: [343][KP in][RP out] (double); builds the tensor-core operator blob
+LfErr lf_setup_m2l_tc(lfmm_ctx* ctx, const double* A64, int KP, int RP)
+{
+    const int nc = lf_nc(ctx->p);
+    ctx->m2l_tc_ok = 0;
+    if (nc > TC_M || KP < nc || RP < nc) return LfErr();
+    const size_t per = (size_t)TC_NKC * TC_AP * TC_A_BYTES;
+    std::vector<uint32_t> blob((size_t)TC_NALL * per / 4, 0u);
+    for (int o = 0; o < TC_NALL; ++o)
+        for (int kc = 0; kc < TC_NKC; ++kc) {
+            unsigned char* p0 = reinterpret_cast<unsigned char*>(blob.data()) + (size_t)o * per +
+                                (size_t)kc * TC_AP * TC_A_BYTES;
+            for (int r = 0; r < TC_M; ++r)
+                for (int k = 0; k < TC_KC; ++k) {
+                    const int kin = kc * TC_KC + k;
+                    double v = (r < nc && kin < nc) ? A64[((size_t)o * KP + kin) * RP + r] : 0.0;
+                    for (int q = 0; q < TC_AP; ++q) {
+                        uint32_t t = host_tf32((float)v);
+                        float tf;
+                        memcpy(&tf, &t, 4);
+                        memcpy(p0 + (size_t)q * TC_A_BYTES + sw64(r, k), &t, 4);
+                        v -= (double)tf;
+                    }
+                }
+        }
+    LF_TRY(lf_reserve(ctx->m2l_Atc, blob.size() * 4));
+    LF_CHECK(cudaMemcpy(ctx->m2l_Atc.ptr, blob.data(), blob.size() * 4, cudaMemcpyHostToDevice));
+    LF_CHECK(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+    ctx->m2l_tc_ok = 1;
+    return LfErr();
+}
+
+// multipoles [box][nc] -> two TF32 pieces per box, rows padded to 128 floats;
+// one more box of zeros stands in for missing sources
+__global__ void k_split_m(const float* __restrict__ M, int nbox, int nc, float* __restrict__ Ms)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t tot = (size_t)(nbox + 1) * TC_MROW;
+    if (i >= tot) return;
+    const int b = (int)(i / TC_MROW), k = (int)(i % TC_MROW);
+    const float x = (b < nbox && k < nc) ? M[(size_t)b * nc + k] : 0.f;
+    const uint32_t hi = to_tf32(x);
+    const uint32_t lo = to_tf32(x - __uint_as_float(hi));
+    Ms[((size_t)b * TC_XP + 0) * TC_MROW + k] = __uint_as_float(hi);
+    Ms[((size_t)b * TC_XP + 1) * TC_MROW + k] = __uint_as_float(lo);
+}
+
+LfErr lf_m2l_tc(lfmm_ctx* ctx, cudaStream_t st)
+{
+    if (ctx->m2l_tc_ntiles == 0) return LfErr();
+    const int nb = ctx->nbox_total;
+    LF_TRY(lf_reserve(ctx->m2l_Ms, (size_t)(nb + 1) * TC_XP * TC_MROW * sizeof(float)));
+    const size_t tot = (size_t)(nb + 1) * TC_MROW;
+    ++ctx->launches, k_split_m<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(ctx->Mexp.as<float>(), nb,
+                                                                              lf_nc(ctx->p), ctx->m2l_Ms.as<float>());
+    TcArgs g;
+    g.tiles = ctx->m2l_tc_tiles.as<int4>();
+    g.sorted = ctx->m2l_sorted.as<int>();
+    g.slots = ctx->m2l_slots.as<int>();
+    g.cls = ctx->m2l_cls.as<int>();
+    g.levelh = ctx->m2l_levelh.as<double>();
+    g.A = ctx->m2l_Atc.as<unsigned char>();
+    g.Ms = ctx->m2l_Ms.as<float>();
+    g.zero_row = nb;
+    g.L = ctx->Lexp.as<float>();
+    g.nc = lf_nc(ctx->p);
+    g.err = reinterpret_cast<int*>(ctx->counts.as<char>() + LFMM_TIMEOUT_OFF);
+    g.groups = ctx->tc_groups;
+    ++ctx->launches, k_m2l_tc<<<ctx->m2l_tc_ntiles * g.groups, TC_THREADS, TC_SMEM, st>>>(g);
+    return lf_cuda(cudaGetLastError(), "m2l tensor-core gemm");
+}
+
+int lf_m2l_tc_tile() { return TC_N; }

@@ -353,7 +353,9 @@ LfErr lf_near_field(lfmm_ctx* ctx, cudaStream_t st)
     LF_CHECK(cudaMemsetAsync(ctx->surr_counters.ptr, 0, 16, st));
     LF_TRY(lf_surrogate_device_view(ctx, &a.sv));
     const int ph = lf_prof_start(ctx, LFMM_TIME_P2P, st);
-    const bool net = a.sv.ready != 0;
+    // the network variant only where the near field holds reaction pairs (it
+    // needs far more registers, which slows the free-space part)
+    const bool net = a.sv.ready != 0 && ctx->stats[LFMM_STAT_P2P_REACTION] > 0;
     if (ctx->precision) {
         if (net)
             ++ctx->launches, k_p2p_net<float><<<leaf.nbox, P2P_T, 0, st>>>(a);

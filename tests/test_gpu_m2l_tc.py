@@ -1,0 +1,56 @@
+"""GPU tests of the tensor-core (tcgen05, 3xTF32) free-space M2L of the float32
+form: against the CUDA-core float32 GEMM, the FP64 path and the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1908_10863_gb300 import LayeredFMM, workloads
+from paper_1908_10863_gb300.lfmm import OPT_TENSOR_CORES
+
+pytestmark = pytest.mark.gpu
+
+
+def _eval(w, p, precision, tc):
+    with LayeredFMM(w.d, w.eps, p, precision=precision) as f:
+        f.set_option(OPT_TENSOR_CORES, tc)
+        f.build(w.xyz, w.layer)
+        phi, E = f.evaluate(w.q)
+        st = f.stats()
+    return phi, E, st
+
+
+@pytest.mark.parametrize("n", [3000, 40000])
+def test_tensor_core_m2l_matches_cuda_cores(n):
+    # 3000: a few partial tiles; 40000: several full 256-target tiles per class
+    w = workloads.config2(n)
+    phi_c, E_c, _ = _eval(w, 10, 1, 0)
+    phi_t, E_t, st = _eval(w, 10, 1, 1)
+    phi_64, E_64, _ = _eval(w, 10, 0, 0)
+    assert st["timeouts"] == 0
+    e_tc = oracle.err2(phi_64, phi_t)
+    e_cc = oracle.err2(phi_64, phi_c)
+    print("n=%d: Err2(phi) vs FP64: tensor cores %.2e, CUDA cores %.2e; field %.2e %.2e"
+          % (n, e_tc, e_cc, oracle.err2(E_64, E_t), oracle.err2(E_64, E_c)))
+    # the tensor-core accumulation keeps the float32 form's error (measured ~2e-6)
+    assert e_tc < 5e-6
+    assert oracle.err2(E_64, E_t) < 2e-6
+    assert oracle.err2(phi_c, phi_t) < 5e-6
+
+
+def test_tensor_core_m2l_against_oracle():
+    w = workloads.config2(20000)
+    phi, E, st = _eval(w, 10, 1, 1)
+    t = workloads.subsample(w.n, 300)
+    ref, refE = oracle.direct(w.d, w.eps, w.xyz, w.layer, w.q, targets=t, mode=oracle.MODE_IMAGES)
+    e = oracle.err2(ref, phi[t])
+    print("config2 20k FP32 tensor-core M2L: Err2 phi %.2e field %.2e" % (e, oracle.err2(refE, E[t])))
+    assert e < 1e-5
+    assert oracle.err2(refE, E[t]) < 5e-5
+
+
+def test_high_order_falls_back_to_cuda_cores():
+    # (p+1)^2 > 128: the tensor-core kernel does not apply; results must still be right
+    w = workloads.config2(5000)
+    phi_t, _, _ = _eval(w, 12, 1, 1)
+    phi_64, _, _ = _eval(w, 12, 0, 0)
+    assert oracle.err2(phi_64, phi_t) < 1e-5
