@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 leg")
     ap.add_argument("--sample", type=int, default=256, help="oracle targets for the accuracy / CPU leg")
     ap.add_argument("--no-near", action="store_true", help="skip the near-interface workload")
+    ap.add_argument("--forms", default="fp32_surrogate,fp32,fp64",
+                    help="comma list of fp32_surrogate, fp32, fp64; the first is the headline")
     return ap.parse_args()
 
 
@@ -271,10 +273,15 @@ def main():
     q_d = torch.from_numpy(w.q).to(dev)
     phi_d = torch.empty(w.n, dtype=torch.float64, device=dev)
     fld_d = torch.empty((w.n, 3), dtype=torch.float64, device=dev)
-    flush = torch.empty(256 << 20 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
+    flush = torch.empty((256 << 20) // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
 
     results = {}
-    forms = [("fp32_surrogate", 1, True), ("fp32", 1, False)] + ([] if args.no_fp64 else [("fp64", 0, False)])
+    known = {"fp32_surrogate": (1, True), "fp32": (1, False), "fp64": (0, False)}
+    forms = [(nm, ) + known[nm] for nm in args.forms.split(",") if nm in known]
+    if args.no_fp64:
+        forms = [fm for fm in forms if fm[0] != "fp64"]
+    if not forms:
+        raise SystemExit("no known form in --forms")
     clocks = Clocks(local)
     headline = forms[0][0]
     for name, prec, surr in forms:

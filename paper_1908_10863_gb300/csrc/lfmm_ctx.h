@@ -92,6 +92,7 @@ struct lfmm_ctx {
     DevBuf box_cbeg;    // int32 (first child id, -1 for leaves)
     DevBuf box_cend;    // int32
     DevBuf box_center;  // LfD4 (x, y, z, layer)
+    DevBuf box_grid;    // int4 (ix, iy, iz, layer): grid cell of the box at its level
     DevBuf flags, idx;  // temporaries
 
     // lists: offsets per level box (near_off[level_box] relative to level base) and entries

@@ -380,7 +380,7 @@ __global__ void k_level_ends(int off, int nb, int64_t n, int child_end, const in
 }
 
 __global__ void k_centers(const uint32_t* __restrict__ bkey, int off, int nb, int level, double h, double ox,
-                          double oy, double oz, LfD4* __restrict__ cen)
+                          double oy, double oz, LfD4* __restrict__ cen, int4* __restrict__ grid)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nb) return;
@@ -389,39 +389,51 @@ __global__ void k_centers(const uint32_t* __restrict__ bkey, int off, int nb, in
     uint32_t mort = (level > 0) ? (k & ((1u << (3 * level)) - 1u)) : 0u;
     uint32_t ix = lf_compact3(mort), iy = lf_compact3(mort >> 1), iz = lf_compact3(mort >> 2);
     cen[off + i] = LfD4{ox + (ix + 0.5) * h, oy + (iy + 0.5) * h, oz + (iz + 0.5) * h, (double)layer};
+    grid[off + i] = make_int4((int)ix, (int)iy, (int)iz, (int)layer);
 }
 
 // ---------------------------------------------------------------------------
 // Lists.
 // ---------------------------------------------------------------------------
 __constant__ LfmmComp c_tree_comp[LFMM_MAXCOMP];
+// per (component, level), in units of the level's box size h, with the box
+// centre of grid cell i at origin + (i + 1/2) h:
+//   K = (o + (s - 1) oz) / h    so that (z_t - z'') / h = (iz_t + 1/2) - s (iz_s + 1/2) - K,
+//   F = (iface - oz) / h        so that (z_t - iface) / h = (iz_t + 1/2) - F,
+//   G = (s oz + o - iface) / h  so that (z'' - iface) / h = s (iz_s + 1/2) + G,
+//   Z = zeta_r / h
+__constant__ float4 c_tree_lc[LFMM_MAXCOMP * 16];
 
-__device__ __forceinline__ bool lf_admissible(const LfmmComp& c, LfD4 ct, LfD4 cs, double h)
+// Far-field admissibility of a (target box, source box) pair of one level, in
+// grid units.  Free space: not neighbours (|di|_inf >= 2).  Reaction: the
+// polarization image of the source box at least 2h away (|.|_inf), target
+// and image on their own sides of the interface, and rho <= |dz| + zeta_r.
+// At levels where interfaces are grid planes the tested quantities are
+// integers or half-integers, so single precision decides them exactly; the
+// small margin on the 2h test only matters on coarser levels.
+__device__ __forceinline__ bool lf_admissible(const LfmmComp& c, float4 k, int4 gt, int4 gs)
 {
-    if (c.is_free) {
-        double D = fmax(fabs(ct.x - cs.x), fmax(fabs(ct.y - cs.y), fabs(ct.z - cs.z)));
-        return D > 1.5 * h;
-    }
-    double psz = c.s * cs.z + c.o;
-    double dx = ct.x - cs.x, dy = ct.y - cs.y, dz = ct.z - psz;
-    double D = fmax(fabs(dx), fmax(fabs(dy), fabs(dz)));
-    if (D < 2.0 * h * (1.0 - 1e-9)) return false;
+    const int ix = abs(gt.x - gs.x), iy = abs(gt.y - gs.y);
+    if (c.is_free) return max(ix, max(iy, abs(gt.z - gs.z))) >= 2;
+    const float s = (float)c.s;
+    const float zt = (float)gt.z + 0.5f, zs = s * ((float)gs.z + 0.5f);
+    const float uz = zt - zs - k.x;
+    const float ux = (float)ix, uy = (float)iy;
+    if (fmaxf(ux, fmaxf(uy, fabsf(uz))) < 2.0f - 1e-3f) return false;
+    const float tside = zt - k.y, pside = zs + k.z;
     if (c.a == 1) {
-        if (!(ct.z > c.iface && psz < c.iface)) return false;
+        if (!(tside > 0.f && pside < 0.f)) return false;
     } else {
-        if (!(ct.z < c.iface && psz > c.iface)) return false;
+        if (!(tside < 0.f && pside > 0.f)) return false;
     }
-    if (c.has_rem) {
-        // keep the remainder integral on the real axis (rho <= z + zeta_r)
-        double rho = sqrt(dx * dx + dy * dy);
-        if (rho > fabs(dz) + c.zeta_r) return false;
-    }
+    // keep the remainder integral on the real axis (rho <= z + zeta_r)
+    if (c.has_rem && sqrtf(ux * ux + uy * uy) > fabsf(uz) + k.w) return false;
     return true;
 }
 
-__global__ void k_list_pass(int level_off, int nb, double h, const int* __restrict__ parent,
+__global__ void k_list_pass(int level_off, int nb, int level, const int* __restrict__ parent,
                             const int* __restrict__ cbeg, const int* __restrict__ cend,
-                            const LfD4* __restrict__ cen, const int* __restrict__ pnear_beg,
+                            const int4* __restrict__ grid, const int* __restrict__ pnear_beg,
                             const int* __restrict__ pnear_end, const uint32_t* __restrict__ near_ent_in,
                             int* __restrict__ cnt, const int* __restrict__ off, uint32_t* __restrict__ m2l_out,
                             uint32_t* __restrict__ m2r_out, uint32_t* __restrict__ near_out, int fill,
@@ -432,7 +444,7 @@ __global__ void k_list_pass(int level_off, int nb, double h, const int* __restri
     if (i >= nb) return;
     int t = level_off + i;
     int pt = parent[t];
-    LfD4 ct = cen[t];
+    const int4 gt = grid[t];
     int nf = 0, nr = 0, nn = 0;
     int wf = fill ? off[i] : 0, wr = fill ? off[nb + i] : 0, wn = fill ? off[2 * nb + i] : 0;
     for (int e = pnear_beg[pt]; e < pnear_end[pt]; ++e) {
@@ -440,10 +452,10 @@ __global__ void k_list_pass(int level_off, int nb, double h, const int* __restri
         int c = (int)(ent >> LFMM_ENT_SHIFT);
         int s = (int)(ent & LFMM_ENT_MASK);
         const LfmmComp& cp = c_tree_comp[c];
+        const float4 k = c_tree_lc[c * 16 + level];
         for (int sc = cbeg[s]; sc < cend[s]; ++sc) {
-            LfD4 cs = cen[sc];
             uint32_t v = ((uint32_t)c << LFMM_ENT_SHIFT) | (uint32_t)sc;
-            if (lf_admissible(cp, ct, cs, h)) {
+            if (lf_admissible(cp, k, gt, grid[sc])) {
                 if (cp.is_free) {
                     if (fill) m2l_out[wf++] = v;
                     ++nf;
@@ -677,6 +689,7 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
     LF_TRY(lf_reserve(ctx->box_cbeg, nb * 4));
     LF_TRY(lf_reserve(ctx->box_cend, nb * 4));
     LF_TRY(lf_reserve(ctx->box_center, nb * sizeof(LfD4)));
+    LF_TRY(lf_reserve(ctx->box_grid, nb * sizeof(int4)));
     LF_TRY(lf_reserve(ctx->flags, (size_t)n * 4));
     LF_TRY(lf_reserve(ctx->scan_tmp, 64));
     DevBuf& idxb = ctx->keys_tmp;  // reuse as scan output
@@ -722,9 +735,24 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
         const LfmmLevel& lv = ctx->levels[l];
         ++ctx->launches, k_centers<<<lf_blocks(lv.nbox, 256), 256, 0, st>>>(bkey, lv.off, lv.nbox, l, lv.h, ctx->origin[0],
                                                             ctx->origin[1], ctx->origin[2],
-                                                            ctx->box_center.as<LfD4>());
+                                                            ctx->box_center.as<LfD4>(), ctx->box_grid.as<int4>());
     }
     LF_TRY(lf_cuda(cudaGetLastError(), "centers"));
+    {
+        // per (component, level) constants of the admissibility test
+        std::vector<float4> lc((size_t)LFMM_MAXCOMP * 16, make_float4(0.f, 0.f, 0.f, 0.f));
+        const double oz = ctx->origin[2];
+        for (int c = 0; c < ctx->ncomp; ++c)
+            for (int l = 0; l <= depth && l < 16; ++l) {
+                const LfmmComp& cp = ctx->comp[c];
+                const double h = ctx->levels[l].h;
+                lc[(size_t)c * 16 + l] = make_float4((float)((cp.o + (cp.s - 1.0) * oz) / h), (float)((cp.iface - oz) / h),
+                                                     (float)((cp.s * oz + cp.o - cp.iface) / h), (float)(cp.zeta_r / h));
+            }
+        LF_CHECK(cudaMemcpyToSymbolAsync(c_tree_lc, lc.data(), sizeof(float4) * lc.size(), 0, cudaMemcpyHostToDevice,
+                                         st));
+        LF_CHECK(cudaStreamSynchronize(st));
+    }
 
     // ---- lists ----
     LF_CHECK(cudaMemcpyToSymbolAsync(c_tree_comp, ctx->comp, sizeof(LfmmComp) * ctx->ncomp, 0,
@@ -786,7 +814,7 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
     for (int l = 1; l <= depth; ++l) {
         LfmmLevel& lv = ctx->levels[l];
         const int n3 = lv.nbox;
-        ++ctx->launches, k_list_pass<<<lf_blocks(n3, 128), 128, 0, st>>>(lv.off, n3, lv.h, par, cbeg, cend, ctx->box_center.as<LfD4>(),
+        ++ctx->launches, k_list_pass<<<lf_blocks(n3, 128), 128, 0, st>>>(lv.off, n3, l, par, cbeg, cend, ctx->box_grid.as<int4>(),
                                                         nbeg, nend, ctx->near_ent.as<uint32_t>(), cnt3, nullptr,
                                                         nullptr, nullptr, nullptr, 0, nullptr);
         LF_TRY(lf_cuda(cudaGetLastError(), "list count"));
@@ -802,7 +830,7 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
         uint32_t* nent = ctx->near_ent.as<uint32_t>();
         // per-level offsets are relative: shift the output pointers
         ++ctx->launches, k_list_pass<<<lf_blocks(n3, 128), 128, 0, st>>>(
-            lv.off, n3, lv.h, par, cbeg, cend, ctx->box_center.as<LfD4>(), nbeg, nend, nent, cnt3, off3,
+            lv.off, n3, l, par, cbeg, cend, ctx->box_grid.as<int4>(), nbeg, nend, nent, cnt3, off3,
             ctx->m2l_ent.as<uint32_t>() + m2l_used, ctx->m2r_ent.as<uint32_t>() + m2r_used, nent + near_used, 1,
             stat);
         ++ctx->launches, k_set_ranges<<<lf_blocks(n3, 256), 256, 0, st>>>(lv.off, n3, off3, cnt3, (int)m2l_used, mbeg, mend);
