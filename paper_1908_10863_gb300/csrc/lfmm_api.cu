@@ -509,8 +509,14 @@ lfmm_status lfmm_create(const double* d, int L, const double* eps, int p, lfmm_c
     LfErr e = setup_components(ctx);
     if (e.empty()) e = lf_cuda(cudaGetDevice(&ctx->device), "cudaGetDevice");
     if (e.empty()) e = lf_cuda(cudaFree(0), "context init");
-    if (e.empty()) e = lf_cuda(cudaStreamCreateWithFlags(&ctx->s_main, cudaStreamNonBlocking), "stream");
-    if (e.empty()) e = lf_cuda(cudaStreamCreateWithFlags(&ctx->s_near, cudaStreamNonBlocking), "stream");
+    // the far field (a chain of dependent per-level launches) is the critical
+    // path; the near field runs beside it at lower priority and fills the gaps
+    int prio_lo = 0, prio_hi = 0;
+    if (e.empty()) e = lf_cuda(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi), "stream priorities");
+    if (e.empty())
+        e = lf_cuda(cudaStreamCreateWithPriority(&ctx->s_main, cudaStreamNonBlocking, prio_hi), "stream");
+    if (e.empty())
+        e = lf_cuda(cudaStreamCreateWithPriority(&ctx->s_near, cudaStreamNonBlocking, prio_lo), "stream");
     if (e.empty()) e = lf_cuda(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming), "event");
     if (e.empty()) e = lf_cuda(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming), "event");
     if (e.empty()) e = setup_rules(ctx);
@@ -573,6 +579,7 @@ static lfmm_status build_common(lfmm_ctx* ctx, int64_t n, const double* xyz_dev,
     prof_reset(ctx);
     int ph = lf_prof_start(ctx, LFMM_TIME_BUILD, ctx->s_main);
     LfErr e = lf_build_tree(ctx, xyz_dev, layer_dev, n, ctx->s_main);
+    if (e.empty()) e = lf_near_prepare(ctx, ctx->s_main);
     lf_prof_stop(ctx, ph, ctx->s_main);
     if (!e.empty()) {
         cudaStreamSynchronize(ctx->s_main);
@@ -709,7 +716,7 @@ void lfmm_destroy(lfmm_ctx* ctx)
                       &ctx->oct_U64, &ctx->oct_U32, &ctx->comp_dev, &ctx->perm, &ctx->xs, &ctx->ys, &ctx->zs,
                       &ctx->keys, &ctx->keys_tmp, &ctx->vals_tmp, &ctx->scan_tmp, &ctx->hist, &ctx->xyz_in,
                       &ctx->layer_in, &ctx->err_flag, &ctx->counts, &ctx->box_key, &ctx->box_pbeg, &ctx->box_pend,
-                      &ctx->box_parent, &ctx->box_cbeg, &ctx->box_cend, &ctx->box_center, &ctx->box_grid, &ctx->flags, &ctx->idx,
+                      &ctx->box_parent, &ctx->box_cbeg, &ctx->box_cend, &ctx->box_center, &ctx->box_grid, &ctx->pos_rel, &ctx->flags, &ctx->idx,
                       &ctx->near_off, &ctx->near_ent, &ctx->m2l_off, &ctx->m2l_ent, &ctx->m2r_off, &ctx->m2r_ent,
                       &ctx->q_sorted, &ctx->Mexp, &ctx->Lexp, &ctx->phi_far, &ctx->phi_near, &ctx->fld_far,
                       &ctx->fld_near, &ctx->q_stage, &ctx->phi_stage, &ctx->fld_stage, &ctx->m2l_A64, &ctx->m2l_A32,
@@ -718,7 +725,8 @@ void lfmm_destroy(lfmm_ctx* ctx)
                       &ctx->m2r_tgt, &ctx->m2r_kstart, &ctx->m2r_kval, &ctx->m2r_tables, &ctx->m2r_levelh,
                       &ctx->m2r_batches, &ctx->surr_theta, &ctx->surr_grad, &ctx->surr_m1,
                       &ctx->surr_m2, &ctx->surr_w, &ctx->surr_b, &ctx->surr_meta, &ctx->surr_err, &ctx->surr_comps,
-                      &ctx->surr_xoff, &ctx->surr_counters, &ctx->m2l_Atc, &ctx->m2l_tc_tiles, &ctx->m2l_Ms};
+                      &ctx->surr_xoff, &ctx->surr_counters, &ctx->m2l_Atc, &ctx->m2l_tc_tiles, &ctx->m2l_Ms, &ctx->m2m_A64, &ctx->m2m_A32,
+                      &ctx->l2l_A64, &ctx->l2l_A32, &ctx->shift_cls, &ctx->m2m_slots, &ctx->shift_tiles};
     for (DevBuf* b : bufs) lf_free(*b);
     for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);

@@ -93,6 +93,7 @@ struct lfmm_ctx {
     DevBuf box_cend;    // int32
     DevBuf box_center;  // LfD4 (x, y, z, layer)
     DevBuf box_grid;    // int4 (ix, iy, iz, layer): grid cell of the box at its level
+    DevBuf pos_rel;     // float4 per sorted charge: offset from its leaf centre
     DevBuf flags, idx;  // temporaries
 
     // lists: offsets per level box (near_off[level_box] relative to level base) and entries
@@ -104,6 +105,10 @@ struct lfmm_ctx {
     int m2l_rm = 0, m2l_rp = 0, m2l_ntiles = 0;
     // tensor-core free M2L (float32 form, (p+1)^2 <= 128)
     DevBuf m2l_Atc, m2l_tc_tiles, m2l_Ms;
+    // M2M / L2L as gathered GEMMs (the same kernel as the free M2L)
+    DevBuf m2m_A64, m2m_A32, l2l_A64, l2l_A32, shift_cls, m2m_slots, shift_tiles;
+    std::vector<int> m2m_first, l2l_first;  // first tile of each level
+    int l2l_tile_base = 0, shift_ready = 0;
     int m2l_tc_ok = 0, m2l_tc_ntiles = 0, use_tc = 1, tc_groups = 27;
     // reaction M2L grouped by geometry key on interface-aligned levels
     DevBuf m2r_keys, m2r_order, m2r_tgt, m2r_kstart, m2r_kval, m2r_tables, m2r_levelh, m2r_batches;
@@ -161,6 +166,7 @@ LfErr lf_radix_sort(lfmm_ctx* ctx, uint32_t* keys, uint32_t* vals, int64_t n, cu
 // ---- evaluation (lfmm_fmm.cu, lfmm_near.cu) ----
 LfErr lf_evaluate_sorted(lfmm_ctx* ctx, const double* q_dev, double* phi_dev, double* field_dev, cudaStream_t st);
 LfErr lf_near_field(lfmm_ctx* ctx, cudaStream_t st);
+LfErr lf_near_prepare(lfmm_ctx* ctx, cudaStream_t st);
 
 // ---- surrogate (lfmm_surrogate.cu) ----
 LfErr lf_surrogate_train(lfmm_ctx* ctx, int64_t nsamples, int epochs, uint64_t seed);
@@ -169,6 +175,8 @@ LfErr lf_surrogate_eval_dev(lfmm_ctx* ctx, int comp, int n, const double* rho, c
 LfErr lf_surrogate_grad_dev(lfmm_ctx* ctx, int comp, int n, const float* x, const float* ystd, double* loss,
                             float* grad);
 LfErr lf_surrogate_device_view(lfmm_ctx* ctx, LfmmSurrView* v);
+
+LfErr lf_shift_gemm(lfmm_ctx* ctx, int level, bool l2l, cudaStream_t st);
 
 // ---- tensor-core free M2L (lfmm_m2l_tc.cu) ----
 // byte offset in ctx->counts of the int counting device waits that ran out

@@ -512,7 +512,10 @@ static LfErr far_field(lfmm_ctx* ctx, cudaStream_t st)
             const LfmmLevel& lv = ctx->levels[l];
             if (lv.nbox == 0) continue;
             ph = lf_prof_start(ctx, LFMM_TIME_M2M, st);
-            ++ctx->launches, k_m2m<R><<<lv.nbox, th, sm, st>>>(lv.off, p, cen, cbeg, cend, octU, M);
+            if (ctx->shift_ready)
+                LF_TRY(lf_shift_gemm(ctx, l, false, st));
+            else
+                ++ctx->launches, k_m2m<R><<<lv.nbox, th, sm, st>>>(lv.off, p, cen, cbeg, cend, octU, M);
             lf_prof_stop(ctx, ph, st);
         }
         LF_TRY(lf_cuda(cudaGetLastError(), "m2m"));
@@ -576,7 +579,10 @@ static LfErr far_field(lfmm_ctx* ctx, cudaStream_t st)
         const LfmmLevel& lv = ctx->levels[l];
         if (lv.nbox == 0) continue;
         ph = lf_prof_start(ctx, LFMM_TIME_L2L, st);
-        ++ctx->launches, k_l2l<R><<<lv.nbox, lth, lsm, st>>>(lv.off, p, cen, par, octU, L);
+        if (ctx->shift_ready)
+            LF_TRY(lf_shift_gemm(ctx, l, true, st));
+        else
+            ++ctx->launches, k_l2l<R><<<lv.nbox, lth, lsm, st>>>(lv.off, p, cen, par, octU, L);
         lf_prof_stop(ctx, ph, st);
         LF_TRY(lf_cuda(cudaGetLastError(), "l2l"));
     }

@@ -13,6 +13,13 @@
 // its tile in registers and, for each of the 189 offsets, gathers the 64
 // source multipoles (zero where a target has no source at that offset) and
 // multiplies them by A_o: 189 register-tiled GEMMs of (p+1)^2 x (p+1)^2 x 64.
+//
+// The same gathered GEMM runs the translations between levels: M2M (eq.
+// metome) with the 8 child-octant maps (each parent gathers its children,
+// one "offset" per octant) and L2L (eq. letole) with one map per child
+// octant (children grouped by octant gather their parent).  Their matrices
+// are the packed real forms of the complex shift formulas, built on the host
+// by applying those formulas to unit coefficient vectors.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -56,6 +63,93 @@ static int gemm_rm(int p)
 // ---------------------------------------------------------------------------
 // Host: operators and offset classes.
 // ---------------------------------------------------------------------------
+// complex coefficient (n, m) of a packed real vector; negative m by
+// X_n^{-m} = (-1)^m conj(X_n^m)
+static void h_get(const double* v, int p, int n, int m, double& re, double& im)
+{
+    const int a = m < 0 ? -m : m;
+    re = v[lf_re(n, a)];
+    im = a > 0 ? v[lf_im(p, n, a)] : 0.0;
+    if (m < 0) {
+        const double s = (a & 1) ? -1.0 : 1.0;
+        re *= s;
+        im *= -s;
+    }
+}
+static void h_getU(const double* ur, const double* ui, int n, int m, double& re, double& im)
+{
+    const int a = m < 0 ? -m : m;
+    re = ur[lf_re(n, a)];
+    im = ui[lf_re(n, a)];
+    if (m < 0) {
+        const double s = (a & 1) ? -1.0 : 1.0;
+        re *= s;
+        im *= -s;
+    }
+}
+// M2M: M_p(n, m) = sum_{k <= n, l} 2^{-k} M_c(k, l) conj(U_{n-k}^{m-l}(d))
+static void h_m2m(int p, const double* ur, const double* ui, const double* in, double* out)
+{
+    for (int n = 0; n <= p; ++n)
+        for (int m = 0; m <= n; ++m) {
+            double ar = 0, ai = 0, sc = 1;
+            for (int k = 0; k <= n; ++k, sc *= 0.5)
+                for (int l = -k; l <= k; ++l) {
+                    const int dm = m - l;
+                    if (dm > n - k || dm < -(n - k)) continue;
+                    double mr, mi, vr, vi;
+                    h_get(in, p, k, l, mr, mi);
+                    h_getU(ur, ui, n - k, dm, vr, vi);
+                    ar += sc * (mr * vr + mi * vi);
+                    ai += sc * (mi * vr - mr * vi);
+                }
+            out[lf_re(n, m)] = ar;
+            if (m > 0) out[lf_im(p, n, m)] = ai;
+        }
+}
+// L2L: L_c(j, i) = 2^{-j} sum_{k >= j, l} L_p(k, l) conj(U_{k-j}^{l-i}(d))
+static void h_l2l(int p, const double* ur, const double* ui, const double* in, double* out)
+{
+    for (int j = 0; j <= p; ++j)
+        for (int i = 0; i <= j; ++i) {
+            double ar = 0, ai = 0;
+            for (int k = j; k <= p; ++k)
+                for (int l = -k; l <= k; ++l) {
+                    const int dm = l - i;
+                    if (dm > k - j || dm < -(k - j)) continue;
+                    double lr, li, vr, vi;
+                    h_get(in, p, k, l, lr, li);
+                    h_getU(ur, ui, k - j, dm, vr, vi);
+                    ar += lr * vr + li * vi;
+                    ai += li * vr - lr * vi;
+                }
+            const double sc = std::ldexp(1.0, -j);
+            out[lf_re(j, i)] = sc * ar;
+            if (i > 0) out[lf_im(p, j, i)] = sc * ai;
+        }
+}
+
+// the 8 octant matrices [k_in][r_out] of M2M (which = 0) or L2L (which = 1)
+static void shift_ops(int p, int KP, int RP, int which, std::vector<double>& A)
+{
+    const int nc = lf_nc(p), nre = lf_nre(p);
+    A.assign((size_t)8 * KP * RP, 0.0);
+    std::vector<double> ur(nre), ui(nre), in(nc), out(nc);
+    for (int o = 0; o < 8; ++o) {
+        const double x = (o & 1) ? 0.25 : -0.25, y = (o & 2) ? 0.25 : -0.25, z = (o & 4) ? 0.25 : -0.25;
+        lf_regular<double>(p, x, y, z, ur.data(), ui.data());
+        for (int k = 0; k < nc; ++k) {
+            std::fill(in.begin(), in.end(), 0.0);
+            in[k] = 1.0;
+            if (which == 0)
+                h_m2m(p, ur.data(), ui.data(), in.data(), out.data());
+            else
+                h_l2l(p, ur.data(), ui.data(), in.data(), out.data());
+            for (int r = 0; r < nc; ++r) A[((size_t)o * KP + k) * RP + r] = out[r];
+        }
+    }
+}
+
 LfErr lf_setup_m2l_ops(lfmm_ctx* ctx)
 {
     const int p = ctx->p;
@@ -134,6 +228,22 @@ LfErr lf_setup_m2l_ops(lfmm_ctx* ctx)
     LF_TRY(lf_reserve(ctx->m2l_inv, sizeof(int) * inv.size()));
     LF_CHECK(cudaMemcpy(ctx->m2l_cls.ptr, cls.data(), sizeof(int) * cls.size(), cudaMemcpyHostToDevice));
     LF_CHECK(cudaMemcpy(ctx->m2l_inv.ptr, inv.data(), sizeof(int) * inv.size(), cudaMemcpyHostToDevice));
+    // M2M / L2L octant matrices: [which][o][k_in][r_out], and their class tables
+    for (int which = 0; which < 2; ++which) {
+        std::vector<double> S;
+        shift_ops(p, KP, RP, which, S);
+        std::vector<float> Sf(S.size());
+        for (size_t i = 0; i < S.size(); ++i) Sf[i] = (float)S[i];
+        DevBuf& b64 = which ? ctx->l2l_A64 : ctx->m2m_A64;
+        DevBuf& b32 = which ? ctx->l2l_A32 : ctx->m2m_A32;
+        LF_TRY(lf_reserve(b64, S.size() * 8));
+        LF_TRY(lf_reserve(b32, Sf.size() * 4));
+        LF_CHECK(cudaMemcpy(b64.ptr, S.data(), S.size() * 8, cudaMemcpyHostToDevice));
+        LF_CHECK(cudaMemcpy(b32.ptr, Sf.data(), Sf.size() * 4, cudaMemcpyHostToDevice));
+    }
+    const int shift_cls[8] = {0, 1, 2, 3, 4, 5, 6, 7};  // M2M: one class of 8 offsets; L2L: 8 classes of 1
+    LF_TRY(lf_reserve(ctx->shift_cls, sizeof(shift_cls)));
+    LF_CHECK(cudaMemcpy(ctx->shift_cls.ptr, shift_cls, sizeof(shift_cls), cudaMemcpyHostToDevice));
     return LfErr();
 }
 
@@ -166,6 +276,15 @@ __global__ void k_fill_slots(int off, int nb, double h, const uint32_t* __restri
     }
 }
 
+__global__ void k_child_slots(int off, int nb, const uint32_t* __restrict__ bkey, const int* __restrict__ parent,
+                              int* __restrict__ slots)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb) return;
+    const int b = off + i, pb = parent[b];
+    if (pb >= 0) slots[(size_t)pb * 8 + (bkey[b] & 7u)] = b;
+}
+
 __global__ void k_class_keys(int off, int nb, int level, const uint32_t* __restrict__ bkey,
                              uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, int base,
                              int* __restrict__ counts)
@@ -181,6 +300,7 @@ __global__ void k_class_keys(int off, int nb, int level, const uint32_t* __restr
 LfErr lf_prepare_m2l(lfmm_ctx* ctx, cudaStream_t st)
 {
     ctx->m2l_ntiles = 0;
+    ctx->shift_ready = 0;
     if (ctx->m2l_rm == 0) return LfErr();
     const int depth = ctx->depth;
     if (depth < 2) return LfErr();
@@ -191,21 +311,31 @@ LfErr lf_prepare_m2l(lfmm_ctx* ctx, cudaStream_t st)
     int* cnt = err + 16;  // [16 levels][8]
     LF_CHECK(cudaMemsetAsync(err, 0, sizeof(int) * (16 + 16 * 8), st));
     int nsort = 0;
-    for (int l = 2; l <= depth; ++l) nsort += ctx->levels[l].nbox;
+    for (int l = 1; l <= depth; ++l) nsort += ctx->levels[l].nbox;
     LF_TRY(lf_reserve(ctx->m2l_keys, (size_t)nsort * 4 + 16));
     LF_TRY(lf_reserve(ctx->m2l_sorted, (size_t)nsort * 4 + 16));
     int base = 0;
-    for (int l = 2; l <= depth; ++l) {
+    for (int l = 1; l <= depth; ++l) {
         const LfmmLevel& lv = ctx->levels[l];
         if (lv.nbox == 0) continue;
-        ++ctx->launches, k_fill_slots<<<lf_blocks(lv.nbox, 128), 128, 0, st>>>(
-            lv.off, lv.nbox, lv.h, ctx->box_key.as<uint32_t>(), ctx->box_center.as<LfD4>(), ctx->m2l_off.as<int>(),
-            ctx->m2l_off.as<int>() + ctx->nbox_total, ctx->m2l_ent.as<uint32_t>(), ctx->m2l_inv.as<int>(),
-            ctx->m2l_slots.as<int>(), err);
+        if (l >= 2)
+            ++ctx->launches, k_fill_slots<<<lf_blocks(lv.nbox, 128), 128, 0, st>>>(
+                lv.off, lv.nbox, lv.h, ctx->box_key.as<uint32_t>(), ctx->box_center.as<LfD4>(), ctx->m2l_off.as<int>(),
+                ctx->m2l_off.as<int>() + ctx->nbox_total, ctx->m2l_ent.as<uint32_t>(), ctx->m2l_inv.as<int>(),
+                ctx->m2l_slots.as<int>(), err);
         ++ctx->launches, k_class_keys<<<lf_blocks(lv.nbox, 256), 256, 0, st>>>(
             lv.off, lv.nbox, l, ctx->box_key.as<uint32_t>(), ctx->m2l_keys.as<uint32_t>(),
             ctx->m2l_sorted.as<uint32_t>(), base, cnt);
         base += lv.nbox;
+    }
+    // M2M slots: children of each parent by octant
+    LF_TRY(lf_reserve(ctx->m2m_slots, nb * 8 * sizeof(int)));
+    LF_CHECK(cudaMemsetAsync(ctx->m2m_slots.ptr, 0xff, nb * 8 * sizeof(int), st));
+    for (int l = 1; l <= depth; ++l) {
+        const LfmmLevel& lv = ctx->levels[l];
+        if (lv.nbox == 0) continue;
+        ++ctx->launches, k_child_slots<<<lf_blocks(lv.nbox, 256), 256, 0, st>>>(
+            lv.off, lv.nbox, ctx->box_key.as<uint32_t>(), ctx->box_parent.as<int>(), ctx->m2m_slots.as<int>());
     }
     LF_TRY(lf_cuda(cudaGetLastError(), "m2l slots"));
     LF_TRY(lf_radix_sort(ctx, ctx->m2l_keys.as<uint32_t>(), ctx->m2l_sorted.as<uint32_t>(), nsort, st));
@@ -213,14 +343,39 @@ LfErr lf_prepare_m2l(lfmm_ctx* ctx, cudaStream_t st)
     LF_CHECK(cudaMemcpyAsync(hcnt, err, sizeof(hcnt), cudaMemcpyDeviceToHost, st));
     LF_CHECK(cudaStreamSynchronize(st));
     if (hcnt[0] != 0) return "internal: free M2L entry outside its offset class";
-    std::vector<int4> tiles;
+    std::vector<int4> tiles, l2l_tiles;
+    std::vector<int> l2l_first(depth + 2, 0);
     int start = 0;
-    for (int l = 2; l <= depth; ++l)
+    for (int l = 1; l <= depth; ++l) {
+        l2l_first[l] = (int)l2l_tiles.size();
         for (int c = 0; c < 8; ++c) {
             int n = hcnt[16 + l * 8 + c];
-            for (int s = 0; s < n; s += G_TB) tiles.push_back(make_int4(l, c, start + s, std::min(G_TB, n - s)));
+            for (int s = 0; s < n; s += G_TB) {
+                if (l >= 2) tiles.push_back(make_int4(l, c, start + s, std::min(G_TB, n - s)));
+                l2l_tiles.push_back(make_int4(l, c, start + s, std::min(G_TB, n - s)));
+            }
             start += n;
         }
+    }
+    l2l_first[depth + 1] = (int)l2l_tiles.size();
+    // M2M tiles: parents of levels 0 .. depth-1 in box order
+    std::vector<int4> m2m_tiles;
+    ctx->m2m_first.assign(depth + 1, 0);
+    for (int l = 0; l < depth; ++l) {
+        ctx->m2m_first[l] = (int)m2m_tiles.size();
+        const LfmmLevel& lv = ctx->levels[l];
+        for (int s = 0; s < lv.nbox; s += G_TB) m2m_tiles.push_back(make_int4(l, 0, lv.off + s, std::min(G_TB, lv.nbox - s)));
+    }
+    ctx->m2m_first[depth] = (int)m2m_tiles.size();
+    ctx->l2l_first = l2l_first;
+    LF_TRY(lf_reserve(ctx->shift_tiles, (m2m_tiles.size() + l2l_tiles.size()) * sizeof(int4) + 16));
+    ctx->l2l_tile_base = (int)m2m_tiles.size();
+    if (!m2m_tiles.empty())
+        LF_CHECK(cudaMemcpyAsync(ctx->shift_tiles.ptr, m2m_tiles.data(), m2m_tiles.size() * sizeof(int4),
+                                 cudaMemcpyHostToDevice, st));
+    if (!l2l_tiles.empty())
+        LF_CHECK(cudaMemcpyAsync(ctx->shift_tiles.as<int4>() + m2m_tiles.size(), l2l_tiles.data(),
+                                 l2l_tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
     ctx->m2l_ntiles = (int)tiles.size();
     if (!tiles.empty()) {
         LF_TRY(lf_reserve(ctx->m2l_tiles, tiles.size() * sizeof(int4)));
@@ -233,10 +388,11 @@ LfErr lf_prepare_m2l(lfmm_ctx* ctx, cudaStream_t st)
     if (ctx->m2l_tc_ok) {
         const int TN = lf_m2l_tc_tile();
         int st0 = 0;
-        for (int l = 2; l <= depth; ++l)
+        for (int l = 1; l <= depth; ++l)
             for (int c = 0; c < 8; ++c) {
                 int n = hcnt[16 + l * 8 + c];
-                for (int s = 0; s < n; s += TN) tct.push_back(make_int4(l, c, st0 + s, std::min(TN, n - s)));
+                if (l >= 2)
+                    for (int s = 0; s < n; s += TN) tct.push_back(make_int4(l, c, st0 + s, std::min(TN, n - s)));
                 st0 += n;
             }
         ctx->m2l_tc_ntiles = (int)tct.size();
@@ -251,6 +407,7 @@ LfErr lf_prepare_m2l(lfmm_ctx* ctx, cudaStream_t st)
     LF_TRY(lf_reserve(ctx->m2l_levelh, sizeof(hl)));
     LF_CHECK(cudaMemcpyAsync(ctx->m2l_levelh.ptr, hl, sizeof(hl), cudaMemcpyHostToDevice, st));
     LF_CHECK(cudaStreamSynchronize(st));
+    ctx->shift_ready = 1;
     return LfErr();
 }
 
@@ -261,10 +418,13 @@ LfErr lf_prepare_m2l(lfmm_ctx* ctx, cudaStream_t st)
 // ---------------------------------------------------------------------------
 struct GemmArgs {
     int p, nc, RP;
-    const int4* tiles;
-    const int* sorted;
-    const int* slots;
-    const int* cls;
+    int noff;           // offsets (gathered sources) per target: 189 (M2L), 8 (M2M), 1 (L2L)
+    int mode;           // 0: L += D / h_level (M2L), 1: L = D (M2M), 2: L += D (L2L)
+    int tile_base;      // first tile of this launch
+    const int4* tiles;  // level, class, start, count
+    const int* sorted;  // targets grouped by class, or null: targets start .. start + count - 1
+    const int* slots;   // [target][noff] source box, or -1
+    const int* cls;     // [class][noff] operator index
     const double* levelh;
     const void* A;
     const void* M;
@@ -284,22 +444,23 @@ __global__ void __launch_bounds__(G_T) k_m2l_gemm(GemmArgs g)
     __shared__ int s_src[G_TB];
     const int tid = threadIdx.x;
     const int cg = tid & 15, rg = tid >> 4;
-    const int4 tile = g.tiles[blockIdx.x];
+    const int4 tile = g.tiles[g.tile_base + blockIdx.x];
     const int level = tile.x, cls = tile.y, start = tile.z, cnt = tile.w;
     const int nc = g.nc;
     const R* A = reinterpret_cast<const R*>(g.A);
     const R* M = reinterpret_cast<const R*>(g.M);
     R* L = reinterpret_cast<R*>(g.L);
-    if (tid < G_TB) s_tb[tid] = (tid < cnt) ? g.sorted[start + tid] : -1;
+    if (tid < G_TB) s_tb[tid] = (tid < cnt) ? (g.sorted ? g.sorted[start + tid] : start + tid) : -1;
     R acc[RM][4];
 #pragma unroll
     for (int r = 0; r < RM; ++r)
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[r][c] = 0;
     __syncthreads();
-    for (int oi = 0; oi < G_NOFF; ++oi) {
-        const int o = g.cls[cls * G_NOFF + oi];
-        if (tid < G_TB) s_src[tid] = (tid < cnt) ? g.slots[(size_t)s_tb[tid] * G_NOFF + oi] : -1;
+    const int noff = g.noff;
+    for (int oi = 0; oi < noff; ++oi) {
+        const int o = g.cls[cls * noff + oi];
+        if (tid < G_TB) s_src[tid] = (tid < cnt) ? g.slots[(size_t)s_tb[tid] * noff + oi] : -1;
         __syncthreads();
         // gather the source multipoles: column j = source of target j (k fastest)
         for (int idx = tid; idx < G_TB * KP; idx += G_T) {
@@ -332,7 +493,7 @@ __global__ void __launch_bounds__(G_T) k_m2l_gemm(GemmArgs g)
         }
         __syncthreads();
     }
-    const R ih = (R)(1.0 / g.levelh[level]);
+    const R ih = (g.mode == 0) ? (R)(1.0 / g.levelh[level]) : R(1);
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         int j = 4 * cg + c;
@@ -341,19 +502,38 @@ __global__ void __launch_bounds__(G_T) k_m2l_gemm(GemmArgs g)
 #pragma unroll
         for (int r = 0; r < RM; ++r) {
             int row = rg * RM + r;
-            if (row < nc) Lt[row] += acc[r][c] * ih;
+            if (row < nc) {
+                if (g.mode == 1)
+                    Lt[row] = acc[r][c];
+                else
+                    Lt[row] += acc[r][c] * ih;
+            }
         }
     }
 }
 
 template <typename R, int RM>
-static LfErr launch_gemm(lfmm_ctx* ctx, cudaStream_t st, const GemmArgs& g)
+static LfErr launch_gemm(lfmm_ctx* ctx, cudaStream_t st, const GemmArgs& g, int ntiles)
 {
+    if (ntiles <= 0) return LfErr();
     constexpr int RP = 16 * RM;
     size_t sm = sizeof(R) * ((size_t)G_KC * RP + (size_t)G_TB * (RP + 1));
     LF_CHECK(cudaFuncSetAttribute(k_m2l_gemm<R, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    ++ctx->launches, k_m2l_gemm<R, RM><<<ctx->m2l_ntiles, G_T, sm, st>>>(g);
-    return lf_cuda(cudaGetLastError(), "m2l gemm");
+    ++ctx->launches, k_m2l_gemm<R, RM><<<ntiles, G_T, sm, st>>>(g);
+    return lf_cuda(cudaGetLastError(), "gathered gemm");
+}
+
+template <typename R>
+static LfErr launch_gemm_rm(lfmm_ctx* ctx, cudaStream_t st, const GemmArgs& g, int ntiles)
+{
+    switch (ctx->m2l_rm) {
+    case 2: return launch_gemm<R, 2>(ctx, st, g, ntiles);
+    case 4: return launch_gemm<R, 4>(ctx, st, g, ntiles);
+    case 8: return launch_gemm<R, 8>(ctx, st, g, ntiles);
+    case 12: return launch_gemm<R, 12>(ctx, st, g, ntiles);
+    case 16: return launch_gemm<R, 16>(ctx, st, g, ntiles);
+    default: return "internal: unsupported GEMM tile";
+    }
 }
 
 template <typename R>
@@ -363,6 +543,9 @@ static LfErr m2l_gemm_t(lfmm_ctx* ctx, cudaStream_t st)
     g.p = ctx->p;
     g.nc = lf_nc(ctx->p);
     g.RP = ctx->m2l_rp;
+    g.noff = G_NOFF;
+    g.mode = 0;
+    g.tile_base = 0;
     g.tiles = ctx->m2l_tiles.as<int4>();
     g.sorted = ctx->m2l_sorted.as<int>();
     g.slots = ctx->m2l_slots.as<int>();
@@ -371,14 +554,49 @@ static LfErr m2l_gemm_t(lfmm_ctx* ctx, cudaStream_t st)
     g.A = sizeof(R) == 8 ? ctx->m2l_A64.ptr : ctx->m2l_A32.ptr;
     g.M = ctx->Mexp.ptr;
     g.L = ctx->Lexp.ptr;
-    switch (ctx->m2l_rm) {
-    case 2: return launch_gemm<R, 2>(ctx, st, g);
-    case 4: return launch_gemm<R, 4>(ctx, st, g);
-    case 8: return launch_gemm<R, 8>(ctx, st, g);
-    case 12: return launch_gemm<R, 12>(ctx, st, g);
-    case 16: return launch_gemm<R, 16>(ctx, st, g);
-    default: return "internal: unsupported GEMM tile";
+    return launch_gemm_rm<R>(ctx, st, g, ctx->m2l_ntiles);
+}
+
+// M2M into the parents of `level` (mode store) or L2L into the boxes of `level`
+template <typename R>
+static LfErr shift_gemm_t(lfmm_ctx* ctx, int level, bool l2l, cudaStream_t st)
+{
+    GemmArgs g;
+    g.p = ctx->p;
+    g.nc = lf_nc(ctx->p);
+    g.RP = ctx->m2l_rp;
+    g.levelh = ctx->m2l_levelh.as<double>();
+    g.cls = ctx->shift_cls.as<int>();
+    g.tiles = ctx->shift_tiles.as<int4>();
+    int first, ntiles;
+    if (!l2l) {
+        g.noff = 8;
+        g.mode = 1;
+        g.sorted = nullptr;
+        g.slots = ctx->m2m_slots.as<int>();
+        g.A = sizeof(R) == 8 ? ctx->m2m_A64.ptr : ctx->m2m_A32.ptr;
+        g.M = ctx->Mexp.ptr;
+        g.L = ctx->Mexp.ptr;
+        first = ctx->m2m_first[level];
+        ntiles = ctx->m2m_first[level + 1] - first;
+    } else {
+        g.noff = 1;
+        g.mode = 2;
+        g.sorted = ctx->m2l_sorted.as<int>();
+        g.slots = ctx->box_parent.as<int>();
+        g.A = sizeof(R) == 8 ? ctx->l2l_A64.ptr : ctx->l2l_A32.ptr;
+        g.M = ctx->Lexp.ptr;
+        g.L = ctx->Lexp.ptr;
+        first = ctx->l2l_tile_base + ctx->l2l_first[level];
+        ntiles = ctx->l2l_first[level + 1] - ctx->l2l_first[level];
     }
+    g.tile_base = first;
+    return launch_gemm_rm<R>(ctx, st, g, ntiles);
+}
+
+LfErr lf_shift_gemm(lfmm_ctx* ctx, int level, bool l2l, cudaStream_t st)
+{
+    return ctx->precision ? shift_gemm_t<float>(ctx, level, l2l, st) : shift_gemm_t<double>(ctx, level, l2l, st);
 }
 
 LfErr lf_m2l_gemm(lfmm_ctx* ctx, cudaStream_t st)

@@ -146,6 +146,102 @@ __global__ void __launch_bounds__(P2P_T) k_p2p(P2PArgs a)
     }
 }
 
+// Float32 near field: one warp per target leaf (leaves hold ~20 charges, so a
+// warp is the natural unit), no block-wide barriers.  Positions come as
+// float offsets from each particle's own leaf centre (computed once per
+// build); the offset between two box centres (or a source box's
+// polarization image and the target box) is formed in double once per warp
+// and entry, so no double arithmetic remains per particle or pair.
+#define PW_WARPS 4
+
+__global__ void k_rel_pos(int leaf_off, int nleaf, const LfD4* __restrict__ cen, const int* __restrict__ pbeg,
+                          const int* __restrict__ pend, const double* __restrict__ xs, const double* __restrict__ ys,
+                          const double* __restrict__ zs, float4* __restrict__ rel)
+{
+    const int li = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (li >= nleaf) return;
+    const int b = leaf_off + li;
+    const LfD4 c = cen[b];
+    for (int i = pbeg[b] + lane; i < pend[b]; i += 32)
+        rel[i] = make_float4((float)(xs[i] - c.x), (float)(ys[i] - c.y), (float)(zs[i] - c.z), 0.f);
+}
+
+__global__ void __launch_bounds__(32 * PW_WARPS) k_p2p_warp(P2PArgs a, const float4* __restrict__ rel, int nleaf)
+{
+    __shared__ float sx[PW_WARPS][32], sy[PW_WARPS][32], sz[PW_WARPS][32], sq[PW_WARPS][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int li = blockIdx.x * PW_WARPS + w;
+    if (li >= nleaf) return;  // whole warp
+    const float* q = reinterpret_cast<const float*>(a.q);
+    const int t = a.leaf_off + li;
+    const LfD4 ct = a.cen[t];
+    const int tb = a.pbeg[t], te = a.pend[t];
+    const int eb = a.nbeg[t], ee = a.nend[t];
+    for (int base = tb; base < te; base += 32) {
+        const int i = base + lane;
+        const bool valid = i < te;
+        float xi = 0.f, yi = 0.f, zi = 0.f;
+        if (valid) {
+            const float4 r = rel[i];
+            xi = r.x;
+            yi = r.y;
+            zi = r.z;
+        }
+        LfSum<float> P, Ex, Ey, Ez;
+        for (int e = eb; e < ee; ++e) {
+            const uint32_t ent = a.nent[e];
+            const int c = (int)(ent >> LFMM_ENT_SHIFT);
+            const int s = (int)(ent & LFMM_ENT_MASK);
+            const LfmmComp& cp = c_ncomp[c];
+            const LfD4 cs = a.cen[s];
+            // source box centre (free) or its polarization image (reaction), relative to the target box
+            const float dx0 = (float)(cs.x - ct.x), dy0 = (float)(cs.y - ct.y);
+            const float dz0 = (float)(cp.is_free ? cs.z - ct.z : cp.s * cs.z + cp.o - ct.z);
+            const float szs = cp.is_free ? 1.f : (float)cp.s;
+            const int sb = a.pbeg[s], se = a.pend[s];
+            for (int cb = sb; cb < se; cb += 32) {
+                const int j = cb + lane;
+                __syncwarp();
+                if (j < se) {
+                    const float4 r = rel[j];
+                    sx[w][lane] = r.x + dx0;
+                    sy[w][lane] = r.y + dy0;
+                    sz[w][lane] = szs * r.z + dz0;
+                    sq[w][lane] = q[j];
+                }
+                __syncwarp();
+                if (!valid) continue;
+                const int cnt = min(32, se - cb);
+                if (cp.is_free) {
+                    for (int u = 0; u < cnt; ++u)
+                        p2p_free_add<float>(xi - sx[w][u], yi - sy[w][u], zi - sz[w][u], sq[w][u], P, Ex, Ey, Ez);
+                } else {
+                    for (int u = 0; u < cnt; ++u)
+                        p2p_reaction_add<float>(cp, xi - sx[w][u], yi - sy[w][u], zi - sz[w][u], sq[w][u], a.Qn, P, Ex,
+                                                Ey, Ez);
+                }
+            }
+        }
+        if (valid) {
+            a.phi[i] = (double)P.s;
+            a.fld[3 * (size_t)i + 0] = (double)Ex.s;
+            a.fld[3 * (size_t)i + 1] = (double)Ey.s;
+            a.fld[3 * (size_t)i + 2] = (double)Ez.s;
+        }
+    }
+}
+
+LfErr lf_near_prepare(lfmm_ctx* ctx, cudaStream_t st)
+{
+    const LfmmLevel& leaf = ctx->levels[ctx->depth];
+    LF_TRY(lf_reserve(ctx->pos_rel, (size_t)ctx->n * sizeof(float4) + 16));
+    if (leaf.nbox > 0)
+        ++ctx->launches, k_rel_pos<<<lf_blocks(leaf.nbox, 4), 128, 0, st>>>(
+            leaf.off, leaf.nbox, ctx->box_center.as<LfD4>(), ctx->box_pbeg.as<int>(), ctx->box_pend.as<int>(),
+            ctx->xs.as<double>(), ctx->ys.as<double>(), ctx->zs.as<double>(), ctx->pos_rel.as<float4>());
+    return lf_cuda(cudaGetLastError(), "relative positions");
+}
+
 // Near field with the learned reaction kernels.  For a trained component each
 // warp first looks its 32 pairs (one source against the warp's 32 targets) up
 // in the error table; if any lane accepts, the warp evaluates the network for
@@ -360,7 +456,8 @@ LfErr lf_near_field(lfmm_ctx* ctx, cudaStream_t st)
         if (net)
             ++ctx->launches, k_p2p_net<float><<<leaf.nbox, P2P_T, 0, st>>>(a);
         else
-            ++ctx->launches, k_p2p<float><<<leaf.nbox, P2P_T, 0, st>>>(a);
+            ++ctx->launches, k_p2p_warp<<<lf_blocks(leaf.nbox, PW_WARPS), 32 * PW_WARPS, 0, st>>>(
+                a, ctx->pos_rel.as<float4>(), leaf.nbox);
     } else {
         if (net)
             ++ctx->launches, k_p2p_net<double><<<leaf.nbox, P2P_T, 0, st>>>(a);

@@ -9,11 +9,13 @@ library and for the CPU oracle alike.
 * :func:`config2` -- same medium, N split equally between the three layers
   (remainder to the middle one): top z in [0.1,1.1], middle [-1.1,-0.1],
   bottom [-2.3,-1.3], x, y uniform in [-0.5,0.5].
-* :func:`near_interface` -- same medium, every charge within ``delta`` of an
-  interface on its own side (top (0, delta], middle [-delta, 0) and
-  (-1.2, -1.2 + delta], bottom [-1.2 - delta, -1.2)); the near field then
-  holds reaction interactions, which the other workloads' trees admit to
-  the far field.
+* :func:`near_interface` -- same medium, every charge between ``hmin`` and
+  ``delta`` from an interface on its own side (top [hmin, delta], middle
+  [-delta, -hmin] and [-1.2 + hmin, -1.2 + delta], bottom
+  [-1.2 - delta, -1.2 - hmin]); the near field then holds reaction
+  interactions, which the other workloads' trees admit to the far field.
+  ``hmin`` (default 1e-3) keeps each charge a finite distance from its own
+  polarization image, as a charge of finite size would be.
 * :func:`paper_p4` -- the irregular domains of Section 4: charges uniform in
   r(theta) = 0.5 - a + a P_4(cos theta), a = (0.1, 0.15, 0.05), centred at
   z = 0.6, -0.6, -1.8, eps = (21.2, 47.5, 62.8), by rejection from the
@@ -74,17 +76,14 @@ def config2(n: int = 1 << 20, seed: int | None = None, eps=EPS_CONFIG) -> Worklo
     return Workload("config2_n%d" % n, np.array(D_CONFIG), np.array(eps, dtype=np.float64), xyz, layer, q)
 
 
-def near_interface(n: int = 1 << 18, delta: float = 0.02, seed: int | None = None, eps=EPS_CONFIG) -> Workload:
+def near_interface(n: int = 1 << 18, delta: float = 0.02, hmin: float = 1e-3, seed: int | None = None,
+                   eps=EPS_CONFIG) -> Workload:
     rng = np.random.Generator(np.random.PCG64(SEED_BASE + 4 if seed is None else seed))
     d0, d1 = D_CONFIG
     sizes = [n // 4, n // 4, n // 4, n - 3 * (n // 4)]
-    spans = [((d0, d0 + delta), 0), ((d0 - delta, d0), 1), ((d1, d1 + delta), 1), ((d1 - delta, d1), 2)]
-    parts = []
-    for cnt, ((lo, hi), l) in zip(sizes, spans):
-        p = _box(rng, cnt, lo, hi)
-        # keep charges strictly inside their layer
-        p[:, 2] = np.clip(p[:, 2], lo + 1e-9, hi - 1e-9)
-        parts.append((p, l))
+    spans = [((d0 + hmin, d0 + delta), 0), ((d0 - delta, d0 - hmin), 1), ((d1 + hmin, d1 + delta), 1),
+             ((d1 - delta, d1 - hmin), 2)]
+    parts = [(_box(rng, cnt, lo, hi), l) for cnt, ((lo, hi), l) in zip(sizes, spans)]
     xyz = np.concatenate([p for p, _ in parts])
     layer = np.concatenate([np.full(p.shape[0], l, dtype=np.int32) for p, l in parts])
     q = rng.uniform(-1.0, 1.0, size=n)

@@ -142,3 +142,21 @@ def test_rejects_points_outside_their_layer():
         f.build(w.xyz, w.layer)  # context still usable
         phi, _ = f.evaluate(w.q)
         assert np.all(np.isfinite(phi))
+
+
+def test_fp32_form_near_interface_matches_fp64():
+    # every charge within 0.02 of an interface: the near field holds reaction
+    # pairs, evaluated in float32 (offsets from leaf centres, compensated sums)
+    w = workloads.near_interface(16000)
+    out = {}
+    for prec in (0, 1):
+        with LayeredFMM(w.d, w.eps, 10, precision=prec) as f:
+            f.build(w.xyz, w.layer)
+            out[prec] = f.evaluate(w.q)
+            st = f.stats()
+    assert st["p2p_reaction"] > 0
+    e_phi = oracle.err2(out[0][0], out[1][0])
+    e_fld = oracle.err2(out[0][1], out[1][1])
+    print("near_interface 16k: FP32 vs FP64 Err2 phi %.2e field %.2e" % (e_phi, e_fld))
+    assert e_phi < 1e-5
+    assert e_fld < 1e-5
