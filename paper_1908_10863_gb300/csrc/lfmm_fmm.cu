@@ -495,6 +495,14 @@ static LfErr far_field(lfmm_ctx* ctx, cudaStream_t st)
     const R* octU = reinterpret_cast<const R*>(sizeof(R) == 8 ? ctx->oct_U64.ptr : ctx->oct_U32.ptr);
     const R* freeT = reinterpret_cast<const R*>(sizeof(R) == 8 ? ctx->free_T64.ptr : ctx->free_T32.ptr);
 
+    // levels below lmin take part in no M2L: no multipoles are needed there and
+    // their locals stay zero, so M2M stops and L2L starts at lmin
+    int lmin = depth;
+    for (int l = 0; l <= depth; ++l)
+        if (ctx->levels[l].m2l_count + ctx->levels[l].m2r_count > 0) {
+            lmin = l;
+            break;
+        }
     // upward pass
     int ph = lf_prof_start(ctx, LFMM_TIME_P2M, st);
     {
@@ -508,7 +516,7 @@ static LfErr far_field(lfmm_ctx* ctx, cudaStream_t st)
     {
         size_t sm = sizeof(R) * (nc + 2 * (size_t)nre);
         int th = ((nre + 31) / 32) * 32;
-        for (int l = depth - 1; l >= 0; --l) {
+        for (int l = depth - 1; l >= lmin; --l) {
             const LfmmLevel& lv = ctx->levels[l];
             if (lv.nbox == 0) continue;
             ph = lf_prof_start(ctx, LFMM_TIME_M2M, st);
@@ -575,7 +583,7 @@ static LfErr far_field(lfmm_ctx* ctx, cudaStream_t st)
         }
         LF_TRY(lf_cuda(cudaGetLastError(), "m2l"));
     }
-    for (int l = 1; l <= depth; ++l) {
+    for (int l = lmin + 1; l <= depth; ++l) {
         const LfmmLevel& lv = ctx->levels[l];
         if (lv.nbox == 0) continue;
         ph = lf_prof_start(ctx, LFMM_TIME_L2L, st);

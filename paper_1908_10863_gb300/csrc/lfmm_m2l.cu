@@ -419,7 +419,8 @@ LfErr lf_prepare_m2l(lfmm_ctx* ctx, cudaStream_t st)
 struct GemmArgs {
     int p, nc, RP;
     int noff;           // offsets (gathered sources) per target: 189 (M2L), 8 (M2M), 1 (L2L)
-    int mode;           // 0: L += D / h_level (M2L), 1: L = D (M2M), 2: L += D (L2L)
+    int mode;           // 0: L += D / h_level (M2L), 1: L = D, 2: L += D (L2L), 3: atomic L += D (M2M)
+    int split;          // 1: one block per (tile, offset) instead of one per tile
     int tile_base;      // first tile of this launch
     const int4* tiles;  // level, class, start, count
     const int* sorted;  // targets grouped by class, or null: targets start .. start + count - 1
@@ -444,7 +445,8 @@ __global__ void __launch_bounds__(G_T) k_m2l_gemm(GemmArgs g)
     __shared__ int s_src[G_TB];
     const int tid = threadIdx.x;
     const int cg = tid & 15, rg = tid >> 4;
-    const int4 tile = g.tiles[g.tile_base + blockIdx.x];
+    const int tix = g.split ? (int)blockIdx.x / g.noff : (int)blockIdx.x;
+    const int4 tile = g.tiles[g.tile_base + tix];
     const int level = tile.x, cls = tile.y, start = tile.z, cnt = tile.w;
     const int nc = g.nc;
     const R* A = reinterpret_cast<const R*>(g.A);
@@ -458,7 +460,8 @@ __global__ void __launch_bounds__(G_T) k_m2l_gemm(GemmArgs g)
         for (int c = 0; c < 4; ++c) acc[r][c] = 0;
     __syncthreads();
     const int noff = g.noff;
-    for (int oi = 0; oi < noff; ++oi) {
+    const int oi0 = g.split ? (int)blockIdx.x % noff : 0, oi1 = g.split ? oi0 + 1 : noff;
+    for (int oi = oi0; oi < oi1; ++oi) {
         const int o = g.cls[cls * noff + oi];
         if (tid < G_TB) s_src[tid] = (tid < cnt) ? g.slots[(size_t)s_tb[tid] * noff + oi] : -1;
         __syncthreads();
@@ -505,6 +508,8 @@ __global__ void __launch_bounds__(G_T) k_m2l_gemm(GemmArgs g)
             if (row < nc) {
                 if (g.mode == 1)
                     Lt[row] = acc[r][c];
+                else if (g.mode == 3)
+                    atomicAdd(Lt + row, acc[r][c]);
                 else
                     Lt[row] += acc[r][c] * ih;
             }
@@ -519,7 +524,8 @@ static LfErr launch_gemm(lfmm_ctx* ctx, cudaStream_t st, const GemmArgs& g, int 
     constexpr int RP = 16 * RM;
     size_t sm = sizeof(R) * ((size_t)G_KC * RP + (size_t)G_TB * (RP + 1));
     LF_CHECK(cudaFuncSetAttribute(k_m2l_gemm<R, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    ++ctx->launches, k_m2l_gemm<R, RM><<<ntiles, G_T, sm, st>>>(g);
+    const int nblk = g.split ? ntiles * g.noff : ntiles;
+    ++ctx->launches, k_m2l_gemm<R, RM><<<nblk, G_T, sm, st>>>(g);
     return lf_cuda(cudaGetLastError(), "gathered gemm");
 }
 
@@ -545,6 +551,7 @@ static LfErr m2l_gemm_t(lfmm_ctx* ctx, cudaStream_t st)
     g.RP = ctx->m2l_rp;
     g.noff = G_NOFF;
     g.mode = 0;
+    g.split = 0;
     g.tile_base = 0;
     g.tiles = ctx->m2l_tiles.as<int4>();
     g.sorted = ctx->m2l_sorted.as<int>();
@@ -569,9 +576,12 @@ static LfErr shift_gemm_t(lfmm_ctx* ctx, int level, bool l2l, cudaStream_t st)
     g.cls = ctx->shift_cls.as<int>();
     g.tiles = ctx->shift_tiles.as<int4>();
     int first, ntiles;
+    g.split = 0;
     if (!l2l) {
+        // one block per (tile of parents, child octant), summed by atomics
         g.noff = 8;
-        g.mode = 1;
+        g.mode = 3;
+        g.split = 1;
         g.sorted = nullptr;
         g.slots = ctx->m2m_slots.as<int>();
         g.A = sizeof(R) == 8 ? ctx->m2m_A64.ptr : ctx->m2m_A32.ptr;
@@ -579,6 +589,9 @@ static LfErr shift_gemm_t(lfmm_ctx* ctx, int level, bool l2l, cudaStream_t st)
         g.L = ctx->Mexp.ptr;
         first = ctx->m2m_first[level];
         ntiles = ctx->m2m_first[level + 1] - first;
+        const LfmmLevel& lv = ctx->levels[level];
+        LF_CHECK(cudaMemsetAsync(reinterpret_cast<R*>(ctx->Mexp.ptr) + (size_t)lv.off * g.nc, 0,
+                                 sizeof(R) * (size_t)lv.nbox * g.nc, st));
     } else {
         g.noff = 1;
         g.mode = 2;

@@ -266,7 +266,15 @@ __global__ void __launch_bounds__(R_T) k_m2r_gemm(RGemmArgs g)
     R* sC = sT + TS * TS;                    // cos(m phi), m <= 2p
     R* sS = sC + TS;
     __shared__ int s_src[R_TB], s_tgt[R_TB];
+    __shared__ unsigned char s_n[RP], s_m[RP], s_im[RP];  // (n, m, imaginary part) of each packed index
     const int tid = threadIdx.x;
+    if (tid < RP) {
+        int n = 0, m = 0, im = 0;
+        if (tid < nc) lf_decode(p, tid, n, m, im);
+        s_n[tid] = (unsigned char)n;
+        s_m[tid] = (unsigned char)m;
+        s_im[tid] = (unsigned char)im;
+    }
     const int cg = tid & 15, rg = tid >> 4;
     const int4 b = g.batches[blockIdx.x];
     const int kidx = b.x, start = b.y, cnt = b.z;
@@ -299,9 +307,8 @@ __global__ void __launch_bounds__(R_T) k_m2r_gemm(RGemmArgs g)
         int kin = idx / RP, rout = idx - kin * RP;
         R v = 0;
         if (kin < nc && rout < nc) {
-            int n, mp, bim, k, l, aim;
-            lf_decode(p, kin, n, mp, bim);
-            lf_decode(p, rout, k, l, aim);
+            const int n = s_n[kin], mp = s_m[kin], bim = s_im[kin];
+            const int k = s_n[rout], l = s_m[rout], aim = s_im[rout];
             // T_N^mu (complex) = e^{i mu phi} T(N, |mu|) with T_N^{-mu} = (-1)^mu conj
             int N = n + k;
             int mu1 = mp + l;
