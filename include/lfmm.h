@@ -127,6 +127,8 @@ enum {
     LFMM_STAT_SURR_NET = 12,      /* near-field reaction pairs of the last evaluate done by the network */
     LFMM_STAT_SURR_QUAD = 13,     /* ... and by the quadrature */
     LFMM_STAT_TIMEOUTS = 14,      /* bounded device waits of the last evaluate that ran out (0 expected) */
+    LFMM_STAT_REACTION_TABLES = 15, /* Sommerfeld tables behind the reaction M2L keys (one per component,
+                                       level, lateral distance and vertical offset) */
     LFMM_STAT_COUNT = 16
 };
 lfmm_status lfmm_get_stats(const lfmm_ctx* ctx, int64_t* out, int nout);

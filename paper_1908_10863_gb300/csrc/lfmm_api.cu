@@ -716,14 +716,14 @@ void lfmm_destroy(lfmm_ctx* ctx)
                       &ctx->oct_U64, &ctx->oct_U32, &ctx->comp_dev, &ctx->perm, &ctx->xs, &ctx->ys, &ctx->zs,
                       &ctx->keys, &ctx->keys_tmp, &ctx->vals_tmp, &ctx->scan_tmp, &ctx->hist, &ctx->xyz_in,
                       &ctx->layer_in, &ctx->err_flag, &ctx->counts, &ctx->box_key, &ctx->box_pbeg, &ctx->box_pend,
-                      &ctx->box_parent, &ctx->box_cbeg, &ctx->box_cend, &ctx->box_center, &ctx->box_grid, &ctx->pos_rel, &ctx->flags, &ctx->idx,
+                      &ctx->box_parent, &ctx->box_cbeg, &ctx->box_cend, &ctx->box_center, &ctx->box_grid, &ctx->pos_rel, &ctx->level_consts, &ctx->flags, &ctx->idx,
                       &ctx->near_off, &ctx->near_ent, &ctx->m2l_off, &ctx->m2l_ent, &ctx->m2r_off, &ctx->m2r_ent,
                       &ctx->q_sorted, &ctx->Mexp, &ctx->Lexp, &ctx->phi_far, &ctx->phi_near, &ctx->fld_far,
                       &ctx->fld_near, &ctx->q_stage, &ctx->phi_stage, &ctx->fld_stage, &ctx->m2l_A64, &ctx->m2l_A32,
                       &ctx->m2l_cls, &ctx->m2l_inv, &ctx->m2l_slots, &ctx->m2l_keys, &ctx->m2l_sorted,
                       &ctx->m2l_tiles, &ctx->m2l_levelh, &ctx->m2r_keys, &ctx->m2r_order,
                       &ctx->m2r_tgt, &ctx->m2r_kstart, &ctx->m2r_kval, &ctx->m2r_tables, &ctx->m2r_levelh,
-                      &ctx->m2r_batches, &ctx->surr_theta, &ctx->surr_grad, &ctx->surr_m1,
+                      &ctx->m2r_batches, &ctx->m2r_tdesc, &ctx->m2r_ktab, &ctx->surr_theta, &ctx->surr_grad, &ctx->surr_m1,
                       &ctx->surr_m2, &ctx->surr_w, &ctx->surr_b, &ctx->surr_meta, &ctx->surr_err, &ctx->surr_comps,
                       &ctx->surr_xoff, &ctx->surr_counters, &ctx->m2l_Atc, &ctx->m2l_tc_tiles, &ctx->m2l_Ms, &ctx->m2m_A64, &ctx->m2m_A32,
                       &ctx->l2l_A64, &ctx->l2l_A32, &ctx->shift_cls, &ctx->m2m_slots, &ctx->shift_tiles};

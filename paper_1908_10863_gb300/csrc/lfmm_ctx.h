@@ -94,6 +94,7 @@ struct lfmm_ctx {
     DevBuf box_center;  // LfD4 (x, y, z, layer)
     DevBuf box_grid;    // int4 (ix, iy, iz, layer): grid cell of the box at its level
     DevBuf pos_rel;     // float4 per sorted charge: offset from its leaf centre
+    DevBuf level_consts;  // float4 [LFMM_MAXCOMP][16]: (K, F, G, Z) of the list tests, in box units
     DevBuf flags, idx;  // temporaries
 
     // lists: offsets per level box (near_off[level_box] relative to level base) and entries
@@ -112,7 +113,8 @@ struct lfmm_ctx {
     int m2l_tc_ok = 0, m2l_tc_ntiles = 0, use_tc = 1, tc_groups = 27;
     // reaction M2L grouped by geometry key on interface-aligned levels
     DevBuf m2r_keys, m2r_order, m2r_tgt, m2r_kstart, m2r_kval, m2r_tables, m2r_levelh, m2r_batches;
-    int m2r_nkeys = 0, m2r_nbatch = 0, m2r_keyed_from = 0;
+    DevBuf m2r_tdesc, m2r_ktab;  // table descriptors (component, level, rho^2, oz); table of each key
+    int m2r_nkeys = 0, m2r_nbatch = 0, m2r_keyed_from = 0, m2r_ntab = 0;
 
     // learned surrogate of the near-field reaction kernels
     DevBuf surr_theta, surr_grad, surr_m1, surr_m2, surr_w, surr_b, surr_meta, surr_err, surr_comps, surr_xoff,

@@ -250,21 +250,20 @@ LfErr lf_setup_m2l_ops(lfmm_ctx* ctx)
 // ---------------------------------------------------------------------------
 // Build: slot table and tiles.
 // ---------------------------------------------------------------------------
-__global__ void k_fill_slots(int off, int nb, double h, const uint32_t* __restrict__ bkey,
-                             const LfD4* __restrict__ cen, const int* __restrict__ mbeg,
-                             const int* __restrict__ mend, const uint32_t* __restrict__ ment,
-                             const int* __restrict__ inv, int* __restrict__ slots, int* __restrict__ err)
+__global__ void k_fill_slots(int off, int nb, const uint32_t* __restrict__ bkey, const int4* __restrict__ grid,
+                             const int* __restrict__ mbeg, const int* __restrict__ mend,
+                             const uint32_t* __restrict__ ment, const int* __restrict__ inv, int* __restrict__ slots,
+                             int* __restrict__ err)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nb) return;
     int t = off + i;
     int c = (int)(bkey[t] & 7u);
-    LfD4 ct = cen[t];
-    double ih = 1.0 / h;
+    const int4 gt = grid[t];
     for (int e = mbeg[t]; e < mend[t]; ++e) {
         int s = (int)(ment[e] & LFMM_ENT_MASK);
-        LfD4 cs = cen[s];
-        int ox = (int)lrint((ct.x - cs.x) * ih), oy = (int)lrint((ct.y - cs.y) * ih), oz = (int)lrint((ct.z - cs.z) * ih);
+        const int4 gs = grid[s];
+        const int ox = gt.x - gs.x, oy = gt.y - gs.y, oz = gt.z - gs.z;
         int loc = -1;
         if (ox >= -3 && ox <= 3 && oy >= -3 && oy <= 3 && oz >= -3 && oz <= 3)
             loc = inv[c * G_NALL + (ox + 3) * 49 + (oy + 3) * 7 + (oz + 3)];
@@ -320,7 +319,7 @@ LfErr lf_prepare_m2l(lfmm_ctx* ctx, cudaStream_t st)
         if (lv.nbox == 0) continue;
         if (l >= 2)
             ++ctx->launches, k_fill_slots<<<lf_blocks(lv.nbox, 128), 128, 0, st>>>(
-                lv.off, lv.nbox, lv.h, ctx->box_key.as<uint32_t>(), ctx->box_center.as<LfD4>(), ctx->m2l_off.as<int>(),
+                lv.off, lv.nbox, ctx->box_key.as<uint32_t>(), ctx->box_grid.as<int4>(), ctx->m2l_off.as<int>(),
                 ctx->m2l_off.as<int>() + ctx->nbox_total, ctx->m2l_ent.as<uint32_t>(), ctx->m2l_inv.as<int>(),
                 ctx->m2l_slots.as<int>(), err);
         ++ctx->launches, k_class_keys<<<lf_blocks(lv.nbox, 256), 256, 0, st>>>(

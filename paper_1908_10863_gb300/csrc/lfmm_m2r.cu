@@ -16,6 +16,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <map>
 #include <vector>
 
 #include "lfmm_ctx.h"
@@ -56,26 +57,30 @@ __host__ __device__ __forceinline__ void rkey_decode(uint32_t key, int& c, int& 
     oz = oi % R_OW - R_OR;
 }
 
-__global__ void k_m2r_keys(int off, int nb, double h, const LfD4* __restrict__ cen, const int* __restrict__ rbeg,
-                           const int* __restrict__ rend, const uint32_t* __restrict__ rent, int level,
-                           uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, int* __restrict__ tgt,
-                           int* __restrict__ bad)
+// Keys of the reaction M2L entries of one aligned level, from the boxes' grid
+// cells: lateral offsets are exact integers; the vertical offset of the
+// source's polarization image, (iz_t + 1/2) - s (iz_s + 1/2) - K, is an integer
+// on aligned levels (checked).
+__global__ void k_m2r_keys(int off, int nb, const int4* __restrict__ grid, const float4* __restrict__ lc,
+                           const int* __restrict__ rbeg, const int* __restrict__ rend,
+                           const uint32_t* __restrict__ rent, int level, uint32_t* __restrict__ keys,
+                           uint32_t* __restrict__ vals, int* __restrict__ tgt, int* __restrict__ bad)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nb) return;
     int t = off + i;
-    LfD4 ct = cen[t];
-    double ih = 1.0 / h;
+    const int4 gt = grid[t];
     for (int e = rbeg[t]; e < rend[t]; ++e) {
         uint32_t v = rent[e];
         int c = (int)(v >> LFMM_ENT_SHIFT);
         int s = (int)(v & LFMM_ENT_MASK);
         const LfmmComp& cp = c_rcomp[c];
-        LfD4 cs = cen[s];
-        double vx = (ct.x - cs.x) * ih, vy = (ct.y - cs.y) * ih, vz = (ct.z - (cp.s * cs.z + cp.o)) * ih;
-        int ox = (int)lrint(vx), oy = (int)lrint(vy), oz = (int)lrint(vz);
-        bool ok = fabs(vx - ox) < 1e-6 && fabs(vy - oy) < 1e-6 && fabs(vz - oz) < 1e-6 && ox >= -R_OR &&
-                  ox <= R_OR && oy >= -R_OR && oy <= R_OR && oz >= -R_OR && oz <= R_OR;
+        const int4 gs = grid[s];
+        const float4 k = lc[c * 16 + level];
+        const float vz = ((float)gt.z + 0.5f) - (float)cp.s * ((float)gs.z + 0.5f) - k.x;
+        const int ox = gt.x - gs.x, oy = gt.y - gs.y, oz = (int)lrintf(vz);
+        bool ok = fabsf(vz - (float)oz) < 1e-3f && ox >= -R_OR && ox <= R_OR && oy >= -R_OR && oy <= R_OR &&
+                  oz >= -R_OR && oz <= R_OR;
         if (!ok) atomicAdd(bad, 1);
         keys[e] = ok ? rkey(c, level, ox, oy, oz) : KEY_NONE;
         vals[e] = (uint32_t)e;
@@ -100,7 +105,10 @@ __global__ void k_key_starts(const uint32_t* __restrict__ keys, int n, const int
 }
 
 // One block per key: the box-unit table (lead + remainder) with the a = 2 sign.
-__global__ void k_m2r_tables(const uint32_t* __restrict__ kval, int nkeys, const double* __restrict__ levelh, int P,
+// One Sommerfeld table per (component, level, rho^2, oz): the table depends on
+// the lateral distance only; the azimuth enters through the phases applied
+// when the operator is assembled.
+__global__ void k_m2r_tables(const int4* __restrict__ tdesc, int ntab, const double* __restrict__ levelh, int P,
                              const double* __restrict__ gt, const double* __restrict__ gw, int Q,
                              double* __restrict__ tables)
 {
@@ -110,10 +118,10 @@ __global__ void k_m2r_tables(const uint32_t* __restrict__ kval, int nkeys, const
     double* sJ = sT + TT;
     double* sA = sJ + Q * TS;
     const int k = blockIdx.x;
-    int c, l, ox, oy, oz;
-    rkey_decode(kval[k], c, l, ox, oy, oz);
+    const int4 d = tdesc[k];
+    const int c = d.x, l = d.y, oz = d.w;
     const LfmmComp& cp = c_rcomp[c];
-    const double rho = sqrt((double)(ox * ox + oy * oy));
+    const double rho = sqrt((double)d.z);
     const double zz = (cp.a == 1) ? (double)oz : (double)(-oz);
     for (int j = threadIdx.x; j < TT; j += blockDim.x) sT[j] = 0.0;
     __syncthreads();
@@ -134,6 +142,9 @@ LfErr lf_prepare_m2r(lfmm_ctx* ctx, cudaStream_t st)
 {
     ctx->m2r_nkeys = 0;
     ctx->m2r_nbatch = 0;
+    ctx->m2r_ntab = 0;
+    ctx->stats[LFMM_STAT_REACTION_KEYS] = 0;
+    ctx->stats[LFMM_STAT_REACTION_TABLES] = 0;
     ctx->m2r_keyed_from = ctx->depth + 1;
     // the keyed GEMM holds a whole operator in shared memory: p <= 10
     if (ctx->m2l_rm == 0 || ctx->m2l_rm > 8 || ctx->m2r_total == 0) return LfErr();
@@ -174,7 +185,7 @@ LfErr lf_prepare_m2r(lfmm_ctx* ctx, cudaStream_t st)
         const LfmmLevel& lv = ctx->levels[l];
         if (lv.nbox == 0 || lv.m2r_count == 0) continue;
         ++ctx->launches, k_m2r_keys<<<lf_blocks(lv.nbox, 128), 128, 0, st>>>(
-            lv.off, lv.nbox, lv.h, ctx->box_center.as<LfD4>(), ctx->m2r_off.as<int>(),
+            lv.off, lv.nbox, ctx->box_grid.as<int4>(), ctx->level_consts.as<float4>(), ctx->m2r_off.as<int>(),
             ctx->m2r_off.as<int>() + ctx->nbox_total, ctx->m2r_ent.as<uint32_t>(), l, keys - first, vals - first,
             ctx->m2r_tgt.as<int>(), bad);
     }
@@ -201,20 +212,45 @@ LfErr lf_prepare_m2r(lfmm_ctx* ctx, cudaStream_t st)
     LF_CHECK(cudaMemcpyAsync(kstart.data(), ctx->m2r_kstart.ptr, sizeof(int) * nk, cudaMemcpyDeviceToHost, st));
     LF_CHECK(cudaStreamSynchronize(st));
     kstart[nk] = ne;
-    // tables, one per key
+    // tables, one per distinct (component, level, rho^2, oz)
+    std::vector<uint32_t> kv(nk);
+    LF_CHECK(cudaMemcpyAsync(kv.data(), ctx->m2r_kval.ptr, sizeof(uint32_t) * nk, cudaMemcpyDeviceToHost, st));
+    LF_CHECK(cudaStreamSynchronize(st));
+    std::vector<int4> tdesc;
+    std::vector<int> ktab(nk);
+    {
+        std::map<uint64_t, int> seen;
+        for (int64_t k = 0; k < nk; ++k) {
+            int c, l, ox, oy, oz;
+            rkey_decode(kv[k], c, l, ox, oy, oz);
+            const int r2 = ox * ox + oy * oy;
+            const uint64_t tk = ((uint64_t)c << 40) | ((uint64_t)l << 32) | ((uint64_t)r2 << 8) | (uint64_t)(oz + 128);
+            auto it = seen.find(tk);
+            if (it == seen.end()) {
+                it = seen.emplace(tk, (int)tdesc.size()).first;
+                tdesc.push_back(make_int4(c, l, r2, oz));
+            }
+            ktab[k] = it->second;
+        }
+    }
+    const int ntab = (int)tdesc.size();
     const int P = ctx->p, TS = 2 * P + 1, TT = TS * TS, Q = ctx->gl_q_m2l;
-    LF_TRY(lf_reserve(ctx->m2r_tables, (size_t)nk * TT * 8 + 16));
+    LF_TRY(lf_reserve(ctx->m2r_tables, (size_t)ntab * TT * 8 + 16));
+    LF_TRY(lf_reserve(ctx->m2r_tdesc, (size_t)ntab * sizeof(int4) + 16));
+    LF_TRY(lf_reserve(ctx->m2r_ktab, (size_t)nk * sizeof(int) + 16));
+    LF_CHECK(cudaMemcpyAsync(ctx->m2r_tdesc.ptr, tdesc.data(), ntab * sizeof(int4), cudaMemcpyHostToDevice, st));
+    LF_CHECK(cudaMemcpyAsync(ctx->m2r_ktab.ptr, ktab.data(), nk * sizeof(int), cudaMemcpyHostToDevice, st));
     double hl[16] = {0};
     for (int l = 0; l <= ctx->depth && l < 16; ++l) hl[l] = ctx->levels[l].h;
     LF_TRY(lf_reserve(ctx->m2r_levelh, sizeof(hl)));
     LF_CHECK(cudaMemcpyAsync(ctx->m2r_levelh.ptr, hl, sizeof(hl), cudaMemcpyHostToDevice, st));
     size_t sm = sizeof(double) * ((size_t)TT + 2 * (size_t)Q * TS);
     LF_CHECK(cudaFuncSetAttribute(k_m2r_tables, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    ++ctx->launches, k_m2r_tables<<<(int)nk, 128, sm, st>>>(ctx->m2r_kval.as<uint32_t>(), (int)nk,
-                                                            ctx->m2r_levelh.as<double>(), P,
-                                                            ctx->gl_t_m2l.as<double>(), ctx->gl_w_m2l.as<double>(), Q,
-                                                            ctx->m2r_tables.as<double>());
+    ++ctx->launches, k_m2r_tables<<<ntab, 128, sm, st>>>(ctx->m2r_tdesc.as<int4>(), ntab,
+                                                         ctx->m2r_levelh.as<double>(), P, ctx->gl_t_m2l.as<double>(),
+                                                         ctx->gl_w_m2l.as<double>(), Q, ctx->m2r_tables.as<double>());
     LF_TRY(lf_cuda(cudaGetLastError(), "m2r tables"));
+    ctx->m2r_ntab = ntab;
     // batches of R_TB pairs of one key
     std::vector<int4> batches;
     for (int k = 0; k < nk; ++k)
@@ -227,6 +263,7 @@ LfErr lf_prepare_m2r(lfmm_ctx* ctx, cudaStream_t st)
                              cudaMemcpyHostToDevice, st));
     LF_CHECK(cudaStreamSynchronize(st));
     ctx->stats[LFMM_STAT_REACTION_KEYS] = nk;
+    ctx->stats[LFMM_STAT_REACTION_TABLES] = ntab;
     return LfErr();
 }
 
@@ -237,7 +274,8 @@ struct RGemmArgs {
     int p, nc;
     const int4* batches;
     const uint32_t* kval;
-    const double* tables;
+    const double* tables;   // one per (component, level, rho^2, oz)
+    const int* ktab;        // table of each key
     const uint32_t* order;  // sorted entry indices
     const uint32_t* ent;    // m2r entries (component | source box)
     const int* tgt;         // target box per entry
@@ -289,7 +327,7 @@ __global__ void __launch_bounds__(R_T) k_m2r_gemm(RGemmArgs g)
         sC[tid] = (R)cs;
         sS[tid] = (R)sn;
     }
-    const double* Tk = g.tables + (size_t)kidx * TS * TS;
+    const double* Tk = g.tables + (size_t)g.ktab[kidx] * TS * TS;
     for (int j = tid; j < TS * TS; j += R_T) sT[j] = (R)Tk[j];
     if (tid < R_TB) {
         if (tid < cnt) {
@@ -395,6 +433,7 @@ static LfErr m2r_apply_t(lfmm_ctx* ctx, cudaStream_t st)
     g.batches = ctx->m2r_batches.as<int4>();
     g.kval = ctx->m2r_kval.as<uint32_t>();
     g.tables = ctx->m2r_tables.as<double>();
+    g.ktab = ctx->m2r_ktab.as<int>();
     g.order = ctx->m2r_order.as<uint32_t>();
     g.ent = ctx->m2r_ent.as<uint32_t>();
     g.tgt = ctx->m2r_tgt.as<int>();

@@ -751,6 +751,9 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
             }
         LF_CHECK(cudaMemcpyToSymbolAsync(c_tree_lc, lc.data(), sizeof(float4) * lc.size(), 0, cudaMemcpyHostToDevice,
                                          st));
+        LF_TRY(lf_reserve(ctx->level_consts, sizeof(float4) * lc.size()));
+        LF_CHECK(cudaMemcpyAsync(ctx->level_consts.ptr, lc.data(), sizeof(float4) * lc.size(), cudaMemcpyHostToDevice,
+                                 st));
         LF_CHECK(cudaStreamSynchronize(st));
     }
 

@@ -19,7 +19,7 @@ OPT_PRECISION, OPT_LEAF_CAP, OPT_PROFILE, OPT_QUAD_NODES, OPT_SURROGATE, OPT_SUR
 OPT_TENSOR_CORES = 7
 STAT_NAMES = ["n", "depth", "boxes", "leaves", "m2l_free", "m2l_reaction", "p2p_free", "p2p_reaction",
               "components", "m2m_edges", "launches", "reaction_keys", "surr_net_pairs", "surr_quad_pairs",
-              "timeouts"]
+              "timeouts", "reaction_tables"]
 SURR_NPARAM = 8835
 SURR_INFO = ["trained", "max_err", "cells_ok", "loss", "n_train", "n_val", "samples_ok"]
 TIME_NAMES = ["p2m", "m2m", "m2l_free", "m2l_reaction", "l2l", "l2p", "p2p", "total", "build"]
