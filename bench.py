@@ -49,6 +49,25 @@ def fp32_peak_tflops(sm_mhz):
     return SMS * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
+# Dense TF32 tensor peak: the measured bf16 GEMM rate of the GB300s
+# times the nominal TF32/BF16 ratio (1.1 / 2.25 PFLOP/s); fallback 1.9 PF bf16.
+TF32_PER_BF16 = 1.1 / 2.25
+# DRAM bytes (read + write) of one k_m2l_tc launch per free-space M2L pair,
+# from an ncu capture of the same workload at N=262,144 (749.6 MB for
+# 10,493,810 pairs), scaled to the bench's pair count.
+TC_DRAM_BYTES_PER_PAIR = 749.6e6 / 10493810
+
+
+def tf32_peak_tflops():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            bf16 = float(json.load(fh)["bf16_tflops"])
+        src = "of measured"
+    except Exception:
+        bf16, src = 1900.0, "of fallback"
+    return bf16 * TF32_PER_BF16, src
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -302,6 +321,7 @@ def main():
         st = f.stats()
         ms = sum(times) / len(times)
         results[name] = {"ms_per_step": ms, "times": times, "timings": tim, "stats": st, "launches": launches,
+                         "prec": prec,
                          "phi": phi_d.cpu().numpy().copy(), "E": fld_d.cpu().numpy().copy(),
                          "surrogate_train_s": train_s}
         if name == headline:
@@ -342,9 +362,25 @@ def main():
     tim = results[headline]["timings"]
     flops = st["m2l_free"] * m2l_flops_per_pair(args.p)
     m2l_ms = tim["m2l_free"]
-    sm_mhz = clk.get("sm_max_mhz") or 2070.0
-    peak = fp32_peak_tflops(sm_mhz)
     achieved = flops / (m2l_ms / 1e3) / 1e12 if m2l_ms > 0 else None
+    tensor_path = results[headline].get("prec", 1) == 1 and (args.p + 1) ** 2 <= 128
+    if tensor_path:
+        peak, src = tf32_peak_tflops()
+        roof = {"kernel": "k_m2l_tc (free-space M2L, tcgen05 3xTF32)", "bound": "tensor", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
+                "traffic": (TC_DRAM_BYTES_PER_PAIR * st["m2l_free"]) if args.p == 10 else None,
+                "peak_note": "dense TF32 = bf16 GEMM burst %s (MEASURED_PEAKS.json) x nominal TF32/BF16 1.1/2.25; "
+                             "algorithmic flops = 8 (p+1)^2 (p+1)(p+2)/2 per box pair (the tensor cores execute "
+                             "3 TF32 products of padded 128x128 operators); duration = the stage's CUDA events "
+                             "inside the timed steps; traffic scaled by pair count from an ncu capture at "
+                             "N=262,144" % src}
+    else:
+        sm_mhz = clk.get("sm_max_mhz") or 2070.0
+        peak = fp32_peak_tflops(sm_mhz)
+        roof = {"kernel": "k_m2l_gemm (free-space M2L, FP32 CUDA cores)", "bound": "alu", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "peak_note": "FP32 CUDA-core peak from unit counts (152 SMs x 128 lanes x 2 flops) at the max SM "
+                             "clock seen; algorithmic flops = 8 (p+1)^2 (p+1)(p+2)/2 per box pair"}
     line = {
         "metric": METRIC,
         "value": value,
@@ -364,12 +400,7 @@ def main():
         "err2": {"phi": forms_out[headline]["err2_phi"], "field": forms_out[headline]["err2_field"],
                  "targets": int(len(t)), "reference": "CPU oracle (FP64 direct sum, exact image series)"},
         "forms": forms_out,
-        "roofline": {"kernel": "k_m2l_gemm (free-space M2L, FP32)", "bound": "alu", "achieved": achieved,
-                     "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
-                     "traffic": None,
-                     "peak_note": "FP32 CUDA-core peak from unit counts (152 SMs x 128 lanes x 2 flops) at the "
-                                  "max SM clock seen; algorithmic flops = 8 (p+1)^2 (p+1)(p+2)/2 per box pair; "
-                                  "duration = the stage's CUDA events inside the timed steps"},
+        "roofline": roof,
         "cpu_baseline": {"value": len(t) / dt, "unit": "particles/s", "cores": threads, "kind": "oracle",
                          "sample": "%d targets (seeded subsample) x all %d sources, exact three-layer image "
                                    "series, %.1f s" % (len(t), w.n, dt)},
