@@ -6,10 +6,9 @@
 // the density stays exact; the network predicts the remainder
 //   y_k = (K_k - lead_k) / s_k,  s_0 = |C_r| / R_r,  s_1 = s_2 = |C_r| / R_r^2,
 // R_r = sqrt(rho^2 + (h + zeta_r)^2), with C_r e^{-k zeta_r} the remainder's
-// leading term, standardised per output.  Inputs (4): rho, the target and
-// source depths below/above their interfaces (h_t, h_s) and h = h_t + h_s,
-// each mapped linearly to [-1, 1] over the trained ranges (the remainder is
-// smooth on the scale zeta_r, so linear inputs suit it).
+// leading term, standardised per output.  Inputs (4): log10 rho, the target
+// and source depths below/above their interfaces (h_t, h_s) and
+// log10(rho / h), h = h_t + h_s, each mapped to about [-1, 1].
 // Network: 4 -> 64 -> 64 -> 64 -> 3, SiLU, one network per component,
 // weights stored as bfloat16, biases and all accumulation in float32.
 //

@@ -45,15 +45,17 @@ __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__floa
 // smallest pair depth h = h_t + h_s the network serves (below it: quadrature)
 #define SURR_HMIN 1e-4f
 
-// features of one pair (see the header comment): rho, the two depths and
-// their sum h, each mapped linearly to [-1, 1] over the trained ranges
+// features of one pair (see the header comment)
 __host__ __device__ __forceinline__ void surr_features(const LfmmSurrMeta& m, float rho, float ht, float hs,
                                                        float f[4])
 {
-    f[0] = rho * (2.0f / 3.0f) - 1.0f;
+    // log10 rho over [-3, log10 3]; the depths over their trained ranges;
+    // log10(rho / h) over about [-4.5, 4.5]
+    const float r = fmaxf(rho, 1e-3f), h = fmaxf(ht + hs, SURR_HMIN);
+    f[0] = (log10f(r) + 1.2614394f) * (1.0f / 1.7385606f);
     f[1] = 2.0f * ht / m.Tt - 1.0f;
     f[2] = 2.0f * hs / m.Ts - 1.0f;
-    f[3] = 2.0f * (ht + hs) / (m.Tt + m.Ts) - 1.0f;
+    f[3] = log10f(r / h) * (1.0f / 4.5f);
 }
 
 // error-table cell of a pair: log10 rho in [-3, log10 3] by log10 h in
