@@ -639,8 +639,9 @@ static lfmm_status eval_common(lfmm_ctx* ctx, int nrhs, const double* q_dev, dou
     prof_reset(ctx);
     cudaError_t ce = cudaMemsetAsync(ctx->counts.as<char>() + LFMM_TIMEOUT_OFF, 0, 4, ctx->s_main);
     if (ce != cudaSuccess) return fail(ctx, lf_cuda(ce, "timeout flag"));
-    for (int r = 0; r < nrhs; ++r) {
-        LfErr e = lf_evaluate_sorted(ctx, q_dev + (size_t)r * n, phi_dev + (size_t)r * n,
+    for (int r = 0; r < nrhs; r += LFMM_RHS_BATCH) {
+        const int nb = nrhs - r < LFMM_RHS_BATCH ? nrhs - r : LFMM_RHS_BATCH;
+        LfErr e = lf_evaluate_sorted(ctx, nb, q_dev + (size_t)r * n, phi_dev + (size_t)r * n,
                                      fld_dev ? fld_dev + (size_t)r * n * 3 : nullptr, ctx->s_main);
         if (!e.empty()) return fail(ctx, e);
     }

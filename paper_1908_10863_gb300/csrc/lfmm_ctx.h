@@ -69,6 +69,7 @@ struct lfmm_ctx {
     // geometry of the grid
     bool built = false;
     int64_t n = 0;
+    int nrhs_b = 1;  // right-hand sides of the evaluation in flight (expansions [nrhs_b][boxes][nc])
     int depth = 0;
     double H = 1.0;
     double origin[3] = {0, 0, 0};
@@ -166,7 +167,10 @@ LfErr lf_m2r_apply(lfmm_ctx* ctx, cudaStream_t st);
 LfErr lf_radix_sort(lfmm_ctx* ctx, uint32_t* keys, uint32_t* vals, int64_t n, cudaStream_t st);
 
 // ---- evaluation (lfmm_fmm.cu, lfmm_near.cu) ----
-LfErr lf_evaluate_sorted(lfmm_ctx* ctx, const double* q_dev, double* phi_dev, double* field_dev, cudaStream_t st);
+LfErr lf_evaluate_sorted(lfmm_ctx* ctx, int nrhs, const double* q_dev, double* phi_dev, double* field_dev,
+                         cudaStream_t st);
+// right-hand sides evaluated in one pass (larger requests are split)
+#define LFMM_RHS_BATCH 64
 LfErr lf_near_field(lfmm_ctx* ctx, cudaStream_t st);
 LfErr lf_near_prepare(lfmm_ctx* ctx, cudaStream_t st);
 

@@ -60,8 +60,10 @@ __global__ void __launch_bounds__(32) k_p2m(int off, int p, const LfD4* __restri
                                             const int* __restrict__ pbeg, const int* __restrict__ pend,
                                             const double* __restrict__ xs, const double* __restrict__ ys,
                                             const double* __restrict__ zs, const R* __restrict__ q, double h,
-                                            R* __restrict__ M)
+                                            R* __restrict__ M, int nrhs, int64_t qstride, size_t mstride)
 {
+    // the harmonics of a chunk of 32 charges are formed once and serve every
+    // right-hand side (charges q[r * qstride + i], multipoles M[r * mstride + ...])
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* su = reinterpret_cast<R*>(smem_raw);
     const int nre = lf_nre(p), nc = lf_nc(p);
@@ -72,10 +74,8 @@ __global__ void __launch_bounds__(32) k_p2m(int off, int p, const LfD4* __restri
     R* ure = su + lane * 2 * nre;
     R* uim = ure + nre;
     constexpr int KMAX = (LFMM_PMAX + 1) * (LFMM_PMAX + 1) / 32 + 1;
-    R acc[KMAX];
     int src[KMAX];
     for (int k = 0; k < KMAX; ++k) {
-        acc[k] = 0;
         int o = lane + 32 * k;
         src[k] = -1;
         if (o < nc) {
@@ -84,31 +84,35 @@ __global__ void __launch_bounds__(32) k_p2m(int off, int p, const LfD4* __restri
             src[k] = im ? (nre + lf_re(n, m)) : lf_re(n, m);
         }
     }
-    for (int start = pbeg[b]; start < pend[b]; start += 32) {
+    const int pb = pbeg[b], pe = pend[b];
+    for (int start = pb; start < pe; start += 32) {
         int i = start + lane;
-        if (i < pend[b]) {
+        if (i < pe) {
             R x = (R)((xs[i] - c.x) * ih), y = (R)((ys[i] - c.y) * ih), z = (R)((zs[i] - c.z) * ih);
             lf_regular<R>(p, x, y, z, ure, uim);
-            R qi = q[i];
-            for (int j = 0; j < nre; ++j) {
-                ure[j] *= qi;
-                uim[j] *= -qi;  // conjugate
-            }
+            for (int j = 0; j < nre; ++j) uim[j] = -uim[j];  // conjugate
         } else {
             for (int j = 0; j < 2 * nre; ++j) ure[j] = 0;
         }
         __syncwarp();
-        for (int k = 0; k < KMAX; ++k) {
-            if (src[k] < 0) continue;
-            R s = 0;
-            for (int r = 0; r < 32; ++r) s += su[r * 2 * nre + src[k]];
-            acc[k] += s;
+        const int cnt = min(32, pe - start);
+        R* sq = su + 32 * 2 * nre;  // this chunk's charges of one right-hand side
+        for (int r = 0; r < nrhs; ++r) {
+            sq[lane] = (i < pe) ? q[(size_t)r * qstride + i] : R(0);
+            __syncwarp();
+            R* out = M + (size_t)r * mstride + (size_t)b * nc;
+            for (int k = 0; k < KMAX; ++k) {
+                if (src[k] < 0) continue;
+                R s = 0;
+                for (int u = 0; u < cnt; ++u) s += sq[u] * su[u * 2 * nre + src[k]];
+                if (start == pb)
+                    out[lane + 32 * k] = s;
+                else
+                    out[lane + 32 * k] += s;
+            }
+            __syncwarp();
         }
-        __syncwarp();
     }
-    R* out = M + (size_t)b * nc;
-    for (int k = 0; k < KMAX; ++k)
-        if (src[k] >= 0) out[lane + 32 * k] = acc[k];
 }
 
 // Complex helpers for packed coefficient arrays (m may be negative).
@@ -384,59 +388,72 @@ __global__ void __launch_bounds__(32) k_l2p(int off, int p, const LfD4* __restri
                                             const int* __restrict__ pbeg, const int* __restrict__ pend,
                                             const double* __restrict__ xs, const double* __restrict__ ys,
                                             const double* __restrict__ zs, double h, const R* __restrict__ L,
-                                            double* __restrict__ phi, double* __restrict__ fld)
+                                            double* __restrict__ phi, double* __restrict__ fld, int nrhs,
+                                            size_t lstride, int64_t ostride)
 {
+    // harmonics of a chunk of 32 charges once, then every right-hand side's
+    // local expansion (L[r * lstride + ...]) in turn; outputs phi[r * ostride + i]
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nre = lf_nre(p), nc = lf_nc(p);
     R* sL = reinterpret_cast<R*>(smem_raw);
     R* su = sL + nc;
     const int lane = threadIdx.x;
     const int b = off + blockIdx.x;
-    for (int j = lane; j < nc; j += 32) sL[j] = L[(size_t)b * nc + j];
-    __syncwarp();
     const LfD4 c = cen[b];
     const double ih = 1.0 / h;
     R* ure = su + lane * 2 * nre;
     R* uim = ure + nre;
-    for (int i = pbeg[b] + lane; i < pend[b]; i += 32) {
-        R x = (R)((xs[i] - c.x) * ih), y = (R)((ys[i] - c.y) * ih), z = (R)((zs[i] - c.z) * ih);
-        lf_regular<R>(p, x, y, z, ure, uim);
-        LfAcc<R> P, Gz, Gx, Gy;
-        for (int n = 0; n <= p; ++n) {
-            // potential: Re(L conj U) with factor 2 for m >= 1
-            P.add(sL[lf_re(n, 0)] * ure[lf_re(n, 0)]);
-            for (int m = 1; m <= n; ++m)
-                P.add(R(2) * (sL[lf_re(n, m)] * ure[lf_re(n, m)] + sL[lf_im(p, n, m)] * uim[lf_re(n, m)]));
-            if (n == 0) continue;
-            // d/dz: L_n^m with U_{n-1}^m
-            Gz.add(sL[lf_re(n, 0)] * ure[lf_re(n - 1, 0)]);
-            for (int m = 1; m <= n - 1; ++m)
-                Gz.add(R(2) * (sL[lf_re(n, m)] * ure[lf_re(n - 1, m)] + sL[lf_im(p, n, m)] * uim[lf_re(n - 1, m)]));
-            // (dx + i dy): sum_{l=1..n} L_n^l conj(U_{n-1}^{l-1}) - L_n^0 U_{n-1}^1
-            //              - sum_{l=1..n-2} conj(L_n^l) U_{n-1}^{l+1}
-            for (int m = 1; m <= n; ++m) {
-                R lr = sL[lf_re(n, m)], li = sL[lf_im(p, n, m)];
-                R ur = ure[lf_re(n - 1, m - 1)], ui = uim[lf_re(n - 1, m - 1)];
-                Gx.add(lr * ur + li * ui);
-                Gy.add(li * ur - lr * ui);
-            }
-            if (n >= 2) {
-                R l0 = sL[lf_re(n, 0)];
-                Gx.add(-l0 * ure[lf_re(n - 1, 1)]);
-                Gy.add(-l0 * uim[lf_re(n - 1, 1)]);
-            }
-            for (int m = 1; m <= n - 2; ++m) {
-                R lr = sL[lf_re(n, m)], li = sL[lf_im(p, n, m)];
-                R ur = ure[lf_re(n - 1, m + 1)], ui = uim[lf_re(n - 1, m + 1)];
-                // -(lr - i li)(ur + i ui)
-                Gx.add(-(lr * ur + li * ui));
-                Gy.add(-(lr * ui - li * ur));
-            }
+    const int pb = pbeg[b], pe = pend[b];
+    for (int start = pb; start < pe; start += 32) {
+        const int i = start + lane;
+        const bool valid = i < pe;
+        if (valid) {
+            R x = (R)((xs[i] - c.x) * ih), y = (R)((ys[i] - c.y) * ih), z = (R)((zs[i] - c.z) * ih);
+            lf_regular<R>(p, x, y, z, ure, uim);
         }
-        phi[i] = (double)P.get();
-        fld[3 * (size_t)i + 0] = -(double)Gx.get() * ih;
-        fld[3 * (size_t)i + 1] = -(double)Gy.get() * ih;
-        fld[3 * (size_t)i + 2] = -(double)Gz.get() * ih;
+        for (int r = 0; r < nrhs; ++r) {
+            __syncwarp();
+            for (int j = lane; j < nc; j += 32) sL[j] = L[(size_t)r * lstride + (size_t)b * nc + j];
+            __syncwarp();
+            if (!valid) continue;
+            LfAcc<R> P, Gz, Gx, Gy;
+            for (int n = 0; n <= p; ++n) {
+                // potential: Re(L conj U) with factor 2 for m >= 1
+                P.add(sL[lf_re(n, 0)] * ure[lf_re(n, 0)]);
+                for (int m = 1; m <= n; ++m)
+                    P.add(R(2) * (sL[lf_re(n, m)] * ure[lf_re(n, m)] + sL[lf_im(p, n, m)] * uim[lf_re(n, m)]));
+                if (n == 0) continue;
+                // d/dz: L_n^m with U_{n-1}^m
+                Gz.add(sL[lf_re(n, 0)] * ure[lf_re(n - 1, 0)]);
+                for (int m = 1; m <= n - 1; ++m)
+                    Gz.add(R(2) * (sL[lf_re(n, m)] * ure[lf_re(n - 1, m)] + sL[lf_im(p, n, m)] * uim[lf_re(n - 1, m)]));
+                // (dx + i dy): sum_{l=1..n} L_n^l conj(U_{n-1}^{l-1}) - L_n^0 U_{n-1}^1
+                //              - sum_{l=1..n-2} conj(L_n^l) U_{n-1}^{l+1}
+                for (int m = 1; m <= n; ++m) {
+                    R lr = sL[lf_re(n, m)], li = sL[lf_im(p, n, m)];
+                    R ur = ure[lf_re(n - 1, m - 1)], ui = uim[lf_re(n - 1, m - 1)];
+                    Gx.add(lr * ur + li * ui);
+                    Gy.add(li * ur - lr * ui);
+                }
+                if (n >= 2) {
+                    R l0 = sL[lf_re(n, 0)];
+                    Gx.add(-l0 * ure[lf_re(n - 1, 1)]);
+                    Gy.add(-l0 * uim[lf_re(n - 1, 1)]);
+                }
+                for (int m = 1; m <= n - 2; ++m) {
+                    R lr = sL[lf_re(n, m)], li = sL[lf_im(p, n, m)];
+                    R ur = ure[lf_re(n - 1, m + 1)], ui = uim[lf_re(n - 1, m + 1)];
+                    // -(lr - i li)(ur + i ui)
+                    Gx.add(-(lr * ur + li * ui));
+                    Gy.add(-(lr * ui - li * ur));
+                }
+            }
+            const size_t o = (size_t)r * ostride + i;
+            phi[o] = (double)P.get();
+            fld[3 * o + 0] = -(double)Gx.get() * ih;
+            fld[3 * o + 1] = -(double)Gy.get() * ih;
+            fld[3 * o + 2] = -(double)Gz.get() * ih;
+        }
     }
 }
 
@@ -447,18 +464,22 @@ template <typename R>
 __global__ void k_gather_q(const double* __restrict__ q, const int32_t* __restrict__ perm, int64_t n,
                            R* __restrict__ qs)
 {
+    // blockIdx.y: right-hand side (vectors of n, caller order in, sorted order out)
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) qs[i] = (R)q[perm[i]];
+    const size_t r = blockIdx.y;
+    if (i < n) qs[r * n + i] = (R)q[r * n + perm[i]];
 }
 
 __global__ void k_combine(int64_t n, const int32_t* __restrict__ perm, const double* __restrict__ pf,
                           const double* __restrict__ pn, const double* __restrict__ ff,
                           const double* __restrict__ fn, double* __restrict__ phi, double* __restrict__ fld)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    // blockIdx.y: right-hand side; all arrays are vectors of n per right-hand side
+    int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i0 >= n) return;
+    const int64_t r = blockIdx.y;
     const double s = 0.079577471545947667884;  // 1 / (4 pi)
-    int64_t j = perm[i];
+    const int64_t i = r * n + i0, j = r * n + perm[i0];
     phi[j] = (pf[i] + pn[i]) * s;
     if (fld) {
         fld[3 * j + 0] = (ff[3 * i + 0] + fn[3 * i + 0]) * s;
@@ -486,6 +507,8 @@ static LfErr far_field(lfmm_ctx* ctx, cudaStream_t st)
     const LfmmLevel& leaf = ctx->levels[depth];
     R* M = ctx->Mexp.as<R>();
     R* L = ctx->Lexp.as<R>();
+    const int nr = ctx->nrhs_b;  // right-hand sides of this pass: expansions [nr][boxes][nc]
+    const size_t ms = (size_t)ctx->nbox_total * nc;
     const LfD4* cen = ctx->box_center.as<LfD4>();
     const int* pbeg = ctx->box_pbeg.as<int>();
     const int* pend = ctx->box_pend.as<int>();
@@ -506,10 +529,11 @@ static LfErr far_field(lfmm_ctx* ctx, cudaStream_t st)
     // upward pass
     int ph = lf_prof_start(ctx, LFMM_TIME_P2M, st);
     {
-        size_t sm = sizeof(R) * 2 * 32 * (size_t)nre;
+        size_t sm = sizeof(R) * (2 * 32 * (size_t)nre + 32);
         LF_CHECK(cudaFuncSetAttribute(k_p2m<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        ++ctx->launches, k_p2m<R><<<leaf.nbox, 32, sm, st>>>(leaf.off, p, cen, pbeg, pend, ctx->xs.as<double>(), ctx->ys.as<double>(),
-                                            ctx->zs.as<double>(), ctx->q_sorted.as<R>(), leaf.h, M);
+        ++ctx->launches, k_p2m<R><<<leaf.nbox, 32, sm, st>>>(leaf.off, p, cen, pbeg, pend, ctx->xs.as<double>(),
+                                                             ctx->ys.as<double>(), ctx->zs.as<double>(),
+                                                             ctx->q_sorted.as<R>(), leaf.h, M, nr, ctx->n, ms);
         LF_TRY(lf_cuda(cudaGetLastError(), "p2m"));
     }
     lf_prof_stop(ctx, ph, st);
@@ -523,7 +547,8 @@ static LfErr far_field(lfmm_ctx* ctx, cudaStream_t st)
             if (ctx->shift_ready)
                 LF_TRY(lf_shift_gemm(ctx, l, false, st));
             else
-                ++ctx->launches, k_m2m<R><<<lv.nbox, th, sm, st>>>(lv.off, p, cen, cbeg, cend, octU, M);
+                for (int r = 0; r < nr; ++r)
+                    ++ctx->launches, k_m2m<R><<<lv.nbox, th, sm, st>>>(lv.off, p, cen, cbeg, cend, octU, M + r * ms);
             lf_prof_stop(ctx, ph, st);
         }
         LF_TRY(lf_cuda(cudaGetLastError(), "m2m"));
@@ -536,7 +561,7 @@ static LfErr far_field(lfmm_ctx* ctx, cudaStream_t st)
     const int mth = ((nc + 31) / 32) * 32;
     const size_t lsm = sizeof(R) * (nc + 2 * (size_t)nre);
     const int lth = ((nre + 31) / 32) * 32;
-    LF_CHECK(cudaMemsetAsync(L, 0, sizeof(R) * (size_t)ctx->nbox_total * nc, st));
+    LF_CHECK(cudaMemsetAsync(L, 0, sizeof(R) * ms * nr, st));
     const bool gemm = ctx->m2l_ntiles > 0;
     if (gemm) {
         ph = lf_prof_start(ctx, LFMM_TIME_M2L_FREE, st);
@@ -570,7 +595,11 @@ static LfErr far_field(lfmm_ctx* ctx, cudaStream_t st)
             a.mend = ctx->m2l_off.as<int>() + ctx->nbox_total;
             a.ment = ctx->m2l_ent.as<uint32_t>();
             ph = lf_prof_start(ctx, LFMM_TIME_M2L_FREE, st);
-            ++ctx->launches, k_m2l<R, false><<<lv.nbox, mth, msm_f, st>>>(a);
+            for (int r = 0; r < nr; ++r) {
+                a.M = M + r * ms;
+                a.L = L + r * ms;
+                ++ctx->launches, k_m2l<R, false><<<lv.nbox, mth, msm_f, st>>>(a);
+            }
             lf_prof_stop(ctx, ph, st);
         }
         if (lv.m2r_count > 0 && l < ctx->m2r_keyed_from) {
@@ -578,7 +607,11 @@ static LfErr far_field(lfmm_ctx* ctx, cudaStream_t st)
             a.mend = ctx->m2r_off.as<int>() + ctx->nbox_total;
             a.ment = ctx->m2r_ent.as<uint32_t>();
             ph = lf_prof_start(ctx, LFMM_TIME_M2L_REACTION, st);
-            ++ctx->launches, k_m2l<R, true><<<lv.nbox, mth, msm_r, st>>>(a);
+            for (int r = 0; r < nr; ++r) {
+                a.M = M + r * ms;
+                a.L = L + r * ms;
+                ++ctx->launches, k_m2l<R, true><<<lv.nbox, mth, msm_r, st>>>(a);
+            }
             lf_prof_stop(ctx, ph, st);
         }
         LF_TRY(lf_cuda(cudaGetLastError(), "m2l"));
@@ -590,7 +623,8 @@ static LfErr far_field(lfmm_ctx* ctx, cudaStream_t st)
         if (ctx->shift_ready)
             LF_TRY(lf_shift_gemm(ctx, l, true, st));
         else
-            ++ctx->launches, k_l2l<R><<<lv.nbox, lth, lsm, st>>>(lv.off, p, cen, par, octU, L);
+            for (int r = 0; r < nr; ++r)
+                ++ctx->launches, k_l2l<R><<<lv.nbox, lth, lsm, st>>>(lv.off, p, cen, par, octU, L + r * ms);
         lf_prof_stop(ctx, ph, st);
         LF_TRY(lf_cuda(cudaGetLastError(), "l2l"));
     }
@@ -598,34 +632,40 @@ static LfErr far_field(lfmm_ctx* ctx, cudaStream_t st)
     {
         size_t sm = sizeof(R) * (nc + 2 * 32 * (size_t)nre);
         LF_CHECK(cudaFuncSetAttribute(k_l2p<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        ++ctx->launches, k_l2p<R><<<leaf.nbox, 32, sm, st>>>(leaf.off, p, cen, pbeg, pend, ctx->xs.as<double>(), ctx->ys.as<double>(),
-                                            ctx->zs.as<double>(), leaf.h, L, ctx->phi_far.as<double>(),
-                                            ctx->fld_far.as<double>());
+        ++ctx->launches, k_l2p<R><<<leaf.nbox, 32, sm, st>>>(leaf.off, p, cen, pbeg, pend, ctx->xs.as<double>(),
+                                                             ctx->ys.as<double>(), ctx->zs.as<double>(), leaf.h, L,
+                                                             ctx->phi_far.as<double>(), ctx->fld_far.as<double>(), nr,
+                                                             ms, ctx->n);
         LF_TRY(lf_cuda(cudaGetLastError(), "l2p"));
     }
     lf_prof_stop(ctx, ph, st);
     return LfErr();
 }
 
-LfErr lf_evaluate_sorted(lfmm_ctx* ctx, const double* q_dev, double* phi_dev, double* field_dev, cudaStream_t st)
+LfErr lf_evaluate_sorted(lfmm_ctx* ctx, int nrhs, const double* q_dev, double* phi_dev, double* field_dev,
+                         cudaStream_t st)
 {
+    // one pass over nrhs charge vectors on the same tree: [nrhs][n] in, [nrhs][n] (and [nrhs][n][3]) out
     const int64_t n = ctx->n;
     const int nc = lf_nc(ctx->p);
     const size_t rs = ctx->precision ? sizeof(float) : sizeof(double);
-    LF_TRY(lf_reserve(ctx->q_sorted, (size_t)n * rs));
-    LF_TRY(lf_reserve(ctx->Mexp, (size_t)ctx->nbox_total * nc * rs));
-    LF_TRY(lf_reserve(ctx->Lexp, (size_t)ctx->nbox_total * nc * rs));
-    LF_TRY(lf_reserve(ctx->phi_far, (size_t)n * 8));
-    LF_TRY(lf_reserve(ctx->phi_near, (size_t)n * 8));
-    LF_TRY(lf_reserve(ctx->fld_far, (size_t)n * 24));
-    LF_TRY(lf_reserve(ctx->fld_near, (size_t)n * 24));
+    const size_t nr = (size_t)nrhs;
+    ctx->nrhs_b = nrhs;
+    LF_TRY(lf_reserve(ctx->q_sorted, (size_t)n * rs * nr));
+    LF_TRY(lf_reserve(ctx->Mexp, (size_t)ctx->nbox_total * nc * rs * nr));
+    LF_TRY(lf_reserve(ctx->Lexp, (size_t)ctx->nbox_total * nc * rs * nr));
+    LF_TRY(lf_reserve(ctx->phi_far, (size_t)n * 8 * nr));
+    LF_TRY(lf_reserve(ctx->phi_near, (size_t)n * 8 * nr));
+    LF_TRY(lf_reserve(ctx->fld_far, (size_t)n * 24 * nr));
+    LF_TRY(lf_reserve(ctx->fld_near, (size_t)n * 24 * nr));
     LF_CHECK(cudaMemcpyToSymbolAsync(c_comp, ctx->comp, sizeof(LfmmComp) * ctx->ncomp, 0, cudaMemcpyHostToDevice, st));
     const int ptot = lf_prof_start(ctx, LFMM_TIME_TOTAL, st);
+    const dim3 g1(lf_blocks(n, 256), (unsigned)nrhs);
     if (ctx->precision)
-        ++ctx->launches, k_gather_q<float><<<lf_blocks(n, 256), 256, 0, st>>>(q_dev, ctx->perm.as<int32_t>(), n, ctx->q_sorted.as<float>());
+        ++ctx->launches, k_gather_q<float><<<g1, 256, 0, st>>>(q_dev, ctx->perm.as<int32_t>(), n, ctx->q_sorted.as<float>());
     else
-        ++ctx->launches, k_gather_q<double><<<lf_blocks(n, 256), 256, 0, st>>>(q_dev, ctx->perm.as<int32_t>(), n,
-                                                                ctx->q_sorted.as<double>());
+        ++ctx->launches, k_gather_q<double><<<g1, 256, 0, st>>>(q_dev, ctx->perm.as<int32_t>(), n,
+                                                               ctx->q_sorted.as<double>());
     LF_TRY(lf_cuda(cudaGetLastError(), "gather q"));
     // near field on its own stream, concurrent with the far field
     LF_CHECK(cudaEventRecord(ctx->ev_fork, st));
@@ -637,9 +677,9 @@ LfErr lf_evaluate_sorted(lfmm_ctx* ctx, const double* q_dev, double* phi_dev, do
     else
         LF_TRY(far_field<double>(ctx, st));
     LF_CHECK(cudaStreamWaitEvent(st, ctx->ev_join, 0));
-    ++ctx->launches, k_combine<<<lf_blocks(n, 256), 256, 0, st>>>(n, ctx->perm.as<int32_t>(), ctx->phi_far.as<double>(),
-                                                  ctx->phi_near.as<double>(), ctx->fld_far.as<double>(),
-                                                  ctx->fld_near.as<double>(), phi_dev, field_dev);
+    ++ctx->launches, k_combine<<<g1, 256, 0, st>>>(n, ctx->perm.as<int32_t>(), ctx->phi_far.as<double>(),
+                                                    ctx->phi_near.as<double>(), ctx->fld_far.as<double>(),
+                                                    ctx->fld_near.as<double>(), phi_dev, field_dev);
     LF_TRY(lf_cuda(cudaGetLastError(), "combine"));
     lf_prof_stop(ctx, ptot, st);
     return LfErr();

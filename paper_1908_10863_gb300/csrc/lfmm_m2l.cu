@@ -429,6 +429,7 @@ struct GemmArgs {
     const void* A;
     const void* M;
     void* L;
+    size_t mstride, lstride;  // per right-hand side (blockIdx.y), in elements
 };
 
 template <typename R, int RM>
@@ -449,8 +450,8 @@ __global__ void __launch_bounds__(G_T) k_m2l_gemm(GemmArgs g)
     const int level = tile.x, cls = tile.y, start = tile.z, cnt = tile.w;
     const int nc = g.nc;
     const R* A = reinterpret_cast<const R*>(g.A);
-    const R* M = reinterpret_cast<const R*>(g.M);
-    R* L = reinterpret_cast<R*>(g.L);
+    const R* M = reinterpret_cast<const R*>(g.M) + (size_t)blockIdx.y * g.mstride;
+    R* L = reinterpret_cast<R*>(g.L) + (size_t)blockIdx.y * g.lstride;
     if (tid < G_TB) s_tb[tid] = (tid < cnt) ? (g.sorted ? g.sorted[start + tid] : start + tid) : -1;
     R acc[RM][4];
 #pragma unroll
@@ -524,7 +525,7 @@ static LfErr launch_gemm(lfmm_ctx* ctx, cudaStream_t st, const GemmArgs& g, int 
     size_t sm = sizeof(R) * ((size_t)G_KC * RP + (size_t)G_TB * (RP + 1));
     LF_CHECK(cudaFuncSetAttribute(k_m2l_gemm<R, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const int nblk = g.split ? ntiles * g.noff : ntiles;
-    ++ctx->launches, k_m2l_gemm<R, RM><<<nblk, G_T, sm, st>>>(g);
+    ++ctx->launches, k_m2l_gemm<R, RM><<<dim3(nblk, ctx->nrhs_b), G_T, sm, st>>>(g);
     return lf_cuda(cudaGetLastError(), "gathered gemm");
 }
 
@@ -560,6 +561,7 @@ static LfErr m2l_gemm_t(lfmm_ctx* ctx, cudaStream_t st)
     g.A = sizeof(R) == 8 ? ctx->m2l_A64.ptr : ctx->m2l_A32.ptr;
     g.M = ctx->Mexp.ptr;
     g.L = ctx->Lexp.ptr;
+    g.mstride = g.lstride = (size_t)ctx->nbox_total * g.nc;
     return launch_gemm_rm<R>(ctx, st, g, ctx->m2l_ntiles);
 }
 
@@ -574,6 +576,7 @@ static LfErr shift_gemm_t(lfmm_ctx* ctx, int level, bool l2l, cudaStream_t st)
     g.levelh = ctx->m2l_levelh.as<double>();
     g.cls = ctx->shift_cls.as<int>();
     g.tiles = ctx->shift_tiles.as<int4>();
+    g.mstride = g.lstride = (size_t)ctx->nbox_total * g.nc;
     int first, ntiles;
     g.split = 0;
     if (!l2l) {
@@ -589,8 +592,8 @@ static LfErr shift_gemm_t(lfmm_ctx* ctx, int level, bool l2l, cudaStream_t st)
         first = ctx->m2m_first[level];
         ntiles = ctx->m2m_first[level + 1] - first;
         const LfmmLevel& lv = ctx->levels[level];
-        LF_CHECK(cudaMemsetAsync(reinterpret_cast<R*>(ctx->Mexp.ptr) + (size_t)lv.off * g.nc, 0,
-                                 sizeof(R) * (size_t)lv.nbox * g.nc, st));
+        LF_CHECK(cudaMemset2DAsync(reinterpret_cast<R*>(ctx->Mexp.ptr) + (size_t)lv.off * g.nc, g.mstride * sizeof(R), 0,
+                                   sizeof(R) * (size_t)lv.nbox * g.nc, ctx->nrhs_b, st));
     } else {
         g.noff = 1;
         g.mode = 2;

@@ -207,6 +207,8 @@ struct TcArgs {
     int zero_row;           // index of the zero box of Ms
     float* L;               // locals [box][nc]
     int nc;
+    size_t ms_stride;       // per right-hand side (blockIdx.y): split multipoles, in floats
+    size_t l_stride;        // per right-hand side: local expansions, in floats
     int groups;             // CTAs per tile (offset groups; divides 189)
     int* err;               // [0]: timeouts
 };
@@ -291,7 +293,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(TcArgs g)
                 const int row = warp * 32 + rl;
                 const uint32_t off = piece * TC_X_BYTES + sw64(row, chunk * 4);
                 if (src >= 0) {
-                    const float* gsrc = g.Ms + ((size_t)src * TC_XP + piece) * TC_MROW + kc * TC_KC + chunk * 4;
+                    const float* gsrc = g.Ms + (size_t)blockIdx.y * g.ms_stride + ((size_t)src * TC_XP + piece) * TC_MROW +
+                                        kc * TC_KC + chunk * 4;
                     cp_async16(xbase + off, gsrc);
                 } else {
                     *reinterpret_cast<float4*>(xs + off) = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -328,7 +331,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(TcArgs g)
 #pragma unroll
                     for (int i = 0; i < 32; ++i) {
                         const int j = col0 + i;
-                        if (j < cnt) atomicAdd(g.L + (size_t)s_tb[j] * nc + row, v[i] * ih);
+                        if (j < cnt) atomicAdd(g.L + (size_t)blockIdx.y * g.l_stride + (size_t)s_tb[j] * nc + row, v[i] * ih);
                     }
                 }
             }
@@ -425,9 +428,12 @@ LfErr lf_setup_m2l_tc(lfmm_ctx* ctx, const double* A64, int KP, int RP)
 // one more box of zeros stands in for missing sources
 __global__ void k_split_m(const float* __restrict__ M, int nbox, int nc, float* __restrict__ Ms)
 {
+    // blockIdx.y: right-hand side
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t tot = (size_t)(nbox + 1) * TC_MROW;
     if (i >= tot) return;
+    M += (size_t)blockIdx.y * nbox * nc;
+    Ms += (size_t)blockIdx.y * (nbox + 1) * TC_XP * TC_MROW;
     const int b = (int)(i / TC_MROW), k = (int)(i % TC_MROW);
     const float x = (b < nbox && k < nc) ? M[(size_t)b * nc + k] : 0.f;
     const uint32_t hi = to_tf32(x);
@@ -440,10 +446,11 @@ LfErr lf_m2l_tc(lfmm_ctx* ctx, cudaStream_t st)
 {
     if (ctx->m2l_tc_ntiles == 0) return LfErr();
     const int nb = ctx->nbox_total;
-    LF_TRY(lf_reserve(ctx->m2l_Ms, (size_t)(nb + 1) * TC_XP * TC_MROW * sizeof(float)));
+    const int nr = ctx->nrhs_b;
+    LF_TRY(lf_reserve(ctx->m2l_Ms, (size_t)(nb + 1) * TC_XP * TC_MROW * sizeof(float) * nr));
     const size_t tot = (size_t)(nb + 1) * TC_MROW;
-    ++ctx->launches, k_split_m<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(ctx->Mexp.as<float>(), nb,
-                                                                              lf_nc(ctx->p), ctx->m2l_Ms.as<float>());
+    ++ctx->launches, k_split_m<<<dim3((unsigned)((tot + 255) / 256), nr), 256, 0, st>>>(
+        ctx->Mexp.as<float>(), nb, lf_nc(ctx->p), ctx->m2l_Ms.as<float>());
     TcArgs g;
     g.tiles = ctx->m2l_tc_tiles.as<int4>();
     g.sorted = ctx->m2l_sorted.as<int>();
@@ -454,10 +461,12 @@ LfErr lf_m2l_tc(lfmm_ctx* ctx, cudaStream_t st)
     g.Ms = ctx->m2l_Ms.as<float>();
     g.zero_row = nb;
     g.L = ctx->Lexp.as<float>();
+    g.ms_stride = (size_t)(nb + 1) * TC_XP * TC_MROW;
+    g.l_stride = (size_t)nb * lf_nc(ctx->p);
     g.nc = lf_nc(ctx->p);
     g.err = reinterpret_cast<int*>(ctx->counts.as<char>() + LFMM_TIMEOUT_OFF);
     g.groups = ctx->tc_groups;
-    ++ctx->launches, k_m2l_tc<<<ctx->m2l_tc_ntiles * g.groups, TC_THREADS, TC_SMEM, st>>>(g);
+    ++ctx->launches, k_m2l_tc<<<dim3(ctx->m2l_tc_ntiles * g.groups, nr), TC_THREADS, TC_SMEM, st>>>(g);
     return lf_cuda(cudaGetLastError(), "m2l tensor-core gemm");
 }
 

@@ -282,6 +282,7 @@ struct RGemmArgs {
     const double* levelh;
     const void* M;
     void* L;
+    size_t stride;          // expansions per right-hand side (blockIdx.y), in elements
 };
 
 template <typename R>
@@ -372,7 +373,7 @@ __global__ void __launch_bounds__(R_T) k_m2r_gemm(RGemmArgs g)
         sA[idx] = v;
     }
     // gather the sources' multipoles
-    const R* M = reinterpret_cast<const R*>(g.M);
+    const R* M = reinterpret_cast<const R*>(g.M) + (size_t)blockIdx.y * g.stride;
     for (int idx = tid; idx < R_TB * KP; idx += R_T) {
         int j = idx / KP, k = idx - j * KP;
         int s = s_src[j];
@@ -398,7 +399,7 @@ __global__ void __launch_bounds__(R_T) k_m2r_gemm(RGemmArgs g)
             for (int q = 0; q < 4; ++q) acc[r][q] += a[r] * x[q];
     }
     const R ih = (R)(1.0 / g.levelh[lev]);
-    R* L = reinterpret_cast<R*>(g.L);
+    R* L = reinterpret_cast<R*>(g.L) + (size_t)blockIdx.y * g.stride;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         int j = 4 * cg + q;
@@ -420,7 +421,7 @@ static LfErr launch_rgemm(lfmm_ctx* ctx, cudaStream_t st, const RGemmArgs& g)
     const int TS = 2 * ctx->p + 1;
     size_t sm = sizeof(R) * ((size_t)RP * RP + (size_t)R_TB * (RP + 1) + (size_t)TS * TS + 2 * (size_t)TS) + 64;
     LF_CHECK(cudaFuncSetAttribute(k_m2r_gemm<R, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    ++ctx->launches, k_m2r_gemm<R, RM><<<ctx->m2r_nbatch, R_T, sm, st>>>(g);
+    ++ctx->launches, k_m2r_gemm<R, RM><<<dim3(ctx->m2r_nbatch, ctx->nrhs_b), R_T, sm, st>>>(g);
     return lf_cuda(cudaGetLastError(), "m2r gemm");
 }
 
@@ -440,6 +441,7 @@ static LfErr m2r_apply_t(lfmm_ctx* ctx, cudaStream_t st)
     g.levelh = ctx->m2r_levelh.as<double>();
     g.M = ctx->Mexp.ptr;
     g.L = ctx->Lexp.ptr;
+    g.stride = (size_t)ctx->nbox_total * g.nc;
     LF_CHECK(cudaMemcpyToSymbolAsync(c_rcomp, ctx->comp, sizeof(LfmmComp) * ctx->ncomp, 0, cudaMemcpyHostToDevice, st));
     switch (ctx->m2l_rm) {
     case 2: return launch_rgemm<R, 2>(ctx, st, g);

@@ -46,55 +46,89 @@ struct P2PArgs {
     const double* xs;
     const double* ys;
     const double* zs;
-    const void* q;
-    double* phi;
-    double* fld;
+    const void* q;    // charges [nr][qstride]
+    double* phi;      // [nr][qstride]
+    double* fld;      // [nr][qstride][3]
+    int64_t qstride;  // charges per right-hand side (n)
+    int nr;           // right-hand sides of this launch (<= the kernel's batch)
     int Qn;
     LfmmSurrView sv;  // learned near-field kernels (sv.ready = 0: quadrature only)
 };
 
 #define P2P_T 128
 
-// Reaction kernels of one pair by the quadrature, accumulated into the sums.
-template <typename R>
-__device__ __forceinline__ void p2p_reaction_add(const LfmmComp& cp, R dx, R dy, R dz, R qs, int Qn, LfSum<R>& P,
-                                                 LfSum<R>& Ex, LfSum<R>& Ey, LfSum<R>& Ez)
+// Sums of one target over a batch of RB right-hand sides.
+template <typename R, int RB>
+struct P2PAcc {
+    LfSum<R> P[RB], Ex[RB], Ey[RB], Ez[RB];
+};
+
+// Free-space kernel of one pair, applied to the nr charges qs[k * qsk] of the batch.
+template <typename R, int RB>
+__device__ __forceinline__ void p2p_free_add(R dx, R dy, R dz, const R* qs, int qsk, int nr, P2PAcc<R, RB>& A)
+{
+    typedef LfMath<R> F;
+    R r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 > R(0)) {
+        R ir = F::Rsqrt(r2);
+        R ir3 = ir * ir * ir;
+#pragma unroll
+        for (int k = 0; k < RB; ++k) {
+            if (k >= nr) break;
+            const R q = qs[k * qsk];
+            const R q3 = q * ir3;
+            A.P[k].add(q * ir);
+            A.Ex[k].add(q3 * dx);
+            A.Ey[k].add(q3 * dy);
+            A.Ez[k].add(q3 * dz);
+        }
+    }
+}
+
+// Reaction kernels of one pair by the quadrature (once), applied to the batch.
+template <typename R, int RB>
+__device__ __forceinline__ void p2p_reaction_add(const LfmmComp& cp, R dx, R dy, R dz, const R* qs, int qsk, int nr,
+                                                 int Qn, P2PAcc<R, RB>& A)
 {
     typedef LfMath<R> F;
     R h = (cp.a == 1) ? dz : -dz;
     R rho = F::Sqrt(dx * dx + dy * dy);
     R k00, k10, k11;
     lf_reaction_pair<R>(cp, rho, h, Qn, c_gl_t, c_gl_w, k00, k10, k11);
-    P.add(qs * k00);
-    Ez.add((cp.a == 1) ? qs * k10 : -qs * k10);
-    if (rho > R(0)) {
-        R g = qs * k11 / rho;
-        Ex.add(g * dx);
-        Ey.add(g * dy);
+    const R k10s = (cp.a == 1) ? k10 : -k10;
+    const R g = rho > R(0) ? k11 / rho : R(0);
+#pragma unroll
+    for (int k = 0; k < RB; ++k) {
+        if (k >= nr) break;
+        const R q = qs[k * qsk];
+        A.P[k].add(q * k00);
+        A.Ez[k].add(q * k10s);
+        if (rho > R(0)) {
+            A.Ex[k].add(q * g * dx);
+            A.Ey[k].add(q * g * dy);
+        }
     }
 }
 
-template <typename R>
-__device__ __forceinline__ void p2p_free_add(R dx, R dy, R dz, R qs, LfSum<R>& P, LfSum<R>& Ex, LfSum<R>& Ey,
-                                             LfSum<R>& Ez)
+template <typename R, int RB>
+__device__ __forceinline__ void p2p_store(const P2PArgs& a, int i, const P2PAcc<R, RB>& A)
 {
-    typedef LfMath<R> F;
-    R r2 = dx * dx + dy * dy + dz * dz;
-    if (r2 > R(0)) {
-        R ir = F::Rsqrt(r2);
-        R qi = qs * ir;
-        R q3 = qi * ir * ir;
-        P.add(qi);
-        Ex.add(q3 * dx);
-        Ey.add(q3 * dy);
-        Ez.add(q3 * dz);
+#pragma unroll
+    for (int k = 0; k < RB; ++k) {
+        if (k >= a.nr) break;
+        const size_t o = (size_t)k * a.qstride + i;
+        a.phi[o] = (double)A.P[k].s;
+        a.fld[3 * o + 0] = (double)A.Ex[k].s;
+        a.fld[3 * o + 1] = (double)A.Ey[k].s;
+        a.fld[3 * o + 2] = (double)A.Ez[k].s;
     }
 }
 
-template <typename R>
+// One block per target leaf (FP64 form), a batch of RB right-hand sides.
+template <typename R, int RB>
 __global__ void __launch_bounds__(P2P_T) k_p2p(P2PArgs a)
 {
-    __shared__ R sx[P2P_T], sy[P2P_T], sz[P2P_T], sq[P2P_T];
+    __shared__ R sx[P2P_T], sy[P2P_T], sz[P2P_T], sq[RB][P2P_T];
     const R* q = reinterpret_cast<const R*>(a.q);
     const int t = a.leaf_off + blockIdx.x;
     const int tid = threadIdx.x;
@@ -109,7 +143,7 @@ __global__ void __launch_bounds__(P2P_T) k_p2p(P2PArgs a)
             yi = (R)(a.ys[i] - ct.y);
             zi = (R)(a.zs[i] - ct.z);
         }
-        LfSum<R> P, Ex, Ey, Ez;
+        P2PAcc<R, RB> A;
         for (int e = a.nbeg[t]; e < a.nend[t]; ++e) {
             const uint32_t ent = a.nent[e];
             const int c = (int)(ent >> LFMM_ENT_SHIFT);
@@ -124,25 +158,24 @@ __global__ void __launch_bounds__(P2P_T) k_p2p(P2PArgs a)
                     sy[tid] = (R)(a.ys[j] - ct.y);
                     double zj = cp.is_free ? a.zs[j] : cp.s * a.zs[j] + cp.o;
                     sz[tid] = (R)(zj - ct.z);
-                    sq[tid] = q[j];
+#pragma unroll
+                    for (int k = 0; k < RB; ++k)
+                        if (k < a.nr) sq[k][tid] = q[(size_t)k * a.qstride + j];
                 }
                 __syncthreads();
                 if (!valid) continue;
                 const int cnt = min(P2P_T, se - cb);
                 if (cp.is_free) {
-                    for (int u = 0; u < cnt; ++u) p2p_free_add<R>(xi - sx[u], yi - sy[u], zi - sz[u], sq[u], P, Ex, Ey, Ez);
+                    for (int u = 0; u < cnt; ++u)
+                        p2p_free_add<R, RB>(xi - sx[u], yi - sy[u], zi - sz[u], &sq[0][u], P2P_T, a.nr, A);
                 } else {
                     for (int u = 0; u < cnt; ++u)
-                        p2p_reaction_add<R>(cp, xi - sx[u], yi - sy[u], zi - sz[u], sq[u], a.Qn, P, Ex, Ey, Ez);
+                        p2p_reaction_add<R, RB>(cp, xi - sx[u], yi - sy[u], zi - sz[u], &sq[0][u], P2P_T, a.nr,
+                                                a.Qn, A);
                 }
             }
         }
-        if (valid) {
-            a.phi[i] = (double)P.s;
-            a.fld[3 * (size_t)i + 0] = (double)Ex.s;
-            a.fld[3 * (size_t)i + 1] = (double)Ey.s;
-            a.fld[3 * (size_t)i + 2] = (double)Ez.s;
-        }
+        if (valid) p2p_store<R, RB>(a, i, A);
     }
 }
 
@@ -166,9 +199,10 @@ __global__ void k_rel_pos(int leaf_off, int nleaf, const LfD4* __restrict__ cen,
         rel[i] = make_float4((float)(xs[i] - c.x), (float)(ys[i] - c.y), (float)(zs[i] - c.z), 0.f);
 }
 
+template <int RB>
 __global__ void __launch_bounds__(32 * PW_WARPS) k_p2p_warp(P2PArgs a, const float4* __restrict__ rel, int nleaf)
 {
-    __shared__ float sx[PW_WARPS][32], sy[PW_WARPS][32], sz[PW_WARPS][32], sq[PW_WARPS][32];
+    __shared__ float sx[PW_WARPS][32], sy[PW_WARPS][32], sz[PW_WARPS][32], sq[PW_WARPS][RB][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int li = blockIdx.x * PW_WARPS + w;
     if (li >= nleaf) return;  // whole warp
@@ -187,7 +221,7 @@ __global__ void __launch_bounds__(32 * PW_WARPS) k_p2p_warp(P2PArgs a, const flo
             yi = r.y;
             zi = r.z;
         }
-        LfSum<float> P, Ex, Ey, Ez;
+        P2PAcc<float, RB> A;
         for (int e = eb; e < ee; ++e) {
             const uint32_t ent = a.nent[e];
             const int c = (int)(ent >> LFMM_ENT_SHIFT);
@@ -207,27 +241,25 @@ __global__ void __launch_bounds__(32 * PW_WARPS) k_p2p_warp(P2PArgs a, const flo
                     sx[w][lane] = r.x + dx0;
                     sy[w][lane] = r.y + dy0;
                     sz[w][lane] = szs * r.z + dz0;
-                    sq[w][lane] = q[j];
+#pragma unroll
+                    for (int k = 0; k < RB; ++k)
+                        if (k < a.nr) sq[w][k][lane] = q[(size_t)k * a.qstride + j];
                 }
                 __syncwarp();
                 if (!valid) continue;
                 const int cnt = min(32, se - cb);
                 if (cp.is_free) {
                     for (int u = 0; u < cnt; ++u)
-                        p2p_free_add<float>(xi - sx[w][u], yi - sy[w][u], zi - sz[w][u], sq[w][u], P, Ex, Ey, Ez);
+                        p2p_free_add<float, RB>(xi - sx[w][u], yi - sy[w][u], zi - sz[w][u], &sq[w][0][u], 32, a.nr,
+                                                A);
                 } else {
                     for (int u = 0; u < cnt; ++u)
-                        p2p_reaction_add<float>(cp, xi - sx[w][u], yi - sy[w][u], zi - sz[w][u], sq[w][u], a.Qn, P, Ex,
-                                                Ey, Ez);
+                        p2p_reaction_add<float, RB>(cp, xi - sx[w][u], yi - sy[w][u], zi - sz[w][u], &sq[w][0][u],
+                                                    32, a.nr, a.Qn, A);
                 }
             }
         }
-        if (valid) {
-            a.phi[i] = (double)P.s;
-            a.fld[3 * (size_t)i + 0] = (double)Ex.s;
-            a.fld[3 * (size_t)i + 1] = (double)Ey.s;
-            a.fld[3 * (size_t)i + 2] = (double)Ez.s;
-        }
+        if (valid) p2p_store<float, RB>(a, i, A);
     }
 }
 
@@ -305,7 +337,8 @@ __global__ void __launch_bounds__(P2P_T) k_p2p_net(P2PArgs a)
         tz[tid] = zi;
         acc[tid][0] = acc[tid][1] = acc[tid][2] = acc[tid][3] = R(0);
         __syncwarp();
-        LfSum<R> P, Ex, Ey, Ez;
+        P2PAcc<R, 1> A;
+        LfSum<R>&P = A.P[0], &Ex = A.Ex[0], &Ey = A.Ey[0], &Ez = A.Ez[0];
         for (int e = a.nbeg[t]; e < a.nend[t]; ++e) {
             const uint32_t ent = a.nent[e];
             const int c = (int)(ent >> LFMM_ENT_SHIFT);
@@ -342,10 +375,10 @@ __global__ void __launch_bounds__(P2P_T) k_p2p_net(P2PArgs a)
                     if (!valid) continue;
                     if (cp.is_free) {
                         for (int u = 0; u < cnt; ++u)
-                            p2p_free_add<R>(xi - sx[u], yi - sy[u], zi - sz[u], sq[u], P, Ex, Ey, Ez);
+                            p2p_free_add<R, 1>(xi - sx[u], yi - sy[u], zi - sz[u], &sq[u], 0, 1, A);
                     } else {
                         for (int u = 0; u < cnt; ++u)
-                            p2p_reaction_add<R>(cp, xi - sx[u], yi - sy[u], zi - sz[u], sq[u], a.Qn, P, Ex, Ey, Ez);
+                            p2p_reaction_add<R, 1>(cp, xi - sx[u], yi - sy[u], zi - sz[u], &sq[u], 0, 1, a.Qn, A);
                         n_quad += cnt;
                     }
                     continue;
@@ -448,23 +481,51 @@ LfErr lf_near_field(lfmm_ctx* ctx, cudaStream_t st)
     LF_TRY(lf_reserve(ctx->surr_counters, 64));
     LF_CHECK(cudaMemsetAsync(ctx->surr_counters.ptr, 0, 16, st));
     LF_TRY(lf_surrogate_device_view(ctx, &a.sv));
+    a.qstride = ctx->n;
+    const int nr = ctx->nrhs_b;
+    const size_t qs = (ctx->precision ? sizeof(float) : sizeof(double)) * (size_t)ctx->n;
     const int ph = lf_prof_start(ctx, LFMM_TIME_P2P, st);
     // the network variant only where the near field holds reaction pairs (it
-    // needs far more registers, which slows the free-space part)
+    // needs far more registers, which slows the free-space part); one launch
+    // per right-hand side.  The quadrature kernels take batches of up to 8.
     const bool net = a.sv.ready != 0 && ctx->stats[LFMM_STAT_P2P_REACTION] > 0;
-    if (ctx->precision) {
-        if (net)
-            ++ctx->launches, k_p2p_net<float><<<leaf.nbox, P2P_T, 0, st>>>(a);
-        else
-            ++ctx->launches, k_p2p_warp<<<lf_blocks(leaf.nbox, PW_WARPS), 32 * PW_WARPS, 0, st>>>(
-                a, ctx->pos_rel.as<float4>(), leaf.nbox);
-    } else {
-        if (net)
-            ++ctx->launches, k_p2p_net<double><<<leaf.nbox, P2P_T, 0, st>>>(a);
-        else
-            ++ctx->launches, k_p2p<double><<<leaf.nbox, P2P_T, 0, st>>>(a);
+    const double* phi0 = a.phi;
+    double* fld0 = a.fld;
+    const char* q0 = reinterpret_cast<const char*>(a.q);
+    const int step = net ? 1 : 8;
+    for (int r0 = 0; r0 < nr; r0 += step) {
+        a.nr = nr - r0 < step ? nr - r0 : step;
+        a.q = q0 + (size_t)r0 * qs;
+        a.phi = const_cast<double*>(phi0) + (size_t)r0 * ctx->n;
+        a.fld = fld0 + (size_t)r0 * ctx->n * 3;
+        if (net) {
+            if (ctx->precision)
+                ++ctx->launches, k_p2p_net<float><<<leaf.nbox, P2P_T, 0, st>>>(a);
+            else
+                ++ctx->launches, k_p2p_net<double><<<leaf.nbox, P2P_T, 0, st>>>(a);
+        } else if (ctx->precision) {
+            const int g = lf_blocks(leaf.nbox, PW_WARPS), T = 32 * PW_WARPS;
+            const float4* rel = ctx->pos_rel.as<float4>();
+            if (a.nr == 1)
+                ++ctx->launches, k_p2p_warp<1><<<g, T, 0, st>>>(a, rel, leaf.nbox);
+            else if (a.nr == 2)
+                ++ctx->launches, k_p2p_warp<2><<<g, T, 0, st>>>(a, rel, leaf.nbox);
+            else if (a.nr <= 4)
+                ++ctx->launches, k_p2p_warp<4><<<g, T, 0, st>>>(a, rel, leaf.nbox);
+            else
+                ++ctx->launches, k_p2p_warp<8><<<g, T, 0, st>>>(a, rel, leaf.nbox);
+        } else {
+            if (a.nr == 1)
+                ++ctx->launches, k_p2p<double, 1><<<leaf.nbox, P2P_T, 0, st>>>(a);
+            else if (a.nr == 2)
+                ++ctx->launches, k_p2p<double, 2><<<leaf.nbox, P2P_T, 0, st>>>(a);
+            else if (a.nr <= 4)
+                ++ctx->launches, k_p2p<double, 4><<<leaf.nbox, P2P_T, 0, st>>>(a);
+            else
+                ++ctx->launches, k_p2p<double, 8><<<leaf.nbox, P2P_T, 0, st>>>(a);
+        }
+        LF_TRY(lf_cuda(cudaGetLastError(), "p2p"));
     }
-    LF_TRY(lf_cuda(cudaGetLastError(), "p2p"));
     lf_prof_stop(ctx, ph, st);
     return LfErr();
 }
