@@ -79,6 +79,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 leg")
     ap.add_argument("--sample", type=int, default=256, help="oracle targets for the accuracy / CPU leg")
     ap.add_argument("--no-near", action="store_true", help="skip the near-interface workload")
+    ap.add_argument("--no-multi", action="store_true", help="skip the many-charge-vector workload")
     ap.add_argument("--forms", default="fp32_surrogate,fp32,fp64",
                     help="comma list of fp32_surrogate, fp32, fp64; the first is the headline")
     return ap.parse_args()
@@ -249,6 +250,41 @@ def near_interface_leg(torch, dev, p, flush):
     return out
 
 
+def multi_rhs_leg(torch, dev, p, flush, nrhs=64, n=1 << 18):
+    """Float32 form, one tree, nrhs charge vectors: one batched call against
+    nrhs single calls (device buffers, CUDA events)."""
+    from paper_1908_10863_gb300 import LayeredFMM, workloads
+    w = workloads.config2(n)
+    Q = np.random.default_rng(workloads.SEED_BASE + 5).uniform(-1.0, 1.0, (nrhs, w.n))
+    q_d = torch.from_numpy(Q).to(dev)
+    phi_d = torch.empty_like(q_d)
+    fld_d = torch.empty((nrhs, w.n, 3), dtype=torch.float64, device=dev)
+    f = LayeredFMM(w.d, w.eps, p, precision=1)
+    xyz_d = torch.from_numpy(w.xyz).to(dev)
+    lay_d = torch.from_numpy(w.layer).to(dev)
+    s = torch.cuda.current_stream()
+    f.build_device(xyz_d, lay_d, s)
+
+    def timed(fn):
+        fn()  # warm-up
+        flush.fill_(1.0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        fn()
+        b.record(s)
+        b.synchronize()
+        return a.elapsed_time(b)
+
+    t_batch = timed(lambda: f.evaluate_device(q_d, phi_d, fld_d, s))
+    t_single = timed(lambda: [f.evaluate_device(q_d[r], phi_d[r], fld_d[r], s) for r in range(nrhs)])
+    f.close()
+    return {"workload": "three-layer medium, N=%d charges split between layers, %d charge vectors q~U[-1,1], "
+                        "p=%d, float32 form, one tree" % (w.n, nrhs, p),
+            "batched_ms": t_batch, "one_at_a_time_ms": t_single,
+            "charges_x_vectors_per_s": w.n * nrhs / (t_batch / 1e3), "speedup": t_single / t_batch}
+
+
 def main():
     args = parse()
     world, rank, local, pg = dist_setup(args)
@@ -338,6 +374,9 @@ def main():
     near = None
     if not args.no_near and rank == 0:
         near = near_interface_leg(torch, dev, args.p, flush)
+    multi = None
+    if not args.no_multi and rank == 0:
+        multi = multi_rhs_leg(torch, dev, args.p, flush)
 
     ms_max = allmax(pg, results[headline]["ms_per_step"])
     e2e_max = allmax(pg, results[headline]["e2e_s"])
@@ -409,6 +448,7 @@ def main():
         "gpu_launches": results[headline]["launches"],
         "clocks": clk,
         "near_interface": near,
+        "multi_rhs": multi,
     }
     print(json.dumps(line))
     barrier(pg)

@@ -250,31 +250,6 @@ LfErr lf_setup_m2l_ops(lfmm_ctx* ctx)
 // ---------------------------------------------------------------------------
 // Build: slot table and tiles.
 // ---------------------------------------------------------------------------
-__global__ void k_fill_slots(int off, int nb, const uint32_t* __restrict__ bkey, const int4* __restrict__ grid,
-                             const int* __restrict__ mbeg, const int* __restrict__ mend,
-                             const uint32_t* __restrict__ ment, const int* __restrict__ inv, int* __restrict__ slots,
-                             int* __restrict__ err)
-{
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nb) return;
-    int t = off + i;
-    int c = (int)(bkey[t] & 7u);
-    const int4 gt = grid[t];
-    for (int e = mbeg[t]; e < mend[t]; ++e) {
-        int s = (int)(ment[e] & LFMM_ENT_MASK);
-        const int4 gs = grid[s];
-        const int ox = gt.x - gs.x, oy = gt.y - gs.y, oz = gt.z - gs.z;
-        int loc = -1;
-        if (ox >= -3 && ox <= 3 && oy >= -3 && oy <= 3 && oz >= -3 && oz <= 3)
-            loc = inv[c * G_NALL + (ox + 3) * 49 + (oy + 3) * 7 + (oz + 3)];
-        if (loc < 0) {
-            atomicAdd(err, 1);
-            continue;
-        }
-        slots[(size_t)t * G_NOFF + loc] = s;
-    }
-}
-
 __global__ void k_child_slots(int off, int nb, const uint32_t* __restrict__ bkey, const int* __restrict__ parent,
                               int* __restrict__ slots)
 {
@@ -304,11 +279,10 @@ LfErr lf_prepare_m2l(lfmm_ctx* ctx, cudaStream_t st)
     const int depth = ctx->depth;
     if (depth < 2) return LfErr();
     const size_t nb = (size_t)ctx->nbox_total;
-    LF_TRY(lf_reserve(ctx->m2l_slots, nb * G_NOFF * sizeof(int)));
-    LF_CHECK(cudaMemsetAsync(ctx->m2l_slots.ptr, 0xff, nb * G_NOFF * sizeof(int), st));
+    // the slot table was filled with the lists; errors counted at `err`
     int* err = reinterpret_cast<int*>(ctx->counts.as<char>() + 24576);
     int* cnt = err + 16;  // [16 levels][8]
-    LF_CHECK(cudaMemsetAsync(err, 0, sizeof(int) * (16 + 16 * 8), st));
+    LF_CHECK(cudaMemsetAsync(cnt, 0, sizeof(int) * 16 * 8, st));
     int nsort = 0;
     for (int l = 1; l <= depth; ++l) nsort += ctx->levels[l].nbox;
     LF_TRY(lf_reserve(ctx->m2l_keys, (size_t)nsort * 4 + 16));
@@ -317,11 +291,6 @@ LfErr lf_prepare_m2l(lfmm_ctx* ctx, cudaStream_t st)
     for (int l = 1; l <= depth; ++l) {
         const LfmmLevel& lv = ctx->levels[l];
         if (lv.nbox == 0) continue;
-        if (l >= 2)
-            ++ctx->launches, k_fill_slots<<<lf_blocks(lv.nbox, 128), 128, 0, st>>>(
-                lv.off, lv.nbox, ctx->box_key.as<uint32_t>(), ctx->box_grid.as<int4>(), ctx->m2l_off.as<int>(),
-                ctx->m2l_off.as<int>() + ctx->nbox_total, ctx->m2l_ent.as<uint32_t>(), ctx->m2l_inv.as<int>(),
-                ctx->m2l_slots.as<int>(), err);
         ++ctx->launches, k_class_keys<<<lf_blocks(lv.nbox, 256), 256, 0, st>>>(
             lv.off, lv.nbox, l, ctx->box_key.as<uint32_t>(), ctx->m2l_keys.as<uint32_t>(),
             ctx->m2l_sorted.as<uint32_t>(), base, cnt);

@@ -437,9 +437,12 @@ __global__ void k_list_pass(int level_off, int nb, int level, const int* __restr
                             const int* __restrict__ pnear_end, const uint32_t* __restrict__ near_ent_in,
                             int* __restrict__ cnt, const int* __restrict__ off, uint32_t* __restrict__ m2l_out,
                             uint32_t* __restrict__ m2r_out, uint32_t* __restrict__ near_out, int fill,
-                            unsigned long long* __restrict__ stat)
+                            unsigned long long* __restrict__ stat, const uint32_t* __restrict__ bkey,
+                            const int* __restrict__ inv, int* __restrict__ slots, int* __restrict__ slot_err)
 {
-    // cnt / off: [3][nb] = free M2L, reaction M2L, near
+    // cnt / off: [3][nb] = free M2L, reaction M2L, near.  With `slots`, the fill
+    // pass also records each free M2L source at its position in the target's
+    // octant-class offset list (slots[t][189], inv[class][343]: position or -1).
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nb) return;
     int t = level_off + i;
@@ -457,7 +460,20 @@ __global__ void k_list_pass(int level_off, int nb, int level, const int* __restr
             uint32_t v = ((uint32_t)c << LFMM_ENT_SHIFT) | (uint32_t)sc;
             if (lf_admissible(cp, k, gt, grid[sc])) {
                 if (cp.is_free) {
-                    if (fill) m2l_out[wf++] = v;
+                    if (fill) {
+                        m2l_out[wf++] = v;
+                        if (slots) {
+                            const int4 gs = grid[sc];
+                            const int ox = gt.x - gs.x, oy = gt.y - gs.y, oz = gt.z - gs.z;
+                            int loc = -1;
+                            if (ox >= -3 && ox <= 3 && oy >= -3 && oy <= 3 && oz >= -3 && oz <= 3)
+                                loc = inv[(int)(bkey[t] & 7u) * 343 + (ox + 3) * 49 + (oy + 3) * 7 + (oz + 3)];
+                            if (loc < 0)
+                                atomicAdd(slot_err, 1);
+                            else
+                                slots[(size_t)t * 189 + loc] = sc;
+                        }
+                    }
                     ++nf;
                 } else {
                     if (fill) m2r_out[wr++] = v;
@@ -814,32 +830,49 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
     LF_TRY(lf_reserve(ctx->hist, (size_t)maxnb * 4 * 6 + 64));
     int* cnt3 = ctx->hist.as<int>();
     int* off3 = cnt3 + 3 * maxnb;
+    // free M2L slot table [box][189] (for the gathered GEMMs), filled with the lists
+    int* slot_err = reinterpret_cast<int*>(ctx->counts.as<char>() + 24576);
+    LF_CHECK(cudaMemsetAsync(slot_err, 0, sizeof(int), st));
+    const bool want_slots = ctx->m2l_rm > 0 && depth >= 2;
+    if (want_slots) {
+        LF_TRY(lf_reserve(ctx->m2l_slots, (size_t)nb * 189 * sizeof(int)));
+        LF_CHECK(cudaMemsetAsync(ctx->m2l_slots.ptr, 0xff, (size_t)nb * 189 * sizeof(int), st));
+    }
+    int hb[4];
     for (int l = 1; l <= depth; ++l) {
         LfmmLevel& lv = ctx->levels[l];
         const int n3 = lv.nbox;
-        ++ctx->launches, k_list_pass<<<lf_blocks(n3, 128), 128, 0, st>>>(lv.off, n3, l, par, cbeg, cend, ctx->box_grid.as<int4>(),
-                                                        nbeg, nend, ctx->near_ent.as<uint32_t>(), cnt3, nullptr,
-                                                        nullptr, nullptr, nullptr, 0, nullptr);
+        ++ctx->launches, k_list_pass<<<lf_blocks(n3, 128), 128, 0, st>>>(
+            lv.off, n3, l, par, cbeg, cend, ctx->box_grid.as<int4>(), nbeg, nend, ctx->near_ent.as<uint32_t>(), cnt3,
+            nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, nullptr);
         LF_TRY(lf_cuda(cudaGetLastError(), "list count"));
-        int64_t tf = 0, tr = 0, tn = 0;
-        LF_TRY(lf_scan_i32(ctx, cnt3, off3, n3, &tf, st));
-        LF_TRY(lf_scan_i32(ctx, cnt3 + n3, off3 + n3, n3, &tr, st));
-        LF_TRY(lf_scan_i32(ctx, cnt3 + 2 * n3, off3 + 2 * n3, n3, &tn, st));
+        // one exclusive scan over the three count arrays; the category bases
+        // and the grand total come back with one synchronisation
+        LF_TRY(lf_scan_i32(ctx, cnt3, off3, 3 * (int64_t)n3, nullptr, st));
+        LF_CHECK(cudaMemcpyAsync(&hb[0], off3 + n3, sizeof(int), cudaMemcpyDeviceToHost, st));
+        LF_CHECK(cudaMemcpyAsync(&hb[1], off3 + 2 * n3, sizeof(int), cudaMemcpyDeviceToHost, st));
+        LF_CHECK(cudaMemcpyAsync(&hb[2], off3 + 3 * n3 - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+        LF_CHECK(cudaMemcpyAsync(&hb[3], cnt3 + 3 * n3 - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+        LF_CHECK(cudaStreamSynchronize(st));
+        const int64_t b1 = hb[0], b2 = hb[1];
+        const int64_t tf = b1, tr = b2 - b1, tn = (int64_t)hb[2] + hb[3] - b2;
         if (near_used + tn > 0x7fffffffLL || m2l_used + tf > 0x7fffffffLL || m2r_used + tr > 0x7fffffffLL)
             return "interaction lists too long";
         LF_TRY(grow_keep(ctx->near_ent, (size_t)(near_used + tn + 1) * 4, (size_t)near_used * 4, st));
         LF_TRY(grow_keep(ctx->m2l_ent, (size_t)(m2l_used + tf + 1) * 4, (size_t)m2l_used * 4, st));
         LF_TRY(grow_keep(ctx->m2r_ent, (size_t)(m2r_used + tr + 1) * 4, (size_t)m2r_used * 4, st));
         uint32_t* nent = ctx->near_ent.as<uint32_t>();
-        // per-level offsets are relative: shift the output pointers
+        // offsets are relative to the concatenated scan: shift the output pointers by each category's base
         ++ctx->launches, k_list_pass<<<lf_blocks(n3, 128), 128, 0, st>>>(
             lv.off, n3, l, par, cbeg, cend, ctx->box_grid.as<int4>(), nbeg, nend, nent, cnt3, off3,
-            ctx->m2l_ent.as<uint32_t>() + m2l_used, ctx->m2r_ent.as<uint32_t>() + m2r_used, nent + near_used, 1,
-            stat);
+            ctx->m2l_ent.as<uint32_t>() + m2l_used, ctx->m2r_ent.as<uint32_t>() + m2r_used - b1,
+            nent + near_used - b2, 1, stat, ctx->box_key.as<uint32_t>(), ctx->m2l_inv.as<int>(),
+            (want_slots && l >= 2) ? ctx->m2l_slots.as<int>() : nullptr, slot_err);
         ++ctx->launches, k_set_ranges<<<lf_blocks(n3, 256), 256, 0, st>>>(lv.off, n3, off3, cnt3, (int)m2l_used, mbeg, mend);
-        ++ctx->launches, k_set_ranges<<<lf_blocks(n3, 256), 256, 0, st>>>(lv.off, n3, off3 + n3, cnt3 + n3, (int)m2r_used, rbeg, rend);
-        ++ctx->launches, k_set_ranges<<<lf_blocks(n3, 256), 256, 0, st>>>(lv.off, n3, off3 + 2 * n3, cnt3 + 2 * n3, (int)near_used,
-                                                          nbeg, nend);
+        ++ctx->launches, k_set_ranges<<<lf_blocks(n3, 256), 256, 0, st>>>(lv.off, n3, off3 + n3, cnt3 + n3,
+                                                                           (int)(m2r_used - b1), rbeg, rend);
+        ++ctx->launches, k_set_ranges<<<lf_blocks(n3, 256), 256, 0, st>>>(lv.off, n3, off3 + 2 * n3, cnt3 + 2 * n3,
+                                                                           (int)(near_used - b2), nbeg, nend);
         LF_TRY(lf_cuda(cudaGetLastError(), "list fill"));
         lv.near_base = near_used;
         lv.near_count = tn;
