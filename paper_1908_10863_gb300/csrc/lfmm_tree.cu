@@ -431,6 +431,10 @@ __device__ __forceinline__ bool lf_admissible(const LfmmComp& c, float4 k, int4 
     return true;
 }
 
+// One warp per target box.  The candidates (children of the parent's near
+// entries) are taken 32 at a time as 4 entries x 8 child slots; admissible
+// ones are counted (count pass) or written in candidate order through a
+// ballot prefix (fill pass), so the lists are deterministic.
 __global__ void k_list_pass(int level_off, int nb, int level, const int* __restrict__ parent,
                             const int* __restrict__ cbeg, const int* __restrict__ cend,
                             const int4* __restrict__ grid, const int* __restrict__ pnear_beg,
@@ -443,55 +447,78 @@ __global__ void k_list_pass(int level_off, int nb, int level, const int* __restr
     // cnt / off: [3][nb] = free M2L, reaction M2L, near.  With `slots`, the fill
     // pass also records each free M2L source at its position in the target's
     // octant-class offset list (slots[t][189], inv[class][343]: position or -1).
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nb) return;
-    int t = level_off + i;
-    int pt = parent[t];
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= nb) return;  // whole warp
+    const int t = level_off + i;
+    const int pt = parent[t];
     const int4 gt = grid[t];
-    int nf = 0, nr = 0, nn = 0;
-    int wf = fill ? off[i] : 0, wr = fill ? off[nb + i] : 0, wn = fill ? off[2 * nb + i] : 0;
-    for (int e = pnear_beg[pt]; e < pnear_end[pt]; ++e) {
-        uint32_t ent = near_ent_in[e];
-        int c = (int)(ent >> LFMM_ENT_SHIFT);
-        int s = (int)(ent & LFMM_ENT_MASK);
-        const LfmmComp& cp = c_tree_comp[c];
-        const float4 k = c_tree_lc[c * 16 + level];
-        for (int sc = cbeg[s]; sc < cend[s]; ++sc) {
-            uint32_t v = ((uint32_t)c << LFMM_ENT_SHIFT) | (uint32_t)sc;
-            if (lf_admissible(cp, k, gt, grid[sc])) {
-                if (cp.is_free) {
-                    if (fill) {
-                        m2l_out[wf++] = v;
-                        if (slots) {
-                            const int4 gs = grid[sc];
-                            const int ox = gt.x - gs.x, oy = gt.y - gs.y, oz = gt.z - gs.z;
-                            int loc = -1;
-                            if (ox >= -3 && ox <= 3 && oy >= -3 && oy <= 3 && oz >= -3 && oz <= 3)
-                                loc = inv[(int)(bkey[t] & 7u) * 343 + (ox + 3) * 49 + (oy + 3) * 7 + (oz + 3)];
-                            if (loc < 0)
-                                atomicAdd(slot_err, 1);
-                            else
-                                slots[(size_t)t * 189 + loc] = sc;
-                        }
-                    }
-                    ++nf;
-                } else {
-                    if (fill) m2r_out[wr++] = v;
-                    ++nr;
-                }
-            } else {
-                if (fill) near_out[wn++] = v;
-                ++nn;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    int nf = 0, nr = 0, nn = 0;  // warp-uniform running counts
+    int wf = 0, wr = 0, wn = 0;
+    if (fill) {
+        wf = off[i];
+        wr = off[nb + i];
+        wn = off[2 * nb + i];
+    }
+    const int cls = slots ? (int)(bkey[t] & 7u) : 0;
+    const int eb = pnear_beg[pt], ee = pnear_end[pt];
+    for (int e0 = eb; e0 < ee; e0 += 4) {
+        const int e = e0 + (lane >> 3), k = lane & 7;
+        int kind = -1;  // 0 free M2L, 1 reaction M2L, 2 near
+        uint32_t v = 0;
+        int sc = -1;
+        if (e < ee) {
+            const uint32_t ent = near_ent_in[e];
+            const int c = (int)(ent >> LFMM_ENT_SHIFT);
+            const int s = (int)(ent & LFMM_ENT_MASK);
+            const int ch = cbeg[s] + k;
+            if (ch < cend[s]) {
+                sc = ch;
+                const LfmmComp& cp = c_tree_comp[c];
+                v = ((uint32_t)c << LFMM_ENT_SHIFT) | (uint32_t)sc;
+                if (lf_admissible(cp, c_tree_lc[c * 16 + level], gt, grid[sc]))
+                    kind = cp.is_free ? 0 : 1;
+                else
+                    kind = 2;
             }
         }
+        const unsigned bf = __ballot_sync(0xffffffffu, kind == 0);
+        const unsigned br = __ballot_sync(0xffffffffu, kind == 1);
+        const unsigned bn = __ballot_sync(0xffffffffu, kind == 2);
+        if (fill) {
+            if (kind == 0) {
+                m2l_out[wf + nf + __popc(bf & lt_mask)] = v;
+                if (slots) {
+                    const int4 gs = grid[sc];
+                    const int ox = gt.x - gs.x, oy = gt.y - gs.y, oz = gt.z - gs.z;
+                    int loc = -1;
+                    if (ox >= -3 && ox <= 3 && oy >= -3 && oy <= 3 && oz >= -3 && oz <= 3)
+                        loc = inv[cls * 343 + (ox + 3) * 49 + (oy + 3) * 7 + (oz + 3)];
+                    if (loc < 0)
+                        atomicAdd(slot_err, 1);
+                    else
+                        slots[(size_t)t * 189 + loc] = sc;
+                }
+            } else if (kind == 1) {
+                m2r_out[wr + nr + __popc(br & lt_mask)] = v;
+            } else if (kind == 2) {
+                near_out[wn + nn + __popc(bn & lt_mask)] = v;
+            }
+        }
+        nf += __popc(bf);
+        nr += __popc(br);
+        nn += __popc(bn);
     }
-    if (!fill) {
-        cnt[i] = nf;
-        cnt[nb + i] = nr;
-        cnt[2 * nb + i] = nn;
-    } else if (stat) {
-        if (nf) atomicAdd(&stat[0], (unsigned long long)nf);
-        if (nr) atomicAdd(&stat[1], (unsigned long long)nr);
+    if (lane == 0) {
+        if (!fill) {
+            cnt[i] = nf;
+            cnt[nb + i] = nr;
+            cnt[2 * nb + i] = nn;
+        } else if (stat) {
+            if (nf) atomicAdd(&stat[0], (unsigned long long)nf);
+            if (nr) atomicAdd(&stat[1], (unsigned long long)nr);
+        }
     }
 }
 
@@ -842,7 +869,7 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
     for (int l = 1; l <= depth; ++l) {
         LfmmLevel& lv = ctx->levels[l];
         const int n3 = lv.nbox;
-        ++ctx->launches, k_list_pass<<<lf_blocks(n3, 128), 128, 0, st>>>(
+        ++ctx->launches, k_list_pass<<<lf_blocks(n3, 4), 128, 0, st>>>(
             lv.off, n3, l, par, cbeg, cend, ctx->box_grid.as<int4>(), nbeg, nend, ctx->near_ent.as<uint32_t>(), cnt3,
             nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, nullptr);
         LF_TRY(lf_cuda(cudaGetLastError(), "list count"));
@@ -863,7 +890,7 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
         LF_TRY(grow_keep(ctx->m2r_ent, (size_t)(m2r_used + tr + 1) * 4, (size_t)m2r_used * 4, st));
         uint32_t* nent = ctx->near_ent.as<uint32_t>();
         // offsets are relative to the concatenated scan: shift the output pointers by each category's base
-        ++ctx->launches, k_list_pass<<<lf_blocks(n3, 128), 128, 0, st>>>(
+        ++ctx->launches, k_list_pass<<<lf_blocks(n3, 4), 128, 0, st>>>(
             lv.off, n3, l, par, cbeg, cend, ctx->box_grid.as<int4>(), nbeg, nend, nent, cnt3, off3,
             ctx->m2l_ent.as<uint32_t>() + m2l_used, ctx->m2r_ent.as<uint32_t>() + m2r_used - b1,
             nent + near_used - b2, 1, stat, ctx->box_key.as<uint32_t>(), ctx->m2l_inv.as<int>(),
