@@ -111,10 +111,15 @@ struct lfmm_ctx {
     DevBuf m2m_A64, m2m_A32, l2l_A64, l2l_A32, shift_cls, m2m_slots, shift_tiles;
     std::vector<int> m2m_first, l2l_first;  // first tile of each level
     int l2l_tile_base = 0, shift_ready = 0;
+    std::vector<int4> m2l_tiles_h, l2l_tiles_h, m2m_tiles_h, tc_tiles_h;  // host staging of asynchronous uploads
+    double m2l_levelh_h[16] = {0};
     int m2l_tc_ok = 0, m2l_tc_ntiles = 0, use_tc = 1, tc_groups = 27;
     // reaction M2L grouped by geometry key on interface-aligned levels
     DevBuf m2r_keys, m2r_order, m2r_tgt, m2r_kstart, m2r_kval, m2r_tables, m2r_levelh, m2r_batches;
     DevBuf m2r_tdesc, m2r_ktab;  // table descriptors (component, level, rho^2, oz); table of each key
+    std::vector<int4> m2r_tdesc_h, m2r_batches_h;  // host staging of asynchronous uploads
+    std::vector<int> m2r_ktab_h;
+    double m2r_levelh_h[16] = {0};
     int m2r_nkeys = 0, m2r_nbatch = 0, m2r_keyed_from = 0, m2r_ntab = 0;
 
     // learned surrogate of the near-field reaction kernels
@@ -164,7 +169,8 @@ LfErr lf_m2l_gemm(lfmm_ctx* ctx, cudaStream_t st);
 LfErr lf_prepare_m2r(lfmm_ctx* ctx, cudaStream_t st);
 LfErr lf_m2r_apply(lfmm_ctx* ctx, cudaStream_t st);
 // stable LSD radix sort of uint32 (key, value) pairs (lfmm_tree.cu); uses keys_tmp, vals_tmp, hist
-LfErr lf_radix_sort(lfmm_ctx* ctx, uint32_t* keys, uint32_t* vals, int64_t n, cudaStream_t st);
+LfErr lf_radix_sort(lfmm_ctx* ctx, uint32_t* keys, uint32_t* vals, int64_t n, cudaStream_t st, int first_pass = 0,
+                    int npass = 4);
 
 // ---- evaluation (lfmm_fmm.cu, lfmm_near.cu) ----
 LfErr lf_evaluate_sorted(lfmm_ctx* ctx, int nrhs, const double* q_dev, double* phi_dev, double* field_dev,

@@ -306,12 +306,20 @@ LfErr lf_prepare_m2l(lfmm_ctx* ctx, cudaStream_t st)
             lv.off, lv.nbox, ctx->box_key.as<uint32_t>(), ctx->box_parent.as<int>(), ctx->m2m_slots.as<int>());
     }
     LF_TRY(lf_cuda(cudaGetLastError(), "m2l slots"));
-    LF_TRY(lf_radix_sort(ctx, ctx->m2l_keys.as<uint32_t>(), ctx->m2l_sorted.as<uint32_t>(), nsort, st));
+    // keys are level << 28 | class << 25 | index: with fewer than 2^24 boxes the
+    // top byte alone orders them (stable within a level and class)
+    if (nsort < (1 << 24))
+        LF_TRY(lf_radix_sort(ctx, ctx->m2l_keys.as<uint32_t>(), ctx->m2l_sorted.as<uint32_t>(), nsort, st, 3, 1));
+    else
+        LF_TRY(lf_radix_sort(ctx, ctx->m2l_keys.as<uint32_t>(), ctx->m2l_sorted.as<uint32_t>(), nsort, st));
     int hcnt[16 + 16 * 8];
     LF_CHECK(cudaMemcpyAsync(hcnt, err, sizeof(hcnt), cudaMemcpyDeviceToHost, st));
     LF_CHECK(cudaStreamSynchronize(st));
     if (hcnt[0] != 0) return "internal: free M2L entry outside its offset class";
-    std::vector<int4> tiles, l2l_tiles;
+    std::vector<int4>& tiles = ctx->m2l_tiles_h;
+    std::vector<int4>& l2l_tiles = ctx->l2l_tiles_h;
+    tiles.clear();
+    l2l_tiles.clear();
     std::vector<int> l2l_first(depth + 2, 0);
     int start = 0;
     for (int l = 1; l <= depth; ++l) {
@@ -327,7 +335,8 @@ LfErr lf_prepare_m2l(lfmm_ctx* ctx, cudaStream_t st)
     }
     l2l_first[depth + 1] = (int)l2l_tiles.size();
     // M2M tiles: parents of levels 0 .. depth-1 in box order
-    std::vector<int4> m2m_tiles;
+    std::vector<int4>& m2m_tiles = ctx->m2m_tiles_h;
+    m2m_tiles.clear();
     ctx->m2m_first.assign(depth + 1, 0);
     for (int l = 0; l < depth; ++l) {
         ctx->m2m_first[l] = (int)m2m_tiles.size();
@@ -351,7 +360,8 @@ LfErr lf_prepare_m2l(lfmm_ctx* ctx, cudaStream_t st)
                                  cudaMemcpyHostToDevice, st));
     }
     // wider tiles of the same (level, class) runs for the tensor-core kernel
-    std::vector<int4> tct;
+    std::vector<int4>& tct = ctx->tc_tiles_h;
+    tct.clear();
     ctx->m2l_tc_ntiles = 0;
     if (ctx->m2l_tc_ok) {
         const int TN = lf_m2l_tc_tile();
@@ -370,11 +380,11 @@ LfErr lf_prepare_m2l(lfmm_ctx* ctx, cudaStream_t st)
                                      cudaMemcpyHostToDevice, st));
         }
     }
-    double hl[16] = {0};
-    for (int l = 0; l <= depth && l < 16; ++l) hl[l] = ctx->levels[l].h;
-    LF_TRY(lf_reserve(ctx->m2l_levelh, sizeof(hl)));
-    LF_CHECK(cudaMemcpyAsync(ctx->m2l_levelh.ptr, hl, sizeof(hl), cudaMemcpyHostToDevice, st));
-    LF_CHECK(cudaStreamSynchronize(st));
+    double* hl = ctx->m2l_levelh_h;
+    for (int l = 0; l < 16; ++l) hl[l] = (l <= depth) ? ctx->levels[l].h : 0.0;
+    LF_TRY(lf_reserve(ctx->m2l_levelh, sizeof(double) * 16));
+    LF_CHECK(cudaMemcpyAsync(ctx->m2l_levelh.ptr, hl, sizeof(double) * 16, cudaMemcpyHostToDevice, st));
+    // (host staging lives in the context; the build synchronises at its end)
     ctx->shift_ready = 1;
     return LfErr();
 }

@@ -190,12 +190,9 @@ LfErr lf_prepare_m2r(lfmm_ctx* ctx, cudaStream_t st)
             ctx->m2r_tgt.as<int>(), bad);
     }
     LF_TRY(lf_cuda(cudaGetLastError(), "m2r keys"));
-    int hbad = 0;
-    LF_CHECK(cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, st));
-    LF_CHECK(cudaStreamSynchronize(st));
-    if (hbad) return "internal: reaction M2L pair with a non-integer or too distant offset on an aligned level";
     // vals hold absolute entry indices (e), keys sorted ascending
-    LF_TRY(lf_radix_sort(ctx, keys, vals, ne, st));
+    // keys use bits 0..20 (component << 16 | level << 12 | offset): three digits
+    LF_TRY(lf_radix_sort(ctx, keys, vals, ne, st, 0, 3));
     LF_TRY(lf_reserve(ctx->flags, (size_t)ne * 4 + 16));
     LF_TRY(lf_reserve(ctx->idx, (size_t)ne * 4 + 16));
     int* fl = ctx->flags.as<int>();
@@ -209,15 +206,19 @@ LfErr lf_prepare_m2r(lfmm_ctx* ctx, cudaStream_t st)
                                                                        ctx->m2r_kval.as<uint32_t>());
     LF_TRY(lf_cuda(cudaGetLastError(), "m2r key starts"));
     std::vector<int> kstart(nk + 1);
+    std::vector<uint32_t> kv(nk);
+    int hbad = 0;
     LF_CHECK(cudaMemcpyAsync(kstart.data(), ctx->m2r_kstart.ptr, sizeof(int) * nk, cudaMemcpyDeviceToHost, st));
+    LF_CHECK(cudaMemcpyAsync(kv.data(), ctx->m2r_kval.ptr, sizeof(uint32_t) * nk, cudaMemcpyDeviceToHost, st));
+    LF_CHECK(cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, st));
     LF_CHECK(cudaStreamSynchronize(st));
+    if (hbad) return "internal: reaction M2L pair with a non-integer or too distant offset on an aligned level";
     kstart[nk] = ne;
     // tables, one per distinct (component, level, rho^2, oz)
-    std::vector<uint32_t> kv(nk);
-    LF_CHECK(cudaMemcpyAsync(kv.data(), ctx->m2r_kval.ptr, sizeof(uint32_t) * nk, cudaMemcpyDeviceToHost, st));
-    LF_CHECK(cudaStreamSynchronize(st));
-    std::vector<int4> tdesc;
-    std::vector<int> ktab(nk);
+    std::vector<int4>& tdesc = ctx->m2r_tdesc_h;
+    std::vector<int>& ktab = ctx->m2r_ktab_h;
+    tdesc.clear();
+    ktab.assign(nk, 0);
     {
         std::map<uint64_t, int> seen;
         for (int64_t k = 0; k < nk; ++k) {
@@ -240,10 +241,10 @@ LfErr lf_prepare_m2r(lfmm_ctx* ctx, cudaStream_t st)
     LF_TRY(lf_reserve(ctx->m2r_ktab, (size_t)nk * sizeof(int) + 16));
     LF_CHECK(cudaMemcpyAsync(ctx->m2r_tdesc.ptr, tdesc.data(), ntab * sizeof(int4), cudaMemcpyHostToDevice, st));
     LF_CHECK(cudaMemcpyAsync(ctx->m2r_ktab.ptr, ktab.data(), nk * sizeof(int), cudaMemcpyHostToDevice, st));
-    double hl[16] = {0};
-    for (int l = 0; l <= ctx->depth && l < 16; ++l) hl[l] = ctx->levels[l].h;
-    LF_TRY(lf_reserve(ctx->m2r_levelh, sizeof(hl)));
-    LF_CHECK(cudaMemcpyAsync(ctx->m2r_levelh.ptr, hl, sizeof(hl), cudaMemcpyHostToDevice, st));
+    double* hl = ctx->m2r_levelh_h;
+    for (int l = 0; l < 16; ++l) hl[l] = (l <= ctx->depth) ? ctx->levels[l].h : 0.0;
+    LF_TRY(lf_reserve(ctx->m2r_levelh, sizeof(double) * 16));
+    LF_CHECK(cudaMemcpyAsync(ctx->m2r_levelh.ptr, hl, sizeof(double) * 16, cudaMemcpyHostToDevice, st));
     size_t sm = sizeof(double) * ((size_t)TT + 2 * (size_t)Q * TS);
     LF_CHECK(cudaFuncSetAttribute(k_m2r_tables, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     ++ctx->launches, k_m2r_tables<<<ntab, 128, sm, st>>>(ctx->m2r_tdesc.as<int4>(), ntab,
@@ -252,7 +253,8 @@ LfErr lf_prepare_m2r(lfmm_ctx* ctx, cudaStream_t st)
     LF_TRY(lf_cuda(cudaGetLastError(), "m2r tables"));
     ctx->m2r_ntab = ntab;
     // batches of R_TB pairs of one key
-    std::vector<int4> batches;
+    std::vector<int4>& batches = ctx->m2r_batches_h;
+    batches.clear();
     for (int k = 0; k < nk; ++k)
         for (int s = kstart[k]; s < kstart[k + 1]; s += R_TB)
             batches.push_back(make_int4(k, s, std::min(R_TB, kstart[k + 1] - s), 0));
@@ -261,7 +263,7 @@ LfErr lf_prepare_m2r(lfmm_ctx* ctx, cudaStream_t st)
     LF_TRY(lf_reserve(ctx->m2r_batches, batches.size() * sizeof(int4) + 16));
     LF_CHECK(cudaMemcpyAsync(ctx->m2r_batches.ptr, batches.data(), batches.size() * sizeof(int4),
                              cudaMemcpyHostToDevice, st));
-    LF_CHECK(cudaStreamSynchronize(st));
+    // (the host staging vectors live in the context; the build synchronises at its end)
     ctx->stats[LFMM_STAT_REACTION_KEYS] = nk;
     ctx->stats[LFMM_STAT_REACTION_TABLES] = ntab;
     return LfErr();

@@ -195,7 +195,10 @@ __global__ void k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t
     }
 }
 
-LfErr lf_radix_sort(lfmm_ctx* ctx, uint32_t* keys, uint32_t* vals, int64_t n, cudaStream_t st)
+// Sorts by the key bits [8 first_pass, 8 (first_pass + npass)); the other
+// bits are ignored (stable within equal digits).
+LfErr lf_radix_sort(lfmm_ctx* ctx, uint32_t* keys, uint32_t* vals, int64_t n, cudaStream_t st, int first_pass,
+                    int npass)
 {
     int nb = lf_blocks(n, RS_TILE);
     LF_TRY(lf_reserve(ctx->keys_tmp, (size_t)n * 4));
@@ -203,7 +206,7 @@ LfErr lf_radix_sort(lfmm_ctx* ctx, uint32_t* keys, uint32_t* vals, int64_t n, cu
     LF_TRY(lf_reserve(ctx->hist, (size_t)256 * nb * 4));
     uint32_t *ka = keys, *va = vals, *kb = ctx->keys_tmp.as<uint32_t>(), *vb = ctx->vals_tmp.as<uint32_t>();
     int* h = ctx->hist.as<int>();
-    for (int pass = 0; pass < 4; ++pass) {
+    for (int pass = first_pass; pass < first_pass + npass; ++pass) {
         int shift = 8 * pass;
         ++ctx->launches, k_radix_hist<<<nb, RS_T, 0, st>>>(ka, n, shift, h, nb);
         LF_TRY(lf_cuda(cudaGetLastError(), "radix hist"));
@@ -213,7 +216,10 @@ LfErr lf_radix_sort(lfmm_ctx* ctx, uint32_t* keys, uint32_t* vals, int64_t n, cu
         std::swap(ka, kb);
         std::swap(va, vb);
     }
-    // four passes: data is back in (keys, vals)
+    if (npass & 1) {  // the result sits in the scratch buffers
+        LF_CHECK(cudaMemcpyAsync(keys, ka, (size_t)n * 4, cudaMemcpyDeviceToDevice, st));
+        LF_CHECK(cudaMemcpyAsync(vals, va, (size_t)n * 4, cudaMemcpyDeviceToDevice, st));
+    }
     return LfErr();
 }
 
@@ -748,9 +754,8 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
         const LfmmLevel& lv = ctx->levels[depth];
         int sh = 3 * (LFMM_FINE_LEVEL - depth);
         ++ctx->launches, k_flags_particles<<<lf_blocks(n, 256), 256, 0, st>>>(keys, n, sh, fl);
-        int64_t total = 0;
-        LF_TRY(lf_scan_i32(ctx, fl, ix, n, &total, st));
-        if (total != lv.nbox) return "internal: leaf box count mismatch";
+        // the box counts per level are known (k_level_counts): no read-back
+        LF_TRY(lf_scan_i32(ctx, fl, ix, n, nullptr, st));
         ++ctx->launches, k_leaf_boxes<<<lf_blocks(n, 256), 256, 0, st>>>(keys, n, sh, fl, ix, lv.off, bkey, pbeg, cbeg, cend);
         ++ctx->launches, k_level_ends<<<lf_blocks(lv.nbox, 256), 256, 0, st>>>(lv.off, lv.nbox, n, 0, pbeg, pend, cbeg, cend, 1);
         LF_TRY(lf_cuda(cudaGetLastError(), "leaf boxes"));
@@ -759,9 +764,7 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
         const LfmmLevel& ch = ctx->levels[l + 1];
         const LfmmLevel& lv = ctx->levels[l];
         ++ctx->launches, k_flags_boxes<<<lf_blocks(ch.nbox, 256), 256, 0, st>>>(bkey, ch.off, ch.nbox, fl);
-        int64_t total = 0;
-        LF_TRY(lf_scan_i32(ctx, fl, ix, ch.nbox, &total, st));
-        if (total != lv.nbox) return "internal: box count mismatch";
+        LF_TRY(lf_scan_i32(ctx, fl, ix, ch.nbox, nullptr, st));
         ++ctx->launches, k_parent_boxes<<<lf_blocks(ch.nbox, 256), 256, 0, st>>>(fl, ix, ch.off, ch.nbox, lv.off, bkey, pbeg, par,
                                                                    cbeg);
         ++ctx->launches, k_level_ends<<<lf_blocks(lv.nbox, 256), 256, 0, st>>>(lv.off, lv.nbox, n, ch.off + ch.nbox, pbeg, pend, cbeg,
