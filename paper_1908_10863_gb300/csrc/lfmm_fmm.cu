@@ -71,7 +71,8 @@ __global__ void __launch_bounds__(32) k_p2m(int off, int p, const LfD4* __restri
     const int b = off + blockIdx.x;
     const LfD4 c = cen[b];
     const double ih = 1.0 / h;
-    R* ure = su + lane * 2 * nre;
+    const int HS = 2 * nre + 1;  // odd row stride: lanes' rows fall in distinct banks
+    R* ure = su + lane * HS;
     R* uim = ure + nre;
     constexpr int KMAX = (LFMM_PMAX + 1) * (LFMM_PMAX + 1) / 32 + 1;
     int src[KMAX];
@@ -96,7 +97,7 @@ __global__ void __launch_bounds__(32) k_p2m(int off, int p, const LfD4* __restri
         }
         __syncwarp();
         const int cnt = min(32, pe - start);
-        R* sq = su + 32 * 2 * nre;  // this chunk's charges of one right-hand side
+        R* sq = su + 32 * HS;  // this chunk's charges of one right-hand side
         for (int r = 0; r < nrhs; ++r) {
             sq[lane] = (i < pe) ? q[(size_t)r * qstride + i] : R(0);
             __syncwarp();
@@ -104,7 +105,7 @@ __global__ void __launch_bounds__(32) k_p2m(int off, int p, const LfD4* __restri
             for (int k = 0; k < KMAX; ++k) {
                 if (src[k] < 0) continue;
                 R s = 0;
-                for (int u = 0; u < cnt; ++u) s += sq[u] * su[u * 2 * nre + src[k]];
+                for (int u = 0; u < cnt; ++u) s += sq[u] * su[u * HS + src[k]];
                 if (start == pb)
                     out[lane + 32 * k] = s;
                 else
@@ -401,7 +402,7 @@ __global__ void __launch_bounds__(32) k_l2p(int off, int p, const LfD4* __restri
     const int b = off + blockIdx.x;
     const LfD4 c = cen[b];
     const double ih = 1.0 / h;
-    R* ure = su + lane * 2 * nre;
+    R* ure = su + lane * (2 * nre + 1);  // odd row stride: no bank conflicts
     R* uim = ure + nre;
     const int pb = pbeg[b], pe = pend[b];
     for (int start = pb; start < pe; start += 32) {
@@ -529,7 +530,7 @@ static LfErr far_field(lfmm_ctx* ctx, cudaStream_t st)
     // upward pass
     int ph = lf_prof_start(ctx, LFMM_TIME_P2M, st);
     {
-        size_t sm = sizeof(R) * (2 * 32 * (size_t)nre + 32);
+        size_t sm = sizeof(R) * (32 * (2 * (size_t)nre + 1) + 32);
         LF_CHECK(cudaFuncSetAttribute(k_p2m<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         ++ctx->launches, k_p2m<R><<<leaf.nbox, 32, sm, st>>>(leaf.off, p, cen, pbeg, pend, ctx->xs.as<double>(),
                                                              ctx->ys.as<double>(), ctx->zs.as<double>(),
@@ -630,7 +631,7 @@ static LfErr far_field(lfmm_ctx* ctx, cudaStream_t st)
     }
     ph = lf_prof_start(ctx, LFMM_TIME_L2P, st);
     {
-        size_t sm = sizeof(R) * (nc + 2 * 32 * (size_t)nre);
+        size_t sm = sizeof(R) * (nc + 32 * (2 * (size_t)nre + 1));
         LF_CHECK(cudaFuncSetAttribute(k_l2p<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         ++ctx->launches, k_l2p<R><<<leaf.nbox, 32, sm, st>>>(leaf.off, p, cen, pbeg, pend, ctx->xs.as<double>(),
                                                              ctx->ys.as<double>(), ctx->zs.as<double>(), leaf.h, L,

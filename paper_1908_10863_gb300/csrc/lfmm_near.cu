@@ -57,15 +57,39 @@ struct P2PArgs {
 
 #define P2P_T 128
 
-// Sums of one target over a batch of RB right-hand sides.
-template <typename R, int RB>
-struct P2PAcc {
-    LfSum<R> P[RB], Ex[RB], Ey[RB], Ez[RB];
+// Sums of one target over a batch of RB right-hand sides: compensated
+// (LfSum) across source boxes, plain (LfPlain) within one source box.
+template <typename R>
+struct LfPlain {
+    R s = 0;
+    __device__ __forceinline__ void add(R x) { s += x; }
 };
+template <typename S, int RB>
+struct P2PAccT {
+    S P[RB], Ex[RB], Ey[RB], Ez[RB];
+};
+template <typename R, int RB>
+using P2PAcc = P2PAccT<LfSum<R>, RB>;
+template <typename R, int RB>
+using P2PPart = P2PAccT<LfPlain<R>, RB>;
+
+// add one source box's partial sums into the compensated totals and clear them
+template <typename R, int RB>
+__device__ __forceinline__ void p2p_flush(P2PPart<R, RB>& part, P2PAcc<R, RB>& A)
+{
+#pragma unroll
+    for (int k = 0; k < RB; ++k) {
+        A.P[k].add(part.P[k].s);
+        A.Ex[k].add(part.Ex[k].s);
+        A.Ey[k].add(part.Ey[k].s);
+        A.Ez[k].add(part.Ez[k].s);
+        part.P[k].s = part.Ex[k].s = part.Ey[k].s = part.Ez[k].s = R(0);
+    }
+}
 
 // Free-space kernel of one pair, applied to the nr charges qs[k * qsk] of the batch.
-template <typename R, int RB>
-__device__ __forceinline__ void p2p_free_add(R dx, R dy, R dz, const R* qs, int qsk, int nr, P2PAcc<R, RB>& A)
+template <typename R, int RB, typename S>
+__device__ __forceinline__ void p2p_free_add(R dx, R dy, R dz, const R* qs, int qsk, int nr, P2PAccT<S, RB>& A)
 {
     typedef LfMath<R> F;
     R r2 = dx * dx + dy * dy + dz * dz;
@@ -86,9 +110,9 @@ __device__ __forceinline__ void p2p_free_add(R dx, R dy, R dz, const R* qs, int 
 }
 
 // Reaction kernels of one pair by the quadrature (once), applied to the batch.
-template <typename R, int RB>
+template <typename R, int RB, typename S>
 __device__ __forceinline__ void p2p_reaction_add(const LfmmComp& cp, R dx, R dy, R dz, const R* qs, int qsk, int nr,
-                                                 int Qn, P2PAcc<R, RB>& A)
+                                                 int Qn, P2PAccT<S, RB>& A)
 {
     typedef LfMath<R> F;
     R h = (cp.a == 1) ? dz : -dz;
@@ -222,6 +246,7 @@ __global__ void __launch_bounds__(32 * PW_WARPS) k_p2p_warp(P2PArgs a, const flo
             zi = r.z;
         }
         P2PAcc<float, RB> A;
+        P2PPart<float, RB> part;
         for (int e = eb; e < ee; ++e) {
             const uint32_t ent = a.nent[e];
             const int c = (int)(ent >> LFMM_ENT_SHIFT);
@@ -251,13 +276,14 @@ __global__ void __launch_bounds__(32 * PW_WARPS) k_p2p_warp(P2PArgs a, const flo
                 if (cp.is_free) {
                     for (int u = 0; u < cnt; ++u)
                         p2p_free_add<float, RB>(xi - sx[w][u], yi - sy[w][u], zi - sz[w][u], &sq[w][0][u], 32, a.nr,
-                                                A);
+                                                part);
                 } else {
                     for (int u = 0; u < cnt; ++u)
                         p2p_reaction_add<float, RB>(cp, xi - sx[w][u], yi - sy[w][u], zi - sz[w][u], &sq[w][0][u],
-                                                    32, a.nr, a.Qn, A);
+                                                    32, a.nr, a.Qn, part);
                 }
             }
+            p2p_flush<float, RB>(part, A);
         }
         if (valid) p2p_store<float, RB>(a, i, A);
     }
