@@ -4,7 +4,7 @@
 // lfmm_m2l.cu, evaluated as D[r][j] = sum_o sum_k A_o[r][k] X_o[j][k] with
 //   r = output coefficient (M = 128 rows, expansions with (p+1)^2 <= 128),
 //   j = target box of the tile (N = 256 columns, one level and octant class),
-//   k = input coefficient of the source at offset o (K = 128 in 8 chunks of 16),
+//   k = input coefficient of the source at offset o (K = 128 in chunks of TC_KC),
 // accumulated in tensor memory (128 lanes x 256 float32 columns).
 //
 // Precision: float32 operands as sums of two TF32 pieces, the operator
@@ -20,17 +20,20 @@
 //
 // One CTA = (tile of 256 targets, one third of its 189 offsets):
 //   warps 0..7  gather the 256 pre-split source multipoles of a (offset,
-//               K chunk) stage with 16-byte cp.async into the 64-byte-swizzled
-//               K-major layout (zeros where a target has no source there), two
-//               stages ahead of the tensor cores; thread 0 also starts the bulk
+//               K chunk) stage with 16-byte cp.async into the swizzled
+//               K-major layout (zeros where a target has no source there), ahead
+//               of the tensor cores; thread 0 also starts the bulk
 //               copy of the matching operator chunk (stored pre-split and
 //               pre-swizzled in HBM);
-//   warp 8      one thread issues the 6 MMAs of a stage and commits them to
+//   warp 8      one thread issues the MMAs of a stage (3 products x K chunk / 8) and commits them to
 //               the stage's "empty" barrier;
 //   epilogue    warps 0..7 read the accumulator (tcgen05.ld), scale by 1/h and
 //               add into the local expansions (float atomics: three CTAs share
 //               a tile).
-// Four stages of 48 KB buffer the operands.  Tiles of one octant class share
+// Four stages of 48 KB (K chunks of 16, 64-byte swizzle) buffer the operands,
+// handed to the tensor cores two stages after their copies start.  (Eight
+// stages of K chunks of 8 with 32-byte swizzle measured 1.5x slower; a longer
+// lag on four stages leaves the tensor cores too little slack.)  Tiles of one octant class share
 // their offset list; each tile walks it from a different starting offset so
 // that concurrent CTAs read different operator chunks.  Every barrier wait is
 // bounded; on a timeout the CTA records an error, stops issuing work, waits
@@ -58,21 +61,24 @@
 
 #define TC_N 256                     // targets per tile (MMA N)
 #define TC_M 128                     // output coefficients (MMA M)
-#define TC_KC 16                     // K elements per stage (64 bytes of float32)
-#define TC_NKC 8                     // K chunks (K = 128)
+#ifndef TC_KC
+#define TC_KC 16                     // K elements per stage (16: 64-byte rows; 8: 32-byte rows, slower)
+#endif
+#define TC_NKC (128 / TC_KC)         // K chunks (K = 128)
 #define TC_ROWB (TC_KC * 4)          // bytes per row of a stage tile
+#define TC_RCH (TC_ROWB / 16)        // 16-byte chunks per row
 #define TC_NOFF 189                  // offsets per octant class
 #define TC_NALL 343
 #define TC_PROD_WARPS 8
 #define TC_THREADS (32 * TC_PROD_WARPS + 32)
-#define TC_A_BYTES (TC_M * TC_ROWB)  // one operator piece of a stage: 8 KB
-#define TC_X_BYTES (TC_N * TC_ROWB)  // one multipole piece of a stage: 16 KB
+#define TC_A_BYTES (TC_M * TC_ROWB)  // one operator piece of a stage
+#define TC_X_BYTES (TC_N * TC_ROWB)  // one multipole piece of a stage
 #define TC_AP 2                      // operator pieces
 #define TC_XP 2                      // multipole pieces
 #define TC_STAGE_BYTES (TC_AP * TC_A_BYTES + TC_XP * TC_X_BYTES)
 #define TC_MROW 128                  // floats per multipole piece row in the split copy (512 B)
-#define TC_STAGES 4
-#define TC_LAG 2                     // stages between a stage's copies and its hand-over
+#define TC_STAGES (TC_KC == 8 ? 8 : 4)  // 24 KB or 48 KB stages
+#define TC_LAG (TC_STAGES / 2)           // stages between a stage's copies and its hand-over
 #define TC_SMEM (TC_STAGES * TC_STAGE_BYTES + 1024)
 #define TC_TMEM_COLS 256
 #define TC_SPIN_CYCLES (1ll << 31)   // ~1 s at 2 GHz
@@ -149,9 +155,9 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr)
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
     d |= (uint64_t)1 << 16;                   // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)(512 >> 4) << 32;          // stride byte offset
+    d |= (uint64_t)((8 * TC_ROWB) >> 4) << 32;  // stride byte offset: 8 rows
     d |= (uint64_t)1 << 46;                   // descriptor version
-    d |= (uint64_t)4 << 61;                   // 64-byte swizzle
+    d |= (uint64_t)(TC_ROWB == 64 ? 4 : 6) << 61;  // 64-byte or 32-byte swizzle
     return d;
 }
 // instruction descriptor: D float32, A and B TF32, both K-major, M x N
@@ -188,12 +194,15 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, float v[32])
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// byte offset of element (row, k) of a 64-byte-swizzled K-major tile (k < 16
-// float32): the 16-byte chunk index (address bits 4-5) is XORed with address
-// bits 7-8, i.e. with (row / 2) mod 4
-__host__ __device__ __forceinline__ uint32_t sw64(int row, int k)
+// byte offset of element (row, k) of a swizzled K-major tile with TC_ROWB-byte
+// rows: the 16-byte chunk index is XORed with the address bits just above the
+// swizzle span -- 64-byte swizzle: chunk (bits 4-5) ^ bits 7-8 = (row / 2) mod 4;
+// 32-byte swizzle: chunk (bit 4) ^ bit 7 = (row / 4) mod 2
+__host__ __device__ __forceinline__ uint32_t swz(int row, int k)
 {
-    return (uint32_t)row * 64u + ((uint32_t)(((k >> 2) ^ (row >> 1)) & 3) << 4) + (uint32_t)(k & 3) * 4u;
+    const uint32_t c = (uint32_t)(k >> 2);
+    const uint32_t x = (TC_ROWB == 64) ? (uint32_t)((row >> 1) & 3) : (uint32_t)((row >> 2) & 1);
+    return (uint32_t)row * TC_ROWB + ((c ^ x) << 4) + (uint32_t)(k & 3) * 4u;
 }
 
 struct TcArgs {
@@ -235,7 +244,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(TcArgs g)
     if (tid < TC_N) s_tb[tid] = (tid < cnt) ? g.sorted[start + tid] : -1;
     if (tid == 0) {
         for (int s = 0; s < TC_STAGES; ++s) {
-            mbar_init(&full_bar[s], 32 * TC_PROD_WARPS + 1);
+            mbar_init(&full_bar[s], TC_PROD_WARPS + 1);  // one arrival per producer warp + the bulk copy's
             mbar_init(&empty_bar[s], 1);
         }
         mbar_init(&done_bar, 1);
@@ -268,7 +277,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(TcArgs g)
             if (it >= TC_STAGES) {
                 if (!mbar_wait(&empty_bar[s], (round - 1) & 1)) atomicExch(&s_abort, 1);
             }
-            if (*(volatile int*)&s_abort) break;
+            if (__any_sync(0xffffffffu, *(volatile int*)&s_abort)) break;  // warp-uniform
             unsigned char* st = sm + (size_t)s * TC_STAGE_BYTES;
             if (ptid == 0) {
                 const int o = g.cls[cl * TC_NOFF + oi];
@@ -284,14 +293,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(TcArgs g)
             // 32 rows x 2 pieces x 4 chunks of 16 B per warp: 8 per lane
             unsigned char* xs = st + TC_AP * TC_A_BYTES;
             const uint32_t xbase = smem_u32(xs);
-            const int chunk = lane & 3;
+            // 32 rows x 2 pieces x TC_RCH chunks of 16 B per warp
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int piece = i >> 2;
-                const int rl = (i & 3) * 8 + (lane >> 2);
+            for (int i = 0; i < 2 * TC_RCH; ++i) {
+                const int piece = i / TC_RCH;
+                const int flat = (i % TC_RCH) * 32 + lane;  // chunk-major over the warp's 32 rows
+                const int rl = flat / TC_RCH, chunk = flat % TC_RCH;
                 const int src = __shfl_sync(0xffffffffu, my_src, rl);
                 const int row = warp * 32 + rl;
-                const uint32_t off = piece * TC_X_BYTES + sw64(row, chunk * 4);
+                const uint32_t off = piece * TC_X_BYTES + swz(row, chunk * 4);
                 if (src >= 0) {
                     const float* gsrc = g.Ms + (size_t)blockIdx.y * g.ms_stride + ((size_t)src * TC_XP + piece) * TC_MROW +
                                         kc * TC_KC + chunk * 4;
@@ -304,12 +314,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(TcArgs g)
             if (it >= TC_LAG) {
                 cp_async_wait<TC_LAG>();
                 fence_async_smem();
-                mbar_arrive(&full_bar[(it - TC_LAG) % TC_STAGES]);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&full_bar[(it - TC_LAG) % TC_STAGES]);
             }
         }
         cp_async_wait<0>();
         fence_async_smem();
-        for (int j = (it > TC_LAG ? it - TC_LAG : 0); j < it; ++j) mbar_arrive(&full_bar[j % TC_STAGES]);
+        __syncwarp();
+        if (lane == 0)
+            for (int j = (it > TC_LAG ? it - TC_LAG : 0); j < it; ++j) mbar_arrive(&full_bar[j % TC_STAGES]);
         // drain: the bulk copies this thread issued complete on their full barriers
         if (ptid == 0 && *(volatile int*)&s_abort) {
             for (int j = (armed > TC_STAGES ? armed - TC_STAGES : 0); j < armed; ++j)
@@ -412,7 +425,7 @@ LfErr lf_setup_m2l_tc(lfmm_ctx* ctx, const double* A64, int KP, int RP)
                         uint32_t t = host_tf32((float)v);
                         float tf;
                         memcpy(&tf, &t, 4);
-                        memcpy(p0 + (size_t)q * TC_A_BYTES + sw64(r, k), &t, 4);
+                        memcpy(p0 + (size_t)q * TC_A_BYTES + swz(r, k), &t, 4);
                         v -= (double)tf;
                     }
                 }
