@@ -80,6 +80,8 @@ def parse():
     ap.add_argument("--sample", type=int, default=256, help="oracle targets for the accuracy / CPU leg")
     ap.add_argument("--no-near", action="store_true", help="skip the near-interface workload")
     ap.add_argument("--no-multi", action="store_true", help="skip the many-charge-vector workload")
+    ap.add_argument("--accuracy-table", action="store_true",
+                    help="instead of timing: Err2 against the oracle for each medium, N, p and precision")
     ap.add_argument("--forms", default="fp32_surrogate,fp32,fp64",
                     help="comma list of fp32_surrogate, fp32, fp64; the first is the headline")
     return ap.parse_args()
@@ -285,6 +287,35 @@ def multi_rhs_leg(torch, dev, p, flush, nrhs=64, n=1 << 18):
             "charges_x_vectors_per_s": w.n * nrhs / (t_batch / 1e3), "speedup": t_single / t_batch}
 
 
+def accuracy_table(torch, dev):
+    """Relative L2 errors (potential and field) of both forms against the CPU
+    oracle (exact image series), one JSON line per case.  Small N: all
+    targets; N = 1M: a seeded target subsample."""
+    import oracle
+    from paper_1908_10863_gb300 import LayeredFMM, workloads
+    cases = [("config1", "(1,5,10)", 1000, 1000), ("config2", "(1,5,10)", 1 << 20, 200),
+             ("config2", "(1,80,2)", 1 << 20, 60)]
+    for name, med, n, ns in cases:
+        eps = workloads.EPS_CONFIG if med == "(1,5,10)" else workloads.EPS_HIGH_CONTRAST
+        w = workloads.config1(n, eps=eps) if name == "config1" else workloads.config2(n, eps=eps)
+        t = np.arange(n) if ns >= n else workloads.subsample(n, ns)
+        t0 = time.perf_counter()
+        ref, refE = oracle.direct(w.d, w.eps, w.xyz, w.layer, w.q, targets=t, mode=oracle.MODE_IMAGES,
+                                  threads=os.cpu_count() or 1)
+        oracle_s = time.perf_counter() - t0
+        for p in (6, 10, 14, 20):
+            for prec in (0, 1):
+                if (n > 100000 and p == 20) or (prec == 1 and p > 14):
+                    continue  # p = 20 on the small case only; the float32 form stops at p = 14
+                with LayeredFMM(w.d, w.eps, p, precision=prec) as f:
+                    f.build(w.xyz, w.layer)
+                    phi, E = f.evaluate(w.q)
+                print(json.dumps({"case": name, "eps": med, "n": n, "targets": int(len(t)), "p": p,
+                                  "form": "fp32" if prec else "fp64", "err2_phi": oracle.err2(ref, phi[t]),
+                                  "err2_field": oracle.err2(refE, E[t]), "oracle_s": round(oracle_s, 1)}),
+                      flush=True)
+
+
 def main():
     args = parse()
     world, rank, local, pg = dist_setup(args)
@@ -321,6 +352,10 @@ def main():
     import torch
     from paper_1908_10863_gb300 import LayeredFMM
 
+    if args.accuracy_table:
+        if rank == 0:
+            accuracy_table(torch, torch.device("cuda", local))
+        return 0
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     xyz_d = torch.from_numpy(w.xyz).to(dev)
