@@ -419,17 +419,20 @@ static LfErr setup_components(lfmm_ctx* ctx)
 }
 
 // Free-space M2L tables: T_N^mu of the offset (t - s)/h in the rotated half
-// plane (rho = |offset_xy|, z = offset_z), for |offset|_inf in {2, 3}.
+// plane (rho = |offset_xy|, z = offset_z), for |offset|_inf in [2, TR]: TR = 3
+// (classic separation) or 5 (wider separation of high orders, whose finer-level
+// pairs reach offsets of 5).
 static LfErr setup_tables(lfmm_ctx* ctx)
 {
     const int p = ctx->p, TS = 2 * p + 1, TT = TS * TS, nre = lf_nre(p);
-    std::vector<double> T((size_t)343 * TT, 0.0);
-    for (int ox = -3; ox <= 3; ++ox)
-        for (int oy = -3; oy <= 3; ++oy)
-            for (int oz = -3; oz <= 3; ++oz) {
+    const int TR = ctx->sep_ext ? 5 : 3, TW = 2 * TR + 1;
+    std::vector<double> T((size_t)TW * TW * TW * TT, 0.0);
+    for (int ox = -TR; ox <= TR; ++ox)
+        for (int oy = -TR; oy <= TR; ++oy)
+            for (int oz = -TR; oz <= TR; ++oz) {
                 int mx = std::max(abs(ox), std::max(abs(oy), abs(oz)));
                 if (mx < 2) continue;
-                double* t = &T[(size_t)((ox + 3) * 49 + (oy + 3) * 7 + (oz + 3)) * TT];
+                double* t = &T[(size_t)(((ox + TR) * TW + (oy + TR)) * TW + (oz + TR)) * TT];
                 double rho = sqrt((double)(ox * ox + oy * oy));
                 for (int mu = 0; mu <= 2 * p; ++mu) lf_theta_column(rho, (double)oz, mu, 2 * p, 1.0, t, TS);
             }
@@ -506,6 +509,7 @@ lfmm_status lfmm_create(const double* d, int L, const double* eps, int p, lfmm_c
     for (int l = 0; l < L; ++l) ctx->d[l] = d[l];
     for (int l = 0; l <= L; ++l) ctx->eps[l] = eps[l];
     ctx->p = p;
+    ctx->sep_ext = (p >= LFMM_SEP_EXT_P) ? 1 : 0;
     LfErr e = setup_components(ctx);
     if (e.empty()) e = lf_cuda(cudaGetDevice(&ctx->device), "cudaGetDevice");
     if (e.empty()) e = lf_cuda(cudaFree(0), "context init");

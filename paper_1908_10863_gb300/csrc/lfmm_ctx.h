@@ -69,7 +69,10 @@ struct lfmm_ctx {
     // geometry of the grid
     bool built = false;
     int64_t n = 0;
-    int nrhs_b = 1;  // right-hand sides of the evaluation in flight (expansions [nrhs_b][boxes][nc])
+    int nrhs_b = 1;
+    // wider separation for high orders: far-field pairs also need a centre
+    // distance of at least sqrt(6) boxes (set at create for p >= LFMM_SEP_EXT_P)
+    int sep_ext = 0;  // right-hand sides of the evaluation in flight (expansions [nrhs_b][boxes][nc])
     int depth = 0;
     double H = 1.0;
     double origin[3] = {0, 0, 0};
@@ -177,6 +180,7 @@ LfErr lf_evaluate_sorted(lfmm_ctx* ctx, int nrhs, const double* q_dev, double* p
                          cudaStream_t st);
 // right-hand sides evaluated in one pass (larger requests are split)
 #define LFMM_RHS_BATCH 64
+#define LFMM_SEP_EXT_P 18
 LfErr lf_near_field(lfmm_ctx* ctx, cudaStream_t st);
 LfErr lf_near_prepare(lfmm_ctx* ctx, cudaStream_t st);
 

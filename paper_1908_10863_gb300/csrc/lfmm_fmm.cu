@@ -265,7 +265,8 @@ struct M2LArgs {
     const uint32_t* ment;
     const void* M;
     void* L;
-    const void* freeT;  // [343][TS*TS] in R
+    const void* freeT;  // [(2 tr + 1)^3][TS*TS] in R, offsets in [-tr, tr]^3
+    int tr;
     const double* gl_t;
     const double* gl_w;
     int Q;
@@ -317,7 +318,8 @@ __global__ void k_m2l(M2LArgs a)
         }
         if (!REACT) {
             int ox = (int)lrint(vx), oy = (int)lrint(vy), oz = (int)lrint(vz);
-            const R* src = freeT + (size_t)((ox + 3) * 49 + (oy + 3) * 7 + (oz + 3)) * TT;
+            const int tw = 2 * a.tr + 1;
+            const R* src = freeT + (size_t)(((ox + a.tr) * tw + (oy + a.tr)) * tw + (oz + a.tr)) * TT;
             for (int j = tid; j < TT; j += blockDim.x) sT[j] = src[j];
         } else {
             const double zz = (cp.a == 1) ? vz : -vz;  // > 0 for valid entries
@@ -588,6 +590,7 @@ static LfErr far_field(lfmm_ctx* ctx, cudaStream_t st)
         a.M = M;
         a.L = L;
         a.freeT = freeT;
+        a.tr = ctx->sep_ext ? 5 : 3;
         a.gl_t = ctx->gl_t_m2l.as<double>();
         a.gl_w = ctx->gl_w_m2l.as<double>();
         a.Q = Q;

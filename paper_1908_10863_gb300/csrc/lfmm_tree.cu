@@ -409,6 +409,7 @@ __constant__ LfmmComp c_tree_comp[LFMM_MAXCOMP];
 //   G = (s oz + o - iface) / h  so that (z'' - iface) / h = s (iz_s + 1/2) + G,
 //   Z = zeta_r / h
 __constant__ float4 c_tree_lc[LFMM_MAXCOMP * 16];
+__constant__ int c_tree_sep;  // 1: also require a centre distance of sqrt(6) boxes
 
 // Far-field admissibility of a (target box, source box) pair of one level, in
 // grid units.  Free space: not neighbours (|di|_inf >= 2).  Reaction: the
@@ -420,12 +421,17 @@ __constant__ float4 c_tree_lc[LFMM_MAXCOMP * 16];
 __device__ __forceinline__ bool lf_admissible(const LfmmComp& c, float4 k, int4 gt, int4 gs)
 {
     const int ix = abs(gt.x - gs.x), iy = abs(gt.y - gs.y);
-    if (c.is_free) return max(ix, max(iy, abs(gt.z - gs.z))) >= 2;
+    if (c.is_free) {
+        const int iz = abs(gt.z - gs.z);
+        if (c_tree_sep && ix * ix + iy * iy + iz * iz < 6) return false;
+        return max(ix, max(iy, iz)) >= 2;
+    }
     const float s = (float)c.s;
     const float zt = (float)gt.z + 0.5f, zs = s * ((float)gs.z + 0.5f);
     const float uz = zt - zs - k.x;
     const float ux = (float)ix, uy = (float)iy;
     if (fmaxf(ux, fmaxf(uy, fabsf(uz))) < 2.0f - 1e-3f) return false;
+    if (c_tree_sep && ux * ux + uy * uy + uz * uz < 6.0f - 1e-3f) return false;
     const float tside = zt - k.y, pside = zs + k.z;
     if (c.a == 1) {
         if (!(tside > 0.f && pside < 0.f)) return false;
@@ -797,6 +803,7 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
             }
         LF_CHECK(cudaMemcpyToSymbolAsync(c_tree_lc, lc.data(), sizeof(float4) * lc.size(), 0, cudaMemcpyHostToDevice,
                                          st));
+        LF_CHECK(cudaMemcpyToSymbolAsync(c_tree_sep, &ctx->sep_ext, sizeof(int), 0, cudaMemcpyHostToDevice, st));
         LF_TRY(lf_reserve(ctx->level_consts, sizeof(float4) * lc.size()));
         LF_CHECK(cudaMemcpyAsync(ctx->level_consts.ptr, lc.data(), sizeof(float4) * lc.size(), cudaMemcpyHostToDevice,
                                  st));
