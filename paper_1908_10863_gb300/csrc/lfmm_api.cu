@@ -523,6 +523,12 @@ lfmm_status lfmm_create(const double* d, int L, const double* eps, int p, lfmm_c
         e = lf_cuda(cudaStreamCreateWithPriority(&ctx->s_near, cudaStreamNonBlocking, prio_lo), "stream");
     if (e.empty()) e = lf_cuda(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming), "event");
     if (e.empty()) e = lf_cuda(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming), "event");
+    // per-context component array: kernels read it by pointer, so contexts with
+    // different media can run side by side (no module-global state)
+    if (e.empty()) e = lf_reserve(ctx->comp_dev, sizeof(LfmmComp) * LFMM_MAXCOMP);
+    if (e.empty())
+        e = lf_cuda(cudaMemcpy(ctx->comp_dev.ptr, ctx->comp, sizeof(LfmmComp) * ctx->ncomp, cudaMemcpyHostToDevice),
+                    "components");
     if (e.empty()) e = setup_rules(ctx);
     if (e.empty()) e = setup_tables(ctx);
     if (e.empty()) e = lf_setup_m2l_ops(ctx);

@@ -29,7 +29,6 @@
 
 static inline int lf_blocks(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
-__constant__ LfmmComp c_comp[LFMM_MAXCOMP];
 
 template <typename R>
 struct LfAcc {  // compensated (Kahan) sum in single precision, plain sum in double
@@ -265,6 +264,7 @@ struct M2LArgs {
     const uint32_t* ment;
     const void* M;
     void* L;
+    const LfmmComp* comps;  // the context's components
     const void* freeT;  // [(2 tr + 1)^3][TS*TS] in R, offsets in [-tr, tr]^3
     int tr;
     const double* gl_t;
@@ -304,7 +304,7 @@ __global__ void k_m2l(M2LArgs a)
         const uint32_t ent = a.ment[e];
         const int c = (int)(ent >> LFMM_ENT_SHIFT);
         const int s = (int)(ent & LFMM_ENT_MASK);
-        const LfmmComp& cp = c_comp[c];
+        const LfmmComp cp = a.comps[c];
         const LfD4 cs = a.cen[s];
         const double psz = cp.is_free ? cs.z : cp.s * cs.z + cp.o;
         const double vx = (ct.x - cs.x) * ih, vy = (ct.y - cs.y) * ih, vz = (ct.z - psz) * ih;
@@ -590,6 +590,7 @@ static LfErr far_field(lfmm_ctx* ctx, cudaStream_t st)
         a.M = M;
         a.L = L;
         a.freeT = freeT;
+        a.comps = ctx->comp_dev.as<LfmmComp>();
         a.tr = ctx->sep_ext ? 5 : 3;
         a.gl_t = ctx->gl_t_m2l.as<double>();
         a.gl_w = ctx->gl_w_m2l.as<double>();
@@ -662,7 +663,6 @@ LfErr lf_evaluate_sorted(lfmm_ctx* ctx, int nrhs, const double* q_dev, double* p
     LF_TRY(lf_reserve(ctx->phi_near, (size_t)n * 8 * nr));
     LF_TRY(lf_reserve(ctx->fld_far, (size_t)n * 24 * nr));
     LF_TRY(lf_reserve(ctx->fld_near, (size_t)n * 24 * nr));
-    LF_CHECK(cudaMemcpyToSymbolAsync(c_comp, ctx->comp, sizeof(LfmmComp) * ctx->ncomp, 0, cudaMemcpyHostToDevice, st));
     const int ptot = lf_prof_start(ctx, LFMM_TIME_TOTAL, st);
     const dim3 g1(lf_blocks(n, 256), (unsigned)nrhs);
     if (ctx->precision)

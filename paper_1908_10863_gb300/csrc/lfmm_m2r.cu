@@ -38,7 +38,6 @@ static inline int lf_blocks(int64_t n, int t) { return (int)((n + t - 1) / t); }
 #define R_T 256   // threads: 16 row groups x 16 column groups
 #define KEY_NONE 0xffffffffu
 
-__constant__ LfmmComp c_rcomp[LFMM_MAXCOMP];
 
 // key = comp (5 bits) | level (4 bits) | offset index (12 bits, offsets in [-7, 7]^3)
 #define R_OR 7
@@ -61,7 +60,8 @@ __host__ __device__ __forceinline__ void rkey_decode(uint32_t key, int& c, int& 
 // cells: lateral offsets are exact integers; the vertical offset of the
 // source's polarization image, (iz_t + 1/2) - s (iz_s + 1/2) - K, is an integer
 // on aligned levels (checked).
-__global__ void k_m2r_keys(int off, int nb, const int4* __restrict__ grid, const float4* __restrict__ lc,
+__global__ void k_m2r_keys(const LfmmComp* __restrict__ comps, int off, int nb, const int4* __restrict__ grid,
+                           const float4* __restrict__ lc,
                            const int* __restrict__ rbeg, const int* __restrict__ rend,
                            const uint32_t* __restrict__ rent, int level, uint32_t* __restrict__ keys,
                            uint32_t* __restrict__ vals, int* __restrict__ tgt, int* __restrict__ bad)
@@ -74,7 +74,7 @@ __global__ void k_m2r_keys(int off, int nb, const int4* __restrict__ grid, const
         uint32_t v = rent[e];
         int c = (int)(v >> LFMM_ENT_SHIFT);
         int s = (int)(v & LFMM_ENT_MASK);
-        const LfmmComp& cp = c_rcomp[c];
+        const LfmmComp& cp = comps[c];
         const int4 gs = grid[s];
         const float4 k = lc[c * 16 + level];
         const float vz = ((float)gt.z + 0.5f) - (float)cp.s * ((float)gs.z + 0.5f) - k.x;
@@ -108,7 +108,8 @@ __global__ void k_key_starts(const uint32_t* __restrict__ keys, int n, const int
 // One Sommerfeld table per (component, level, rho^2, oz): the table depends on
 // the lateral distance only; the azimuth enters through the phases applied
 // when the operator is assembled.
-__global__ void k_m2r_tables(const int4* __restrict__ tdesc, int ntab, const double* __restrict__ levelh, int P,
+__global__ void k_m2r_tables(const LfmmComp* __restrict__ comps, const int4* __restrict__ tdesc, int ntab,
+                             const double* __restrict__ levelh, int P,
                              const double* __restrict__ gt, const double* __restrict__ gw, int Q,
                              double* __restrict__ tables)
 {
@@ -120,7 +121,7 @@ __global__ void k_m2r_tables(const int4* __restrict__ tdesc, int ntab, const dou
     const int k = blockIdx.x;
     const int4 d = tdesc[k];
     const int c = d.x, l = d.y, oz = d.w;
-    const LfmmComp& cp = c_rcomp[c];
+    const LfmmComp cp = comps[c];
     const double rho = sqrt((double)d.z);
     const double zz = (cp.a == 1) ? (double)oz : (double)(-oz);
     for (int j = threadIdx.x; j < TT; j += blockDim.x) sT[j] = 0.0;
@@ -172,7 +173,6 @@ LfErr lf_prepare_m2r(lfmm_ctx* ctx, cudaStream_t st)
     }
     if (first < 0) return LfErr();
     const int ne = (int)(last - first);
-    LF_CHECK(cudaMemcpyToSymbolAsync(c_rcomp, ctx->comp, sizeof(LfmmComp) * ctx->ncomp, 0, cudaMemcpyHostToDevice, st));
     LF_TRY(lf_reserve(ctx->m2r_keys, (size_t)ne * 4 + 16));
     LF_TRY(lf_reserve(ctx->m2r_order, (size_t)ne * 4 + 16));
     LF_TRY(lf_reserve(ctx->m2r_tgt, (size_t)ctx->m2r_total * 4 + 16));
@@ -185,7 +185,7 @@ LfErr lf_prepare_m2r(lfmm_ctx* ctx, cudaStream_t st)
         const LfmmLevel& lv = ctx->levels[l];
         if (lv.nbox == 0 || lv.m2r_count == 0) continue;
         ++ctx->launches, k_m2r_keys<<<lf_blocks(lv.nbox, 128), 128, 0, st>>>(
-            lv.off, lv.nbox, ctx->box_grid.as<int4>(), ctx->level_consts.as<float4>(), ctx->m2r_off.as<int>(),
+            ctx->comp_dev.as<LfmmComp>(), lv.off, lv.nbox, ctx->box_grid.as<int4>(), ctx->level_consts.as<float4>(), ctx->m2r_off.as<int>(),
             ctx->m2r_off.as<int>() + ctx->nbox_total, ctx->m2r_ent.as<uint32_t>(), l, keys - first, vals - first,
             ctx->m2r_tgt.as<int>(), bad);
     }
@@ -247,7 +247,7 @@ LfErr lf_prepare_m2r(lfmm_ctx* ctx, cudaStream_t st)
     LF_CHECK(cudaMemcpyAsync(ctx->m2r_levelh.ptr, hl, sizeof(double) * 16, cudaMemcpyHostToDevice, st));
     size_t sm = sizeof(double) * ((size_t)TT + 2 * (size_t)Q * TS);
     LF_CHECK(cudaFuncSetAttribute(k_m2r_tables, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    ++ctx->launches, k_m2r_tables<<<ntab, 128, sm, st>>>(ctx->m2r_tdesc.as<int4>(), ntab,
+    ++ctx->launches, k_m2r_tables<<<ntab, 128, sm, st>>>(ctx->comp_dev.as<LfmmComp>(), ctx->m2r_tdesc.as<int4>(), ntab,
                                                          ctx->m2r_levelh.as<double>(), P, ctx->gl_t_m2l.as<double>(),
                                                          ctx->gl_w_m2l.as<double>(), Q, ctx->m2r_tables.as<double>());
     LF_TRY(lf_cuda(cudaGetLastError(), "m2r tables"));
@@ -285,6 +285,7 @@ struct RGemmArgs {
     const void* M;
     void* L;
     size_t stride;          // expansions per right-hand side (blockIdx.y), in elements
+    const LfmmComp* comps;  // the context's components
 };
 
 template <typename R>
@@ -322,7 +323,7 @@ __global__ void __launch_bounds__(R_T) k_m2r_gemm(RGemmArgs g)
     int c, lev, ox, oy, oz;
     rkey_decode(g.kval[kidx], c, lev, ox, oy, oz);
     (void)oz;
-    const LfmmComp& cp = c_rcomp[c];
+    const LfmmComp& cp = g.comps[c];
     const double phi = (ox == 0 && oy == 0) ? 0.0 : atan2((double)oy, (double)ox);
     if (tid < TS) {
         double sn, cs;
@@ -444,7 +445,7 @@ static LfErr m2r_apply_t(lfmm_ctx* ctx, cudaStream_t st)
     g.M = ctx->Mexp.ptr;
     g.L = ctx->Lexp.ptr;
     g.stride = (size_t)ctx->nbox_total * g.nc;
-    LF_CHECK(cudaMemcpyToSymbolAsync(c_rcomp, ctx->comp, sizeof(LfmmComp) * ctx->ncomp, 0, cudaMemcpyHostToDevice, st));
+    g.comps = ctx->comp_dev.as<LfmmComp>();
     switch (ctx->m2l_rm) {
     case 2: return launch_rgemm<R, 2>(ctx, st, g);
     case 4: return launch_rgemm<R, 4>(ctx, st, g);

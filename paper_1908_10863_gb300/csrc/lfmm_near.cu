@@ -31,9 +31,6 @@
 
 static inline int lf_blocks(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
-__constant__ LfmmComp c_ncomp[LFMM_MAXCOMP];
-__constant__ double c_gl_t[LFMM_QMAX];
-__constant__ double c_gl_w[LFMM_QMAX];
 
 struct P2PArgs {
     int leaf_off;
@@ -52,6 +49,9 @@ struct P2PArgs {
     int64_t qstride;  // charges per right-hand side (n)
     int nr;           // right-hand sides of this launch (<= the kernel's batch)
     int Qn;
+    const LfmmComp* comps;  // the context's components
+    const double* gl_t;     // near-field quadrature rule (Qn nodes and weights)
+    const double* gl_w;
     LfmmSurrView sv;  // learned near-field kernels (sv.ready = 0: quadrature only)
 };
 
@@ -112,13 +112,13 @@ __device__ __forceinline__ void p2p_free_add(R dx, R dy, R dz, const R* qs, int 
 // Reaction kernels of one pair by the quadrature (once), applied to the batch.
 template <typename R, int RB, typename S>
 __device__ __forceinline__ void p2p_reaction_add(const LfmmComp& cp, R dx, R dy, R dz, const R* qs, int qsk, int nr,
-                                                 int Qn, P2PAccT<S, RB>& A)
+                                                 int Qn, const double* gl_t, const double* gl_w, P2PAccT<S, RB>& A)
 {
     typedef LfMath<R> F;
     R h = (cp.a == 1) ? dz : -dz;
     R rho = F::Sqrt(dx * dx + dy * dy);
     R k00, k10, k11;
-    lf_reaction_pair<R>(cp, rho, h, Qn, c_gl_t, c_gl_w, k00, k10, k11);
+    lf_reaction_pair<R>(cp, rho, h, Qn, gl_t, gl_w, k00, k10, k11);
     const R k10s = (cp.a == 1) ? k10 : -k10;
     const R g = rho > R(0) ? k11 / rho : R(0);
 #pragma unroll
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(P2P_T) k_p2p(P2PArgs a)
             const uint32_t ent = a.nent[e];
             const int c = (int)(ent >> LFMM_ENT_SHIFT);
             const int s = (int)(ent & LFMM_ENT_MASK);
-            const LfmmComp& cp = c_ncomp[c];
+            const LfmmComp& cp = a.comps[c];
             const int sb = a.pbeg[s], se = a.pend[s];
             for (int cb = sb; cb < se; cb += P2P_T) {
                 const int j = cb + tid;
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(P2P_T) k_p2p(P2PArgs a)
                 } else {
                     for (int u = 0; u < cnt; ++u)
                         p2p_reaction_add<R, RB>(cp, xi - sx[u], yi - sy[u], zi - sz[u], &sq[0][u], P2P_T, a.nr,
-                                                a.Qn, A);
+                                                a.Qn, a.gl_t, a.gl_w, A);
                 }
             }
         }
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(32 * PW_WARPS) k_p2p_warp(P2PArgs a, const flo
             const uint32_t ent = a.nent[e];
             const int c = (int)(ent >> LFMM_ENT_SHIFT);
             const int s = (int)(ent & LFMM_ENT_MASK);
-            const LfmmComp& cp = c_ncomp[c];
+            const LfmmComp& cp = a.comps[c];
             const LfD4 cs = a.cen[s];
             // source box centre (free) or its polarization image (reaction), relative to the target box
             const float dx0 = (float)(cs.x - ct.x), dy0 = (float)(cs.y - ct.y);
@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(32 * PW_WARPS) k_p2p_warp(P2PArgs a, const flo
                 } else {
                     for (int u = 0; u < cnt; ++u)
                         p2p_reaction_add<float, RB>(cp, xi - sx[w][u], yi - sy[w][u], zi - sz[w][u], &sq[w][0][u],
-                                                    32, a.nr, a.Qn, part);
+                                                    32, a.nr, a.Qn, a.gl_t, a.gl_w, part);
                 }
             }
             p2p_flush<float, RB>(part, A);
@@ -314,7 +314,8 @@ LfErr lf_near_prepare(lfmm_ctx* ctx, cudaStream_t st)
 template <typename R>
 __device__ __forceinline__ void p2p_drain(const LfmmComp& cp, const uint16_t* qe, int count, int lane, int wbase,
                                           const R* tx, const R* ty, const R* tz, const R* sx, const R* sy,
-                                          const R* sz, const R* sq, R (*acc)[4], int Qn)
+                                          const R* sz, const R* sq, R (*acc)[4], int Qn, const double* gl_t,
+                                          const double* gl_w)
 {
     typedef LfMath<R> F;
     if (lane >= count) return;
@@ -324,7 +325,7 @@ __device__ __forceinline__ void p2p_drain(const LfmmComp& cp, const uint16_t* qe
     R h = (cp.a == 1) ? dz : -dz;
     R rho = F::Sqrt(dx * dx + dy * dy);
     R k00, k10, k11;
-    lf_reaction_pair<R>(cp, rho, h, Qn, c_gl_t, c_gl_w, k00, k10, k11);
+    lf_reaction_pair<R>(cp, rho, h, Qn, gl_t, gl_w, k00, k10, k11);
     R qs = sq[u];
     atomicAdd(&acc[o][0], qs * k00);
     atomicAdd(&acc[o][3], (cp.a == 1) ? qs * k10 : -qs * k10);
@@ -369,7 +370,7 @@ __global__ void __launch_bounds__(P2P_T) k_p2p_net(P2PArgs a)
             const uint32_t ent = a.nent[e];
             const int c = (int)(ent >> LFMM_ENT_SHIFT);
             const int s = (int)(ent & LFMM_ENT_MASK);
-            const LfmmComp& cp = c_ncomp[c];
+            const LfmmComp& cp = a.comps[c];
             const int sb = a.pbeg[s], se = a.pend[s];
             const bool use_net = !cp.is_free && a.sv.meta[c].trained;
             LfmmSurrMeta sm;
@@ -404,7 +405,7 @@ __global__ void __launch_bounds__(P2P_T) k_p2p_net(P2PArgs a)
                             p2p_free_add<R, 1>(xi - sx[u], yi - sy[u], zi - sz[u], &sq[u], 0, 1, A);
                     } else {
                         for (int u = 0; u < cnt; ++u)
-                            p2p_reaction_add<R, 1>(cp, xi - sx[u], yi - sy[u], zi - sz[u], &sq[u], 0, 1, a.Qn, A);
+                            p2p_reaction_add<R, 1>(cp, xi - sx[u], yi - sy[u], zi - sz[u], &sq[u], 0, 1, a.Qn, a.gl_t, a.gl_w, A);
                         n_quad += cnt;
                     }
                     continue;
@@ -445,14 +446,14 @@ __global__ void __launch_bounds__(P2P_T) k_p2p_net(P2PArgs a)
                         if (qn >= 32) {
                             __syncwarp();
                             qn -= 32;
-                            p2p_drain<R>(cp, &qbuf[wid][qn], 32, lane, wbase, tx, ty, tz, sx, sy, sz, sq, acc, a.Qn);
+                            p2p_drain<R>(cp, &qbuf[wid][qn], 32, lane, wbase, tx, ty, tz, sx, sy, sz, sq, acc, a.Qn, a.gl_t, a.gl_w);
                             __syncwarp();
                         }
                     }
                 }
                 if (qn > 0) {
                     __syncwarp();
-                    p2p_drain<R>(cp, &qbuf[wid][0], qn, lane, wbase, tx, ty, tz, sx, sy, sz, sq, acc, a.Qn);
+                    p2p_drain<R>(cp, &qbuf[wid][0], qn, lane, wbase, tx, ty, tz, sx, sy, sz, sq, acc, a.Qn, a.gl_t, a.gl_w);
                     __syncwarp();
                 }
             }
@@ -475,19 +476,8 @@ __global__ void __launch_bounds__(P2P_T) k_p2p_net(P2PArgs a)
     }
 }
 
-static LfErr upload_consts(lfmm_ctx* ctx, cudaStream_t st)
-{
-    LF_CHECK(cudaMemcpyToSymbolAsync(c_ncomp, ctx->comp, sizeof(LfmmComp) * ctx->ncomp, 0, cudaMemcpyHostToDevice, st));
-    LF_CHECK(cudaMemcpyToSymbolAsync(c_gl_t, ctx->gl_t_near.ptr, sizeof(double) * ctx->gl_q_near, 0,
-                                     cudaMemcpyDeviceToDevice, st));
-    LF_CHECK(cudaMemcpyToSymbolAsync(c_gl_w, ctx->gl_w_near.ptr, sizeof(double) * ctx->gl_q_near, 0,
-                                     cudaMemcpyDeviceToDevice, st));
-    return LfErr();
-}
-
 LfErr lf_near_field(lfmm_ctx* ctx, cudaStream_t st)
 {
-    LF_TRY(upload_consts(ctx, st));
     const LfmmLevel& leaf = ctx->levels[ctx->depth];
     P2PArgs a;
     a.leaf_off = leaf.off;
@@ -504,6 +494,9 @@ LfErr lf_near_field(lfmm_ctx* ctx, cudaStream_t st)
     a.phi = ctx->phi_near.as<double>();
     a.fld = ctx->fld_near.as<double>();
     a.Qn = ctx->gl_q_near;
+    a.comps = ctx->comp_dev.as<LfmmComp>();
+    a.gl_t = ctx->gl_t_near.as<double>();
+    a.gl_w = ctx->gl_w_near.as<double>();
     LF_TRY(lf_reserve(ctx->surr_counters, 64));
     LF_CHECK(cudaMemsetAsync(ctx->surr_counters.ptr, 0, 16, st));
     LF_TRY(lf_surrogate_device_view(ctx, &a.sv));
@@ -587,13 +580,14 @@ LfErr lf_sommerfeld_tables_dev(lfmm_ctx* ctx, int comp, int npts, const double* 
     return lf_cuda(cudaGetLastError(), "sommerfeld tables");
 }
 
-__global__ void k_reaction_kernel(int comp, int npts, const double* __restrict__ rho, const double* __restrict__ h,
-                                  int Q, double* __restrict__ out)
+__global__ void k_reaction_kernel(const LfmmComp* __restrict__ comps, const double* __restrict__ gl_t,
+                                  const double* __restrict__ gl_w, int comp, int npts, const double* __restrict__ rho,
+                                  const double* __restrict__ h, int Q, double* __restrict__ out)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= npts) return;
     double k00, k10, k11;
-    lf_reaction_pair<double>(c_ncomp[comp], rho[i], h[i], Q, c_gl_t, c_gl_w, k00, k10, k11);
+    lf_reaction_pair<double>(comps[comp], rho[i], h[i], Q, gl_t, gl_w, k00, k10, k11);
     out[3 * (size_t)i] = k00;
     out[3 * (size_t)i + 1] = k10;
     out[3 * (size_t)i + 2] = k11;
@@ -601,8 +595,9 @@ __global__ void k_reaction_kernel(int comp, int npts, const double* __restrict__
 
 LfErr lf_reaction_kernel_dev(lfmm_ctx* ctx, int comp, int npts, const double* rho, const double* h, double* out)
 {
-    LF_TRY(upload_consts(ctx, ctx->s_main));
-    ++ctx->launches, k_reaction_kernel<<<lf_blocks(npts, 128), 128, 0, ctx->s_main>>>(comp, npts, rho, h, ctx->gl_q_near, out);
+    ++ctx->launches, k_reaction_kernel<<<lf_blocks(npts, 128), 128, 0, ctx->s_main>>>(
+        ctx->comp_dev.as<LfmmComp>(), ctx->gl_t_near.as<double>(), ctx->gl_w_near.as<double>(), comp, npts, rho, h,
+        ctx->gl_q_near, out);
     return lf_cuda(cudaGetLastError(), "reaction kernel");
 }
 
@@ -689,9 +684,10 @@ extern "C" lfmm_status lfmm_reaction_kernel_noalloc(lfmm_ctx* ctx, int l, int lp
     cudaStream_t st = ctx->s_main;
     if (e.empty()) e = lf_cuda(cudaMemcpyAsync(drho, rho, sizeof(double) * npts, cudaMemcpyHostToDevice, st), "copy");
     if (e.empty()) e = lf_cuda(cudaMemcpyAsync(dh, h, sizeof(double) * npts, cudaMemcpyHostToDevice, st), "copy");
-    if (e.empty()) e = upload_consts(ctx, st);
     if (e.empty()) {
-        ++ctx->launches, k_reaction_kernel<<<lf_blocks(npts, 128), 128, 0, st>>>(c, npts, drho, dh, ctx->gl_q_near, dout);
+        ++ctx->launches, k_reaction_kernel<<<lf_blocks(npts, 128), 128, 0, st>>>(
+            ctx->comp_dev.as<LfmmComp>(), ctx->gl_t_near.as<double>(), ctx->gl_w_near.as<double>(), c, npts, drho, dh,
+            ctx->gl_q_near, dout);
         e = lf_cuda(cudaGetLastError(), "reaction kernel");
     }
     if (e.empty())

@@ -401,15 +401,19 @@ __global__ void k_centers(const uint32_t* __restrict__ bkey, int off, int nb, in
 // ---------------------------------------------------------------------------
 // Lists.
 // ---------------------------------------------------------------------------
-__constant__ LfmmComp c_tree_comp[LFMM_MAXCOMP];
-// per (component, level), in units of the level's box size h, with the box
+// The medium as the list kernels see it: the context's components and, per
+// (component, level), in units of the level's box size h, with the box
 // centre of grid cell i at origin + (i + 1/2) h:
 //   K = (o + (s - 1) oz) / h    so that (z_t - z'') / h = (iz_t + 1/2) - s (iz_s + 1/2) - K,
 //   F = (iface - oz) / h        so that (z_t - iface) / h = (iz_t + 1/2) - F,
 //   G = (s oz + o - iface) / h  so that (z'' - iface) / h = s (iz_s + 1/2) + G,
 //   Z = zeta_r / h
-__constant__ float4 c_tree_lc[LFMM_MAXCOMP * 16];
-__constant__ int c_tree_sep;  // 1: also require a centre distance of sqrt(6) boxes
+// (lc[c * 16 + level]); sep = 1 also requires a centre distance of sqrt(6) boxes.
+struct LfListMedium {
+    const LfmmComp* comps;
+    const float4* lc;
+    int sep;
+};
 
 // Far-field admissibility of a (target box, source box) pair of one level, in
 // grid units.  Free space: not neighbours (|di|_inf >= 2).  Reaction: the
@@ -418,12 +422,12 @@ __constant__ int c_tree_sep;  // 1: also require a centre distance of sqrt(6) bo
 // At levels where interfaces are grid planes the tested quantities are
 // integers or half-integers, so single precision decides them exactly; the
 // small margin on the 2h test only matters on coarser levels.
-__device__ __forceinline__ bool lf_admissible(const LfmmComp& c, float4 k, int4 gt, int4 gs)
+__device__ __forceinline__ bool lf_admissible(const LfmmComp& c, float4 k, int sep, int4 gt, int4 gs)
 {
     const int ix = abs(gt.x - gs.x), iy = abs(gt.y - gs.y);
     if (c.is_free) {
         const int iz = abs(gt.z - gs.z);
-        if (c_tree_sep && ix * ix + iy * iy + iz * iz < 6) return false;
+        if (sep && ix * ix + iy * iy + iz * iz < 6) return false;
         return max(ix, max(iy, iz)) >= 2;
     }
     const float s = (float)c.s;
@@ -431,7 +435,7 @@ __device__ __forceinline__ bool lf_admissible(const LfmmComp& c, float4 k, int4 
     const float uz = zt - zs - k.x;
     const float ux = (float)ix, uy = (float)iy;
     if (fmaxf(ux, fmaxf(uy, fabsf(uz))) < 2.0f - 1e-3f) return false;
-    if (c_tree_sep && ux * ux + uy * uy + uz * uz < 6.0f - 1e-3f) return false;
+    if (sep && ux * ux + uy * uy + uz * uz < 6.0f - 1e-3f) return false;
     const float tside = zt - k.y, pside = zs + k.z;
     if (c.a == 1) {
         if (!(tside > 0.f && pside < 0.f)) return false;
@@ -447,7 +451,7 @@ __device__ __forceinline__ bool lf_admissible(const LfmmComp& c, float4 k, int4 
 // entries) are taken 32 at a time as 4 entries x 8 child slots; admissible
 // ones are counted (count pass) or written in candidate order through a
 // ballot prefix (fill pass), so the lists are deterministic.
-__global__ void k_list_pass(int level_off, int nb, int level, const int* __restrict__ parent,
+__global__ void k_list_pass(LfListMedium med, int level_off, int nb, int level, const int* __restrict__ parent,
                             const int* __restrict__ cbeg, const int* __restrict__ cend,
                             const int4* __restrict__ grid, const int* __restrict__ pnear_beg,
                             const int* __restrict__ pnear_end, const uint32_t* __restrict__ near_ent_in,
@@ -487,9 +491,9 @@ __global__ void k_list_pass(int level_off, int nb, int level, const int* __restr
             const int ch = cbeg[s] + k;
             if (ch < cend[s]) {
                 sc = ch;
-                const LfmmComp& cp = c_tree_comp[c];
+                const LfmmComp& cp = med.comps[c];
                 v = ((uint32_t)c << LFMM_ENT_SHIFT) | (uint32_t)sc;
-                if (lf_admissible(cp, c_tree_lc[c * 16 + level], gt, grid[sc]))
+                if (lf_admissible(cp, med.lc[c * 16 + level], med.sep, gt, grid[sc]))
                     kind = cp.is_free ? 0 : 1;
                 else
                     kind = 2;
@@ -544,7 +548,7 @@ __global__ void k_set_ranges(int level_off, int nb, const int* __restrict__ off,
 }
 
 // particle-pair statistics of the leaf-level near lists
-__global__ void k_p2p_stats(int level_off, int nb, const int* __restrict__ nbeg, const int* __restrict__ nend,
+__global__ void k_p2p_stats(const LfmmComp* __restrict__ comps, int level_off, int nb, const int* __restrict__ nbeg, const int* __restrict__ nend,
                             const uint32_t* __restrict__ ent, const int* __restrict__ pbeg,
                             const int* __restrict__ pend, unsigned long long* __restrict__ stat)
 {
@@ -558,7 +562,7 @@ __global__ void k_p2p_stats(int level_off, int nb, const int* __restrict__ nbeg,
         int c = (int)(v >> LFMM_ENT_SHIFT);
         int s = (int)(v & LFMM_ENT_MASK);
         unsigned long long ns = (unsigned long long)(pend[s] - pbeg[s]);
-        if (c_tree_comp[c].is_free) f += nt * ns; else r += nt * ns;
+        if (comps[c].is_free) f += nt * ns; else r += nt * ns;
     }
     if (f) atomicAdd(&stat[2], f);
     if (r) atomicAdd(&stat[3], r);
@@ -801,9 +805,6 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
                 lc[(size_t)c * 16 + l] = make_float4((float)((cp.o + (cp.s - 1.0) * oz) / h), (float)((cp.iface - oz) / h),
                                                      (float)((cp.s * oz + cp.o - cp.iface) / h), (float)(cp.zeta_r / h));
             }
-        LF_CHECK(cudaMemcpyToSymbolAsync(c_tree_lc, lc.data(), sizeof(float4) * lc.size(), 0, cudaMemcpyHostToDevice,
-                                         st));
-        LF_CHECK(cudaMemcpyToSymbolAsync(c_tree_sep, &ctx->sep_ext, sizeof(int), 0, cudaMemcpyHostToDevice, st));
         LF_TRY(lf_reserve(ctx->level_consts, sizeof(float4) * lc.size()));
         LF_CHECK(cudaMemcpyAsync(ctx->level_consts.ptr, lc.data(), sizeof(float4) * lc.size(), cudaMemcpyHostToDevice,
                                  st));
@@ -811,8 +812,7 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
     }
 
     // ---- lists ----
-    LF_CHECK(cudaMemcpyToSymbolAsync(c_tree_comp, ctx->comp, sizeof(LfmmComp) * ctx->ncomp, 0,
-                                     cudaMemcpyHostToDevice, st));
+    const LfListMedium med{ctx->comp_dev.as<LfmmComp>(), ctx->level_consts.as<float4>(), ctx->sep_ext};
     LF_TRY(lf_reserve(ctx->near_off, nb * 4 * 2));  // beg, end
     LF_TRY(lf_reserve(ctx->m2l_off, nb * 4 * 2));
     LF_TRY(lf_reserve(ctx->m2r_off, nb * 4 * 2));
@@ -880,7 +880,7 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
         LfmmLevel& lv = ctx->levels[l];
         const int n3 = lv.nbox;
         ++ctx->launches, k_list_pass<<<lf_blocks(n3, 4), 128, 0, st>>>(
-            lv.off, n3, l, par, cbeg, cend, ctx->box_grid.as<int4>(), nbeg, nend, ctx->near_ent.as<uint32_t>(), cnt3,
+            med, lv.off, n3, l, par, cbeg, cend, ctx->box_grid.as<int4>(), nbeg, nend, ctx->near_ent.as<uint32_t>(), cnt3,
             nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, nullptr);
         LF_TRY(lf_cuda(cudaGetLastError(), "list count"));
         // one exclusive scan over the three count arrays; the category bases
@@ -901,7 +901,7 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
         uint32_t* nent = ctx->near_ent.as<uint32_t>();
         // offsets are relative to the concatenated scan: shift the output pointers by each category's base
         ++ctx->launches, k_list_pass<<<lf_blocks(n3, 4), 128, 0, st>>>(
-            lv.off, n3, l, par, cbeg, cend, ctx->box_grid.as<int4>(), nbeg, nend, nent, cnt3, off3,
+            med, lv.off, n3, l, par, cbeg, cend, ctx->box_grid.as<int4>(), nbeg, nend, nent, cnt3, off3,
             ctx->m2l_ent.as<uint32_t>() + m2l_used, ctx->m2r_ent.as<uint32_t>() + m2r_used - b1,
             nent + near_used - b2, 1, stat, ctx->box_key.as<uint32_t>(), ctx->m2l_inv.as<int>(),
             (want_slots && l >= 2) ? ctx->m2l_slots.as<int>() : nullptr, slot_err);
@@ -926,7 +926,7 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
     ctx->m2l_total = m2l_used;
     {
         const LfmmLevel& lf = ctx->levels[depth];
-        ++ctx->launches, k_p2p_stats<<<lf_blocks(lf.nbox, 256), 256, 0, st>>>(lf.off, lf.nbox, nbeg, nend,
+        ++ctx->launches, k_p2p_stats<<<lf_blocks(lf.nbox, 256), 256, 0, st>>>(ctx->comp_dev.as<LfmmComp>(), lf.off, lf.nbox, nbeg, nend,
                                                               ctx->near_ent.as<uint32_t>(), pbeg, pend, stat);
         LF_TRY(lf_cuda(cudaGetLastError(), "p2p stats"));
     }
