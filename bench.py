@@ -80,6 +80,7 @@ def parse():
     ap.add_argument("--sample", type=int, default=256, help="oracle targets for the accuracy / CPU leg")
     ap.add_argument("--no-near", action="store_true", help="skip the near-interface workload")
     ap.add_argument("--no-multi", action="store_true", help="skip the many-charge-vector workload")
+    ap.add_argument("--no-batch", action="store_true", help="skip the many-problem workload")
     ap.add_argument("--accuracy-table", action="store_true",
                     help="instead of timing: Err2 against the oracle for each medium, N, p and precision")
     ap.add_argument("--forms", default="fp32_surrogate,fp32,fp64",
@@ -287,6 +288,62 @@ def multi_rhs_leg(torch, dev, p, flush, nrhs=64, n=1 << 18):
             "charges_x_vectors_per_s": w.n * nrhs / (t_batch / 1e3), "speedup": t_single / t_batch}
 
 
+def many_problems_leg(torch, dev, p, flush, k=48):
+    """Float32 form, k independent three-layer problems with log-uniform sizes
+    in [2k, 100k]: one CUDA graph replay per evaluation against the same
+    launches issued directly and against k one-at-a-time evaluations."""
+    from paper_1908_10863_gb300 import LayeredFMM, LayeredFMMBatch, workloads
+    import oracle
+    probs = workloads.uneven_problems(k)
+    ms = []
+    for w in probs:
+        f = LayeredFMM(w.d, w.eps, p, precision=1)
+        f.build(w.xyz, w.layer)
+        ms.append(f)
+    s = torch.cuda.current_stream()
+    out = {"workload": "%d independent three-layer problems (eps=(1,5,10), charges split between layers, "
+                       "q~U[-1,1]), N log-uniform in [2000, 100000] (total %d), p=%d, float32 form"
+                       % (k, sum(w.n for w in probs), p)}
+
+    def timed(fn, reps=5):
+        fn()
+        fn()  # direct run + capture, then one replay
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            fn()
+            b.record(s)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return sorted(ts)[len(ts) // 2]
+
+    total = sum(w.n for w in probs)
+    res = {}
+    for graph in (True, False):
+        b = LayeredFMMBatch(ms, graph=graph)
+        q = torch.from_numpy(b.concat([w.q for w in probs])).to(dev)
+        phi = torch.empty_like(q)
+        fld = torch.empty(3 * total, dtype=torch.float64, device=dev)
+        res[graph] = (timed(lambda: b.evaluate_device(q, phi, fld, s)), b.info(), phi.cpu().numpy())
+        b.close()
+    qd = [torch.from_numpy(w.q).to(dev) for w in probs]
+    pd = [torch.empty_like(x) for x in qd]
+    fd = [torch.empty((x.shape[0], 3), dtype=torch.float64, device=dev) for x in qd]
+    t_seq = timed(lambda: [m.evaluate_device(a, b_, c, s) for m, a, b_, c in zip(ms, qd, pd, fd)])
+    seq_phi = np.concatenate([x.cpu().numpy() for x in pd])
+    for m in ms:
+        m.close()
+    t_g, info, phi_g = res[True]
+    out.update({"graph_ms": t_g, "direct_ms": res[False][0], "one_at_a_time_ms": t_seq,
+                "particles_per_s": total / (t_g / 1e3), "speedup_vs_one_at_a_time": t_seq / t_g,
+                "graph_nodes": info["graph_nodes"], "kernel_nodes": info["kernel_nodes"],
+                "err2_phi_graph_vs_one_at_a_time": oracle.err2(seq_phi, phi_g)})
+    return out
+
+
 def accuracy_table(torch, dev):
     """Relative L2 errors (potential and field) of both forms against the CPU
     oracle (exact image series), one JSON line per case.  Small N: all
@@ -412,6 +469,9 @@ def main():
     multi = None
     if not args.no_multi and rank == 0:
         multi = multi_rhs_leg(torch, dev, args.p, flush)
+    many = None
+    if not args.no_batch and rank == 0:
+        many = many_problems_leg(torch, dev, args.p, flush)
 
     ms_max = allmax(pg, results[headline]["ms_per_step"])
     e2e_max = allmax(pg, results[headline]["e2e_s"])
@@ -484,6 +544,7 @@ def main():
         "clocks": clk,
         "near_interface": near,
         "multi_rhs": multi,
+        "many_problems": many,
     }
     print(json.dumps(line))
     barrier(pg)

@@ -107,6 +107,64 @@ const char* lfmm_last_error(const lfmm_ctx* ctx);
 /* Release every resource of ctx.  NULL is allowed. */
 void lfmm_destroy(lfmm_ctx* ctx);
 
+/* ---- many independent problems in one launch --------------------------- */
+
+/* A batch of k built contexts (independent problems: own geometry, own
+ * medium), evaluated together.  The paper evaluates one problem at a time;
+ * batching is a library interface for workloads of many uneven problems.
+ *   ctxs      : k distinct built contexts; they must outlive the batch.
+ *   nrhs      : charge vectors per problem (NULL: one each).
+ *   use_graph : 1 = capture the batch's launches once into a CUDA graph and
+ *               replay it (one cudaGraphLaunch per evaluation, the problems'
+ *               kernels as concurrent graph branches); 0 = launch them
+ *               directly every time, on the same concurrent streams.
+ * Charges, potentials and fields are concatenated over the problems:
+ * problem i occupies [off_i, off_{i+1}) of q and phi ([nrhs_i][n_i] inside,
+ * charges in that context's input order) and [3 off_i, 3 off_{i+1}) of the
+ * field (lfmm_batch_offsets gives off).
+ * Rebuilding a member or changing one of its options is allowed: the next
+ * evaluation sees the changed serial of that context, runs directly once and
+ * captures again.  Members must not be evaluated on their own while a batch
+ * evaluation is in flight, and must not have profiling on (LFMM_ESTATE). */
+typedef struct lfmm_batch lfmm_batch;
+lfmm_status lfmm_batch_create(lfmm_ctx* const* ctxs, int k, const int* nrhs, int use_graph, lfmm_batch** out);
+
+/* off[0..k]: prefix sums of n_i * nrhs_i (host array of k + 1 entries). */
+lfmm_status lfmm_batch_offsets(const lfmm_batch* b, int64_t* off);
+
+/* Evaluate every problem from device arrays (float64, layout above), ordered
+ * on cuda_stream.  Returns once the work is enqueued, except on the first
+ * call and after a member changed: that call launches directly, waits for it
+ * (these launches size every buffer) and captures the graph for the next
+ * calls.  Different array addresses than at capture time trigger a new
+ * capture (no direct run).  field_dev may be NULL. */
+lfmm_status lfmm_batch_evaluate_device(lfmm_batch* b, const double* q_dev, double* phi_dev, double* field_dev,
+                                       void* cuda_stream);
+
+/* Same with host arrays: copies in, evaluates, copies out and checks every
+ * problem's bounded device waits (LFMM_ETIMEOUT if one ran out). */
+lfmm_status lfmm_batch_evaluate(lfmm_batch* b, const double* q, double* phi, double* field);
+
+/* Counters (host array of up to LFMM_BATCH_INFO_COUNT int64). */
+enum {
+    LFMM_BATCH_PROBLEMS = 0,
+    LFMM_BATCH_CHARGES = 1,        /* sum of n_i * nrhs_i */
+    LFMM_BATCH_GRAPH_NODES = 2,    /* nodes of the captured graph (0 if none) */
+    LFMM_BATCH_KERNEL_NODES = 3,   /* of which kernel launches */
+    LFMM_BATCH_CAPTURES = 4,
+    LFMM_BATCH_GRAPH_LAUNCHES = 5,
+    LFMM_BATCH_DIRECT_RUNS = 6,
+    LFMM_BATCH_TIMEOUTS = 7,       /* device waits that ran out in the last evaluation (synchronises) */
+    LFMM_BATCH_INFO_COUNT = 8
+};
+lfmm_status lfmm_batch_info(lfmm_batch* b, int64_t* out, int nout);
+
+/* Message of the last failed batch call ("" if none). */
+const char* lfmm_batch_last_error(const lfmm_batch* b);
+
+/* Release the batch (not its contexts).  NULL is allowed. */
+void lfmm_batch_destroy(lfmm_batch* b);
+
 /* ---- inspection and measurement --------------------------------------- */
 
 /* Counters of the current build (host array of at least LFMM_STAT_COUNT

@@ -3,4 +3,4 @@
 ``LayeredFMM`` wraps the C ABI of ``include/lfmm.h``; all work runs in the
 CUDA library built from ``csrc/``.
 """
-from .lfmm import LayeredFMM, LfmmError, gauss_laguerre, load  # noqa: F401
+from .lfmm import LayeredFMM, LayeredFMMBatch, LfmmError, gauss_laguerre, load  # noqa: F401

@@ -544,10 +544,19 @@ lfmm_status lfmm_create(const double* d, int L, const double* eps, int p, lfmm_c
     return LFMM_OK;
 }
 
+static lfmm_status set_option(lfmm_ctx* ctx, int opt, double v);
+
 lfmm_status lfmm_set_option(lfmm_ctx* ctx, int opt, double v)
 {
     if (!ctx) return LFMM_EINVAL;
     ctx->err.clear();
+    const lfmm_status s = set_option(ctx, opt, v);
+    if (s == LFMM_OK) ++ctx->serial;
+    return s;
+}
+
+static lfmm_status set_option(lfmm_ctx* ctx, int opt, double v)
+{
     switch (opt) {
     case LFMM_OPT_PRECISION:
         if (v != 0.0 && v != 1.0) return fail(ctx, "EINVAL: precision must be 0 or 1");
@@ -600,6 +609,7 @@ static lfmm_status build_common(lfmm_ctx* ctx, int64_t n, const double* xyz_dev,
     if (ctx->profile) prof_collect(ctx, false);
     prof_reset(ctx);
     ctx->built = true;
+    ++ctx->serial;
     return LFMM_OK;
 }
 
@@ -643,7 +653,9 @@ lfmm_status lfmm_build_device(lfmm_ctx* ctx, int64_t n, const double* xyz_dev, c
     return build_common(ctx, n, xyz_dev, layer_dev);
 }
 
-static lfmm_status eval_common(lfmm_ctx* ctx, int nrhs, const double* q_dev, double* phi_dev, double* fld_dev)
+}  // extern "C"
+
+lfmm_status lf_eval_enqueue(lfmm_ctx* ctx, int nrhs, const double* q_dev, double* phi_dev, double* fld_dev)
 {
     const int64_t n = ctx->n;
     prof_reset(ctx);
@@ -657,6 +669,8 @@ static lfmm_status eval_common(lfmm_ctx* ctx, int nrhs, const double* q_dev, dou
     }
     return LFMM_OK;
 }
+
+extern "C" {
 
 lfmm_status lfmm_evaluate(lfmm_ctx* ctx, int nrhs, const double* q, double* phi, double* field)
 {
@@ -673,7 +687,7 @@ lfmm_status lfmm_evaluate(lfmm_ctx* ctx, int nrhs, const double* q, double* phi,
     if (!e.empty()) return fail(ctx, e);
     cudaError_t ce = cudaMemcpyAsync(ctx->q_stage.ptr, q, (size_t)n * nrhs * 8, cudaMemcpyHostToDevice, ctx->s_main);
     if (ce != cudaSuccess) return fail(ctx, lf_cuda(ce, "copy charges"));
-    lfmm_status s = eval_common(ctx, nrhs, ctx->q_stage.as<double>(), ctx->phi_stage.as<double>(),
+    lfmm_status s = lf_eval_enqueue(ctx, nrhs, ctx->q_stage.as<double>(), ctx->phi_stage.as<double>(),
                                 field ? ctx->fld_stage.as<double>() : nullptr);
     if (s != LFMM_OK) {
         cudaStreamSynchronize(ctx->s_main);
@@ -704,7 +718,7 @@ lfmm_status lfmm_evaluate_device(lfmm_ctx* ctx, int nrhs, const double* q_dev, d
     cudaError_t ce = cudaEventRecord(ctx->ev_fork, us);
     if (ce == cudaSuccess) ce = cudaStreamWaitEvent(ctx->s_main, ctx->ev_fork, 0);
     if (ce != cudaSuccess) return fail(ctx, lf_cuda(ce, "stream order"));
-    lfmm_status s = eval_common(ctx, nrhs, q_dev, phi_dev, field_dev);
+    lfmm_status s = lf_eval_enqueue(ctx, nrhs, q_dev, phi_dev, field_dev);
     if (s != LFMM_OK) return s;
     ce = cudaEventRecord(ctx->ev_join, ctx->s_main);
     if (ce == cudaSuccess) ce = cudaStreamWaitEvent(us, ctx->ev_join, 0);
@@ -835,6 +849,7 @@ lfmm_status lfmm_surrogate_train(lfmm_ctx* ctx, int64_t nsamples, int epochs, ui
     ctx->err.clear();
     prof_reset(ctx);
     LfErr e = lf_surrogate_train(ctx, nsamples, epochs, seed);
+    ++ctx->serial;
     if (!e.empty()) {
         cudaStreamSynchronize(ctx->s_main);
         return fail(ctx, e);
@@ -898,6 +913,7 @@ lfmm_status lfmm_surrogate_set_params(lfmm_ctx* ctx, int l, int lp, int a, int b
         e = lf_cuda(cudaMemcpyAsync(ctx->surr_theta.as<float>() + (size_t)c * LFMM_SURR_NP, theta, LFMM_SURR_NP * 4, cudaMemcpyHostToDevice, ctx->s_main), "copy params");
     if (e.empty()) e = lf_surrogate_pack(ctx, c);
     if (e.empty()) e = lf_cuda(cudaStreamSynchronize(ctx->s_main), "pack");
+    ++ctx->serial;
     return fail(ctx, e);
 }
 

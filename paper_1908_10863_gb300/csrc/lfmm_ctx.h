@@ -45,6 +45,9 @@ struct lfmm_ctx {
     int quad_nodes_near = 32;
     int near_pole = 0;  // density denominator has a real zero in (0, 1.5]
     std::string err;
+    // bumped by every successful build, option change and surrogate update:
+    // a captured evaluation is valid only for the serial it was captured at
+    uint64_t serial = 0;
 
     // components
     int ncomp = 0;
@@ -178,6 +181,9 @@ LfErr lf_radix_sort(lfmm_ctx* ctx, uint32_t* keys, uint32_t* vals, int64_t n, cu
 // ---- evaluation (lfmm_fmm.cu, lfmm_near.cu) ----
 LfErr lf_evaluate_sorted(lfmm_ctx* ctx, int nrhs, const double* q_dev, double* phi_dev, double* field_dev,
                          cudaStream_t st);
+// enqueue nrhs evaluations on ctx->s_main (no host synchronisation, no
+// allocation once the buffers have grown to this size: capturable)
+lfmm_status lf_eval_enqueue(lfmm_ctx* ctx, int nrhs, const double* q_dev, double* phi_dev, double* fld_dev);
 // right-hand sides evaluated in one pass (larger requests are split)
 #define LFMM_RHS_BATCH 64
 #define LFMM_SEP_EXT_P 18

@@ -44,7 +44,11 @@ EXPORTED = ["lfmm_create", "lfmm_set_option", "lfmm_build", "lfmm_build_device",
             "lfmm_evaluate_device", "lfmm_last_error", "lfmm_destroy", "lfmm_get_stats", "lfmm_get_timings",
             "lfmm_sommerfeld_tables", "lfmm_reaction_kernel", "lfmm_reaction_kernel_noalloc", "lfmm_gauss_laguerre",
             "lfmm_surrogate_train", "lfmm_surrogate_info", "lfmm_surrogate_eval", "lfmm_surrogate_get_params",
-            "lfmm_surrogate_set_params", "lfmm_surrogate_forward", "lfmm_surrogate_loss_grad"]
+            "lfmm_surrogate_set_params", "lfmm_surrogate_forward", "lfmm_surrogate_loss_grad",
+            "lfmm_batch_create", "lfmm_batch_offsets", "lfmm_batch_evaluate_device", "lfmm_batch_evaluate",
+            "lfmm_batch_info", "lfmm_batch_last_error", "lfmm_batch_destroy"]
+BATCH_INFO = ["problems", "charges", "graph_nodes", "kernel_nodes", "captures", "graph_launches", "direct_runs",
+              "timeouts"]
 NOALLOC_MAX_POINTS = 65536
 
 
@@ -87,8 +91,17 @@ def load(build: bool = True):
     lib.lfmm_surrogate_set_params.argtypes = [_ctxp] + comp + [_fp]
     lib.lfmm_surrogate_forward.argtypes = [_ctxp] + comp + [ctypes.c_int, _fp, _fp]
     lib.lfmm_surrogate_loss_grad.argtypes = [_ctxp] + comp + [ctypes.c_int, _fp, _fp, _dp, _fp]
+    lib.lfmm_batch_create.argtypes = [ctypes.POINTER(_ctxp), ctypes.c_int, _ip, ctypes.c_int, ctypes.POINTER(_vp)]
+    lib.lfmm_batch_offsets.argtypes = [_vp, _lp]
+    lib.lfmm_batch_evaluate_device.argtypes = [_vp, _vp, _vp, _vp, _vp]
+    lib.lfmm_batch_evaluate.argtypes = [_vp, _dp, _dp, _dp]
+    lib.lfmm_batch_info.argtypes = [_vp, _lp, ctypes.c_int]
+    lib.lfmm_batch_last_error.argtypes = [_vp]
+    lib.lfmm_batch_last_error.restype = ctypes.c_char_p
+    lib.lfmm_batch_destroy.argtypes = [_vp]
+    lib.lfmm_batch_destroy.restype = None
     for name in EXPORTED:
-        if name not in ("lfmm_last_error", "lfmm_destroy"):
+        if name not in ("lfmm_last_error", "lfmm_destroy", "lfmm_batch_last_error", "lfmm_batch_destroy"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -286,3 +299,97 @@ class LayeredFMM:
 
     def __exit__(self, *a):
         self.close()
+
+
+class LayeredFMMBatch:
+    """Many built problems (``LayeredFMM`` objects) evaluated together: one
+    CUDA graph launch per evaluation when ``graph`` is true (see
+    ``lfmm_batch_create`` in include/lfmm.h).  The members must stay open
+    while the batch is used."""
+
+    def __init__(self, members, nrhs=None, graph: bool = True):
+        lib = load()
+        self._lib = lib
+        self.members = list(members)
+        k = len(self.members)
+        arr = (_ctxp * k)(*[m._ctx for m in self.members])
+        nr = None if nrhs is None else np.ascontiguousarray(nrhs, dtype=np.int32)
+        self.nrhs = [1] * k if nrhs is None else [int(v) for v in nr]
+        h = _vp()
+        st = lib.lfmm_batch_create(arr, k, _ptr(nr, _ip) if nr is not None else None, 1 if graph else 0,
+                                   ctypes.byref(h))
+        if st != OK:
+            raise LfmmError(st, "lfmm_batch_create")
+        self._b = h
+        off = np.zeros(k + 1, dtype=np.int64)
+        self._check(lib.lfmm_batch_offsets(self._b, _ptr(off, _lp)), "lfmm_batch_offsets")
+        self.offsets = off
+        self.total = int(off[-1])
+
+    def _check(self, st, what):
+        if st != OK:
+            msg = self._lib.lfmm_batch_last_error(self._b)
+            raise LfmmError(st, "%s: %s" % (what, msg.decode() if msg else ""))
+
+    def concat(self, qs):
+        """Per-problem charge arrays ([n_i] or [nrhs_i, n_i]) -> one concatenated host array."""
+        return np.concatenate([_f64(q).ravel() for q in qs])
+
+    def split(self, a, field=False):
+        out = []
+        for i, m in enumerate(self.members):
+            o0, o1 = int(self.offsets[i]), int(self.offsets[i + 1])
+            if field:
+                v = a[3 * o0:3 * o1].reshape(self.nrhs[i], m.n, 3)
+            else:
+                v = a[o0:o1].reshape(self.nrhs[i], m.n)
+            out.append(v[0] if self.nrhs[i] == 1 else v)
+        return out
+
+    def evaluate(self, qs, field: bool = True):
+        """qs: list of per-problem host charges -> (list of phi, list of E or None)."""
+        q = self.concat(qs)
+        if q.shape[0] != self.total:
+            raise ValueError("need %d charges in all, got %d" % (self.total, q.shape[0]))
+        phi = np.zeros(self.total)
+        fld = np.zeros(3 * self.total) if field else None
+        self._check(self._lib.lfmm_batch_evaluate(self._b, _ptr(q), _ptr(phi), _ptr(fld) if field else None),
+                    "lfmm_batch_evaluate")
+        return self.split(phi), (self.split(fld, True) if field else None)
+
+    def evaluate_host(self, q, phi, field=None):
+        """Concatenated host arrays (float64, e.g. pinned torch tensors' numpy views) in and out."""
+        self._check(self._lib.lfmm_batch_evaluate(self._b, _ptr(q), _ptr(phi),
+                                                  _ptr(field) if field is not None else None),
+                    "lfmm_batch_evaluate")
+
+    def evaluate_device(self, q, phi, field=None, stream=None):
+        """Concatenated float64 CUDA tensors: q, phi [total], field [3 total] or None."""
+        s = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+        self._check(self._lib.lfmm_batch_evaluate_device(self._b, ctypes.c_void_p(q.data_ptr()),
+                                                         ctypes.c_void_p(phi.data_ptr()),
+                                                         ctypes.c_void_p(field.data_ptr())
+                                                         if field is not None else None, s),
+                    "lfmm_batch_evaluate_device")
+
+    def info(self) -> dict:
+        out = np.zeros(len(BATCH_INFO), dtype=np.int64)
+        self._check(self._lib.lfmm_batch_info(self._b, _ptr(out, _lp), len(BATCH_INFO)), "lfmm_batch_info")
+        return {k: int(v) for k, v in zip(BATCH_INFO, out)}
+
+    def close(self):
+        if getattr(self, "_b", None):
+            self._lib.lfmm_batch_destroy(self._b)
+            self._b = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -20,6 +20,9 @@ library and for the CPU oracle alike.
   r(theta) = 0.5 - a + a P_4(cos theta), a = (0.1, 0.15, 0.05), centred at
   z = 0.6, -0.6, -1.8, eps = (21.2, 47.5, 62.8), by rejection from the
   bounding cube.
+* :func:`uneven_problems` -- k independent config2-shaped problems whose
+  sizes are log-uniform in [nmin, nmax] (the batched form's many uneven
+  problems), each with its own seed.
 Charges are uniform in [-1, 1].  Every generator uses numpy's PCG64 with
 seed 20190829 + config index unless a seed is given.
 """
@@ -113,6 +116,14 @@ def paper_p4(counts=(912, 640, 1296), seed: int | None = None) -> Workload:
     layer = np.concatenate(lay)
     q = rng.uniform(-1.0, 1.0, size=xyz.shape[0])
     return Workload("paper_p4_%d" % xyz.shape[0], np.array(D_CONFIG), np.array(EPS_PAPER), xyz, layer, q)
+
+
+def uneven_problems(k: int = 48, nmin: int = 2000, nmax: int = 100000, seed: int | None = None,
+                    eps=EPS_CONFIG) -> list:
+    rng = np.random.Generator(np.random.PCG64(SEED_BASE + 7 if seed is None else seed))
+    sizes = np.exp(rng.uniform(np.log(nmin), np.log(nmax), size=k)).astype(np.int64)
+    seeds = rng.integers(0, 2 ** 31, size=k)
+    return [config2(int(n), seed=int(sd), eps=eps) for n, sd in zip(sizes, seeds)]
 
 
 def subsample(n: int, count: int, seed: int = SEED_BASE + 3) -> np.ndarray:

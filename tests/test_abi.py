@@ -54,3 +54,15 @@ def test_gauss_laguerre_rule(Q):
 def test_gauss_laguerre_rejects_bad_order():
     with pytest.raises(binding.LfmmError):
         binding.gauss_laguerre(0)
+
+
+def test_batch_create_rejects_bad_arguments_without_a_device():
+    # argument checks come before any CUDA call
+    lib = binding.load()
+    h = ctypes.c_void_p()
+    assert lib.lfmm_batch_create(None, 3, None, 1, ctypes.byref(h)) == binding.EINVAL
+    assert lib.lfmm_batch_create((ctypes.c_void_p * 1)(None), 1, None, 1, ctypes.byref(h)) == binding.EINVAL
+    assert lib.lfmm_batch_create((ctypes.c_void_p * 1)(None), 0, None, 1, None) == binding.EINVAL
+    assert not h.value
+    lib.lfmm_batch_destroy(None)
+    assert lib.lfmm_batch_last_error(None) == b"null batch"
