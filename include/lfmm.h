@@ -57,8 +57,10 @@ enum {
     LFMM_OPT_QUAD_NODES = 4, /* Gauss-Laguerre nodes of the M2L remainder integrals (16..128, default 64) */
     LFMM_OPT_SURROGATE = 5,  /* 1 = near-field reaction kernels by the trained network (default 0) */
     LFMM_OPT_SURROGATE_TOL = 6, /* error estimate above which a pair falls back to quadrature (default 1e-6) */
-    LFMM_OPT_TENSOR_CORES = 7   /* 1 = float32 free M2L on the tensor cores (3xTF32) where (p+1)^2 <= 128
+    LFMM_OPT_TENSOR_CORES = 7,  /* 1 = float32 free M2L on the tensor cores (3xTF32) where (p+1)^2 <= 128
                                    (default); 0 = on the CUDA cores */
+    LFMM_OPT_P2P_SPLIT = 8      /* near list of a leaf shared by this many warps/blocks of the P2P kernels:
+                                   0 = chosen from the leaf count (default), else 1, 2, 4, 8 or 16 */
 };
 
 /* Create a context for the medium.
@@ -106,6 +108,26 @@ const char* lfmm_last_error(const lfmm_ctx* ctx);
 
 /* Release every resource of ctx.  NULL is allowed. */
 void lfmm_destroy(lfmm_ctx* ctx);
+
+/* ---- tuning ------------------------------------------------------------- */
+
+/* Pick the launch settings of this geometry by timing them on the device
+ * (CUDA events on the context's stream); the paper tunes nothing at run time,
+ * this is a library facility.  Coordinate search, in this order:
+ *   1. leaf capacity (tree depth) in {10, 20, 40, 80, 160};
+ *   2. float32 form with (p+1)^2 <= 128: free M2L on tensor cores or CUDA cores;
+ *   3. near-list split of the P2P kernels in {automatic, 1, 2, 4, 8, 16}.
+ * Each setting is timed as the median of `reps` (>= 1) evaluations of one
+ * charge vector (mode 0) or builds plus evaluations (mode 1), after one
+ * untimed run.  Afterwards the options hold the winner and ctx is built
+ * with it.
+ *   xyz, layer : host arrays as for lfmm_build.
+ *   report     : host [max_rows][LFMM_TUNE_COLS] or NULL: leaf capacity,
+ *                tensor cores, split, tree depth, milliseconds, 1 for the winner.
+ *   nrows      : rows written (may be NULL). */
+#define LFMM_TUNE_COLS 6
+lfmm_status lfmm_autotune(lfmm_ctx* ctx, int64_t n, const double* xyz, const int32_t* layer, int mode, int reps,
+                          double* report, int max_rows, int* nrows);
 
 /* ---- many independent problems in one launch --------------------------- */
 

@@ -583,6 +583,13 @@ static lfmm_status set_option(lfmm_ctx* ctx, int opt, double v)
     case LFMM_OPT_TENSOR_CORES:
         ctx->use_tc = (v != 0.0);
         return LFMM_OK;
+    case LFMM_OPT_P2P_SPLIT: {
+        const int k = (int)v;
+        if ((double)k != v || k < 0 || k > LFMM_P2P_SPLIT_MAX || (k & (k - 1)))
+            return fail(ctx, "EINVAL: near-list split must be 0 (automatic) or a power of two <= 16");
+        ctx->p2p_split = k;
+        return LFMM_OK;
+    }
     case LFMM_OPT_SURROGATE_TOL:
         if (!(v > 0.0)) return fail(ctx, "EINVAL: tolerance must be positive");
         ctx->surr_tol = v;
@@ -592,7 +599,9 @@ static lfmm_status set_option(lfmm_ctx* ctx, int opt, double v)
     }
 }
 
-static lfmm_status build_common(lfmm_ctx* ctx, int64_t n, const double* xyz_dev, const int32_t* layer_dev)
+}  // extern "C"
+
+lfmm_status lf_build_dev(lfmm_ctx* ctx, int64_t n, const double* xyz_dev, const int32_t* layer_dev)
 {
     ctx->built = false;
     prof_reset(ctx);
@@ -612,6 +621,8 @@ static lfmm_status build_common(lfmm_ctx* ctx, int64_t n, const double* xyz_dev,
     ++ctx->serial;
     return LFMM_OK;
 }
+
+extern "C" {
 
 lfmm_status lfmm_build(lfmm_ctx* ctx, int64_t n, const double* xyz, const int32_t* layer)
 {
@@ -637,7 +648,7 @@ lfmm_status lfmm_build(lfmm_ctx* ctx, int64_t n, const double* xyz, const int32_
     if (ce == cudaSuccess)
         ce = cudaMemcpyAsync(ctx->layer_in.ptr, layer, (size_t)n * 4, cudaMemcpyHostToDevice, ctx->s_main);
     if (ce != cudaSuccess) return fail(ctx, lf_cuda(ce, "copy inputs"));
-    return build_common(ctx, n, ctx->xyz_in.as<double>(), ctx->layer_in.as<int32_t>());
+    return lf_build_dev(ctx, n, ctx->xyz_in.as<double>(), ctx->layer_in.as<int32_t>());
 }
 
 lfmm_status lfmm_build_device(lfmm_ctx* ctx, int64_t n, const double* xyz_dev, const int32_t* layer_dev,
@@ -650,7 +661,7 @@ lfmm_status lfmm_build_device(lfmm_ctx* ctx, int64_t n, const double* xyz_dev, c
     cudaError_t ce = cudaEventRecord(ctx->ev_fork, us);
     if (ce == cudaSuccess) ce = cudaStreamWaitEvent(ctx->s_main, ctx->ev_fork, 0);
     if (ce != cudaSuccess) return fail(ctx, lf_cuda(ce, "stream order"));
-    return build_common(ctx, n, xyz_dev, layer_dev);
+    return lf_build_dev(ctx, n, xyz_dev, layer_dev);
 }
 
 }  // extern "C"

@@ -48,6 +48,7 @@ struct lfmm_ctx {
     // bumped by every successful build, option change and surrogate update:
     // a captured evaluation is valid only for the serial it was captured at
     uint64_t serial = 0;
+    int p2p_split = 0;  // near-list sharing of the P2P kernels (0: by occupancy)
 
     // components
     int ncomp = 0;
@@ -184,6 +185,9 @@ LfErr lf_evaluate_sorted(lfmm_ctx* ctx, int nrhs, const double* q_dev, double* p
 // enqueue nrhs evaluations on ctx->s_main (no host synchronisation, no
 // allocation once the buffers have grown to this size: capturable)
 lfmm_status lf_eval_enqueue(lfmm_ctx* ctx, int nrhs, const double* q_dev, double* phi_dev, double* fld_dev);
+// build from device inputs on ctx->s_main (synchronises it)
+lfmm_status lf_build_dev(lfmm_ctx* ctx, int64_t n, const double* xyz_dev, const int32_t* layer_dev);
+#define LFMM_P2P_SPLIT_MAX 16
 // right-hand sides evaluated in one pass (larger requests are split)
 #define LFMM_RHS_BATCH 64
 #define LFMM_SEP_EXT_P 18

@@ -442,8 +442,10 @@ __global__ void __launch_bounds__(G_T) k_m2l_gemm(GemmArgs g)
     const int oi0 = g.split ? (int)blockIdx.x % noff : 0, oi1 = g.split ? oi0 + 1 : noff;
     for (int oi = oi0; oi < oi1; ++oi) {
         const int o = g.cls[cls * noff + oi];
-        if (tid < G_TB) s_src[tid] = (tid < cnt) ? g.slots[(size_t)s_tb[tid] * noff + oi] : -1;
-        __syncthreads();
+        const int sj = (tid < cnt) ? g.slots[(size_t)s_tb[tid] * noff + oi] : -1;
+        if (tid < G_TB) s_src[tid] = sj;
+        // block-uniform: skip offsets where no target of the tile has a source
+        if (!__syncthreads_or(sj >= 0)) continue;
         // gather the source multipoles: column j = source of target j (k fastest)
         for (int idx = tid; idx < G_TB * KP; idx += G_T) {
             int j = idx / KP, k = idx - j * KP;
@@ -489,6 +491,8 @@ __global__ void __launch_bounds__(G_T) k_m2l_gemm(GemmArgs g)
                     Lt[row] = acc[r][c];
                 else if (g.mode == 3)
                     atomicAdd(Lt + row, acc[r][c]);
+                else if (g.split)
+                    atomicAdd(Lt + row, acc[r][c] * ih);
                 else
                     Lt[row] += acc[r][c] * ih;
             }
@@ -541,6 +545,8 @@ static LfErr m2l_gemm_t(lfmm_ctx* ctx, cudaStream_t st)
     g.M = ctx->Mexp.ptr;
     g.L = ctx->Lexp.ptr;
     g.mstride = g.lstride = (size_t)ctx->nbox_total * g.nc;
+    // too few tiles to fill the SMs (small trees): one block per (tile, offset), summed by atomics
+    g.split = (int64_t)ctx->m2l_ntiles * ctx->nrhs_b < 4 * 152;
     return launch_gemm_rm<R>(ctx, st, g, ctx->m2l_ntiles);
 }
 

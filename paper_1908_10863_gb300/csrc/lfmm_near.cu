@@ -48,6 +48,8 @@ struct P2PArgs {
     double* fld;      // [nr][qstride][3]
     int64_t qstride;  // charges per right-hand side (n)
     int nr;           // right-hand sides of this launch (<= the kernel's batch)
+    int split;        // near list of a leaf shared by this many warps / blocks (1: whole list, stored;
+                      // > 1: interleaved entries, partial sums added atomically into zeroed outputs)
     int Qn;
     const LfmmComp* comps;  // the context's components
     const double* gl_t;     // near-field quadrature rule (Qn nodes and weights)
@@ -141,10 +143,17 @@ __device__ __forceinline__ void p2p_store(const P2PArgs& a, int i, const P2PAcc<
     for (int k = 0; k < RB; ++k) {
         if (k >= a.nr) break;
         const size_t o = (size_t)k * a.qstride + i;
-        a.phi[o] = (double)A.P[k].s;
-        a.fld[3 * o + 0] = (double)A.Ex[k].s;
-        a.fld[3 * o + 1] = (double)A.Ey[k].s;
-        a.fld[3 * o + 2] = (double)A.Ez[k].s;
+        if (a.split > 1) {
+            atomicAdd(a.phi + o, (double)A.P[k].s);
+            atomicAdd(a.fld + 3 * o + 0, (double)A.Ex[k].s);
+            atomicAdd(a.fld + 3 * o + 1, (double)A.Ey[k].s);
+            atomicAdd(a.fld + 3 * o + 2, (double)A.Ez[k].s);
+        } else {
+            a.phi[o] = (double)A.P[k].s;
+            a.fld[3 * o + 0] = (double)A.Ex[k].s;
+            a.fld[3 * o + 1] = (double)A.Ey[k].s;
+            a.fld[3 * o + 2] = (double)A.Ez[k].s;
+        }
     }
 }
 
@@ -154,7 +163,8 @@ __global__ void __launch_bounds__(P2P_T) k_p2p(P2PArgs a)
 {
     __shared__ R sx[P2P_T], sy[P2P_T], sz[P2P_T], sq[RB][P2P_T];
     const R* q = reinterpret_cast<const R*>(a.q);
-    const int t = a.leaf_off + blockIdx.x;
+    const int t = a.leaf_off + (int)blockIdx.x / a.split;
+    const int part0 = (int)blockIdx.x % a.split;
     const int tid = threadIdx.x;
     const LfD4 ct = a.cen[t];
     const int tb = a.pbeg[t], te = a.pend[t];
@@ -168,7 +178,7 @@ __global__ void __launch_bounds__(P2P_T) k_p2p(P2PArgs a)
             zi = (R)(a.zs[i] - ct.z);
         }
         P2PAcc<R, RB> A;
-        for (int e = a.nbeg[t]; e < a.nend[t]; ++e) {
+        for (int e = a.nbeg[t] + part0; e < a.nend[t]; e += a.split) {
             const uint32_t ent = a.nent[e];
             const int c = (int)(ent >> LFMM_ENT_SHIFT);
             const int s = (int)(ent & LFMM_ENT_MASK);
@@ -228,8 +238,9 @@ __global__ void __launch_bounds__(32 * PW_WARPS) k_p2p_warp(P2PArgs a, const flo
 {
     __shared__ float sx[PW_WARPS][32], sy[PW_WARPS][32], sz[PW_WARPS][32], sq[PW_WARPS][RB][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int li = blockIdx.x * PW_WARPS + w;
-    if (li >= nleaf) return;  // whole warp
+    const int wi = blockIdx.x * PW_WARPS + w;
+    if (wi >= nleaf * a.split) return;  // whole warp
+    const int li = wi / a.split, part0 = wi - li * a.split;
     const float* q = reinterpret_cast<const float*>(a.q);
     const int t = a.leaf_off + li;
     const LfD4 ct = a.cen[t];
@@ -247,7 +258,7 @@ __global__ void __launch_bounds__(32 * PW_WARPS) k_p2p_warp(P2PArgs a, const flo
         }
         P2PAcc<float, RB> A;
         P2PPart<float, RB> part;
-        for (int e = eb; e < ee; ++e) {
+        for (int e = eb + part0; e < ee; e += a.split) {
             const uint32_t ent = a.nent[e];
             const int c = (int)(ent >> LFMM_ENT_SHIFT);
             const int s = (int)(ent & LFMM_ENT_MASK);
@@ -345,7 +356,8 @@ __global__ void __launch_bounds__(P2P_T) k_p2p_net(P2PArgs a)
     __shared__ R acc[P2P_T][4];  // deferred (phi, Ex, Ey, Ez) per target
     __shared__ uint16_t qbuf[P2P_W][P2P_QCAP];
     const R* q = reinterpret_cast<const R*>(a.q);
-    const int t = a.leaf_off + blockIdx.x;
+    const int t = a.leaf_off + (int)blockIdx.x / a.split;
+    const int part0 = (int)blockIdx.x % a.split;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, wbase = tid & ~31;
     const LfD4 ct = a.cen[t];
     const int tb = a.pbeg[t], te = a.pend[t];
@@ -366,7 +378,7 @@ __global__ void __launch_bounds__(P2P_T) k_p2p_net(P2PArgs a)
         __syncwarp();
         P2PAcc<R, 1> A;
         LfSum<R>&P = A.P[0], &Ex = A.Ex[0], &Ey = A.Ey[0], &Ez = A.Ez[0];
-        for (int e = a.nbeg[t]; e < a.nend[t]; ++e) {
+        for (int e = a.nbeg[t] + part0; e < a.nend[t]; e += a.split) {
             const uint32_t ent = a.nent[e];
             const int c = (int)(ent >> LFMM_ENT_SHIFT);
             const int s = (int)(ent & LFMM_ENT_MASK);
@@ -464,10 +476,17 @@ __global__ void __launch_bounds__(P2P_T) k_p2p_net(P2PArgs a)
             Ex.add(acc[tid][1]);
             Ey.add(acc[tid][2]);
             Ez.add(acc[tid][3]);
-            a.phi[i] = (double)P.s;
-            a.fld[3 * (size_t)i + 0] = (double)Ex.s;
-            a.fld[3 * (size_t)i + 1] = (double)Ey.s;
-            a.fld[3 * (size_t)i + 2] = (double)Ez.s;
+            if (a.split > 1) {
+                atomicAdd(a.phi + i, (double)P.s);
+                atomicAdd(a.fld + 3 * (size_t)i + 0, (double)Ex.s);
+                atomicAdd(a.fld + 3 * (size_t)i + 1, (double)Ey.s);
+                atomicAdd(a.fld + 3 * (size_t)i + 2, (double)Ez.s);
+            } else {
+                a.phi[i] = (double)P.s;
+                a.fld[3 * (size_t)i + 0] = (double)Ex.s;
+                a.fld[3 * (size_t)i + 1] = (double)Ey.s;
+                a.fld[3 * (size_t)i + 2] = (double)Ez.s;
+            }
         }
     }
     if (n_net | n_quad) {
@@ -508,6 +527,21 @@ LfErr lf_near_field(lfmm_ctx* ctx, cudaStream_t st)
     // needs far more registers, which slows the free-space part); one launch
     // per right-hand side.  The quadrature kernels take batches of up to 8.
     const bool net = a.sv.ready != 0 && ctx->stats[LFMM_STAT_P2P_REACTION] > 0;
+    // Few leaves (small problems) leave most SMs idle with one warp or block
+    // per leaf: share each near list between `split` of them.  A set value
+    // (ctx->p2p_split, e.g. from the tuner) wins over this occupancy rule.
+    const bool warp_kernel = !net && ctx->precision;
+    int split = ctx->p2p_split;
+    if (split <= 0) {
+        const int want = warp_kernel ? 152 * 32 : 152 * 8;  // warps, or blocks of P2P_T threads
+        split = 1;
+        while (split < LFMM_P2P_SPLIT_MAX && (int64_t)leaf.nbox * split * 2 <= want) split *= 2;
+    }
+    a.split = split;
+    if (split > 1) {
+        LF_CHECK(cudaMemsetAsync(a.phi, 0, sizeof(double) * (size_t)ctx->n * nr, st));
+        LF_CHECK(cudaMemsetAsync(a.fld, 0, 3 * sizeof(double) * (size_t)ctx->n * nr, st));
+    }
     const double* phi0 = a.phi;
     double* fld0 = a.fld;
     const char* q0 = reinterpret_cast<const char*>(a.q);
@@ -519,11 +553,11 @@ LfErr lf_near_field(lfmm_ctx* ctx, cudaStream_t st)
         a.fld = fld0 + (size_t)r0 * ctx->n * 3;
         if (net) {
             if (ctx->precision)
-                ++ctx->launches, k_p2p_net<float><<<leaf.nbox, P2P_T, 0, st>>>(a);
+                ++ctx->launches, k_p2p_net<float><<<leaf.nbox * split, P2P_T, 0, st>>>(a);
             else
-                ++ctx->launches, k_p2p_net<double><<<leaf.nbox, P2P_T, 0, st>>>(a);
+                ++ctx->launches, k_p2p_net<double><<<leaf.nbox * split, P2P_T, 0, st>>>(a);
         } else if (ctx->precision) {
-            const int g = lf_blocks(leaf.nbox, PW_WARPS), T = 32 * PW_WARPS;
+            const int g = lf_blocks((int64_t)leaf.nbox * split, PW_WARPS), T = 32 * PW_WARPS;
             const float4* rel = ctx->pos_rel.as<float4>();
             if (a.nr == 1)
                 ++ctx->launches, k_p2p_warp<1><<<g, T, 0, st>>>(a, rel, leaf.nbox);
@@ -535,13 +569,13 @@ LfErr lf_near_field(lfmm_ctx* ctx, cudaStream_t st)
                 ++ctx->launches, k_p2p_warp<8><<<g, T, 0, st>>>(a, rel, leaf.nbox);
         } else {
             if (a.nr == 1)
-                ++ctx->launches, k_p2p<double, 1><<<leaf.nbox, P2P_T, 0, st>>>(a);
+                ++ctx->launches, k_p2p<double, 1><<<leaf.nbox * split, P2P_T, 0, st>>>(a);
             else if (a.nr == 2)
-                ++ctx->launches, k_p2p<double, 2><<<leaf.nbox, P2P_T, 0, st>>>(a);
+                ++ctx->launches, k_p2p<double, 2><<<leaf.nbox * split, P2P_T, 0, st>>>(a);
             else if (a.nr <= 4)
-                ++ctx->launches, k_p2p<double, 4><<<leaf.nbox, P2P_T, 0, st>>>(a);
+                ++ctx->launches, k_p2p<double, 4><<<leaf.nbox * split, P2P_T, 0, st>>>(a);
             else
-                ++ctx->launches, k_p2p<double, 8><<<leaf.nbox, P2P_T, 0, st>>>(a);
+                ++ctx->launches, k_p2p<double, 8><<<leaf.nbox * split, P2P_T, 0, st>>>(a);
         }
         LF_TRY(lf_cuda(cudaGetLastError(), "p2p"));
     }

@@ -16,7 +16,8 @@ from . import build as _build
 
 OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETIMEOUT, ENUMERIC = range(7)
 OPT_PRECISION, OPT_LEAF_CAP, OPT_PROFILE, OPT_QUAD_NODES, OPT_SURROGATE, OPT_SURROGATE_TOL = 1, 2, 3, 4, 5, 6
-OPT_TENSOR_CORES = 7
+OPT_TENSOR_CORES, OPT_P2P_SPLIT = 7, 8
+TUNE_COLS = ["leaf_cap", "tensor_cores", "split", "depth", "ms", "chosen"]
 STAT_NAMES = ["n", "depth", "boxes", "leaves", "m2l_free", "m2l_reaction", "p2p_free", "p2p_reaction",
               "components", "m2m_edges", "launches", "reaction_keys", "surr_net_pairs", "surr_quad_pairs",
               "timeouts", "reaction_tables"]
@@ -46,7 +47,7 @@ EXPORTED = ["lfmm_create", "lfmm_set_option", "lfmm_build", "lfmm_build_device",
             "lfmm_surrogate_train", "lfmm_surrogate_info", "lfmm_surrogate_eval", "lfmm_surrogate_get_params",
             "lfmm_surrogate_set_params", "lfmm_surrogate_forward", "lfmm_surrogate_loss_grad",
             "lfmm_batch_create", "lfmm_batch_offsets", "lfmm_batch_evaluate_device", "lfmm_batch_evaluate",
-            "lfmm_batch_info", "lfmm_batch_last_error", "lfmm_batch_destroy"]
+            "lfmm_batch_info", "lfmm_batch_last_error", "lfmm_batch_destroy", "lfmm_autotune"]
 BATCH_INFO = ["problems", "charges", "graph_nodes", "kernel_nodes", "captures", "graph_launches", "direct_runs",
               "timeouts"]
 NOALLOC_MAX_POINTS = 65536
@@ -91,6 +92,8 @@ def load(build: bool = True):
     lib.lfmm_surrogate_set_params.argtypes = [_ctxp] + comp + [_fp]
     lib.lfmm_surrogate_forward.argtypes = [_ctxp] + comp + [ctypes.c_int, _fp, _fp]
     lib.lfmm_surrogate_loss_grad.argtypes = [_ctxp] + comp + [ctypes.c_int, _fp, _fp, _dp, _fp]
+    lib.lfmm_autotune.argtypes = [_ctxp, ctypes.c_int64, _dp, _ip, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int,
+                                  ctypes.POINTER(ctypes.c_int)]
     lib.lfmm_batch_create.argtypes = [ctypes.POINTER(_ctxp), ctypes.c_int, _ip, ctypes.c_int, ctypes.POINTER(_vp)]
     lib.lfmm_batch_offsets.argtypes = [_vp, _lp]
     lib.lfmm_batch_evaluate_device.argtypes = [_vp, _vp, _vp, _vp, _vp]
@@ -192,6 +195,18 @@ class LayeredFMM:
                                                    ctypes.c_void_p(phi.data_ptr()),
                                                    ctypes.c_void_p(field.data_ptr()) if field is not None else None,
                                                    s), "lfmm_evaluate_device")
+
+    def autotune(self, xyz, layer, mode: int = 0, reps: int = 3):
+        """Time candidate settings on this geometry and keep the fastest (the
+        context is left built with it).  Returns one dict per timed setting."""
+        xyz = _f64(xyz).reshape(-1, 3)
+        layer = np.ascontiguousarray(layer, dtype=np.int32)
+        rows = np.zeros((64, len(TUNE_COLS)))
+        nrows = ctypes.c_int(0)
+        self._check(self._lib.lfmm_autotune(self._ctx, xyz.shape[0], _ptr(xyz), _ptr(layer, _ip), int(mode),
+                                            int(reps), _ptr(rows), 64, ctypes.byref(nrows)), "lfmm_autotune")
+        self.n = xyz.shape[0]
+        return [dict(zip(TUNE_COLS, r)) for r in rows[:nrows.value]]
 
     def stats(self) -> dict:
         out = np.zeros(16, dtype=np.int64)
