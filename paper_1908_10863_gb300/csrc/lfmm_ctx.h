@@ -128,6 +128,8 @@ struct lfmm_ctx {
     std::vector<int> m2r_ktab_h;
     double m2r_levelh_h[16] = {0};
     int m2r_nkeys = 0, m2r_nbatch = 0, m2r_keyed_from = 0, m2r_ntab = 0;
+    DevBuf m2r_ops;         // assembled operator per key, [nkeys][RP][RP] in the precision below
+    int m2r_ops_prec = -1;  // 0 FP64, 1 FP32, -1 not assembled for this build
 
     // learned surrogate of the near-field reaction kernels
     DevBuf surr_theta, surr_grad, surr_m1, surr_m2, surr_w, surr_b, surr_meta, surr_err, surr_comps, surr_xoff,
@@ -175,6 +177,7 @@ LfErr lf_m2l_gemm(lfmm_ctx* ctx, cudaStream_t st);
 // ---- reaction M2L by geometry key (lfmm_m2r.cu) ----
 LfErr lf_prepare_m2r(lfmm_ctx* ctx, cudaStream_t st);
 LfErr lf_m2r_apply(lfmm_ctx* ctx, cudaStream_t st);
+LfErr lf_m2r_ops(lfmm_ctx* ctx, cudaStream_t st);
 // stable LSD radix sort of uint32 (key, value) pairs (lfmm_tree.cu); uses keys_tmp, vals_tmp, hist
 LfErr lf_radix_sort(lfmm_ctx* ctx, uint32_t* keys, uint32_t* vals, int64_t n, cudaStream_t st, int first_pass = 0,
                     int npass = 4);

@@ -144,6 +144,7 @@ LfErr lf_prepare_m2r(lfmm_ctx* ctx, cudaStream_t st)
     ctx->m2r_nkeys = 0;
     ctx->m2r_nbatch = 0;
     ctx->m2r_ntab = 0;
+    ctx->m2r_ops_prec = -1;
     ctx->stats[LFMM_STAT_REACTION_KEYS] = 0;
     ctx->stats[LFMM_STAT_REACTION_TABLES] = 0;
     ctx->m2r_keyed_from = ctx->depth + 1;
@@ -266,50 +267,35 @@ LfErr lf_prepare_m2r(lfmm_ctx* ctx, cudaStream_t st)
     // (the host staging vectors live in the context; the build synchronises at its end)
     ctx->stats[LFMM_STAT_REACTION_KEYS] = nk;
     ctx->stats[LFMM_STAT_REACTION_TABLES] = ntab;
-    return LfErr();
+    return lf_m2r_ops(ctx, st);
 }
 
 // ---------------------------------------------------------------------------
-// Evaluation: batched GEMM per key with atomic accumulation.
+// Evaluation: one operator per key (assembled once per build and precision),
+// then batched GEMMs with atomic accumulation.
 // ---------------------------------------------------------------------------
-struct RGemmArgs {
+struct ROpArgs {
     int p, nc;
-    const int4* batches;
     const uint32_t* kval;
     const double* tables;   // one per (component, level, rho^2, oz)
     const int* ktab;        // table of each key
-    const uint32_t* order;  // sorted entry indices
-    const uint32_t* ent;    // m2r entries (component | source box)
-    const int* tgt;         // target box per entry
-    const double* levelh;
-    const void* M;
-    void* L;
-    size_t stride;          // expansions per right-hand side (blockIdx.y), in elements
     const LfmmComp* comps;  // the context's components
+    void* ops;              // [nkeys][RP][RP]: A_key[k_in][r_out], zero padded
 };
 
-template <typename R>
-__device__ __forceinline__ void atomic_add_r(R* a, R v)
-{
-    atomicAdd(a, v);
-}
-
-template <typename R, int RM>
-__global__ void __launch_bounds__(R_T) k_m2r_gemm(RGemmArgs g)
+// One block per key: A_key from its table, the lateral phases e^{i mu phi}
+// and the signs (eq. coefintable with the reflection of the multipole).
+template <typename R, int RP>
+__global__ void __launch_bounds__(R_T) k_m2r_ops(ROpArgs g)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int RP = 16 * RM;
-    constexpr int KP = RP;
-    constexpr int XS = KP + 1;
-    const int p = g.p, nc = g.nc, nre = lf_nre(p), TS = 2 * p + 1;
-    R* sA = reinterpret_cast<R*>(smem_raw);  // [KP][RP]
-    R* sX = sA + KP * RP;                    // [R_TB][XS]
-    R* sT = sX + R_TB * XS;                  // [TS*TS]
+    const int p = g.p, nc = g.nc, TS = 2 * p + 1;
+    R* sT = reinterpret_cast<R*>(smem_raw);  // [TS*TS]
     R* sC = sT + TS * TS;                    // cos(m phi), m <= 2p
     R* sS = sC + TS;
-    __shared__ int s_src[R_TB], s_tgt[R_TB];
     __shared__ unsigned char s_n[RP], s_m[RP], s_im[RP];  // (n, m, imaginary part) of each packed index
     const int tid = threadIdx.x;
+    const int kidx = blockIdx.x;
     if (tid < RP) {
         int n = 0, m = 0, im = 0;
         if (tid < nc) lf_decode(p, tid, n, m, im);
@@ -317,11 +303,9 @@ __global__ void __launch_bounds__(R_T) k_m2r_gemm(RGemmArgs g)
         s_m[tid] = (unsigned char)m;
         s_im[tid] = (unsigned char)im;
     }
-    const int cg = tid & 15, rg = tid >> 4;
-    const int4 b = g.batches[blockIdx.x];
-    const int kidx = b.x, start = b.y, cnt = b.z;
     int c, lev, ox, oy, oz;
     rkey_decode(g.kval[kidx], c, lev, ox, oy, oz);
+    (void)lev;
     (void)oz;
     const LfmmComp& cp = g.comps[c];
     const double phi = (ox == 0 && oy == 0) ? 0.0 : atan2((double)oy, (double)ox);
@@ -333,56 +317,67 @@ __global__ void __launch_bounds__(R_T) k_m2r_gemm(RGemmArgs g)
     }
     const double* Tk = g.tables + (size_t)g.ktab[kidx] * TS * TS;
     for (int j = tid; j < TS * TS; j += R_T) sT[j] = (R)Tk[j];
-    if (tid < R_TB) {
-        if (tid < cnt) {
-            uint32_t e = g.order[start + tid];
-            s_src[tid] = (int)(g.ent[e] & LFMM_ENT_MASK);
-            s_tgt[tid] = g.tgt[e];
-        } else {
-            s_src[tid] = -1;
-            s_tgt[tid] = -1;
-        }
-    }
     __syncthreads();
-    // operator A[k_in][r_out] from the table, the phases and the signs
-    for (int idx = tid; idx < KP * RP; idx += R_T) {
-        int kin = idx / RP, rout = idx - kin * RP;
+    R* A = reinterpret_cast<R*>(g.ops) + (size_t)kidx * RP * RP;
+    for (int idx = tid; idx < RP * RP; idx += R_T) {
+        const int kin = idx / RP, rout = idx - kin * RP;
         R v = 0;
         if (kin < nc && rout < nc) {
             const int n = s_n[kin], mp = s_m[kin], bim = s_im[kin];
             const int k = s_n[rout], l = s_m[rout], aim = s_im[rout];
             // T_N^mu (complex) = e^{i mu phi} T(N, |mu|) with T_N^{-mu} = (-1)^mu conj
-            int N = n + k;
-            int mu1 = mp + l;
-            R c1 = sT[N * TS + mu1] * sC[mu1], d1 = sT[N * TS + mu1] * sS[mu1];
-            R c2 = 0, d2 = 0, s = 0;
+            const int N = n + k;
+            const int mu1 = mp + l;
+            const R c1 = sT[N * TS + mu1] * sC[mu1], d1 = sT[N * TS + mu1] * sS[mu1];
+            R c2 = 0, d2 = 0, sg = 0;
             if (mp > 0) {
-                int mu2 = l - mp, a2 = mu2 < 0 ? -mu2 : mu2;
-                R tv = sT[N * TS + a2];
+                const int mu2 = l - mp, a2 = mu2 < 0 ? -mu2 : mu2;
+                const R tv = sT[N * TS + a2];
                 c2 = tv * sC[a2];
                 d2 = tv * sS[a2];
                 if (mu2 < 0) {
                     if (a2 & 1) c2 = -c2; else d2 = -d2;
                 }
-                s = (mp & 1) ? R(-1) : R(1);
+                sg = (mp & 1) ? R(-1) : R(1);
             }
-            R sk = (k & 1) ? R(-1) : R(1);
-            if (!aim && !bim) v = sk * (c1 + s * c2);
-            else if (!aim && bim) v = sk * (-d1 + s * d2);
-            else if (aim && !bim) v = sk * (d1 + s * d2);
-            else v = sk * (c1 - s * c2);
+            const R sk = (k & 1) ? R(-1) : R(1);
+            if (!aim && !bim) v = sk * (c1 + sg * c2);
+            else if (!aim && bim) v = sk * (-d1 + sg * d2);
+            else if (aim && !bim) v = sk * (d1 + sg * d2);
+            else v = sk * (c1 - sg * c2);
             if (cp.refl && ((n + mp) & 1)) v = -v;
         }
-        sA[idx] = v;
+        A[idx] = v;
     }
-    // gather the sources' multipoles
-    const R* M = reinterpret_cast<const R*>(g.M) + (size_t)blockIdx.y * g.stride;
-    for (int idx = tid; idx < R_TB * KP; idx += R_T) {
-        int j = idx / KP, k = idx - j * KP;
-        int s = s_src[j];
-        sX[j * XS + k] = (s >= 0 && k < nc) ? M[(size_t)s * nc + k] : R(0);
-    }
-    __syncthreads();
+}
+
+struct RGemmArgs {
+    int p, nc;
+    const int4* batches;    // key, first sorted entry, count
+    const uint32_t* kval;
+    const void* ops;        // [nkeys][RP][RP]
+    const uint32_t* order;  // sorted entry indices
+    const uint32_t* ent;    // m2r entries (component | source box)
+    const int* tgt;         // target box per entry
+    const double* levelh;
+    const void* M;
+    void* L;
+    size_t stride;          // expansions per right-hand side (blockIdx.y), in elements
+};
+
+// Y = A X over the first 4 * CG columns (CG column groups of 4; the rest of
+// the 256 threads split the RP rows), scaled by 1/h and added into the
+// targets' local expansions.
+template <typename R, int RP, int CG>
+__device__ __forceinline__ void m2r_tile(const R* __restrict__ sA, const R* __restrict__ sX, int cnt,
+                                         const int* s_tgt, R ih, R* __restrict__ L, int nc)
+{
+    constexpr int KP = RP, XS = KP + 1;
+    constexpr int RG = R_T / CG;  // row groups
+    constexpr int RM = RP / RG;   // rows per thread
+    static_assert(RM >= 1 && RM * RG == RP, "tile shape");
+    const int tid = threadIdx.x;
+    const int cg = tid % CG, rg = tid / CG;
     R acc[RM][4];
 #pragma unroll
     for (int r = 0; r < RM; ++r)
@@ -401,43 +396,107 @@ __global__ void __launch_bounds__(R_T) k_m2r_gemm(RGemmArgs g)
 #pragma unroll
             for (int q = 0; q < 4; ++q) acc[r][q] += a[r] * x[q];
     }
-    const R ih = (R)(1.0 / g.levelh[lev]);
-    R* L = reinterpret_cast<R*>(g.L) + (size_t)blockIdx.y * g.stride;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        int j = 4 * cg + q;
+        const int j = 4 * cg + q;
         if (j >= cnt) continue;
         R* Lt = L + (size_t)s_tgt[j] * nc;
 #pragma unroll
         for (int r = 0; r < RM; ++r) {
-            int row = rg * RM + r;
-            if (row < nc) atomic_add_r(Lt + row, acc[r][q] * ih);
+            const int row = rg * RM + r;
+            if (row < nc) atomicAdd(Lt + row, acc[r][q] * ih);
         }
     }
-    (void)nre;
 }
 
-template <typename R, int RM>
-static LfErr launch_rgemm(lfmm_ctx* ctx, cudaStream_t st, const RGemmArgs& g)
+// One block per batch of up to R_TB pairs of one key.
+template <typename R, int RP>
+__global__ void __launch_bounds__(R_T) k_m2r_gemm(RGemmArgs g)
 {
-    constexpr int RP = 16 * RM;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int KP = RP;
+    constexpr int XS = KP + 1;
+    constexpr int CG_MIN = (R_T / RP) > 4 ? (R_T / RP) : 4;  // at least one row per thread
+    const int nc = g.nc;
+    R* sA = reinterpret_cast<R*>(smem_raw);  // [KP][RP]
+    R* sX = sA + KP * RP;                    // [R_TB][XS]
+    __shared__ int s_src[R_TB], s_tgt[R_TB];
+    const int tid = threadIdx.x;
+    const int4 b = g.batches[blockIdx.x];
+    const int kidx = b.x, start = b.y, cnt = b.z;
+    int c, lev, ox, oy, oz;
+    rkey_decode(g.kval[kidx], c, lev, ox, oy, oz);
+    // the key's operator: a contiguous copy in 16-byte pieces
+    {
+        const float4* src = reinterpret_cast<const float4*>(reinterpret_cast<const R*>(g.ops) +
+                                                            (size_t)kidx * KP * RP);
+        float4* dst = reinterpret_cast<float4*>(sA);
+        constexpr int NV = KP * RP * (int)sizeof(R) / 16;
+        for (int i = tid; i < NV; i += R_T) dst[i] = src[i];
+    }
+    if (tid < R_TB) {
+        if (tid < cnt) {
+            const uint32_t e = g.order[start + tid];
+            s_src[tid] = (int)(g.ent[e] & LFMM_ENT_MASK);
+            s_tgt[tid] = g.tgt[e];
+        } else {
+            s_src[tid] = -1;
+            s_tgt[tid] = -1;
+        }
+    }
+    __syncthreads();
+    // columns the tile shape below reads (block-uniform)
+    const int cgs = cnt > 32 ? 16 : (cnt > 16 ? 8 : 4);
+    const int ncol = 4 * (cgs > CG_MIN ? cgs : CG_MIN);
+    const R* M = reinterpret_cast<const R*>(g.M) + (size_t)blockIdx.y * g.stride;
+    for (int idx = tid; idx < ncol * KP; idx += R_T) {
+        const int j = idx / KP, k = idx - j * KP;
+        const int s = s_src[j];
+        sX[j * XS + k] = (s >= 0 && k < nc) ? M[(size_t)s * nc + k] : R(0);
+    }
+    __syncthreads();
+    const R ih = (R)(1.0 / g.levelh[lev]);
+    R* L = reinterpret_cast<R*>(g.L) + (size_t)blockIdx.y * g.stride;
+    if (cgs == 16 || CG_MIN >= 16)
+        m2r_tile<R, RP, 16>(sA, sX, cnt, s_tgt, ih, L, nc);
+    else if (cgs == 8 || CG_MIN >= 8)
+        m2r_tile<R, RP, (CG_MIN > 8 ? CG_MIN : 8)>(sA, sX, cnt, s_tgt, ih, L, nc);
+    else
+        m2r_tile<R, RP, CG_MIN>(sA, sX, cnt, s_tgt, ih, L, nc);
+}
+
+template <typename R, int RP>
+static LfErr m2r_build_ops(lfmm_ctx* ctx, cudaStream_t st)
+{
+    const int nk = ctx->m2r_nkeys;
+    LF_TRY(lf_reserve(ctx->m2r_ops, (size_t)nk * RP * RP * sizeof(R) + 16));
+    ROpArgs g;
+    g.p = ctx->p;
+    g.nc = lf_nc(ctx->p);
+    g.kval = ctx->m2r_kval.as<uint32_t>();
+    g.tables = ctx->m2r_tables.as<double>();
+    g.ktab = ctx->m2r_ktab.as<int>();
+    g.comps = ctx->comp_dev.as<LfmmComp>();
+    g.ops = ctx->m2r_ops.ptr;
     const int TS = 2 * ctx->p + 1;
-    size_t sm = sizeof(R) * ((size_t)RP * RP + (size_t)R_TB * (RP + 1) + (size_t)TS * TS + 2 * (size_t)TS) + 64;
-    LF_CHECK(cudaFuncSetAttribute(k_m2r_gemm<R, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    ++ctx->launches, k_m2r_gemm<R, RM><<<dim3(ctx->m2r_nbatch, ctx->nrhs_b), R_T, sm, st>>>(g);
-    return lf_cuda(cudaGetLastError(), "m2r gemm");
+    const size_t sm = sizeof(R) * ((size_t)TS * TS + 2 * (size_t)TS) + 16;
+    LF_CHECK(cudaFuncSetAttribute(k_m2r_ops<R, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    ++ctx->launches, k_m2r_ops<R, RP><<<nk, R_T, sm, st>>>(g);
+    LF_TRY(lf_cuda(cudaGetLastError(), "m2r operators"));
+    ctx->m2r_ops_prec = sizeof(R) == 4 ? 1 : 0;
+    return LfErr();
 }
 
-template <typename R>
-static LfErr m2r_apply_t(lfmm_ctx* ctx, cudaStream_t st)
+template <typename R, int RP>
+static LfErr m2r_apply_rp(lfmm_ctx* ctx, cudaStream_t st)
 {
+    if (ctx->m2r_ops_prec != (sizeof(R) == 4 ? 1 : 0)) LF_TRY((m2r_build_ops<R, RP>(ctx, st)));
     RGemmArgs g;
     g.p = ctx->p;
     g.nc = lf_nc(ctx->p);
     g.batches = ctx->m2r_batches.as<int4>();
     g.kval = ctx->m2r_kval.as<uint32_t>();
-    g.tables = ctx->m2r_tables.as<double>();
-    g.ktab = ctx->m2r_ktab.as<int>();
+    g.ops = ctx->m2r_ops.ptr;
     g.order = ctx->m2r_order.as<uint32_t>();
     g.ent = ctx->m2r_ent.as<uint32_t>();
     g.tgt = ctx->m2r_tgt.as<int>();
@@ -445,11 +504,31 @@ static LfErr m2r_apply_t(lfmm_ctx* ctx, cudaStream_t st)
     g.M = ctx->Mexp.ptr;
     g.L = ctx->Lexp.ptr;
     g.stride = (size_t)ctx->nbox_total * g.nc;
-    g.comps = ctx->comp_dev.as<LfmmComp>();
+    const size_t sm = sizeof(R) * ((size_t)RP * RP + (size_t)R_TB * (RP + 1)) + 16;
+    LF_CHECK(cudaFuncSetAttribute(k_m2r_gemm<R, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    ++ctx->launches, k_m2r_gemm<R, RP><<<dim3(ctx->m2r_nbatch, ctx->nrhs_b), R_T, sm, st>>>(g);
+    return lf_cuda(cudaGetLastError(), "m2r gemm");
+}
+
+template <typename R>
+static LfErr m2r_apply_t(lfmm_ctx* ctx, cudaStream_t st)
+{
     switch (ctx->m2l_rm) {
-    case 2: return launch_rgemm<R, 2>(ctx, st, g);
-    case 4: return launch_rgemm<R, 4>(ctx, st, g);
-    case 8: return launch_rgemm<R, 8>(ctx, st, g);
+    case 2: return m2r_apply_rp<R, 32>(ctx, st);
+    case 4: return m2r_apply_rp<R, 64>(ctx, st);
+    case 8: return m2r_apply_rp<R, 128>(ctx, st);
+    default: return "internal: reaction GEMM supports p <= 10";
+    }
+}
+
+// assemble the operators of the keys for the current precision (build time)
+LfErr lf_m2r_ops(lfmm_ctx* ctx, cudaStream_t st)
+{
+    if (ctx->m2r_nbatch == 0) return LfErr();
+    switch (ctx->m2l_rm) {
+    case 2: return ctx->precision ? m2r_build_ops<float, 32>(ctx, st) : m2r_build_ops<double, 32>(ctx, st);
+    case 4: return ctx->precision ? m2r_build_ops<float, 64>(ctx, st) : m2r_build_ops<double, 64>(ctx, st);
+    case 8: return ctx->precision ? m2r_build_ops<float, 128>(ctx, st) : m2r_build_ops<double, 128>(ctx, st);
     default: return "internal: reaction GEMM supports p <= 10";
     }
 }

@@ -161,3 +161,24 @@ def test_fp32_form_near_interface_matches_fp64():
     print("near_interface 16k: FP32 vs FP64 Err2 phi %.2e field %.2e" % (e_phi, e_fld))
     assert e_phi < 1e-5
     assert e_fld < 1e-5
+
+
+@pytest.mark.parametrize("p", [4, 8, 10])
+def test_precision_change_after_build_reassembles_reaction_operators(p):
+    # the keyed reaction operators are assembled at build time in the build's
+    # precision; a later precision change must assemble them again
+    w = workloads.config2(20000)
+    with LayeredFMM(w.d, w.eps, p) as f:
+        f.build(w.xyz, w.layer)
+        assert f.stats()["reaction_keys"] > 0
+        ref64 = f.evaluate(w.q)
+        f.set_option(1, 1)
+        got32 = f.evaluate(w.q)
+        f.set_option(1, 0)
+        again64 = f.evaluate(w.q)
+    with LayeredFMM(w.d, w.eps, p, precision=1) as g:
+        g.build(w.xyz, w.layer)
+        ref32 = g.evaluate(w.q)
+    assert oracle.err2(ref64[0], again64[0]) < 1e-13
+    assert oracle.err2(ref32[0], got32[0]) < 1e-6
+    assert oracle.err2(ref64[0], got32[0]) < 1e-5
