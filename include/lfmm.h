@@ -59,8 +59,11 @@ enum {
     LFMM_OPT_SURROGATE_TOL = 6, /* error estimate above which a pair falls back to quadrature (default 1e-6) */
     LFMM_OPT_TENSOR_CORES = 7,  /* 1 = float32 free M2L on the tensor cores (3xTF32) where (p+1)^2 <= 128
                                    (default); 0 = on the CUDA cores */
-    LFMM_OPT_P2P_SPLIT = 8      /* near list of a leaf shared by this many warps/blocks of the P2P kernels:
+    LFMM_OPT_P2P_SPLIT = 8,     /* near list of a leaf shared by this many warps/blocks of the P2P kernels:
                                    0 = chosen from the leaf count (default), else 1, 2, 4, 8 or 16 */
+    LFMM_OPT_TC_GROUPS = 9      /* tensor-core free M2L: CTAs per 256-target tile, each summing 189/groups
+                                   offsets in its tensor-memory accumulator before a float atomic add;
+                                   a divisor of 189 (default 27: 7 offsets per accumulation) */
 };
 
 /* Create a context for the medium.

@@ -583,6 +583,13 @@ static lfmm_status set_option(lfmm_ctx* ctx, int opt, double v)
     case LFMM_OPT_TENSOR_CORES:
         ctx->use_tc = (v != 0.0);
         return LFMM_OK;
+    case LFMM_OPT_TC_GROUPS: {
+        const int k = (int)v;
+        if ((double)k != v || k < 1 || 189 % k != 0)
+            return fail(ctx, "EINVAL: tensor-core groups must divide 189");
+        ctx->tc_groups = k;
+        return LFMM_OK;
+    }
     case LFMM_OPT_P2P_SPLIT: {
         const int k = (int)v;
         if ((double)k != v || k < 0 || k > LFMM_P2P_SPLIT_MAX || (k & (k - 1)))

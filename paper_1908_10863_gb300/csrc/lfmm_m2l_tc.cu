@@ -28,13 +28,13 @@
 //   warp 8      one thread issues the MMAs of a stage (3 products x K chunk / 8) and commits them to
 //               the stage's "empty" barrier;
 //   epilogue    warps 0..7 read the accumulator (tcgen05.ld), scale by 1/h and
-//               add into the local expansions (float atomics: three CTAs share
-//               a tile).
-// Four stages of 48 KB (K chunks of 16, 64-byte swizzle) buffer the operands,
-// handed to the tensor cores two stages after their copies start.  (Eight
-// stages of K chunks of 8 with 32-byte swizzle measured 1.5x slower; a longer
-// lag on four stages leaves the tensor cores too little slack.)  Tiles of one octant class share
-// their offset list; each tile walks it from a different starting offset so
+//               add into the local expansions (float atomics: the CTAs of a
+//               tile's offset groups meet there).
+// Two stages of 48 KB (K chunks of 16, 64-byte swizzle) per CTA buffer the
+// operands, handed to the tensor cores one stage after their copies start;
+// two CTAs share an SM, so four stages are in flight per SM.  (K chunks of 8
+// with 32-byte swizzle, or one CTA per SM with four stages, measured slower.)
+// Tiles of one octant class share their offset list; each tile walks it from a different starting offset so
 // that concurrent CTAs read different operator chunks.  Every barrier wait is
 // bounded; on a timeout the CTA records an error, stops issuing work, waits
 // (bounded) for its copies in flight and frees its tensor memory.
@@ -62,7 +62,7 @@
 #define TC_N 256                     // targets per tile (MMA N)
 #define TC_M 128                     // output coefficients (MMA M)
 #ifndef TC_KC
-#define TC_KC 16                     // K elements per stage (16: 64-byte rows; 8: 32-byte rows, slower)
+#define TC_KC 16                     // K elements per stage (64-byte rows)
 #endif
 #define TC_NKC (128 / TC_KC)         // K chunks (K = 128)
 #define TC_ROWB (TC_KC * 4)          // bytes per row of a stage tile
@@ -77,8 +77,19 @@
 #define TC_XP 2                      // multipole pieces
 #define TC_STAGE_BYTES (TC_AP * TC_A_BYTES + TC_XP * TC_X_BYTES)
 #define TC_MROW 128                  // floats per multipole piece row in the split copy (512 B)
-#define TC_STAGES (TC_KC == 8 ? 8 : 4)  // 24 KB or 48 KB stages
+// Two CTAs per SM (97 KB of shared memory and 256 tensor-memory columns
+// each), two 48 KB stages apiece: one CTA's prologue, gathers and atomic
+// epilogue overlap the other's MMAs.  Measured at N = 1M, p = 10: 2.39 ms
+// against 2.63 ms for one CTA per SM with four stages.
+#ifndef TC_STAGES
+#define TC_STAGES 2
+#endif
+#ifndef TC_LAG
 #define TC_LAG (TC_STAGES / 2)           // stages between a stage's copies and its hand-over
+#endif
+#ifndef TC_MINB
+#define TC_MINB 2                        // resident CTAs per SM
+#endif
 #define TC_SMEM (TC_STAGES * TC_STAGE_BYTES + 1024)
 #define TC_TMEM_COLS 256
 #define TC_SPIN_CYCLES (1ll << 31)   // ~1 s at 2 GHz
@@ -222,7 +233,7 @@ struct TcArgs {
     int* err;               // [0]: timeouts
 };
 
-__global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(TcArgs g)
+__global__ void __launch_bounds__(TC_THREADS, TC_MINB) k_m2l_tc(TcArgs g)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -433,6 +444,7 @@ LfErr lf_setup_m2l_tc(lfmm_ctx* ctx, const double* A64, int KP, int RP)
     LF_TRY(lf_reserve(ctx->m2l_Atc, blob.size() * 4));
     LF_CHECK(cudaMemcpy(ctx->m2l_Atc.ptr, blob.data(), blob.size() * 4, cudaMemcpyHostToDevice));
     LF_CHECK(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+    LF_CHECK(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     ctx->m2l_tc_ok = 1;
     return LfErr();
 }

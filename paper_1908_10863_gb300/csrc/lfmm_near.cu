@@ -233,6 +233,9 @@ __global__ void k_rel_pos(int leaf_off, int nleaf, const LfD4* __restrict__ cen,
         rel[i] = make_float4((float)(xs[i] - c.x), (float)(ys[i] - c.y), (float)(zs[i] - c.z), 0.f);
 }
 
+// A leaf of at most 16 (8) charges gives each target 2 (4) lanes, each
+// taking a contiguous part of every staged source box; their sums meet by
+// shuffles at the end.
 template <int RB>
 __global__ void __launch_bounds__(32 * PW_WARPS) k_p2p_warp(P2PArgs a, const float4* __restrict__ rel, int nleaf)
 {
@@ -246,8 +249,12 @@ __global__ void __launch_bounds__(32 * PW_WARPS) k_p2p_warp(P2PArgs a, const flo
     const LfD4 ct = a.cen[t];
     const int tb = a.pbeg[t], te = a.pend[t];
     const int eb = a.nbeg[t], ee = a.nend[t];
-    for (int base = tb; base < te; base += 32) {
-        const int i = base + lane;
+    const int nt = te - tb;
+    const int G = nt <= 8 ? 4 : (nt <= 16 ? 2 : 1);  // lanes per target (warp-uniform)
+    const int T = 32 / G;                             // targets per pass
+    const int ti = lane % T, slice = lane / T;
+    for (int base = tb; base < te; base += T) {
+        const int i = base + ti;
         const bool valid = i < te;
         float xi = 0.f, yi = 0.f, zi = 0.f;
         if (valid) {
@@ -284,19 +291,39 @@ __global__ void __launch_bounds__(32 * PW_WARPS) k_p2p_warp(P2PArgs a, const flo
                 __syncwarp();
                 if (!valid) continue;
                 const int cnt = min(32, se - cb);
+                // this lane's contiguous share of the staged sources
+                const int u0 = (slice * cnt) / G, u1 = ((slice + 1) * cnt) / G;
                 if (cp.is_free) {
-                    for (int u = 0; u < cnt; ++u)
+                    for (int u = u0; u < u1; ++u)
                         p2p_free_add<float, RB>(xi - sx[w][u], yi - sy[w][u], zi - sz[w][u], &sq[w][0][u], 32, a.nr,
                                                 part);
                 } else {
-                    for (int u = 0; u < cnt; ++u)
+                    for (int u = u0; u < u1; ++u)
                         p2p_reaction_add<float, RB>(cp, xi - sx[w][u], yi - sy[w][u], zi - sz[w][u], &sq[w][0][u],
                                                     32, a.nr, a.Qn, a.gl_t, a.gl_w, part);
                 }
             }
             p2p_flush<float, RB>(part, A);
         }
-        if (valid) p2p_store<float, RB>(a, i, A);
+        if (G > 1) {
+            // the lanes of one target meet (every lane takes part in the shuffles)
+#pragma unroll
+            for (int k = 0; k < RB; ++k) {
+                float v0 = A.P[k].s - A.P[k].c, v1 = A.Ex[k].s - A.Ex[k].c;
+                float v2 = A.Ey[k].s - A.Ey[k].c, v3 = A.Ez[k].s - A.Ez[k].c;
+                for (int off = T; off < 32; off <<= 1) {
+                    v0 += __shfl_xor_sync(0xffffffffu, v0, off);
+                    v1 += __shfl_xor_sync(0xffffffffu, v1, off);
+                    v2 += __shfl_xor_sync(0xffffffffu, v2, off);
+                    v3 += __shfl_xor_sync(0xffffffffu, v3, off);
+                }
+                A.P[k].s = v0;
+                A.Ex[k].s = v1;
+                A.Ey[k].s = v2;
+                A.Ez[k].s = v3;
+            }
+        }
+        if (valid && slice == 0) p2p_store<float, RB>(a, i, A);
     }
 }
 

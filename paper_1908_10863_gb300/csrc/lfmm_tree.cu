@@ -717,12 +717,21 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
     int hc[16];
     LF_CHECK(cudaMemcpyAsync(hc, cnt, sizeof(int) * 16, cudaMemcpyDeviceToHost, st));
     LF_CHECK(cudaStreamSynchronize(st));
+    // the level whose mean leaf occupancy is nearest (in ratio) to half the
+    // capacity, among the levels whose mean stays within the capacity
     int depth = LFMM_FINE_LEVEL;
-    for (int l = 0; l <= LFMM_FINE_LEVEL; ++l) {
-        double mean = (double)n / (double)hc[l];
-        if (mean <= 0.5 * ctx->leaf_cap) {
-            depth = l;
-            break;
+    {
+        const double want = 0.5 * ctx->leaf_cap;
+        double best = INFINITY;
+        for (int l = 0; l <= LFMM_FINE_LEVEL; ++l) {
+            const double mean = (double)n / (double)hc[l];
+            if (mean > ctx->leaf_cap) continue;
+            const double d = fabs(log(mean / want));
+            if (d < best) {
+                best = d;
+                depth = l;
+            }
+            if (mean < want) break;  // finer levels only move further away
         }
     }
     ctx->depth = depth;

@@ -16,7 +16,7 @@ from . import build as _build
 
 OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETIMEOUT, ENUMERIC = range(7)
 OPT_PRECISION, OPT_LEAF_CAP, OPT_PROFILE, OPT_QUAD_NODES, OPT_SURROGATE, OPT_SURROGATE_TOL = 1, 2, 3, 4, 5, 6
-OPT_TENSOR_CORES, OPT_P2P_SPLIT = 7, 8
+OPT_TENSOR_CORES, OPT_P2P_SPLIT, OPT_TC_GROUPS = 7, 8, 9
 TUNE_COLS = ["leaf_cap", "tensor_cores", "split", "depth", "ms", "chosen"]
 STAT_NAMES = ["n", "depth", "boxes", "leaves", "m2l_free", "m2l_reaction", "p2p_free", "p2p_reaction",
               "components", "m2m_edges", "launches", "reaction_keys", "surr_net_pairs", "surr_quad_pairs",

@@ -55,7 +55,7 @@ def test_batch_graph_matches_single_evaluations(precision, tol):
         _close(ms)
     print(info)
     assert info["direct_runs"] == 1 and info["captures"] == 1 and info["graph_launches"] == 2
-    assert info["kernel_nodes"] > 7 * 10 and info["timeouts"] == 0
+    assert info["kernel_nodes"] >= 7 * 5 and info["timeouts"] == 0  # every problem's stages are in the graph
 
 
 def test_batch_mixed_media_multi_rhs_and_oracle():

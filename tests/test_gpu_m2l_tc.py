@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 import oracle
-from paper_1908_10863_gb300 import LayeredFMM, workloads
+from paper_1908_10863_gb300 import LayeredFMM, LfmmError, workloads
 from paper_1908_10863_gb300.lfmm import OPT_TENSOR_CORES
 
 pytestmark = pytest.mark.gpu
@@ -54,3 +54,22 @@ def test_high_order_falls_back_to_cuda_cores():
     phi_t, _, _ = _eval(w, 12, 1, 1)
     phi_64, _, _ = _eval(w, 12, 0, 0)
     assert oracle.err2(phi_64, phi_t) < 1e-5
+
+
+def test_offset_groups_option():
+    # fewer CTAs per tile sum more offsets in one tensor-memory accumulator:
+    # same result up to float32 accumulation, and only divisors of 189 pass
+    from paper_1908_10863_gb300.lfmm import EINVAL, OPT_TC_GROUPS
+    w = workloads.config2(40000)
+    with LayeredFMM(w.d, w.eps, 10, precision=1) as f:
+        f.build(w.xyz, w.layer)
+        ref, _ = f.evaluate(w.q)
+        f.set_option(OPT_TC_GROUPS, 9)
+        phi, _ = f.evaluate(w.q)
+        for bad in (0, 2, 10, 190):
+            with pytest.raises(LfmmError) as ei:
+                f.set_option(OPT_TC_GROUPS, bad)
+            assert ei.value.status == EINVAL
+    e = oracle.err2(ref, phi)
+    print("groups 9 vs 27: Err2 %.2e" % e)
+    assert e < 1e-5
