@@ -53,9 +53,9 @@ def fp32_peak_tflops(sm_mhz):
 # times the nominal TF32/BF16 ratio (1.1 / 2.25 PFLOP/s); fallback 1.9 PF bf16.
 TF32_PER_BF16 = 1.1 / 2.25
 # DRAM bytes (read + write) of one k_m2l_tc launch per free-space M2L pair,
-# from an ncu capture of the same workload at N=262,144 (749.6 MB for
-# 10,493,810 pairs), scaled to the bench's pair count.
-TC_DRAM_BYTES_PER_PAIR = 749.6e6 / 10493810
+# from an ncu capture of the bench's own workload (N=1,048,576, p=10: 882.4 MB
+# read + 37.7 MB written for 10,905,072 pairs), scaled to the bench's pair count.
+TC_DRAM_BYTES_PER_PAIR = (882.354944e6 + 37.73184e6) / 10905072
 
 
 def tf32_peak_tflops():
@@ -507,7 +507,7 @@ def main():
                              "algorithmic flops = 8 (p+1)^2 (p+1)(p+2)/2 per box pair (the tensor cores execute "
                              "3 TF32 products of padded 128x128 operators); duration = the stage's CUDA events "
                              "inside the timed steps; traffic scaled by pair count from an ncu capture at "
-                             "N=262,144" % src}
+                             "N=1,048,576" % src}
     else:
         sm_mhz = clk.get("sm_max_mhz") or 2070.0
         peak = fp32_peak_tflops(sm_mhz)
