@@ -101,7 +101,8 @@ struct lfmm_ctx {
     DevBuf box_cend;    // int32
     DevBuf box_center;  // LfD4 (x, y, z, layer)
     DevBuf box_grid;    // int4 (ix, iy, iz, layer): grid cell of the box at its level
-    DevBuf pos_rel;     // float4 per sorted charge: offset from its leaf centre
+    DevBuf pos_rel;  // float4 per sorted charge: offset from its leaf centre
+    DevBuf leaf_of;  // leaf (global box id) of each sorted charge
     DevBuf level_consts;  // float4 [LFMM_MAXCOMP][16]: (K, F, G, Z) of the list tests, in box units
     DevBuf flags, idx;  // temporaries
 

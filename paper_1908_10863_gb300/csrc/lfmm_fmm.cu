@@ -50,68 +50,102 @@ struct LfAcc<double> {
 };
 
 // ---------------------------------------------------------------------------
-// P2M (eq. mefreespace / melayerupgoingimage): M_n^m = sum_j q_j conj(U_n^m((x_j - s)/h)).
-// One warp per leaf box; lanes own particles while the harmonics are formed
-// and coefficients while they are summed.
+// Regular solid harmonics U_k^j(x, y, z), column by column (j = 0..p, then
+// k = j..p), by the recurrences of the diagonal U_j^j = (x + iy) U_{j-1}^{j-1} / (2j),
+// U_{j+1}^j = z U_j^j and (k^2 - j^2) U_k^j = (2k - 1) z U_{k-1}^j - r^2 U_{k-2}^j,
+// handing each value to f(k, j, re, im) as it is formed: no array is needed.
 // ---------------------------------------------------------------------------
-template <typename R>
-__global__ void __launch_bounds__(32) k_p2m(int off, int p, const LfD4* __restrict__ cen,
-                                            const int* __restrict__ pbeg, const int* __restrict__ pend,
-                                            const double* __restrict__ xs, const double* __restrict__ ys,
-                                            const double* __restrict__ zs, const R* __restrict__ q, double h,
-                                            R* __restrict__ M, int nrhs, int64_t qstride, size_t mstride)
+template <typename R, typename F>
+__device__ __forceinline__ void lf_regular_walk(int p, R x, R y, R z, F&& f)
 {
-    // the harmonics of a chunk of 32 charges are formed once and serve every
-    // right-hand side (charges q[r * qstride + i], multipoles M[r * mstride + ...])
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    R* su = reinterpret_cast<R*>(smem_raw);
-    const int nre = lf_nre(p), nc = lf_nc(p);
-    const int lane = threadIdx.x;
-    const int b = off + blockIdx.x;
-    const LfD4 c = cen[b];
-    const double ih = 1.0 / h;
-    const int HS = 2 * nre + 1;  // odd row stride: lanes' rows fall in distinct banks
-    R* ure = su + lane * HS;
-    R* uim = ure + nre;
-    constexpr int KMAX = (LFMM_PMAX + 1) * (LFMM_PMAX + 1) / 32 + 1;
-    int src[KMAX];
-    for (int k = 0; k < KMAX; ++k) {
-        int o = lane + 32 * k;
-        src[k] = -1;
-        if (o < nc) {
-            int n, m, im;
-            lf_decode(p, o, n, m, im);
-            src[k] = im ? (nre + lf_re(n, m)) : lf_re(n, m);
+    const R r2 = x * x + y * y + z * z;
+    R dre = 1, dim = 0;
+    for (int j = 0; j <= p; ++j) {
+        if (j > 0) {
+            const R inv = R(1) / R(2 * j);
+            const R nre = (dre * x - dim * y) * inv;
+            const R nim = (dre * y + dim * x) * inv;
+            dre = nre;
+            dim = nim;
+        }
+        f(j, j, dre, dim);
+        R p1re = dre, p1im = dim, p2re = 0, p2im = 0;
+        for (int k = j + 1; k <= p; ++k) {
+            R ure, uim;
+            if (k == j + 1) {
+                ure = z * p1re;
+                uim = z * p1im;
+            } else {
+                const R inv = R(1) / R(k * k - j * j);
+                const R a = R(2 * k - 1) * z;
+                ure = (a * p1re - r2 * p2re) * inv;
+                uim = (a * p1im - r2 * p2im) * inv;
+            }
+            p2re = p1re;
+            p2im = p1im;
+            p1re = ure;
+            p1im = uim;
+            f(k, j, ure, uim);
         }
     }
-    const int pb = pbeg[b], pe = pend[b];
-    for (int start = pb; start < pe; start += 32) {
-        int i = start + lane;
-        if (i < pe) {
-            R x = (R)((xs[i] - c.x) * ih), y = (R)((ys[i] - c.y) * ih), z = (R)((zs[i] - c.z) * ih);
-            lf_regular<R>(p, x, y, z, ure, uim);
-            for (int j = 0; j < nre; ++j) uim[j] = -uim[j];  // conjugate
-        } else {
-            for (int j = 0; j < 2 * nre; ++j) ure[j] = 0;
-        }
-        __syncwarp();
-        const int cnt = min(32, pe - start);
-        R* sq = su + 32 * HS;  // this chunk's charges of one right-hand side
-        for (int r = 0; r < nrhs; ++r) {
-            sq[lane] = (i < pe) ? q[(size_t)r * qstride + i] : R(0);
-            __syncwarp();
-            R* out = M + (size_t)r * mstride + (size_t)b * nc;
-            for (int k = 0; k < KMAX; ++k) {
-                if (src[k] < 0) continue;
-                R s = 0;
-                for (int u = 0; u < cnt; ++u) s += sq[u] * su[u * HS + src[k]];
-                if (start == pb)
-                    out[lane + 32 * k] = s;
-                else
-                    out[lane + 32 * k] += s;
+}
+
+// ---------------------------------------------------------------------------
+// P2M (eq. mefreespace / melayerupgoingimage): M_n^m = sum_j q_j conj(U_n^m((x_j - s)/h)).
+// One thread per charge (sorted order, so the charges of a leaf are
+// consecutive): each coefficient is summed over the lanes of one leaf by a
+// segmented shuffle reduction and added by the leaf's first lane of the warp
+// into the (zeroed) multipoles.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(128) k_p2m(int64_t n, int p, const int* __restrict__ leaf_of,
+                                             const LfD4* __restrict__ cen, const double* __restrict__ xs,
+                                             const double* __restrict__ ys, const double* __restrict__ zs,
+                                             const R* __restrict__ q, double h, R* __restrict__ M, int nrhs,
+                                             int64_t qstride, size_t mstride)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const bool valid = i < n;
+    const int b = valid ? leaf_of[i] : -1 - lane;  // a lane past the end is a segment of its own
+    // same[k]: lane + 2^k holds a charge of the same leaf (segments are contiguous)
+    unsigned same = 0;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const int d = 1 << k;
+        const int bd = __shfl_down_sync(0xffffffffu, b, d);
+        if (lane + d < 32 && bd == b) same |= 1u << k;
+    }
+    const int bprev = __shfl_up_sync(0xffffffffu, b, 1);  // every lane takes part
+    const bool head = valid && (lane == 0 || bprev != b);
+    R x = 0, y = 0, z = 0;
+    if (valid) {
+        const LfD4 c = cen[b];
+        const double ih = 1.0 / h;
+        x = (R)((xs[i] - c.x) * ih);
+        y = (R)((ys[i] - c.y) * ih);
+        z = (R)((zs[i] - c.z) * ih);
+    }
+    const int nc = lf_nc(p);
+    for (int r = 0; r < nrhs; ++r) {
+        const R qv = valid ? q[(size_t)r * qstride + i] : R(0);
+        R* Mb = M + (size_t)r * mstride + (size_t)(valid ? b : 0) * nc;
+        lf_regular_walk<R>(p, x, y, z, [&](int k, int j, R ure, R uim) {
+            R vre = qv * ure, vim = -qv * uim;  // q conj(U)
+#pragma unroll
+            for (int s = 0; s < 5; ++s) {
+                const R wre = __shfl_down_sync(0xffffffffu, vre, 1 << s);
+                const R wim = __shfl_down_sync(0xffffffffu, vim, 1 << s);
+                if (same & (1u << s)) {
+                    vre += wre;
+                    vim += wim;
+                }
             }
-            __syncwarp();
-        }
+            if (head) {
+                atomicAdd(Mb + lf_re(k, j), vre);
+                if (j > 0) atomicAdd(Mb + lf_im(p, k, j), vim);
+            }
+        });
     }
 }
 
@@ -384,79 +418,56 @@ __global__ void k_m2l(M2LArgs a)
 // ---------------------------------------------------------------------------
 // L2P with gradient: Phi = sum L_k^l conj(U_k^l((x - t)/h)),
 // dz Phi = sum L_k^l conj(U_{k-1}^l), (dx + i dy) Phi = sum L_k^l conj(U_{k-1}^{l-1}).
-// One warp per leaf box.
+// One thread per charge.  Every harmonic U_k^j is paired, as the recurrence
+// forms it, with the coefficients it multiplies: L_k^j (potential), L_{k+1}^j
+// (dz), L_{k+1}^{j+1} and L_{k+1}^{j-1} (dx, dy); the local expansion of the
+// charge's leaf is read through the cache (the lanes of a warp share a few
+// leaves).
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void __launch_bounds__(32) k_l2p(int off, int p, const LfD4* __restrict__ cen,
-                                            const int* __restrict__ pbeg, const int* __restrict__ pend,
-                                            const double* __restrict__ xs, const double* __restrict__ ys,
-                                            const double* __restrict__ zs, double h, const R* __restrict__ L,
-                                            double* __restrict__ phi, double* __restrict__ fld, int nrhs,
-                                            size_t lstride, int64_t ostride)
+__global__ void __launch_bounds__(128) k_l2p(int64_t n, int p, const int* __restrict__ leaf_of,
+                                             const LfD4* __restrict__ cen, const double* __restrict__ xs,
+                                             const double* __restrict__ ys, const double* __restrict__ zs, double h,
+                                             const R* __restrict__ L, double* __restrict__ phi,
+                                             double* __restrict__ fld, int nrhs, size_t lstride, int64_t ostride)
 {
-    // harmonics of a chunk of 32 charges once, then every right-hand side's
-    // local expansion (L[r * lstride + ...]) in turn; outputs phi[r * ostride + i]
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int nre = lf_nre(p), nc = lf_nc(p);
-    R* sL = reinterpret_cast<R*>(smem_raw);
-    R* su = sL + nc;
-    const int lane = threadIdx.x;
-    const int b = off + blockIdx.x;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int b = leaf_of[i];
     const LfD4 c = cen[b];
     const double ih = 1.0 / h;
-    R* ure = su + lane * (2 * nre + 1);  // odd row stride: no bank conflicts
-    R* uim = ure + nre;
-    const int pb = pbeg[b], pe = pend[b];
-    for (int start = pb; start < pe; start += 32) {
-        const int i = start + lane;
-        const bool valid = i < pe;
-        if (valid) {
-            R x = (R)((xs[i] - c.x) * ih), y = (R)((ys[i] - c.y) * ih), z = (R)((zs[i] - c.z) * ih);
-            lf_regular<R>(p, x, y, z, ure, uim);
-        }
-        for (int r = 0; r < nrhs; ++r) {
-            __syncwarp();
-            for (int j = lane; j < nc; j += 32) sL[j] = L[(size_t)r * lstride + (size_t)b * nc + j];
-            __syncwarp();
-            if (!valid) continue;
-            LfAcc<R> P, Gz, Gx, Gy;
-            for (int n = 0; n <= p; ++n) {
-                // potential: Re(L conj U) with factor 2 for m >= 1
-                P.add(sL[lf_re(n, 0)] * ure[lf_re(n, 0)]);
-                for (int m = 1; m <= n; ++m)
-                    P.add(R(2) * (sL[lf_re(n, m)] * ure[lf_re(n, m)] + sL[lf_im(p, n, m)] * uim[lf_re(n, m)]));
-                if (n == 0) continue;
-                // d/dz: L_n^m with U_{n-1}^m
-                Gz.add(sL[lf_re(n, 0)] * ure[lf_re(n - 1, 0)]);
-                for (int m = 1; m <= n - 1; ++m)
-                    Gz.add(R(2) * (sL[lf_re(n, m)] * ure[lf_re(n - 1, m)] + sL[lf_im(p, n, m)] * uim[lf_re(n - 1, m)]));
-                // (dx + i dy): sum_{l=1..n} L_n^l conj(U_{n-1}^{l-1}) - L_n^0 U_{n-1}^1
-                //              - sum_{l=1..n-2} conj(L_n^l) U_{n-1}^{l+1}
-                for (int m = 1; m <= n; ++m) {
-                    R lr = sL[lf_re(n, m)], li = sL[lf_im(p, n, m)];
-                    R ur = ure[lf_re(n - 1, m - 1)], ui = uim[lf_re(n - 1, m - 1)];
-                    Gx.add(lr * ur + li * ui);
-                    Gy.add(li * ur - lr * ui);
-                }
-                if (n >= 2) {
-                    R l0 = sL[lf_re(n, 0)];
-                    Gx.add(-l0 * ure[lf_re(n - 1, 1)]);
-                    Gy.add(-l0 * uim[lf_re(n - 1, 1)]);
-                }
-                for (int m = 1; m <= n - 2; ++m) {
-                    R lr = sL[lf_re(n, m)], li = sL[lf_im(p, n, m)];
-                    R ur = ure[lf_re(n - 1, m + 1)], ui = uim[lf_re(n - 1, m + 1)];
-                    // -(lr - i li)(ur + i ui)
-                    Gx.add(-(lr * ur + li * ui));
-                    Gy.add(-(lr * ui - li * ur));
-                }
+    const R x = (R)((xs[i] - c.x) * ih), y = (R)((ys[i] - c.y) * ih), z = (R)((zs[i] - c.z) * ih);
+    const int nc = lf_nc(p);
+    for (int r = 0; r < nrhs; ++r) {
+        const R* Lb = L + (size_t)r * lstride + (size_t)b * nc;
+        LfAcc<R> P, Gz, Gx, Gy;
+        lf_regular_walk<R>(p, x, y, z, [&](int k, int j, R ur, R ui) {
+            if (j == 0)
+                P.add(__ldg(Lb + lf_re(k, 0)) * ur);
+            else
+                P.add(R(2) * (__ldg(Lb + lf_re(k, j)) * ur + __ldg(Lb + lf_im(p, k, j)) * ui));
+            if (k + 1 > p) return;
+            if (j == 0)
+                Gz.add(__ldg(Lb + lf_re(k + 1, 0)) * ur);
+            else
+                Gz.add(R(2) * (__ldg(Lb + lf_re(k + 1, j)) * ur + __ldg(Lb + lf_im(p, k + 1, j)) * ui));
+            // L_{k+1}^{j+1} conj(U_k^j)
+            R lr = __ldg(Lb + lf_re(k + 1, j + 1)), li = __ldg(Lb + lf_im(p, k + 1, j + 1));
+            Gx.add(lr * ur + li * ui);
+            Gy.add(li * ur - lr * ui);
+            if (j >= 1) {
+                // -conj(L_{k+1}^{j-1}) U_k^j (L_{k+1}^0 is real)
+                lr = __ldg(Lb + lf_re(k + 1, j - 1));
+                li = (j > 1) ? __ldg(Lb + lf_im(p, k + 1, j - 1)) : R(0);
+                Gx.add(-(lr * ur + li * ui));
+                Gy.add(-(lr * ui - li * ur));
             }
-            const size_t o = (size_t)r * ostride + i;
-            phi[o] = (double)P.get();
-            fld[3 * o + 0] = -(double)Gx.get() * ih;
-            fld[3 * o + 1] = -(double)Gy.get() * ih;
-            fld[3 * o + 2] = -(double)Gz.get() * ih;
-        }
+        });
+        const size_t o = (size_t)r * ostride + i;
+        phi[o] = (double)P.get();
+        fld[3 * o + 0] = -(double)Gx.get() * ih;
+        fld[3 * o + 1] = -(double)Gy.get() * ih;
+        fld[3 * o + 2] = -(double)Gz.get() * ih;
     }
 }
 
@@ -532,11 +543,12 @@ static LfErr far_field(lfmm_ctx* ctx, cudaStream_t st)
     // upward pass
     int ph = lf_prof_start(ctx, LFMM_TIME_P2M, st);
     {
-        size_t sm = sizeof(R) * (32 * (2 * (size_t)nre + 1) + 32);
-        LF_CHECK(cudaFuncSetAttribute(k_p2m<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        ++ctx->launches, k_p2m<R><<<leaf.nbox, 32, sm, st>>>(leaf.off, p, cen, pbeg, pend, ctx->xs.as<double>(),
-                                                             ctx->ys.as<double>(), ctx->zs.as<double>(),
-                                                             ctx->q_sorted.as<R>(), leaf.h, M, nr, ctx->n, ms);
+        // the leaf multipoles are sums of atomic contributions: zero them first
+        LF_CHECK(cudaMemset2DAsync(M + (size_t)leaf.off * nc, ms * sizeof(R), 0, sizeof(R) * (size_t)leaf.nbox * nc,
+                                   nr, st));
+        ++ctx->launches, k_p2m<R><<<lf_blocks(ctx->n, 128), 128, 0, st>>>(
+            ctx->n, p, ctx->leaf_of.as<int>(), cen, ctx->xs.as<double>(), ctx->ys.as<double>(),
+            ctx->zs.as<double>(), ctx->q_sorted.as<R>(), leaf.h, M, nr, ctx->n, ms);
         LF_TRY(lf_cuda(cudaGetLastError(), "p2m"));
     }
     lf_prof_stop(ctx, ph, st);
@@ -635,12 +647,9 @@ static LfErr far_field(lfmm_ctx* ctx, cudaStream_t st)
     }
     ph = lf_prof_start(ctx, LFMM_TIME_L2P, st);
     {
-        size_t sm = sizeof(R) * (nc + 32 * (2 * (size_t)nre + 1));
-        LF_CHECK(cudaFuncSetAttribute(k_l2p<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        ++ctx->launches, k_l2p<R><<<leaf.nbox, 32, sm, st>>>(leaf.off, p, cen, pbeg, pend, ctx->xs.as<double>(),
-                                                             ctx->ys.as<double>(), ctx->zs.as<double>(), leaf.h, L,
-                                                             ctx->phi_far.as<double>(), ctx->fld_far.as<double>(), nr,
-                                                             ms, ctx->n);
+        ++ctx->launches, k_l2p<R><<<lf_blocks(ctx->n, 128), 128, 0, st>>>(
+            ctx->n, p, ctx->leaf_of.as<int>(), cen, ctx->xs.as<double>(), ctx->ys.as<double>(),
+            ctx->zs.as<double>(), leaf.h, L, ctx->phi_far.as<double>(), ctx->fld_far.as<double>(), nr, ms, ctx->n);
         LF_TRY(lf_cuda(cudaGetLastError(), "l2p"));
     }
     lf_prof_stop(ctx, ph, st);

@@ -223,14 +223,16 @@ __global__ void __launch_bounds__(P2P_T) k_p2p(P2PArgs a)
 
 __global__ void k_rel_pos(int leaf_off, int nleaf, const LfD4* __restrict__ cen, const int* __restrict__ pbeg,
                           const int* __restrict__ pend, const double* __restrict__ xs, const double* __restrict__ ys,
-                          const double* __restrict__ zs, float4* __restrict__ rel)
+                          const double* __restrict__ zs, float4* __restrict__ rel, int* __restrict__ leaf_of)
 {
     const int li = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (li >= nleaf) return;
     const int b = leaf_off + li;
     const LfD4 c = cen[b];
-    for (int i = pbeg[b] + lane; i < pend[b]; i += 32)
+    for (int i = pbeg[b] + lane; i < pend[b]; i += 32) {
         rel[i] = make_float4((float)(xs[i] - c.x), (float)(ys[i] - c.y), (float)(zs[i] - c.z), 0.f);
+        leaf_of[i] = b;
+    }
 }
 
 // A leaf of at most 16 (8) charges gives each target 2 (4) lanes, each
@@ -331,10 +333,12 @@ LfErr lf_near_prepare(lfmm_ctx* ctx, cudaStream_t st)
 {
     const LfmmLevel& leaf = ctx->levels[ctx->depth];
     LF_TRY(lf_reserve(ctx->pos_rel, (size_t)ctx->n * sizeof(float4) + 16));
+    LF_TRY(lf_reserve(ctx->leaf_of, (size_t)ctx->n * sizeof(int) + 16));
     if (leaf.nbox > 0)
         ++ctx->launches, k_rel_pos<<<lf_blocks(leaf.nbox, 4), 128, 0, st>>>(
             leaf.off, leaf.nbox, ctx->box_center.as<LfD4>(), ctx->box_pbeg.as<int>(), ctx->box_pend.as<int>(),
-            ctx->xs.as<double>(), ctx->ys.as<double>(), ctx->zs.as<double>(), ctx->pos_rel.as<float4>());
+            ctx->xs.as<double>(), ctx->ys.as<double>(), ctx->zs.as<double>(), ctx->pos_rel.as<float4>(),
+            ctx->leaf_of.as<int>());
     return lf_cuda(cudaGetLastError(), "relative positions");
 }
 
