@@ -115,6 +115,9 @@ struct lfmm_ctx {
     int m2l_rm = 0, m2l_rp = 0, m2l_ntiles = 0;
     // tensor-core free M2L (float32 form, (p+1)^2 <= 128)
     DevBuf m2l_Atc, m2l_tc_tiles, m2l_Ms;
+    DevBuf m2m_Atc, l2l_Atc, tc_shift_tiles;        // tensor-core M2M / L2L operators and tiles
+    std::vector<int> tc_m2m_first, tc_l2l_first;    // first tensor-core translation tile of each level
+    std::vector<int4> tc_shift_h;
     // M2M / L2L as gathered GEMMs (the same kernel as the free M2L)
     DevBuf m2m_A64, m2m_A32, l2l_A64, l2l_A32, shift_cls, m2m_slots, shift_tiles;
     std::vector<int> m2m_first, l2l_first;  // first tile of each level
@@ -211,7 +214,8 @@ LfErr lf_shift_gemm(lfmm_ctx* ctx, int level, bool l2l, cudaStream_t st);
 // ---- tensor-core free M2L (lfmm_m2l_tc.cu) ----
 // byte offset in ctx->counts of the int counting device waits that ran out
 #define LFMM_TIMEOUT_OFF 40960
-LfErr lf_setup_m2l_tc(lfmm_ctx* ctx, const double* A64, int KP, int RP);
+LfErr lf_setup_m2l_tc(lfmm_ctx* ctx, const double* A64, const double* M2M64, const double* L2L64, int KP, int RP);
+LfErr lf_shift_tc(lfmm_ctx* ctx, int level, bool l2l, cudaStream_t st);
 LfErr lf_m2l_tc(lfmm_ctx* ctx, cudaStream_t st);
 int lf_m2l_tc_tile();
 LfErr lf_surrogate_alloc(lfmm_ctx* ctx);

@@ -202,7 +202,6 @@ LfErr lf_setup_m2l_ops(lfmm_ctx* ctx)
                     }
             }
     (void)nc;
-    LF_TRY(lf_setup_m2l_tc(ctx, A64.data(), KP, RP));
     std::vector<float> A32(A64.size());
     for (size_t i = 0; i < A64.size(); ++i) A32[i] = (float)A64[i];
     LF_TRY(lf_reserve(ctx->m2l_A64, A64.size() * 8));
@@ -229,8 +228,9 @@ LfErr lf_setup_m2l_ops(lfmm_ctx* ctx)
     LF_CHECK(cudaMemcpy(ctx->m2l_cls.ptr, cls.data(), sizeof(int) * cls.size(), cudaMemcpyHostToDevice));
     LF_CHECK(cudaMemcpy(ctx->m2l_inv.ptr, inv.data(), sizeof(int) * inv.size(), cudaMemcpyHostToDevice));
     // M2M / L2L octant matrices: [which][o][k_in][r_out], and their class tables
+    std::vector<double> S2[2];
     for (int which = 0; which < 2; ++which) {
-        std::vector<double> S;
+        std::vector<double>& S = S2[which];
         shift_ops(p, KP, RP, which, S);
         std::vector<float> Sf(S.size());
         for (size_t i = 0; i < S.size(); ++i) Sf[i] = (float)S[i];
@@ -241,6 +241,7 @@ LfErr lf_setup_m2l_ops(lfmm_ctx* ctx)
         LF_CHECK(cudaMemcpy(b64.ptr, S.data(), S.size() * 8, cudaMemcpyHostToDevice));
         LF_CHECK(cudaMemcpy(b32.ptr, Sf.data(), Sf.size() * 4, cudaMemcpyHostToDevice));
     }
+    LF_TRY(lf_setup_m2l_tc(ctx, A64.data(), S2[0].data(), S2[1].data(), KP, RP));
     const int shift_cls[8] = {0, 1, 2, 3, 4, 5, 6, 7};  // M2M: one class of 8 offsets; L2L: 8 classes of 1
     LF_TRY(lf_reserve(ctx->shift_cls, sizeof(shift_cls)));
     LF_CHECK(cudaMemcpy(ctx->shift_cls.ptr, shift_cls, sizeof(shift_cls), cudaMemcpyHostToDevice));
@@ -374,6 +375,35 @@ LfErr lf_prepare_m2l(lfmm_ctx* ctx, cudaStream_t st)
                 st0 += n;
             }
         ctx->m2l_tc_ntiles = (int)tct.size();
+        // translations: M2M tiles of parents (levels 0 .. depth-1, box order),
+        // L2L tiles of children grouped by octant (levels 1 .. depth)
+        std::vector<int4>& sht = ctx->tc_shift_h;
+        sht.clear();
+        ctx->tc_m2m_first.assign(depth + 2, 0);
+        ctx->tc_l2l_first.assign(depth + 2, 0);
+        for (int l = 0; l <= depth; ++l) {
+            ctx->tc_m2m_first[l] = (int)sht.size();
+            const LfmmLevel& lv = ctx->levels[l];
+            if (l < depth)
+                for (int s = 0; s < lv.nbox; s += TN) sht.push_back(make_int4(l, 0, lv.off + s, std::min(TN, lv.nbox - s)));
+        }
+        ctx->tc_m2m_first[depth + 1] = (int)sht.size();
+        int st1 = 0;
+        for (int l = 1; l <= depth; ++l) {
+            ctx->tc_l2l_first[l] = (int)sht.size();
+            for (int c = 0; c < 8; ++c) {
+                const int n = hcnt[16 + l * 8 + c];
+                for (int s = 0; s < n; s += TN) sht.push_back(make_int4(l, c, st1 + s, std::min(TN, n - s)));
+                st1 += n;
+            }
+        }
+        ctx->tc_l2l_first[0] = ctx->tc_l2l_first[1];
+        ctx->tc_l2l_first[depth + 1] = (int)sht.size();
+        if (!sht.empty()) {
+            LF_TRY(lf_reserve(ctx->tc_shift_tiles, sht.size() * sizeof(int4)));
+            LF_CHECK(cudaMemcpyAsync(ctx->tc_shift_tiles.ptr, sht.data(), sht.size() * sizeof(int4),
+                                     cudaMemcpyHostToDevice, st));
+        }
         if (!tct.empty()) {
             LF_TRY(lf_reserve(ctx->m2l_tc_tiles, tct.size() * sizeof(int4)));
             LF_CHECK(cudaMemcpyAsync(ctx->m2l_tc_tiles.ptr, tct.data(), tct.size() * sizeof(int4),
@@ -554,6 +584,13 @@ static LfErr m2l_gemm_t(lfmm_ctx* ctx, cudaStream_t st)
 template <typename R>
 static LfErr shift_gemm_t(lfmm_ctx* ctx, int level, bool l2l, cudaStream_t st)
 {
+    // The L2L into the leaves runs on the tensor cores in the float32 form
+    // (the CUDA-core gather of parent locals is latency-bound there).  The
+    // other translations stay on the CUDA cores: at N = 1M, p = 10 the
+    // tensor-core M2M saved 0.05 ms, and chaining 3xTF32 L2L over every level
+    // raised Err2(phi) from 2.0e-6 to 3.2e-6.
+    if (sizeof(R) == 4 && l2l && level == ctx->depth && ctx->use_tc && ctx->m2l_tc_ok)
+        return lf_shift_tc(ctx, level, l2l, st);
     GemmArgs g;
     g.p = ctx->p;
     g.nc = lf_nc(ctx->p);

@@ -218,9 +218,11 @@ __host__ __device__ __forceinline__ uint32_t swz(int row, int k)
 
 struct TcArgs {
     const int4* tiles;      // level, class, start, count
-    const int* sorted;      // target boxes grouped by (level, class)
-    const int* slots;       // [box][189] source box at each offset of the class, or -1
-    const int* cls;         // [8][189] offset index (0..342) of each class position
+    const int* sorted;      // target boxes grouped by (level, class), or null: targets start .. start + count - 1
+    const int* slots;       // [box][noff] source box at each offset of the class, or -1
+    const int* cls;         // [class][noff] operator index of each class position
+    int noff;               // offsets per class: 189 (M2L), 8 (M2M: children), 1 (L2L: parent)
+    int unit_scale;         // 1: add D as it is (M2M, L2L); 0: add D / h_level (M2L)
     const double* levelh;   // box size per level
     const unsigned char* A; // [343][4 chunks][2 pieces x 16 KB], pre-swizzled
     const float* Ms;        // split multipoles [box + 1][2 pieces][128] (last box: zeros)
@@ -229,7 +231,7 @@ struct TcArgs {
     int nc;
     size_t ms_stride;       // per right-hand side (blockIdx.y): split multipoles, in floats
     size_t l_stride;        // per right-hand side: local expansions, in floats
-    int groups;             // CTAs per tile (offset groups; divides 189)
+    int groups;             // CTAs per tile (offset groups; divides noff)
     int* err;               // [0]: timeouts
 };
 
@@ -247,12 +249,12 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MINB) k_m2l_tc(TcArgs g)
     const int item = blockIdx.x;
     const int4 tile = g.tiles[item / g.groups];
     const int grp = item % g.groups;
-    const int goff = TC_NOFF / g.groups;
+    const int goff = g.noff / g.groups;
     const int level = tile.x, cl = tile.y, start = tile.z, cnt = tile.w;
     const int nc = g.nc;
     const int nstage = goff * TC_NKC;
 
-    if (tid < TC_N) s_tb[tid] = (tid < cnt) ? g.sorted[start + tid] : -1;
+    if (tid < TC_N) s_tb[tid] = (tid < cnt) ? (g.sorted ? g.sorted[start + tid] : start + tid) : -1;
     if (tid == 0) {
         for (int s = 0; s < TC_STAGES; ++s) {
             mbar_init(&full_bar[s], TC_PROD_WARPS + 1);  // one arrival per producer warp + the bulk copy's
@@ -291,7 +293,7 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MINB) k_m2l_tc(TcArgs g)
             if (__any_sync(0xffffffffu, *(volatile int*)&s_abort)) break;  // warp-uniform
             unsigned char* st = sm + (size_t)s * TC_STAGE_BYTES;
             if (ptid == 0) {
-                const int o = g.cls[cl * TC_NOFF + oi];
+                const int o = g.cls[cl * g.noff + oi];
                 mbar_arrive_tx(&full_bar[s], TC_AP * TC_A_BYTES);
                 bulk_g2s(st, g.A + ((size_t)o * TC_NKC + kc) * (TC_AP * TC_A_BYTES), TC_AP * TC_A_BYTES,
                          &full_bar[s]);
@@ -299,7 +301,7 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MINB) k_m2l_tc(TcArgs g)
             }
             if (kc == 0) {
                 const int tb = s_tb[warp * 32 + lane];
-                my_src = (tb >= 0) ? g.slots[(size_t)tb * TC_NOFF + oi] : -1;
+                my_src = (tb >= 0) ? g.slots[(size_t)tb * g.noff + oi] : -1;
             }
             // 32 rows x 2 pieces x 4 chunks of 16 B per warp: 8 per lane
             unsigned char* xs = st + TC_AP * TC_A_BYTES;
@@ -345,7 +347,7 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MINB) k_m2l_tc(TcArgs g)
         if (ok && !*(volatile int*)&s_abort) {
             const int q = warp & 3, half = warp >> 2;
             const int row = 32 * q + lane;
-            const float ih = (float)(1.0 / g.levelh[level]);
+            const float ih = g.unit_scale ? 1.f : (float)(1.0 / g.levelh[level]);
 #pragma unroll 1
             for (int ch = 0; ch < 4; ++ch) {
                 const int col0 = half * 128 + ch * 32;
@@ -416,15 +418,13 @@ static inline uint32_t host_tf32(float x)
     return u;
 }
 
-// A64: [343][KP in][RP out] (double); builds the tensor-core operator blob
-LfErr lf_setup_m2l_tc(lfmm_ctx* ctx, const double* A64, int KP, int RP)
+// A64: [nops][KP in][RP out] (double) -> the tensor-core operator blob:
+// per operator TC_NKC K chunks of two TF32 pieces, pre-swizzled
+static LfErr tc_blob(const double* A64, int nops, int KP, int RP, int nc, DevBuf& out)
 {
-    const int nc = lf_nc(ctx->p);
-    ctx->m2l_tc_ok = 0;
-    if (nc > TC_M || KP < nc || RP < nc) return LfErr();
     const size_t per = (size_t)TC_NKC * TC_AP * TC_A_BYTES;
-    std::vector<uint32_t> blob((size_t)TC_NALL * per / 4, 0u);
-    for (int o = 0; o < TC_NALL; ++o)
+    std::vector<uint32_t> blob((size_t)nops * per / 4, 0u);
+    for (int o = 0; o < nops; ++o)
         for (int kc = 0; kc < TC_NKC; ++kc) {
             unsigned char* p0 = reinterpret_cast<unsigned char*>(blob.data()) + (size_t)o * per +
                                 (size_t)kc * TC_AP * TC_A_BYTES;
@@ -441,30 +441,66 @@ LfErr lf_setup_m2l_tc(lfmm_ctx* ctx, const double* A64, int KP, int RP)
                     }
                 }
         }
-    LF_TRY(lf_reserve(ctx->m2l_Atc, blob.size() * 4));
-    LF_CHECK(cudaMemcpy(ctx->m2l_Atc.ptr, blob.data(), blob.size() * 4, cudaMemcpyHostToDevice));
+    LF_TRY(lf_reserve(out, blob.size() * 4));
+    LF_CHECK(cudaMemcpy(out.ptr, blob.data(), blob.size() * 4, cudaMemcpyHostToDevice));
+    return LfErr();
+}
+
+// A64: [343][KP][RP] free M2L operators; M2M, L2L: [8][KP][RP] octant operators
+LfErr lf_setup_m2l_tc(lfmm_ctx* ctx, const double* A64, const double* M2M64, const double* L2L64, int KP, int RP)
+{
+    const int nc = lf_nc(ctx->p);
+    ctx->m2l_tc_ok = 0;
+    if (nc > TC_M || KP < nc || RP < nc) return LfErr();
+    LF_TRY(tc_blob(A64, TC_NALL, KP, RP, nc, ctx->m2l_Atc));
+    LF_TRY(tc_blob(M2M64, 8, KP, RP, nc, ctx->m2m_Atc));
+    LF_TRY(tc_blob(L2L64, 8, KP, RP, nc, ctx->l2l_Atc));
     LF_CHECK(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
     LF_CHECK(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     ctx->m2l_tc_ok = 1;
     return LfErr();
 }
 
-// multipoles [box][nc] -> two TF32 pieces per box, rows padded to 128 floats;
-// one more box of zeros stands in for missing sources
-__global__ void k_split_m(const float* __restrict__ M, int nbox, int nc, float* __restrict__ Ms)
+// expansions [box][nc] -> two TF32 pieces per box, rows padded to 128 floats,
+// for the boxes b0 .. b0 + count - 1 (the arrays hold nbox boxes per
+// right-hand side, blockIdx.y)
+__global__ void k_split_m(const float* __restrict__ M, int nbox, int nc, int b0, int count, float* __restrict__ Ms)
 {
-    // blockIdx.y: right-hand side
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const size_t tot = (size_t)(nbox + 1) * TC_MROW;
-    if (i >= tot) return;
+    if (i >= (size_t)count * TC_MROW) return;
     M += (size_t)blockIdx.y * nbox * nc;
     Ms += (size_t)blockIdx.y * (nbox + 1) * TC_XP * TC_MROW;
-    const int b = (int)(i / TC_MROW), k = (int)(i % TC_MROW);
-    const float x = (b < nbox && k < nc) ? M[(size_t)b * nc + k] : 0.f;
+    const int b = b0 + (int)(i / TC_MROW), k = (int)(i % TC_MROW);
+    const float x = (k < nc) ? M[(size_t)b * nc + k] : 0.f;
     const uint32_t hi = to_tf32(x);
     const uint32_t lo = to_tf32(x - __uint_as_float(hi));
     Ms[((size_t)b * TC_XP + 0) * TC_MROW + k] = __uint_as_float(hi);
     Ms[((size_t)b * TC_XP + 1) * TC_MROW + k] = __uint_as_float(lo);
+}
+
+static LfErr split_boxes(lfmm_ctx* ctx, const float* src, int b0, int count, cudaStream_t st)
+{
+    if (count <= 0) return LfErr();
+    const int nb = ctx->nbox_total, nr = ctx->nrhs_b;
+    LF_TRY(lf_reserve(ctx->m2l_Ms, (size_t)(nb + 1) * TC_XP * TC_MROW * sizeof(float) * nr));
+    const size_t tot = (size_t)count * TC_MROW;
+    ++ctx->launches, k_split_m<<<dim3((unsigned)((tot + 255) / 256), nr), 256, 0, st>>>(
+        src, nb, lf_nc(ctx->p), b0, count, ctx->m2l_Ms.as<float>());
+    return lf_cuda(cudaGetLastError(), "split");
+}
+
+static TcArgs tc_args(lfmm_ctx* ctx)
+{
+    const int nb = ctx->nbox_total;
+    TcArgs g;
+    g.levelh = ctx->m2l_levelh.as<double>();
+    g.Ms = ctx->m2l_Ms.as<float>();
+    g.zero_row = nb;
+    g.ms_stride = (size_t)(nb + 1) * TC_XP * TC_MROW;
+    g.l_stride = (size_t)nb * lf_nc(ctx->p);
+    g.nc = lf_nc(ctx->p);
+    g.err = reinterpret_cast<int*>(ctx->counts.as<char>() + LFMM_TIMEOUT_OFF);
+    return g;
 }
 
 LfErr lf_m2l_tc(lfmm_ctx* ctx, cudaStream_t st)
@@ -472,27 +508,61 @@ LfErr lf_m2l_tc(lfmm_ctx* ctx, cudaStream_t st)
     if (ctx->m2l_tc_ntiles == 0) return LfErr();
     const int nb = ctx->nbox_total;
     const int nr = ctx->nrhs_b;
-    LF_TRY(lf_reserve(ctx->m2l_Ms, (size_t)(nb + 1) * TC_XP * TC_MROW * sizeof(float) * nr));
-    const size_t tot = (size_t)(nb + 1) * TC_MROW;
-    ++ctx->launches, k_split_m<<<dim3((unsigned)((tot + 255) / 256), nr), 256, 0, st>>>(
-        ctx->Mexp.as<float>(), nb, lf_nc(ctx->p), ctx->m2l_Ms.as<float>());
-    TcArgs g;
+    LF_TRY(split_boxes(ctx, ctx->Mexp.as<float>(), 0, nb, st));
+    TcArgs g = tc_args(ctx);
     g.tiles = ctx->m2l_tc_tiles.as<int4>();
     g.sorted = ctx->m2l_sorted.as<int>();
     g.slots = ctx->m2l_slots.as<int>();
     g.cls = ctx->m2l_cls.as<int>();
-    g.levelh = ctx->m2l_levelh.as<double>();
+    g.noff = TC_NOFF;
+    g.unit_scale = 0;
     g.A = ctx->m2l_Atc.as<unsigned char>();
-    g.Ms = ctx->m2l_Ms.as<float>();
-    g.zero_row = nb;
     g.L = ctx->Lexp.as<float>();
-    g.ms_stride = (size_t)(nb + 1) * TC_XP * TC_MROW;
-    g.l_stride = (size_t)nb * lf_nc(ctx->p);
-    g.nc = lf_nc(ctx->p);
-    g.err = reinterpret_cast<int*>(ctx->counts.as<char>() + LFMM_TIMEOUT_OFF);
     g.groups = ctx->tc_groups;
     ++ctx->launches, k_m2l_tc<<<dim3(ctx->m2l_tc_ntiles * g.groups, nr), TC_THREADS, TC_SMEM, st>>>(g);
     return lf_cuda(cudaGetLastError(), "m2l tensor-core gemm");
+}
+
+// M2M into the parents at `level` (from their children one level down), or
+// L2L into the boxes at `level` (from their parents), on the tensor cores:
+// the source expansions are split into TF32 pieces first; the products are
+// added atomically (M2M into zeroed parents, L2L onto the M2L results).
+LfErr lf_shift_tc(lfmm_ctx* ctx, int level, bool l2l, cudaStream_t st)
+{
+    const int t0 = l2l ? ctx->tc_l2l_first[level] : ctx->tc_m2m_first[level];
+    const int t1 = l2l ? ctx->tc_l2l_first[level + 1] : ctx->tc_m2m_first[level + 1];
+    if (t1 <= t0) return LfErr();
+    const int nr = ctx->nrhs_b, nc = lf_nc(ctx->p);
+    const LfmmLevel& src = ctx->levels[l2l ? level - 1 : level + 1];
+    TcArgs g;
+    if (l2l) {
+        LF_TRY(split_boxes(ctx, ctx->Lexp.as<float>(), src.off, src.nbox, st));
+        g = tc_args(ctx);
+        g.sorted = ctx->m2l_sorted.as<int>();
+        g.slots = ctx->box_parent.as<int>();
+        g.noff = 1;
+        g.A = ctx->l2l_Atc.as<unsigned char>();
+        g.L = ctx->Lexp.as<float>();
+        g.groups = 1;
+    } else {
+        LF_TRY(split_boxes(ctx, ctx->Mexp.as<float>(), src.off, src.nbox, st));
+        const LfmmLevel& lv = ctx->levels[level];
+        const size_t ms = (size_t)ctx->nbox_total * nc;
+        LF_CHECK(cudaMemset2DAsync(ctx->Mexp.as<float>() + (size_t)lv.off * nc, ms * sizeof(float), 0,
+                                   sizeof(float) * (size_t)lv.nbox * nc, nr, st));
+        g = tc_args(ctx);
+        g.sorted = nullptr;
+        g.slots = ctx->m2m_slots.as<int>();
+        g.noff = 8;
+        g.A = ctx->m2m_Atc.as<unsigned char>();
+        g.L = ctx->Mexp.as<float>();
+        g.groups = 8;  // one child octant per CTA, summed by the atomics
+    }
+    g.tiles = ctx->tc_shift_tiles.as<int4>() + t0;
+    g.cls = ctx->shift_cls.as<int>();
+    g.unit_scale = 1;
+    ++ctx->launches, k_m2l_tc<<<dim3((t1 - t0) * g.groups, nr), TC_THREADS, TC_SMEM, st>>>(g);
+    return lf_cuda(cudaGetLastError(), l2l ? "l2l tensor-core gemm" : "m2m tensor-core gemm");
 }
 
 int lf_m2l_tc_tile() { return TC_N; }
