@@ -109,6 +109,7 @@ struct lfmm_ctx {
     // lists: offsets per level box (near_off[level_box] relative to level base) and entries
     DevBuf near_off, near_ent, m2l_off, m2l_ent, m2r_off, m2r_ent;
     int64_t near_total = 0, m2l_total = 0, m2r_total = 0;
+    int64_t list_cap[3] = {0, 0, 0};  // near, free M2L, reaction M2L entry capacities (grow-only)
 
     // free-space M2L as per-offset GEMMs (p <= 15)
     DevBuf m2l_A64, m2l_A32, m2l_cls, m2l_inv, m2l_slots, m2l_keys, m2l_sorted, m2l_tiles, m2l_levelh;

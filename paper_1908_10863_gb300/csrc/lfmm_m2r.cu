@@ -66,11 +66,12 @@ __global__ void k_m2r_keys(const LfmmComp* __restrict__ comps, int off, int nb, 
                            const uint32_t* __restrict__ rent, int level, uint32_t* __restrict__ keys,
                            uint32_t* __restrict__ vals, int* __restrict__ tgt, int* __restrict__ bad)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    // one warp per target box, lanes over its entries
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (i >= nb) return;
-    int t = off + i;
+    const int t = off + i;
     const int4 gt = grid[t];
-    for (int e = rbeg[t]; e < rend[t]; ++e) {
+    for (int e = rbeg[t] + (threadIdx.x & 31); e < rend[t]; e += 32) {
         uint32_t v = rent[e];
         int c = (int)(v >> LFMM_ENT_SHIFT);
         int s = (int)(v & LFMM_ENT_MASK);
@@ -185,7 +186,7 @@ LfErr lf_prepare_m2r(lfmm_ctx* ctx, cudaStream_t st)
     for (int l = la; l <= ctx->depth; ++l) {
         const LfmmLevel& lv = ctx->levels[l];
         if (lv.nbox == 0 || lv.m2r_count == 0) continue;
-        ++ctx->launches, k_m2r_keys<<<lf_blocks(lv.nbox, 128), 128, 0, st>>>(
+        ++ctx->launches, k_m2r_keys<<<lf_blocks(lv.nbox, 4), 128, 0, st>>>(
             ctx->comp_dev.as<LfmmComp>(), lv.off, lv.nbox, ctx->box_grid.as<int4>(), ctx->level_consts.as<float4>(), ctx->m2r_off.as<int>(),
             ctx->m2r_off.as<int>() + ctx->nbox_total, ctx->m2r_ent.as<uint32_t>(), l, keys - first, vals - first,
             ctx->m2r_tgt.as<int>(), bad);

@@ -447,22 +447,33 @@ __device__ __forceinline__ bool lf_admissible(const LfmmComp& c, float4 k, int s
     return true;
 }
 
+// Where the lists of one level go: entries are appended to the three arrays
+// at positions taken from device counters, so no level waits for the host.
+struct ListOut {
+    uint32_t* near_ent;  // parents' near entries are read from here too
+    uint32_t* m2l_ent;
+    uint32_t* m2r_ent;
+    unsigned* used;      // [0] near, [1] free M2L, [2] reaction M2L entries taken so far
+    unsigned cap0, cap1, cap2;
+    int* overflow;       // set when an array's capacity would be exceeded (nothing is written past it)
+    int *nbeg, *nend, *mbeg, *mend, *rbeg, *rend;
+};
+
 // One warp per target box.  The candidates (children of the parent's near
-// entries) are taken 32 at a time as 4 entries x 8 child slots; admissible
-// ones are counted (count pass) or written in candidate order through a
-// ballot prefix (fill pass), so the lists are deterministic.
-__global__ void k_list_pass(LfListMedium med, int level_off, int nb, int level, const int* __restrict__ parent,
-                            const int* __restrict__ cbeg, const int* __restrict__ cend,
-                            const int4* __restrict__ grid, const int* __restrict__ pnear_beg,
-                            const int* __restrict__ pnear_end, const uint32_t* __restrict__ near_ent_in,
-                            int* __restrict__ cnt, const int* __restrict__ off, uint32_t* __restrict__ m2l_out,
-                            uint32_t* __restrict__ m2r_out, uint32_t* __restrict__ near_out, int fill,
-                            unsigned long long* __restrict__ stat, const uint32_t* __restrict__ bkey,
-                            const int* __restrict__ inv, int* __restrict__ slots, int* __restrict__ slot_err)
+// entries) are taken 32 at a time as 4 entries x 8 child slots.  A first pass
+// counts the admissible ones per category; lane 0 then takes that many
+// positions in each array; a second pass writes them in candidate order
+// through a ballot prefix, so each box's lists are deterministic (the boxes'
+// segments are placed in whatever order the warps reach the counters).
+// With `slots`, the second pass also records each free M2L source at its
+// position in the target's octant-class offset list (slots[t][189],
+// inv[class][343]: position or -1).
+__global__ void k_list_level(LfListMedium med, int level_off, int nb, int level, const int* __restrict__ parent,
+                             const int* __restrict__ cbeg, const int* __restrict__ cend,
+                             const int4* __restrict__ grid, ListOut o, unsigned long long* __restrict__ stat,
+                             const uint32_t* __restrict__ bkey, const int* __restrict__ inv, int* __restrict__ slots,
+                             int* __restrict__ slot_err)
 {
-    // cnt / off: [3][nb] = free M2L, reaction M2L, near.  With `slots`, the fill
-    // pass also records each free M2L source at its position in the target's
-    // octant-class offset list (slots[t][189], inv[class][343]: position or -1).
     const int lane = threadIdx.x & 31;
     const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (i >= nb) return;  // whole warp
@@ -470,102 +481,116 @@ __global__ void k_list_pass(LfListMedium med, int level_off, int nb, int level, 
     const int pt = parent[t];
     const int4 gt = grid[t];
     const unsigned lt_mask = (1u << lane) - 1u;
-    int nf = 0, nr = 0, nn = 0;  // warp-uniform running counts
-    int wf = 0, wr = 0, wn = 0;
-    if (fill) {
-        wf = off[i];
-        wr = off[nb + i];
-        wn = off[2 * nb + i];
-    }
     const int cls = slots ? (int)(bkey[t] & 7u) : 0;
-    const int eb = pnear_beg[pt], ee = pnear_end[pt];
-    for (int e0 = eb; e0 < ee; e0 += 4) {
-        const int e = e0 + (lane >> 3), k = lane & 7;
-        int kind = -1;  // 0 free M2L, 1 reaction M2L, 2 near
-        uint32_t v = 0;
-        int sc = -1;
-        if (e < ee) {
-            const uint32_t ent = near_ent_in[e];
-            const int c = (int)(ent >> LFMM_ENT_SHIFT);
-            const int s = (int)(ent & LFMM_ENT_MASK);
-            const int ch = cbeg[s] + k;
-            if (ch < cend[s]) {
-                sc = ch;
-                const LfmmComp& cp = med.comps[c];
-                v = ((uint32_t)c << LFMM_ENT_SHIFT) | (uint32_t)sc;
-                if (lf_admissible(cp, med.lc[c * 16 + level], med.sep, gt, grid[sc]))
-                    kind = cp.is_free ? 0 : 1;
-                else
-                    kind = 2;
-            }
-        }
-        const unsigned bf = __ballot_sync(0xffffffffu, kind == 0);
-        const unsigned br = __ballot_sync(0xffffffffu, kind == 1);
-        const unsigned bn = __ballot_sync(0xffffffffu, kind == 2);
-        if (fill) {
-            if (kind == 0) {
-                m2l_out[wf + nf + __popc(bf & lt_mask)] = v;
-                if (slots) {
-                    const int4 gs = grid[sc];
-                    const int ox = gt.x - gs.x, oy = gt.y - gs.y, oz = gt.z - gs.z;
-                    int loc = -1;
-                    if (ox >= -3 && ox <= 3 && oy >= -3 && oy <= 3 && oz >= -3 && oz <= 3)
-                        loc = inv[cls * 343 + (ox + 3) * 49 + (oy + 3) * 7 + (oz + 3)];
-                    if (loc < 0)
-                        atomicAdd(slot_err, 1);
+    const int eb = o.nbeg[pt], ee = o.nend[pt];
+    int wf = 0, wr = 0, wn = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        int nf = 0, nr = 0, nn = 0;  // warp-uniform running counts
+        for (int e0 = eb; e0 < ee; e0 += 4) {
+            const int e = e0 + (lane >> 3), k = lane & 7;
+            int kind = -1;  // 0 free M2L, 1 reaction M2L, 2 near
+            uint32_t v = 0;
+            int sc = -1;
+            if (e < ee) {
+                const uint32_t ent = o.near_ent[e];
+                const int c = (int)(ent >> LFMM_ENT_SHIFT);
+                const int s = (int)(ent & LFMM_ENT_MASK);
+                const int ch = cbeg[s] + k;
+                if (ch < cend[s]) {
+                    sc = ch;
+                    const LfmmComp& cp = med.comps[c];
+                    v = ((uint32_t)c << LFMM_ENT_SHIFT) | (uint32_t)sc;
+                    if (lf_admissible(cp, med.lc[c * 16 + level], med.sep, gt, grid[sc]))
+                        kind = cp.is_free ? 0 : 1;
                     else
-                        slots[(size_t)t * 189 + loc] = sc;
+                        kind = 2;
                 }
-            } else if (kind == 1) {
-                m2r_out[wr + nr + __popc(br & lt_mask)] = v;
-            } else if (kind == 2) {
-                near_out[wn + nn + __popc(bn & lt_mask)] = v;
             }
+            const unsigned bf = __ballot_sync(0xffffffffu, kind == 0);
+            const unsigned br = __ballot_sync(0xffffffffu, kind == 1);
+            const unsigned bn = __ballot_sync(0xffffffffu, kind == 2);
+            if (pass == 1) {
+                if (kind == 0) {
+                    o.m2l_ent[wf + nf + __popc(bf & lt_mask)] = v;
+                    if (slots) {
+                        const int4 gs = grid[sc];
+                        const int ox = gt.x - gs.x, oy = gt.y - gs.y, oz = gt.z - gs.z;
+                        int loc = -1;
+                        if (ox >= -3 && ox <= 3 && oy >= -3 && oy <= 3 && oz >= -3 && oz <= 3)
+                            loc = inv[cls * 343 + (ox + 3) * 49 + (oy + 3) * 7 + (oz + 3)];
+                        if (loc < 0)
+                            atomicAdd(slot_err, 1);
+                        else
+                            slots[(size_t)t * 189 + loc] = sc;
+                    }
+                } else if (kind == 1) {
+                    o.m2r_ent[wr + nr + __popc(br & lt_mask)] = v;
+                } else if (kind == 2) {
+                    o.near_ent[wn + nn + __popc(bn & lt_mask)] = v;
+                }
+            }
+            nf += __popc(bf);
+            nr += __popc(br);
+            nn += __popc(bn);
         }
-        nf += __popc(bf);
-        nr += __popc(br);
-        nn += __popc(bn);
-    }
-    if (lane == 0) {
-        if (!fill) {
-            cnt[i] = nf;
-            cnt[nb + i] = nr;
-            cnt[2 * nb + i] = nn;
-        } else if (stat) {
-            if (nf) atomicAdd(&stat[0], (unsigned long long)nf);
-            if (nr) atomicAdd(&stat[1], (unsigned long long)nr);
+        if (pass == 1) {
+            if (lane == 0 && stat) {
+                if (nf) atomicAdd(&stat[0], (unsigned long long)nf);
+                if (nr) atomicAdd(&stat[1], (unsigned long long)nr);
+            }
+            break;
         }
+        // take the positions, and publish the ranges (empty where an array is full)
+        int ok = 0;
+        if (lane == 0) {
+            wn = (int)atomicAdd(&o.used[0], (unsigned)nn);
+            wf = (int)atomicAdd(&o.used[1], (unsigned)nf);
+            wr = (int)atomicAdd(&o.used[2], (unsigned)nr);
+            ok = (unsigned)wn + nn <= o.cap0 && (unsigned)wf + nf <= o.cap1 && (unsigned)wr + nr <= o.cap2;
+            if (!ok) atomicExch(o.overflow, 1);
+            o.nbeg[t] = ok ? wn : 0;
+            o.nend[t] = ok ? wn + nn : 0;
+            o.mbeg[t] = ok ? wf : 0;
+            o.mend[t] = ok ? wf + nf : 0;
+            o.rbeg[t] = ok ? wr : 0;
+            o.rend[t] = ok ? wr + nr : 0;
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) return;  // whole warp
+        wn = __shfl_sync(0xffffffffu, wn, 0);
+        wf = __shfl_sync(0xffffffffu, wf, 0);
+        wr = __shfl_sync(0xffffffffu, wr, 0);
     }
 }
 
-__global__ void k_set_ranges(int level_off, int nb, const int* __restrict__ off, const int* __restrict__ cnt,
-                             int base, int* __restrict__ beg, int* __restrict__ end)
+// particle-pair statistics of the leaf-level near lists (one warp per leaf,
+// lanes over its entries)
+__global__ void k_p2p_stats(const LfmmComp* __restrict__ comps, int level_off, int nb, const int* __restrict__ nbeg,
+                            const int* __restrict__ nend, const uint32_t* __restrict__ ent,
+                            const int* __restrict__ pbeg, const int* __restrict__ pend,
+                            unsigned long long* __restrict__ stat)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nb) return;
-    beg[level_off + i] = base + off[i];
-    end[level_off + i] = base + off[i] + cnt[i];
-}
-
-// particle-pair statistics of the leaf-level near lists
-__global__ void k_p2p_stats(const LfmmComp* __restrict__ comps, int level_off, int nb, const int* __restrict__ nbeg, const int* __restrict__ nend,
-                            const uint32_t* __restrict__ ent, const int* __restrict__ pbeg,
-                            const int* __restrict__ pend, unsigned long long* __restrict__ stat)
-{
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nb) return;
-    int t = level_off + i;
-    unsigned long long nt = (unsigned long long)(pend[t] - pbeg[t]);
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (i >= nb) return;  // whole warp
+    const int t = level_off + i;
+    const unsigned long long nt = (unsigned long long)(pend[t] - pbeg[t]);
     unsigned long long f = 0, r = 0;
-    for (int e = nbeg[t]; e < nend[t]; ++e) {
-        uint32_t v = ent[e];
-        int c = (int)(v >> LFMM_ENT_SHIFT);
-        int s = (int)(v & LFMM_ENT_MASK);
-        unsigned long long ns = (unsigned long long)(pend[s] - pbeg[s]);
+    for (int e = nbeg[t] + lane; e < nend[t]; e += 32) {
+        const uint32_t v = ent[e];
+        const int c = (int)(v >> LFMM_ENT_SHIFT);
+        const int s = (int)(v & LFMM_ENT_MASK);
+        const unsigned long long ns = (unsigned long long)(pend[s] - pbeg[s]);
         if (comps[c].is_free) f += nt * ns; else r += nt * ns;
     }
-    if (f) atomicAdd(&stat[2], f);
-    if (r) atomicAdd(&stat[3], r);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        f += __shfl_down_sync(0xffffffffu, f, d);
+        r += __shfl_down_sync(0xffffffffu, r, d);
+    }
+    if (lane == 0) {
+        if (f) atomicAdd(&stat[2], f);
+        if (r) atomicAdd(&stat[3], r);
+    }
 }
 
 // grow a buffer keeping its first `keep` bytes
@@ -832,7 +857,7 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
     int* rbeg = ctx->m2r_off.as<int>();
     int* rend = rbeg + nb;
     // level 0: near(root_t) = root of the source layer of every component
-    int64_t near_used = 0, m2l_used = 0, m2r_used = 0;
+    int64_t near_used = 0;
     {
         const LfmmLevel& r = ctx->levels[0];
         std::vector<uint32_t> rk(r.nbox);
@@ -870,78 +895,95 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
         ctx->levels[0].near_count = near_used;
     }
     unsigned long long* stat = reinterpret_cast<unsigned long long*>(ctx->counts.as<char>() + 20480);
-    LF_CHECK(cudaMemsetAsync(stat, 0, 8 * 8, st));
-    int maxnb = 0;
-    for (int l = 0; l <= depth; ++l) maxnb = std::max(maxnb, ctx->levels[l].nbox);
-    LF_TRY(lf_reserve(ctx->hist, (size_t)maxnb * 4 * 6 + 64));
-    int* cnt3 = ctx->hist.as<int>();
-    int* off3 = cnt3 + 3 * maxnb;
     // free M2L slot table [box][189] (for the gathered GEMMs), filled with the lists
     int* slot_err = reinterpret_cast<int*>(ctx->counts.as<char>() + 24576);
-    LF_CHECK(cudaMemsetAsync(slot_err, 0, sizeof(int), st));
     const bool want_slots = ctx->m2l_rm > 0 && depth >= 2;
-    if (want_slots) {
-        LF_TRY(lf_reserve(ctx->m2l_slots, (size_t)nb * 189 * sizeof(int)));
-        LF_CHECK(cudaMemsetAsync(ctx->m2l_slots.ptr, 0xff, (size_t)nb * 189 * sizeof(int), st));
+    if (want_slots) LF_TRY(lf_reserve(ctx->m2l_slots, (size_t)nb * 189 * sizeof(int)));
+    // list counters [3], overflow flag, and the counters after each level [17][3]
+    unsigned* used = reinterpret_cast<unsigned*>(ctx->counts.as<char>() + 28672);
+    int* overflow = reinterpret_cast<int*>(used + 3);
+    unsigned* snap = used + 4;
+    const int64_t nroot = near_used;
+    // capacities: the last build's, at least a per-box estimate; one more pass
+    // with the measured totals when an array overflows (first builds)
+    for (int k = 0; k < 3; ++k)
+        if (ctx->list_cap[k] == 0) ctx->list_cap[k] = (int64_t)nb * (k == 0 ? 64 : (k == 1 ? 189 : 16)) + nroot + 1024;
+    unsigned long long hs[8];
+    std::vector<unsigned> hsnap(3 * (size_t)(depth + 1));
+    for (int attempt = 0;; ++attempt) {
+        if (ctx->list_cap[0] > 0x7fffffffLL || ctx->list_cap[1] > 0x7fffffffLL || ctx->list_cap[2] > 0x7fffffffLL)
+            return "interaction lists too long";
+        // the root entries were uploaded to the front of near_ent: keep them if it grows
+        LF_TRY(grow_keep(ctx->near_ent, (size_t)ctx->list_cap[0] * 4 + 16, (size_t)nroot * 4, st));
+        LF_TRY(lf_reserve(ctx->m2l_ent, (size_t)ctx->list_cap[1] * 4 + 16));
+        LF_TRY(lf_reserve(ctx->m2r_ent, (size_t)ctx->list_cap[2] * 4 + 16));
+        const unsigned init[4] = {(unsigned)nroot, 0u, 0u, 0u};
+        LF_CHECK(cudaMemcpyAsync(used, init, sizeof(init), cudaMemcpyHostToDevice, st));
+        LF_CHECK(cudaMemsetAsync(stat, 0, 8 * 8, st));
+        LF_CHECK(cudaMemsetAsync(slot_err, 0, sizeof(int), st));
+        if (want_slots) LF_CHECK(cudaMemsetAsync(ctx->m2l_slots.ptr, 0xff, (size_t)nb * 189 * sizeof(int), st));
+        ListOut o;
+        o.near_ent = ctx->near_ent.as<uint32_t>();
+        o.m2l_ent = ctx->m2l_ent.as<uint32_t>();
+        o.m2r_ent = ctx->m2r_ent.as<uint32_t>();
+        o.used = used;
+        o.cap0 = (unsigned)ctx->list_cap[0];
+        o.cap1 = (unsigned)ctx->list_cap[1];
+        o.cap2 = (unsigned)ctx->list_cap[2];
+        o.overflow = overflow;
+        o.nbeg = nbeg;
+        o.nend = nend;
+        o.mbeg = mbeg;
+        o.mend = mend;
+        o.rbeg = rbeg;
+        o.rend = rend;
+        LF_CHECK(cudaMemcpyAsync(snap, used, 3 * sizeof(unsigned), cudaMemcpyDeviceToDevice, st));
+        for (int l = 1; l <= depth; ++l) {
+            const LfmmLevel& lv = ctx->levels[l];
+            if (lv.nbox > 0)
+                ++ctx->launches, k_list_level<<<lf_blocks(lv.nbox, 4), 128, 0, st>>>(
+                    med, lv.off, lv.nbox, l, par, cbeg, cend, ctx->box_grid.as<int4>(), o, stat,
+                    ctx->box_key.as<uint32_t>(), ctx->m2l_inv.as<int>(),
+                    (want_slots && l >= 2) ? ctx->m2l_slots.as<int>() : nullptr, slot_err);
+            LF_CHECK(cudaMemcpyAsync(snap + 3 * l, used, 3 * sizeof(unsigned), cudaMemcpyDeviceToDevice, st));
+        }
+        LF_TRY(lf_cuda(cudaGetLastError(), "lists"));
+        const LfmmLevel& lf = ctx->levels[depth];
+        ++ctx->launches, k_p2p_stats<<<lf_blocks(lf.nbox, 8), 256, 0, st>>>(ctx->comp_dev.as<LfmmComp>(), lf.off,
+                                                                          lf.nbox, nbeg, nend, o.near_ent, pbeg,
+                                                                          pend, stat);
+        LF_TRY(lf_cuda(cudaGetLastError(), "p2p stats"));
+        int hov = 0;
+        unsigned hused[3];
+        LF_CHECK(cudaMemcpyAsync(hs, stat, sizeof(hs), cudaMemcpyDeviceToHost, st));
+        LF_CHECK(cudaMemcpyAsync(&hov, overflow, sizeof(int), cudaMemcpyDeviceToHost, st));
+        LF_CHECK(cudaMemcpyAsync(hused, used, sizeof(hused), cudaMemcpyDeviceToHost, st));
+        LF_CHECK(cudaMemcpyAsync(hsnap.data(), snap, sizeof(unsigned) * hsnap.size(), cudaMemcpyDeviceToHost, st));
+        LF_CHECK(cudaStreamSynchronize(st));
+        if (!hov) break;
+        if (attempt >= 8) return "internal: interaction lists keep overflowing";
+        // the counters kept counting past the capacities, but boxes below a
+        // full array found no candidates: grow to at least the counted totals
+        // and at least double what overflowed
+        for (int k = 0; k < 3; ++k) {
+            const int64_t need = (int64_t)hused[k] + hused[k] / 8 + 1024;
+            if (need > ctx->list_cap[k]) ctx->list_cap[k] = std::max(need, 2 * ctx->list_cap[k]);
+        }
     }
-    int hb[4];
     for (int l = 1; l <= depth; ++l) {
         LfmmLevel& lv = ctx->levels[l];
-        const int n3 = lv.nbox;
-        ++ctx->launches, k_list_pass<<<lf_blocks(n3, 4), 128, 0, st>>>(
-            med, lv.off, n3, l, par, cbeg, cend, ctx->box_grid.as<int4>(), nbeg, nend, ctx->near_ent.as<uint32_t>(), cnt3,
-            nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, nullptr);
-        LF_TRY(lf_cuda(cudaGetLastError(), "list count"));
-        // one exclusive scan over the three count arrays; the category bases
-        // and the grand total come back with one synchronisation
-        LF_TRY(lf_scan_i32(ctx, cnt3, off3, 3 * (int64_t)n3, nullptr, st));
-        LF_CHECK(cudaMemcpyAsync(&hb[0], off3 + n3, sizeof(int), cudaMemcpyDeviceToHost, st));
-        LF_CHECK(cudaMemcpyAsync(&hb[1], off3 + 2 * n3, sizeof(int), cudaMemcpyDeviceToHost, st));
-        LF_CHECK(cudaMemcpyAsync(&hb[2], off3 + 3 * n3 - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
-        LF_CHECK(cudaMemcpyAsync(&hb[3], cnt3 + 3 * n3 - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
-        LF_CHECK(cudaStreamSynchronize(st));
-        const int64_t b1 = hb[0], b2 = hb[1];
-        const int64_t tf = b1, tr = b2 - b1, tn = (int64_t)hb[2] + hb[3] - b2;
-        if (near_used + tn > 0x7fffffffLL || m2l_used + tf > 0x7fffffffLL || m2r_used + tr > 0x7fffffffLL)
-            return "interaction lists too long";
-        LF_TRY(grow_keep(ctx->near_ent, (size_t)(near_used + tn + 1) * 4, (size_t)near_used * 4, st));
-        LF_TRY(grow_keep(ctx->m2l_ent, (size_t)(m2l_used + tf + 1) * 4, (size_t)m2l_used * 4, st));
-        LF_TRY(grow_keep(ctx->m2r_ent, (size_t)(m2r_used + tr + 1) * 4, (size_t)m2r_used * 4, st));
-        uint32_t* nent = ctx->near_ent.as<uint32_t>();
-        // offsets are relative to the concatenated scan: shift the output pointers by each category's base
-        ++ctx->launches, k_list_pass<<<lf_blocks(n3, 4), 128, 0, st>>>(
-            med, lv.off, n3, l, par, cbeg, cend, ctx->box_grid.as<int4>(), nbeg, nend, nent, cnt3, off3,
-            ctx->m2l_ent.as<uint32_t>() + m2l_used, ctx->m2r_ent.as<uint32_t>() + m2r_used - b1,
-            nent + near_used - b2, 1, stat, ctx->box_key.as<uint32_t>(), ctx->m2l_inv.as<int>(),
-            (want_slots && l >= 2) ? ctx->m2l_slots.as<int>() : nullptr, slot_err);
-        ++ctx->launches, k_set_ranges<<<lf_blocks(n3, 256), 256, 0, st>>>(lv.off, n3, off3, cnt3, (int)m2l_used, mbeg, mend);
-        ++ctx->launches, k_set_ranges<<<lf_blocks(n3, 256), 256, 0, st>>>(lv.off, n3, off3 + n3, cnt3 + n3,
-                                                                           (int)(m2r_used - b1), rbeg, rend);
-        ++ctx->launches, k_set_ranges<<<lf_blocks(n3, 256), 256, 0, st>>>(lv.off, n3, off3 + 2 * n3, cnt3 + 2 * n3,
-                                                                           (int)(near_used - b2), nbeg, nend);
-        LF_TRY(lf_cuda(cudaGetLastError(), "list fill"));
-        lv.near_base = near_used;
-        lv.near_count = tn;
-        lv.m2l_base = m2l_used;
-        lv.m2l_count = tf;
-        lv.m2r_base = m2r_used;
-        lv.m2r_count = tr;
-        near_used += tn;
-        m2l_used += tf;
-        m2r_used += tr;
+        const unsigned* a0 = &hsnap[3 * (size_t)(l - 1)];
+        const unsigned* a1 = &hsnap[3 * (size_t)l];
+        lv.near_base = a0[0];
+        lv.near_count = (int64_t)a1[0] - a0[0];
+        lv.m2l_base = a0[1];
+        lv.m2l_count = (int64_t)a1[1] - a0[1];
+        lv.m2r_base = a0[2];
+        lv.m2r_count = (int64_t)a1[2] - a0[2];
     }
-    ctx->m2r_total = m2r_used;
-    ctx->near_total = near_used;
-    ctx->m2l_total = m2l_used;
-    {
-        const LfmmLevel& lf = ctx->levels[depth];
-        ++ctx->launches, k_p2p_stats<<<lf_blocks(lf.nbox, 256), 256, 0, st>>>(ctx->comp_dev.as<LfmmComp>(), lf.off, lf.nbox, nbeg, nend,
-                                                              ctx->near_ent.as<uint32_t>(), pbeg, pend, stat);
-        LF_TRY(lf_cuda(cudaGetLastError(), "p2p stats"));
-    }
-    unsigned long long hs[8];
-    LF_CHECK(cudaMemcpyAsync(hs, stat, sizeof(hs), cudaMemcpyDeviceToHost, st));
-    LF_CHECK(cudaStreamSynchronize(st));
+    ctx->near_total = hsnap[3 * (size_t)depth + 0];
+    ctx->m2l_total = hsnap[3 * (size_t)depth + 1];
+    ctx->m2r_total = hsnap[3 * (size_t)depth + 2];
     ctx->stats[LFMM_STAT_N] = n;
     ctx->stats[LFMM_STAT_DEPTH] = depth;
     ctx->stats[LFMM_STAT_BOXES] = tot;

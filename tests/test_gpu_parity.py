@@ -182,3 +182,24 @@ def test_precision_change_after_build_reassembles_reaction_operators(p):
     assert oracle.err2(ref64[0], again64[0]) < 1e-13
     assert oracle.err2(ref32[0], got32[0]) < 1e-6
     assert oracle.err2(ref64[0], got32[0]) < 1e-5
+
+
+def test_rebuild_larger_geometry_grows_the_lists():
+    # list arrays keep the capacity of the first build; a much larger
+    # geometry overflows them once and is rebuilt with measured capacities
+    small = workloads.config2(2000, seed=3)
+    big = workloads.config2(150000, seed=4)
+    with LayeredFMM(big.d, big.eps, 6) as f:
+        f.build(small.xyz, small.layer)
+        f.evaluate(small.q)
+        f.build(big.xyz, big.layer)
+        phi, E = f.evaluate(big.q)
+        st = f.stats()
+    with LayeredFMM(big.d, big.eps, 6) as g:
+        g.build(big.xyz, big.layer)
+        phi0, E0 = g.evaluate(big.q)
+        st0 = g.stats()
+    for k in ("boxes", "m2l_free", "m2l_reaction", "p2p_free", "p2p_reaction"):
+        assert st[k] == st0[k], k
+    assert oracle.err2(phi0, phi) < 1e-13
+    assert oracle.err2(E0, E) < 1e-13
