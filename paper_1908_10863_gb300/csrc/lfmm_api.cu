@@ -15,7 +15,9 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <cfloat>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "../../include/lfmm.h"
@@ -473,6 +475,51 @@ static lfmm_status fail(lfmm_ctx* ctx, const LfErr& e)
     return status_of(e);
 }
 
+// ---- host-side input checks (no device work for invalid inputs) ----
+// Branch-free passes over [0, n) split between a few threads for large n;
+// the first offending index is located only when a pass reports one.
+template <typename F>
+static bool any_bad(int64_t n, F bad_range)
+{
+    const int64_t chunk = 1 << 18;
+    const unsigned hw = std::thread::hardware_concurrency();
+    const int nt = (int)std::min<int64_t>(std::min<unsigned>(hw ? hw : 1, 8u), (n + chunk - 1) / chunk);
+    if (nt <= 1) return bad_range(0, n);
+    std::vector<std::thread> th;
+    std::vector<char> res(nt, 0);
+    for (int k = 0; k < nt; ++k)
+        th.emplace_back([&, k] { res[k] = bad_range(n * k / nt, n * (k + 1) / nt); });
+    for (auto& t : th) t.join();
+    for (char r : res)
+        if (r) return true;
+    return false;
+}
+
+// layer l spans dd[l + 1] < z < dd[l] with dd[0] = +inf, dd[L + 1] = -inf
+static bool points_bad(const lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int64_t b, int64_t e)
+{
+    double dd[4];  // at most two interfaces
+    const int L = ctx->L;
+    dd[0] = INFINITY;
+    for (int k = 0; k < L; ++k) dd[k + 1] = ctx->d[k];
+    dd[L + 1] = -INFINITY;
+    int bad = 0;
+    for (int64_t i = b; i < e; ++i) {
+        const int l = layer[i];
+        const int lc = l < 0 ? 0 : (l > L ? L : l);
+        const double x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+        bad |= (l != lc) | !(z < dd[lc]) | !(z > dd[lc + 1]) | !(fabs(x) <= DBL_MAX) | !(fabs(y) <= DBL_MAX);
+    }
+    return bad != 0;
+}
+
+static bool charges_bad(const double* q, int64_t b, int64_t e)
+{
+    int bad = 0;
+    for (int64_t i = b; i < e; ++i) bad |= !(fabs(q[i]) <= DBL_MAX);
+    return bad != 0;
+}
+
 int lf_find_comp(const lfmm_ctx* ctx, int l, int lp, int a, int b)
 {
     for (int c = 0; c < ctx->ncomp; ++c) {
@@ -636,17 +683,19 @@ lfmm_status lfmm_build(lfmm_ctx* ctx, int64_t n, const double* xyz, const int32_
     if (!ctx) return LFMM_EINVAL;
     ctx->err.clear();
     if (n < 1 || !xyz || !layer) return fail(ctx, "EINVAL: need n >= 1 and non-null arrays");
-    for (int64_t i = 0; i < n; ++i) {
-        int l = layer[i];
-        double z = xyz[3 * i + 2];
-        if (l < 0 || l > ctx->L || (l > 0 && !(z < ctx->d[l - 1])) || (l < ctx->L && !(z > ctx->d[l]))) {
-            char buf[128];
-            snprintf(buf, sizeof buf, "EINVAL: charge %lld has an invalid layer id or lies outside its layer",
-                     (long long)i);
-            return fail(ctx, buf);
+    if (any_bad(n, [&](int64_t b, int64_t e) { return points_bad(ctx, xyz, layer, b, e); })) {
+        for (int64_t i = 0; i < n; ++i) {
+            const int l = layer[i];
+            const double z = xyz[3 * i + 2];
+            if (l < 0 || l > ctx->L || (l > 0 && !(z < ctx->d[l - 1])) || (l < ctx->L && !(z > ctx->d[l]))) {
+                char buf[128];
+                snprintf(buf, sizeof buf, "EINVAL: charge %lld has an invalid layer id or lies outside its layer",
+                         (long long)i);
+                return fail(ctx, buf);
+            }
+            if (!std::isfinite(xyz[3 * i]) || !std::isfinite(xyz[3 * i + 1]) || !std::isfinite(z))
+                return fail(ctx, "EINVAL: non-finite coordinate");
         }
-        if (!std::isfinite(xyz[3 * i]) || !std::isfinite(xyz[3 * i + 1]) || !std::isfinite(z))
-            return fail(ctx, "EINVAL: non-finite coordinate");
     }
     LfErr e = lf_reserve(ctx->xyz_in, (size_t)n * 24);
     if (e.empty()) e = lf_reserve(ctx->layer_in, (size_t)n * 4);
@@ -697,8 +746,8 @@ lfmm_status lfmm_evaluate(lfmm_ctx* ctx, int nrhs, const double* q, double* phi,
     if (!ctx->built) return fail(ctx, "ESTATE: evaluate before a successful build"), LFMM_ESTATE;
     if (nrhs < 1 || !q || !phi) return fail(ctx, "EINVAL: need nrhs >= 1, q and phi");
     const int64_t n = ctx->n;
-    for (int64_t i = 0; i < n * nrhs; ++i)
-        if (!std::isfinite(q[i])) return fail(ctx, "ENUMERIC: non-finite charge"), LFMM_ENUMERIC;
+    if (any_bad(n * nrhs, [&](int64_t b, int64_t e) { return charges_bad(q, b, e); }))
+        return fail(ctx, "ENUMERIC: non-finite charge"), LFMM_ENUMERIC;
     LfErr e = lf_reserve(ctx->q_stage, (size_t)n * nrhs * 8);
     if (e.empty()) e = lf_reserve(ctx->phi_stage, (size_t)n * nrhs * 8);
     if (e.empty() && field) e = lf_reserve(ctx->fld_stage, (size_t)n * nrhs * 24);

@@ -173,12 +173,24 @@ class LayeredFMM:
                                                 ctypes.c_void_p(layer.data_ptr()), s), "lfmm_build_device")
         self.n = n
 
-    def evaluate(self, q, field: bool = True):
-        """q: [n] or [nrhs, n] host charges -> (phi, E) host arrays."""
+    def evaluate(self, q, field: bool = True, out=None):
+        """q: [n] or [nrhs, n] host charges -> (phi, E) host arrays.  `out`
+        may give preallocated float64 C-contiguous arrays (phi shaped like q,
+        E like q plus a trailing 3, or None) that are written and returned."""
         q = _f64(q)
         single = q.ndim == 1
         q2 = q.reshape(1, -1) if single else q
         nrhs = q2.shape[0]
+        if out is not None:
+            phi_o, fld_o = out
+            for a, shp in ((phi_o, q.shape), (fld_o, q.shape + (3,))):
+                if a is not None and (a.shape != shp or a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]):
+                    raise ValueError("out arrays must be C-contiguous float64 of shapes %s and %s"
+                                     % (q.shape, q.shape + (3,)))
+            field = fld_o is not None
+            self._check(self._lib.lfmm_evaluate(self._ctx, nrhs, _ptr(q2), _ptr(phi_o),
+                                                _ptr(fld_o) if field else None), "lfmm_evaluate")
+            return phi_o, fld_o
         phi = np.zeros_like(q2)
         fld = np.zeros(q2.shape + (3,)) if field else None
         self._check(self._lib.lfmm_evaluate(self._ctx, nrhs, _ptr(q2), _ptr(phi), _ptr(fld) if field else None),

@@ -203,3 +203,32 @@ def test_rebuild_larger_geometry_grows_the_lists():
         assert st[k] == st0[k], k
     assert oracle.err2(phi0, phi) < 1e-13
     assert oracle.err2(E0, E) < 1e-13
+
+
+def test_host_inputs_checked_before_device_work():
+    w = workloads.config2(300000, seed=5)  # large enough for the threaded checks
+    with LayeredFMM(w.d, w.eps, 6) as f:
+        for bad_i, what in ((123456, "nan"), (299999, "layer"), (7, "inf")):
+            xyz = w.xyz.copy()
+            lay = w.layer.copy()
+            if what == "nan":
+                xyz[bad_i, 0] = np.nan
+            elif what == "inf":
+                xyz[bad_i, 2] = np.inf
+            else:
+                lay[bad_i] = 3
+            with pytest.raises(LfmmError) as ei:
+                f.build(xyz, lay)
+            assert "EINVAL" in str(ei.value), what
+        f.build(w.xyz, w.layer)
+        q = w.q.copy()
+        q[200000] = np.nan
+        with pytest.raises(LfmmError) as ei:
+            f.evaluate(q)
+        assert "ENUMERIC" in str(ei.value)
+        phi = np.empty(w.n)
+        E = np.empty((w.n, 3))
+        r = f.evaluate(w.q, out=(phi, E))
+        assert r[0] is phi and r[1] is E
+        ref_phi, ref_E = f.evaluate(w.q)
+        assert np.array_equal(phi, ref_phi) or oracle.err2(ref_phi, phi) < 1e-14
