@@ -241,7 +241,11 @@ __global__ void k_rel_pos(int leaf_off, int nleaf, const LfD4* __restrict__ cen,
 template <int RB>
 __global__ void __launch_bounds__(32 * PW_WARPS) k_p2p_warp(P2PArgs a, const float4* __restrict__ rel, int nleaf)
 {
-    __shared__ float sx[PW_WARPS][32], sy[PW_WARPS][32], sz[PW_WARPS][32], sq[PW_WARPS][RB][32];
+    // one charge vector: sources staged as (x, y, z, q), one 16-byte shared load per pair
+    constexpr bool ONE = (RB == 1);
+    __shared__ float sx[PW_WARPS][ONE ? 1 : 32], sy[PW_WARPS][ONE ? 1 : 32], sz[PW_WARPS][ONE ? 1 : 32],
+        sq[PW_WARPS][RB][ONE ? 1 : 32];
+    __shared__ float4 sp[PW_WARPS][ONE ? 32 : 1];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int wi = blockIdx.x * PW_WARPS + w;
     if (wi >= nleaf * a.split) return;  // whole warp
@@ -283,18 +287,49 @@ __global__ void __launch_bounds__(32 * PW_WARPS) k_p2p_warp(P2PArgs a, const flo
                 __syncwarp();
                 if (j < se) {
                     const float4 r = rel[j];
-                    sx[w][lane] = r.x + dx0;
-                    sy[w][lane] = r.y + dy0;
-                    sz[w][lane] = szs * r.z + dz0;
+                    if constexpr (ONE) {
+                        sp[w][lane] = make_float4(r.x + dx0, r.y + dy0, szs * r.z + dz0, q[j]);
+                    } else {
+                        sx[w][lane] = r.x + dx0;
+                        sy[w][lane] = r.y + dy0;
+                        sz[w][lane] = szs * r.z + dz0;
 #pragma unroll
-                    for (int k = 0; k < RB; ++k)
-                        if (k < a.nr) sq[w][k][lane] = q[(size_t)k * a.qstride + j];
+                        for (int k = 0; k < RB; ++k)
+                            if (k < a.nr) sq[w][k][lane] = q[(size_t)k * a.qstride + j];
+                    }
                 }
                 __syncwarp();
                 if (!valid) continue;
                 const int cnt = min(32, se - cb);
                 // this lane's contiguous share of the staged sources
                 const int u0 = (slice * cnt) / G, u1 = ((slice + 1) * cnt) / G;
+                if constexpr (ONE) {
+                    if (cp.is_free) {
+                        float& P = part.P[0].s;
+                        float& Ex = part.Ex[0].s;
+                        float& Ey = part.Ey[0].s;
+                        float& Ez = part.Ez[0].s;
+#pragma unroll 4
+                        for (int u = u0; u < u1; ++u) {
+                            const float4 v = sp[w][u];
+                            const float dx = xi - v.x, dy = yi - v.y, dz = zi - v.z;
+                            const float r2 = dx * dx + dy * dy + dz * dz;
+                            const float ir = (r2 > 0.f) ? rsqrtf(r2) : 0.f;  // the target itself: no term
+                            const float q3 = v.w * ir * ir * ir;
+                            P += v.w * ir;
+                            Ex += q3 * dx;
+                            Ey += q3 * dy;
+                            Ez += q3 * dz;
+                        }
+                    } else {
+                        for (int u = u0; u < u1; ++u) {
+                            const float4 v = sp[w][u];
+                            p2p_reaction_add<float, 1>(cp, xi - v.x, yi - v.y, zi - v.z, &sp[w][u].w, 0, 1, a.Qn,
+                                                       a.gl_t, a.gl_w, part);
+                        }
+                    }
+                    continue;
+                }
                 if (cp.is_free) {
                     for (int u = u0; u < u1; ++u)
                         p2p_free_add<float, RB>(xi - sx[w][u], yi - sy[w][u], zi - sz[w][u], &sq[w][0][u], 32, a.nr,
