@@ -581,6 +581,7 @@ lfmm_status lfmm_create(const double* d, int L, const double* eps, int p, lfmm_c
     if (e.empty()) e = lf_setup_m2l_ops(ctx);
     // the setup tables travel by pageable copies on the legacy stream, which
     // the context's non-blocking streams do not wait for
+    if (e.empty()) e = lf_cuda(cudaMallocHost(&ctx->host_pin, 4096), "pinned host buffer");
     if (e.empty()) e = lf_cuda(cudaDeviceSynchronize(), "setup copies");
     if (!e.empty()) {
         lfmm_status s = status_of(e);
@@ -825,6 +826,7 @@ void lfmm_destroy(lfmm_ctx* ctx)
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     if (ctx->s_main) cudaStreamDestroy(ctx->s_main);
     if (ctx->s_near) cudaStreamDestroy(ctx->s_near);
+    if (ctx->host_pin) cudaFreeHost(ctx->host_pin);
     delete ctx;
 }
 

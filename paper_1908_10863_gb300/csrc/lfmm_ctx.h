@@ -124,6 +124,10 @@ struct lfmm_ctx {
     std::vector<int> m2m_first, l2l_first;  // first tile of each level
     int l2l_tile_base = 0, shift_ready = 0;
     std::vector<int4> m2l_tiles_h, l2l_tiles_h, m2m_tiles_h, tc_tiles_h;  // host staging of asynchronous uploads
+    std::vector<float4> level_consts_h;
+    void* host_pin = nullptr;  // small pinned host buffer for readbacks that must not wait
+    std::vector<uint32_t> root_ent_h;
+    std::vector<int> root_beg_h, root_end_h, root_zero_h;
     double m2l_levelh_h[16] = {0};
     int m2l_tc_ok = 0, m2l_tc_ntiles = 0, use_tc = 1, tc_groups = 27;
     // reaction M2L grouped by geometry key on interface-aligned levels

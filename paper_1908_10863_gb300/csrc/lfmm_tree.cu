@@ -710,19 +710,11 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
     uint32_t* vals = ctx->idx.as<uint32_t>();
     ++ctx->launches, k_make_keys<<<lf_blocks(n, 256), 256, 0, st>>>(xyz, layer, n, kp, keys, vals, ctx->err_flag.as<int>());
     LF_TRY(lf_cuda(cudaGetLastError(), "make keys"));
-    int herr[4];
-    LF_CHECK(cudaMemcpyAsync(herr, ctx->err_flag.ptr, sizeof(herr), cudaMemcpyDeviceToHost, st));
-    LF_CHECK(cudaStreamSynchronize(st));
-    if (herr[0] & 2) {
-        char buf[160];
-        snprintf(buf, sizeof buf, "EINVAL: non-finite coordinate at charge %d", herr[1]);
-        return buf;
-    }
-    if (herr[0] & 1) {
-        char buf[160];
-        snprintf(buf, sizeof buf, "EINVAL: charge %d has an invalid layer id or lies outside its layer", herr[1]);
-        return buf;
-    }
+    // the flags come back (into pinned memory, without waiting) with the level
+    // counts: a rejected point gets a clamped, valid key, so the sort and the
+    // counts below stay in bounds
+    int* herr = reinterpret_cast<int*>(ctx->host_pin);
+    LF_CHECK(cudaMemcpyAsync(herr, ctx->err_flag.ptr, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
     LF_TRY(lf_radix_sort(ctx, keys, vals, n, st));
 
     // sorted particle arrays
@@ -742,6 +734,17 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
     int hc[16];
     LF_CHECK(cudaMemcpyAsync(hc, cnt, sizeof(int) * 16, cudaMemcpyDeviceToHost, st));
     LF_CHECK(cudaStreamSynchronize(st));
+    if (herr[0] & 2) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "EINVAL: non-finite coordinate at charge %d", herr[1]);
+        return buf;
+    }
+    if (herr[0] & 1) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "EINVAL: charge %d has an invalid layer id or lies outside its layer", herr[1]);
+        return buf;
+    }
+
     // the level whose mean leaf occupancy is nearest (in ratio) to half the
     // capacity, among the levels whose mean stays within the capacity
     int depth = LFMM_FINE_LEVEL;
@@ -830,7 +833,9 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
     LF_TRY(lf_cuda(cudaGetLastError(), "centers"));
     {
         // per (component, level) constants of the admissibility test
-        std::vector<float4> lc((size_t)LFMM_MAXCOMP * 16, make_float4(0.f, 0.f, 0.f, 0.f));
+        // host staging owned by the context: the copy needs no synchronisation
+        std::vector<float4>& lc = ctx->level_consts_h;
+        lc.assign((size_t)LFMM_MAXCOMP * 16, make_float4(0.f, 0.f, 0.f, 0.f));
         const double oz = ctx->origin[2];
         for (int c = 0; c < ctx->ncomp; ++c)
             for (int l = 0; l <= depth && l < 16; ++l) {
@@ -842,7 +847,6 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
         LF_TRY(lf_reserve(ctx->level_consts, sizeof(float4) * lc.size()));
         LF_CHECK(cudaMemcpyAsync(ctx->level_consts.ptr, lc.data(), sizeof(float4) * lc.size(), cudaMemcpyHostToDevice,
                                  st));
-        LF_CHECK(cudaStreamSynchronize(st));
     }
 
     // ---- lists ----
@@ -866,8 +870,15 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
         int root_of[3] = {-1, -1, -1};
         for (int i = 0; i < r.nbox; ++i) root_of[rk[i]] = r.off + i;
         for (int l = 0; l < 3; ++l) ctx->nlayer_used[l] = root_of[l] >= 0;
-        std::vector<uint32_t> ent;
-        std::vector<int> hb(r.nbox), he(r.nbox), zero(r.nbox, 0);
+        // host staging owned by the context: the copies need no synchronisation
+        std::vector<uint32_t>& ent = ctx->root_ent_h;
+        std::vector<int>& hb = ctx->root_beg_h;
+        std::vector<int>& he = ctx->root_end_h;
+        std::vector<int>& zero = ctx->root_zero_h;
+        ent.clear();
+        hb.assign(r.nbox, 0);
+        he.assign(r.nbox, 0);
+        zero.assign(r.nbox, 0);
         for (int i = 0; i < r.nbox; ++i) {
             int tl = (int)rk[i];
             hb[i] = (int)ent.size();
@@ -889,7 +900,6 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
         LF_CHECK(cudaMemcpyAsync(mend + r.off, zero.data(), 4 * r.nbox, cudaMemcpyHostToDevice, st));
         LF_CHECK(cudaMemcpyAsync(rbeg + r.off, zero.data(), 4 * r.nbox, cudaMemcpyHostToDevice, st));
         LF_CHECK(cudaMemcpyAsync(rend + r.off, zero.data(), 4 * r.nbox, cudaMemcpyHostToDevice, st));
-        LF_CHECK(cudaStreamSynchronize(st));
         near_used = (int64_t)ent.size();
         ctx->levels[0].near_base = 0;
         ctx->levels[0].near_count = near_used;

@@ -232,3 +232,25 @@ def test_host_inputs_checked_before_device_work():
         assert r[0] is phi and r[1] is E
         ref_phi, ref_E = f.evaluate(w.q)
         assert np.array_equal(phi, ref_phi) or oracle.err2(ref_phi, phi) < 1e-14
+
+
+def test_device_inputs_checked_on_the_device():
+    # build_device has no host copy to check: the key kernel flags bad points
+    # and the build returns EINVAL, leaving the context usable
+    torch = pytest.importorskip("torch")
+    w = workloads.config2(50000, seed=6)
+    dev = torch.device("cuda")
+    with LayeredFMM(w.d, w.eps, 6) as f:
+        for what in ("nan", "layer"):
+            xyz = w.xyz.copy()
+            lay = w.layer.copy()
+            if what == "nan":
+                xyz[4321, 1] = np.nan
+            else:
+                lay[4321] = -1
+            with pytest.raises(LfmmError) as ei:
+                f.build_device(torch.from_numpy(xyz).to(dev), torch.from_numpy(lay).to(dev))
+            assert "EINVAL" in str(ei.value), what
+        f.build_device(torch.from_numpy(w.xyz).to(dev), torch.from_numpy(w.layer).to(dev))
+        phi, _ = f.evaluate(w.q)
+        assert np.all(np.isfinite(phi))
