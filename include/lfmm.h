@@ -106,6 +106,16 @@ lfmm_status lfmm_evaluate(lfmm_ctx* ctx, int nrhs, const double* q, double* phi,
 lfmm_status lfmm_evaluate_device(lfmm_ctx* ctx, int nrhs, const double* q_dev, double* phi_dev, double* field_dev,
                                  void* cuda_stream);
 
+/* Self-check of failure detection (the paper has no counterpart).  Every
+ * wait of the device pipelines is bounded: when one runs out, the kernel
+ * counts a timeout, releases what it holds and returns, and the evaluate
+ * reports LFMM_ETIMEOUT.  This call exercises that path on purpose: one
+ * thread waits on a barrier that will never complete, with a budget of
+ * limit_ms milliseconds (0 < limit_ms <= 2000).  Returns LFMM_ETIMEOUT when
+ * the wait ran out and was reported (the expected outcome); the context
+ * stays usable and its timeout counter is cleared. */
+lfmm_status lfmm_check_bounded_wait(lfmm_ctx* ctx, double limit_ms);
+
 /* Message of the last failed call on ctx ("" if none); valid until the next call. */
 const char* lfmm_last_error(const lfmm_ctx* ctx);
 

@@ -798,6 +798,19 @@ lfmm_status lfmm_evaluate_device(lfmm_ctx* ctx, int nrhs, const double* q_dev, d
     return LFMM_OK;
 }
 
+lfmm_status lfmm_check_bounded_wait(lfmm_ctx* ctx, double limit_ms)
+{
+    if (!ctx) return LFMM_EINVAL;
+    ctx->err.clear();
+    if (!(limit_ms > 0.0 && limit_ms <= 2000.0)) return fail(ctx, "EINVAL: limit_ms must be in (0, 2000]");
+    LfErr e = lf_reserve(ctx->counts, 65536);
+    int timed_out = 0;
+    if (e.empty()) e = lf_wait_probe(ctx, limit_ms, &timed_out);
+    if (!e.empty()) return fail(ctx, e);
+    if (timed_out) return fail(ctx, "ETIMEOUT: the probe's wait ran out, as designed"), LFMM_ETIMEOUT;
+    return LFMM_OK;
+}
+
 const char* lfmm_last_error(const lfmm_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 void lfmm_destroy(lfmm_ctx* ctx)

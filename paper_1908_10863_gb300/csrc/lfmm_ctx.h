@@ -221,6 +221,7 @@ LfErr lf_shift_gemm(lfmm_ctx* ctx, int level, bool l2l, cudaStream_t st);
 #define LFMM_TIMEOUT_OFF 40960
 LfErr lf_setup_m2l_tc(lfmm_ctx* ctx, const double* A64, const double* M2M64, const double* L2L64, int KP, int RP);
 LfErr lf_shift_tc(lfmm_ctx* ctx, int level, bool l2l, cudaStream_t st);
+LfErr lf_wait_probe(lfmm_ctx* ctx, double limit_ms, int* timed_out);
 LfErr lf_m2l_tc(lfmm_ctx* ctx, cudaStream_t st);
 int lf_m2l_tc_tile();
 LfErr lf_surrogate_alloc(lfmm_ctx* ctx);

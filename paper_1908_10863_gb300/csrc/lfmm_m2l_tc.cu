@@ -126,15 +126,17 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity)
         : "memory");
     return ok != 0;
 }
-// bounded wait: false after ~1 s
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+// bounded wait: false after `limit` cycles
+__device__ __forceinline__ bool mbar_wait_for(uint64_t* bar, uint32_t parity, long long limit)
 {
     if (mbar_try(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try(bar, parity))
-        if (clock64() - t0 > TC_SPIN_CYCLES) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
 }
+// the pipeline's waits: false after ~1 s
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) { return mbar_wait_for(bar, parity, TC_SPIN_CYCLES); }
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
 {
     asm volatile(
@@ -563,6 +565,37 @@ LfErr lf_shift_tc(lfmm_ctx* ctx, int level, bool l2l, cudaStream_t st)
     g.unit_scale = 1;
     ++ctx->launches, k_m2l_tc<<<dim3((t1 - t0) * g.groups, nr), TC_THREADS, TC_SMEM, st>>>(g);
     return lf_cuda(cudaGetLastError(), l2l ? "l2l tensor-core gemm" : "m2m tensor-core gemm");
+}
+
+// Self-check of the bounded-wait path: one thread waits on a barrier that
+// expects two arrivals and gets one, so the wait must run out after `limit`
+// cycles and count a timeout, exactly as a stalled pipeline stage would.
+__global__ void k_wait_probe(long long limit, int* err)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 2);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_arrive(&bar);
+    if (!mbar_wait_for(&bar, 0, limit)) atomicAdd(err, 1);
+}
+
+LfErr lf_wait_probe(lfmm_ctx* ctx, double limit_ms, int* timed_out)
+{
+    int khz = 0;  // SM clock; the GB300's maximum (2.07 GHz) if the runtime does not report it
+    if (cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, ctx->device) != cudaSuccess) {
+        (void)cudaGetLastError();
+        khz = 0;
+    }
+    if (khz <= 0) khz = 2070000;
+    const long long limit = (long long)(limit_ms * (double)khz);
+    int* err = reinterpret_cast<int*>(ctx->counts.as<char>() + LFMM_TIMEOUT_OFF);
+    LF_CHECK(cudaMemsetAsync(err, 0, sizeof(int), ctx->s_main));
+    ++ctx->launches, k_wait_probe<<<1, 32, 0, ctx->s_main>>>(limit, err);
+    LF_TRY(lf_cuda(cudaGetLastError(), "wait probe"));
+    LF_CHECK(lf_d2h(timed_out, err, sizeof(int), ctx->s_main));
+    LF_CHECK(cudaMemsetAsync(err, 0, sizeof(int), ctx->s_main));
+    return LfErr();
 }
 
 int lf_m2l_tc_tile() { return TC_N; }

@@ -47,7 +47,8 @@ EXPORTED = ["lfmm_create", "lfmm_set_option", "lfmm_build", "lfmm_build_device",
             "lfmm_surrogate_train", "lfmm_surrogate_info", "lfmm_surrogate_eval", "lfmm_surrogate_get_params",
             "lfmm_surrogate_set_params", "lfmm_surrogate_forward", "lfmm_surrogate_loss_grad",
             "lfmm_batch_create", "lfmm_batch_offsets", "lfmm_batch_evaluate_device", "lfmm_batch_evaluate",
-            "lfmm_batch_info", "lfmm_batch_last_error", "lfmm_batch_destroy", "lfmm_autotune"]
+            "lfmm_batch_info", "lfmm_batch_last_error", "lfmm_batch_destroy", "lfmm_autotune",
+            "lfmm_check_bounded_wait"]
 BATCH_INFO = ["problems", "charges", "graph_nodes", "kernel_nodes", "captures", "graph_launches", "direct_runs",
               "timeouts"]
 NOALLOC_MAX_POINTS = 65536
@@ -92,6 +93,7 @@ def load(build: bool = True):
     lib.lfmm_surrogate_set_params.argtypes = [_ctxp] + comp + [_fp]
     lib.lfmm_surrogate_forward.argtypes = [_ctxp] + comp + [ctypes.c_int, _fp, _fp]
     lib.lfmm_surrogate_loss_grad.argtypes = [_ctxp] + comp + [ctypes.c_int, _fp, _fp, _dp, _fp]
+    lib.lfmm_check_bounded_wait.argtypes = [_ctxp, ctypes.c_double]
     lib.lfmm_autotune.argtypes = [_ctxp, ctypes.c_int64, _dp, _ip, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int,
                                   ctypes.POINTER(ctypes.c_int)]
     lib.lfmm_batch_create.argtypes = [ctypes.POINTER(_ctxp), ctypes.c_int, _ip, ctypes.c_int, ctypes.POINTER(_vp)]
@@ -219,6 +221,14 @@ class LayeredFMM:
                                             int(reps), _ptr(rows), 64, ctypes.byref(nrows)), "lfmm_autotune")
         self.n = xyz.shape[0]
         return [dict(zip(TUNE_COLS, r)) for r in rows[:nrows.value]]
+
+    def check_bounded_wait(self, limit_ms: float = 10.0) -> int:
+        """Run the device's bounded-wait self-check; returns its status code
+        (ETIMEOUT is the expected outcome)."""
+        st = self._lib.lfmm_check_bounded_wait(self._ctx, float(limit_ms))
+        if st not in (OK, ETIMEOUT):
+            self._check(st, "lfmm_check_bounded_wait")
+        return st
 
     def stats(self) -> dict:
         out = np.zeros(16, dtype=np.int64)

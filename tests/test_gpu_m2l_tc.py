@@ -73,3 +73,21 @@ def test_offset_groups_option():
     e = oracle.err2(ref, phi)
     print("groups 9 vs 27: Err2 %.2e" % e)
     assert e < 1e-5
+
+
+def test_bounded_wait_runs_out_and_is_reported():
+    # a device wait that can never complete: it must give up after its
+    # budget, count a timeout and leave the context usable
+    import time
+    from paper_1908_10863_gb300.lfmm import ETIMEOUT
+    w = workloads.config2(5000)
+    with LayeredFMM(w.d, w.eps, 8, precision=1) as f:
+        f.build(w.xyz, w.layer)
+        t0 = time.perf_counter()
+        assert f.check_bounded_wait(20.0) == ETIMEOUT
+        dt = time.perf_counter() - t0
+        assert dt < 5.0
+        with pytest.raises(LfmmError):
+            f.check_bounded_wait(0.0)
+        phi, _ = f.evaluate(w.q)
+        assert np.all(np.isfinite(phi)) and f.stats()["timeouts"] == 0
