@@ -477,12 +477,27 @@ __global__ void __launch_bounds__(G_T) k_m2l_gemm(GemmArgs g)
         // block-uniform: skip offsets where no target of the tile has a source
         if (!__syncthreads_or(sj >= 0)) continue;
         // gather the source multipoles: column j = source of target j (k fastest)
-        for (int idx = tid; idx < G_TB * KP; idx += G_T) {
-            int j = idx / KP, k = idx - j * KP;
-            int s = s_src[j];
-            R v = 0;
-            if (s >= 0 && k < nc) v = M[(size_t)s * nc + k];
-            sX[j * XS + k] = v;
+        // eight loads in flight per thread before their stores
+        for (int b0 = tid; b0 < G_TB * KP; b0 += 8 * G_T) {
+            R v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int idx = b0 + u * G_T;
+                v[u] = R(0);
+                if (idx < G_TB * KP) {
+                    const int j = idx / KP, k = idx - j * KP;
+                    const int s = s_src[j];
+                    if (s >= 0 && k < nc) v[u] = M[(size_t)s * nc + k];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int idx = b0 + u * G_T;
+                if (idx < G_TB * KP) {
+                    const int j = idx / KP, k = idx - j * KP;
+                    sX[j * XS + k] = v[u];
+                }
+            }
         }
         const R* Ao = A + (size_t)o * KP * RP;
         for (int kc = 0; kc < KP; kc += G_KC) {

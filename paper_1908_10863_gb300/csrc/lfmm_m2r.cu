@@ -450,10 +450,28 @@ __global__ void __launch_bounds__(R_T) k_m2r_gemm(RGemmArgs g)
     const int cgs = cnt > 32 ? 16 : (cnt > 16 ? 8 : 4);
     const int ncol = 4 * (cgs > CG_MIN ? cgs : CG_MIN);
     const R* M = reinterpret_cast<const R*>(g.M) + (size_t)blockIdx.y * g.stride;
-    for (int idx = tid; idx < ncol * KP; idx += R_T) {
-        const int j = idx / KP, k = idx - j * KP;
-        const int s = s_src[j];
-        sX[j * XS + k] = (s >= 0 && k < nc) ? M[(size_t)s * nc + k] : R(0);
+    // eight loads in flight per thread before their stores
+    const int tot = ncol * KP;
+    for (int b0 = tid; b0 < tot; b0 += 8 * R_T) {
+        R v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int idx = b0 + u * R_T;
+            v[u] = R(0);
+            if (idx < tot) {
+                const int j = idx / KP, k = idx - j * KP;
+                const int s = s_src[j];
+                if (s >= 0 && k < nc) v[u] = M[(size_t)s * nc + k];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int idx = b0 + u * R_T;
+            if (idx < tot) {
+                const int j = idx / KP, k = idx - j * KP;
+                sX[j * XS + k] = v[u];
+            }
+        }
     }
     __syncthreads();
     const R ih = (R)(1.0 / g.levelh[lev]);
