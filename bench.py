@@ -81,6 +81,8 @@ def parse():
     ap.add_argument("--no-near", action="store_true", help="skip the near-interface workload")
     ap.add_argument("--no-multi", action="store_true", help="skip the many-charge-vector workload")
     ap.add_argument("--no-batch", action="store_true", help="skip the many-problem workload")
+    ap.add_argument("--acc-targets", default="200,60",
+                    help="oracle targets of the two N = 1M cases of --accuracy-table")
     ap.add_argument("--accuracy-table", action="store_true",
                     help="instead of timing: Err2 against the oracle for each medium, N, p and precision")
     ap.add_argument("--forms", default="fp32_surrogate,fp32,fp64",
@@ -344,14 +346,14 @@ def many_problems_leg(torch, dev, p, flush, k=48):
     return out
 
 
-def accuracy_table(torch, dev):
+def accuracy_table(torch, dev, targets=(200, 60)):
     """Relative L2 errors (potential and field) of both forms against the CPU
     oracle (exact image series), one JSON line per case.  Small N: all
-    targets; N = 1M: a seeded target subsample."""
+    targets; N = 1M: a seeded target subsample of the given sizes."""
     import oracle
     from paper_1908_10863_gb300 import LayeredFMM, workloads
-    cases = [("config1", "(1,5,10)", 1000, 1000), ("config2", "(1,5,10)", 1 << 20, 200),
-             ("config2", "(1,80,2)", 1 << 20, 60)]
+    cases = [("config1", "(1,5,10)", 1000, 1000), ("config2", "(1,5,10)", 1 << 20, targets[0]),
+             ("config2", "(1,80,2)", 1 << 20, targets[1])]
     for name, med, n, ns in cases:
         eps = workloads.EPS_CONFIG if med == "(1,5,10)" else workloads.EPS_HIGH_CONTRAST
         w = workloads.config1(n, eps=eps) if name == "config1" else workloads.config2(n, eps=eps)
@@ -411,7 +413,7 @@ def main():
 
     if args.accuracy_table:
         if rank == 0:
-            accuracy_table(torch, torch.device("cuda", local))
+            accuracy_table(torch, torch.device("cuda", local), tuple(int(v) for v in args.acc_targets.split(",")))
         return 0
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
