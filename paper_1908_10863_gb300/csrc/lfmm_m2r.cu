@@ -363,7 +363,8 @@ struct RGemmArgs {
     const double* levelh;
     const void* M;
     void* L;
-    size_t stride;          // expansions per right-hand side (blockIdx.y), in elements
+    size_t stride;          // expansions per right-hand side, in elements
+    int nr;                 // right-hand sides, applied in turn with the operator staged once
 };
 
 // Y = A X over the first 4 * CG columns (CG column groups of 4; the rest of
@@ -449,39 +450,42 @@ __global__ void __launch_bounds__(R_T) k_m2r_gemm(RGemmArgs g)
     // columns the tile shape below reads (block-uniform)
     const int cgs = cnt > 32 ? 16 : (cnt > 16 ? 8 : 4);
     const int ncol = 4 * (cgs > CG_MIN ? cgs : CG_MIN);
-    const R* M = reinterpret_cast<const R*>(g.M) + (size_t)blockIdx.y * g.stride;
-    // eight loads in flight per thread before their stores
-    const int tot = ncol * KP;
-    for (int b0 = tid; b0 < tot; b0 += 8 * R_T) {
-        R v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int idx = b0 + u * R_T;
-            v[u] = R(0);
-            if (idx < tot) {
-                const int j = idx / KP, k = idx - j * KP;
-                const int s = s_src[j];
-                if (s >= 0 && k < nc) v[u] = M[(size_t)s * nc + k];
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int idx = b0 + u * R_T;
-            if (idx < tot) {
-                const int j = idx / KP, k = idx - j * KP;
-                sX[j * XS + k] = v[u];
-            }
-        }
-    }
-    __syncthreads();
     const R ih = (R)(1.0 / g.levelh[lev]);
-    R* L = reinterpret_cast<R*>(g.L) + (size_t)blockIdx.y * g.stride;
-    if (cgs == 16 || CG_MIN >= 16)
-        m2r_tile<R, RP, 16>(sA, sX, cnt, s_tgt, ih, L, nc);
-    else if (cgs == 8 || CG_MIN >= 8)
-        m2r_tile<R, RP, (CG_MIN > 8 ? CG_MIN : 8)>(sA, sX, cnt, s_tgt, ih, L, nc);
-    else
-        m2r_tile<R, RP, CG_MIN>(sA, sX, cnt, s_tgt, ih, L, nc);
+    const int tot = ncol * KP;
+    for (int r = 0; r < g.nr; ++r) {
+        if (r > 0) __syncthreads();  // the previous vector's products are read out of sX
+        const R* M = reinterpret_cast<const R*>(g.M) + (size_t)r * g.stride;
+        // eight loads in flight per thread before their stores
+        for (int b0 = tid; b0 < tot; b0 += 8 * R_T) {
+            R v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int idx = b0 + u * R_T;
+                v[u] = R(0);
+                if (idx < tot) {
+                    const int j = idx / KP, k = idx - j * KP;
+                    const int s = s_src[j];
+                    if (s >= 0 && k < nc) v[u] = M[(size_t)s * nc + k];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int idx = b0 + u * R_T;
+                if (idx < tot) {
+                    const int j = idx / KP, k = idx - j * KP;
+                    sX[j * XS + k] = v[u];
+                }
+            }
+        }
+        __syncthreads();
+        R* L = reinterpret_cast<R*>(g.L) + (size_t)r * g.stride;
+        if (cgs == 16 || CG_MIN >= 16)
+            m2r_tile<R, RP, 16>(sA, sX, cnt, s_tgt, ih, L, nc);
+        else if (cgs == 8 || CG_MIN >= 8)
+            m2r_tile<R, RP, (CG_MIN > 8 ? CG_MIN : 8)>(sA, sX, cnt, s_tgt, ih, L, nc);
+        else
+            m2r_tile<R, RP, CG_MIN>(sA, sX, cnt, s_tgt, ih, L, nc);
+    }
 }
 
 template <typename R, int RP>
@@ -523,9 +527,10 @@ static LfErr m2r_apply_rp(lfmm_ctx* ctx, cudaStream_t st)
     g.M = ctx->Mexp.ptr;
     g.L = ctx->Lexp.ptr;
     g.stride = (size_t)ctx->nbox_total * g.nc;
+    g.nr = ctx->nrhs_b;
     const size_t sm = sizeof(R) * ((size_t)RP * RP + (size_t)R_TB * (RP + 1)) + 16;
     LF_CHECK(cudaFuncSetAttribute(k_m2r_gemm<R, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    ++ctx->launches, k_m2r_gemm<R, RP><<<dim3(ctx->m2r_nbatch, ctx->nrhs_b), R_T, sm, st>>>(g);
+    ++ctx->launches, k_m2r_gemm<R, RP><<<ctx->m2r_nbatch, R_T, sm, st>>>(g);
     return lf_cuda(cudaGetLastError(), "m2r gemm");
 }
 

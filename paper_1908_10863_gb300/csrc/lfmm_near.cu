@@ -591,7 +591,9 @@ LfErr lf_near_field(lfmm_ctx* ctx, cudaStream_t st)
     const int ph = lf_prof_start(ctx, LFMM_TIME_P2P, st);
     // the network variant only where the near field holds reaction pairs (it
     // needs far more registers, which slows the free-space part); one launch
-    // per right-hand side.  The quadrature kernels take batches of up to 8.
+    // per right-hand side.  The quadrature kernels take batches of up to 4
+    // (float32: more registers per thread cost more than the shared pair
+    // geometry saves) or 8 (FP64).
     const bool net = a.sv.ready != 0 && ctx->stats[LFMM_STAT_P2P_REACTION] > 0;
     // Few leaves (small problems) leave most SMs idle with one warp or block
     // per leaf: share each near list between `split` of them.  A set value
@@ -611,7 +613,7 @@ LfErr lf_near_field(lfmm_ctx* ctx, cudaStream_t st)
     const double* phi0 = a.phi;
     double* fld0 = a.fld;
     const char* q0 = reinterpret_cast<const char*>(a.q);
-    const int step = net ? 1 : 8;
+    const int step = net ? 1 : (ctx->precision ? 4 : 8);
     for (int r0 = 0; r0 < nr; r0 += step) {
         a.nr = nr - r0 < step ? nr - r0 : step;
         a.q = q0 + (size_t)r0 * qs;
