@@ -254,3 +254,29 @@ def test_device_inputs_checked_on_the_device():
         f.build_device(torch.from_numpy(w.xyz).to(dev), torch.from_numpy(w.layer).to(dev))
         phi, _ = f.evaluate(w.q)
         assert np.all(np.isfinite(phi))
+
+
+@pytest.mark.parametrize("precision,tol", [(1, 1e-5), (0, 1e-5)])
+def test_full_size_sampled_against_oracle(precision, tol):
+    # the benchmark's own workload and call path (device buffers, N = 1M,
+    # p = 10), checked on a seeded sample of targets the oracle computes one by one
+    torch = pytest.importorskip("torch")
+    w = workloads.config2(1 << 20)
+    t = workloads.subsample(w.n, 48, seed=11)
+    ref, refE = oracle.direct(w.d, w.eps, w.xyz, w.layer, w.q, targets=t, mode=oracle.MODE_IMAGES)
+    dev = torch.device("cuda")
+    s = torch.cuda.current_stream()
+    with LayeredFMM(w.d, w.eps, 10, precision=precision) as f:
+        f.build_device(torch.from_numpy(w.xyz).to(dev), torch.from_numpy(w.layer).to(dev), s)
+        q = torch.from_numpy(w.q).to(dev)
+        phi = torch.empty_like(q)
+        fld = torch.empty((w.n, 3), dtype=torch.float64, device=dev)
+        f.evaluate_device(q, phi, fld, s)
+        torch.cuda.synchronize()
+        st = f.stats()
+    e_phi = oracle.err2(ref, phi.cpu().numpy()[t])
+    e_fld = oracle.err2(refE, fld.cpu().numpy()[t])
+    print("N=1M precision %d: Err2 phi %.2e field %.2e (48 targets), %d free M2L pairs" % (precision, e_phi, e_fld,
+                                                                                        st["m2l_free"]))
+    assert st["timeouts"] == 0
+    assert e_phi < tol and e_fld < 5 * tol
