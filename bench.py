@@ -243,17 +243,23 @@ def near_interface_leg(torch, dev, p, flush):
     for prec, pname in ((0, "fp64"), (1, "fp32")):
         f = LayeredFMM(w.d, w.eps, p, precision=prec)
         f.surrogate_train(SURR_SAMPLES, SURR_EPOCHS, SURR_SEED)
+        table_err = f.near_tables()
         phis = {}
-        for use in (0, 1):
-            f.set_option(5, use)
+        # near-field reaction kernels by quadrature, by the network, by the pre-computed tables
+        for kind, surr, tab in (("quadrature", 0, 0), ("network", 1, 0), ("tables", 0, 1)):
+            f.set_option(5, surr)
+            f.set_option(10, tab)
             times, launches, stages = run_form(f, xyz_d, lay_d, q_d, phi_d, fld_d, torch, 2, 1, flush)
             st = f.stats()
-            key = pname + ("_network" if use else "_quadrature")
-            out[key] = {"ms_per_step": sum(times) / len(times), "p2p_ms": stages["p2p"],
-                        "pairs_network": st["surr_net_pairs"], "pairs_quadrature": st["surr_quad_pairs"]}
-            phis[use] = phi_d.cpu().numpy().copy()
-        out[pname + "_network"]["err2_phi_vs_quadrature"] = oracle.err2(phis[0], phis[1])
-        out[pname + "_p2p_speedup"] = out[pname + "_quadrature"]["p2p_ms"] / out[pname + "_network"]["p2p_ms"]
+            out[pname + "_" + kind] = {"ms_per_step": sum(times) / len(times), "p2p_ms": stages["p2p"],
+                                       "pairs_network": st["surr_net_pairs"], "pairs_quadrature": st["surr_quad_pairs"]}
+            phis[kind] = phi_d.cpu().numpy().copy()
+        f.set_option(10, 0)
+        for kind in ("network", "tables"):
+            out[pname + "_" + kind]["err2_phi_vs_quadrature"] = oracle.err2(phis["quadrature"], phis[kind])
+            out[pname + "_" + kind + "_p2p_speedup"] = (out[pname + "_quadrature"]["p2p_ms"] /
+                                                        out[pname + "_" + kind]["p2p_ms"])
+        out[pname + "_tables"]["table_max_rel_err"] = table_err
         f.close()
     return out
 

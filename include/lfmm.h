@@ -61,9 +61,11 @@ enum {
                                    (default); 0 = on the CUDA cores */
     LFMM_OPT_P2P_SPLIT = 8,     /* near list of a leaf shared by this many warps/blocks of the P2P kernels:
                                    0 = chosen from the leaf count (default), else 1, 2, 4, 8 or 16 */
-    LFMM_OPT_TC_GROUPS = 9      /* tensor-core free M2L: CTAs per 256-target tile, each summing 189/groups
+    LFMM_OPT_TC_GROUPS = 9,     /* tensor-core free M2L: CTAs per 256-target tile, each summing 189/groups
                                    offsets in its tensor-memory accumulator before a float atomic add;
                                    a divisor of 189 (default 27: 7 offsets per accumulation) */
+    LFMM_OPT_NEAR_TABLES = 10   /* 1 = near-field reaction kernels with their remainder from pre-computed
+                                   tables (built on first use, see lfmm_near_tables); 0 = quadrature (default) */
 };
 
 /* Create a context for the medium.
@@ -105,6 +107,19 @@ lfmm_status lfmm_evaluate(lfmm_ctx* ctx, int nrhs, const double* q, double* phi,
  * work is enqueued on that stream (no host synchronisation). */
 lfmm_status lfmm_evaluate_device(lfmm_ctx* ctx, int nrhs, const double* q_dev, double* phi_dev, double* field_dev,
                                  void* cuda_stream);
+
+/* Pre-computed tables for the near-field reaction kernels (Section 4's
+ * "pre-computed tables" variant, here for I_00, I_10, I_11 of each reaction
+ * component): the closed-form leading image stays exact; the remainder,
+ * scaled as T_N = Z^{N+1} r_N with Z = h + zeta_r, is tabulated over
+ * s = rho / Z in [0, 4] and w = zeta_r / Z in [0, 1] (257 x 129 points,
+ * FP64, the M2L quadrature rule) and read by fourth-order Lagrange
+ * interpolation; pairs beyond the table keep the quadrature.  Builds the
+ * tables if needed (once per context) and writes the largest deviation of the
+ * interpolated kernels from the quadrature at 2048 seeded points per
+ * component, relative to |I_00| (field kernels times the distance), to
+ * *max_rel_err (may be NULL).  Does not switch them on (LFMM_OPT_NEAR_TABLES). */
+lfmm_status lfmm_near_tables(lfmm_ctx* ctx, double* max_rel_err);
 
 /* Self-check of failure detection (the paper has no counterpart).  Every
  * wait of the device pipelines is bounded: when one runs out, the kernel

@@ -631,6 +631,14 @@ static lfmm_status set_option(lfmm_ctx* ctx, int opt, double v)
     case LFMM_OPT_TENSOR_CORES:
         ctx->use_tc = (v != 0.0);
         return LFMM_OK;
+    case LFMM_OPT_NEAR_TABLES:
+        if (v != 0.0 && v != 1.0) return fail(ctx, "EINVAL: near tables option must be 0 or 1");
+        if (v == 1.0 && !ctx->near_tab_ready) {
+            const LfErr e = lf_near_tables(ctx, nullptr);
+            if (!e.empty()) return fail(ctx, e);
+        }
+        ctx->use_near_tab = (v != 0.0);
+        return LFMM_OK;
     case LFMM_OPT_TC_GROUPS: {
         const int k = (int)v;
         if ((double)k != v || k < 1 || 189 % k != 0)
@@ -798,6 +806,14 @@ lfmm_status lfmm_evaluate_device(lfmm_ctx* ctx, int nrhs, const double* q_dev, d
     return LFMM_OK;
 }
 
+lfmm_status lfmm_near_tables(lfmm_ctx* ctx, double* max_rel_err)
+{
+    if (!ctx) return LFMM_EINVAL;
+    ctx->err.clear();
+    const LfErr e = lf_near_tables(ctx, max_rel_err);
+    return e.empty() ? LFMM_OK : fail(ctx, e);
+}
+
 lfmm_status lfmm_check_bounded_wait(lfmm_ctx* ctx, double limit_ms)
 {
     if (!ctx) return LFMM_EINVAL;
@@ -822,7 +838,7 @@ void lfmm_destroy(lfmm_ctx* ctx)
                       &ctx->oct_U64, &ctx->oct_U32, &ctx->comp_dev, &ctx->perm, &ctx->xs, &ctx->ys, &ctx->zs,
                       &ctx->keys, &ctx->keys_tmp, &ctx->vals_tmp, &ctx->scan_tmp, &ctx->hist, &ctx->xyz_in,
                       &ctx->layer_in, &ctx->err_flag, &ctx->counts, &ctx->box_key, &ctx->box_pbeg, &ctx->box_pend,
-                      &ctx->box_parent, &ctx->box_cbeg, &ctx->box_cend, &ctx->box_center, &ctx->box_grid, &ctx->pos_rel, &ctx->leaf_of, &ctx->level_consts, &ctx->flags, &ctx->idx,
+                      &ctx->box_parent, &ctx->box_cbeg, &ctx->box_cend, &ctx->box_center, &ctx->box_grid, &ctx->pos_rel, &ctx->leaf_of, &ctx->near_tab, &ctx->level_consts, &ctx->flags, &ctx->idx,
                       &ctx->near_off, &ctx->near_ent, &ctx->m2l_off, &ctx->m2l_ent, &ctx->m2r_off, &ctx->m2r_ent,
                       &ctx->q_sorted, &ctx->Mexp, &ctx->Lexp, &ctx->phi_far, &ctx->phi_near, &ctx->fld_far,
                       &ctx->fld_near, &ctx->q_stage, &ctx->phi_stage, &ctx->fld_stage, &ctx->m2l_A64, &ctx->m2l_A32,

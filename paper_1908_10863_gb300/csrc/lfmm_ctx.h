@@ -126,6 +126,9 @@ struct lfmm_ctx {
     std::vector<int4> m2l_tiles_h, l2l_tiles_h, m2m_tiles_h, tc_tiles_h;  // host staging of asynchronous uploads
     std::vector<float4> level_consts_h;
     void* host_pin = nullptr;  // small pinned host buffer for readbacks that must not wait
+    DevBuf near_tab;            // remainder tables of the near-field reaction kernels
+    int near_tab_ready = 0, use_near_tab = 0;
+    double near_tab_err = -1.0;  // largest relative deviation from the quadrature at the check points
     std::vector<uint32_t> root_ent_h;
     std::vector<int> root_beg_h, root_end_h, root_zero_h;
     double m2l_levelh_h[16] = {0};
@@ -205,6 +208,7 @@ lfmm_status lf_build_dev(lfmm_ctx* ctx, int64_t n, const double* xyz_dev, const 
 #define LFMM_SEP_EXT_P 18
 LfErr lf_near_field(lfmm_ctx* ctx, cudaStream_t st);
 LfErr lf_near_prepare(lfmm_ctx* ctx, cudaStream_t st);
+LfErr lf_near_tables(lfmm_ctx* ctx, double* max_err);
 
 // ---- surrogate (lfmm_surrogate.cu) ----
 LfErr lf_surrogate_train(lfmm_ctx* ctx, int64_t nsamples, int epochs, uint64_t seed);

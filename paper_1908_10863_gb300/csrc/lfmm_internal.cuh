@@ -329,9 +329,94 @@ struct LfSum<double> {
 };
 
 // Reaction pair kernel: (I_00, I_10, I_11') of one component at (rho, h).
+// ---------------------------------------------------------------------------
+// Pre-computed remainder tables of the near-field reaction kernels (the
+// paper's "pre-computed tables" variant of Section 4, here for the three
+// near-field kernels of each reaction component).  With Z = h + zeta_r,
+// s = rho / Z and w = zeta_r / Z (in (0, 1]), the scaled remainders
+// T00 = Z r00, T10 = Z^2 r10, T11 = Z^2 r11 are smooth functions of (s, w):
+// in t = k Z they are integrals of e^{-t} f(x) t^N J_mu(t s) with
+// x = exp(-D t w / zeta_r).  They are tabulated on a uniform grid of
+// LF_NT_NS x LF_NT_NW points over [0, LF_NT_SMAX] x [0, 1] and read back by
+// 4 x 4-point Lagrange interpolation (fourth order); pairs with s beyond the
+// table keep the quadrature.
+#define LF_NT_NS 257
+#define LF_NT_NW 129
+#define LF_NT_SMAX 4.0
+#define LF_NT_PER (3 * LF_NT_NS * LF_NT_NW)  // doubles per component: [kernel][w][s]
+
+// the three scaled remainders at (s, w) by the quadrature rule in t
+__device__ __forceinline__ void lf_nt_point(const LfmmComp& c, double s, double w, int Q, const double* gl_t,
+                                            const double* gl_w, double out[3])
+{
+    double a00 = 0.0, a10 = 0.0, a11 = 0.0;
+    const double dw = c.D * w / c.zeta_r;
+    for (int q = 0; q < Q; ++q) {
+        const double t = gl_t[q];
+        const double x = exp(-dw * t);
+        double num = c.rem[4];
+        for (int i = 3; i >= 0; --i) num = num * x + c.rem[i];
+        const double den = (c.den[2] * x + c.den[1]) * x + c.den[0];
+        const double f = gl_w[q] * num / den;
+        const double j0v = j0(t * s), j1v = j1(t * s);
+        a00 += f * j0v;
+        a10 += f * t * j0v;
+        a11 += f * t * j1v;
+    }
+    out[0] = a00;
+    out[1] = a10;
+    out[2] = a11;
+}
+
+// weights of the 4-point Lagrange stencil at position x in [0, 3]
+template <typename R>
+__device__ __forceinline__ void lf_lagrange4(R x, R wgt[4])
+{
+    const R x1 = x - R(1), x2 = x - R(2), x3 = x - R(3);
+    wgt[0] = -x1 * x2 * x3 * R(1.0 / 6.0);
+    wgt[1] = x * x2 * x3 * R(0.5);
+    wgt[2] = -x * x1 * x3 * R(0.5);
+    wgt[3] = x * x1 * x2 * R(1.0 / 6.0);
+}
+
+// remainders from the component's table ctab; false where the table does not reach
+template <typename R>
+__device__ __forceinline__ bool lf_nt_remainder(const double* __restrict__ ctab, const LfmmComp& c, R rho, R h,
+                                                R& r00, R& r10, R& r11)
+{
+    const R Z = h + (R)c.zeta_r;
+    const R iZ = R(1) / Z;
+    const R fs = rho * iZ * R((LF_NT_NS - 1) / LF_NT_SMAX);
+    if (!(fs <= R(LF_NT_NS - 1))) return false;
+    const R fw = (R)c.zeta_r * iZ * R(LF_NT_NW - 1);
+    int is = (int)fs - 1, iw = (int)fw - 1;
+    is = is < 0 ? 0 : (is > LF_NT_NS - 4 ? LF_NT_NS - 4 : is);
+    iw = iw < 0 ? 0 : (iw > LF_NT_NW - 4 ? LF_NT_NW - 4 : iw);
+    R ws[4], ww[4];
+    lf_lagrange4<R>(fs - (R)is, ws);
+    lf_lagrange4<R>(fw - (R)iw, ww);
+    R acc[3] = {R(0), R(0), R(0)};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const double* tk = ctab + (size_t)k * LF_NT_NS * LF_NT_NW + (size_t)iw * LF_NT_NS + is;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            R row = R(0);
+#pragma unroll
+            for (int a = 0; a < 4; ++a) row += ws[a] * (R)__ldg(tk + (size_t)b * LF_NT_NS + a);
+            acc[k] += ww[b] * row;
+        }
+    }
+    r00 = acc[0] * iZ;
+    r10 = acc[1] * iZ * iZ;
+    r11 = acc[2] * iZ * iZ;
+    return true;
+}
+
 template <typename R>
 __device__ __forceinline__ void lf_reaction_pair(const LfmmComp& c, R rho, R h, int Q, const double* gl_t,
-                                                 const double* gl_w, R& k00, R& k10, R& k11)
+                                                 const double* gl_w, R& k00, R& k10, R& k11,
+                                                 const double* ctab = nullptr)
 {
     typedef LfMath<R> F;
     R H = h + (R)c.zeta;
@@ -343,6 +428,15 @@ __device__ __forceinline__ void lf_reaction_pair(const LfmmComp& c, R rho, R h, 
     k10 = C * H * ir3;
     k11 = C * rho * ir3;
     if (!c.has_rem) return;
+    if (ctab) {
+        R r00, r10, r11;
+        if (lf_nt_remainder<R>(ctab, c, rho, h, r00, r10, r11)) {
+            k00 += r00;
+            k10 += r10;
+            k11 += r11;
+            return;
+        }
+    }
     R Z = h + (R)c.zeta_r;
     R iZ = R(1) / Z;
     R D = (R)c.D;

@@ -15,6 +15,9 @@
 
 #include <mutex>
 
+#include <algorithm>
+#include <cmath>
+
 #include "lfmm_ctx.h"
 #include "lfmm_surrogate.cuh"
 
@@ -54,8 +57,10 @@ struct P2PArgs {
     const LfmmComp* comps;  // the context's components
     const double* gl_t;     // near-field quadrature rule (Qn nodes and weights)
     const double* gl_w;
+    const double* ntab;  // remainder tables [component][LF_NT_PER], or null: the quadrature
     LfmmSurrView sv;  // learned near-field kernels (sv.ready = 0: quadrature only)
 };
+#define LF_CTAB(a, c) ((a).ntab ? (a).ntab + (size_t)(c) * LF_NT_PER : nullptr)
 
 #define P2P_T 128
 
@@ -111,16 +116,18 @@ __device__ __forceinline__ void p2p_free_add(R dx, R dy, R dz, const R* qs, int 
     }
 }
 
-// Reaction kernels of one pair by the quadrature (once), applied to the batch.
+// Reaction kernels of one pair by the quadrature, or by the component's
+// remainder table ctab where given (once), applied to the batch.
 template <typename R, int RB, typename S>
 __device__ __forceinline__ void p2p_reaction_add(const LfmmComp& cp, R dx, R dy, R dz, const R* qs, int qsk, int nr,
-                                                 int Qn, const double* gl_t, const double* gl_w, P2PAccT<S, RB>& A)
+                                                 int Qn, const double* gl_t, const double* gl_w, P2PAccT<S, RB>& A,
+                                                 const double* ctab)
 {
     typedef LfMath<R> F;
     R h = (cp.a == 1) ? dz : -dz;
     R rho = F::Sqrt(dx * dx + dy * dy);
     R k00, k10, k11;
-    lf_reaction_pair<R>(cp, rho, h, Qn, gl_t, gl_w, k00, k10, k11);
+    lf_reaction_pair<R>(cp, rho, h, Qn, gl_t, gl_w, k00, k10, k11, ctab);
     const R k10s = (cp.a == 1) ? k10 : -k10;
     const R g = rho > R(0) ? k11 / rho : R(0);
 #pragma unroll
@@ -205,7 +212,7 @@ __global__ void __launch_bounds__(P2P_T) k_p2p(P2PArgs a)
                 } else {
                     for (int u = 0; u < cnt; ++u)
                         p2p_reaction_add<R, RB>(cp, xi - sx[u], yi - sy[u], zi - sz[u], &sq[0][u], P2P_T, a.nr,
-                                                a.Qn, a.gl_t, a.gl_w, A);
+                                                a.Qn, a.gl_t, a.gl_w, A, LF_CTAB(a, c));
                 }
             }
         }
@@ -325,7 +332,7 @@ __global__ void __launch_bounds__(32 * PW_WARPS) k_p2p_warp(P2PArgs a, const flo
                         for (int u = u0; u < u1; ++u) {
                             const float4 v = sp[w][u];
                             p2p_reaction_add<float, 1>(cp, xi - v.x, yi - v.y, zi - v.z, &sp[w][u].w, 0, 1, a.Qn,
-                                                       a.gl_t, a.gl_w, part);
+                                                       a.gl_t, a.gl_w, part, LF_CTAB(a, c));
                         }
                     }
                     continue;
@@ -337,7 +344,7 @@ __global__ void __launch_bounds__(32 * PW_WARPS) k_p2p_warp(P2PArgs a, const flo
                 } else {
                     for (int u = u0; u < u1; ++u)
                         p2p_reaction_add<float, RB>(cp, xi - sx[w][u], yi - sy[w][u], zi - sz[w][u], &sq[w][0][u],
-                                                    32, a.nr, a.Qn, a.gl_t, a.gl_w, part);
+                                                    32, a.nr, a.Qn, a.gl_t, a.gl_w, part, LF_CTAB(a, c));
                 }
             }
             p2p_flush<float, RB>(part, A);
@@ -392,7 +399,7 @@ template <typename R>
 __device__ __forceinline__ void p2p_drain(const LfmmComp& cp, const uint16_t* qe, int count, int lane, int wbase,
                                           const R* tx, const R* ty, const R* tz, const R* sx, const R* sy,
                                           const R* sz, const R* sq, R (*acc)[4], int Qn, const double* gl_t,
-                                          const double* gl_w)
+                                          const double* gl_w, const double* ctab)
 {
     typedef LfMath<R> F;
     if (lane >= count) return;
@@ -402,7 +409,7 @@ __device__ __forceinline__ void p2p_drain(const LfmmComp& cp, const uint16_t* qe
     R h = (cp.a == 1) ? dz : -dz;
     R rho = F::Sqrt(dx * dx + dy * dy);
     R k00, k10, k11;
-    lf_reaction_pair<R>(cp, rho, h, Qn, gl_t, gl_w, k00, k10, k11);
+    lf_reaction_pair<R>(cp, rho, h, Qn, gl_t, gl_w, k00, k10, k11, ctab);
     R qs = sq[u];
     atomicAdd(&acc[o][0], qs * k00);
     atomicAdd(&acc[o][3], (cp.a == 1) ? qs * k10 : -qs * k10);
@@ -483,7 +490,7 @@ __global__ void __launch_bounds__(P2P_T) k_p2p_net(P2PArgs a)
                             p2p_free_add<R, 1>(xi - sx[u], yi - sy[u], zi - sz[u], &sq[u], 0, 1, A);
                     } else {
                         for (int u = 0; u < cnt; ++u)
-                            p2p_reaction_add<R, 1>(cp, xi - sx[u], yi - sy[u], zi - sz[u], &sq[u], 0, 1, a.Qn, a.gl_t, a.gl_w, A);
+                            p2p_reaction_add<R, 1>(cp, xi - sx[u], yi - sy[u], zi - sz[u], &sq[u], 0, 1, a.Qn, a.gl_t, a.gl_w, A, LF_CTAB(a, c));
                         n_quad += cnt;
                     }
                     continue;
@@ -524,14 +531,14 @@ __global__ void __launch_bounds__(P2P_T) k_p2p_net(P2PArgs a)
                         if (qn >= 32) {
                             __syncwarp();
                             qn -= 32;
-                            p2p_drain<R>(cp, &qbuf[wid][qn], 32, lane, wbase, tx, ty, tz, sx, sy, sz, sq, acc, a.Qn, a.gl_t, a.gl_w);
+                            p2p_drain<R>(cp, &qbuf[wid][qn], 32, lane, wbase, tx, ty, tz, sx, sy, sz, sq, acc, a.Qn, a.gl_t, a.gl_w, LF_CTAB(a, c));
                             __syncwarp();
                         }
                     }
                 }
                 if (qn > 0) {
                     __syncwarp();
-                    p2p_drain<R>(cp, &qbuf[wid][0], qn, lane, wbase, tx, ty, tz, sx, sy, sz, sq, acc, a.Qn, a.gl_t, a.gl_w);
+                    p2p_drain<R>(cp, &qbuf[wid][0], qn, lane, wbase, tx, ty, tz, sx, sy, sz, sq, acc, a.Qn, a.gl_t, a.gl_w, LF_CTAB(a, c));
                     __syncwarp();
                 }
             }
@@ -582,6 +589,7 @@ LfErr lf_near_field(lfmm_ctx* ctx, cudaStream_t st)
     a.comps = ctx->comp_dev.as<LfmmComp>();
     a.gl_t = ctx->gl_t_near.as<double>();
     a.gl_w = ctx->gl_w_near.as<double>();
+    a.ntab = (ctx->use_near_tab && ctx->near_tab_ready) ? ctx->near_tab.as<double>() : nullptr;
     LF_TRY(lf_reserve(ctx->surr_counters, 64));
     LF_CHECK(cudaMemsetAsync(ctx->surr_counters.ptr, 0, 16, st));
     LF_TRY(lf_surrogate_device_view(ctx, &a.sv));
@@ -648,6 +656,115 @@ LfErr lf_near_field(lfmm_ctx* ctx, cudaStream_t st)
         LF_TRY(lf_cuda(cudaGetLastError(), "p2p"));
     }
     lf_prof_stop(ctx, ph, st);
+    return LfErr();
+}
+
+// ---------------------------------------------------------------------------
+// Remainder tables of the near-field reaction kernels (built once per
+// medium): one thread per (component, w, s) grid point, FP64 quadrature with
+// the M2L rule; then a check of the interpolated kernels against the
+// quadrature at seeded points.
+// ---------------------------------------------------------------------------
+__global__ void k_near_tables(const LfmmComp* __restrict__ comps, int ncomp, int Q, const double* __restrict__ gt,
+                              const double* __restrict__ gw, double* __restrict__ tab)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t per = (int64_t)LF_NT_NS * LF_NT_NW;
+    if (i >= per * ncomp) return;
+    const int c = (int)(i / per);
+    const int r = (int)(i - (int64_t)c * per);
+    const int iw = r / LF_NT_NS, is = r - iw * LF_NT_NS;
+    const LfmmComp cp = comps[c];
+    double out[3] = {0.0, 0.0, 0.0};
+    if (!cp.is_free && cp.has_rem)
+        lf_nt_point(cp, is * (LF_NT_SMAX / (LF_NT_NS - 1)), iw * (1.0 / (LF_NT_NW - 1)), Q, gt, gw, out);
+    double* t = tab + (size_t)c * LF_NT_PER + r;
+    t[0] = out[0];
+    t[per] = out[1];
+    t[2 * per] = out[2];
+}
+
+// err[i]: largest deviation of the three interpolated kernels from the
+// quadrature, relative to |I_00| (field kernels times the distance R)
+__global__ void k_near_tables_check(const LfmmComp* __restrict__ comps, const int* __restrict__ pc,
+                                    const double* __restrict__ prho, const double* __restrict__ ph, int n, int Q,
+                                    const double* __restrict__ gt, const double* __restrict__ gw,
+                                    const double* __restrict__ tab, double* __restrict__ err)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const LfmmComp& cp = comps[pc[i]];
+    double a00, a10, a11, b00, b10, b11;
+    lf_reaction_pair<double>(cp, prho[i], ph[i], Q, gt, gw, a00, a10, a11);
+    lf_reaction_pair<double>(cp, prho[i], ph[i], Q, gt, gw, b00, b10, b11, tab + (size_t)pc[i] * LF_NT_PER);
+    const double H = ph[i] + cp.zeta;
+    const double R = sqrt(prho[i] * prho[i] + H * H);
+    const double sc = fabs(a00) > 1e-300 ? 1.0 / fabs(a00) : 0.0;
+    err[i] = fmax(fabs(b00 - a00), fmax(fabs(b10 - a10), fabs(b11 - a11)) * R) * sc;
+}
+
+LfErr lf_near_tables(lfmm_ctx* ctx, double* max_err)
+{
+    cudaStream_t st = ctx->s_main;
+    const int nc = ctx->ncomp, Q = ctx->gl_q_m2l;
+    if (!ctx->near_tab_ready) {
+        LF_TRY(lf_reserve(ctx->near_tab, sizeof(double) * (size_t)LF_NT_PER * nc));
+        const int64_t tot = (int64_t)LF_NT_NS * LF_NT_NW * nc;
+        ++ctx->launches, k_near_tables<<<lf_blocks(tot, 128), 128, 0, st>>>(
+            ctx->comp_dev.as<LfmmComp>(), nc, Q, ctx->gl_t_m2l.as<double>(), ctx->gl_w_m2l.as<double>(),
+            ctx->near_tab.as<double>());
+        LF_TRY(lf_cuda(cudaGetLastError(), "near tables"));
+    }
+    // seeded check points: per reaction component, s uniform over the table,
+    // depth sum h log-uniform in [1e-4, 3]
+    std::vector<int> pc;
+    std::vector<double> prho, ph;
+    uint64_t x = 0x9e3779b97f4a7c15ull;
+    auto uni = [&x]() {
+        x = x * 6364136223846793005ull + 1442695040888963407ull;
+        return (double)(x >> 11) * (1.0 / 9007199254740992.0);
+    };
+    for (int c = 0; c < nc; ++c) {
+        const LfmmComp& cp = ctx->comp[c];
+        if (cp.is_free || !cp.has_rem) continue;
+        for (int k = 0; k < 2048; ++k) {
+            const double h = pow(10.0, -4.0 + uni() * (4.0 + log10(3.0)));
+            const double sv = uni() * LF_NT_SMAX * 0.999;
+            pc.push_back(c);
+            ph.push_back(h);
+            prho.push_back(sv * (h + cp.zeta_r));
+        }
+    }
+    double worst = 0.0;
+    const int n = (int)pc.size();
+    if (n > 0) {
+        DevBuf dpc, drho, dh, derr;
+        LfErr e = lf_reserve(dpc, sizeof(int) * n);
+        if (e.empty()) e = lf_reserve(drho, sizeof(double) * n);
+        if (e.empty()) e = lf_reserve(dh, sizeof(double) * n);
+        if (e.empty()) e = lf_reserve(derr, sizeof(double) * n);
+        std::vector<double> herr(n, 0.0);
+        if (e.empty()) e = lf_cuda(cudaMemcpyAsync(dpc.ptr, pc.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st), "copy");
+        if (e.empty()) e = lf_cuda(cudaMemcpyAsync(drho.ptr, prho.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st), "copy");
+        if (e.empty()) e = lf_cuda(cudaMemcpyAsync(dh.ptr, ph.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st), "copy");
+        if (e.empty()) {
+            ++ctx->launches, k_near_tables_check<<<lf_blocks(n, 128), 128, 0, st>>>(
+                ctx->comp_dev.as<LfmmComp>(), dpc.as<int>(), drho.as<double>(), dh.as<double>(), n, Q,
+                ctx->gl_t_m2l.as<double>(), ctx->gl_w_m2l.as<double>(), ctx->near_tab.as<double>(),
+                derr.as<double>());
+            e = lf_cuda(cudaGetLastError(), "near tables check");
+        }
+        if (e.empty()) e = lf_cuda(lf_d2h(herr.data(), derr.ptr, sizeof(double) * n, st), "check");
+        for (DevBuf* b : {&dpc, &drho, &dh, &derr})
+            if (b->ptr) cudaFree(b->ptr);
+        if (!e.empty()) return e;
+        for (double v : herr) worst = std::max(worst, v);
+    } else {
+        LF_TRY(lf_cuda(cudaStreamSynchronize(st), "near tables"));
+    }
+    ctx->near_tab_ready = 1;
+    ctx->near_tab_err = worst;
+    if (max_err) *max_err = worst;
     return LfErr();
 }
 

@@ -16,7 +16,7 @@ from . import build as _build
 
 OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETIMEOUT, ENUMERIC = range(7)
 OPT_PRECISION, OPT_LEAF_CAP, OPT_PROFILE, OPT_QUAD_NODES, OPT_SURROGATE, OPT_SURROGATE_TOL = 1, 2, 3, 4, 5, 6
-OPT_TENSOR_CORES, OPT_P2P_SPLIT, OPT_TC_GROUPS = 7, 8, 9
+OPT_TENSOR_CORES, OPT_P2P_SPLIT, OPT_TC_GROUPS, OPT_NEAR_TABLES = 7, 8, 9, 10
 TUNE_COLS = ["leaf_cap", "tensor_cores", "split", "depth", "ms", "chosen"]
 STAT_NAMES = ["n", "depth", "boxes", "leaves", "m2l_free", "m2l_reaction", "p2p_free", "p2p_reaction",
               "components", "m2m_edges", "launches", "reaction_keys", "surr_net_pairs", "surr_quad_pairs",
@@ -48,7 +48,7 @@ EXPORTED = ["lfmm_create", "lfmm_set_option", "lfmm_build", "lfmm_build_device",
             "lfmm_surrogate_set_params", "lfmm_surrogate_forward", "lfmm_surrogate_loss_grad",
             "lfmm_batch_create", "lfmm_batch_offsets", "lfmm_batch_evaluate_device", "lfmm_batch_evaluate",
             "lfmm_batch_info", "lfmm_batch_last_error", "lfmm_batch_destroy", "lfmm_autotune",
-            "lfmm_check_bounded_wait"]
+            "lfmm_check_bounded_wait", "lfmm_near_tables"]
 BATCH_INFO = ["problems", "charges", "graph_nodes", "kernel_nodes", "captures", "graph_launches", "direct_runs",
               "timeouts"]
 NOALLOC_MAX_POINTS = 65536
@@ -94,6 +94,7 @@ def load(build: bool = True):
     lib.lfmm_surrogate_forward.argtypes = [_ctxp] + comp + [ctypes.c_int, _fp, _fp]
     lib.lfmm_surrogate_loss_grad.argtypes = [_ctxp] + comp + [ctypes.c_int, _fp, _fp, _dp, _fp]
     lib.lfmm_check_bounded_wait.argtypes = [_ctxp, ctypes.c_double]
+    lib.lfmm_near_tables.argtypes = [_ctxp, _dp]
     lib.lfmm_autotune.argtypes = [_ctxp, ctypes.c_int64, _dp, _ip, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int,
                                   ctypes.POINTER(ctypes.c_int)]
     lib.lfmm_batch_create.argtypes = [ctypes.POINTER(_ctxp), ctypes.c_int, _ip, ctypes.c_int, ctypes.POINTER(_vp)]
@@ -221,6 +222,13 @@ class LayeredFMM:
                                             int(reps), _ptr(rows), 64, ctypes.byref(nrows)), "lfmm_autotune")
         self.n = xyz.shape[0]
         return [dict(zip(TUNE_COLS, r)) for r in rows[:nrows.value]]
+
+    def near_tables(self) -> float:
+        """Build (once) the near-field remainder tables; returns their largest
+        relative deviation from the quadrature at the check points."""
+        e = ctypes.c_double(0.0)
+        self._check(self._lib.lfmm_near_tables(self._ctx, ctypes.byref(e)), "lfmm_near_tables")
+        return e.value
 
     def check_bounded_wait(self, limit_ms: float = 10.0) -> int:
         """Run the device's bounded-wait self-check; returns its status code
