@@ -302,7 +302,8 @@ def multi_rhs_leg(torch, dev, p, flush, nrhs=64, n=1 << 18):
 def many_problems_leg(torch, dev, p, flush, k=48):
     """Float32 form, k independent three-layer problems with log-uniform sizes
     in [2k, 100k]: one CUDA graph replay per evaluation against the same
-    launches issued directly and against k one-at-a-time evaluations."""
+    launches issued directly and against k one-at-a-time evaluations, and the
+    graph again after every problem tuned its settings (lfmm_autotune)."""
     from paper_1908_10863_gb300 import LayeredFMM, LayeredFMMBatch, workloads
     import oracle
     probs = workloads.uneven_problems(k)
@@ -345,9 +346,23 @@ def many_problems_leg(torch, dev, p, flush, k=48):
     fd = [torch.empty((x.shape[0], 3), dtype=torch.float64, device=dev) for x in qd]
     t_seq = timed(lambda: [m.evaluate_device(a, b_, c, s) for m, a, b_, c in zip(ms, qd, pd, fd)])
     seq_phi = np.concatenate([x.cpu().numpy() for x in pd])
+    # the same batch after each problem picked its own settings (evaluation-time tuning)
+    t0 = time.perf_counter()
+    for m, w in zip(ms, probs):
+        m.autotune(w.xyz, w.layer, mode=0, reps=2)
+    tune_s = time.perf_counter() - t0
+    b = LayeredFMMBatch(ms, graph=True)
+    q = torch.from_numpy(b.concat([w.q for w in probs])).to(dev)
+    phi = torch.empty_like(q)
+    fld = torch.empty(3 * total, dtype=torch.float64, device=dev)
+    t_tuned = timed(lambda: b.evaluate_device(q, phi, fld, s))
+    phi_t = phi.cpu().numpy()
+    b.close()
     for m in ms:
         m.close()
     t_g, info, phi_g = res[True]
+    out.update({"graph_tuned_ms": t_tuned, "tuning_s": tune_s, "particles_per_s_tuned": total / (t_tuned / 1e3),
+                "err2_phi_tuned_vs_default": oracle.err2(phi_g, phi_t)})
     out.update({"graph_ms": t_g, "direct_ms": res[False][0], "one_at_a_time_ms": t_seq,
                 "particles_per_s": total / (t_g / 1e3), "speedup_vs_one_at_a_time": t_seq / t_g,
                 "graph_nodes": info["graph_nodes"], "kernel_nodes": info["kernel_nodes"],
