@@ -387,3 +387,104 @@ def test_bf16_rounding_reference():
     torch = pytest.importorskip("torch")
     ref = torch.tensor(v).to(torch.bfloat16).to(torch.float64).numpy()
     assert np.array_equal(r, ref)
+
+
+# ---------------------------------------------------------------------------
+# General media (more than two interfaces): the oracle's per-k linear solve of
+# Appendix A covers any number of layers.  These pins fix it for four layers.
+# ---------------------------------------------------------------------------
+D4 = [0.0, -0.6, -1.2]
+ZR4 = {0: (0.1, 1.1), 1: (-0.55, -0.05), 2: (-1.15, -0.65), 3: (-2.3, -1.3)}
+
+
+def _points4(rng, n):
+    lay = rng.integers(0, 4, n).astype(np.int32)
+    xyz = np.zeros((n, 3))
+    xyz[:, :2] = rng.uniform(-0.5, 0.5, (n, 2))
+    for i in range(n):
+        xyz[i, 2] = rng.uniform(*ZR4[int(lay[i])])
+    return xyz, lay
+
+
+def test_thirty_six_components_for_four_layers():
+    # a layer has a reaction term per bounding interface (eqs. generalcomponents,
+    # zexponential): 2L of them over all layers, so (2L)^2 reaction components
+    L = 3
+    comps = [(l, lp, a, b) for l in range(L + 1) for lp in range(L + 1) for a in (1, 2) for b in (1, 2)
+             if not (a == 1 and l == L) and not (a == 2 and l == 0)
+             and not (b == 1 and lp == L) and not (b == 2 and lp == 0)]
+    assert len(comps) == 36
+    for k in (0.1, 1.0, 4.0):
+        for lp in range(4):
+            s = oracle.sigma(D4, [1.0, 5.0, 2.0, 10.0], k, lp)
+            for l in range(4):
+                for a in (1, 2):
+                    for b in (1, 2):
+                        if (l, lp, a, b) not in comps:
+                            assert s[l, a - 1, b - 1] == 0.0
+
+
+@pytest.mark.parametrize("merge", ["inner", "top"])
+def test_equal_eps_interface_disappears(merge):
+    # an interface between two layers of the same permittivity is no interface:
+    # the four-layer potential equals the three-layer one, which the exact image
+    # series evaluates independently of the linear solve
+    rng = np.random.default_rng(41)
+    xyz, lay = _points4(rng, 80)
+    q = rng.uniform(-1, 1, 80)
+    if merge == "inner":      # layers 1 and 2 share eps = 5: interfaces (0, -1.2) remain
+        eps4, d3, lay3 = [1.0, 5.0, 5.0, 10.0], [0.0, -1.2], np.where(lay >= 2, lay - 1, lay)
+    else:                      # layers 0 and 1 share eps = 1: interfaces (-0.6, -1.2) remain
+        eps4, d3, lay3 = [1.0, 1.0, 5.0, 10.0], [-0.6, -1.2], np.maximum(lay - 1, 0)
+    eps3 = [eps4[0], eps4[2], eps4[3]] if merge == "inner" else [eps4[1], eps4[2], eps4[3]]
+    t = np.arange(30)
+    p4, f4 = oracle.direct(D4, eps4, xyz, lay, q, targets=t, mode=oracle.MODE_QUAD)
+    p3, f3 = oracle.direct(d3, eps3, xyz, lay3.astype(np.int32), q, targets=t, mode=oracle.MODE_IMAGES)
+    assert oracle.err2(p3, p4) < 1e-11
+    assert oracle.err2(f3, f4) < 1e-10
+
+
+def test_uniform_four_layer_medium_is_coulomb():
+    rng = np.random.default_rng(43)
+    xyz, lay = _points4(rng, 40)
+    q = rng.uniform(-1, 1, 40)
+    p4, f4 = oracle.direct(D4, [3.0] * 4, xyz, lay, q, mode=oracle.MODE_QUAD)
+    p0, f0 = oracle.direct([], [3.0], xyz, np.zeros(40, np.int32), q)
+    assert np.max(np.abs(p4 - p0)) < 1e-13 * np.max(np.abs(p0))
+    assert np.max(np.abs(f4 - f0)) < 1e-12 * np.max(np.abs(f0))
+
+
+@pytest.mark.parametrize("src_layer", [1, 2])
+def test_transmission_conditions_four_layers(src_layer):
+    # eq. transmissioncond at every interface of a four-layer medium
+    eps = [2.0, 7.0, 1.5, 12.0]
+    rp = np.array([0.05, -0.1, -0.3 if src_layer == 1 else -0.9])
+    for j, dj in enumerate(D4):
+        above, below = j, j + 1
+        x = np.array([0.2, 0.15, dj])
+
+        def total(l, pt):
+            u, g = oracle.reaction_pair(D4, eps, l, src_layer, pt, rp, mode=oracle.MODE_QUAD)
+            if l == src_layer:
+                R = pt - rp
+                u += 1 / np.linalg.norm(R)
+                g = g - R / np.linalg.norm(R) ** 3
+            return u, g
+        ua, ga = total(above, x)
+        ub, gb = total(below, x)
+        assert ua == pytest.approx(ub, rel=1e-10)
+        assert eps[above] * ga[2] == pytest.approx(eps[below] * gb[2], rel=1e-9)
+        assert ga[0] == pytest.approx(gb[0], rel=1e-9)
+
+
+def test_reciprocity_four_layers():
+    eps = [2.0, 7.0, 1.5, 12.0]
+    rng = np.random.default_rng(47)
+    for l in range(4):
+        for lp in range(4):
+            r = np.array([*rng.uniform(-0.5, 0.5, 2), rng.uniform(*ZR4[l])])
+            rp = np.array([*rng.uniform(-0.5, 0.5, 2), rng.uniform(*ZR4[lp])])
+            u1, _ = oracle.reaction_pair(D4, eps, l, lp, r, rp)
+            u2, _ = oracle.reaction_pair(D4, eps, lp, l, rp, r)
+            free = 1.0 / np.linalg.norm(r - rp) if l == lp else 0.0
+            assert eps[l] * (u1 + free) == pytest.approx(eps[lp] * (u2 + free), rel=1e-11)
