@@ -70,7 +70,12 @@ enum {
 
 /* Create a context for the medium.
  *   d   : host, L interface heights, strictly decreasing (Section 3.1).
- *   L   : number of interfaces, 0 <= L <= 2 (one to three layers).
+ *   L   : number of interfaces, 0 <= L <= 3 (one to four layers).  With
+ *         three interfaces the reaction densities are evaluated by solving
+ *         the interface problem of Appendix A at each quadrature node (the
+ *         learned near-field kernels stay limited to three layers); when the
+ *         interface gaps share a unit, grid planes contain the interfaces and
+ *         the reaction M2L uses its keyed tables on the aligned levels.
  *   eps : host, L+1 permittivities > 0, layer 0 on top.
  *   p   : truncation order of all expansions, 1 <= p <= 20 (FP64) and
  *         p <= 14 in the FP32 form.

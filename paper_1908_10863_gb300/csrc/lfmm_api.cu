@@ -223,7 +223,10 @@ static LfErr setup_rules(lfmm_ctx* ctx)
     LF_TRY(make_rule(ctx->near_pole, 32, ctx->near_pole ? 48 : ctx->quad_nodes, T, W));
     LF_TRY(upload_rule(ctx->gl_t_m2l, ctx->gl_w_m2l, T, W));
     ctx->gl_q_m2l = (int)T.size();
-    LF_TRY(make_rule(ctx->near_pole, 32, ctx->near_pole ? 48 : 32, T, W));
+    // four layers: the remainder mixes more exponential rates, and the field
+    // kernels (one more power of k) need 64 nodes for 1e-12 where 32 give 1e-9
+    const int qnear = (ctx->L >= 3) ? 64 : (ctx->near_pole ? 48 : 32);
+    LF_TRY(make_rule(ctx->near_pole, 32, qnear, T, W));
     LF_TRY(upload_rule(ctx->gl_t_near, ctx->gl_w_near, T, W));
     ctx->gl_q_near = (int)T.size();
     return LfErr();
@@ -313,6 +316,87 @@ static void poly_fit3(const double* xs, const double* ys, double* c)
     c[0] = ys[0] - d1 * xs[0] + d2 * xs[0] * xs[1];
 }
 
+// Reflection or transmission coefficient of interface i (layer i above,
+// i + 1 below) for a wave arriving from layer u and leaving into layer v: the
+// two-layer problem of that interface alone.
+static double iface_coef(const double* eps, int i, int u, int v)
+{
+    const int o = (u == i) ? i + 1 : i;
+    if (v == u) return (eps[u] - eps[o]) / (eps[u] + eps[o]);
+    return 2.0 * eps[u] / (eps[u] + eps[v]);
+}
+
+// Density of a reaction component for three or more interfaces.  The free part
+// of the source leaves interface i_s (d_lp for b = 1, d_{lp-1} for b = 2) and
+// the reaction term of the target leaves interface i_t (d_l for a = 1,
+// d_{l-1} for a = 2).  Every contribution follows a path of reflections and
+// transmissions between interfaces, each full crossing of layer j adding
+// e^{-k D_j}.  The direct path gives the leading term C e^{-k zeta} with
+// zeta = |d_{i_s} - d_{i_t}| and C the product of the single-interface
+// coefficients along it; any other path with the same ends crosses some layer
+// twice more, so the remainder decays at least like e^{-k (zeta + 2 D_min)}.
+// The leading term is checked against the interface problem at large k, and
+// the remainder series (lf_sigma_rem) against the solve at moderate k.
+static LfErr setup_general_density(const lfmm_ctx* ctx, LfmmComp& c)
+{
+    const int L = ctx->L;
+    const double* d = ctx->d;
+    const double* eps = ctx->eps;
+    const int is = (c.b == 1) ? c.lp : c.lp - 1;
+    const int it = (c.a == 1) ? c.l : c.l - 1;
+    double C;
+    if (is == it) {
+        C = iface_coef(eps, is, c.lp, c.l);
+    } else if (it > is) {  // downward
+        C = iface_coef(eps, is, c.lp, is + 1);
+        for (int i = is + 1; i < it; ++i) C *= iface_coef(eps, i, i, i + 1);
+        C *= iface_coef(eps, it, it, c.l);
+    } else {  // upward
+        C = iface_coef(eps, is, c.lp, is);
+        for (int i = is - 1; i > it; --i) C *= iface_coef(eps, i, i + 1, i);
+        C *= iface_coef(eps, it, it + 1, c.l);
+    }
+    double dmin = INFINITY;
+    for (int j = 1; j < L; ++j) dmin = std::min(dmin, d[j - 1] - d[j]);
+    c.C = C;
+    c.zeta = fabs(d[is] - d[it]);
+    c.zeta_r = c.zeta + 2.0 * dmin;
+    c.has_rem = 1;
+    c.D = dmin;
+    // coupling steps of the remainder series: D_min (N + 1) >= zeta_r, plus one
+    c.nterm = std::min(60, (int)std::ceil(c.zeta_r / dmin) + 1);
+    const double k1 = std::min(30.0 / dmin, 600.0 / std::max(c.zeta, 1e-300));
+    const double lead = lf_sigma_solve(c, k1) * exp(k1 * c.zeta);
+    if (!(fabs(lead - C) <= 1e-8 * (1.0 + fabs(C)))) return "EINVAL: interface problem of the medium is singular";
+    // where the subtraction is still harmless the series must reproduce it
+    for (double kk : {0.05 / dmin, 0.5 / dmin, 2.0 / dmin}) {
+        const double direct = (lf_sigma_solve(c, kk) * exp(kk * c.zeta) - C) * exp(kk * (c.zeta_r - c.zeta));
+        const double series = lf_sigma_rem<true>(c, kk);
+        if (!(fabs(series - direct) <= 1e-9 * (1.0 + fabs(direct))))
+            return "EINVAL: remainder series of the interface problem does not converge";
+    }
+    return LfErr();
+}
+
+// Whether the determinant of the interface problem changes sign for
+// k in [-ln(1.5) / D_max, 0]: a pole just left of the integration range, which
+// the composite quadrature rule resolves (the same criterion as x <= 1.5 for
+// one inner layer).
+static bool general_near_pole(const lfmm_ctx* ctx, const LfmmComp& c)
+{
+    double dmax = 0.0;
+    for (int j = 1; j < ctx->L; ++j) dmax = std::max(dmax, ctx->d[j - 1] - ctx->d[j]);
+    const double klo = -log(1.5) / dmax;
+    double prev = 0.0;
+    for (int k = 0; k <= 300; ++k) {
+        double det = 0.0;
+        lf_sigma_solve(c, klo * (1.0 - k / 300.0), &det);
+        if (k > 0 && det * prev <= 0.0) return true;
+        prev = det;
+    }
+    return false;
+}
+
 static LfErr setup_components(lfmm_ctx* ctx)
 {
     const int L = ctx->L;
@@ -347,7 +431,13 @@ static LfErr setup_components(lfmm_ctx* ctx)
                     if (a == 2 && b == 2) { c.s = -1.0; c.o = d[l - 1] + d[lp - 1]; }
                     c.refl = c.s < 0;
                     c.iface = (a == 1) ? d[l] : d[l - 1];
-                    if (L == 1) {
+                    c.nif = L;
+                    for (int j = 0; j < L; ++j) c.md[j] = d[j];
+                    for (int j = 0; j <= L; ++j) c.me[j] = ctx->eps[j];
+                    if (L >= 3) {
+                        LF_TRY(setup_general_density(ctx, c));
+                        if (general_near_pole(ctx, c)) ctx->near_pole = 1;
+                    } else if (L == 1) {
                         c.D = 0.0;
                         c.C = sigma_two_layer(ctx->eps, l, lp, a, b);
                         c.zeta = 0.0;
@@ -498,7 +588,7 @@ static bool any_bad(int64_t n, F bad_range)
 // layer l spans dd[l + 1] < z < dd[l] with dd[0] = +inf, dd[L + 1] = -inf
 static bool points_bad(const lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int64_t b, int64_t e)
 {
-    double dd[4];  // at most two interfaces
+    double dd[LFMM_MAXL + 2];
     const int L = ctx->L;
     dd[0] = INFINITY;
     for (int k = 0; k < L; ++k) dd[k + 1] = ctx->d[k];
@@ -544,12 +634,13 @@ lfmm_status lfmm_create(const double* d, int L, const double* eps, int p, lfmm_c
 {
     if (!out) return LFMM_EINVAL;
     *out = nullptr;
-    if (L < 0 || L > 2 || p < 1 || p > LFMM_PMAX || !eps || (L > 0 && !d)) return LFMM_EINVAL;
+    if (L < 0 || L > LFMM_MAXL || p < 1 || p > LFMM_PMAX || !eps || (L > 0 && !d)) return LFMM_EINVAL;
     for (int l = 0; l <= L; ++l)
         if (!(eps[l] > 0.0) || !std::isfinite(eps[l])) return LFMM_EINVAL;
     for (int l = 0; l < L; ++l)
         if (!std::isfinite(d[l])) return LFMM_EINVAL;
-    if (L == 2 && !(d[0] > d[1])) return LFMM_EINVAL;
+    for (int l = 1; l < L; ++l)
+        if (!(d[l - 1] > d[l])) return LFMM_EINVAL;
     lfmm_ctx* ctx = new (std::nothrow) lfmm_ctx();
     if (!ctx) return LFMM_ENOMEM;
     ctx->L = L;

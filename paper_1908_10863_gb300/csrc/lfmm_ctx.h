@@ -34,8 +34,8 @@ struct LfmmLevel {
 struct lfmm_ctx {
     // medium and order
     int L = 0;
-    double d[2] = {0, 0};
-    double eps[3] = {1, 1, 1};
+    double d[LFMM_MAXL] = {0};
+    double eps[LFMM_MAXL + 1] = {1, 1, 1, 1};
     int p = 0;
     // options
     int precision = 0;
@@ -43,7 +43,7 @@ struct lfmm_ctx {
     int profile = 0;
     int quad_nodes = 64;
     int quad_nodes_near = 32;
-    int near_pole = 0;  // density denominator has a real zero in (0, 1.5]
+    int near_pole = 0;  // the interface problem has a pole just left of k = 0 (x = e^{-kD} in (1, 1.5])
     std::string err;
     // bumped by every successful build, option change and surrogate update:
     // a captured evaluation is valid only for the serial it was captured at
@@ -80,7 +80,7 @@ struct lfmm_ctx {
     int depth = 0;
     double H = 1.0;
     double origin[3] = {0, 0, 0};
-    int nlayer_used[3] = {0, 0, 0};
+    int nlayer_used[LFMM_MAXL + 1] = {0};
     std::vector<LfmmLevel> levels;  // index = level 0..depth
     int nbox_total = 0;
 

@@ -306,7 +306,8 @@ struct M2LArgs {
     int Q;
 };
 
-template <typename R, bool REACT>
+// GEN: reaction components of media of four layers
+template <typename R, bool REACT, bool GEN = false>
 __global__ void k_m2l(M2LArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -357,7 +358,7 @@ __global__ void k_m2l(M2LArgs a)
             for (int j = tid; j < TT; j += blockDim.x) sT[j] = src[j];
         } else {
             const double zz = (cp.a == 1) ? vz : -vz;  // > 0 for valid entries
-            lf_sommerfeld_table_block(cp, rho, zz, a.h, 2 * p, sTd, TS, a.Q, a.gl_t, a.gl_w, sJ, sA);
+            lf_sommerfeld_table_block<GEN>(cp, rho, zz, a.h, 2 * p, sTd, TS, a.Q, a.gl_t, a.gl_w, sJ, sA);
             for (int j = tid; j < TT; j += blockDim.x) {
                 int N = j / TS, mu = j - N * TS;
                 double v = (mu <= N) ? sTd[j] : 0.0;
@@ -573,6 +574,9 @@ static LfErr far_field(lfmm_ctx* ctx, cudaStream_t st)
     const size_t msm_f = m2l_smem<R>(p, Q, false), msm_r = m2l_smem<R>(p, Q, true);
     LF_CHECK(cudaFuncSetAttribute(k_m2l<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm_f));
     LF_CHECK(cudaFuncSetAttribute(k_m2l<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm_r));
+    const bool general = ctx->L >= 3;
+    if (general)
+        LF_CHECK(cudaFuncSetAttribute(k_m2l<R, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm_r));
     const int mth = ((nc + 31) / 32) * 32;
     const size_t lsm = sizeof(R) * (nc + 2 * (size_t)nre);
     const int lth = ((nre + 31) / 32) * 32;
@@ -627,7 +631,10 @@ static LfErr far_field(lfmm_ctx* ctx, cudaStream_t st)
             for (int r = 0; r < nr; ++r) {
                 a.M = M + r * ms;
                 a.L = L + r * ms;
-                ++ctx->launches, k_m2l<R, true><<<lv.nbox, mth, msm_r, st>>>(a);
+                if (general)
+                    ++ctx->launches, k_m2l<R, true, true><<<lv.nbox, mth, msm_r, st>>>(a);
+                else
+                    ++ctx->launches, k_m2l<R, true><<<lv.nbox, mth, msm_r, st>>>(a);
             }
             lf_prof_stop(ctx, ph, st);
         }

@@ -37,7 +37,8 @@
 #include <stdint.h>
 
 #define LFMM_PMAX 20
-#define LFMM_MAXCOMP 24
+#define LFMM_MAXL 3      // interfaces (four layers: the layer id takes two bits of a box key)
+#define LFMM_MAXCOMP 40  // (L + 1) free + (2L)^2 reaction components
 #define LFMM_QMAX 128
 #define LFMM_FINE_LEVEL 10
 #define LFMM_ENT_SHIFT 26
@@ -82,6 +83,12 @@ struct LfmmComp {
     double zeta_r;   // remainder ~ exp(-k zeta_r)
     double rem[5];   // remainder numerator / x^{zeta_r / D}
     double den[3];   // den[0] = 1
+    // more than two interfaces: sigma(k) has no single x; it is evaluated by
+    // solving the interface problem of the medium at each k
+    int nif;                         // interfaces of the medium
+    int nterm;                       // coupling steps summed for the remainder (nif >= 3)
+    double md[LFMM_MAXL];            // interface heights
+    double me[LFMM_MAXL + 1];        // permittivities
 };
 
 __host__ __device__ __forceinline__ int lf_nre(int p) { return (p + 1) * (p + 2) / 2; }
@@ -236,21 +243,197 @@ __device__ __forceinline__ void lf_bessel_j_set(double x, int nmax, double* out)
     for (int m = 0; m <= nmax; ++m) out[m] *= inv;
 }
 
-__device__ __forceinline__ double lf_poly(const double* c, int n, double x)
+__host__ __device__ __forceinline__ double lf_poly(const double* c, int n, double x)
 {
     double v = 0.0;
     for (int i = n - 1; i >= 0; --i) v = v * x + c[i];
     return v;
 }
 
-// Box-unit Sommerfeld table of one component (block-cooperative, FP64):
-//   T[N*ld + mu] = S^{N+1} K_{N,mu}(rho, z) for 0 <= mu <= N <= nmax,
-// rho_h = rho / S, z_h = z / S (z > 0).  K = C T_N^mu(rho, z + zeta) (the
-// leading exponential of sigma, closed form) + the remainder integral by
-// Q-point Gauss-Laguerre in t = k (z + zeta_r):
-//   (1/Z) sum_q w_q J_mu(k_q rho) k_q^N [sigma_r(k_q) e^{k_q zeta_r}].
-// Scratch: sJ[Q*(nmax+1)], sA[Q*(nmax+1)] doubles in shared memory.
-// All threads of the block must call it; ends with __syncthreads().
+// The spectral interface problem (Section 3.1, Appendix A) of a medium with
+// 3 <= nif <= LFMM_MAXL interfaces at one k.  In layer j the reaction part is
+// A_j e^{-k(z - d_j)} (j < L) + B_j e^{-k(d_{j-1} - z)} (j > 0); the free part
+// of the source in layer lp is split at its interfaces: b = 1 keeps the part
+// that reaches d_lp (value 1 there, slope +k), b = 2 the part that reaches
+// d_{lp-1} (value 1, slope -k).  Each interface d_i gives two rows
+// (continuity of u and of eps du/dz, divided by k) in the unknowns ordered
+// A_0, B_1, A_1, B_2, ..., B_L: A_i (column 2i) and B_{i+1} (column 2i + 1)
+// belong to interface i, whose rows couple them with the constant block
+//   A0_i = [[1, -1], [-eps_i, -eps_{i+1}]]
+// and reach the neighbouring interfaces' unknowns B_i and A_{i+1} through
+// x_i = e^{-k D_i} and x_{i+1} (the coupling X).  sigma^{1b} = A_l,
+// sigma^{2b} = B_l.
+struct LfIfaceProblem {
+    int L;
+    double x[LFMM_MAXL + 1];  // x[j] = e^{-k D_j} of the inner layers 1 .. L-1
+    const double* eps;
+};
+
+__host__ __device__ __forceinline__ void lf_iface_setup(const LfmmComp& c, double k, LfIfaceProblem& P)
+{
+    P.L = c.nif;
+    P.eps = c.me;
+    for (int j = 0; j <= LFMM_MAXL; ++j) P.x[j] = 0.0;
+    for (int j = 1; j < c.nif; ++j) P.x[j] = exp(-k * (c.md[j - 1] - c.md[j]));
+}
+
+// v <- T v with T = -A0^{-1} X (one more coupling step between interfaces)
+__host__ __device__ __forceinline__ void lf_iface_step(const LfIfaceProblem& P, double* v)
+{
+    double w[2 * LFMM_MAXL];
+    const int L = P.L;
+    for (int i = 0; i < L; ++i) {
+        const double ea = P.eps[i], eb = P.eps[i + 1];
+        double cu = 0.0, fl = 0.0;
+        if (i > 0) {  // B_i of interface i - 1
+            cu += P.x[i] * v[2 * i - 1];
+            fl += ea * P.x[i] * v[2 * i - 1];
+        }
+        if (i + 1 < L) {  // A_{i+1} of interface i + 1
+            cu -= P.x[i + 1] * v[2 * i + 2];
+            fl += eb * P.x[i + 1] * v[2 * i + 2];
+        }
+        // -A0_i^{-1} (cu, fl), A0_i^{-1} = [[eb, -1], [-ea, -1]] / (ea + eb)
+        const double s = 1.0 / (ea + eb);
+        w[2 * i] = -(eb * cu - fl) * s;
+        w[2 * i + 1] = (ea * cu + fl) * s;
+    }
+    for (int r = 0; r < 2 * L; ++r) v[r] = w[r];
+}
+
+// the uncoupled response u0 = A0^{-1} b to the component's source term
+__host__ __device__ __forceinline__ void lf_iface_u0(const LfmmComp& c, const LfIfaceProblem& P, double* u0)
+{
+    for (int r = 0; r < 2 * P.L; ++r) u0[r] = 0.0;
+    const int i = (c.b == 1) ? c.lp : c.lp - 1;
+    const double ea = P.eps[i], eb = P.eps[i + 1];
+    // right-hand side of interface i: b = 1 (source above): (-1, -ea); b = 2 (below): (+1, -eb)
+    const double cu = (c.b == 1) ? -1.0 : 1.0, fl = (c.b == 1) ? -ea : -eb;
+    const double s = 1.0 / (ea + eb);
+    u0[2 * i] = (eb * cu - fl) * s;
+    u0[2 * i + 1] = (-ea * cu - fl) * s;
+}
+
+// Full solve (dense elimination with partial pivoting, n = 2L <= 6) of the
+// interface problem; returns the component's density sigma^{ab}_{l lp}(k)
+// and, if asked, the whole solution u and the determinant (whose sign
+// locates poles).
+__host__ __device__ __forceinline__ double lf_sigma_solve(const LfmmComp& c, double k, double* det = nullptr,
+                                                          double* u = nullptr)
+{
+    const int L = c.nif, n = 2 * L;
+    double M[2 * LFMM_MAXL][2 * LFMM_MAXL + 1];
+    for (int r = 0; r < n; ++r)
+        for (int j = 0; j <= n; ++j) M[r][j] = 0.0;
+    for (int i = 0; i < L; ++i) {
+        double* cu = M[2 * i];
+        double* fl = M[2 * i + 1];
+        const double ea = c.me[i], eb = c.me[i + 1];
+        // layer i (above) at z = d_i
+        cu[2 * i] += 1.0;
+        fl[2 * i] -= ea;
+        if (i > 0) {
+            const double x = exp(-k * (c.md[i - 1] - c.md[i]));
+            cu[2 * i - 1] += x;
+            fl[2 * i - 1] += ea * x;
+        }
+        // layer i + 1 (below) at z = d_i, subtracted
+        cu[2 * i + 1] -= 1.0;
+        fl[2 * i + 1] -= eb;
+        if (i + 1 < L) {
+            const double x = exp(-k * (c.md[i] - c.md[i + 1]));
+            cu[2 * i + 2] -= x;
+            fl[2 * i + 2] += eb * x;
+        }
+        // the source's free part, on the right-hand side
+        if (c.b == 1 && i == c.lp) {  // source above d_i
+            cu[n] -= 1.0;
+            fl[n] -= ea;
+        }
+        if (c.b == 2 && i + 1 == c.lp) {  // source below d_i
+            cu[n] += 1.0;
+            fl[n] -= eb;
+        }
+    }
+    double dt = 1.0;
+    for (int col = 0; col < n; ++col) {
+        int pr = col;
+        for (int r = col + 1; r < n; ++r)
+            if (fabs(M[r][col]) > fabs(M[pr][col])) pr = r;
+        if (pr != col) {
+            for (int j = 0; j <= n; ++j) {
+                const double t = M[col][j];
+                M[col][j] = M[pr][j];
+                M[pr][j] = t;
+            }
+            dt = -dt;
+        }
+        const double pv = M[col][col];
+        dt *= pv;
+        if (pv == 0.0) {
+            if (det) *det = 0.0;
+            return 0.0;
+        }
+        for (int r = col + 1; r < n; ++r) {
+            const double f = M[r][col] / pv;
+            for (int j = col; j <= n; ++j) M[r][j] -= f * M[col][j];
+        }
+    }
+    if (det) *det = dt;
+    double xs[2 * LFMM_MAXL];
+    for (int r = n - 1; r >= 0; --r) {
+        double v = M[r][n];
+        for (int j = r + 1; j < n; ++j) v -= M[r][j] * xs[j];
+        xs[r] = v / M[r][r];
+    }
+    if (u)
+        for (int r = 0; r < n; ++r) u[r] = xs[r];
+    return (c.a == 1) ? xs[2 * c.l] : xs[2 * c.l - 1];
+}
+
+// The remainder of a reaction density in the form every quadrature uses:
+//   (sigma(k) - C e^{-k zeta}) e^{k zeta_r},
+// bounded for k >= 0.  Up to two interfaces it is rem(x) / den(x) with
+// x = e^{-k D}.  Beyond, the solution of (A0 + X) u = b satisfies
+// u = u0 + T u (T = -A0^{-1} X, u0 = A0^{-1} b), hence for any N
+//   u = sum_{n <= N} T^n u0 + T^{N+1} u.
+// T moves a response one interface on and multiplies it by the crossed
+// layer's x, so the target entry of T^n u0 vanishes for n < m (m = layers
+// between the source's and the target's interface) and equals the direct
+// path C e^{-k zeta} for n = m.  The remainder is therefore the sum of the
+// terms n = m+1 .. N plus the tail T^{N+1} u: products of small factors, with
+// no cancellation against C.  With D_min (N+1) >= zeta_r the tail's rounding
+// error stays below e^{-k zeta_r} times machine precision, so the scaled
+// remainder keeps full relative accuracy at every k.  The solve and the
+// series are compiled only into kernels instantiated with GEN (launched for
+// media of four layers), so the kernels of thinner media keep their registers.
+template <bool GEN>
+__host__ __device__ __forceinline__ double lf_sigma_rem(const LfmmComp& c, double k)
+{
+    if (!GEN || c.nif <= 2) {
+        const double x = exp(-c.D * k);
+        return lf_poly(c.rem, 5, x) / lf_poly(c.den, 3, x);
+    }
+    LfIfaceProblem P;
+    lf_iface_setup(c, k, P);
+    double u[2 * LFMM_MAXL], v[2 * LFMM_MAXL];
+    lf_sigma_solve(c, k, nullptr, u);
+    lf_iface_u0(c, P, v);
+    const int it = (c.a == 1) ? 2 * c.l : 2 * c.l - 1;  // target entry
+    const int is = (c.b == 1) ? c.lp : c.lp - 1, ib = (c.a == 1) ? c.l : c.l - 1;
+    const int m = is > ib ? is - ib : ib - is;
+    const int N = c.nterm;
+    double rem = 0.0;
+    for (int n = 1; n <= N; ++n) {
+        lf_iface_step(P, v);
+        if (n > m) rem += v[it];
+    }
+    for (int n = 0; n <= N; ++n) lf_iface_step(P, u);
+    rem += u[it];
+    return rem * exp(k * c.zeta_r);
+}
+
+template <bool GEN = false>
 __device__ __forceinline__ void lf_sommerfeld_table_block(const LfmmComp& c, double rho_h, double z_h, double S,
                                                           int nmax, double* T, int ld, int Q, const double* gl_t,
                                                           const double* gl_w, double* sJ, double* sA)
@@ -261,12 +444,11 @@ __device__ __forceinline__ void lf_sommerfeld_table_block(const LfmmComp& c, dou
         lf_theta_column(rho_h, z_h + c.zeta / S, mu, nmax, c.C, T, ld);
     if (c.has_rem) {
         const double Zh = z_h + c.zeta_r / S;
-        const double Dh = c.D / S;
         const double iZ = 1.0 / Zh;
         for (int q = tid; q < Q; q += nt) {
             double kap = gl_t[q] * iZ;
-            double x = exp(-Dh * kap);
-            double rt = lf_poly(c.rem, 5, x) / lf_poly(c.den, 3, x);
+            // kap is in box units: the density's k is kap / S
+            double rt = lf_sigma_rem<GEN>(c, kap / S);
             double a = gl_w[q] * iZ * rt;
             double* Arow = sA + q * w;
             for (int N = 0; N <= nmax; ++N) {
@@ -346,18 +528,16 @@ struct LfSum<double> {
 #define LF_NT_PER (3 * LF_NT_NS * LF_NT_NW)  // doubles per component: [kernel][w][s]
 
 // the three scaled remainders at (s, w) by the quadrature rule in t
+template <bool GEN = false>
 __device__ __forceinline__ void lf_nt_point(const LfmmComp& c, double s, double w, int Q, const double* gl_t,
                                             const double* gl_w, double out[3])
 {
     double a00 = 0.0, a10 = 0.0, a11 = 0.0;
-    const double dw = c.D * w / c.zeta_r;
+    // t = k Z and w = zeta_r / Z: k = t w / zeta_r
+    const double kw = w / c.zeta_r;
     for (int q = 0; q < Q; ++q) {
         const double t = gl_t[q];
-        const double x = exp(-dw * t);
-        double num = c.rem[4];
-        for (int i = 3; i >= 0; --i) num = num * x + c.rem[i];
-        const double den = (c.den[2] * x + c.den[1]) * x + c.den[0];
-        const double f = gl_w[q] * num / den;
+        const double f = gl_w[q] * lf_sigma_rem<GEN>(c, t * kw);
         const double j0v = j0(t * s), j1v = j1(t * s);
         a00 += f * j0v;
         a10 += f * t * j0v;
@@ -413,7 +593,7 @@ __device__ __forceinline__ bool lf_nt_remainder(const double* __restrict__ ctab,
     return true;
 }
 
-template <typename R>
+template <typename R, bool GEN = false>
 __device__ __forceinline__ void lf_reaction_pair(const LfmmComp& c, R rho, R h, int Q, const double* gl_t,
                                                  const double* gl_w, R& k00, R& k10, R& k11,
                                                  const double* ctab = nullptr)
@@ -442,11 +622,20 @@ __device__ __forceinline__ void lf_reaction_pair(const LfmmComp& c, R rho, R h, 
     R D = (R)c.D;
     for (int q = 0; q < Q; ++q) {
         R kap = (R)gl_t[q] * iZ;
-        R x = F::Exp(-D * kap);
-        R num = (R)c.rem[4];
-        for (int i = 3; i >= 0; --i) num = num * x + (R)c.rem[i];
-        R den = ((R)c.den[2] * x + (R)c.den[1]) * x + (R)c.den[0];
-        R w = (R)gl_w[q] * iZ * num / den;
+        R w;
+        if (!GEN || c.nif <= 2) {
+            R x = F::Exp(-D * kap);
+            R num = (R)c.rem[4];
+            for (int i = 3; i >= 0; --i) num = num * x + (R)c.rem[i];
+            R den = ((R)c.den[2] * x + (R)c.den[1]) * x + (R)c.den[0];
+            R rt = num / den;
+            w = (R)gl_w[q] * iZ * rt;
+        } else {
+            // the solved remainder carries rounding noise times e^{k (zeta_r - zeta)},
+            // which only the node weight (~e^{-t}) brings back to size: form the
+            // product in double before narrowing
+            w = (R)(gl_w[q] * (double)iZ * lf_sigma_rem<true>(c, (double)kap));
+        }
         R a = kap * rho;
         R j0v = F::J0(a), j1v = F::J1(a);
         k00 += w * j0v;

@@ -39,7 +39,7 @@ static inline int lf_blocks(int64_t n, int t) { return (int)((n + t - 1) / t); }
 #define KEY_NONE 0xffffffffu
 
 
-// key = comp (5 bits) | level (4 bits) | offset index (12 bits, offsets in [-7, 7]^3)
+// key = comp (6 bits) | level (4 bits) | offset index (12 bits, offsets in [-7, 7]^3)
 #define R_OR 7
 #define R_OW (2 * R_OR + 1)
 __host__ __device__ __forceinline__ uint32_t rkey(int c, int l, int ox, int oy, int oz)
@@ -109,6 +109,7 @@ __global__ void k_key_starts(const uint32_t* __restrict__ keys, int n, const int
 // One Sommerfeld table per (component, level, rho^2, oz): the table depends on
 // the lateral distance only; the azimuth enters through the phases applied
 // when the operator is assembled.
+template <bool GEN>
 __global__ void k_m2r_tables(const LfmmComp* __restrict__ comps, const int4* __restrict__ tdesc, int ntab,
                              const double* __restrict__ levelh, int P,
                              const double* __restrict__ gt, const double* __restrict__ gw, int Q,
@@ -127,7 +128,7 @@ __global__ void k_m2r_tables(const LfmmComp* __restrict__ comps, const int4* __r
     const double zz = (cp.a == 1) ? (double)oz : (double)(-oz);
     for (int j = threadIdx.x; j < TT; j += blockDim.x) sT[j] = 0.0;
     __syncthreads();
-    lf_sommerfeld_table_block(cp, rho, zz, levelh[l], 2 * P, sT, TS, Q, gt, gw, sJ, sA);
+    lf_sommerfeld_table_block<GEN>(cp, rho, zz, levelh[l], 2 * P, sT, TS, Q, gt, gw, sJ, sA);
     double* out = tables + (size_t)k * TT;
     for (int j = threadIdx.x; j < TT; j += blockDim.x) {
         int N = j / TS, mu = j - N * TS;
@@ -193,7 +194,7 @@ LfErr lf_prepare_m2r(lfmm_ctx* ctx, cudaStream_t st)
     }
     LF_TRY(lf_cuda(cudaGetLastError(), "m2r keys"));
     // vals hold absolute entry indices (e), keys sorted ascending
-    // keys use bits 0..20 (component << 16 | level << 12 | offset): three digits
+    // keys use bits 0..21 (component << 16 | level << 12 | offset): three digits
     LF_TRY(lf_radix_sort(ctx, keys, vals, ne, st, 0, 3));
     LF_TRY(lf_reserve(ctx->flags, (size_t)ne * 4 + 16));
     LF_TRY(lf_reserve(ctx->idx, (size_t)ne * 4 + 16));
@@ -248,8 +249,9 @@ LfErr lf_prepare_m2r(lfmm_ctx* ctx, cudaStream_t st)
     LF_TRY(lf_reserve(ctx->m2r_levelh, sizeof(double) * 16));
     LF_CHECK(cudaMemcpyAsync(ctx->m2r_levelh.ptr, hl, sizeof(double) * 16, cudaMemcpyHostToDevice, st));
     size_t sm = sizeof(double) * ((size_t)TT + 2 * (size_t)Q * TS);
-    LF_CHECK(cudaFuncSetAttribute(k_m2r_tables, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    ++ctx->launches, k_m2r_tables<<<ntab, 128, sm, st>>>(ctx->comp_dev.as<LfmmComp>(), ctx->m2r_tdesc.as<int4>(), ntab,
+    auto tabk = (ctx->L >= 3) ? k_m2r_tables<true> : k_m2r_tables<false>;
+    LF_CHECK(cudaFuncSetAttribute(tabk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    ++ctx->launches, tabk<<<ntab, 128, sm, st>>>(ctx->comp_dev.as<LfmmComp>(), ctx->m2r_tdesc.as<int4>(), ntab,
                                                          ctx->m2r_levelh.as<double>(), P, ctx->gl_t_m2l.as<double>(),
                                                          ctx->gl_w_m2l.as<double>(), Q, ctx->m2r_tables.as<double>());
     LF_TRY(lf_cuda(cudaGetLastError(), "m2r tables"));

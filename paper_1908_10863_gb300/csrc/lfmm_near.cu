@@ -118,7 +118,7 @@ __device__ __forceinline__ void p2p_free_add(R dx, R dy, R dz, const R* qs, int 
 
 // Reaction kernels of one pair by the quadrature, or by the component's
 // remainder table ctab where given (once), applied to the batch.
-template <typename R, int RB, typename S>
+template <typename R, int RB, bool GEN = false, typename S>
 __device__ __forceinline__ void p2p_reaction_add(const LfmmComp& cp, R dx, R dy, R dz, const R* qs, int qsk, int nr,
                                                  int Qn, const double* gl_t, const double* gl_w, P2PAccT<S, RB>& A,
                                                  const double* ctab)
@@ -127,7 +127,7 @@ __device__ __forceinline__ void p2p_reaction_add(const LfmmComp& cp, R dx, R dy,
     R h = (cp.a == 1) ? dz : -dz;
     R rho = F::Sqrt(dx * dx + dy * dy);
     R k00, k10, k11;
-    lf_reaction_pair<R>(cp, rho, h, Qn, gl_t, gl_w, k00, k10, k11, ctab);
+    lf_reaction_pair<R, GEN>(cp, rho, h, Qn, gl_t, gl_w, k00, k10, k11, ctab);
     const R k10s = (cp.a == 1) ? k10 : -k10;
     const R g = rho > R(0) ? k11 / rho : R(0);
 #pragma unroll
@@ -165,7 +165,8 @@ __device__ __forceinline__ void p2p_store(const P2PArgs& a, int i, const P2PAcc<
 }
 
 // One block per target leaf (FP64 form), a batch of RB right-hand sides.
-template <typename R, int RB>
+// GEN: media of four layers (both forms, one right-hand side per launch).
+template <typename R, int RB, bool GEN = false>
 __global__ void __launch_bounds__(P2P_T) k_p2p(P2PArgs a)
 {
     __shared__ R sx[P2P_T], sy[P2P_T], sz[P2P_T], sq[RB][P2P_T];
@@ -211,8 +212,8 @@ __global__ void __launch_bounds__(P2P_T) k_p2p(P2PArgs a)
                         p2p_free_add<R, RB>(xi - sx[u], yi - sy[u], zi - sz[u], &sq[0][u], P2P_T, a.nr, A);
                 } else {
                     for (int u = 0; u < cnt; ++u)
-                        p2p_reaction_add<R, RB>(cp, xi - sx[u], yi - sy[u], zi - sz[u], &sq[0][u], P2P_T, a.nr,
-                                                a.Qn, a.gl_t, a.gl_w, A, LF_CTAB(a, c));
+                        p2p_reaction_add<R, RB, GEN>(cp, xi - sx[u], yi - sy[u], zi - sz[u], &sq[0][u], P2P_T,
+                                                     a.nr, a.Qn, a.gl_t, a.gl_w, A, LF_CTAB(a, c));
                 }
             }
         }
@@ -606,7 +607,8 @@ LfErr lf_near_field(lfmm_ctx* ctx, cudaStream_t st)
     // Few leaves (small problems) leave most SMs idle with one warp or block
     // per leaf: share each near list between `split` of them.  A set value
     // (ctx->p2p_split, e.g. from the tuner) wins over this occupancy rule.
-    const bool warp_kernel = !net && ctx->precision;
+    const bool general = ctx->L >= 3;
+    const bool warp_kernel = !net && !general && ctx->precision;
     int split = ctx->p2p_split;
     if (split <= 0) {
         const int want = warp_kernel ? 152 * 32 : 152 * 8;  // warps, or blocks of P2P_T threads
@@ -621,13 +623,18 @@ LfErr lf_near_field(lfmm_ctx* ctx, cudaStream_t st)
     const double* phi0 = a.phi;
     double* fld0 = a.fld;
     const char* q0 = reinterpret_cast<const char*>(a.q);
-    const int step = net ? 1 : (ctx->precision ? 4 : 8);
+    const int step = (net || general) ? 1 : (ctx->precision ? 4 : 8);
     for (int r0 = 0; r0 < nr; r0 += step) {
         a.nr = nr - r0 < step ? nr - r0 : step;
         a.q = q0 + (size_t)r0 * qs;
         a.phi = const_cast<double*>(phi0) + (size_t)r0 * ctx->n;
         a.fld = fld0 + (size_t)r0 * ctx->n * 3;
-        if (net) {
+        if (general) {
+            if (ctx->precision)
+                ++ctx->launches, k_p2p<float, 1, true><<<leaf.nbox * split, P2P_T, 0, st>>>(a);
+            else
+                ++ctx->launches, k_p2p<double, 1, true><<<leaf.nbox * split, P2P_T, 0, st>>>(a);
+        } else if (net) {
             if (ctx->precision)
                 ++ctx->launches, k_p2p_net<float><<<leaf.nbox * split, P2P_T, 0, st>>>(a);
             else
@@ -665,6 +672,7 @@ LfErr lf_near_field(lfmm_ctx* ctx, cudaStream_t st)
 // the M2L rule; then a check of the interpolated kernels against the
 // quadrature at seeded points.
 // ---------------------------------------------------------------------------
+template <bool GEN>
 __global__ void k_near_tables(const LfmmComp* __restrict__ comps, int ncomp, int Q, const double* __restrict__ gt,
                               const double* __restrict__ gw, double* __restrict__ tab)
 {
@@ -677,7 +685,7 @@ __global__ void k_near_tables(const LfmmComp* __restrict__ comps, int ncomp, int
     const LfmmComp cp = comps[c];
     double out[3] = {0.0, 0.0, 0.0};
     if (!cp.is_free && cp.has_rem)
-        lf_nt_point(cp, is * (LF_NT_SMAX / (LF_NT_NS - 1)), iw * (1.0 / (LF_NT_NW - 1)), Q, gt, gw, out);
+        lf_nt_point<GEN>(cp, is * (LF_NT_SMAX / (LF_NT_NS - 1)), iw * (1.0 / (LF_NT_NW - 1)), Q, gt, gw, out);
     double* t = tab + (size_t)c * LF_NT_PER + r;
     t[0] = out[0];
     t[per] = out[1];
@@ -686,6 +694,7 @@ __global__ void k_near_tables(const LfmmComp* __restrict__ comps, int ncomp, int
 
 // err[i]: largest deviation of the three interpolated kernels from the
 // quadrature, relative to |I_00| (field kernels times the distance R)
+template <bool GEN>
 __global__ void k_near_tables_check(const LfmmComp* __restrict__ comps, const int* __restrict__ pc,
                                     const double* __restrict__ prho, const double* __restrict__ ph, int n, int Q,
                                     const double* __restrict__ gt, const double* __restrict__ gw,
@@ -695,8 +704,8 @@ __global__ void k_near_tables_check(const LfmmComp* __restrict__ comps, const in
     if (i >= n) return;
     const LfmmComp& cp = comps[pc[i]];
     double a00, a10, a11, b00, b10, b11;
-    lf_reaction_pair<double>(cp, prho[i], ph[i], Q, gt, gw, a00, a10, a11);
-    lf_reaction_pair<double>(cp, prho[i], ph[i], Q, gt, gw, b00, b10, b11, tab + (size_t)pc[i] * LF_NT_PER);
+    lf_reaction_pair<double, GEN>(cp, prho[i], ph[i], Q, gt, gw, a00, a10, a11);
+    lf_reaction_pair<double, GEN>(cp, prho[i], ph[i], Q, gt, gw, b00, b10, b11, tab + (size_t)pc[i] * LF_NT_PER);
     const double H = ph[i] + cp.zeta;
     const double R = sqrt(prho[i] * prho[i] + H * H);
     const double sc = fabs(a00) > 1e-300 ? 1.0 / fabs(a00) : 0.0;
@@ -710,7 +719,8 @@ LfErr lf_near_tables(lfmm_ctx* ctx, double* max_err)
     if (!ctx->near_tab_ready) {
         LF_TRY(lf_reserve(ctx->near_tab, sizeof(double) * (size_t)LF_NT_PER * nc));
         const int64_t tot = (int64_t)LF_NT_NS * LF_NT_NW * nc;
-        ++ctx->launches, k_near_tables<<<lf_blocks(tot, 128), 128, 0, st>>>(
+        auto kern = (ctx->L >= 3) ? k_near_tables<true> : k_near_tables<false>;
+        ++ctx->launches, kern<<<lf_blocks(tot, 128), 128, 0, st>>>(
             ctx->comp_dev.as<LfmmComp>(), nc, Q, ctx->gl_t_m2l.as<double>(), ctx->gl_w_m2l.as<double>(),
             ctx->near_tab.as<double>());
         LF_TRY(lf_cuda(cudaGetLastError(), "near tables"));
@@ -748,7 +758,8 @@ LfErr lf_near_tables(lfmm_ctx* ctx, double* max_err)
         if (e.empty()) e = lf_cuda(cudaMemcpyAsync(drho.ptr, prho.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st), "copy");
         if (e.empty()) e = lf_cuda(cudaMemcpyAsync(dh.ptr, ph.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st), "copy");
         if (e.empty()) {
-            ++ctx->launches, k_near_tables_check<<<lf_blocks(n, 128), 128, 0, st>>>(
+            auto kern = (ctx->L >= 3) ? k_near_tables_check<true> : k_near_tables_check<false>;
+            ++ctx->launches, kern<<<lf_blocks(n, 128), 128, 0, st>>>(
                 ctx->comp_dev.as<LfmmComp>(), dpc.as<int>(), drho.as<double>(), dh.as<double>(), n, Q,
                 ctx->gl_t_m2l.as<double>(), ctx->gl_w_m2l.as<double>(), ctx->near_tab.as<double>(),
                 derr.as<double>());
@@ -771,6 +782,7 @@ LfErr lf_near_tables(lfmm_ctx* ctx, double* max_err)
 // ---------------------------------------------------------------------------
 // Parity entry points: the same device routines on caller-given geometries.
 // ---------------------------------------------------------------------------
+template <bool GEN>
 __global__ void k_som_tables(LfmmComp c, int npts, const double* __restrict__ rho, const double* __restrict__ z,
                              double S, int P, const double* __restrict__ gt, const double* __restrict__ gw, int Q,
                              double* __restrict__ out)
@@ -783,7 +795,7 @@ __global__ void k_som_tables(LfmmComp c, int npts, const double* __restrict__ rh
     const int i = blockIdx.x;
     for (int j = threadIdx.x; j < TT; j += blockDim.x) sT[j] = 0.0;
     __syncthreads();
-    lf_sommerfeld_table_block(c, rho[i] / S, z[i] / S, S, 2 * P, sT, TS, Q, gt, gw, sJ, sA);
+    lf_sommerfeld_table_block<GEN>(c, rho[i] / S, z[i] / S, S, 2 * P, sT, TS, Q, gt, gw, sJ, sA);
     for (int j = threadIdx.x; j < TT; j += blockDim.x) out[(size_t)i * TT + j] = sT[j];
 }
 
@@ -793,12 +805,14 @@ LfErr lf_sommerfeld_tables_dev(lfmm_ctx* ctx, int comp, int npts, const double* 
     const int TS = 2 * P + 1;
     const int Q = ctx->gl_q_m2l;
     size_t sm = sizeof(double) * ((size_t)TS * TS + 2 * (size_t)Q * TS);
-    LF_CHECK(cudaFuncSetAttribute(k_som_tables, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    ++ctx->launches, k_som_tables<<<npts, 128, sm, ctx->s_main>>>(ctx->comp[comp], npts, rho, z, S, P, ctx->gl_t_m2l.as<double>(),
+    auto kern = (ctx->L >= 3) ? k_som_tables<true> : k_som_tables<false>;
+    LF_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    ++ctx->launches, kern<<<npts, 128, sm, ctx->s_main>>>(ctx->comp[comp], npts, rho, z, S, P, ctx->gl_t_m2l.as<double>(),
                                                   ctx->gl_w_m2l.as<double>(), Q, out);
     return lf_cuda(cudaGetLastError(), "sommerfeld tables");
 }
 
+template <bool GEN>
 __global__ void k_reaction_kernel(const LfmmComp* __restrict__ comps, const double* __restrict__ gl_t,
                                   const double* __restrict__ gl_w, int comp, int npts, const double* __restrict__ rho,
                                   const double* __restrict__ h, int Q, double* __restrict__ out)
@@ -806,7 +820,7 @@ __global__ void k_reaction_kernel(const LfmmComp* __restrict__ comps, const doub
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= npts) return;
     double k00, k10, k11;
-    lf_reaction_pair<double>(comps[comp], rho[i], h[i], Q, gl_t, gl_w, k00, k10, k11);
+    lf_reaction_pair<double, GEN>(comps[comp], rho[i], h[i], Q, gl_t, gl_w, k00, k10, k11);
     out[3 * (size_t)i] = k00;
     out[3 * (size_t)i + 1] = k10;
     out[3 * (size_t)i + 2] = k11;
@@ -814,7 +828,8 @@ __global__ void k_reaction_kernel(const LfmmComp* __restrict__ comps, const doub
 
 LfErr lf_reaction_kernel_dev(lfmm_ctx* ctx, int comp, int npts, const double* rho, const double* h, double* out)
 {
-    ++ctx->launches, k_reaction_kernel<<<lf_blocks(npts, 128), 128, 0, ctx->s_main>>>(
+    auto kern = (ctx->L >= 3) ? k_reaction_kernel<true> : k_reaction_kernel<false>;
+    ++ctx->launches, kern<<<lf_blocks(npts, 128), 128, 0, ctx->s_main>>>(
         ctx->comp_dev.as<LfmmComp>(), ctx->gl_t_near.as<double>(), ctx->gl_w_near.as<double>(), comp, npts, rho, h,
         ctx->gl_q_near, out);
     return lf_cuda(cudaGetLastError(), "reaction kernel");
@@ -904,7 +919,8 @@ extern "C" lfmm_status lfmm_reaction_kernel_noalloc(lfmm_ctx* ctx, int l, int lp
     if (e.empty()) e = lf_cuda(cudaMemcpyAsync(drho, rho, sizeof(double) * npts, cudaMemcpyHostToDevice, st), "copy");
     if (e.empty()) e = lf_cuda(cudaMemcpyAsync(dh, h, sizeof(double) * npts, cudaMemcpyHostToDevice, st), "copy");
     if (e.empty()) {
-        ++ctx->launches, k_reaction_kernel<<<lf_blocks(npts, 128), 128, 0, st>>>(
+        auto kern = (ctx->L >= 3) ? k_reaction_kernel<true> : k_reaction_kernel<false>;
+        ++ctx->launches, kern<<<lf_blocks(npts, 128), 128, 0, st>>>(
             ctx->comp_dev.as<LfmmComp>(), ctx->gl_t_near.as<double>(), ctx->gl_w_near.as<double>(), c, npts, drho, dh,
             ctx->gl_q_near, dout);
         e = lf_cuda(cudaGetLastError(), "reaction kernel");

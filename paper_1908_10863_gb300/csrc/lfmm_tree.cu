@@ -256,10 +256,10 @@ __global__ void k_bounds(const double* __restrict__ xyz, int64_t n, double* __re
 
 struct KeyParams {
     int L;
-    double d[2];
+    double d[LFMM_MAXL];
     double org[3];
     double hfine;
-    int iz_lo[3], iz_hi[3];
+    int iz_lo[LFMM_MAXL + 1], iz_hi[LFMM_MAXL + 1];
 };
 
 __global__ void k_make_keys(const double* __restrict__ xyz, const int32_t* __restrict__ layer, int64_t n,
@@ -640,9 +640,28 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
     ext = std::max(ext, 1e-12) * (1.0 + 1e-9) + 1e-300;
 
     // ---- grid: interfaces are planes of every level >= the alignment level ----
+    // With two or more interfaces whose distances from d0 are multiples of a
+    // common unit u (at most 8 units per inner layer), u is the alignment unit;
+    // other media get a grid whose cells may straddle an interface (the layer
+    // id in the box key keeps the layers apart, and reaction pairs of such
+    // boxes fail the side test of the lists and stay in the near field).
     double H, oz;
-    if (ctx->L == 2) {
-        double D = ctx->d[0] - ctx->d[1];
+    double unit = 0.0;
+    if (ctx->L >= 2) {
+        double dmin = INFINITY;
+        for (int j = 1; j < ctx->L; ++j) dmin = std::min(dmin, ctx->d[j - 1] - ctx->d[j]);
+        for (int m = 1; m <= 8 && unit == 0.0; ++m) {
+            const double u = dmin / m;
+            bool ok = true;
+            for (int j = 1; j < ctx->L; ++j) {
+                const double r = (ctx->d[0] - ctx->d[j]) / u;
+                if (fabs(r - std::round(r)) > 1e-9 * r || r > 8.0 * m * ctx->L) ok = false;
+            }
+            if (ok) unit = u;
+        }
+    }
+    if (unit > 0.0) {
+        const double D = unit;
         H = D;
         for (;;) {
             // origin: a multiple of D below d0 such that [oz, oz + H] covers [lo, hi]
@@ -683,17 +702,24 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
 
     KeyParams kp;
     kp.L = ctx->L;
-    kp.d[0] = ctx->d[0];
-    kp.d[1] = ctx->d[1];
+    for (int j = 0; j < LFMM_MAXL; ++j) kp.d[j] = (j < ctx->L) ? ctx->d[j] : 0.0;
     for (int k = 0; k < 3; ++k) kp.org[k] = ctx->origin[k];
     kp.hfine = H / (double)(1 << LFMM_FINE_LEVEL);
     const int top = (1 << LFMM_FINE_LEVEL) - 1;
-    for (int l = 0; l < 3; ++l) {
+    // fine cells a layer's points may take: interfaces on cell planes (L == 1 or
+    // an alignment unit) bound them exactly; otherwise the straddling cells count
+    const bool planes = ctx->L == 1 || unit > 0.0;
+    for (int l = 0; l <= LFMM_MAXL; ++l) {
         kp.iz_lo[l] = 0;
         kp.iz_hi[l] = top;
         if (l <= ctx->L) {
-            if (l < ctx->L) kp.iz_lo[l] = std::max(0, (int)std::llround((ctx->d[l] - oz) / kp.hfine));
-            if (l > 0) kp.iz_hi[l] = std::min(top, (int)std::llround((ctx->d[l - 1] - oz) / kp.hfine) - 1);
+            if (planes) {
+                if (l < ctx->L) kp.iz_lo[l] = std::max(0, (int)std::llround((ctx->d[l] - oz) / kp.hfine));
+                if (l > 0) kp.iz_hi[l] = std::min(top, (int)std::llround((ctx->d[l - 1] - oz) / kp.hfine) - 1);
+            } else {
+                if (l < ctx->L) kp.iz_lo[l] = std::max(0, std::min(top, (int)std::floor((ctx->d[l] - oz) / kp.hfine)));
+                if (l > 0) kp.iz_hi[l] = std::max(0, std::min(top, (int)std::floor((ctx->d[l - 1] - oz) / kp.hfine)));
+            }
             if (kp.iz_hi[l] < kp.iz_lo[l]) kp.iz_hi[l] = kp.iz_lo[l];
         }
     }
@@ -867,9 +893,10 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
         std::vector<uint32_t> rk(r.nbox);
         LF_CHECK(cudaMemcpyAsync(rk.data(), bkey + r.off, 4 * r.nbox, cudaMemcpyDeviceToHost, st));
         LF_CHECK(cudaStreamSynchronize(st));
-        int root_of[3] = {-1, -1, -1};
+        int root_of[LFMM_MAXL + 1];
+        for (int l = 0; l <= LFMM_MAXL; ++l) root_of[l] = -1;
         for (int i = 0; i < r.nbox; ++i) root_of[rk[i]] = r.off + i;
-        for (int l = 0; l < 3; ++l) ctx->nlayer_used[l] = root_of[l] >= 0;
+        for (int l = 0; l <= LFMM_MAXL; ++l) ctx->nlayer_used[l] = root_of[l] >= 0;
         // host staging owned by the context: the copies need no synchronisation
         std::vector<uint32_t>& ent = ctx->root_ent_h;
         std::vector<int>& hb = ctx->root_beg_h;

@@ -126,6 +126,27 @@ def uneven_problems(k: int = 48, nmin: int = 2000, nmax: int = 100000, seed: int
     return [config2(int(n), seed=int(sd), eps=eps) for n, sd in zip(sizes, seeds)]
 
 
+D_FOUR = (0.0, -0.6, -1.2)          # inner layers of equal thickness: interfaces are grid planes
+D_FOUR_UNALIGNED = (0.0, -0.55, -1.2371)  # gaps with no common unit: cells straddle interfaces
+EPS_FOUR = (2.0, 7.0, 1.5, 12.0)
+
+
+def four_layers(n: int = 4000, seed: int | None = None, d=D_FOUR, eps=EPS_FOUR, margin: float = 0.05) -> Workload:
+    """Four layers, N split equally: a unit-thick slab above d0, the two inner
+    layers (each kept `margin` from its interfaces) and a unit-thick slab
+    below the last interface, x, y in [-0.5, 0.5], q ~ U[-1, 1]."""
+    rng = np.random.Generator(np.random.PCG64(SEED_BASE + 8 if seed is None else seed))
+    d = tuple(float(v) for v in d)
+    spans = [(d[0] + 0.1, d[0] + 1.1), (d[1] + margin, d[0] - margin), (d[2] + margin, d[1] - margin),
+             (d[2] - 1.1, d[2] - 0.1)]
+    sizes = [n // 4] * 3 + [n - 3 * (n // 4)]
+    parts = [(_box(rng, cnt, lo, hi), l) for l, (cnt, (lo, hi)) in enumerate(zip(sizes, spans))]
+    xyz = np.concatenate([p for p, _ in parts])
+    layer = np.concatenate([np.full(p.shape[0], l, dtype=np.int32) for p, l in parts])
+    q = rng.uniform(-1.0, 1.0, size=n)
+    return Workload("four_layers_n%d" % n, np.array(d), np.array(eps, dtype=np.float64), xyz, layer, q)
+
+
 def subsample(n: int, count: int, seed: int = SEED_BASE + 3) -> np.ndarray:
     """The first ``count`` indices of a seeded permutation of range(n)."""
     rng = np.random.Generator(np.random.PCG64(seed))
