@@ -82,6 +82,7 @@ def parse():
     ap.add_argument("--no-near", action="store_true", help="skip the near-interface workload")
     ap.add_argument("--no-multi", action="store_true", help="skip the many-charge-vector workload")
     ap.add_argument("--no-batch", action="store_true", help="skip the many-problem workload")
+    ap.add_argument("--no-four", action="store_true", help="skip the four-layer workload")
     ap.add_argument("--acc-targets", default="200,60",
                     help="oracle targets of the two N = 1M cases of --accuracy-table")
     ap.add_argument("--accuracy-table", action="store_true",
@@ -261,6 +262,48 @@ def near_interface_leg(torch, dev, p, flush):
                                                         out[pname + "_" + kind]["p2p_ms"])
         out[pname + "_tables"]["table_max_rel_err"] = table_err
         f.close()
+    return out
+
+
+def four_layer_leg(torch, dev, p, flush, n=1 << 20, targets=48):
+    """Media of four layers at N = 1M: interfaces (0, -0.6, -1.2), both forms
+    timed on eps = (2, 7, 1.5, 12); accuracy on eps = (1, 5, 5, 10), whose
+    middle interface separates equal permittivities, against the exact
+    three-layer image series (the oracle's quadrature is too slow at 1M)."""
+    from paper_1908_10863_gb300 import LayeredFMM, workloads
+    import oracle
+    out = {"workload": "four-layer medium d=(0,-0.6,-1.2), N=%d charges split equally between layers, q~U[-1,1], "
+                       "p=%d, leaf 40" % (n, p)}
+    for eps, tag in ((workloads.EPS_FOUR, "timed"), ((1.0, 5.0, 5.0, 10.0), "merged")):
+        w = workloads.four_layers(n, eps=eps)
+        xyz_d = torch.from_numpy(w.xyz).to(dev)
+        lay_d = torch.from_numpy(w.layer).to(dev)
+        q_d = torch.from_numpy(w.q).to(dev)
+        phi_d = torch.empty(w.n, dtype=torch.float64, device=dev)
+        fld_d = torch.empty((w.n, 3), dtype=torch.float64, device=dev)
+        for prec, pname in ((1, "fp32"), (0, "fp64")):
+            if tag == "merged" and prec == 0:
+                continue
+            f = LayeredFMM(w.d, w.eps, p, precision=prec)
+            steps = 3 if prec else 2
+            times, launches, stages = run_form(f, xyz_d, lay_d, q_d, phi_d, fld_d, torch, steps, 1, flush)
+            st = f.stats()
+            f.close()
+            ms = sum(times) / len(times)
+            if tag == "timed":
+                out[pname] = {"ms_per_step": ms, "particles_per_s": w.n / (ms / 1e3),
+                              "stage_ms": stages, "components": st["components"],
+                              "m2l_reaction": st["m2l_reaction"], "p2p_reaction": st["p2p_reaction"],
+                              "reaction_tables": st["reaction_tables"]}
+            else:
+                t = workloads.subsample(w.n, targets)
+                lay3 = np.where(w.layer >= 2, w.layer - 1, w.layer).astype(np.int32)
+                ref, refE = oracle.direct([0.0, -1.2], [1.0, 5.0, 10.0], w.xyz, lay3, w.q, targets=t,
+                                          mode=oracle.MODE_IMAGES)
+                phi = phi_d.cpu().numpy()
+                fld = fld_d.cpu().numpy()
+                out["merged_fp32"] = {"ms_per_step": ms, "err2_phi": oracle.err2(ref, phi[t]),
+                                      "err2_field": oracle.err2(refE, fld[t]), "targets": int(len(t))}
     return out
 
 
@@ -501,6 +544,12 @@ def main():
     many = None
     if not args.no_batch and rank == 0:
         many = many_problems_leg(torch, dev, args.p, flush)
+    four = None
+    if not args.no_four and rank == 0:
+        try:
+            four = four_layer_leg(torch, dev, args.p, flush)
+        except Exception as exc:  # a secondary workload never voids the headline line
+            four = {"error": "%s: %s" % (type(exc).__name__, exc)}
 
     ms_max = allmax(pg, results[headline]["ms_per_step"])
     e2e_max = allmax(pg, results[headline]["e2e_s"])
@@ -574,6 +623,7 @@ def main():
         "near_interface": near,
         "multi_rhs": multi,
         "many_problems": many,
+        "four_layers": four,
     }
     print(json.dumps(line))
     barrier(pg)

@@ -607,7 +607,10 @@ LfErr lf_near_field(lfmm_ctx* ctx, cudaStream_t st)
     // Few leaves (small problems) leave most SMs idle with one warp or block
     // per leaf: share each near list between `split` of them.  A set value
     // (ctx->p2p_split, e.g. from the tuner) wins over this occupancy rule.
-    const bool general = ctx->L >= 3;
+    // media of four layers need the solved densities only for reaction pairs
+    // of the near lists (counted at every build); without any, the kernels of
+    // thinner media compute the free-space pairs alone and are exact
+    const bool general = ctx->L >= 3 && ctx->stats[LFMM_STAT_P2P_REACTION] > 0;
     const bool warp_kernel = !net && !general && ctx->precision;
     int split = ctx->p2p_split;
     if (split <= 0) {

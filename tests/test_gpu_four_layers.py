@@ -131,3 +131,21 @@ def test_high_order_converges():
     e_phi = oracle.err2(ref, phi[t])
     print("four layers p=16: Err2 phi %.2e field %.2e" % (e_phi, oracle.err2(refE, E[t])))
     assert e_phi < 5e-8 and oracle.err2(refE, E[t]) < 5e-7
+
+
+def test_large_problem_without_near_reaction_pairs():
+    # at N = 1M the leaves are small enough that no polarization image comes
+    # near a target: the near field is free space only and runs the float32
+    # warp kernel; the far field carries every reaction pair
+    w = workloads.four_layers(1 << 20, eps=(1.0, 5.0, 5.0, 10.0))
+    with LayeredFMM(w.d, w.eps, 10, precision=1) as f:
+        f.build(w.xyz, w.layer)
+        st = f.stats()
+        phi, E = f.evaluate(w.q)
+    assert st["p2p_reaction"] == 0 and st["m2l_reaction"] > 0
+    t = workloads.subsample(w.n, 32)
+    lay3 = np.where(w.layer >= 2, w.layer - 1, w.layer).astype(np.int32)
+    ref, refE = oracle.direct([0.0, -1.2], [1.0, 5.0, 10.0], w.xyz, lay3, w.q, targets=t, mode=oracle.MODE_IMAGES)
+    e_phi, e_fld = oracle.err2(ref, phi[t]), oracle.err2(refE, E[t])
+    print("four layers N=1M float32: Err2 phi %.2e field %.2e" % (e_phi, e_fld))
+    assert e_phi < 1e-5 and e_fld < 1e-4
