@@ -474,7 +474,9 @@ static void reaction_images(const double* d, const double* eps, int l, int lp, c
                     g[3] -= c3 * H * dh;
                 }
                 gq *= -qq;
-                if (fabs(gq) * nmax / (1.0 - fabs(qq)) < 1e-18 * nmax) break;
+                /* geometric tail below 1e-18 of the largest numerator; a
+                 * density that vanishes (equal permittivities) has no terms */
+                if (nmax == 0.0 || fabs(gq) / (1.0 - fabs(qq)) < 1e-18) break;
             }
         }
 }
