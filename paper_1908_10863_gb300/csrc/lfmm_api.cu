@@ -8,7 +8,11 @@
 // x = 0, 1/2, 1 and fits numerator and denominator (both of degree <= 2) to
 // obtain, per component, sigma = num(x)/den(x), its leading behaviour
 // C exp(-k zeta) (the lowest power of x) and the remainder
-// sigma - C exp(-k zeta) = exp(-k zeta_r) rem(x)/den(x).
+// sigma - C exp(-k zeta) = exp(-k zeta_r) rem(x)/den(x).  Four layers have
+// two inner thicknesses and no single x: there the leading term comes from
+// the direct path between the source's and the target's interfaces
+// (setup_general_density) and the devices solve the interface problem at
+// each quadrature node (lf_sigma_solve, lf_sigma_rem in lfmm_internal.cuh).
 #include <cuda_runtime.h>
 #include <math.h>
 

@@ -2,11 +2,14 @@
 //
 // Algorithm 1 of the paper starts by forming the polarization coordinates and
 // an adaptive tree.  Here every layer's charges live in one global uniform
-// grid whose planes contain the interfaces (so no box of an aligned level
+// grid whose planes contain the interfaces whenever their distances share a
+// unit (always for up to three layers), so no box of an aligned level
 // straddles an interface, which is the centre condition of eq.
-// imagecentercond).  Polarization boxes are the source boxes mapped by
-// z'' = s z + o (eq. eqpolarizedsource); their multipoles are the physical
-// ones up to the sign (-1)^{n+m} of a reflection.  Lists come from a dual
+// imagecentercond.  Otherwise a box (of one layer: the layer id is part of
+// its key) may straddle an interface; the list test below still requires the
+// target and image box centres on their own sides.  Polarization boxes are
+// the source boxes mapped by z'' = s z + o (eq. eqpolarizedsource); their
+// multipoles are the physical ones up to the sign (-1)^{n+m} of a reflection.  Lists come from a dual
 // traversal per level: the candidates of a target box are the children of
 // its parent's near list; an admissible candidate (one box of separation,
 // sides of the interface respected for reaction components) becomes an M2L
