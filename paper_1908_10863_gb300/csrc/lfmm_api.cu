@@ -367,8 +367,12 @@ static LfErr setup_general_density(const lfmm_ctx* ctx, LfmmComp& c)
     c.zeta_r = c.zeta + 2.0 * dmin;
     c.has_rem = 1;
     c.D = dmin;
-    // coupling steps of the remainder series: D_min (N + 1) >= zeta_r, plus one
-    c.nterm = std::min(60, (int)std::ceil(c.zeta_r / dmin) + 1);
+    // coupling steps of the remainder series: D_min (N + 1) >= zeta_r, plus
+    // one.  Fewer would let the tail's rounding grow like e^{k zeta_r} at the
+    // large nodes, so a medium needing more than the limit is refused.
+    const double nsteps = std::ceil(c.zeta_r / dmin) + 1.0;
+    if (!(nsteps <= 1024.0)) return "EINVAL: an inner layer is too thin against the layers it sits between";
+    c.nterm = (int)nsteps;
     const double k1 = std::min(30.0 / dmin, 600.0 / std::max(c.zeta, 1e-300));
     const double lead = lf_sigma_solve(c, k1) * exp(k1 * c.zeta);
     if (!(fabs(lead - C) <= 1e-8 * (1.0 + fabs(C)))) return "EINVAL: interface problem of the medium is singular";
