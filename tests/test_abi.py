@@ -66,3 +66,38 @@ def test_batch_create_rejects_bad_arguments_without_a_device():
     assert not h.value
     lib.lfmm_batch_destroy(None)
     assert lib.lfmm_batch_last_error(None) == b"null batch"
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include "lfmm.h"
+/* the boundary from plain C: the header is C11, every call takes plain
+ * pointers and sizes; only the host-only helper runs without a device */
+int main(void) {
+    double t[32], w[32];
+    if (lfmm_gauss_laguerre(32, t, w) != LFMM_OK) return 2;
+    if (lfmm_gauss_laguerre(0, t, w) != LFMM_EINVAL) return 3;
+    double m0 = 0.0, m1 = 0.0;
+    for (int i = 0; i < 32; ++i) { m0 += w[i]; m1 += w[i] * t[i]; }
+    printf("%.17g %.17g\n", m0, m1);   /* int e^{-t} = 1, int t e^{-t} = 1 */
+    lfmm_destroy(NULL);                /* NULL-safe */
+    return 0;
+}
+"""
+
+
+def test_header_is_plain_c_and_links(tmp_path):
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    lib = os.path.realpath(binding.library_path())
+    src = tmp_path / "abi.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "abi"
+    subprocess.run([gcc, "-std=c11", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+                    str(src), "-L", os.path.dirname(lib), "-llfmm", "-Wl,-rpath," + os.path.dirname(lib),
+                    "-o", str(exe)], check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    assert abs(float(out[0]) - 1.0) < 1e-13 and abs(float(out[1]) - 1.0) < 1e-13
