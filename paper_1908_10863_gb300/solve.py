@@ -158,3 +158,33 @@ def plate_panels(center, size, nside: int, layer: int):
     X, Y = np.meshgrid(u, u, indexing="ij")
     xyz = np.column_stack([X.ravel() + center[0], Y.ravel() + center[1], np.full(nside * nside, center[2])])
     return xyz, np.full(nside * nside, h / math.sqrt(math.pi)), np.full(nside * nside, layer, dtype=np.int32)
+
+
+class TargetSet:
+    """Potential and field at points that carry no charge (targets separate
+    from the sources, as an integral-equation or post-processing step needs).
+    The targets join the tree as zero charges: the FMM's sum at a charge is
+    the layered-Green's-function sum over every other charge, and a zero
+    charge adds nothing to anyone else's.  A target placed exactly on a
+    source skips that source's singular free-space term, as the charges'
+    own self terms are skipped.
+
+    ``evaluate(q)`` takes the source charges ([n] or [nrhs, n]) and returns
+    (phi, E) at the targets ([nt] / [nrhs, nt] and [..., nt, 3]).
+    """
+
+    def __init__(self, fmm, xyz, layer, target_xyz, target_layer):
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+        txyz = np.ascontiguousarray(target_xyz, dtype=np.float64).reshape(-1, 3)
+        self.n, self.nt = int(xyz.shape[0]), int(txyz.shape[0])
+        self.fmm = fmm
+        fmm.build(np.concatenate([xyz, txyz]),
+                  np.concatenate([np.asarray(layer, dtype=np.int32), np.asarray(target_layer, dtype=np.int32)]))
+
+    def evaluate(self, q, field: bool = True):
+        q = np.asarray(q, dtype=np.float64)
+        if q.shape[-1] != self.n:
+            raise ValueError("expected %d source charges, got %d" % (self.n, q.shape[-1]))
+        pad = np.zeros(q.shape[:-1] + (self.nt,))
+        phi, E = self.fmm.evaluate(np.ascontiguousarray(np.concatenate([q, pad], axis=-1)), field=field)
+        return phi[..., self.n:], (E[..., self.n:, :] if field else None)

@@ -22,6 +22,10 @@ class OracleSum:
         self.xyz, self.layer = np.asarray(xyz), np.asarray(layer, dtype=np.int32)
 
     def evaluate(self, q, field=True):
+        q = np.asarray(q)
+        if q.ndim == 2:  # several charge vectors, like the FMM's [nrhs, n]
+            res = [self.evaluate(row, field) for row in q]
+            return np.stack([r[0] for r in res]), (np.stack([r[1] for r in res]) if field else None)
         phi, E = oracle.direct(self.d, self.eps, self.xyz, self.layer, q, mode=self.mode)
         return phi, (E if field else None)
 
@@ -102,3 +106,35 @@ def test_capacitance_scales_with_permittivity():
     C1, _ = capacitance(PanelSystem(OracleSum(D3, [1.0] * 3), [1.0] * 3, xyz, lay, rad), cond, tol=1e-12)
     C3, _ = capacitance(PanelSystem(OracleSum(D3, [3.0] * 3), [3.0] * 3, xyz, lay, rad), cond, tol=1e-12)
     assert np.allclose(C3, 3.0 * C1, rtol=1e-9, atol=0)
+
+
+def test_separate_targets_match_pair_sums():
+    # potential and field at charge-free points, against the oracle's reaction
+    # kernel summed pair by pair (plus the Coulomb term for sources in the
+    # target's layer): independent of the zero-charge construction
+    from paper_1908_10863_gb300.solve import TargetSet
+    eps = [1.0, 5.0, 10.0]
+    rng = np.random.default_rng(21)
+    zr = {0: (0.1, 1.1), 1: (-1.1, -0.1), 2: (-2.3, -1.3)}
+    n, nt = 40, 7
+    lay = rng.integers(0, 3, n).astype(np.int32)
+    xyz = np.array([[*rng.uniform(-0.5, 0.5, 2), rng.uniform(*zr[int(l)])] for l in lay])
+    tl = rng.integers(0, 3, nt).astype(np.int32)
+    txyz = np.array([[*rng.uniform(-0.5, 0.5, 2), rng.uniform(*zr[int(l)])] for l in tl])
+    q = rng.uniform(-1.0, 1.0, n)
+    ts = TargetSet(OracleSum(D3, eps), xyz, lay, txyz, tl)
+    phi, E = ts.evaluate(q)
+    ref_phi, ref_E = np.zeros(nt), np.zeros((nt, 3))
+    for i in range(nt):
+        for j in range(n):
+            u, g = oracle.reaction_pair(D3, eps, int(tl[i]), int(lay[j]), txyz[i], xyz[j], mode=oracle.MODE_IMAGES)
+            if tl[i] == lay[j]:
+                R = txyz[i] - xyz[j]
+                u += 1.0 / np.linalg.norm(R)
+                g = g - R / np.linalg.norm(R) ** 3
+            ref_phi[i] += q[j] * u / (4 * np.pi)
+            ref_E[i] -= q[j] * g / (4 * np.pi)
+    assert np.max(np.abs(phi - ref_phi)) < 1e-12 * np.max(np.abs(ref_phi))
+    assert np.max(np.abs(E - ref_E)) < 1e-11 * np.max(np.abs(ref_E))
+    phi2, _ = ts.evaluate(np.stack([q, 2.0 * q]))  # several charge vectors at once
+    assert phi2.shape == (2, nt) and np.allclose(phi2[1], 2.0 * phi, rtol=1e-13, atol=0)
