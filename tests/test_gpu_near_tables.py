@@ -2,7 +2,6 @@
 kernels: their interpolation error against the quadrature, the FMM with them
 against the FMM with the quadrature and against the oracle, and what they
 gain in the near field."""
-import numpy as np
 import pytest
 
 import oracle

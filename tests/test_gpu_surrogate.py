@@ -16,7 +16,7 @@ import pytest
 import oracle
 from oracle import mlp
 from paper_1908_10863_gb300 import LayeredFMM, LfmmError, workloads
-from paper_1908_10863_gb300.lfmm import OPT_PROFILE, OPT_SURROGATE, OPT_SURROGATE_TOL
+from paper_1908_10863_gb300.lfmm import OPT_PROFILE, OPT_SURROGATE
 
 pytestmark = pytest.mark.gpu
 D3 = [0.0, -1.2]
