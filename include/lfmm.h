@@ -358,6 +358,24 @@ lfmm_status lfmm_reaction_kernel_noalloc(lfmm_ctx* ctx, int l, int lp, int a, in
  * order Q (weight e^{-t} on [0, inf)) as used by the quadratures. */
 lfmm_status lfmm_gauss_laguerre(int Q, double* nodes, double* weights);
 
+/* Host-only helper (no device needed): the components a context for this
+ * medium would evaluate (Section 3.3, eqs. generalcomponents, zexponential,
+ * eqpolarizedsource), the free-space ones first.
+ *   d, L, eps : as for lfmm_create (EINVAL under the same conditions).
+ *   out       : host, max_rows x LFMM_MEDIUM_COLS doubles, row-major, or NULL;
+ *               per component (l, lp, a, b, is_free, s, o, iface, C, zeta,
+ *               zeta_r): target layer l, source layer lp, the polarization
+ *               map z'' = s z' + o, the interface between targets and
+ *               polarization sources, the density's leading term
+ *               C exp(-k zeta), and the decay rate zeta_r of the remainder
+ *               sigma - C exp(-k zeta) (-1 where there is none).  a = b = 0
+ *               for free-space components.
+ *   nrows     : receives the rows written (out given) or the component count.
+ * The caller owns out. */
+#define LFMM_MEDIUM_COLS 11
+lfmm_status lfmm_medium_components(const double* d, int L, const double* eps, double* out, int max_rows,
+                                   int* nrows);
+
 #ifdef __cplusplus
 }
 #endif

@@ -638,17 +638,50 @@ lfmm_status lfmm_gauss_laguerre(int Q, double* nodes, double* weights)
     return gauss_laguerre(Q, nodes, weights) ? LFMM_EINVAL : LFMM_OK;
 }
 
+// interfaces finite and strictly decreasing, permittivities finite and positive
+static bool medium_ok(const double* d, int L, const double* eps)
+{
+    if (L < 0 || L > LFMM_MAXL || !eps || (L > 0 && !d)) return false;
+    for (int l = 0; l <= L; ++l)
+        if (!(eps[l] > 0.0) || !std::isfinite(eps[l])) return false;
+    for (int l = 0; l < L; ++l)
+        if (!std::isfinite(d[l])) return false;
+    for (int l = 1; l < L; ++l)
+        if (!(d[l - 1] > d[l])) return false;
+    return true;
+}
+
+lfmm_status lfmm_medium_components(const double* d, int L, const double* eps, double* out, int max_rows, int* nrows)
+{
+    if (nrows) *nrows = 0;
+    if (!medium_ok(d, L, eps) || (out && max_rows < 0)) return LFMM_EINVAL;
+    lfmm_ctx* ctx = new (std::nothrow) lfmm_ctx();
+    if (!ctx) return LFMM_ENOMEM;
+    ctx->L = L;
+    for (int l = 0; l < L; ++l) ctx->d[l] = d[l];
+    for (int l = 0; l <= L; ++l) ctx->eps[l] = eps[l];
+    const lfmm_status st = status_of(setup_components(ctx));  // host only
+    if (st == LFMM_OK) {
+        const int nc = ctx->ncomp;
+        const int w = out ? std::min(nc, max_rows) : 0;
+        for (int c = 0; c < w; ++c) {
+            const LfmmComp& cp = ctx->comp[c];
+            const double row[LFMM_MEDIUM_COLS] = {(double)cp.l, (double)cp.lp, (double)cp.a, (double)cp.b,
+                                                  (double)cp.is_free, cp.s, cp.o, cp.iface, cp.C, cp.zeta,
+                                                  cp.has_rem ? cp.zeta_r : -1.0};
+            std::copy(row, row + LFMM_MEDIUM_COLS, out + (size_t)c * LFMM_MEDIUM_COLS);
+        }
+        if (nrows) *nrows = out ? w : nc;
+    }
+    delete ctx;
+    return st;
+}
+
 lfmm_status lfmm_create(const double* d, int L, const double* eps, int p, lfmm_ctx** out)
 {
     if (!out) return LFMM_EINVAL;
     *out = nullptr;
-    if (L < 0 || L > LFMM_MAXL || p < 1 || p > LFMM_PMAX || !eps || (L > 0 && !d)) return LFMM_EINVAL;
-    for (int l = 0; l <= L; ++l)
-        if (!(eps[l] > 0.0) || !std::isfinite(eps[l])) return LFMM_EINVAL;
-    for (int l = 0; l < L; ++l)
-        if (!std::isfinite(d[l])) return LFMM_EINVAL;
-    for (int l = 1; l < L; ++l)
-        if (!(d[l - 1] > d[l])) return LFMM_EINVAL;
+    if (!medium_ok(d, L, eps) || p < 1 || p > LFMM_PMAX) return LFMM_EINVAL;
     lfmm_ctx* ctx = new (std::nothrow) lfmm_ctx();
     if (!ctx) return LFMM_ENOMEM;
     ctx->L = L;

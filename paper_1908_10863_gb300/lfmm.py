@@ -48,7 +48,7 @@ EXPORTED = ["lfmm_create", "lfmm_set_option", "lfmm_build", "lfmm_build_device",
             "lfmm_surrogate_set_params", "lfmm_surrogate_forward", "lfmm_surrogate_loss_grad",
             "lfmm_batch_create", "lfmm_batch_offsets", "lfmm_batch_evaluate_device", "lfmm_batch_evaluate",
             "lfmm_batch_info", "lfmm_batch_last_error", "lfmm_batch_destroy", "lfmm_autotune",
-            "lfmm_check_bounded_wait", "lfmm_near_tables"]
+            "lfmm_check_bounded_wait", "lfmm_near_tables", "lfmm_medium_components"]
 BATCH_INFO = ["problems", "charges", "graph_nodes", "kernel_nodes", "captures", "graph_launches", "direct_runs",
               "timeouts"]
 NOALLOC_MAX_POINTS = 65536
@@ -84,6 +84,7 @@ def load(build: bool = True):
     lib.lfmm_reaction_kernel.argtypes = [_ctxp] + [ctypes.c_int] * 5 + [_dp, _dp, _dp]
     lib.lfmm_reaction_kernel_noalloc.argtypes = [_ctxp] + [ctypes.c_int] * 5 + [_dp, _dp, _dp]
     lib.lfmm_gauss_laguerre.argtypes = [ctypes.c_int, _dp, _dp]
+    lib.lfmm_medium_components.argtypes = [_dp, ctypes.c_int, _dp, _dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     _fp = ctypes.POINTER(ctypes.c_float)
     comp = [ctypes.c_int] * 4
     lib.lfmm_surrogate_train.argtypes = [_ctxp, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64]
@@ -129,6 +130,24 @@ def gauss_laguerre(Q: int):
     if st != OK:
         raise LfmmError(st, "lfmm_gauss_laguerre")
     return t, w
+
+
+MEDIUM_COLS = ["l", "lp", "a", "b", "is_free", "s", "o", "iface", "C", "zeta", "zeta_r"]
+
+
+def medium_components(d, eps):
+    """The components a context for this medium evaluates, one dict each
+    (host-only call; see ``lfmm_medium_components``)."""
+    d = _f64(d)
+    eps = _f64(eps)
+    L = int(d.shape[0])
+    out = np.zeros((64, len(MEDIUM_COLS)))
+    n = ctypes.c_int(0)
+    st = load().lfmm_medium_components(_ptr(d) if L else None, L, _ptr(eps), _ptr(out), 64, ctypes.byref(n))
+    if st != OK:
+        raise LfmmError(st, "lfmm_medium_components")
+    ints = {"l", "lp", "a", "b", "is_free"}
+    return [{k: (int(v) if k in ints else float(v)) for k, v in zip(MEDIUM_COLS, r)} for r in out[:n.value]]
 
 
 class LayeredFMM:
