@@ -189,6 +189,13 @@ def oracle_sample(w, count):
     return t, ref, refE, dt, threads
 
 
+def err2_per_layer(ref, got, layers):
+    """Err2 of Section 4 over the sampled targets of each layer, keyed by layer id."""
+    import oracle
+    layers = np.asarray(layers)
+    return {str(int(l)): oracle.err2(ref[layers == l], got[layers == l]) for l in np.unique(layers)}
+
+
 def m2l_flops_per_pair(p):
     # dense M2L: (p+1)^2 source coefficients x (p+1)(p+2)/2 target coefficients, complex MAC = 8 flops
     return 8 * (p + 1) ** 2 * (p + 1) * (p + 2) // 2
@@ -568,6 +575,11 @@ def main():
         forms_out[name] = {"particles_per_s": w.n / (r["ms_per_step"] / 1e3), "ms_per_step": r["ms_per_step"],
                            "err2_phi": e2p, "err2_field": e2E, "stage_ms": r["timings"],
                            "build_stats": {k: v for k, v in r["stats"].items() if k != "launches"}}
+        try:  # per-layer breakdown of the same sample; never voids the line
+            forms_out[name]["err2_phi_per_layer"] = err2_per_layer(ref, r["phi"][t], w.layer[t])
+            forms_out[name]["err2_field_per_layer"] = err2_per_layer(refE, r["E"][t], w.layer[t])
+        except Exception as exc:
+            forms_out[name]["err2_per_layer_error"] = "%s: %s" % (type(exc).__name__, exc)
         if r["surrogate_train_s"] is not None:
             forms_out[name]["surrogate_train_s"] = r["surrogate_train_s"]
     st = results[headline]["stats"]
@@ -610,6 +622,8 @@ def main():
                                                  "learned near-field reaction kernels on (tolerance 1e-6)",
                    "l2": "256 MB buffer written between timed steps (L2 flushed)", "parallelism": "replicas"},
         "err2": {"phi": forms_out[headline]["err2_phi"], "field": forms_out[headline]["err2_field"],
+                 "phi_per_layer": forms_out[headline].get("err2_phi_per_layer"),
+                 "field_per_layer": forms_out[headline].get("err2_field_per_layer"),
                  "targets": int(len(t)), "reference": "CPU oracle (FP64 direct sum, exact image series)"},
         "forms": forms_out,
         "roofline": roof,
