@@ -16,7 +16,11 @@ Functions follow the paper's definitions:
   by adaptive Gauss-Kronrod, or by the exact three-layer image series.
 * :func:`direct` -- Phi and E = -grad Phi at target charges by direct
   summation (eqs. potential1, totalinteraction), 1/(4 pi) included, free-space
-  self term excluded, reaction self term included.
+  self term excluded, reaction self term included.  In quadrature mode the
+  density's k -> infinity limit is integrated in closed form (Lipschitz
+  integral) and only the decaying rest by adaptive quadrature, so charges
+  next to an interface converge.  A quadrature that runs out of panels raises
+  :class:`OracleNotConverged` instead of returning a partial sum.
 * :func:`err2`, :func:`errmax` -- the error norms of Section 4.
 """
 from __future__ import annotations
@@ -35,6 +39,11 @@ _lib = None
 _dp = ctypes.POINTER(ctypes.c_double)
 _i32p = ctypes.POINTER(ctypes.c_int32)
 _i64p = ctypes.POINTER(ctypes.c_int64)
+
+
+class OracleNotConverged(RuntimeError):
+    """An adaptive quadrature ran out of panels before meeting its tolerance;
+    the oracle refuses to return the partial sum."""
 
 
 def build(force: bool = False) -> str:
@@ -106,8 +115,11 @@ def sigma3_closed(d, eps, k: float, l: int, lp: int, a: int, b: int) -> float:
 def sommerfeld_K(d, eps, l, lp, a, b, N, mu, rho, z, sigma_one=False, tol=1e-13) -> float:
     """int_0^inf J_mu(k rho) k^N e^{-kz} sigma^{ab}_{l lp}(k) dk by adaptive quadrature."""
     d = _arr(d); eps = _arr(eps)
-    return _load().oracle_sommerfeld_K(len(d), _ptr(d), _ptr(eps), l, lp, a, b, N, mu, float(rho), float(z),
-                                       1 if sigma_one else 0, float(tol))
+    v = _load().oracle_sommerfeld_K(len(d), _ptr(d), _ptr(eps), l, lp, a, b, N, mu, float(rho), float(z),
+                                    1 if sigma_one else 0, float(tol))
+    if not np.isfinite(v):
+        raise OracleNotConverged("sommerfeld_K: invalid component or the adaptive quadrature did not converge")
+    return v
 
 
 def sommerfeld_K_images(d, eps, l, lp, a, b, N, mu, rho, z) -> float:
@@ -138,6 +150,8 @@ def direct(d, eps, xyz, layer, q, targets=None, mode=MODE_QUAD, tol=1e-12, threa
     field = np.zeros((nt, 3))
     rc = _load().oracle_direct(len(d), _ptr(d), _ptr(eps), n, _ptr(xyz), _ptr(layer, _i32p), _ptr(q), nt,
                                _ptr(targets, _i64p), int(mode), float(tol), _ptr(phi), _ptr(field), int(threads))
+    if rc == -2:
+        raise OracleNotConverged("oracle_direct: an adaptive quadrature ran out of panels before its tolerance")
     if rc:
         raise ValueError("oracle_direct rejected the input")
     return phi, field
@@ -148,8 +162,11 @@ def reaction_pair(d, eps, l, lp, r, rp, mode=MODE_QUAD, tol=1e-13):
     d = _arr(d); eps = _arr(eps)
     r = _arr(r); rp = _arr(rp)
     g = np.zeros(4)
-    if _load().oracle_reaction_pair(len(d), _ptr(d), _ptr(eps), l, lp, _ptr(r), _ptr(rp), int(mode), float(tol),
-                                    _ptr(g)):
+    rc = _load().oracle_reaction_pair(len(d), _ptr(d), _ptr(eps), l, lp, _ptr(r), _ptr(rp), int(mode), float(tol),
+                                      _ptr(g))
+    if rc == -2:
+        raise OracleNotConverged("oracle_reaction_pair: the adaptive quadrature did not converge")
+    if rc:
         raise ValueError("oracle_reaction_pair failed")
     return g[0], g[1:].copy()
 

@@ -242,13 +242,20 @@ static void gk15(vec_integrand fn, const void* ctx, int dim, double a, double b,
 typedef struct { double a, b, K[GK_MAXDIM], E[GK_MAXDIM]; } gk_panel;
 
 /* Globally adaptive: keep bisecting the panel with the largest error until
- * the summed error is below tol * (sum of |panel integrals|) per component. */
-static void gk_adaptive(vec_integrand fn, const void* ctx, int dim, double a, double b, int npanel0, double tol,
-                        double* out)
+ * the summed error is below tol * (sum of |panel integrals|) + floor[c] per
+ * component (floor may be NULL: no absolute part).  Returns 0 when that holds.  When the panel budget runs out first it
+ * returns 1 and writes NaN to every output, so that an unconverged sum can
+ * never pass for a result. */
+static int gk_adaptive(vec_integrand fn, const void* ctx, int dim, double a, double b, int npanel0, double tol,
+                       const double* floor, double* out)
 {
-    enum { MAXP = 6000 };
+    enum { MAXP = 20000 };
     gk_panel* P = (gk_panel*)malloc(sizeof(gk_panel) * MAXP);
-    int np = 0;
+    int np = 0, status = 1;
+    if (!P) {
+        for (int c = 0; c < dim; ++c) out[c] = NAN;
+        return 1;
+    }
     if (npanel0 < 1) npanel0 = 1;
     if (npanel0 > MAXP / 2) npanel0 = MAXP / 2;
     for (int i = 0; i < npanel0; ++i) {
@@ -257,15 +264,20 @@ static void gk_adaptive(vec_integrand fn, const void* ctx, int dim, double a, do
         gk15(fn, ctx, dim, P[np].a, P[np].b, P[np].K, P[np].E);
         ++np;
     }
-    for (int it = 0; it < 100000; ++it) {
+    for (;;) {
         double tot[GK_MAXDIM] = {0}, scale[GK_MAXDIM] = {0}, errs[GK_MAXDIM] = {0};
         for (int i = 0; i < np; ++i)
             for (int c = 0; c < dim; ++c) { tot[c] += P[i].K[c]; scale[c] += fabs(P[i].K[c]); errs[c] += P[i].E[c]; }
         int done = 1;
         for (int c = 0; c < dim; ++c)
-            if (errs[c] > tol * scale[c] + 1e-300) done = 0;
-        if (done || np >= MAXP - 1) {
+            if (!(errs[c] <= tol * scale[c] + (floor ? floor[c] : 0.0) + 1e-300)) done = 0;
+        if (done) {
             for (int c = 0; c < dim; ++c) out[c] = tot[c];
+            status = 0;
+            break;
+        }
+        if (np >= MAXP - 1) {
+            for (int c = 0; c < dim; ++c) out[c] = NAN;
             break;
         }
         /* bisect the worst panel (worst relative to its component scale) */
@@ -287,6 +299,7 @@ static void gk_adaptive(vec_integrand fn, const void* ctx, int dim, double a, do
         ++np;
     }
     free(P);
+    return status;
 }
 
 /* ------------------------------------------------------------------ */
@@ -326,7 +339,7 @@ double oracle_sommerfeld_K(int L, const double* d, const double* eps, int l, int
     double kmax = (N + 50.0 + 2.0 * sqrt((double)N + 1.0) * 6.0) / z;
     int np = 8 + (int)ceil(kmax * rho / OR_PI);
     double out;
-    gk_adaptive(knm_integrand, &c, 1, 0.0, kmax, np, tol, &out);
+    gk_adaptive(knm_integrand, &c, 1, 0.0, kmax, np, tol, NULL, &out); /* NaN if unconverged */
     return out;
 }
 
@@ -388,9 +401,11 @@ typedef struct {
     int l, lp;
     double rho, z, zp;
     int sigma_mode; /* 0 spectral solve, 1 sigma==1 (fake density for tests) */
+    const double* s_inf; /* sigma(k -> inf) per component, subtracted (mode 0) */
 } pair_ctx;
 
-/* f[0] = sum_ab e^{-k h} sigma J0(k rho)
+/* With s(k) = sigma(k) - sigma_inf (mode 0) or s = 1 (mode 1):
+ * f[0] = sum_ab e^{-k h} s J0(k rho)
  * f[1] = d/dz of the same
  * f[2] = d/drho of the same */
 static void pair_integrand(double k, const void* vctx, double* f)
@@ -407,7 +422,8 @@ static void pair_integrand(double k, const void* vctx, double* f)
             if (!comp_exists(c->L, c->l, c->lp, a, b)) continue;
             double dh;
             double h = comp_h(c->d, c->l, c->lp, a, b, c->z, c->zp, &dh);
-            double sg = (c->sigma_mode == 1) ? 1.0 : s[(c->l * 2 + a - 1) * 2 + b - 1];
+            int ci = (c->l * 2 + a - 1) * 2 + b - 1;
+            double sg = (c->sigma_mode == 1) ? 1.0 : s[ci] - c->s_inf[ci];
             double e = exp(-k * h) * sg;
             F += e;
             Fz += -k * dh * e;
@@ -427,22 +443,81 @@ static double min_h(int L, const double* d, int l, int lp, double z, double zp)
 }
 
 /* Reaction Green's function sum_ab u^{ab}_{l,lp}(r, r') (times 4 pi) and its
- * target gradient, by adaptive quadrature.  g[0] = 4 pi u, g[1..3] = 4 pi grad u. */
-static void reaction_quad(int L, const double* d, const double* eps, int sigma_mode, int l, int lp, const double* r,
-                          const double* rp, double tol, double* g)
+ * target gradient (eqs. generalcomponents, zexponential).
+ *
+ * Mode 0 (density from the spectral solve).  As k -> inf the interfaces
+ * decouple, and sigma(k) tends to sigma_inf, the solve with every
+ * e^{-k(d_{j-1}-d_j)} set to 0: the single-interface reflection coefficient
+ * when the source's and target's interfaces coincide, 0 otherwise.  The
+ * integral is split exactly as
+ *   int J0(k rho) e^{-kh} sigma dk = sigma_inf / sqrt(rho^2 + h^2)
+ *                                  + int J0(k rho) e^{-kh} (sigma - sigma_inf) dk,
+ * the first term by the Lipschitz integral int_0^inf J0(k rho) e^{-kh} dk =
+ * 1/sqrt(rho^2 + h^2) (and its h and rho derivatives for the field), the
+ * second by adaptive Gauss-Kronrod.  sigma - sigma_inf decays at least like
+ * e^{-k Dmin}, Dmin the thinnest inner layer (another interface lies at
+ * least Dmin away, and any other path adds 2 Dmin), so the quadrature's
+ * interval and oscillation count stay bounded as h -> 0, where the unsplit
+ * integrand would need 1/h of the range.  With two layers sigma is constant
+ * and the second term vanishes.
+ *
+ * Mode 1 (sigma == 1, the fake density of the tests): the unsplit integral by
+ * quadrature, which exercises the quadrature itself.
+ *
+ * g[0] = 4 pi u, g[1..3] = 4 pi grad u.  Returns 0, or 1 (and NaN in g) when
+ * the quadrature did not converge. */
+static int reaction_quad(int L, const double* d, const double* eps, int sigma_mode, int l, int lp, const double* r,
+                         const double* rp, double tol, double* g)
 {
     double dx = r[0] - rp[0], dy = r[1] - rp[1];
     double rho = sqrt(dx * dx + dy * dy);
-    pair_ctx c = {L, d, eps, l, lp, rho, r[2], rp[2], sigma_mode};
+    double s_inf[4 * (OR_MAXL + 1)];
+    memset(s_inf, 0, sizeof(s_inf));
+    double G0 = 0.0, Gz = 0.0, Grho = 0.0; /* closed-form part */
+    if (sigma_mode == 0) {
+        if (oracle_sigma(L, d, eps, INFINITY, lp, s_inf)) { g[0] = g[1] = g[2] = g[3] = NAN; return 1; }
+        for (int a = 1; a <= 2; ++a)
+            for (int b = 1; b <= 2; ++b) {
+                if (!comp_exists(L, l, lp, a, b)) continue;
+                double dh, h = comp_h(d, l, lp, a, b, r[2], rp[2], &dh);
+                double si = s_inf[(l * 2 + a - 1) * 2 + b - 1];
+                double R2 = rho * rho + h * h, R = sqrt(R2);
+                G0 += si / R;
+                Gz += -si * dh * h / (R2 * R);
+                Grho += -si * rho / (R2 * R);
+            }
+    }
+    pair_ctx c = {L, d, eps, l, lp, rho, r[2], rp[2], sigma_mode, s_inf};
     double hmin = min_h(L, d, l, lp, r[2], rp[2]);
-    double kmax = 48.0 / hmin;
+    double kmax;
+    if (sigma_mode == 0) {
+        if (L < 2) { /* sigma constant in k: nothing left to integrate */
+            g[0] = G0; g[3] = Gz;
+            g[1] = rho > 0 ? Grho * dx / rho : 0.0;
+            g[2] = rho > 0 ? Grho * dy / rho : 0.0;
+            return 0;
+        }
+        double Dmin = INFINITY;
+        for (int j = 1; j < L; ++j) Dmin = fmin(Dmin, d[j - 1] - d[j]);
+        kmax = 60.0 / (hmin + Dmin);
+    } else {
+        kmax = 48.0 / hmin;
+    }
     int np = 4 + (int)ceil(kmax * rho / OR_PI);
+    /* Mode 0: the tolerance is relative to the whole integral, closed-form
+     * part included, with a floor of 1e-3 of a unit image at the nearest
+     * exponent distance (a remainder that vanishes, as with equal
+     * permittivities, is then not chased into rounding noise). */
+    double Rh = sqrt(rho * rho + hmin * hmin);
+    double fl[3] = {tol * (fabs(G0) + 1e-3 / Rh), tol * (fabs(Gz) + 1e-3 / (Rh * Rh)),
+                    tol * (fabs(Grho) + 1e-3 / (Rh * Rh))};
     double I[3];
-    gk_adaptive(pair_integrand, &c, 3, 0.0, kmax, np, tol, I);
-    g[0] = I[0];
-    g[3] = I[1];
-    if (rho > 0) { g[1] = I[2] * dx / rho; g[2] = I[2] * dy / rho; }
+    int st = gk_adaptive(pair_integrand, &c, 3, 0.0, kmax, np, tol, sigma_mode == 0 ? fl : NULL, I);
+    g[0] = G0 + I[0];
+    g[3] = Gz + I[1];
+    if (rho > 0) { g[1] = (Grho + I[2]) * dx / rho; g[2] = (Grho + I[2]) * dy / rho; }
     else { g[1] = g[2] = 0.0; }
+    return st;
 }
 
 /* Same quantity by the exact three-layer image series. */
@@ -489,7 +564,8 @@ static void reaction_images(const double* d, const double* eps, int l, int lp, c
  *         2 reaction by quadrature with the fake density sigma == 1,
  *         3 free-space part only.
  *   phi[nt], field[nt*3] (field may be NULL).
- * Returns 0, or -1 on bad input. */
+ * Returns 0, -1 on bad input, or -2 when an adaptive quadrature ran out of
+ * panels before meeting its tolerance (the affected outputs are NaN). */
 int oracle_direct(int L, const double* d, const double* eps, int64_t n, const double* xyz, const int32_t* layer,
                   const double* q, int64_t nt, const int64_t* targets, int mode, double tol, double* phi,
                   double* field, int nthreads)
@@ -504,9 +580,10 @@ int oracle_direct(int L, const double* d, const double* eps, int64_t n, const do
         if (l < L && !(z > d[l])) return -1;
     }
     const double inv4pi = 1.0 / (4.0 * OR_PI);
+    int failed = 0;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 1)
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : failed)
 #endif
     for (int64_t t = 0; t < nt; ++t) {
         int64_t i = targets[t];
@@ -526,14 +603,14 @@ int oracle_direct(int L, const double* d, const double* eps, int64_t n, const do
             if (mode == 3 || L == 0) continue;
             double g[4];
             if (mode == 1) reaction_images(d, eps, l, lp, r, rp, g);
-            else reaction_quad(L, d, eps, mode == 2 ? 1 : 0, l, lp, r, rp, tol, g);
+            else failed |= reaction_quad(L, d, eps, mode == 2 ? 1 : 0, l, lp, r, rp, tol, g);
             P += q[j] * g[0];
             Ex -= q[j] * g[1]; Ey -= q[j] * g[2]; Ez -= q[j] * g[3];
         }
         phi[t] = P * inv4pi;
         if (field) { field[3 * t] = Ex * inv4pi; field[3 * t + 1] = Ey * inv4pi; field[3 * t + 2] = Ez * inv4pi; }
     }
-    return 0;
+    return failed ? -2 : 0;
 }
 
 /* Reaction Green's function of one pair (4 pi u and 4 pi grad_r u), exposed
@@ -545,8 +622,8 @@ int oracle_reaction_pair(int L, const double* d, const double* eps, int l, int l
     if (mode == 1) {
         if (L != 2) return -1;
         reaction_images(d, eps, l, lp, r, rp, g);
-    } else {
-        reaction_quad(L, d, eps, mode == 2 ? 1 : 0, l, lp, r, rp, tol, g);
+    } else if (reaction_quad(L, d, eps, mode == 2 ? 1 : 0, l, lp, r, rp, tol, g)) {
+        return -2;
     }
     return 0;
 }

@@ -164,6 +164,48 @@ def test_direct_quadrature_matches_image_series(eps):
     assert np.max(np.abs(f1 - f0)) < 1e-10 * np.max(np.abs(f1))
 
 
+@pytest.mark.parametrize("eps", [MEDIA[0], MEDIA[1]])
+def test_quadrature_next_to_interfaces_matches_image_series(eps):
+    # Charges 1e-5 .. 1e-2 from an interface, the regime of the near field
+    # (Section 3.1's components with a short exponent distance h): the
+    # quadrature of the spectral-solve density must agree with the exact
+    # three-layer image series in potential and gradient, for every pair of
+    # layers and every side of each interface.
+    sides = [(0, lambda h: 0.0 + h), (1, lambda h: 0.0 - h), (1, lambda h: -1.2 + h), (2, lambda h: -1.2 - h)]
+    worst = 0.0
+    for ht in (1e-5, 1e-4, 1e-3, 1e-2):
+        for hs in (1e-5, 1e-3):
+            for lt, zt in sides:
+                for ls, zs in sides:
+                    for rho in (0.0, 0.03, 0.4, 1.0):
+                        r = np.array([0.1, -0.2, zt(ht)])
+                        rp = np.array([0.1 + rho * 0.6, -0.2 + rho * 0.8, zs(hs)])
+                        uq, gq = oracle.reaction_pair(D3, eps, lt, ls, r, rp, mode=oracle.MODE_QUAD, tol=1e-13)
+                        ui, gi = oracle.reaction_pair(D3, eps, lt, ls, r, rp, mode=oracle.MODE_IMAGES)
+                        assert abs(uq - ui) <= 1e-10 * abs(ui) + 1e-13, (ht, hs, lt, ls, rho)
+                        assert np.linalg.norm(gq - gi) <= 1e-10 * np.linalg.norm(gi) + 1e-13, (ht, hs, lt, ls, rho)
+                        worst = max(worst, abs(uq - ui) / abs(ui))
+    assert worst < 1e-10
+
+
+def test_quadrature_reports_non_convergence():
+    # A planted failure: the unsplit integral of J0(k rho) e^{-kh} (the sigma == 1
+    # mode) at h = 1e-8 and rho = 1 spans ~1e9 Bessel oscillations, far beyond
+    # the panel budget.  The oracle must refuse, not return the partial sum.
+    r = np.array([0.0, 0.0, -0.6]); rp = np.array([1.0, 0.0, -0.6])
+    d_near = [-0.6 + 5e-9, -1.2]
+    with pytest.raises(oracle.OracleNotConverged):
+        oracle.reaction_pair(d_near, MEDIA[0], 1, 1, r, rp, mode=oracle.MODE_SIGMA_ONE)
+    xyz = np.array([r, rp]); lay = np.array([1, 1], np.int32)
+    with pytest.raises(oracle.OracleNotConverged):
+        oracle.direct(d_near, MEDIA[0], xyz, lay, np.ones(2), mode=oracle.MODE_SIGMA_ONE)
+    # the same pair with the spectral-solve density converges (split form)
+    u, g = oracle.reaction_pair(d_near, MEDIA[0], 1, 1, r, rp, mode=oracle.MODE_QUAD)
+    ui, gi = oracle.reaction_pair(d_near, MEDIA[0], 1, 1, r, rp, mode=oracle.MODE_IMAGES)
+    assert u == pytest.approx(ui, rel=1e-11)
+    assert np.allclose(g, gi, rtol=1e-10, atol=1e-12 * np.linalg.norm(gi))
+
+
 def test_homogeneous_medium_is_coulomb():
     rng = np.random.default_rng(5)
     n = 40
@@ -475,6 +517,53 @@ def test_transmission_conditions_four_layers(src_layer):
         assert ua == pytest.approx(ub, rel=1e-10)
         assert eps[above] * ga[2] == pytest.approx(eps[below] * gb[2], rel=1e-9)
         assert ga[0] == pytest.approx(gb[0], rel=1e-9)
+
+
+@pytest.mark.parametrize("h", [1e-3, 1e-4])
+def test_transmission_conditions_four_layers_next_to_interfaces(h):
+    # eq. transmissioncond at each interface, with the source a distance h
+    # below it and the evaluation point right above the source (rho = 0.01):
+    # the exponent distances are ~h, the regime of the near field
+    eps = [2.0, 7.0, 1.5, 12.0]
+    for j, dj in enumerate(D4):
+        above, below = j, j + 1
+        rp = np.array([0.05, -0.1, dj - h])
+        x = np.array([0.06, -0.1, dj])
+
+        def total(l, pt):
+            u, g = oracle.reaction_pair(D4, eps, l, below, pt, rp, mode=oracle.MODE_QUAD)
+            if l == below:
+                R = pt - rp
+                u += 1 / np.linalg.norm(R)
+                g = g - R / np.linalg.norm(R) ** 3
+            return u, g
+        ua, ga = total(above, x)
+        ub, gb = total(below, x)
+        assert ua == pytest.approx(ub, rel=1e-10)
+        assert eps[above] * ga[2] == pytest.approx(eps[below] * gb[2], rel=1e-9)
+        assert ga[0] == pytest.approx(gb[0], rel=1e-9)
+
+
+def test_equal_eps_interface_disappears_next_to_interfaces():
+    # eps = (1, 5, 5, 10): the interface at -0.6 disappears, and charges 1e-4
+    # from the remaining interfaces (0 and -1.2) must see the three-layer
+    # image series' potential and field
+    rng = np.random.default_rng(53)
+    n = 60
+    lay = rng.integers(0, 4, n).astype(np.int32)
+    side = {0: (0.0, 1.0), 1: (0.0, -1.0), 2: (-1.2, 1.0), 3: (-1.2, -1.0)}
+    xyz = np.zeros((n, 3))
+    xyz[:, :2] = rng.uniform(-0.5, 0.5, (n, 2))
+    for i in range(n):
+        base, sgn = side[int(lay[i])]
+        xyz[i, 2] = base + sgn * 10 ** rng.uniform(-4, -2)
+    q = rng.uniform(-1, 1, n)
+    lay3 = np.where(lay >= 2, lay - 1, lay).astype(np.int32)
+    t = np.arange(20)
+    p4, f4 = oracle.direct(D4, [1.0, 5.0, 5.0, 10.0], xyz, lay, q, targets=t, mode=oracle.MODE_QUAD)
+    p3, f3 = oracle.direct(D3, [1.0, 5.0, 10.0], xyz, lay3, q, targets=t, mode=oracle.MODE_IMAGES)
+    assert oracle.err2(p3, p4) < 1e-11
+    assert oracle.err2(f3, f4) < 1e-10
 
 
 def test_reciprocity_four_layers():
