@@ -339,17 +339,20 @@ lfmm_status lfmm_surrogate_loss_grad(lfmm_ctx* ctx, int l, int lp, int a, int b,
                                      const float* y, double* loss, float* grad);
 
 /* Allocation-free variant of lfmm_reaction_kernel, for callers that may not
- * allocate device memory during the call (stream capture, real-time loops,
- * hosts with a fixed device-memory budget).  The paper has no counterpart;
- * this is a library interface only.
- * Same arguments and results as lfmm_reaction_kernel (host arrays).  Inputs
- * and outputs are staged through one static device array shared by all calls
+ * allocate device memory during the call: real-time or embedded loops whose
+ * rules forbid allocator calls after start-up, and hosts on which another
+ * runtime owns the device-memory budget.  The paper has no counterpart; this
+ * is a library interface only.
+ * Same arguments and results as lfmm_reaction_kernel (host arrays, copied in
+ * and out; the call waits for the context's stream).  Inputs and outputs are
+ * staged through one static device array shared by all calls
  * (LFMM_NOALLOC_MAX_POINTS points, 2.6 MB per GPU that loads the library, held
  * until process exit); the call makes no cudaMalloc / cudaFree.
  *   npts : 1 <= npts <= LFMM_NOALLOC_MAX_POINTS, else LFMM_EINVAL.
- * The first call on a device resolves the array's device address (make it
- * before any stream capture).  Calls that overlap on the GPU race on the
- * shared array: serialise them.  Synchronises the context's stream. */
+ * The context's device must be the current device (else LFMM_EINVAL).  The
+ * first call on a device resolves the array's device address, so that first
+ * call should come before any stream capture.  Calls that overlap on the GPU
+ * race on the shared array: serialise them. */
 #define LFMM_NOALLOC_MAX_POINTS 65536
 lfmm_status lfmm_reaction_kernel_noalloc(lfmm_ctx* ctx, int l, int lp, int a, int b, int npts, const double* rho,
                                          const double* h, double* out);
@@ -370,8 +373,10 @@ lfmm_status lfmm_gauss_laguerre(int Q, double* nodes, double* weights);
  *               C exp(-k zeta), and the decay rate zeta_r of the remainder
  *               sigma - C exp(-k zeta) (-1 where there is none).  a = b = 0
  *               for free-space components.
- *   nrows     : receives the rows written (out given) or the component count.
- * The caller owns out. */
+ *   nrows     : receives the component count (also when out is too small).
+ * With out given and max_rows below the component count nothing is written
+ * and the call returns LFMM_EINVAL: call with out = NULL first to learn the
+ * count.  The caller owns out. */
 #define LFMM_MEDIUM_COLS 11
 lfmm_status lfmm_medium_components(const double* d, int L, const double* eps, double* out, int max_rows,
                                    int* nrows);

@@ -661,9 +661,12 @@ lfmm_status lfmm_medium_components(const double* d, int L, const double* eps, do
     for (int l = 0; l < L; ++l) ctx->d[l] = d[l];
     for (int l = 0; l <= L; ++l) ctx->eps[l] = eps[l];
     const lfmm_status st = status_of(setup_components(ctx));  // host only
+    lfmm_status ret = st;
     if (st == LFMM_OK) {
         const int nc = ctx->ncomp;
-        const int w = out ? std::min(nc, max_rows) : 0;
+        if (nrows) *nrows = nc;  // always the full count
+        const int w = (out && max_rows >= nc) ? nc : 0;
+        if (out && max_rows < nc) ret = LFMM_EINVAL;  // too small: nothing written
         for (int c = 0; c < w; ++c) {
             const LfmmComp& cp = ctx->comp[c];
             const double row[LFMM_MEDIUM_COLS] = {(double)cp.l, (double)cp.lp, (double)cp.a, (double)cp.b,
@@ -671,10 +674,9 @@ lfmm_status lfmm_medium_components(const double* d, int L, const double* eps, do
                                                   cp.has_rem ? cp.zeta_r : -1.0};
             std::copy(row, row + LFMM_MEDIUM_COLS, out + (size_t)c * LFMM_MEDIUM_COLS);
         }
-        if (nrows) *nrows = out ? w : nc;
     }
     delete ctx;
-    return st;
+    return ret;
 }
 
 lfmm_status lfmm_create(const double* d, int L, const double* eps, int p, lfmm_ctx** out)

@@ -842,12 +842,15 @@ LfErr lf_reaction_kernel_dev(lfmm_ctx* ctx, int comp, int npts, const double* rh
 // Allocation-free variant of lfmm_reaction_kernel.
 //
 // Some callers cannot allocate device memory at the point where they need the
-// layered reaction kernel: code running inside a stream capture, real-time or
-// embedded loops that forbid allocator calls, or hosts that manage a fixed
-// device-memory budget themselves.  lfmm_reaction_kernel stages its inputs and
-// outputs through buffers it allocates on every call; this variant stages them
-// through one file-scope device array instead, so the call itself makes no
-// cudaMalloc / cudaFree (or any other allocating call).
+// layered reaction kernel: real-time or embedded loops whose rules forbid
+// allocator calls after start-up, and hosts that hand this library a device
+// on which another runtime already owns the memory budget.
+// lfmm_reaction_kernel stages its inputs and outputs through buffers it
+// allocates on every call; this variant stages them through one file-scope
+// device array instead, so the call itself makes no cudaMalloc / cudaFree (or
+// any other allocating call).  Like lfmm_reaction_kernel it copies from and
+// to the caller's host arrays and waits for the context's stream before it
+// returns.
 //
 // The array holds LFMM_NOALLOC_MAX_POINTS points (rho, h and three outputs per
 // point: 5 doubles, 2.6 MB).  It is defined once per process and every GPU
@@ -858,30 +861,24 @@ LfErr lf_reaction_kernel_dev(lfmm_ctx* ctx, int comp, int npts, const double* rh
 // device) race on the array and must be serialised by the caller.
 //
 // The device address of the array is resolved with cudaGetSymbolAddress the
-// first time the entry point runs on a device (with that device current) and
-// cached per device; that first call therefore must not happen inside a stream
-// capture.
+// first time the entry point runs on a device and cached per device; that
+// first call therefore must come before any stream capture.  The call runs on
+// the device the context was created on, which must be the current device.
 // ---------------------------------------------------------------------------
 static __device__ __align__(256) double g_noalloc_scratch[5 * LFMM_NOALLOC_MAX_POINTS];
 
 static std::mutex g_noalloc_mutex;
 static double* g_noalloc_ptr[LFMM_MAX_DEVICES] = {nullptr};
 
+// The array's device address on `device`, which the caller has checked is
+// the current device.
 static LfErr noalloc_scratch(int device, double** out)
 {
     if (device < 0 || device >= LFMM_MAX_DEVICES) return "EINVAL: device index out of range";
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
     if (!g_noalloc_ptr[device]) {
-        int cur = -1;
-        cudaError_t e = cudaGetDevice(&cur);
-        if (e != cudaSuccess) return lf_cuda(e, "cudaGetDevice");
-        if (cur != device) {
-            e = cudaSetDevice(device);
-            if (e != cudaSuccess) return lf_cuda(e, "cudaSetDevice");
-        }
         void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (cur != device) cudaSetDevice(cur);
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return lf_cuda(e, "cudaGetSymbolAddress");
         g_noalloc_ptr[device] = static_cast<double*>(p);
     }
@@ -906,6 +903,17 @@ extern "C" lfmm_status lfmm_reaction_kernel_noalloc(lfmm_ctx* ctx, int l, int lp
     if (npts > LFMM_NOALLOC_MAX_POINTS) {
         ctx->err = "EINVAL: npts exceeds LFMM_NOALLOC_MAX_POINTS (" + std::to_string(LFMM_NOALLOC_MAX_POINTS) +
                    ") of the allocation-free entry point";
+        return LFMM_EINVAL;
+    }
+    int cur = -1;
+    cudaError_t ce = cudaGetDevice(&cur);
+    if (ce != cudaSuccess) {
+        ctx->err = lf_cuda(ce, "cudaGetDevice");
+        return LFMM_ECUDA;
+    }
+    if (cur != ctx->device) {
+        ctx->err = "EINVAL: the current device (" + std::to_string(cur) + ") is not the context's device (" +
+                   std::to_string(ctx->device) + "); make the context's device current first";
         return LFMM_EINVAL;
     }
     for (int i = 0; i < npts; ++i)

@@ -141,9 +141,13 @@ def medium_components(d, eps):
     d = _f64(d)
     eps = _f64(eps)
     L = int(d.shape[0])
-    out = np.zeros((64, len(MEDIUM_COLS)))
+    lib = load()
     n = ctypes.c_int(0)
-    st = load().lfmm_medium_components(_ptr(d) if L else None, L, _ptr(eps), _ptr(out), 64, ctypes.byref(n))
+    st = lib.lfmm_medium_components(_ptr(d) if L else None, L, _ptr(eps), None, 0, ctypes.byref(n))
+    if st != OK:
+        raise LfmmError(st, "lfmm_medium_components")
+    out = np.zeros((n.value, len(MEDIUM_COLS)))
+    st = lib.lfmm_medium_components(_ptr(d) if L else None, L, _ptr(eps), _ptr(out), n.value, ctypes.byref(n))
     if st != OK:
         raise LfmmError(st, "lfmm_medium_components")
     ints = {"l", "lp", "a", "b", "is_free"}

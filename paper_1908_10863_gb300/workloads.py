@@ -20,6 +20,9 @@ library and for the CPU oracle alike.
   r(theta) = 0.5 - a + a P_4(cos theta), a = (0.1, 0.15, 0.05), centred at
   z = 0.6, -0.6, -1.8, eps = (21.2, 47.5, 62.8), by rejection from the
   bounding cube.
+* :func:`four_layers` / :func:`four_layers_near_interface` -- media of four
+  layers: slabs away from the interfaces, or every charge within ``delta``
+  of an interface on its own side.
 * :func:`uneven_problems` -- k independent config2-shaped problems whose
   sizes are log-uniform in [nmin, nmax] (the batched form's many uneven
   problems), each with its own seed.
@@ -145,6 +148,28 @@ def four_layers(n: int = 4000, seed: int | None = None, d=D_FOUR, eps=EPS_FOUR, 
     layer = np.concatenate([np.full(p.shape[0], l, dtype=np.int32) for p, l in parts])
     q = rng.uniform(-1.0, 1.0, size=n)
     return Workload("four_layers_n%d" % n, np.array(d), np.array(eps, dtype=np.float64), xyz, layer, q)
+
+
+def four_layers_near_interface(n: int = 3000, delta: float = 0.02, hmin: float = 1e-3, seed: int | None = None,
+                               d=D_FOUR, eps=EPS_FOUR) -> Workload:
+    """Four layers, every charge between ``hmin`` and ``delta`` from an
+    interface on its own side: N split equally between the six sides of the
+    three interfaces (above and below each), x, y in [-0.5, 0.5],
+    q ~ U[-1, 1].  The near field then holds reaction interactions of every
+    layer pair, which the general-medium near-field kernels evaluate."""
+    rng = np.random.Generator(np.random.PCG64(SEED_BASE + 9 if seed is None else seed))
+    d = tuple(float(v) for v in d)
+    spans = []
+    for j, dj in enumerate(d):
+        spans.append(((dj + hmin, dj + delta), j))          # layer j, above interface j
+        spans.append(((dj - delta, dj - hmin), j + 1))      # layer j + 1, below it
+    sizes = [n // 6] * 5 + [n - 5 * (n // 6)]
+    parts = [(_box(rng, cnt, lo, hi), l) for cnt, ((lo, hi), l) in zip(sizes, spans)]
+    xyz = np.concatenate([p for p, _ in parts])
+    layer = np.concatenate([np.full(p.shape[0], l, dtype=np.int32) for p, l in parts])
+    q = rng.uniform(-1.0, 1.0, size=n)
+    return Workload("four_layers_near_interface_n%d" % n, np.array(d), np.array(eps, dtype=np.float64), xyz,
+                    layer, q)
 
 
 def subsample(n: int, count: int, seed: int = SEED_BASE + 3) -> np.ndarray:

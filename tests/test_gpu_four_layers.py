@@ -4,6 +4,8 @@ Every reference is the CPU oracle: its adaptive Gauss-Kronrod integrals of
 its own per-k linear solve, or, where one interface separates equal
 permittivities, the exact image series of the three-layer medium it reduces to.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -84,6 +86,29 @@ def test_fmm_matches_oracle(aligned, precision, tol):
     print("four layers aligned=%s precision=%d: Err2 phi %.2e field %.2e, stats %s"
           % (aligned, precision, e_phi, e_fld, st))
     assert e_phi < tol and e_fld < 20 * tol
+
+
+# Every charge 1e-3 .. 0.02 from an interface: the near field holds reaction
+# pairs of every layer pair, evaluated by the general-medium block kernel (one
+# interface-problem solve per quadrature node); the reference is the oracle's
+# quadrature of its own per-k solve (Sommerfeld limit in closed form).
+@pytest.mark.parametrize("aligned", [True, False])
+@pytest.mark.parametrize("precision,tol_phi,tol_fld", [(0, 1e-5, 1e-4), (1, 2e-5, 1e-4)])
+def test_near_interface_matches_quadrature_oracle(aligned, precision, tol_phi, tol_fld):
+    d = workloads.D_FOUR if aligned else workloads.D_FOUR_UNALIGNED
+    w = workloads.four_layers_near_interface(3000, d=d)
+    with LayeredFMM(w.d, w.eps, 10, precision=precision) as f:
+        f.build(w.xyz, w.layer)
+        st = f.stats()
+        phi, E = f.evaluate(w.q)
+    assert st["p2p_reaction"] > 0
+    t = workloads.subsample(w.n, 48)
+    ref, refE = oracle.direct(w.d, w.eps, w.xyz, w.layer, w.q, targets=t, mode=oracle.MODE_QUAD,
+                              threads=os.cpu_count() or 1)
+    e_phi, e_fld = oracle.err2(ref, phi[t]), oracle.err2(refE, E[t])
+    print("four layers near interfaces aligned=%s precision=%d: Err2 phi %.2e field %.2e (p2p_reaction %d)"
+          % (aligned, precision, e_phi, e_fld, st["p2p_reaction"]))
+    assert e_phi < tol_phi and e_fld < tol_fld
 
 
 def test_equal_permittivity_interface_matches_three_layer_images():

@@ -188,3 +188,12 @@ def test_surrogate_gain_in_near_field(trained, precision):
                                                     100 * frac, oracle.err2(res[0][1], res[1][1])))
     assert frac > 0.0
     assert oracle.err2(res[0][1], res[1][1]) < (1e-6 if precision == 0 else 1e-5)
+    gain = res[0][0] / res[1][0]
+    if precision == 0:
+        # FP64 form: the network (bfloat16 tensor-core MMAs) replaces the FP64
+        # quadrature of about half the reaction pairs; measured 1.6-2.0x
+        assert gain > 1.3
+    else:
+        # float32 form: the float32 quadrature is cheaper than the network
+        # (measured 0.44x), so the network is a loss there
+        assert gain < 1.0

@@ -70,3 +70,19 @@ def test_components_match_oracle(d, eps):
 def test_invalid_media_rejected(d, eps):
     with pytest.raises(LfmmError):
         medium_components(d, eps)
+
+
+def test_short_output_is_refused_with_the_full_count():
+    # four layers have 4 free + 36 reaction components; a buffer for 10 rows
+    # is refused (nothing written) and the count still comes back
+    import ctypes
+    from paper_1908_10863_gb300 import lfmm
+    d = np.array([0.0, -0.6, -1.2]); eps = np.array([2.0, 7.0, 1.5, 12.0])
+    dp = ctypes.POINTER(ctypes.c_double)
+    out = np.full((10, len(lfmm.MEDIUM_COLS)), 7.0)
+    n = ctypes.c_int(-1)
+    st = lfmm.load().lfmm_medium_components(d.ctypes.data_as(dp), 3, eps.ctypes.data_as(dp),
+                                            out.ctypes.data_as(dp), 10, ctypes.byref(n))
+    assert st == lfmm.EINVAL and n.value == 40
+    assert np.all(out == 7.0)
+    assert len(medium_components(d, eps)) == 40
