@@ -87,6 +87,10 @@ def parse():
                     help="oracle targets of the two N = 1M cases of --accuracy-table")
     ap.add_argument("--accuracy-table", action="store_true",
                     help="instead of timing: Err2 against the oracle for each medium, N, p and precision")
+    ap.add_argument("--sweep", action="store_true",
+                    help="instead of the headline: time and Err2 for N in {64k, 256k, 1M} x p in {6, 10, 14} x form")
+    ap.add_argument("--matched-orders", default="8,9",
+                    help="orders of the plain FP64 form timed beside the headline for the matched-accuracy line")
     ap.add_argument("--forms", default="fp32_surrogate,fp32,fp64",
                     help="comma list of fp32_surrogate, fp32, fp64; the first is the headline")
     return ap.parse_args()
@@ -370,7 +374,8 @@ def many_problems_leg(torch, dev, p, flush, k=48):
     """Float32 form, k independent three-layer problems with log-uniform sizes
     in [2k, 100k]: one CUDA graph replay per evaluation against the same
     launches issued directly and against k one-at-a-time evaluations, and the
-    graph again after every problem tuned its settings (lfmm_autotune)."""
+    graph again after the batch tuner picked settings for the whole batch
+    (lfmm_batch_autotune)."""
     from paper_1908_10863_gb300 import LayeredFMM, LayeredFMMBatch, workloads
     import oracle
     probs = workloads.uneven_problems(k)
@@ -413,12 +418,12 @@ def many_problems_leg(torch, dev, p, flush, k=48):
     fd = [torch.empty((x.shape[0], 3), dtype=torch.float64, device=dev) for x in qd]
     t_seq = timed(lambda: [m.evaluate_device(a, b_, c, s) for m, a, b_, c in zip(ms, qd, pd, fd)])
     seq_phi = np.concatenate([x.cpu().numpy() for x in pd])
-    # the same batch after each problem picked its own settings (evaluation-time tuning)
-    t0 = time.perf_counter()
-    for m, w in zip(ms, probs):
-        m.autotune(w.xyz, w.layer, mode=0, reps=2)
-    tune_s = time.perf_counter() - t0
+    # the batch tuned as a whole (lfmm_batch_autotune times graph replays of
+    # the whole batch for settings applied to every member)
     b = LayeredFMMBatch(ms, graph=True)
+    t0 = time.perf_counter()
+    rows = b.autotune(reps=3)
+    tune_s = time.perf_counter() - t0
     q = torch.from_numpy(b.concat([w.q for w in probs])).to(dev)
     phi = torch.empty_like(q)
     fld = torch.empty(3 * total, dtype=torch.float64, device=dev)
@@ -428,8 +433,11 @@ def many_problems_leg(torch, dev, p, flush, k=48):
     for m in ms:
         m.close()
     t_g, info, phi_g = res[True]
-    out.update({"graph_tuned_ms": t_tuned, "tuning_s": tune_s, "particles_per_s_tuned": total / (t_tuned / 1e3),
-                "err2_phi_tuned_vs_default": oracle.err2(phi_g, phi_t)})
+    best = [r for r in rows if r["chosen"]]
+    out.update({"graph_batch_tuned_ms": t_tuned, "batch_tuning_s": tune_s,
+                "particles_per_s_batch_tuned": total / (t_tuned / 1e3),
+                "batch_tuned_setting": best[0] if best else None, "batch_tuner_rows": rows,
+                "err2_phi_batch_tuned_vs_default": oracle.err2(phi_g, phi_t)})
     out.update({"graph_ms": t_g, "direct_ms": res[False][0], "one_at_a_time_ms": t_seq,
                 "particles_per_s": total / (t_g / 1e3), "speedup_vs_one_at_a_time": t_seq / t_g,
                 "graph_nodes": info["graph_nodes"], "kernel_nodes": info["kernel_nodes"],
@@ -440,30 +448,69 @@ def many_problems_leg(torch, dev, p, flush, k=48):
 def accuracy_table(torch, dev, targets=(200, 60)):
     """Relative L2 errors (potential and field) of both forms against the CPU
     oracle (exact image series), one JSON line per case.  Small N: all
-    targets; N = 1M: a seeded target subsample of the given sizes."""
+    targets; N = 1M: a seeded target subsample of the given sizes.  The
+    paper_p4 case is Section 4's accuracy experiment (P4-shaped domains,
+    eps = (21.2, 47.5, 62.8), N = 2,848), Err2 against p."""
     import oracle
     from paper_1908_10863_gb300 import LayeredFMM, workloads
-    cases = [("config1", "(1,5,10)", 1000, 1000), ("config2", "(1,5,10)", 1 << 20, targets[0]),
-             ("config2", "(1,80,2)", 1 << 20, targets[1])]
-    for name, med, n, ns in cases:
-        eps = workloads.EPS_CONFIG if med == "(1,5,10)" else workloads.EPS_HIGH_CONTRAST
-        w = workloads.config1(n, eps=eps) if name == "config1" else workloads.config2(n, eps=eps)
-        t = np.arange(n) if ns >= n else workloads.subsample(n, ns)
+    cases = [("paper_p4", "(21.2,47.5,62.8)", 2848, 2848, (2, 4, 6, 8, 10, 12, 14, 16, 18, 20)),
+             ("config1", "(1,5,10)", 1000, 1000, (6, 10, 14, 20)),
+             ("config2", "(1,5,10)", 1 << 20, targets[0], (6, 10, 14)),
+             ("config2", "(1,80,2)", 1 << 20, targets[1], (6, 10, 14))]
+    for name, med, n, ns, plist in cases:
+        if name == "paper_p4":
+            w = workloads.paper_p4()
+        else:
+            eps = workloads.EPS_CONFIG if med == "(1,5,10)" else workloads.EPS_HIGH_CONTRAST
+            w = workloads.config1(n, eps=eps) if name == "config1" else workloads.config2(n, eps=eps)
+        t = np.arange(w.n) if ns >= w.n else workloads.subsample(w.n, ns)
         t0 = time.perf_counter()
         ref, refE = oracle.direct(w.d, w.eps, w.xyz, w.layer, w.q, targets=t, mode=oracle.MODE_IMAGES,
                                   threads=os.cpu_count() or 1)
         oracle_s = time.perf_counter() - t0
-        for p in (6, 10, 14, 20):
+        for p in plist:
             for prec in (0, 1):
-                if (n > 100000 and p == 20) or (prec == 1 and p > 14):
-                    continue  # p = 20 on the small case only; the float32 form stops at p = 14
+                if prec == 1 and p > 14:
+                    continue  # the float32 form stops at p = 14
                 with LayeredFMM(w.d, w.eps, p, precision=prec) as f:
                     f.build(w.xyz, w.layer)
                     phi, E = f.evaluate(w.q)
-                print(json.dumps({"case": name, "eps": med, "n": n, "targets": int(len(t)), "p": p,
+                print(json.dumps({"case": name, "eps": med, "n": w.n, "targets": int(len(t)), "p": p,
                                   "form": "fp32" if prec else "fp64", "err2_phi": oracle.err2(ref, phi[t]),
                                   "err2_field": oracle.err2(refE, E[t]), "oracle_s": round(oracle_s, 1)}),
                       flush=True)
+
+
+def sweep(torch, dev, flush, sizes=(1 << 16, 1 << 18, 1 << 20), orders=(6, 10, 14), sample=256):
+    """Three-layer split workload (eps = (1, 5, 10)): build + evaluate time per
+    step and Err2 against the oracle (exact image series, a seeded sample of
+    targets) for every N, p and form; one JSON line per case."""
+    import oracle
+    from paper_1908_10863_gb300 import LayeredFMM, workloads
+    for n in sizes:
+        w = workloads.config2(n)
+        t = workloads.subsample(w.n, sample)
+        ref, refE = oracle.direct(w.d, w.eps, w.xyz, w.layer, w.q, targets=t, mode=oracle.MODE_IMAGES,
+                                  threads=os.cpu_count() or 1)
+        xyz_d = torch.from_numpy(w.xyz).to(dev)
+        lay_d = torch.from_numpy(w.layer).to(dev)
+        q_d = torch.from_numpy(w.q).to(dev)
+        phi_d = torch.empty(w.n, dtype=torch.float64, device=dev)
+        fld_d = torch.empty((w.n, 3), dtype=torch.float64, device=dev)
+        for p in orders:
+            for prec in (1, 0):
+                with LayeredFMM(w.d, w.eps, p, precision=prec) as f:
+                    steps = 5 if prec else 2
+                    times, launches, stages = run_form(f, xyz_d, lay_d, q_d, phi_d, fld_d, torch, steps, 1, flush)
+                    st = f.stats()
+                ms = sum(times) / len(times)
+                phi, E = phi_d.cpu().numpy(), fld_d.cpu().numpy()
+                print(json.dumps({"sweep": "config2", "n": n, "p": p, "form": "fp32" if prec else "fp64",
+                                  "ms_per_step": ms, "particles_per_s": n / (ms / 1e3), "build_ms": stages["build"],
+                                  "evaluate_ms": stages["total"], "m2l_free_ms": stages["m2l_free"],
+                                  "p2p_ms": stages["p2p"], "m2l_pairs": st["m2l_free"], "depth": st["depth"],
+                                  "err2_phi": oracle.err2(ref, phi[t]), "err2_field": oracle.err2(refE, E[t]),
+                                  "targets": sample}), flush=True)
 
 
 def main():
@@ -506,6 +553,12 @@ def main():
         if rank == 0:
             accuracy_table(torch, torch.device("cuda", local), tuple(int(v) for v in args.acc_targets.split(",")))
         return 0
+    if args.sweep:
+        if rank == 0:
+            torch.cuda.set_device(local)
+            dev = torch.device("cuda", local)
+            sweep(torch, dev, torch.empty((256 << 20) // 4, dtype=torch.float32, device=dev))
+        return 0
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     xyz_d = torch.from_numpy(w.xyz).to(dev)
@@ -545,6 +598,21 @@ def main():
                          "prec": prec,
                          "phi": phi_d.cpu().numpy().copy(), "E": fld_d.cpu().numpy().copy(),
                          "surrogate_train_s": train_s}
+        if name == headline and prec == 1:
+            # the near-field kernel alone (not overlapped with the far field),
+            # CUDA events on its stream, for its own roofline; untimed by the step
+            f.set_option(13, 1)
+            f.set_option(3, 1)
+            stream = torch.cuda.current_stream()
+            f.build_device(xyz_d, lay_d, stream)
+            near_ms = []
+            for _ in range(4):
+                f.evaluate_device(q_d, phi_d, fld_d, stream)
+                torch.cuda.synchronize()
+                near_ms.append(f.timings()["p2p"])
+            f.set_option(3, 0)
+            f.set_option(13, 0)
+            results[name]["near_alone_ms"] = statistics.median(near_ms[1:])
         if name == headline:
             # end-to-end through the host-buffer C ABI (copies inside the timed region)
             e2e_t = []
@@ -559,6 +627,16 @@ def main():
                 e2e_t.append(time.perf_counter() - t0)
             results[name]["e2e_s"] = sum(e2e_t) / len(e2e_t)
         f.close()
+    # the plain FP64 form at lower orders, for the comparison at matched accuracy
+    matched_runs = {}
+    if rank == 0 and not args.no_fp64 and args.matched_orders:
+        for pm in sorted({int(v) for v in args.matched_orders.split(",") if v.strip()}):
+            if pm == args.p:
+                continue
+            f = LayeredFMM(w.d, w.eps, pm, precision=0)
+            times, launches, tim = run_form(f, xyz_d, lay_d, q_d, phi_d, fld_d, torch, 2, 1, flush)
+            f.close()
+            matched_runs[pm] = {"ms_per_step": sum(times) / len(times), "phi": phi_d.cpu().numpy().copy()}
     near = None
     if not args.no_near and rank == 0:
         near = near_interface_leg(torch, dev, args.p, flush)
@@ -599,6 +677,22 @@ def main():
             forms_out[name]["err2_per_layer_error"] = "%s: %s" % (type(exc).__name__, exc)
         if r["surrogate_train_s"] is not None:
             forms_out[name]["surrogate_train_s"] = r["surrogate_train_s"]
+    matched = None
+    if "fp64" in results and headline != "fp64":
+        fp64_rows = [{"p": args.p, "err2_phi": forms_out["fp64"]["err2_phi"],
+                      "particles_per_s": forms_out["fp64"]["particles_per_s"]}]
+        for pm, r in matched_runs.items():
+            fp64_rows.append({"p": pm, "err2_phi": oracle.err2(ref, r["phi"][t]),
+                              "particles_per_s": w.n / (r["ms_per_step"] / 1e3)})
+        fp64_rows.sort(key=lambda d: d["p"])
+        target = forms_out[headline]["err2_phi"]
+        ok = [d for d in fp64_rows if d["err2_phi"] <= target]
+        best = ok[0] if ok else None
+        matched = {"headline_p": args.p, "headline_err2_phi": target, "fp64": fp64_rows,
+                   "fp64_p_at_matched_accuracy": best["p"] if best else None,
+                   "speedup_vs_fp64_at_matched_accuracy": (value / world / best["particles_per_s"]) if best else None,
+                   "note": "the smallest FP64 order whose Err2(phi) on the same oracle sample is at most the "
+                           "headline form's; speedup = headline particles/s / that FP64 form's"}
     st = results[headline]["stats"]
     tim = results[headline]["timings"]
     flops = st["m2l_free"] * m2l_flops_per_pair(args.p)
@@ -622,6 +716,21 @@ def main():
                 "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
                 "peak_note": "FP32 CUDA-core peak from unit counts (152 SMs x 128 lanes x 2 flops) at the max SM "
                              "clock seen; algorithmic flops = 8 (p+1)^2 (p+1)(p+2)/2 per box pair"}
+    roof_p2p = None
+    if results[headline].get("near_alone_ms"):
+        pairs = st["p2p_free"] + st["p2p_reaction"]
+        t_near = results[headline]["near_alone_ms"]
+        sm_mhz = (clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0)
+        pk = fp32_peak_tflops(sm_mhz)
+        ach = pairs * 20 / (t_near / 1e3) / 1e12
+        roof_p2p = {"kernel": "k_p2p_free_staged (float32 near field, free space)" if st["p2p_reaction"] == 0
+                    else "near field (float32, with reaction pairs)",
+                    "bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                    "traffic": None, "pairs": pairs, "ms": t_near,
+                    "peak_note": "FP32 CUDA-core peak from unit counts (152 SMs x 128 lanes x 2 flops) at the median "
+                                 "SM clock sampled in the timed region; algorithmic flops = 20 per near pair "
+                                 "(potential and field); duration = CUDA events around the near field run alone "
+                                 "(not beside the far field), after the timed steps"}
     line = {
         "metric": METRIC,
         "value": value,
@@ -643,6 +752,7 @@ def main():
                  "targets": int(len(t)), "reference": "CPU oracle (FP64 direct sum, exact image series)"},
         "forms": forms_out,
         "roofline": roof,
+        "roofline_near_field": roof_p2p,
         "cpu_baseline": {"value": len(t) / dt, "unit": "particles/s", "cores": threads, "kind": "oracle",
                          "sample": "%d targets (seeded subsample) x all %d sources, exact three-layer image "
                                    "series, %.1f s" % (len(t), w.n, dt)},
@@ -653,6 +763,7 @@ def main():
                             "near_reaction_pairs": int(st.get("p2p_reaction", 0))},
         "gpu_launches": results[headline]["launches"],
         "clocks": clk,
+        "matched_accuracy": matched,
         "near_interface": near,
         "multi_rhs": multi,
         "many_problems": many,

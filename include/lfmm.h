@@ -64,8 +64,18 @@ enum {
     LFMM_OPT_TC_GROUPS = 9,     /* tensor-core free M2L: CTAs per 256-target tile, each summing 189/groups
                                    offsets in its tensor-memory accumulator before a float atomic add;
                                    a divisor of 189 (default 27: 7 offsets per accumulation) */
-    LFMM_OPT_NEAR_TABLES = 10   /* 1 = near-field reaction kernels with their remainder from pre-computed
+    LFMM_OPT_NEAR_TABLES = 10,  /* 1 = near-field reaction kernels with their remainder from pre-computed
                                    tables (built on first use, see lfmm_near_tables); 0 = quadrature (default) */
+    LFMM_OPT_TC_PERSISTENT = 11, /* tensor-core free M2L: 1 = one persistent CTA per SM walking the
+                                   (tile, offset group) units with a double-buffered accumulator, for
+                                   launches of at least 4 units per SM (default); 0 = one CTA per unit
+                                   always.  Same arithmetic and result either way. */
+    LFMM_OPT_P2P_STAGED = 12,   /* float32 near field with one charge vector and no reaction pairs in the near
+                                   lists: 1 = each warp stages its leaf's whole near list once (default);
+                                   0 = staging per source box.  Same pairs either way. */
+    LFMM_OPT_SERIAL_NEAR = 13   /* 1 = run the near field on the calling stream before the far field instead
+                                   of beside it (then its stage time in lfmm_get_timings is the near-field
+                                   kernels' own duration); 0 = concurrent (default).  Same result. */
 };
 
 /* Create a context for the medium.
@@ -213,6 +223,25 @@ enum {
     LFMM_BATCH_INFO_COUNT = 8
 };
 lfmm_status lfmm_batch_info(lfmm_batch* b, int64_t* out, int nout);
+
+/* Tune the batch as a whole: a coordinate search over settings applied to
+ * every member, each timed as the median of `reps` (>= 1) graph replays of
+ * the whole batch (CUDA events on the batch's stream, after the direct run
+ * and capture a changed setting brings), with unit charges:
+ *   1. tensor-core free M2L (float32 form) for every member, for none, or for
+ *      the members of at least 20,000 / 60,000 charges;
+ *   2. near-list split of the P2P kernels: automatic, 1, 2, 4, 8;
+ *   3. near-field reaction kernels from the pre-computed tables (members
+ *      whose near lists hold reaction pairs; see lfmm_near_tables).
+ * A member tuned alone picks the settings that fill the GPU with its own
+ * work; in a batch the members fill it together, which is what this times.
+ * Afterwards every member holds the winner.  Needs use_graph = 1.
+ *   report : host [max_rows][LFMM_BATCH_TUNE_COLS] or NULL: smallest member
+ *            size on the tensor cores (> every size: none), split, tables,
+ *            milliseconds, 1 for the winner.
+ *   nrows  : rows written (may be NULL). */
+#define LFMM_BATCH_TUNE_COLS 5
+lfmm_status lfmm_batch_autotune(lfmm_batch* b, int reps, double* report, int max_rows, int* nrows);
 
 /* Message of the last failed batch call ("" if none). */
 const char* lfmm_batch_last_error(const lfmm_batch* b);

@@ -765,6 +765,18 @@ static lfmm_status set_option(lfmm_ctx* ctx, int opt, double v)
     case LFMM_OPT_TENSOR_CORES:
         ctx->use_tc = (v != 0.0);
         return LFMM_OK;
+    case LFMM_OPT_SERIAL_NEAR:
+        if (v != 0.0 && v != 1.0) return fail(ctx, "EINVAL: serial near-field option must be 0 or 1");
+        ctx->serial_near = (v != 0.0);
+        return LFMM_OK;
+    case LFMM_OPT_P2P_STAGED:
+        if (v != 0.0 && v != 1.0) return fail(ctx, "EINVAL: staged near-field option must be 0 or 1");
+        ctx->p2p_staged = (v != 0.0);
+        return LFMM_OK;
+    case LFMM_OPT_TC_PERSISTENT:
+        if (v != 0.0 && v != 1.0) return fail(ctx, "EINVAL: persistent tensor-core option must be 0 or 1");
+        ctx->tc_persistent = (v != 0.0);
+        return LFMM_OK;
     case LFMM_OPT_NEAR_TABLES:
         if (v != 0.0 && v != 1.0) return fail(ctx, "EINVAL: near tables option must be 0 or 1");
         if (v == 1.0 && !ctx->near_tab_ready) {

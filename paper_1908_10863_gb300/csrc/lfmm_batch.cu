@@ -9,7 +9,9 @@
 // following evaluations are a single cudaGraphLaunch in which the problems'
 // kernels run as concurrent branches.  No allocation and no host
 // synchronisation happen inside the captured region.
+#include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "lfmm_ctx.h"
 
@@ -242,6 +244,137 @@ lfmm_status lfmm_batch_evaluate(lfmm_batch* b, const double* q, double* phi, dou
     for (size_t i = 0; i < tmo.size(); ++i)
         if (tmo[i])
             return bfail(b, "ETIMEOUT: a device wait of problem " + std::to_string(i) + " ran out", LFMM_ETIMEOUT);
+    return LFMM_OK;
+}
+
+// One candidate setting applied to every member: tensor-core free M2L for the
+// members with at least tc_min charges (float32 form), near-list split, and
+// the pre-computed near-field tables for members whose near lists hold
+// reaction pairs.
+struct BatchSetting {
+    int64_t tc_min;
+    int split;
+    int tables;
+};
+
+static lfmm_status apply_setting(lfmm_batch* b, const BatchSetting& s)
+{
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+        lfmm_ctx* c = b->ctx[i];
+        lfmm_status st = lfmm_set_option(c, LFMM_OPT_TENSOR_CORES, c->n >= s.tc_min ? 1.0 : 0.0);
+        if (st == LFMM_OK) st = lfmm_set_option(c, LFMM_OPT_P2P_SPLIT, (double)s.split);
+        const bool tab = s.tables && c->stats[LFMM_STAT_P2P_REACTION] > 0;
+        if (st == LFMM_OK) st = lfmm_set_option(c, LFMM_OPT_NEAR_TABLES, tab ? 1.0 : 0.0);
+        if (st != LFMM_OK) return bfail(b, "problem " + std::to_string(i) + ": " + c->err, st);
+    }
+    return LFMM_OK;
+}
+
+// Median milliseconds of `reps` graph replays of the whole batch (after the
+// direct run and capture that a changed setting brings).
+static lfmm_status time_batch(lfmm_batch* b, int reps, double* ms)
+{
+    double* q = b->q_stage.as<double>();
+    double* phi = b->phi_stage.as<double>();
+    double* fld = b->fld_stage.as<double>();
+    lfmm_status st = run(b, q, phi, fld);  // direct run + capture
+    if (st == LFMM_OK) st = run(b, q, phi, fld);  // one replay
+    if (st != LFMM_OK) return st;
+    std::vector<float> t;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    for (int r = 0; r < reps && ce == cudaSuccess; ++r) {
+        ce = cudaEventRecord(e0, b->s);
+        if (ce == cudaSuccess && (st = run(b, q, phi, fld)) != LFMM_OK) break;
+        if (ce == cudaSuccess) ce = cudaEventRecord(e1, b->s);
+        if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+        float v = 0.f;
+        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&v, e0, e1);
+        t.push_back(v);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st != LFMM_OK) return st;
+    if (ce != cudaSuccess) return bfail(b, lf_cuda(ce, "batch timing"), LFMM_ECUDA);
+    std::sort(t.begin(), t.end());
+    *ms = t[t.size() / 2];
+    return LFMM_OK;
+}
+
+lfmm_status lfmm_batch_autotune(lfmm_batch* b, int reps, double* report, int max_rows, int* nrows)
+{
+    if (!b) return LFMM_EINVAL;
+    b->err.clear();
+    if (nrows) *nrows = 0;
+    if (reps < 1 || (report && max_rows < 0)) return bfail(b, "EINVAL: reps >= 1", LFMM_EINVAL);
+    if (!b->use_graph) return bfail(b, "ESTATE: the tuner times graph replays (use_graph = 1)", LFMM_ESTATE);
+    const int64_t n = b->off.back();
+    // unit charges (timing does not depend on the values) in the batch's staging buffers
+    LfErr e = lf_reserve(b->q_stage, (size_t)n * 8);
+    if (e.empty()) e = lf_reserve(b->phi_stage, (size_t)n * 8);
+    if (e.empty()) e = lf_reserve(b->fld_stage, (size_t)n * 24);
+    if (!e.empty()) return bfail(b, e, LFMM_ENOMEM);
+    {
+        std::vector<double> ones((size_t)n, 1.0);
+        cudaError_t ce = cudaMemcpyAsync(b->q_stage.ptr, ones.data(), (size_t)n * 8, cudaMemcpyHostToDevice, b->s);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(b->s);
+        if (ce != cudaSuccess) return bfail(b, lf_cuda(ce, "tuning charges"), LFMM_ECUDA);
+    }
+    int64_t nmax = 0;
+    for (lfmm_ctx* c : b->ctx) nmax = std::max<int64_t>(nmax, c->n);
+    std::vector<double> rows;
+    auto timed = [&](const BatchSetting& s, double* ms) -> lfmm_status {
+        lfmm_status st = apply_setting(b, s);
+        if (st == LFMM_OK) st = time_batch(b, reps, ms);
+        if (st == LFMM_OK) {
+            const double r[LFMM_BATCH_TUNE_COLS] = {(double)std::min<int64_t>(s.tc_min, nmax + 1), (double)s.split,
+                                                    (double)s.tables, *ms, 0.0};
+            rows.insert(rows.end(), r, r + LFMM_BATCH_TUNE_COLS);
+        }
+        return st;
+    };
+    BatchSetting best{0, 0, 0};
+    double best_ms = 0.0;
+    lfmm_status st = timed(best, &best_ms);
+    size_t best_row = 0;
+    // 1. which members take the tensor-core free M2L (all, none, the larger ones)
+    const int64_t tcs[3] = {nmax + 1, 20000, 60000};
+    for (int i = 0; i < 3 && st == LFMM_OK; ++i) {
+        BatchSetting s = best;
+        s.tc_min = tcs[i];
+        double ms = 0.0;
+        st = timed(s, &ms);
+        if (st == LFMM_OK && ms < best_ms) best = s, best_ms = ms, best_row = rows.size() / LFMM_BATCH_TUNE_COLS - 1;
+    }
+    // 2. near-list split
+    const int splits[4] = {1, 2, 4, 8};
+    for (int i = 0; i < 4 && st == LFMM_OK; ++i) {
+        BatchSetting s = best;
+        s.split = splits[i];
+        double ms = 0.0;
+        st = timed(s, &ms);
+        if (st == LFMM_OK && ms < best_ms) best = s, best_ms = ms, best_row = rows.size() / LFMM_BATCH_TUNE_COLS - 1;
+    }
+    // 3. near-field reaction kernels from the pre-computed tables
+    if (st == LFMM_OK) {
+        BatchSetting s = best;
+        s.tables = 1;
+        double ms = 0.0;
+        st = timed(s, &ms);
+        if (st == LFMM_OK && ms < best_ms) best = s, best_ms = ms, best_row = rows.size() / LFMM_BATCH_TUNE_COLS - 1;
+    }
+    if (st == LFMM_OK) st = apply_setting(b, best);
+    if (st != LFMM_OK) return st;
+    rows[best_row * LFMM_BATCH_TUNE_COLS + 4] = 1.0;
+    const int nr = (int)(rows.size() / LFMM_BATCH_TUNE_COLS);
+    if (report) {
+        const int w = std::min(nr, max_rows);
+        std::copy(rows.begin(), rows.begin() + (size_t)w * LFMM_BATCH_TUNE_COLS, report);
+        if (nrows) *nrows = w;
+    } else if (nrows) {
+        *nrows = nr;
+    }
     return LFMM_OK;
 }
 

@@ -104,6 +104,12 @@ struct lfmm_ctx {
     DevBuf pos_rel;  // float4 per sorted charge: offset from its leaf centre
     DevBuf leaf_of;  // leaf (global box id) of each sorted charge
     DevBuf level_consts;  // float4 [LFMM_MAXCOMP][16]: (K, F, G, Z) of the list tests, in box units
+    DevBuf p2p_consts;    // float4 [LFMM_MAXCOMP]: (s, K, is_free, 0) at the leaf level, for the float32 near field
+    int tc_persistent = 1;     // free M2L on the tensor cores: persistent kernel (1) or one CTA per work unit (0)
+    int num_sms = 152;
+    int p2p_staged = 1;        // float32 free-space near field: staged-list kernel (1) or per-box staging (0)
+    int serial_near = 0;       // 1: near field on the calling stream before the far field (no overlap)
+    int leaf_int_offsets = 0;  // 1: every polarization image of a leaf box is a leaf grid cell (K integral)
     DevBuf flags, idx;  // temporaries
 
     // lists: offsets per level box (near_off[level_box] relative to level base) and entries
@@ -125,6 +131,7 @@ struct lfmm_ctx {
     int l2l_tile_base = 0, shift_ready = 0;
     std::vector<int4> m2l_tiles_h, l2l_tiles_h, m2m_tiles_h, tc_tiles_h;  // host staging of asynchronous uploads
     std::vector<float4> level_consts_h;
+    std::vector<float4> p2p_consts_h;
     void* host_pin = nullptr;  // small pinned host buffer for readbacks that must not wait
     DevBuf near_tab;            // remainder tables of the near-field reaction kernels
     int near_tab_ready = 0, use_near_tab = 0;

@@ -687,16 +687,26 @@ LfErr lf_evaluate_sorted(lfmm_ctx* ctx, int nrhs, const double* q_dev, double* p
         ++ctx->launches, k_gather_q<double><<<g1, 256, 0, st>>>(q_dev, ctx->perm.as<int32_t>(), n,
                                                                ctx->q_sorted.as<double>());
     LF_TRY(lf_cuda(cudaGetLastError(), "gather q"));
-    // near field on its own stream, concurrent with the far field
-    LF_CHECK(cudaEventRecord(ctx->ev_fork, st));
-    LF_CHECK(cudaStreamWaitEvent(ctx->s_near, ctx->ev_fork, 0));
-    LF_TRY(lf_near_field(ctx, ctx->s_near));
-    LF_CHECK(cudaEventRecord(ctx->ev_join, ctx->s_near));
-    if (ctx->precision)
-        LF_TRY(far_field<float>(ctx, st));
-    else
-        LF_TRY(far_field<double>(ctx, st));
-    LF_CHECK(cudaStreamWaitEvent(st, ctx->ev_join, 0));
+    if (ctx->serial_near) {
+        // near field alone on the calling stream, before the far field (its
+        // stage time is then the near-field kernels' own duration)
+        LF_TRY(lf_near_field(ctx, st));
+        if (ctx->precision)
+            LF_TRY(far_field<float>(ctx, st));
+        else
+            LF_TRY(far_field<double>(ctx, st));
+    } else {
+        // near field on its own stream, concurrent with the far field
+        LF_CHECK(cudaEventRecord(ctx->ev_fork, st));
+        LF_CHECK(cudaStreamWaitEvent(ctx->s_near, ctx->ev_fork, 0));
+        LF_TRY(lf_near_field(ctx, ctx->s_near));
+        LF_CHECK(cudaEventRecord(ctx->ev_join, ctx->s_near));
+        if (ctx->precision)
+            LF_TRY(far_field<float>(ctx, st));
+        else
+            LF_TRY(far_field<double>(ctx, st));
+        LF_CHECK(cudaStreamWaitEvent(st, ctx->ev_join, 0));
+    }
     ++ctx->launches, k_combine<<<g1, 256, 0, st>>>(n, ctx->perm.as<int32_t>(), ctx->phi_far.as<double>(),
                                                     ctx->phi_near.as<double>(), ctx->fld_far.as<double>(),
                                                     ctx->fld_near.as<double>(), phi_dev, field_dev);

@@ -441,7 +441,7 @@ struct GemmArgs {
     size_t mstride, lstride;  // per right-hand side (blockIdx.y), in elements
 };
 
-template <typename R, int RM>
+template <typename R, int RM, bool COMPF = false>
 __global__ void __launch_bounds__(G_T) k_m2l_gemm(GemmArgs g)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -462,11 +462,22 @@ __global__ void __launch_bounds__(G_T) k_m2l_gemm(GemmArgs g)
     const R* M = reinterpret_cast<const R*>(g.M) + (size_t)blockIdx.y * g.mstride;
     R* L = reinterpret_cast<R*>(g.L) + (size_t)blockIdx.y * g.lstride;
     if (tid < G_TB) s_tb[tid] = (tid < cnt) ? (g.sorted ? g.sorted[start + tid] : start + tid) : -1;
-    R acc[RM][4];
+    // float32 free M2L (COMPF): each offset's products are summed into a
+    // fresh partial, which is then added into the total with compensation
+    // (Kahan), so that the rounding of the (p+1)^2 x 189 additions per output
+    // does not pile up in one float.  FP64, and the translations between
+    // levels (at most 8 offsets), sum directly.
+    constexpr bool COMP = COMPF && sizeof(R) == 4;
+    constexpr int RC = COMP ? RM : 1;
+    R acc[RM][4], part[RC][4], cmp[RC][4];
 #pragma unroll
     for (int r = 0; r < RM; ++r)
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[r][c] = 0;
+#pragma unroll
+    for (int r = 0; r < RC; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) part[r][c] = cmp[r][c] = 0;
     __syncthreads();
     const int noff = g.noff;
     const int oi0 = g.split ? (int)blockIdx.x % noff : 0, oi1 = g.split ? oi0 + 1 : noff;
@@ -517,10 +528,33 @@ __global__ void __launch_bounds__(G_T) k_m2l_gemm(GemmArgs g)
 #pragma unroll
                 for (int r = 0; r < RM; ++r)
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) acc[r][c] += a[r] * x[c];
+                    for (int c = 0; c < 4; ++c) {
+                        if constexpr (COMP)
+                            part[r][c] += a[r] * x[c];
+                        else
+                            acc[r][c] += a[r] * x[c];
+                    }
             }
         }
         __syncthreads();
+        if constexpr (COMP) {
+#pragma unroll
+            for (int r = 0; r < RM; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const R y = part[r][c] - cmp[r][c];
+                    const R t = acc[r][c] + y;
+                    cmp[r][c] = (t - acc[r][c]) - y;
+                    acc[r][c] = t;
+                    part[r][c] = 0;
+                }
+        }
+    }
+    if constexpr (COMP) {
+#pragma unroll
+        for (int r = 0; r < RM; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[r][c] -= cmp[r][c];
     }
     const R ih = (g.mode == 0) ? (R)(1.0 / g.levelh[level]) : R(1);
 #pragma unroll
@@ -551,9 +585,20 @@ static LfErr launch_gemm(lfmm_ctx* ctx, cudaStream_t st, const GemmArgs& g, int 
     if (ntiles <= 0) return LfErr();
     constexpr int RP = 16 * RM;
     size_t sm = sizeof(R) * ((size_t)G_KC * RP + (size_t)G_TB * (RP + 1));
-    LF_CHECK(cudaFuncSetAttribute(k_m2l_gemm<R, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const int nblk = g.split ? ntiles * g.noff : ntiles;
-    ++ctx->launches, k_m2l_gemm<R, RM><<<dim3(nblk, ctx->nrhs_b), G_T, sm, st>>>(g);
+    // compensated sums where one block adds many offsets into one output
+    if constexpr (sizeof(R) == 4) {
+        if (g.noff == G_NOFF && !g.split) {
+            LF_CHECK(cudaFuncSetAttribute(k_m2l_gemm<R, RM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)sm));
+            ++ctx->launches, k_m2l_gemm<R, RM, true><<<dim3(nblk, ctx->nrhs_b), G_T, sm, st>>>(g);
+            return lf_cuda(cudaGetLastError(), "gathered gemm");
+        }
+    }
+    {
+        LF_CHECK(cudaFuncSetAttribute(k_m2l_gemm<R, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        ++ctx->launches, k_m2l_gemm<R, RM><<<dim3(nblk, ctx->nrhs_b), G_T, sm, st>>>(g);
+    }
     return lf_cuda(cudaGetLastError(), "gathered gemm");
 }
 

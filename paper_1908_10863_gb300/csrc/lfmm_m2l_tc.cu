@@ -285,6 +285,10 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MINB) k_m2l_tc(TcArgs g)
         const int rot = (item / g.groups) % goff;
         int armed = 0;         // stages with a bulk copy issued by this thread, for the bounded drain
         int my_src = -1;       // source of row (warp * 32 + lane) at the current offset
+        // the source at the next offset is loaded one offset ahead (its
+        // latency hides behind the current offset's gathers)
+        const int my_tb = s_tb[warp * 32 + lane];
+        int nxt_src = (my_tb >= 0) ? g.slots[(size_t)my_tb * g.noff + grp * goff + rot % goff] : -1;
         int it = 0;
         for (; it < nstage; ++it) {
             const int s = it % TC_STAGES, round = it / TC_STAGES;
@@ -302,8 +306,9 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MINB) k_m2l_tc(TcArgs g)
                 armed = it + 1;
             }
             if (kc == 0) {
-                const int tb = s_tb[warp * 32 + lane];
-                my_src = (tb >= 0) ? g.slots[(size_t)tb * g.noff + oi] : -1;
+                my_src = nxt_src;
+                const int on = it / TC_NKC + 1;
+                if (on < goff && my_tb >= 0) nxt_src = g.slots[(size_t)my_tb * g.noff + grp * goff + (on + rot) % goff];
             }
             // 32 rows x 2 pieces x 4 chunks of 16 B per warp: 8 per lane
             unsigned char* xs = st + TC_AP * TC_A_BYTES;
@@ -408,6 +413,240 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MINB) k_m2l_tc(TcArgs g)
 }
 
 // ---------------------------------------------------------------------------
+// Persistent form of the free M2L (one CTA per SM).
+//
+// The work units are the (tile, offset group) pairs of k_m2l_tc; each CTA
+// walks units u = blockIdx.x, blockIdx.x + gridDim.x, ... with one pipeline
+// that never drains between units:
+//   warps 0..7   producers: operator chunk by bulk copy, multipole rows by
+//                16-byte cp.async gathers, TCP_STAGES stages of 48 KB, each
+//                handed to the tensor cores TCP_LAG stages after its copies
+//                start (stage counter global over the CTA's units);
+//   warp 8       one thread issues the MMAs of a unit into one of two
+//                256-column tensor-memory accumulators (unit parity), and
+//                commits the unit to that accumulator's "full" barrier;
+//   warps 9..12  epilogue: read the finished accumulator (tcgen05.ld; warp w
+//                reads lanes 32 (w mod 4) .. + 31), scale by 1/h and add into
+//                the local expansions, then release the accumulator, while
+//                the tensor cores already work on the next unit.
+// Same arithmetic, offset groups and error behaviour as k_m2l_tc; every
+// barrier wait is bounded as there.
+// ---------------------------------------------------------------------------
+#ifndef TCP_STAGES
+#define TCP_STAGES 4
+#endif
+#ifndef TCP_LAG
+#define TCP_LAG 2
+#endif
+#define TCP_EPI_WARPS 4
+#define TCP_THREADS (32 * (TC_PROD_WARPS + 1 + TCP_EPI_WARPS))
+#define TCP_SMEM (TCP_STAGES * TC_STAGE_BYTES + 1024)
+#define TCP_TMEM_COLS 512
+
+__global__ void __launch_bounds__(TCP_THREADS, 1) k_m2l_tcp(TcArgs g, int nunits)
+{
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                         ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full_bar[TCP_STAGES], empty_bar[TCP_STAGES], accf_bar[2], acce_bar[2];
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int goff = g.noff / g.groups;
+    const int nstage = goff * TC_NKC;  // stages per unit
+    const int nc = g.nc;
+
+    if (tid == 0) {
+        for (int s = 0; s < TCP_STAGES; ++s) {
+            mbar_init(&full_bar[s], TC_PROD_WARPS + 1);  // one arrival per producer warp + the bulk copy's
+            mbar_init(&empty_bar[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf_bar[b], 1);              // the MMA thread's commit
+            mbar_init(&acce_bar[b], TCP_EPI_WARPS);  // one arrival per epilogue warp
+        }
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == TC_PROD_WARPS) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(TCP_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+
+    if (warp < TC_PROD_WARPS) {
+        // ---------------- producers ----------------
+        const int row = warp * 32 + lane;  // this thread's target row of every tile
+        int armed = 0;                     // stages with a bulk copy issued by this thread
+        int it = 0;                        // global stage counter
+        bool stop = false;
+        for (int u = blockIdx.x; u < nunits && !stop; u += gridDim.x) {
+            const int4 tile = g.tiles[u / g.groups];
+            const int grp = u % g.groups;
+            const int cl = tile.y, start = tile.z, cnt = tile.w;
+            const int my_tb = (row < cnt) ? (g.sorted ? g.sorted[start + row] : start + row) : -1;
+            const int rot = (u / g.groups) % goff;
+            int my_src = -1;
+            // the source at the next offset is loaded one offset ahead
+            int nxt_src = (my_tb >= 0) ? g.slots[(size_t)my_tb * g.noff + grp * goff + rot % goff] : -1;
+            for (int j = 0; j < nstage; ++j, ++it) {
+                const int s = it % TCP_STAGES, round = it / TCP_STAGES;
+                const int oi = grp * goff + (j / TC_NKC + rot) % goff, kc = j % TC_NKC;
+                if (it >= TCP_STAGES) {
+                    if (!mbar_wait(&empty_bar[s], (round - 1) & 1)) atomicExch(&s_abort, 1);
+                }
+                if (__any_sync(0xffffffffu, *(volatile int*)&s_abort)) {  // warp-uniform
+                    stop = true;
+                    break;
+                }
+                unsigned char* st = sm + (size_t)s * TC_STAGE_BYTES;
+                if (row == 0) {
+                    const int o = g.cls[cl * g.noff + oi];
+                    mbar_arrive_tx(&full_bar[s], TC_AP * TC_A_BYTES);
+                    bulk_g2s(st, g.A + ((size_t)o * TC_NKC + kc) * (TC_AP * TC_A_BYTES), TC_AP * TC_A_BYTES,
+                             &full_bar[s]);
+                    armed = it + 1;
+                }
+                if (kc == 0) {
+                    my_src = nxt_src;
+                    const int on = j / TC_NKC + 1;
+                    if (on < goff && my_tb >= 0)
+                        nxt_src = g.slots[(size_t)my_tb * g.noff + grp * goff + (on + rot) % goff];
+                }
+                unsigned char* xs = st + TC_AP * TC_A_BYTES;
+                const uint32_t xbase = smem_u32(xs);
+#pragma unroll
+                for (int i = 0; i < 2 * TC_RCH; ++i) {
+                    const int piece = i / TC_RCH;
+                    const int flat = (i % TC_RCH) * 32 + lane;  // chunk-major over the warp's 32 rows
+                    const int rl = flat / TC_RCH, chunk = flat % TC_RCH;
+                    const int src = __shfl_sync(0xffffffffu, my_src, rl);
+                    const int r = warp * 32 + rl;
+                    const uint32_t off = piece * TC_X_BYTES + swz(r, chunk * 4);
+                    if (src >= 0) {
+                        const float* gsrc = g.Ms + (size_t)blockIdx.y * g.ms_stride +
+                                            ((size_t)src * TC_XP + piece) * TC_MROW + kc * TC_KC + chunk * 4;
+                        cp_async16(xbase + off, gsrc);
+                    } else {
+                        *reinterpret_cast<float4*>(xs + off) = make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                }
+                cp_async_commit();
+                if (it >= TCP_LAG) {
+                    cp_async_wait<TCP_LAG>();
+                    fence_async_smem();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&full_bar[(it - TCP_LAG) % TCP_STAGES]);
+                }
+            }
+        }
+        cp_async_wait<0>();
+        fence_async_smem();
+        __syncwarp();
+        if (lane == 0)
+            for (int j = (it > TCP_LAG ? it - TCP_LAG : 0); j < it; ++j) mbar_arrive(&full_bar[j % TCP_STAGES]);
+        // drain: the bulk copies this thread issued complete on their full barriers
+        if (row == 0 && *(volatile int*)&s_abort) {
+            for (int j = (armed > TCP_STAGES ? armed - TCP_STAGES : 0); j < armed; ++j)
+                mbar_wait(&full_bar[j % TCP_STAGES], (j / TCP_STAGES) & 1);
+        }
+    } else if (warp == TC_PROD_WARPS) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            const uint32_t idesc = tc_idesc(TC_M, TC_N);
+            int it = 0, ul = 0;
+            bool ok = true;
+            for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x, ++ul) {
+                const int b = ul & 1;
+                if (ul >= 2 && !mbar_wait(&acce_bar[b], ((ul >> 1) - 1) & 1)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t acc = tmem + (uint32_t)(b * TC_N);
+                for (int j = 0; j < nstage; ++j, ++it) {
+                    const int s = it % TCP_STAGES, round = it / TCP_STAGES;
+                    if (!mbar_wait(&full_bar[s], round & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t base = smem_u32(sm + (size_t)s * TC_STAGE_BYTES);
+                    const uint32_t xb = base + TC_AP * TC_A_BYTES;
+                    const int pa[3] = {0, 0, 1}, px[3] = {0, 1, 0};  // a1 x1, a1 x2, a2 x1
+#pragma unroll
+                    for (int prod = 0; prod < 3; ++prod) {
+                        const uint32_t a = base + pa[prod] * TC_A_BYTES;
+                        const uint32_t bb = xb + px[prod] * TC_X_BYTES;
+#pragma unroll
+                        for (int ks = 0; ks < TC_KC / 8; ++ks)
+                            tc_mma(acc, smem_desc(a + 32 * ks), smem_desc(bb + 32 * ks), idesc,
+                                   (j | prod | ks) != 0 ? 1u : 0u);
+                    }
+                    tc_commit(&empty_bar[s]);
+                }
+                if (!ok) break;
+                tc_commit(&accf_bar[b]);
+            }
+            if (!ok) atomicExch(&s_abort, 1);
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue ----------------
+        // (no barrier between the epilogue warps: each decides on its own,
+        // so a warp that gives up on a timed-out wait cannot strand another)
+        const int q = warp & 3;  // tensor-memory lanes 32 q .. 32 q + 31
+        const int r = 32 * q + lane;
+        int ul = 0;
+        for (int u = blockIdx.x; u < nunits; u += gridDim.x, ++ul) {
+            const int b = ul & 1;
+            const int4 tile = g.tiles[u / g.groups];
+            const int level = tile.x, start = tile.z, cnt = tile.w;
+            const bool ok = mbar_wait(&accf_bar[b], (ul >> 1) & 1);
+            tc_fence_after();
+            if (!ok || *(volatile int*)&s_abort) {
+                if (lane == 0) atomicAdd(g.err, 1);
+                atomicExch(&s_abort, 1);
+                break;
+            }
+            const float ih = g.unit_scale ? 1.f : (float)(1.0 / g.levelh[level]);
+            float* Lb = g.L + (size_t)blockIdx.y * g.l_stride;
+#pragma unroll 1
+            for (int ch = 0; ch < TC_N / 32; ++ch) {
+                const int col0 = ch * 32;
+                if (col0 >= cnt) break;  // warp-uniform
+                // target box of column col0 + lane, handed to every lane by shuffles
+                const int jl = col0 + lane;
+                const int tbl = (jl < cnt) ? (g.sorted ? g.sorted[start + jl] : start + jl) : -1;
+                float v[32];
+                tc_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * TC_N + col0), v);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const int tb = __shfl_sync(0xffffffffu, tbl, i);
+                    if (r < nc && tb >= 0) atomicAdd(Lb + (size_t)tb * nc + r, v[i] * ih);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce_bar[b]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == TC_PROD_WARPS) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCP_TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Host: operator blob and launch.
 // ---------------------------------------------------------------------------
 static inline uint32_t host_tf32(float x)
@@ -459,6 +698,11 @@ LfErr lf_setup_m2l_tc(lfmm_ctx* ctx, const double* A64, const double* M2M64, con
     LF_TRY(tc_blob(L2L64, 8, KP, RP, nc, ctx->l2l_Atc));
     LF_CHECK(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
     LF_CHECK(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    LF_CHECK(cudaFuncSetAttribute(k_m2l_tcp, cudaFuncAttributeMaxDynamicSharedMemorySize, TCP_SMEM));
+    LF_CHECK(cudaFuncSetAttribute(k_m2l_tcp, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    int nsm = 0;
+    LF_CHECK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
+    ctx->num_sms = nsm > 0 ? nsm : 152;
     ctx->m2l_tc_ok = 1;
     return LfErr();
 }
@@ -521,7 +765,19 @@ LfErr lf_m2l_tc(lfmm_ctx* ctx, cudaStream_t st)
     g.A = ctx->m2l_Atc.as<unsigned char>();
     g.L = ctx->Lexp.as<float>();
     g.groups = ctx->tc_groups;
-    ++ctx->launches, k_m2l_tc<<<dim3(ctx->m2l_tc_ntiles * g.groups, nr), TC_THREADS, TC_SMEM, st>>>(g);
+    const int nunits = ctx->m2l_tc_ntiles * g.groups;
+    // the persistent form pays off when every SM walks many units; a small
+    // tree (or one of many problems sharing the GPU in a batch) keeps one
+    // CTA per unit, two of which share an SM
+    if (ctx->tc_persistent && nunits * nr >= 4 * ctx->num_sms) {
+        // one CTA per SM (shared memory and the 512 tensor-memory columns allow
+        // no second); all right-hand sides share the SMs
+        int per = std::max(1, ctx->num_sms / std::max(1, nr));
+        per = std::min(per, nunits);
+        ++ctx->launches, k_m2l_tcp<<<dim3(per, nr), TCP_THREADS, TCP_SMEM, st>>>(g, nunits);
+    } else {
+        ++ctx->launches, k_m2l_tc<<<dim3(nunits, nr), TC_THREADS, TC_SMEM, st>>>(g);
+    }
     return lf_cuda(cudaGetLastError(), "m2l tensor-core gemm");
 }
 

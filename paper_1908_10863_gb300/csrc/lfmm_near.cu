@@ -59,6 +59,13 @@ struct P2PArgs {
     const double* gl_w;
     const double* ntab;  // remainder tables [component][LF_NT_PER], or null: the quadrature
     LfmmSurrView sv;  // learned near-field kernels (sv.ready = 0: quadrature only)
+    // float32 warp kernel on a leaf level whose polarization images are grid
+    // cells: box grid cells and per component (s, K, is_free) in leaf units,
+    // so that every centre offset is an exact small integer times hleaf (null:
+    // offsets from the FP64 centres)
+    const int4* grid;
+    const float4* pcon;
+    float hleaf;
 };
 #define LF_CTAB(a, c) ((a).ntab ? (a).ntab + (size_t)(c) * LF_NT_PER : nullptr)
 
@@ -260,7 +267,8 @@ __global__ void __launch_bounds__(32 * PW_WARPS) k_p2p_warp(P2PArgs a, const flo
     const int li = wi / a.split, part0 = wi - li * a.split;
     const float* q = reinterpret_cast<const float*>(a.q);
     const int t = a.leaf_off + li;
-    const LfD4 ct = a.cen[t];
+    const LfD4 ct = a.grid ? LfD4{0.0, 0.0, 0.0, 0.0} : a.cen[t];
+    const int4 gt = a.grid ? a.grid[t] : make_int4(0, 0, 0, 0);
     const int tb = a.pbeg[t], te = a.pend[t];
     const int eb = a.nbeg[t], ee = a.nend[t];
     const int nt = te - tb;
@@ -284,11 +292,23 @@ __global__ void __launch_bounds__(32 * PW_WARPS) k_p2p_warp(P2PArgs a, const flo
             const int c = (int)(ent >> LFMM_ENT_SHIFT);
             const int s = (int)(ent & LFMM_ENT_MASK);
             const LfmmComp& cp = a.comps[c];
-            const LfD4 cs = a.cen[s];
             // source box centre (free) or its polarization image (reaction), relative to the target box
-            const float dx0 = (float)(cs.x - ct.x), dy0 = (float)(cs.y - ct.y);
-            const float dz0 = (float)(cp.is_free ? cs.z - ct.z : cp.s * cs.z + cp.o - ct.z);
-            const float szs = cp.is_free ? 1.f : (float)cp.s;
+            float dx0, dy0, dz0, szs;
+            if (a.grid) {
+                // (z_t - z'') / h = (iz_t + 1/2) - s (iz_s + 1/2) - K with K an integer on this level
+                const int4 gs = a.grid[s];
+                const float4 pc = a.pcon[c];
+                szs = pc.x;
+                dx0 = (float)(gs.x - gt.x) * a.hleaf;
+                dy0 = (float)(gs.y - gt.y) * a.hleaf;
+                dz0 = (pc.x * ((float)gs.z + 0.5f) - ((float)gt.z + 0.5f) + pc.y) * a.hleaf;
+            } else {
+                const LfD4 cs = a.cen[s];
+                dx0 = (float)(cs.x - ct.x);
+                dy0 = (float)(cs.y - ct.y);
+                dz0 = (float)(cp.is_free ? cs.z - ct.z : cp.s * cs.z + cp.o - ct.z);
+                szs = cp.is_free ? 1.f : (float)cp.s;
+            }
             const int sb = a.pbeg[s], se = a.pend[s];
             for (int cb = sb; cb < se; cb += 32) {
                 const int j = cb + lane;
@@ -369,6 +389,246 @@ __global__ void __launch_bounds__(32 * PW_WARPS) k_p2p_warp(P2PArgs a, const flo
             }
         }
         if (valid && slice == 0) p2p_store<float, RB>(a, i, A);
+    }
+}
+
+// Float32 free-space near field, one charge vector, when no near list holds
+// a reaction entry (the benchmark-size trees): one warp per target leaf, as
+// k_p2p_warp, but the warp first stages its whole near list in shared memory
+// (as float offsets from the target leaf centre, with the charge), the
+// leaf's own box first, and then runs one tight loop over the staged sources
+// for each pass of targets.  Only the leaf's own box can hold the target
+// itself, so only its pairs keep the r > 0 test.  Lists of more than PF_CAP
+// sources are staged in rounds of whole boxes (a box larger than PF_CAP in
+// pieces).  Partial sums are compensated every 32 sources.  Box centre
+// offsets come from the integer grid cells (leaf levels whose images are
+// grid cells; this kernel serves free-space entries only).
+#define PF_WARPS 4
+#define PF_CAP 512
+#define PF_UNR 2  // staging loads in flight per lane
+
+struct PfCursor {
+    int k;    // next entry of this warp (index into its strided subsequence), -1: the own box
+    int off;  // sources of that box already staged
+};
+
+// Stage sources from the cursor on, whole boxes while they fit (a box larger
+// than the capacity in pieces).  Returns the staged count; *nself is the
+// number of own-box sources at the front; *more is set if sources remain.
+__device__ __noinline__ int pf_fill(const P2PArgs& a, const float4* __restrict__ rel, const float* __restrict__ q,
+                                       float4* S, int t, int4 gt, int tb, int te, int eb, int nmine, int part0,
+                                       PfCursor& cur, int& nself, bool& more, int lane)
+{
+    int fill = 0;
+    nself = 0;
+    if (cur.k < 0) {  // the own box (zero centre offset)
+        const int n = min(te - tb - cur.off, PF_CAP);
+        for (int u = lane; u < n; u += 32) {
+            const int j = tb + cur.off + u;
+            const float4 r = rel[j];
+            S[u] = make_float4(r.x, r.y, r.z, q[j]);
+        }
+        fill = nself = n;
+        cur.off += n;
+        if (tb + cur.off >= te) {
+            cur.k = 0;
+            cur.off = 0;
+        }
+    }
+    // the other boxes, up to 32 entries at a time: lane j reads entry cur.k + j
+    // (all metadata loads in flight at once), a warp scan places the boxes,
+    // and a flattened copy fills the staging area
+    while (cur.k >= 0 && cur.k < nmine && fill < PF_CAP) {
+        const int j = cur.k + lane;
+        int b0 = 0, n = 0;
+        float dx0 = 0.f, dy0 = 0.f, dz0 = 0.f;
+        if (j < nmine) {
+            const uint32_t ent = a.nent[eb + part0 + j * a.split];
+            const int sb = (int)(ent & LFMM_ENT_MASK);
+            if (sb != t) {  // the own box: staged by the part-0 warp at the front
+                b0 = a.pbeg[sb];
+                n = a.pend[sb] - b0;
+                const int4 gs = a.grid[sb];
+                dx0 = (float)(gs.x - gt.x) * a.hleaf;
+                dy0 = (float)(gs.y - gt.y) * a.hleaf;
+                dz0 = (float)(gs.z - gt.z) * a.hleaf;
+            }
+            if (lane == 0) {  // a box begun in the previous round
+                b0 += cur.off;
+                n -= cur.off;
+            }
+        }
+        int incl = n;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int excl = incl - n;
+        const int room = PF_CAP - fill;
+        // entries that fit whole (incl is non-decreasing over the lanes)
+        const int m = min(__popc(__ballot_sync(0xffffffffu, incl <= room)), nmine - cur.k);
+        if (m == 0) {
+            // the first box alone overflows: next round, or a piece of it
+            if (fill > 0) break;
+            const int n0 = __shfl_sync(0xffffffffu, n, 0), b00 = __shfl_sync(0xffffffffu, b0, 0);
+            const float x0 = __shfl_sync(0xffffffffu, dx0, 0), y0 = __shfl_sync(0xffffffffu, dy0, 0),
+                        z0 = __shfl_sync(0xffffffffu, dz0, 0);
+            const int take = min(n0, room);
+            for (int u = lane; u < take; u += 32) {
+                const float4 r = rel[b00 + u];
+                S[u] = make_float4(r.x + x0, r.y + y0, r.z + z0, q[b00 + u]);
+            }
+            fill = take;
+            cur.off += take;
+            break;
+        }
+        const int tot = __shfl_sync(0xffffffffu, incl, m - 1);
+        // slot u of [0, tot) belongs to the entry e with excl_e <= u < incl_e
+        for (int base = 0; base < tot; base += 32 * PF_UNR) {
+            int src[PF_UNR];
+            float ox[PF_UNR], oy[PF_UNR], oz[PF_UNR];
+#pragma unroll
+            for (int h = 0; h < PF_UNR; ++h) {
+                const int u = base + 32 * h + lane;
+                int lo = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int c = lo + step;
+                    const int ex = __shfl_sync(0xffffffffu, excl, c & 31);
+                    if (c < m && ex <= u) lo = c;
+                }
+                src[h] = __shfl_sync(0xffffffffu, b0, lo) + (u - __shfl_sync(0xffffffffu, excl, lo));
+                ox[h] = __shfl_sync(0xffffffffu, dx0, lo);
+                oy[h] = __shfl_sync(0xffffffffu, dy0, lo);
+                oz[h] = __shfl_sync(0xffffffffu, dz0, lo);
+                if (u >= tot) src[h] = -1;
+            }
+            float4 r[PF_UNR];
+            float qq[PF_UNR];
+#pragma unroll
+            for (int h = 0; h < PF_UNR; ++h)
+                if (src[h] >= 0) {
+                    r[h] = rel[src[h]];
+                    qq[h] = q[src[h]];
+                }
+#pragma unroll
+            for (int h = 0; h < PF_UNR; ++h)
+                if (src[h] >= 0)
+                    S[fill + base + 32 * h + lane] = make_float4(r[h].x + ox[h], r[h].y + oy[h], r[h].z + oz[h], qq[h]);
+        }
+        fill += tot;
+        cur.k += m;
+        cur.off = 0;
+    }
+    more = (cur.k < 0) || (cur.k < nmine);
+    return fill;
+}
+
+// pairs of one target with staged sources [u0, u1), compensated every 32
+template <bool SELF>
+__device__ __forceinline__ void pf_pairs(const float4* S, int u0, int u1, float xi, float yi, float zi,
+                                         P2PAcc<float, 1>& A)
+{
+    for (int c0 = u0; c0 < u1; c0 += 32) {
+        const int c1 = min(c0 + 32, u1);
+        float P = 0.f, Ex = 0.f, Ey = 0.f, Ez = 0.f;
+#pragma unroll 8
+        for (int u = c0; u < c1; ++u) {
+            const float4 v = S[u];
+            const float dx = xi - v.x, dy = yi - v.y, dz = zi - v.z;
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            float ir = rsqrtf(r2);
+            if (SELF) ir = (r2 > 0.f) ? ir : 0.f;  // the target itself: no term
+            const float qi = v.w * ir;
+            const float q3 = qi * ir * ir;
+            P += qi;
+            Ex += q3 * dx;
+            Ey += q3 * dy;
+            Ez += q3 * dz;
+        }
+        A.P[0].add(P);
+        A.Ex[0].add(Ex);
+        A.Ey[0].add(Ey);
+        A.Ez[0].add(Ez);
+    }
+}
+
+__global__ void __launch_bounds__(32 * PF_WARPS, 6) k_p2p_free_staged(P2PArgs a, const float4* __restrict__ rel,
+                                                                    int nleaf)
+{
+    __shared__ float4 sp[PF_WARPS][PF_CAP];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int wi = blockIdx.x * PF_WARPS + w;
+    if (wi >= nleaf * a.split) return;  // whole warp
+    const int li = wi / a.split, part0 = wi - li * a.split;
+    const float* q = reinterpret_cast<const float*>(a.q);
+    float4* S = sp[w];
+    const int t = a.leaf_off + li;
+    const int4 gt = a.grid[t];
+    const int tb = a.pbeg[t], te = a.pend[t];
+    const int eb = a.nbeg[t], ee = a.nend[t];
+    const int nmine = (ee - eb > part0) ? (ee - eb - part0 + a.split - 1) / a.split : 0;
+    const int nt = te - tb;
+    const int lg = nt <= 8 ? 2 : (nt <= 16 ? 1 : 0);  // log2 of the lanes per target (warp-uniform)
+    const int T = 32 >> lg;                          // targets per pass
+    const int ti = lane & (T - 1), slice = lane >> (5 - lg);
+    const PfCursor start{part0 == 0 ? -1 : 0, 0};
+    // the first round stages everything when the list fits: later passes reuse it
+    PfCursor cur = start;
+    int nself = 0;
+    bool more = false;
+    int fill = pf_fill(a, rel, q, S, t, gt, tb, te, eb, nmine, part0, cur, nself, more, lane);
+    const bool once = !more;
+    __syncwarp();
+    for (int base = tb; base < te; base += T) {
+        const int i = base + ti;
+        const bool valid = i < te;
+        float xi = 0.f, yi = 0.f, zi = 0.f;
+        if (valid) {
+            const float4 r = rel[i];
+            xi = r.x;
+            yi = r.y;
+            zi = r.z;
+        }
+        P2PAcc<float, 1> A;
+        if (!once && base != tb) {  // stage the first round again
+            cur = start;
+            __syncwarp();
+            fill = pf_fill(a, rel, q, S, t, gt, tb, te, eb, nmine, part0, cur, nself, more, lane);
+            __syncwarp();
+        }
+        for (;;) {
+            if (valid) {
+                // this lane's contiguous share of the own-box part and of the rest
+                const int a0 = (slice * nself) >> lg, a1 = ((slice + 1) * nself) >> lg;
+                const int nr = fill - nself;
+                const int b0 = nself + ((slice * nr) >> lg), b1 = nself + (((slice + 1) * nr) >> lg);
+                pf_pairs<true>(S, a0, a1, xi, yi, zi, A);
+                pf_pairs<false>(S, b0, b1, xi, yi, zi, A);
+            }
+            if (once || !more) break;
+            __syncwarp();
+            fill = pf_fill(a, rel, q, S, t, gt, tb, te, eb, nmine, part0, cur, nself, more, lane);
+            __syncwarp();
+        }
+        if (lg > 0) {
+            // the lanes of one target meet (every lane takes part in the shuffles)
+            float v0 = A.P[0].s - A.P[0].c, v1 = A.Ex[0].s - A.Ex[0].c;
+            float v2 = A.Ey[0].s - A.Ey[0].c, v3 = A.Ez[0].s - A.Ez[0].c;
+            for (int off = T; off < 32; off <<= 1) {
+                v0 += __shfl_xor_sync(0xffffffffu, v0, off);
+                v1 += __shfl_xor_sync(0xffffffffu, v1, off);
+                v2 += __shfl_xor_sync(0xffffffffu, v2, off);
+                v3 += __shfl_xor_sync(0xffffffffu, v3, off);
+            }
+            A.P[0].s = v0;
+            A.Ex[0].s = v1;
+            A.Ey[0].s = v2;
+            A.Ez[0].s = v3;
+            A.P[0].c = A.Ex[0].c = A.Ey[0].c = A.Ez[0].c = 0.f;
+        }
+        if (valid && slice == 0) p2p_store<float, 1>(a, i, A);
     }
 }
 
@@ -591,6 +851,13 @@ LfErr lf_near_field(lfmm_ctx* ctx, cudaStream_t st)
     a.gl_t = ctx->gl_t_near.as<double>();
     a.gl_w = ctx->gl_w_near.as<double>();
     a.ntab = (ctx->use_near_tab && ctx->near_tab_ready) ? ctx->near_tab.as<double>() : nullptr;
+    a.grid = nullptr;
+    a.pcon = nullptr;
+    a.hleaf = (float)leaf.h;
+    if (ctx->leaf_int_offsets) {
+        a.grid = ctx->box_grid.as<int4>();
+        a.pcon = ctx->p2p_consts.as<float4>();
+    }
     LF_TRY(lf_reserve(ctx->surr_counters, 64));
     LF_CHECK(cudaMemsetAsync(ctx->surr_counters.ptr, 0, 16, st));
     LF_TRY(lf_surrogate_device_view(ctx, &a.sv));
@@ -645,7 +912,10 @@ LfErr lf_near_field(lfmm_ctx* ctx, cudaStream_t st)
         } else if (ctx->precision) {
             const int g = lf_blocks((int64_t)leaf.nbox * split, PW_WARPS), T = 32 * PW_WARPS;
             const float4* rel = ctx->pos_rel.as<float4>();
-            if (a.nr == 1)
+            if (a.nr == 1 && a.grid && ctx->stats[LFMM_STAT_P2P_REACTION] == 0 && ctx->p2p_staged)
+                ++ctx->launches, k_p2p_free_staged<<<lf_blocks((int64_t)leaf.nbox * split, PF_WARPS), 32 * PF_WARPS, 0,
+                                                     st>>>(a, rel, leaf.nbox);
+            else if (a.nr == 1)
                 ++ctx->launches, k_p2p_warp<1><<<g, T, 0, st>>>(a, rel, leaf.nbox);
             else if (a.nr == 2)
                 ++ctx->launches, k_p2p_warp<2><<<g, T, 0, st>>>(a, rel, leaf.nbox);

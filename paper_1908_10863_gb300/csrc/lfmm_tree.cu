@@ -19,6 +19,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <vector>
 
@@ -876,6 +877,24 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
         LF_TRY(lf_reserve(ctx->level_consts, sizeof(float4) * lc.size()));
         LF_CHECK(cudaMemcpyAsync(ctx->level_consts.ptr, lc.data(), sizeof(float4) * lc.size(), cudaMemcpyHostToDevice,
                                  st));
+        // the leaf level's image offsets for the float32 near field: exact
+        // when every K is an integer (interfaces on leaf grid planes)
+        std::vector<float4>& pc = ctx->p2p_consts_h;
+        pc.assign((size_t)LFMM_MAXCOMP, make_float4(0.f, 0.f, 0.f, 0.f));
+        bool integral = depth < 16;
+        const double hl = ctx->levels[depth].h;
+        for (int c = 0; c < ctx->ncomp && integral; ++c) {
+            const LfmmComp& cp = ctx->comp[c];
+            const double K = cp.is_free ? 0.0 : (cp.o + (cp.s - 1.0) * oz) / hl;
+            if (!(std::fabs(K - std::nearbyint(K)) <= 1e-9 * (1.0 + std::fabs(K))) || std::fabs(K) > 1e6) integral = false;
+            pc[c] = make_float4(cp.is_free ? 1.f : (float)cp.s, (float)std::nearbyint(K), (float)cp.is_free, 0.f);
+        }
+        ctx->leaf_int_offsets = integral ? 1 : 0;
+        if (integral) {
+            LF_TRY(lf_reserve(ctx->p2p_consts, sizeof(float4) * pc.size()));
+            LF_CHECK(cudaMemcpyAsync(ctx->p2p_consts.ptr, pc.data(), sizeof(float4) * pc.size(),
+                                     cudaMemcpyHostToDevice, st));
+        }
     }
 
     // ---- lists ----

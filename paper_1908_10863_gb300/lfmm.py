@@ -16,8 +16,10 @@ from . import build as _build
 
 OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETIMEOUT, ENUMERIC = range(7)
 OPT_PRECISION, OPT_LEAF_CAP, OPT_PROFILE, OPT_QUAD_NODES, OPT_SURROGATE, OPT_SURROGATE_TOL = 1, 2, 3, 4, 5, 6
-OPT_TENSOR_CORES, OPT_P2P_SPLIT, OPT_TC_GROUPS, OPT_NEAR_TABLES = 7, 8, 9, 10
+OPT_TENSOR_CORES, OPT_P2P_SPLIT, OPT_TC_GROUPS, OPT_NEAR_TABLES, OPT_TC_PERSISTENT = 7, 8, 9, 10, 11
+OPT_P2P_STAGED, OPT_SERIAL_NEAR = 12, 13
 TUNE_COLS = ["leaf_cap", "tensor_cores", "split", "depth", "ms", "chosen"]
+BATCH_TUNE_COLS = ["tc_min_charges", "split", "tables", "ms", "chosen"]
 STAT_NAMES = ["n", "depth", "boxes", "leaves", "m2l_free", "m2l_reaction", "p2p_free", "p2p_reaction",
               "components", "m2m_edges", "launches", "reaction_keys", "surr_net_pairs", "surr_quad_pairs",
               "timeouts", "reaction_tables"]
@@ -47,7 +49,7 @@ EXPORTED = ["lfmm_create", "lfmm_set_option", "lfmm_build", "lfmm_build_device",
             "lfmm_surrogate_train", "lfmm_surrogate_info", "lfmm_surrogate_eval", "lfmm_surrogate_get_params",
             "lfmm_surrogate_set_params", "lfmm_surrogate_forward", "lfmm_surrogate_loss_grad",
             "lfmm_batch_create", "lfmm_batch_offsets", "lfmm_batch_evaluate_device", "lfmm_batch_evaluate",
-            "lfmm_batch_info", "lfmm_batch_last_error", "lfmm_batch_destroy", "lfmm_autotune",
+            "lfmm_batch_info", "lfmm_batch_autotune", "lfmm_batch_last_error", "lfmm_batch_destroy", "lfmm_autotune",
             "lfmm_check_bounded_wait", "lfmm_near_tables", "lfmm_medium_components"]
 BATCH_INFO = ["problems", "charges", "graph_nodes", "kernel_nodes", "captures", "graph_launches", "direct_runs",
               "timeouts"]
@@ -103,6 +105,7 @@ def load(build: bool = True):
     lib.lfmm_batch_evaluate_device.argtypes = [_vp, _vp, _vp, _vp, _vp]
     lib.lfmm_batch_evaluate.argtypes = [_vp, _dp, _dp, _dp]
     lib.lfmm_batch_info.argtypes = [_vp, _lp, ctypes.c_int]
+    lib.lfmm_batch_autotune.argtypes = [_vp, ctypes.c_int, _dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     lib.lfmm_batch_last_error.argtypes = [_vp]
     lib.lfmm_batch_last_error.restype = ctypes.c_char_p
     lib.lfmm_batch_destroy.argtypes = [_vp]
@@ -444,6 +447,14 @@ class LayeredFMMBatch:
         out = np.zeros(len(BATCH_INFO), dtype=np.int64)
         self._check(self._lib.lfmm_batch_info(self._b, _ptr(out, _lp), len(BATCH_INFO)), "lfmm_batch_info")
         return {k: int(v) for k, v in zip(BATCH_INFO, out)}
+
+    def autotune(self, reps: int = 3):
+        """Tune the batch as a whole (lfmm_batch_autotune); one dict per timed setting."""
+        rows = np.zeros((32, len(BATCH_TUNE_COLS)))
+        n = ctypes.c_int(0)
+        self._check(self._lib.lfmm_batch_autotune(self._b, int(reps), _ptr(rows), 32, ctypes.byref(n)),
+                    "lfmm_batch_autotune")
+        return [dict(zip(BATCH_TUNE_COLS, r)) for r in rows[:n.value]]
 
     def close(self):
         if getattr(self, "_b", None):

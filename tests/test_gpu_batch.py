@@ -174,3 +174,41 @@ def test_batch_argument_and_state_errors():
     finally:
         a.close()
         c.close()
+
+
+def test_batch_autotune_times_the_whole_graph():
+    # the tuner applies each candidate to every member, times graph replays of
+    # the whole batch and leaves the winner set; results stay those of the
+    # members evaluated one at a time (float32 form), and against the oracle
+    probs = workloads.uneven_problems(8, 2000, 40000, seed=9)
+    ms = _members(probs, 8, 1)
+    try:
+        with LayeredFMMBatch(ms) as b:
+            rows = b.autotune(reps=2)
+            print("batch tuner:", rows)
+            assert len(rows) == 9 and sum(r["chosen"] for r in rows) == 1
+            best = [r for r in rows if r["chosen"]][0]
+            assert best["ms"] == min(r["ms"] for r in rows) and all(r["ms"] > 0 for r in rows)
+            qs = _charges(probs, 7)
+            phi, E = b.evaluate(qs)
+            singles = [m.evaluate(q) for m, q in zip(ms, qs)]
+            assert _worst(phi, [s[0] for s in singles]) < 1e-6
+            w = probs[3]
+            t = workloads.subsample(w.n, 60)
+            ref, _ = oracle.direct(w.d, w.eps, w.xyz, w.layer, qs[3], targets=t, mode=oracle.MODE_IMAGES)
+            assert oracle.err2(ref, phi[3][t]) < 1e-5
+            assert b.info()["timeouts"] == 0
+    finally:
+        _close(ms)
+
+
+def test_batch_autotune_needs_the_graph():
+    probs = workloads.uneven_problems(2, 2000, 4000, seed=3)
+    ms = _members(probs, 6, 1)
+    try:
+        with LayeredFMMBatch(ms, graph=False) as b:
+            with pytest.raises(LfmmError) as ei:
+                b.autotune(reps=1)
+            assert ei.value.status == ESTATE
+    finally:
+        _close(ms)

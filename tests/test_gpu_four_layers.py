@@ -93,7 +93,9 @@ def test_fmm_matches_oracle(aligned, precision, tol):
 # interface-problem solve per quadrature node); the reference is the oracle's
 # quadrature of its own per-k solve (Sommerfeld limit in closed form).
 @pytest.mark.parametrize("aligned", [True, False])
-@pytest.mark.parametrize("precision,tol_phi,tol_fld", [(0, 1e-5, 1e-4), (1, 2e-5, 1e-4)])
+# measured Err2 (phi, field): aligned 3.0e-6 1.1e-6 (FP64), 3.2e-6 4.9e-6 (float32);
+# unaligned 1.3e-6 3.8e-7, 1.5e-6 4.1e-6
+@pytest.mark.parametrize("precision,tol_phi,tol_fld", [(0, 6e-6, 5e-6), (1, 6e-6, 1.5e-5)])
 def test_near_interface_matches_quadrature_oracle(aligned, precision, tol_phi, tol_fld):
     d = workloads.D_FOUR if aligned else workloads.D_FOUR_UNALIGNED
     w = workloads.four_layers_near_interface(3000, d=d)

@@ -145,7 +145,8 @@ def test_rejects_points_outside_their_layer():
         assert np.all(np.isfinite(phi))
 
 
-@pytest.mark.parametrize("precision,tol_phi,tol_fld", [(0, 5e-6, 5e-5), (1, 1e-5, 5e-5)])
+# measured Err2 (phi, field): 3.45e-6 4.7e-6 (FP64), 3.46e-6 5.2e-6 (float32)
+@pytest.mark.parametrize("precision,tol_phi,tol_fld", [(0, 6e-6, 1.2e-5), (1, 6e-6, 1.5e-5)])
 def test_near_interface_forms_match_oracle(precision, tol_phi, tol_fld):
     # every charge within 0.02 of an interface: the near field holds reaction
     # pairs (float32 form: offsets from leaf centres, compensated sums); each
