@@ -68,8 +68,8 @@ enum {
                                    tables (built on first use, see lfmm_near_tables); 0 = quadrature (default) */
     LFMM_OPT_TC_PERSISTENT = 11, /* tensor-core free M2L: 1 = one persistent CTA per SM walking the
                                    (tile, offset group) units with a double-buffered accumulator, for
-                                   launches of at least 4 units per SM (default); 0 = one CTA per unit
-                                   always.  Same arithmetic and result either way. */
+                                   launches of at least 4 units per SM; 0 = one CTA per unit, two CTAs per
+                                   SM (default; measured as fast at N = 1M).  Same arithmetic and result. */
     LFMM_OPT_P2P_STAGED = 12,   /* float32 near field with one charge vector and no reaction pairs in the near
                                    lists: 1 = each warp stages its leaf's whole near list once (default);
                                    0 = staging per source box.  Same pairs either way. */
@@ -80,12 +80,14 @@ enum {
 
 /* Create a context for the medium.
  *   d   : host, L interface heights, strictly decreasing (Section 3.1).
- *   L   : number of interfaces, 0 <= L <= 3 (one to four layers).  With
- *         three interfaces the reaction densities are evaluated by solving
- *         the interface problem of Appendix A at each quadrature node (the
- *         learned near-field kernels stay limited to three layers); when the
- *         interface gaps share a unit, grid planes contain the interfaces and
- *         the reaction M2L uses its keyed tables on the aligned levels.
+ *   L   : number of interfaces, 0 <= L <= 4 (one to five layers).  With
+ *         three or four interfaces the reaction densities are evaluated by
+ *         solving the interface problem of Appendix A at each quadrature node
+ *         (the learned near-field kernels stay limited to three layers); when
+ *         the interface gaps share a unit, grid planes contain the interfaces
+ *         and the reaction M2L uses its keyed tables on the aligned levels.
+ *         Five layers take three bits of a box key for the layer id, so their
+ *         trees stop at level 9.
  *   eps : host, L+1 permittivities > 0, layer 0 on top.
  *   p   : truncation order of all expansions, 1 <= p <= 20 (FP64) and
  *         p <= 14 in the FP32 form.

@@ -227,7 +227,7 @@ static LfErr setup_rules(lfmm_ctx* ctx)
     LF_TRY(make_rule(ctx->near_pole, 32, ctx->near_pole ? 48 : ctx->quad_nodes, T, W));
     LF_TRY(upload_rule(ctx->gl_t_m2l, ctx->gl_w_m2l, T, W));
     ctx->gl_q_m2l = (int)T.size();
-    // four layers: the remainder mixes more exponential rates, and the field
+    // four or five layers: the remainder mixes more exponential rates, and the field
     // kernels (one more power of k) need 64 nodes for 1e-12 where 32 give 1e-9
     const int qnear = (ctx->L >= 3) ? 64 : (ctx->near_pole ? 48 : 32);
     LF_TRY(make_rule(ctx->near_pole, 32, qnear, T, W));
@@ -704,6 +704,7 @@ lfmm_status lfmm_create(const double* d, int L, const double* eps, int p, lfmm_c
         e = lf_cuda(cudaStreamCreateWithPriority(&ctx->s_near, cudaStreamNonBlocking, prio_lo), "stream");
     if (e.empty()) e = lf_cuda(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming), "event");
     if (e.empty()) e = lf_cuda(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming), "event");
+    if (e.empty()) e = lf_cuda(cudaEventCreateWithFlags(&ctx->ev_m2r, cudaEventDisableTiming), "event");
     // per-context component array: kernels read it by pointer, so contexts with
     // different media can run side by side (no module-global state)
     if (e.empty()) e = lf_reserve(ctx->comp_dev, sizeof(LfmmComp) * LFMM_MAXCOMP);
@@ -998,6 +999,7 @@ void lfmm_destroy(lfmm_ctx* ctx)
     for (DevBuf* b : bufs) lf_free(*b);
     for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_m2r) cudaEventDestroy(ctx->ev_m2r);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     if (ctx->s_main) cudaStreamDestroy(ctx->s_main);
     if (ctx->s_near) cudaStreamDestroy(ctx->s_near);

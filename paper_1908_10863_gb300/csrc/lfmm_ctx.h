@@ -35,7 +35,7 @@ struct lfmm_ctx {
     // medium and order
     int L = 0;
     double d[LFMM_MAXL] = {0};
-    double eps[LFMM_MAXL + 1] = {1, 1, 1, 1};
+    double eps[LFMM_MAXL + 1] = {1, 1, 1, 1, 1};
     int p = 0;
     // options
     int precision = 0;
@@ -105,7 +105,7 @@ struct lfmm_ctx {
     DevBuf leaf_of;  // leaf (global box id) of each sorted charge
     DevBuf level_consts;  // float4 [LFMM_MAXCOMP][16]: (K, F, G, Z) of the list tests, in box units
     DevBuf p2p_consts;    // float4 [LFMM_MAXCOMP]: (s, K, is_free, 0) at the leaf level, for the float32 near field
-    int tc_persistent = 1;     // free M2L on the tensor cores: persistent kernel (1) or one CTA per work unit (0)
+    int tc_persistent = 0;     // free M2L on the tensor cores: persistent kernel (1) or one CTA per work unit (0)
     int num_sms = 152;
     int p2p_staged = 1;        // float32 free-space near field: staged-list kernel (1) or per-box staging (0)
     int serial_near = 0;       // 1: near field on the calling stream before the far field (no overlap)
@@ -149,6 +149,9 @@ struct lfmm_ctx {
     int m2r_nkeys = 0, m2r_nbatch = 0, m2r_keyed_from = 0, m2r_ntab = 0;
     DevBuf m2r_ops;         // assembled operator per key, [nkeys][RP][RP] in the precision below
     int m2r_ops_prec = -1;  // 0 FP64, 1 FP32, -1 not assembled for this build
+    int m2r_dev_pending = 0;  // 1: the keys' tables and operators are still to be computed (first evaluation)
+    cudaEvent_t ev_m2r = nullptr;  // recorded after them on the stream that computed them
+    int m2r_wait = 0;              // 1: the far field must wait for ev_m2r before the reaction M2L
 
     // learned surrogate of the near-field reaction kernels
     DevBuf surr_theta, surr_grad, surr_m1, surr_m2, surr_w, surr_b, surr_meta, surr_err, surr_comps, surr_xoff,
@@ -197,6 +200,7 @@ LfErr lf_m2l_gemm(lfmm_ctx* ctx, cudaStream_t st);
 LfErr lf_prepare_m2r(lfmm_ctx* ctx, cudaStream_t st);
 LfErr lf_m2r_apply(lfmm_ctx* ctx, cudaStream_t st);
 LfErr lf_m2r_ops(lfmm_ctx* ctx, cudaStream_t st);
+LfErr lf_m2r_device(lfmm_ctx* ctx, cudaStream_t st);
 // stable LSD radix sort of uint32 (key, value) pairs (lfmm_tree.cu); uses keys_tmp, vals_tmp, hist
 LfErr lf_radix_sort(lfmm_ctx* ctx, uint32_t* keys, uint32_t* vals, int64_t n, cudaStream_t st, int first_pass = 0,
                     int npass = 4);

@@ -306,7 +306,7 @@ struct M2LArgs {
     int Q;
 };
 
-// GEN: reaction components of media of four layers
+// GEN: reaction components of media of four or five layers
 template <typename R, bool REACT, bool GEN = false>
 __global__ void k_m2l(M2LArgs a)
 {
@@ -590,6 +590,10 @@ static LfErr far_field(lfmm_ctx* ctx, cudaStream_t st)
             LF_TRY(lf_m2l_gemm(ctx, st));
         lf_prof_stop(ctx, ph, st);
     }
+    if (ctx->m2r_wait) {
+        LF_CHECK(cudaStreamWaitEvent(st, ctx->ev_m2r, 0));
+        ctx->m2r_wait = 0;
+    }
     if (ctx->m2r_nbatch > 0) {
         ph = lf_prof_start(ctx, LFMM_TIME_M2L_REACTION, st);
         LF_TRY(lf_m2r_apply(ctx, st));
@@ -687,7 +691,12 @@ LfErr lf_evaluate_sorted(lfmm_ctx* ctx, int nrhs, const double* q_dev, double* p
         ++ctx->launches, k_gather_q<double><<<g1, 256, 0, st>>>(q_dev, ctx->perm.as<int32_t>(), n,
                                                                ctx->q_sorted.as<double>());
     LF_TRY(lf_cuda(cudaGetLastError(), "gather q"));
+    // the reaction M2L's tables and operators of a fresh build: on the
+    // near-field stream ahead of the near field, beside the far field's
+    // upward pass; the far field waits for them before the reaction M2L
+    const bool m2r_dev = ctx->m2r_dev_pending != 0;
     if (ctx->serial_near) {
+        if (m2r_dev) LF_TRY(lf_m2r_device(ctx, st));
         // near field alone on the calling stream, before the far field (its
         // stage time is then the near-field kernels' own duration)
         LF_TRY(lf_near_field(ctx, st));
@@ -699,6 +708,11 @@ LfErr lf_evaluate_sorted(lfmm_ctx* ctx, int nrhs, const double* q_dev, double* p
         // near field on its own stream, concurrent with the far field
         LF_CHECK(cudaEventRecord(ctx->ev_fork, st));
         LF_CHECK(cudaStreamWaitEvent(ctx->s_near, ctx->ev_fork, 0));
+        if (m2r_dev) {
+            LF_TRY(lf_m2r_device(ctx, ctx->s_near));
+            LF_CHECK(cudaEventRecord(ctx->ev_m2r, ctx->s_near));
+            ctx->m2r_wait = 1;
+        }
         LF_TRY(lf_near_field(ctx, ctx->s_near));
         LF_CHECK(cudaEventRecord(ctx->ev_join, ctx->s_near));
         if (ctx->precision)

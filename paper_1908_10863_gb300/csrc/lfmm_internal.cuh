@@ -37,11 +37,17 @@
 #include <stdint.h>
 
 #define LFMM_PMAX 20
-#define LFMM_MAXL 3      // interfaces (four layers: the layer id takes two bits of a box key)
-#define LFMM_MAXCOMP 40  // (L + 1) free + (2L)^2 reaction components
+#define LFMM_MAXL 4      // interfaces (five layers)
+#define LFMM_MAXCOMP 69  // (L + 1) free + (2L)^2 reaction components
 #define LFMM_QMAX 128
+// A box key holds the layer id above the Morton code of the fine grid: a
+// fine level of 10 (30 bits) leaves two bits, four layers; five layers take
+// three bits over a fine level of 9 (lf_fine_level).
 #define LFMM_FINE_LEVEL 10
-#define LFMM_ENT_SHIFT 26
+__host__ __device__ __forceinline__ int lf_fine_level(int L) { return L >= 4 ? 9 : LFMM_FINE_LEVEL; }
+// interaction-list entry: component << LFMM_ENT_SHIFT | box (7 bits of
+// component, up to 2^25 boxes)
+#define LFMM_ENT_SHIFT 25
 #define LFMM_ENT_MASK ((1u << LFMM_ENT_SHIFT) - 1u)
 #define LFMM_MAX_DEVICES 64
 

@@ -39,7 +39,7 @@ static inline int lf_blocks(int64_t n, int t) { return (int)((n + t - 1) / t); }
 #define KEY_NONE 0xffffffffu
 
 
-// key = comp (6 bits) | level (4 bits) | offset index (12 bits, offsets in [-7, 7]^3)
+// key = comp (7 bits) | level (4 bits) | offset index (12 bits, offsets in [-7, 7]^3)
 #define R_OR 7
 #define R_OW (2 * R_OR + 1)
 __host__ __device__ __forceinline__ uint32_t rkey(int c, int l, int ox, int oy, int oz)
@@ -147,6 +147,7 @@ LfErr lf_prepare_m2r(lfmm_ctx* ctx, cudaStream_t st)
     ctx->m2r_nbatch = 0;
     ctx->m2r_ntab = 0;
     ctx->m2r_ops_prec = -1;
+    ctx->m2r_dev_pending = 0;
     ctx->stats[LFMM_STAT_REACTION_KEYS] = 0;
     ctx->stats[LFMM_STAT_REACTION_TABLES] = 0;
     ctx->m2r_keyed_from = ctx->depth + 1;
@@ -248,13 +249,8 @@ LfErr lf_prepare_m2r(lfmm_ctx* ctx, cudaStream_t st)
     for (int l = 0; l < 16; ++l) hl[l] = (l <= ctx->depth) ? ctx->levels[l].h : 0.0;
     LF_TRY(lf_reserve(ctx->m2r_levelh, sizeof(double) * 16));
     LF_CHECK(cudaMemcpyAsync(ctx->m2r_levelh.ptr, hl, sizeof(double) * 16, cudaMemcpyHostToDevice, st));
-    size_t sm = sizeof(double) * ((size_t)TT + 2 * (size_t)Q * TS);
-    auto tabk = (ctx->L >= 3) ? k_m2r_tables<true> : k_m2r_tables<false>;
-    LF_CHECK(cudaFuncSetAttribute(tabk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    ++ctx->launches, tabk<<<ntab, 128, sm, st>>>(ctx->comp_dev.as<LfmmComp>(), ctx->m2r_tdesc.as<int4>(), ntab,
-                                                         ctx->m2r_levelh.as<double>(), P, ctx->gl_t_m2l.as<double>(),
-                                                         ctx->gl_w_m2l.as<double>(), Q, ctx->m2r_tables.as<double>());
-    LF_TRY(lf_cuda(cudaGetLastError(), "m2r tables"));
+    (void)P;
+    (void)Q;
     ctx->m2r_ntab = ntab;
     // batches of R_TB pairs of one key
     std::vector<int4>& batches = ctx->m2r_batches_h;
@@ -270,7 +266,34 @@ LfErr lf_prepare_m2r(lfmm_ctx* ctx, cudaStream_t st)
     // (the host staging vectors live in the context; the build synchronises at its end)
     ctx->stats[LFMM_STAT_REACTION_KEYS] = nk;
     ctx->stats[LFMM_STAT_REACTION_TABLES] = ntab;
-    return lf_m2r_ops(ctx, st);
+    // the tables and operators themselves are device work of the first
+    // evaluation after this build (lf_m2r_device), beside its upward pass
+    ctx->m2r_dev_pending = 1;
+    return LfErr();
+}
+
+// Sommerfeld tables of the keys (FP64) and the keys' operators in the
+// current precision, enqueued on `st` (the first evaluation after a build
+// runs this on the near-field stream, so it overlaps the far field's upward
+// pass and free M2L; the reaction M2L waits for it).
+LfErr lf_m2r_device(lfmm_ctx* ctx, cudaStream_t st)
+{
+    if (ctx->m2r_nbatch == 0 || ctx->m2r_ntab == 0) {
+        ctx->m2r_dev_pending = 0;
+        return LfErr();
+    }
+    const int ntab = ctx->m2r_ntab;
+    const int P = ctx->p, TS = 2 * P + 1, TT = TS * TS, Q = ctx->gl_q_m2l;
+    size_t sm = sizeof(double) * ((size_t)TT + 2 * (size_t)Q * TS);
+    auto tabk = (ctx->L >= 3) ? k_m2r_tables<true> : k_m2r_tables<false>;
+    LF_CHECK(cudaFuncSetAttribute(tabk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    ++ctx->launches, tabk<<<ntab, 128, sm, st>>>(ctx->comp_dev.as<LfmmComp>(), ctx->m2r_tdesc.as<int4>(), ntab,
+                                                 ctx->m2r_levelh.as<double>(), P, ctx->gl_t_m2l.as<double>(),
+                                                 ctx->gl_w_m2l.as<double>(), Q, ctx->m2r_tables.as<double>());
+    LF_TRY(lf_cuda(cudaGetLastError(), "m2r tables"));
+    LF_TRY(lf_m2r_ops(ctx, st));
+    ctx->m2r_dev_pending = 0;  // only once both are enqueued
+    return LfErr();
 }
 
 // ---------------------------------------------------------------------------

@@ -172,7 +172,7 @@ __device__ __forceinline__ void p2p_store(const P2PArgs& a, int i, const P2PAcc<
 }
 
 // One block per target leaf (FP64 form), a batch of RB right-hand sides.
-// GEN: media of four layers (both forms, one right-hand side per launch).
+// GEN: media of four or five layers (both forms, one right-hand side per launch).
 template <typename R, int RB, bool GEN = false>
 __global__ void __launch_bounds__(P2P_T) k_p2p(P2PArgs a)
 {
@@ -874,7 +874,7 @@ LfErr lf_near_field(lfmm_ctx* ctx, cudaStream_t st)
     // Few leaves (small problems) leave most SMs idle with one warp or block
     // per leaf: share each near list between `split` of them.  A set value
     // (ctx->p2p_split, e.g. from the tuner) wins over this occupancy rule.
-    // media of four layers need the solved densities only for reaction pairs
+    // media of four or five layers need the solved densities only for reaction pairs
     // of the near lists (counted at every build); without any, the kernels of
     // thinner media compute the free-space pairs alone and are exact
     const bool general = ctx->L >= 3 && ctx->stats[LFMM_STAT_P2P_REACTION] > 0;

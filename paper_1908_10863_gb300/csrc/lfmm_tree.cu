@@ -260,6 +260,7 @@ __global__ void k_bounds(const double* __restrict__ xyz, int64_t n, double* __re
 
 struct KeyParams {
     int L;
+    int fine;  // fine grid level of the keys (lf_fine_level)
     double d[LFMM_MAXL];
     double org[3];
     double hfine;
@@ -288,19 +289,19 @@ __global__ void k_make_keys(const double* __restrict__ xyz, const int32_t* __res
         atomicOr(&err[0], 1);
         l = 0;
     }
-    const int top = (1 << LFMM_FINE_LEVEL) - 1;
+    const int top = (1 << kp.fine) - 1;
     int ix = (int)floor((x - kp.org[0]) / kp.hfine);
     int iy = (int)floor((y - kp.org[1]) / kp.hfine);
     int iz = (int)floor((z - kp.org[2]) / kp.hfine);
     ix = min(max(ix, 0), top);
     iy = min(max(iy, 0), top);
     iz = min(max(iz, kp.iz_lo[l]), kp.iz_hi[l]);
-    keys[i] = ((uint32_t)l << 30) | lf_spread3((uint32_t)ix) | (lf_spread3((uint32_t)iy) << 1) |
+    keys[i] = ((uint32_t)l << (3 * kp.fine)) | lf_spread3((uint32_t)ix) | (lf_spread3((uint32_t)iy) << 1) |
               (lf_spread3((uint32_t)iz) << 2);
     vals[i] = (uint32_t)i;
 }
 
-__global__ void k_level_counts(const uint32_t* __restrict__ keys, int64_t n, int* __restrict__ counts)
+__global__ void k_level_counts(const uint32_t* __restrict__ keys, int64_t n, int fine, int* __restrict__ counts)
 {
     __shared__ int s[LFMM_FINE_LEVEL + 1];
     if (threadIdx.x <= LFMM_FINE_LEVEL) s[threadIdx.x] = 0;
@@ -308,13 +309,13 @@ __global__ void k_level_counts(const uint32_t* __restrict__ keys, int64_t n, int
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
         uint32_t k = keys[i], kp = (i > 0) ? keys[i - 1] : 0u;
-        for (int l = 0; l <= LFMM_FINE_LEVEL; ++l) {
-            int sh = 3 * (LFMM_FINE_LEVEL - l);
+        for (int l = 0; l <= fine; ++l) {
+            int sh = 3 * (fine - l);
             if (i == 0 || (k >> sh) != (kp >> sh)) atomicAdd(&s[l], 1);
         }
     }
     __syncthreads();
-    if (threadIdx.x <= LFMM_FINE_LEVEL && s[threadIdx.x]) atomicAdd(&counts[threadIdx.x], s[threadIdx.x]);
+    if (threadIdx.x <= fine && s[threadIdx.x]) atomicAdd(&counts[threadIdx.x], s[threadIdx.x]);
 }
 
 __global__ void k_gather_sorted(const double* __restrict__ xyz, const uint32_t* __restrict__ vals, int64_t n,
@@ -622,7 +623,7 @@ static LfErr grow_keep(DevBuf& b, size_t bytes, size_t keep, cudaStream_t st)
 // ---------------------------------------------------------------------------
 LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int64_t n, cudaStream_t st)
 {
-    if (n > (int64_t)LFMM_ENT_MASK) return "too many charges for this build (max 2^26)";
+    if (n > (int64_t)LFMM_ENT_MASK) return "too many charges for this build (max 2^25)";
     // ---- bounds ----
     const int nbb = 256;
     LF_TRY(lf_reserve(ctx->counts, 65536));  // [0,16K) bounds partials, 16K level counts, 20K stats
@@ -706,10 +707,12 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
 
     KeyParams kp;
     kp.L = ctx->L;
+    const int fine = lf_fine_level(ctx->L);
+    kp.fine = fine;
     for (int j = 0; j < LFMM_MAXL; ++j) kp.d[j] = (j < ctx->L) ? ctx->d[j] : 0.0;
     for (int k = 0; k < 3; ++k) kp.org[k] = ctx->origin[k];
-    kp.hfine = H / (double)(1 << LFMM_FINE_LEVEL);
-    const int top = (1 << LFMM_FINE_LEVEL) - 1;
+    kp.hfine = H / (double)(1 << fine);
+    const int top = (1 << fine) - 1;
     // fine cells a layer's points may take: interfaces on cell planes (L == 1 or
     // an alignment unit) bound them exactly; otherwise the straddling cells count
     const bool planes = ctx->L == 1 || unit > 0.0;
@@ -759,7 +762,7 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
     // ---- depth ----
     int* cnt = reinterpret_cast<int*>(ctx->counts.as<char>() + 16384);
     LF_CHECK(cudaMemsetAsync(cnt, 0, sizeof(int) * 16, st));
-    ++ctx->launches, k_level_counts<<<lf_blocks(n, 256), 256, 0, st>>>(keys, n, cnt);
+    ++ctx->launches, k_level_counts<<<lf_blocks(n, 256), 256, 0, st>>>(keys, n, fine, cnt);
     LF_TRY(lf_cuda(cudaGetLastError(), "level counts"));
     int hc[16];
     LF_CHECK(cudaMemcpyAsync(hc, cnt, sizeof(int) * 16, cudaMemcpyDeviceToHost, st));
@@ -777,11 +780,11 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
 
     // the level whose mean leaf occupancy is nearest (in ratio) to half the
     // capacity, among the levels whose mean stays within the capacity
-    int depth = LFMM_FINE_LEVEL;
+    int depth = fine;
     {
         const double want = 0.5 * ctx->leaf_cap;
         double best = INFINITY;
-        for (int l = 0; l <= LFMM_FINE_LEVEL; ++l) {
+        for (int l = 0; l <= fine; ++l) {
             const double mean = (double)n / (double)hc[l];
             if (mean > ctx->leaf_cap) continue;
             const double d = fabs(log(mean / want));
@@ -829,7 +832,7 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
     // leaf level
     {
         const LfmmLevel& lv = ctx->levels[depth];
-        int sh = 3 * (LFMM_FINE_LEVEL - depth);
+        int sh = 3 * (fine - depth);
         ++ctx->launches, k_flags_particles<<<lf_blocks(n, 256), 256, 0, st>>>(keys, n, sh, fl);
         // the box counts per level are known (k_level_counts): no read-back
         LF_TRY(lf_scan_i32(ctx, fl, ix, n, nullptr, st));

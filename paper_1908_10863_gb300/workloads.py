@@ -23,6 +23,8 @@ library and for the CPU oracle alike.
 * :func:`four_layers` / :func:`four_layers_near_interface` -- media of four
   layers: slabs away from the interfaces, or every charge within ``delta``
   of an interface on its own side.
+* :func:`five_layers` -- media of five layers, slabs or charges next to the
+  interfaces.
 * :func:`uneven_problems` -- k independent config2-shaped problems whose
   sizes are log-uniform in [nmin, nmax] (the batched form's many uneven
   problems), each with its own seed.
@@ -148,6 +150,38 @@ def four_layers(n: int = 4000, seed: int | None = None, d=D_FOUR, eps=EPS_FOUR, 
     layer = np.concatenate([np.full(p.shape[0], l, dtype=np.int32) for p, l in parts])
     q = rng.uniform(-1.0, 1.0, size=n)
     return Workload("four_layers_n%d" % n, np.array(d), np.array(eps, dtype=np.float64), xyz, layer, q)
+
+
+D_FIVE = (0.0, -0.6, -1.2, -1.8)         # inner layers of equal thickness
+D_FIVE_UNALIGNED = (0.0, -0.45, -1.1, -1.6371)
+EPS_FIVE = (2.0, 7.0, 1.5, 12.0, 4.0)
+
+
+def five_layers(n: int = 5000, seed: int | None = None, d=D_FIVE, eps=EPS_FIVE, margin: float = 0.05,
+                near: float = 0.0) -> Workload:
+    """Five layers, N split equally: a unit-thick slab above d0, the three
+    inner layers (each kept `margin` from its interfaces) and a unit-thick
+    slab below the last interface, x, y in [-0.5, 0.5], q ~ U[-1, 1].  With
+    near > 0 every charge lies instead between 1e-3 and `near` from an
+    interface on its own side (the eight sides split equally)."""
+    rng = np.random.Generator(np.random.PCG64(SEED_BASE + 10 if seed is None else seed))
+    d = tuple(float(v) for v in d)
+    if near > 0.0:
+        spans = []
+        for j, dj in enumerate(d):
+            spans.append(((dj + 1e-3, dj + near), j))
+            spans.append(((dj - near, dj - 1e-3), j + 1))
+        sizes = [n // 8] * 7 + [n - 7 * (n // 8)]
+        parts = [(_box(rng, cnt, lo, hi), l) for cnt, ((lo, hi), l) in zip(sizes, spans)]
+    else:
+        spans = [(d[0] + 0.1, d[0] + 1.1)] + [(d[j] + margin, d[j - 1] - margin) for j in range(1, 4)] + \
+                [(d[3] - 1.1, d[3] - 0.1)]
+        sizes = [n // 5] * 4 + [n - 4 * (n // 5)]
+        parts = [(_box(rng, cnt, lo, hi), l) for l, (cnt, (lo, hi)) in enumerate(zip(sizes, spans))]
+    xyz = np.concatenate([p for p, _ in parts])
+    layer = np.concatenate([np.full(p.shape[0], l, dtype=np.int32) for p, l in parts])
+    q = rng.uniform(-1.0, 1.0, size=n)
+    return Workload("five_layers_n%d" % n, np.array(d), np.array(eps, dtype=np.float64), xyz, layer, q)
 
 
 def four_layers_near_interface(n: int = 3000, delta: float = 0.02, hmin: float = 1e-3, seed: int | None = None,

@@ -1,4 +1,4 @@
-"""The four-layer density routines of the CUDA library (``lf_sigma_solve`` and
+"""The four- and five-layer density routines of the CUDA library (``lf_sigma_solve`` and
 the coupling-series remainder ``lf_sigma_rem<true>``, host-and-device code in
 ``lfmm_internal.cuh``) compiled for the host and checked against the oracle's
 independent solve of the interface problem.  No GPU is needed: nvcc compiles
@@ -43,7 +43,9 @@ int main() {
 ''' % HDR.replace("\\", "/")
 
 MEDIA = [([0.0, -0.6, -1.2], [2.0, 7.0, 1.5, 12.0]), ([0.0, -0.55, -1.2371], [1.0, 80.0, 2.0, 5.0]),
-         ([0.3, -0.2, -1.0], [5.0, 1.0, 30.0, 2.0])]
+         ([0.3, -0.2, -1.0], [5.0, 1.0, 30.0, 2.0]),
+         ([0.0, -0.6, -1.2, -1.8], [2.0, 7.0, 1.5, 12.0, 4.0]),
+         ([0.0, -0.45, -1.1, -1.6], [1.0, 40.0, 3.0, 9.0, 1.5])]
 
 
 @pytest.fixture(scope="module")

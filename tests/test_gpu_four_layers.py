@@ -33,8 +33,8 @@ def test_medium_limits():
     with LayeredFMM(w.d, w.eps, 4) as f:
         f.build(w.xyz, w.layer)
         assert f.stats()["components"] == 4 + 36
-    with pytest.raises(LfmmError):          # four interfaces: beyond the box key's layer bits
-        LayeredFMM([0.0, -1.0, -2.0, -3.0], [1.0] * 5, 4)
+    with pytest.raises(LfmmError):          # five interfaces: beyond the supported five layers
+        LayeredFMM([0.0, -1.0, -2.0, -3.0, -4.0], [1.0] * 6, 4)
     with pytest.raises(LfmmError):          # interfaces not strictly decreasing
         LayeredFMM([0.0, -1.0, -0.5], [1.0] * 4, 4)
     with pytest.raises(LfmmError):

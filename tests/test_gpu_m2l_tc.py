@@ -105,8 +105,7 @@ def test_persistent_kernel_matches_one_cta_per_unit(n, nrhs):
     Q = np.stack([np.roll(w.q, 7 * r) for r in range(nrhs)]) if nrhs > 1 else w.q
     with LayeredFMM(w.d, w.eps, 10, precision=1) as f:
         f.build(w.xyz, w.layer)
-        f.set_option(OPT_TC_PERSISTENT, 0)
-        phi0, E0 = f.evaluate(Q)
+        phi0, E0 = f.evaluate(Q)  # default: one CTA per unit
         f.set_option(OPT_TC_PERSISTENT, 1)
         phi1, E1 = f.evaluate(Q)
         assert f.stats()["timeouts"] == 0

@@ -11,7 +11,9 @@ from paper_1908_10863_gb300.lfmm import medium_components
 
 MEDIA = [([], [2.0]), ([0.0], [3.0, 11.0]), ([0.0, -1.2], [1.0, 5.0, 10.0]), ([0.0, -1.2], [1.0, 80.0, 2.0]),
          ([0.0, -1.2], [21.2, 47.5, 62.8]), ([0.0, -0.6, -1.2], [2.0, 7.0, 1.5, 12.0]),
-         ([0.0, -0.55, -1.2371], [1.0, 80.0, 2.0, 5.0]), ([0.3, -0.2, -1.0], [5.0, 1.0, 30.0, 2.0])]
+         ([0.0, -0.55, -1.2371], [1.0, 80.0, 2.0, 5.0]), ([0.3, -0.2, -1.0], [5.0, 1.0, 30.0, 2.0]),
+         ([0.0, -0.6, -1.2, -1.8], [2.0, 7.0, 1.5, 12.0, 4.0]),
+         ([0.0, -0.45, -1.1, -1.6], [1.0, 40.0, 3.0, 9.0, 1.5])]
 
 
 def _exponent(d, l, lp, a, b, z, zp):
@@ -65,7 +67,7 @@ def test_components_match_oracle(d, eps):
             assert abs(g) < 50.0 * (1.0 + abs(C)), (l, lp, a, b, k, g)
 
 
-@pytest.mark.parametrize("d,eps", [([0.0, -1.0, -2.0, -3.0], [1.0] * 5), ([0.0, -1.0, -0.5], [1.0] * 4),
+@pytest.mark.parametrize("d,eps", [([0.0, -1.0, -2.0, -3.0, -4.0], [1.0] * 6), ([0.0, -1.0, -0.5], [1.0] * 4),
                                    ([0.0, -1.0], [1.0, -2.0, 3.0]), ([0.0, np.nan], [1.0, 2.0, 3.0])])
 def test_invalid_media_rejected(d, eps):
     with pytest.raises(LfmmError):

@@ -577,3 +577,64 @@ def test_reciprocity_four_layers():
             u2, _ = oracle.reaction_pair(D4, eps, lp, l, rp, r)
             free = 1.0 / np.linalg.norm(r - rp) if l == lp else 0.0
             assert eps[l] * (u1 + free) == pytest.approx(eps[lp] * (u2 + free), rel=1e-11)
+
+
+D5 = [0.0, -0.6, -1.2, -1.8]
+
+
+@pytest.mark.parametrize("src_layer", [1, 3])
+def test_transmission_conditions_five_layers(src_layer):
+    # eq. transmissioncond at every interface of a five-layer medium
+    eps = [2.0, 7.0, 1.5, 12.0, 4.0]
+    rp = np.array([0.05, -0.1, -0.3 if src_layer == 1 else -1.5])
+    for j, dj in enumerate(D5):
+        above, below = j, j + 1
+        x = np.array([0.2, 0.15, dj])
+
+        def total(l, pt):
+            u, g = oracle.reaction_pair(D5, eps, l, src_layer, pt, rp, mode=oracle.MODE_QUAD)
+            if l == src_layer:
+                R = pt - rp
+                u += 1 / np.linalg.norm(R)
+                g = g - R / np.linalg.norm(R) ** 3
+            return u, g
+        ua, ga = total(above, x)
+        ub, gb = total(below, x)
+        assert ua == pytest.approx(ub, rel=1e-10)
+        assert eps[above] * ga[2] == pytest.approx(eps[below] * gb[2], rel=1e-9)
+        assert ga[0] == pytest.approx(gb[0], rel=1e-9)
+
+
+def test_five_layers_with_two_vanishing_interfaces_match_three_layer_images():
+    # eps = (1, 5, 5, 10, 10): the interfaces at -0.6 and -1.8 separate equal
+    # permittivities and disappear, leaving the three-layer medium (1, 5, 10)
+    # with interfaces 0 and -1.2, whose exact image series is independent
+    rng = np.random.default_rng(59)
+    n = 50
+    lay = rng.integers(0, 5, n).astype(np.int32)
+    zr = {0: (0.05, 1.0), 1: (-0.55, -0.05), 2: (-1.15, -0.65), 3: (-1.75, -1.25), 4: (-2.8, -1.85)}
+    xyz = np.zeros((n, 3))
+    xyz[:, :2] = rng.uniform(-0.5, 0.5, (n, 2))
+    for i in range(n):
+        xyz[i, 2] = rng.uniform(*zr[int(lay[i])])
+    q = rng.uniform(-1, 1, n)
+    lay3 = np.array([0, 1, 1, 2, 2], np.int32)[lay]
+    t = np.arange(20)
+    p5, f5 = oracle.direct(D5, [1.0, 5.0, 5.0, 10.0, 10.0], xyz, lay, q, targets=t, mode=oracle.MODE_QUAD)
+    p3, f3 = oracle.direct(D3, [1.0, 5.0, 10.0], xyz, lay3, q, targets=t, mode=oracle.MODE_IMAGES)
+    assert oracle.err2(p3, p5) < 1e-11
+    assert oracle.err2(f3, f5) < 1e-10
+
+
+def test_reciprocity_five_layers():
+    eps = [2.0, 7.0, 1.5, 12.0, 4.0]
+    zr = {0: (0.1, 1.0), 1: (-0.55, -0.05), 2: (-1.15, -0.65), 3: (-1.75, -1.25), 4: (-2.8, -1.9)}
+    rng = np.random.default_rng(67)
+    for l in range(5):
+        for lp in range(5):
+            r = np.array([*rng.uniform(-0.5, 0.5, 2), rng.uniform(*zr[l])])
+            rp = np.array([*rng.uniform(-0.5, 0.5, 2), rng.uniform(*zr[lp])])
+            u1, _ = oracle.reaction_pair(D5, eps, l, lp, r, rp)
+            u2, _ = oracle.reaction_pair(D5, eps, lp, l, rp, r)
+            free = 1.0 / np.linalg.norm(r - rp) if l == lp else 0.0
+            assert eps[l] * (u1 + free) == pytest.approx(eps[lp] * (u2 + free), rel=1e-11)
