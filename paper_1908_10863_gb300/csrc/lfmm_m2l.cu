@@ -260,15 +260,24 @@ __global__ void k_child_slots(int off, int nb, const uint32_t* __restrict__ bkey
     if (pb >= 0) slots[(size_t)pb * 8 + (bkey[b] & 7u)] = b;
 }
 
-__global__ void k_class_keys(int off, int nb, int level, const uint32_t* __restrict__ bkey,
-                             uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, int base,
-                             int* __restrict__ counts)
+// Levels 1 .. depth in one launch: sort position j belongs to level l when
+// base[l] <= j < base[l] + nb[l] (levels in increasing order).
+struct ClassLevels {
+    int depth;
+    int off[17], nb[17], base[17];
+};
+
+__global__ void k_class_keys(ClassLevels lv, int nsort, const uint32_t* __restrict__ bkey,
+                             uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, int* __restrict__ counts)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nb) return;
-    int c = (int)(bkey[off + i] & 7u);
-    keys[base + i] = ((uint32_t)level << 28) | ((uint32_t)c << 25) | (uint32_t)i;
-    vals[base + i] = (uint32_t)(off + i);
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nsort) return;
+    int level = 1;
+    while (level < lv.depth && j >= lv.base[level] + lv.nb[level]) ++level;
+    const int i = j - lv.base[level];
+    const int c = (int)(bkey[lv.off[level] + i] & 7u);
+    keys[j] = ((uint32_t)level << 28) | ((uint32_t)c << 25) | (uint32_t)i;
+    vals[j] = (uint32_t)(lv.off[level] + i);
     atomicAdd(&counts[level * 8 + c], 1);
 }
 
@@ -288,24 +297,25 @@ LfErr lf_prepare_m2l(lfmm_ctx* ctx, cudaStream_t st)
     for (int l = 1; l <= depth; ++l) nsort += ctx->levels[l].nbox;
     LF_TRY(lf_reserve(ctx->m2l_keys, (size_t)nsort * 4 + 16));
     LF_TRY(lf_reserve(ctx->m2l_sorted, (size_t)nsort * 4 + 16));
+    ClassLevels cl;
+    cl.depth = depth;
     int base = 0;
     for (int l = 1; l <= depth; ++l) {
-        const LfmmLevel& lv = ctx->levels[l];
-        if (lv.nbox == 0) continue;
-        ++ctx->launches, k_class_keys<<<lf_blocks(lv.nbox, 256), 256, 0, st>>>(
-            lv.off, lv.nbox, l, ctx->box_key.as<uint32_t>(), ctx->m2l_keys.as<uint32_t>(),
-            ctx->m2l_sorted.as<uint32_t>(), base, cnt);
-        base += lv.nbox;
+        cl.off[l] = ctx->levels[l].off;
+        cl.nb[l] = ctx->levels[l].nbox;
+        cl.base[l] = base;
+        base += ctx->levels[l].nbox;
     }
-    // M2M slots: children of each parent by octant
+    if (nsort > 0)
+        ++ctx->launches, k_class_keys<<<lf_blocks(nsort, 256), 256, 0, st>>>(
+            cl, nsort, ctx->box_key.as<uint32_t>(), ctx->m2l_keys.as<uint32_t>(), ctx->m2l_sorted.as<uint32_t>(), cnt);
+    // M2M slots: children of each parent by octant (every box of levels
+    // 1 .. depth, which hold the ids below the roots', in one launch)
     LF_TRY(lf_reserve(ctx->m2m_slots, nb * 8 * sizeof(int)));
     LF_CHECK(cudaMemsetAsync(ctx->m2m_slots.ptr, 0xff, nb * 8 * sizeof(int), st));
-    for (int l = 1; l <= depth; ++l) {
-        const LfmmLevel& lv = ctx->levels[l];
-        if (lv.nbox == 0) continue;
-        ++ctx->launches, k_child_slots<<<lf_blocks(lv.nbox, 256), 256, 0, st>>>(
-            lv.off, lv.nbox, ctx->box_key.as<uint32_t>(), ctx->box_parent.as<int>(), ctx->m2m_slots.as<int>());
-    }
+    if (ctx->levels[0].off > 0)
+        ++ctx->launches, k_child_slots<<<lf_blocks(ctx->levels[0].off, 256), 256, 0, st>>>(
+            0, ctx->levels[0].off, ctx->box_key.as<uint32_t>(), ctx->box_parent.as<int>(), ctx->m2m_slots.as<int>());
     LF_TRY(lf_cuda(cudaGetLastError(), "m2l slots"));
     // keys are level << 28 | class << 25 | index: with fewer than 2^24 boxes the
     // top byte alone orders them (stable within a level and class)

@@ -151,8 +151,9 @@ LfErr lf_prepare_m2r(lfmm_ctx* ctx, cudaStream_t st)
     ctx->stats[LFMM_STAT_REACTION_KEYS] = 0;
     ctx->stats[LFMM_STAT_REACTION_TABLES] = 0;
     ctx->m2r_keyed_from = ctx->depth + 1;
-    // the keyed GEMM holds a whole operator in shared memory: p <= 10
-    if (ctx->m2l_rm == 0 || ctx->m2l_rm > 8 || ctx->m2r_total == 0) return LfErr();
+    // the keyed GEMM holds a whole operator in shared memory (p <= 10) or
+    // stages it in chunks (p <= 15)
+    if (ctx->m2l_rm == 0 || ctx->m2l_rm > 16 || ctx->m2r_total == 0) return LfErr();
     // first level whose grid planes contain the interfaces
     int la = ctx->depth + 1;
     for (int l = 0; l <= ctx->depth; ++l) {
@@ -513,6 +514,127 @@ __global__ void __launch_bounds__(R_T) k_m2r_gemm(RGemmArgs g)
     }
 }
 
+// Orders 11 .. 15 ((p+1)^2 up to 256): the key's operator is too large for
+// shared memory, so it is staged in chunks of R_KC input rows while the
+// gathered multipoles stay resident; the same tile shapes as m2r_tile.
+#define R_KC 32
+
+template <typename R, int RP, int CG>
+__device__ __forceinline__ void m2r_tile_kc(const R* __restrict__ A, R* __restrict__ sA, const R* __restrict__ sX,
+                                            int cnt, const int* s_tgt, R ih, R* __restrict__ L, int nc)
+{
+    constexpr int KP = RP, XS = KP + 1;
+    constexpr int RG = R_T / CG;  // row groups
+    constexpr int RM = RP / RG;   // rows per thread
+    static_assert(RM >= 1 && RM * RG == RP, "tile shape");
+    const int tid = threadIdx.x;
+    const int cg = tid % CG, rg = tid / CG;
+    R acc[RM][4];
+#pragma unroll
+    for (int r = 0; r < RM; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[r][q] = 0;
+    for (int kc = 0; kc < KP; kc += R_KC) {
+        __syncthreads();  // the previous chunk has been read
+        {
+            const float4* src = reinterpret_cast<const float4*>(A + (size_t)kc * RP);
+            float4* dst = reinterpret_cast<float4*>(sA);
+            constexpr int NV = R_KC * RP * (int)sizeof(R) / 16;
+            for (int i = tid; i < NV; i += R_T) dst[i] = src[i];
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < R_KC; ++kk) {
+            R a[RM];
+#pragma unroll
+            for (int r = 0; r < RM; ++r) a[r] = sA[kk * RP + rg * RM + r];
+            R x[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) x[q] = sX[(4 * cg + q) * XS + kc + kk];
+#pragma unroll
+            for (int r = 0; r < RM; ++r)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[r][q] += a[r] * x[q];
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int j = 4 * cg + q;
+        if (j >= cnt) continue;
+        R* Lt = L + (size_t)s_tgt[j] * nc;
+#pragma unroll
+        for (int r = 0; r < RM; ++r) {
+            const int row = rg * RM + r;
+            if (row < nc) atomicAdd(Lt + row, acc[r][q] * ih);
+        }
+    }
+}
+
+template <typename R, int RP>
+__global__ void __launch_bounds__(R_T) k_m2r_gemm_kc(RGemmArgs g)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int KP = RP;
+    constexpr int XS = KP + 1;
+    const int nc = g.nc;
+    R* sA = reinterpret_cast<R*>(smem_raw);  // [R_KC][RP]
+    R* sX = sA + R_KC * RP;                  // [R_TB][XS]
+    __shared__ int s_src[R_TB], s_tgt[R_TB];
+    const int tid = threadIdx.x;
+    const int4 b = g.batches[blockIdx.x];
+    const int kidx = b.x, start = b.y, cnt = b.z;
+    int c, lev, ox, oy, oz;
+    rkey_decode(g.kval[kidx], c, lev, ox, oy, oz);
+    const R* A = reinterpret_cast<const R*>(g.ops) + (size_t)kidx * KP * RP;
+    if (tid < R_TB) {
+        if (tid < cnt) {
+            const uint32_t e = g.order[start + tid];
+            s_src[tid] = (int)(g.ent[e] & LFMM_ENT_MASK);
+            s_tgt[tid] = g.tgt[e];
+        } else {
+            s_src[tid] = -1;
+            s_tgt[tid] = -1;
+        }
+    }
+    __syncthreads();
+    const int cgs = cnt > 32 ? 16 : (cnt > 16 ? 8 : 4);
+    const int ncol = 4 * cgs;
+    const R ih = (R)(1.0 / g.levelh[lev]);
+    const int tot = ncol * KP;
+    for (int r = 0; r < g.nr; ++r) {
+        if (r > 0) __syncthreads();  // the previous vector's products are read out of sX
+        const R* M = reinterpret_cast<const R*>(g.M) + (size_t)r * g.stride;
+        for (int b0 = tid; b0 < tot; b0 += 8 * R_T) {
+            R v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int idx = b0 + u * R_T;
+                v[u] = R(0);
+                if (idx < tot) {
+                    const int j = idx / KP, k = idx - j * KP;
+                    const int s = s_src[j];
+                    if (s >= 0 && k < nc) v[u] = M[(size_t)s * nc + k];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int idx = b0 + u * R_T;
+                if (idx < tot) {
+                    const int j = idx / KP, k = idx - j * KP;
+                    sX[j * XS + k] = v[u];
+                }
+            }
+        }
+        R* L = reinterpret_cast<R*>(g.L) + (size_t)r * g.stride;
+        if (cgs == 16)
+            m2r_tile_kc<R, RP, 16>(A, sA, sX, cnt, s_tgt, ih, L, nc);
+        else if (cgs == 8)
+            m2r_tile_kc<R, RP, 8>(A, sA, sX, cnt, s_tgt, ih, L, nc);
+        else
+            m2r_tile_kc<R, RP, 4>(A, sA, sX, cnt, s_tgt, ih, L, nc);
+    }
+}
+
 template <typename R, int RP>
 static LfErr m2r_build_ops(lfmm_ctx* ctx, cudaStream_t st)
 {
@@ -559,6 +681,30 @@ static LfErr m2r_apply_rp(lfmm_ctx* ctx, cudaStream_t st)
     return lf_cuda(cudaGetLastError(), "m2r gemm");
 }
 
+template <typename R, int RP>
+static LfErr m2r_apply_kc(lfmm_ctx* ctx, cudaStream_t st)
+{
+    if (ctx->m2r_ops_prec != (sizeof(R) == 4 ? 1 : 0)) LF_TRY((m2r_build_ops<R, RP>(ctx, st)));
+    RGemmArgs g;
+    g.p = ctx->p;
+    g.nc = lf_nc(ctx->p);
+    g.batches = ctx->m2r_batches.as<int4>();
+    g.kval = ctx->m2r_kval.as<uint32_t>();
+    g.ops = ctx->m2r_ops.ptr;
+    g.order = ctx->m2r_order.as<uint32_t>();
+    g.ent = ctx->m2r_ent.as<uint32_t>();
+    g.tgt = ctx->m2r_tgt.as<int>();
+    g.levelh = ctx->m2r_levelh.as<double>();
+    g.M = ctx->Mexp.ptr;
+    g.L = ctx->Lexp.ptr;
+    g.stride = (size_t)ctx->nbox_total * g.nc;
+    g.nr = ctx->nrhs_b;
+    const size_t sm = sizeof(R) * ((size_t)R_KC * RP + (size_t)R_TB * (RP + 1)) + 16;
+    LF_CHECK(cudaFuncSetAttribute(k_m2r_gemm_kc<R, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    ++ctx->launches, k_m2r_gemm_kc<R, RP><<<ctx->m2r_nbatch, R_T, sm, st>>>(g);
+    return lf_cuda(cudaGetLastError(), "m2r gemm (operator chunks)");
+}
+
 template <typename R>
 static LfErr m2r_apply_t(lfmm_ctx* ctx, cudaStream_t st)
 {
@@ -566,7 +712,9 @@ static LfErr m2r_apply_t(lfmm_ctx* ctx, cudaStream_t st)
     case 2: return m2r_apply_rp<R, 32>(ctx, st);
     case 4: return m2r_apply_rp<R, 64>(ctx, st);
     case 8: return m2r_apply_rp<R, 128>(ctx, st);
-    default: return "internal: reaction GEMM supports p <= 10";
+    case 12: return m2r_apply_kc<R, 192>(ctx, st);
+    case 16: return m2r_apply_kc<R, 256>(ctx, st);
+    default: return "internal: reaction GEMM supports p <= 15";
     }
 }
 
@@ -578,7 +726,9 @@ LfErr lf_m2r_ops(lfmm_ctx* ctx, cudaStream_t st)
     case 2: return ctx->precision ? m2r_build_ops<float, 32>(ctx, st) : m2r_build_ops<double, 32>(ctx, st);
     case 4: return ctx->precision ? m2r_build_ops<float, 64>(ctx, st) : m2r_build_ops<double, 64>(ctx, st);
     case 8: return ctx->precision ? m2r_build_ops<float, 128>(ctx, st) : m2r_build_ops<double, 128>(ctx, st);
-    default: return "internal: reaction GEMM supports p <= 10";
+    case 12: return ctx->precision ? m2r_build_ops<float, 192>(ctx, st) : m2r_build_ops<double, 192>(ctx, st);
+    case 16: return ctx->precision ? m2r_build_ops<float, 256>(ctx, st) : m2r_build_ops<double, 256>(ctx, st);
+    default: return "internal: reaction GEMM supports p <= 15";
     }
 }
 

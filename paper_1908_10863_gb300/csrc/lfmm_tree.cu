@@ -390,11 +390,23 @@ __global__ void k_level_ends(int off, int nb, int64_t n, int child_end, const in
     if (!is_leaf) cend[b] = (i + 1 < nb) ? cbeg[b + 1] : child_end;
 }
 
-__global__ void k_centers(const uint32_t* __restrict__ bkey, int off, int nb, int level, double h, double ox,
-                          double oy, double oz, LfD4* __restrict__ cen, int4* __restrict__ grid)
+// Every level in one launch: box b belongs to level l when off[l] <= b <
+// off[l] + nb[l] (finest level first in the box ids).
+struct CenterLevels {
+    int depth;
+    int off[17];
+    double h[17];
+};
+
+__global__ void k_centers(const uint32_t* __restrict__ bkey, int nbox, CenterLevels lv, double ox, double oy,
+                          double oz, LfD4* __restrict__ cen, int4* __restrict__ grid)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nb) return;
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    int level = lv.depth;
+    while (level > 0 && b >= lv.off[level - 1]) --level;
+    const double h = lv.h[level];
+    const int off = lv.off[level], i = b - off;
     uint32_t k = bkey[off + i];
     uint32_t layer = k >> (3 * level);
     uint32_t mort = (level > 0) ? (k & ((1u << (3 * level)) - 1u)) : 0u;
@@ -857,11 +869,16 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
         std::vector<int> mone(r.nbox, -1);
         LF_CHECK(cudaMemcpyAsync(par + r.off, mone.data(), sizeof(int) * r.nbox, cudaMemcpyHostToDevice, st));
     }
-    for (int l = 0; l <= depth; ++l) {
-        const LfmmLevel& lv = ctx->levels[l];
-        ++ctx->launches, k_centers<<<lf_blocks(lv.nbox, 256), 256, 0, st>>>(bkey, lv.off, lv.nbox, l, lv.h, ctx->origin[0],
-                                                            ctx->origin[1], ctx->origin[2],
-                                                            ctx->box_center.as<LfD4>(), ctx->box_grid.as<int4>());
+    {
+        CenterLevels cl;
+        cl.depth = depth;
+        for (int l = 0; l <= depth; ++l) {
+            cl.off[l] = ctx->levels[l].off;
+            cl.h[l] = ctx->levels[l].h;
+        }
+        ++ctx->launches, k_centers<<<lf_blocks(tot, 256), 256, 0, st>>>(bkey, tot, cl, ctx->origin[0], ctx->origin[1],
+                                                                        ctx->origin[2], ctx->box_center.as<LfD4>(),
+                                                                        ctx->box_grid.as<int4>());
     }
     LF_TRY(lf_cuda(cudaGetLastError(), "centers"));
     {

@@ -118,3 +118,23 @@ def test_high_contrast_full_size(high_contrast_ref, p, precision):
           % (p, "fp32" if precision else "fp64", len(t), *e))
     bp, bf = HIGH_CONTRAST[p, precision]
     assert e[0] < bp and e[1] < bf
+
+
+# Section 4's accuracy experiment: P4-shaped domains, eps = (21.2, 47.5, 62.8),
+# N = 2,848, every charge a target.  Measured Err2(phi) FP64:
+# p = 4 5.57e-4, 8 1.23e-5, 12 4.70e-7, 16 2.68e-8, 20 1.65e-10.
+PAPER_P4 = {4: 1e-3, 8: 2.5e-5, 12: 1e-6, 16: 6e-8, 20: 5e-10}
+
+
+def test_paper_p4_domains_converge_geometrically():
+    w = workloads.paper_p4()
+    ref, refE = oracle.direct(w.d, w.eps, w.xyz, w.layer, w.q, mode=oracle.MODE_IMAGES)
+    t = np.arange(w.n)
+    errs = {}
+    for p, bound in PAPER_P4.items():
+        errs[p] = _err(w, p, 0, t, ref, refE)
+        print("paper P4 domains p=%d fp64: Err2 phi %.2e field %.2e" % (p, *errs[p]))
+        assert errs[p][0] < bound
+    ps = sorted(errs)
+    for a, b in zip(ps, ps[1:]):  # every 4 orders gain more than a factor of 10
+        assert errs[b][0] < 0.1 * errs[a][0]

@@ -165,7 +165,7 @@ def test_near_interface_forms_match_oracle(precision, tol_phi, tol_fld):
     assert e_fld < tol_fld
 
 
-@pytest.mark.parametrize("p", [4, 8, 10])
+@pytest.mark.parametrize("p", [4, 8, 10, 12, 14])
 def test_precision_change_after_build_reassembles_reaction_operators(p):
     # the keyed reaction operators are assembled at build time in the build's
     # precision; a later precision change must assemble them again
@@ -282,3 +282,20 @@ def test_full_size_sampled_against_oracle(precision, tol):
                                                                                         st["m2l_free"]))
     assert st["timeouts"] == 0
     assert e_phi < tol and e_fld < 5 * tol
+
+
+@pytest.mark.parametrize("p,tol", [(12, 1e-6), (14, 3e-7)])
+def test_keyed_reaction_m2l_high_order_against_oracle(p, tol):
+    # orders 11 .. 15 stage each key's operator in chunks; FP64 against the
+    # exact image series (measured at N = 20,000: p = 12 ~5e-7, p = 14 ~1e-7)
+    w = workloads.config2(20000)
+    with LayeredFMM(w.d, w.eps, p) as f:
+        f.build(w.xyz, w.layer)
+        st = f.stats()
+        phi, E = f.evaluate(w.q)
+    assert st["reaction_keys"] > 0
+    t = workloads.subsample(w.n, 300)
+    ref, refE = oracle.direct(w.d, w.eps, w.xyz, w.layer, w.q, targets=t, mode=oracle.MODE_IMAGES)
+    e = oracle.err2(ref, phi[t])
+    print("config2 20k p=%d FP64 keyed reaction M2L: Err2 phi %.2e field %.2e" % (p, e, oracle.err2(refE, E[t])))
+    assert e < tol
