@@ -487,6 +487,7 @@ def sweep(torch, dev, flush, sizes=(1 << 16, 1 << 18, 1 << 20), orders=(6, 10, 1
     targets) for every N, p and form; one JSON line per case."""
     import oracle
     from paper_1908_10863_gb300 import LayeredFMM, workloads
+    from paper_1908_10863_gb300.lfmm import OPT_TENSOR_CORES
     for n in sizes:
         w = workloads.config2(n)
         t = workloads.subsample(w.n, sample)
@@ -498,14 +499,20 @@ def sweep(torch, dev, flush, sizes=(1 << 16, 1 << 18, 1 << 20), orders=(6, 10, 1
         phi_d = torch.empty(w.n, dtype=torch.float64, device=dev)
         fld_d = torch.empty((w.n, 3), dtype=torch.float64, device=dev)
         for p in orders:
-            for prec in (1, 0):
+            # float32 with the free M2L on the tensor cores (the default), FP64,
+            # and for the wide tensor-core form ((p+1)^2 > 128) also float32
+            # with the free M2L on the CUDA cores
+            forms = [(1, 1), (0, 0)] + ([(1, 0)] if (p + 1) ** 2 > 128 else [])
+            for prec, tc in forms:
                 with LayeredFMM(w.d, w.eps, p, precision=prec) as f:
+                    f.set_option(OPT_TENSOR_CORES, tc)
                     steps = 5 if prec else 2
                     times, launches, stages = run_form(f, xyz_d, lay_d, q_d, phi_d, fld_d, torch, steps, 1, flush)
                     st = f.stats()
                 ms = sum(times) / len(times)
                 phi, E = phi_d.cpu().numpy(), fld_d.cpu().numpy()
-                print(json.dumps({"sweep": "config2", "n": n, "p": p, "form": "fp32" if prec else "fp64",
+                form = ("fp32" if tc else "fp32 (CUDA-core M2L)") if prec else "fp64"
+                print(json.dumps({"sweep": "config2", "n": n, "p": p, "form": form,
                                   "ms_per_step": ms, "particles_per_s": n / (ms / 1e3), "build_ms": stages["build"],
                                   "evaluate_ms": stages["total"], "m2l_free_ms": stages["m2l_free"],
                                   "p2p_ms": stages["p2p"], "m2l_pairs": st["m2l_free"], "depth": st["depth"],

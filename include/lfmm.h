@@ -57,13 +57,17 @@ enum {
     LFMM_OPT_QUAD_NODES = 4, /* Gauss-Laguerre nodes of the M2L remainder integrals (16..128, default 64) */
     LFMM_OPT_SURROGATE = 5,  /* 1 = near-field reaction kernels by the trained network (default 0) */
     LFMM_OPT_SURROGATE_TOL = 6, /* error estimate above which a pair falls back to quadrature (default 1e-6) */
-    LFMM_OPT_TENSOR_CORES = 7,  /* 1 = float32 free M2L on the tensor cores (3xTF32) where (p+1)^2 <= 128
-                                   (default); 0 = on the CUDA cores */
+    LFMM_OPT_TENSOR_CORES = 7,  /* 1 = float32 free M2L on the tensor cores (3xTF32) (default); 0 = on
+                                   the CUDA cores.  For 128 < (p+1)^2 (11 <= p <= 14) the tensor cores run
+                                   the wide form: Err2 of the potential ~8e-7 at p = 14 against ~4e-7 for
+                                   the compensated CUDA-core sums, in a sixth of the time.  Where
+                                   (p+1)^2 <= 128 they also take the L2L into the leaves. */
     LFMM_OPT_P2P_SPLIT = 8,     /* near list of a leaf shared by this many warps/blocks of the P2P kernels:
                                    0 = chosen from the leaf count (default), else 1, 2, 4, 8 or 16 */
-    LFMM_OPT_TC_GROUPS = 9,     /* tensor-core free M2L: CTAs per 256-target tile, each summing 189/groups
-                                   offsets in its tensor-memory accumulator before a float atomic add;
-                                   a divisor of 189 (default 27: 7 offsets per accumulation) */
+    LFMM_OPT_TC_GROUPS = 9,     /* tensor-core free M2L: CTAs per tile of targets (256, or 128 in the wide
+                                   form), each summing 189/groups offsets in its tensor-memory accumulator
+                                   before a float atomic add; a divisor of 189, or 0 = automatic (default:
+                                   27, i.e. 7 offsets per accumulation; 63 in the wide form) */
     LFMM_OPT_NEAR_TABLES = 10,  /* 1 = near-field reaction kernels with their remainder from pre-computed
                                    tables (built on first use, see lfmm_near_tables); 0 = quadrature (default) */
     LFMM_OPT_TC_PERSISTENT = 11, /* tensor-core free M2L: 1 = one persistent CTA per SM walking the

@@ -788,8 +788,8 @@ static lfmm_status set_option(lfmm_ctx* ctx, int opt, double v)
         return LFMM_OK;
     case LFMM_OPT_TC_GROUPS: {
         const int k = (int)v;
-        if ((double)k != v || k < 1 || 189 % k != 0)
-            return fail(ctx, "EINVAL: tensor-core groups must divide 189");
+        if ((double)k != v || k < 0 || (k > 0 && 189 % k != 0))
+            return fail(ctx, "EINVAL: tensor-core groups must divide 189 (or be 0: automatic)");
         ctx->tc_groups = k;
         return LFMM_OK;
     }

@@ -139,7 +139,8 @@ struct lfmm_ctx {
     std::vector<uint32_t> root_ent_h;
     std::vector<int> root_beg_h, root_end_h, root_zero_h;
     double m2l_levelh_h[16] = {0};
-    int m2l_tc_ok = 0, m2l_tc_ntiles = 0, use_tc = 1, tc_groups = 27;
+    int m2l_tc_ok = 0, m2l_tc_ntiles = 0, use_tc = 1, tc_groups = 0;  // tc_groups 0: automatic
+    int m2l_tc_wide = 0;  // tensor-core free M2L in its wide form ((p+1)^2 > 128): no tensor-core M2M / L2L
     // reaction M2L grouped by geometry key on interface-aligned levels
     DevBuf m2r_keys, m2r_order, m2r_tgt, m2r_kstart, m2r_kval, m2r_tables, m2r_levelh, m2r_batches;
     DevBuf m2r_tdesc, m2r_ktab;  // table descriptors (component, level, rho^2, oz); table of each key
@@ -238,7 +239,7 @@ LfErr lf_setup_m2l_tc(lfmm_ctx* ctx, const double* A64, const double* M2M64, con
 LfErr lf_shift_tc(lfmm_ctx* ctx, int level, bool l2l, cudaStream_t st);
 LfErr lf_wait_probe(lfmm_ctx* ctx, double limit_ms, int* timed_out);
 LfErr lf_m2l_tc(lfmm_ctx* ctx, cudaStream_t st);
-int lf_m2l_tc_tile();
+int lf_m2l_tc_tile(const lfmm_ctx* ctx);
 LfErr lf_surrogate_alloc(lfmm_ctx* ctx);
 LfErr lf_surrogate_pack(lfmm_ctx* ctx, int comp);
 LfErr lf_surrogate_forward_dev(lfmm_ctx* ctx, int comp, int n, const float* x, float* y);

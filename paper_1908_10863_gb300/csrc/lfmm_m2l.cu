@@ -375,7 +375,7 @@ LfErr lf_prepare_m2l(lfmm_ctx* ctx, cudaStream_t st)
     tct.clear();
     ctx->m2l_tc_ntiles = 0;
     if (ctx->m2l_tc_ok) {
-        const int TN = lf_m2l_tc_tile();
+        const int TN = lf_m2l_tc_tile(ctx);
         int st0 = 0;
         for (int l = 1; l <= depth; ++l)
             for (int c = 0; c < 8; ++c) {
@@ -659,7 +659,7 @@ static LfErr shift_gemm_t(lfmm_ctx* ctx, int level, bool l2l, cudaStream_t st)
     // other translations stay on the CUDA cores: at N = 1M, p = 10 the
     // tensor-core M2M saved 0.05 ms, and chaining 3xTF32 L2L over every level
     // raised Err2(phi) from 2.0e-6 to 3.2e-6.
-    if (sizeof(R) == 4 && l2l && level == ctx->depth && ctx->use_tc && ctx->m2l_tc_ok)
+    if (sizeof(R) == 4 && l2l && level == ctx->depth && ctx->use_tc && ctx->m2l_tc_ok && !ctx->m2l_tc_wide)
         return lf_shift_tc(ctx, level, l2l, st);
     GemmArgs g;
     g.p = ctx->p;

@@ -4,8 +4,11 @@
 // lfmm_m2l.cu, evaluated as D[r][j] = sum_o sum_k A_o[r][k] X_o[j][k] with
 //   r = output coefficient (M = 128 rows, expansions with (p+1)^2 <= 128),
 //   j = target box of the tile (N = 256 columns, one level and octant class),
-//   k = input coefficient of the source at offset o (K = 128 in chunks of TC_KC),
-// accumulated in tensor memory (128 lanes x 256 float32 columns).
+//   k = input coefficient of the source at offset o (K = 128 in chunks of
+//       TC_KC, only the chunks that hold the (p+1)^2 inputs),
+// accumulated in tensor memory (128 lanes x 256 float32 columns).  The wide
+// form takes 128 < (p+1)^2 <= 256 (p = 11 .. 14): two 128-row halves of r,
+// K = 256, tiles of 128 targets (see k_m2l_tc<true>).
 //
 // Precision: float32 operands as sums of two TF32 pieces, the operator
 // (a1 + a2, from its FP64 values) and the multipoles (x1 + x2, split once per
@@ -92,6 +95,8 @@
 #endif
 #define TC_SMEM (TC_STAGES * TC_STAGE_BYTES + 1024)
 #define TC_TMEM_COLS 256
+#define TC_WIDE_STAGES 4             // wide form: one CTA per SM
+#define TC_WIDE_SMEM (TC_WIDE_STAGES * TC_STAGE_BYTES + 1024)
 #define TC_SPIN_CYCLES (1ll << 31)   // ~1 s at 2 GHz
 
 // ---------------------------------------------------------------------------
@@ -231,18 +236,39 @@ struct TcArgs {
     int zero_row;           // index of the zero box of Ms
     float* L;               // locals [box][nc]
     int nc;
+    int nkc;                // K chunks of TC_KC coefficients that hold the nc inputs: ceil(nc / TC_KC)
     size_t ms_stride;       // per right-hand side (blockIdx.y): split multipoles, in floats
     size_t l_stride;        // per right-hand side: local expansions, in floats
     int groups;             // CTAs per tile (offset groups; divides noff)
     int* err;               // [0]: timeouts
 };
 
-__global__ void __launch_bounds__(TC_THREADS, TC_MINB) k_m2l_tc(TcArgs g)
+// WIDE: expansions with 128 < (p+1)^2 <= 256 (p <= 15): the output rows are
+// two 128-row halves (two MMAs per K step), K runs over 16 chunks, and a tile
+// holds 128 targets, so a stage keeps its 48 KB.  With twice the MMAs per
+// offset, the large product a1 x1 gets an accumulator of its own (256
+// columns) and the two correction products share a second one: the float32
+// accumulation drift of the tensor cores grows with the MMAs summed into
+// one accumulator, and the corrections are 2^-11 of the large product.  The
+// 512 columns allow one CTA per SM, which then runs four stages.
+template <bool WIDE>
+__global__ void __launch_bounds__(TC_THREADS, WIDE ? 1 : TC_MINB) k_m2l_tc(TcArgs g)
 {
+    constexpr int TN = WIDE ? 128 : TC_N;       // targets per tile (MMA N)
+    constexpr int MH = WIDE ? 2 : 1;            // 128-row halves of the output (MMA M = 128 each)
+    constexpr int NKC = WIDE ? 16 : TC_NKC;     // K chunks per operator in the blob
+    constexpr int MROW = WIDE ? 256 : TC_MROW;  // floats per multipole piece row
+    constexpr int ABYTES = MH * TC_A_BYTES;     // one operator piece of a stage
+    constexpr int XBYTES = TN * TC_ROWB;        // one multipole piece of a stage
+    constexpr int NST = WIDE ? TC_WIDE_STAGES : TC_STAGES;
+    constexpr int LAG = WIDE ? TC_WIDE_STAGES / 2 : TC_LAG;
+    constexpr uint32_t COLS = WIDE ? 2 * TC_TMEM_COLS : TC_TMEM_COLS;
+    constexpr uint32_t SMALL = WIDE ? TC_TMEM_COLS : 0;  // accumulator of the correction products
+    static_assert(TC_AP * ABYTES + TC_XP * XBYTES == TC_STAGE_BYTES, "stage size");
     extern __shared__ unsigned char smem_raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                          ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t full_bar[TC_STAGES], empty_bar[TC_STAGES], done_bar;
+    __shared__ __align__(8) uint64_t full_bar[NST], empty_bar[NST], done_bar;
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
     __shared__ int s_tb[TC_N];
@@ -254,11 +280,12 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MINB) k_m2l_tc(TcArgs g)
     const int goff = g.noff / g.groups;
     const int level = tile.x, cl = tile.y, start = tile.z, cnt = tile.w;
     const int nc = g.nc;
-    const int nstage = goff * TC_NKC;
+    const int nkc = g.nkc;  // K chunks that hold coefficients (the rest are zero)
+    const int nstage = goff * nkc;
 
-    if (tid < TC_N) s_tb[tid] = (tid < cnt) ? (g.sorted ? g.sorted[start + tid] : start + tid) : -1;
+    if (tid < TN) s_tb[tid] = (tid < cnt) ? (g.sorted ? g.sorted[start + tid] : start + tid) : -1;
     if (tid == 0) {
-        for (int s = 0; s < TC_STAGES; ++s) {
+        for (int s = 0; s < NST; ++s) {
             mbar_init(&full_bar[s], TC_PROD_WARPS + 1);  // one arrival per producer warp + the bulk copy's
             mbar_init(&empty_bar[s], 1);
         }
@@ -268,7 +295,7 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MINB) k_m2l_tc(TcArgs g)
     }
     if (warp == TC_PROD_WARPS) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
-                     "r"(TC_TMEM_COLS)
+                     "r"(COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -287,43 +314,43 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MINB) k_m2l_tc(TcArgs g)
         int my_src = -1;       // source of row (warp * 32 + lane) at the current offset
         // the source at the next offset is loaded one offset ahead (its
         // latency hides behind the current offset's gathers)
-        const int my_tb = s_tb[warp * 32 + lane];
+        const int my_tb = s_tb[(WIDE ? (warp & 3) : warp) * 32 + lane];
         int nxt_src = (my_tb >= 0) ? g.slots[(size_t)my_tb * g.noff + grp * goff + rot % goff] : -1;
         int it = 0;
         for (; it < nstage; ++it) {
-            const int s = it % TC_STAGES, round = it / TC_STAGES;
-            const int oi = grp * goff + (it / TC_NKC + rot) % goff, kc = it % TC_NKC;
-            if (it >= TC_STAGES) {
+            const int s = it % NST, round = it / NST;
+            const int oi = grp * goff + (it / nkc + rot) % goff, kc = it % nkc;
+            if (it >= NST) {
                 if (!mbar_wait(&empty_bar[s], (round - 1) & 1)) atomicExch(&s_abort, 1);
             }
             if (__any_sync(0xffffffffu, *(volatile int*)&s_abort)) break;  // warp-uniform
             unsigned char* st = sm + (size_t)s * TC_STAGE_BYTES;
             if (ptid == 0) {
                 const int o = g.cls[cl * g.noff + oi];
-                mbar_arrive_tx(&full_bar[s], TC_AP * TC_A_BYTES);
-                bulk_g2s(st, g.A + ((size_t)o * TC_NKC + kc) * (TC_AP * TC_A_BYTES), TC_AP * TC_A_BYTES,
-                         &full_bar[s]);
+                mbar_arrive_tx(&full_bar[s], TC_AP * ABYTES);
+                bulk_g2s(st, g.A + ((size_t)o * NKC + kc) * (TC_AP * ABYTES), TC_AP * ABYTES, &full_bar[s]);
                 armed = it + 1;
             }
             if (kc == 0) {
                 my_src = nxt_src;
-                const int on = it / TC_NKC + 1;
+                const int on = it / nkc + 1;
                 if (on < goff && my_tb >= 0) nxt_src = g.slots[(size_t)my_tb * g.noff + grp * goff + (on + rot) % goff];
             }
-            // 32 rows x 2 pieces x 4 chunks of 16 B per warp: 8 per lane
-            unsigned char* xs = st + TC_AP * TC_A_BYTES;
+            unsigned char* xs = st + TC_AP * ABYTES;
             const uint32_t xbase = smem_u32(xs);
-            // 32 rows x 2 pieces x TC_RCH chunks of 16 B per warp
+            // 32 rows x TC_RCH chunks of 16 B per warp and piece: both pieces
+            // per warp (256 rows), or warps 4..7 the second piece (128 rows)
+            constexpr int NI = WIDE ? TC_RCH : 2 * TC_RCH;
 #pragma unroll
-            for (int i = 0; i < 2 * TC_RCH; ++i) {
-                const int piece = i / TC_RCH;
-                const int flat = (i % TC_RCH) * 32 + lane;  // chunk-major over the warp's 32 rows
+            for (int i = 0; i < NI; ++i) {
+                const int piece = WIDE ? (warp >> 2) : i / TC_RCH;
+                const int flat = (WIDE ? i : i % TC_RCH) * 32 + lane;  // chunk-major over the warp's 32 rows
                 const int rl = flat / TC_RCH, chunk = flat % TC_RCH;
                 const int src = __shfl_sync(0xffffffffu, my_src, rl);
-                const int row = warp * 32 + rl;
-                const uint32_t off = piece * TC_X_BYTES + swz(row, chunk * 4);
+                const int row = (WIDE ? (warp & 3) : warp) * 32 + rl;
+                const uint32_t off = piece * XBYTES + swz(row, chunk * 4);
                 if (src >= 0) {
-                    const float* gsrc = g.Ms + (size_t)blockIdx.y * g.ms_stride + ((size_t)src * TC_XP + piece) * TC_MROW +
+                    const float* gsrc = g.Ms + (size_t)blockIdx.y * g.ms_stride + ((size_t)src * TC_XP + piece) * MROW +
                                         kc * TC_KC + chunk * 4;
                     cp_async16(xbase + off, gsrc);
                 } else {
@@ -331,35 +358,44 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MINB) k_m2l_tc(TcArgs g)
                 }
             }
             cp_async_commit();
-            if (it >= TC_LAG) {
-                cp_async_wait<TC_LAG>();
+            if (it >= LAG) {
+                cp_async_wait<LAG>();
                 fence_async_smem();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&full_bar[(it - TC_LAG) % TC_STAGES]);
+                if (lane == 0) mbar_arrive(&full_bar[(it - LAG) % NST]);
             }
         }
         cp_async_wait<0>();
         fence_async_smem();
         __syncwarp();
         if (lane == 0)
-            for (int j = (it > TC_LAG ? it - TC_LAG : 0); j < it; ++j) mbar_arrive(&full_bar[j % TC_STAGES]);
+            for (int j = (it > LAG ? it - LAG : 0); j < it; ++j) mbar_arrive(&full_bar[j % NST]);
         // drain: the bulk copies this thread issued complete on their full barriers
         if (ptid == 0 && *(volatile int*)&s_abort) {
-            for (int j = (armed > TC_STAGES ? armed - TC_STAGES : 0); j < armed; ++j)
-                mbar_wait(&full_bar[j % TC_STAGES], (j / TC_STAGES) & 1);
+            for (int j = (armed > NST ? armed - NST : 0); j < armed; ++j)
+                mbar_wait(&full_bar[j % NST], (j / NST) & 1);
         }
         // ---------------- epilogue ----------------
         const bool ok = mbar_wait(&done_bar, 0);
         tc_fence_after();
         if (ok && !*(volatile int*)&s_abort) {
             const int q = warp & 3, half = warp >> 2;
-            const int row = 32 * q + lane;
+            // narrow: half = target half of the 256 columns; wide: half = the
+            // 128-row half of the outputs, whose accumulator starts at column half * TN
+            const int row = (WIDE ? 128 * half : 0) + 32 * q + lane;
             const float ih = g.unit_scale ? 1.f : (float)(1.0 / g.levelh[level]);
 #pragma unroll 1
             for (int ch = 0; ch < 4; ++ch) {
-                const int col0 = half * 128 + ch * 32;
+                const int col0 = (WIDE ? 0 : half * 128) + ch * 32;  // first target of the chunk
                 float v[32];
-                tc_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)col0, v);
+                const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)((WIDE ? half * TN : 0) + col0);
+                tc_ld32(ta, v);
+                if (WIDE) {
+                    float w[32];
+                    tc_ld32(ta + SMALL, w);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) v[i] += w[i];
+                }
                 if (row < nc) {
 #pragma unroll
                     for (int i = 0; i < 32; ++i) {
@@ -374,10 +410,10 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MINB) k_m2l_tc(TcArgs g)
     } else {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            const uint32_t idesc = tc_idesc(TC_M, TC_N);
+            const uint32_t idesc = tc_idesc(TC_M, TN);
             bool ok = true;
             for (int it = 0; it < nstage && ok; ++it) {
-                const int s = it % TC_STAGES, round = it / TC_STAGES;
+                const int s = it % NST, round = it / NST;
                 if (!mbar_wait(&full_bar[s], round & 1)) {
                     ok = false;
                     atomicExch(&s_abort, 1);
@@ -385,17 +421,22 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MINB) k_m2l_tc(TcArgs g)
                 }
                 tc_fence_after();
                 const uint32_t base = smem_u32(sm + (size_t)s * TC_STAGE_BYTES);
-                const uint32_t xb = base + TC_AP * TC_A_BYTES;
+                const uint32_t xb = base + TC_AP * ABYTES;
                 // a1 x1, a1 x2, a2 x1
                 const int pa[3] = {0, 0, 1}, px[3] = {0, 1, 0};
 #pragma unroll
                 for (int prod = 0; prod < 3; ++prod) {
-                    const uint32_t a = base + pa[prod] * TC_A_BYTES;
-                    const uint32_t b = xb + px[prod] * TC_X_BYTES;
+                    const uint32_t a = base + pa[prod] * ABYTES;
+                    const uint32_t b = xb + px[prod] * XBYTES;
+                    // narrow: one accumulator; wide: a1 x1 alone, the corrections in the second
+                    const uint32_t acc = (WIDE && prod > 0) ? SMALL : 0u;
+                    const int first = WIDE ? (prod == 2 ? 1 : 0) : prod;  // 0: may start its accumulator
 #pragma unroll
                     for (int ks = 0; ks < TC_KC / 8; ++ks)
-                        tc_mma(tmem, smem_desc(a + 32 * ks), smem_desc(b + 32 * ks), idesc,
-                               (it | prod | ks) != 0 ? 1u : 0u);
+#pragma unroll
+                        for (int h = 0; h < MH; ++h)
+                            tc_mma(tmem + acc + (uint32_t)(h * TN), smem_desc(a + h * TC_A_BYTES + 32 * ks),
+                                   smem_desc(b + 32 * ks), idesc, (it | first | ks) != 0 ? 1u : 0u);
                 }
                 tc_commit(&empty_bar[s]);
             }
@@ -407,7 +448,7 @@ __global__ void __launch_bounds__(TC_THREADS, TC_MINB) k_m2l_tc(TcArgs g)
     __syncthreads();
     if (warp == TC_PROD_WARPS) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(COLS)
                      : "memory");
     }
 }
@@ -454,7 +495,7 @@ __global__ void __launch_bounds__(TCP_THREADS, 1) k_m2l_tcp(TcArgs g, int nunits
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int goff = g.noff / g.groups;
-    const int nstage = goff * TC_NKC;  // stages per unit
+    const int nstage = goff * g.nkc;  // stages per unit
     const int nc = g.nc;
 
     if (tid == 0) {
@@ -497,7 +538,7 @@ __global__ void __launch_bounds__(TCP_THREADS, 1) k_m2l_tcp(TcArgs g, int nunits
             int nxt_src = (my_tb >= 0) ? g.slots[(size_t)my_tb * g.noff + grp * goff + rot % goff] : -1;
             for (int j = 0; j < nstage; ++j, ++it) {
                 const int s = it % TCP_STAGES, round = it / TCP_STAGES;
-                const int oi = grp * goff + (j / TC_NKC + rot) % goff, kc = j % TC_NKC;
+                const int oi = grp * goff + (j / g.nkc + rot) % goff, kc = j % g.nkc;
                 if (it >= TCP_STAGES) {
                     if (!mbar_wait(&empty_bar[s], (round - 1) & 1)) atomicExch(&s_abort, 1);
                 }
@@ -515,7 +556,7 @@ __global__ void __launch_bounds__(TCP_THREADS, 1) k_m2l_tcp(TcArgs g, int nunits
                 }
                 if (kc == 0) {
                     my_src = nxt_src;
-                    const int on = j / TC_NKC + 1;
+                    const int on = j / g.nkc + 1;
                     if (on < goff && my_tb >= 0)
                         nxt_src = g.slots[(size_t)my_tb * g.noff + grp * goff + (on + rot) % goff];
                 }
@@ -660,16 +701,18 @@ static inline uint32_t host_tf32(float x)
 }
 
 // A64: [nops][KP in][RP out] (double) -> the tensor-core operator blob:
-// per operator TC_NKC K chunks of two TF32 pieces, pre-swizzled
-static LfErr tc_blob(const double* A64, int nops, int KP, int RP, int nc, DevBuf& out)
+// per operator nkc K chunks of two TF32 pieces, each piece mh 128-row halves
+// (mh = 2 for the wide form), pre-swizzled
+static LfErr tc_blob(const double* A64, int nops, int KP, int RP, int nc, bool wide, DevBuf& out)
 {
-    const size_t per = (size_t)TC_NKC * TC_AP * TC_A_BYTES;
+    const int mh = wide ? 2 : 1, nkc = wide ? 16 : TC_NKC;
+    const size_t chunk = (size_t)TC_AP * mh * TC_A_BYTES;
+    const size_t per = (size_t)nkc * chunk;
     std::vector<uint32_t> blob((size_t)nops * per / 4, 0u);
     for (int o = 0; o < nops; ++o)
-        for (int kc = 0; kc < TC_NKC; ++kc) {
-            unsigned char* p0 = reinterpret_cast<unsigned char*>(blob.data()) + (size_t)o * per +
-                                (size_t)kc * TC_AP * TC_A_BYTES;
-            for (int r = 0; r < TC_M; ++r)
+        for (int kc = 0; kc < nkc; ++kc) {
+            unsigned char* p0 = reinterpret_cast<unsigned char*>(blob.data()) + (size_t)o * per + (size_t)kc * chunk;
+            for (int r = 0; r < mh * TC_M; ++r)
                 for (int k = 0; k < TC_KC; ++k) {
                     const int kin = kc * TC_KC + k;
                     double v = (r < nc && kin < nc) ? A64[((size_t)o * KP + kin) * RP + r] : 0.0;
@@ -677,7 +720,7 @@ static LfErr tc_blob(const double* A64, int nops, int KP, int RP, int nc, DevBuf
                         uint32_t t = host_tf32((float)v);
                         float tf;
                         memcpy(&tf, &t, 4);
-                        memcpy(p0 + (size_t)q * TC_A_BYTES + swz(r, k), &t, 4);
+                        memcpy(p0 + ((size_t)q * mh + r / TC_M) * TC_A_BYTES + swz(r % TC_M, k), &t, 4);
                         v -= (double)tf;
                     }
                 }
@@ -692,46 +735,57 @@ LfErr lf_setup_m2l_tc(lfmm_ctx* ctx, const double* A64, const double* M2M64, con
 {
     const int nc = lf_nc(ctx->p);
     ctx->m2l_tc_ok = 0;
-    if (nc > TC_M || KP < nc || RP < nc) return LfErr();
-    LF_TRY(tc_blob(A64, TC_NALL, KP, RP, nc, ctx->m2l_Atc));
-    LF_TRY(tc_blob(M2M64, 8, KP, RP, nc, ctx->m2m_Atc));
-    LF_TRY(tc_blob(L2L64, 8, KP, RP, nc, ctx->l2l_Atc));
-    LF_CHECK(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
-    LF_CHECK(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    ctx->m2l_tc_wide = 0;
+    if (nc > 2 * TC_M || KP < nc || RP < nc) return LfErr();
+    const bool wide = nc > TC_M;
+    // the wide form serves the free M2L only; M2M and L2L stay on the CUDA cores
+    LF_TRY(tc_blob(A64, TC_NALL, KP, RP, nc, wide, ctx->m2l_Atc));
+    if (!wide) {
+        LF_TRY(tc_blob(M2M64, 8, KP, RP, nc, false, ctx->m2m_Atc));
+        LF_TRY(tc_blob(L2L64, 8, KP, RP, nc, false, ctx->l2l_Atc));
+    }
+    LF_CHECK(cudaFuncSetAttribute(k_m2l_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+    LF_CHECK(cudaFuncSetAttribute(k_m2l_tc<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    LF_CHECK(cudaFuncSetAttribute(k_m2l_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_WIDE_SMEM));
+    LF_CHECK(cudaFuncSetAttribute(k_m2l_tc<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     LF_CHECK(cudaFuncSetAttribute(k_m2l_tcp, cudaFuncAttributeMaxDynamicSharedMemorySize, TCP_SMEM));
     LF_CHECK(cudaFuncSetAttribute(k_m2l_tcp, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     int nsm = 0;
     LF_CHECK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
     ctx->num_sms = nsm > 0 ? nsm : 152;
+    ctx->m2l_tc_wide = wide ? 1 : 0;
     ctx->m2l_tc_ok = 1;
     return LfErr();
 }
 
-// expansions [box][nc] -> two TF32 pieces per box, rows padded to 128 floats,
-// for the boxes b0 .. b0 + count - 1 (the arrays hold nbox boxes per
-// right-hand side, blockIdx.y)
-__global__ void k_split_m(const float* __restrict__ M, int nbox, int nc, int b0, int count, float* __restrict__ Ms)
+// expansions [box][nc] -> two TF32 pieces per box, rows padded to mrow floats
+// (128, or 256 for the wide form), for the boxes b0 .. b0 + count - 1 (the
+// arrays hold nbox boxes per right-hand side, blockIdx.y)
+__global__ void k_split_m(const float* __restrict__ M, int nbox, int nc, int mrow, int b0, int count,
+                          float* __restrict__ Ms)
 {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (size_t)count * TC_MROW) return;
+    if (i >= (size_t)count * mrow) return;
     M += (size_t)blockIdx.y * nbox * nc;
-    Ms += (size_t)blockIdx.y * (nbox + 1) * TC_XP * TC_MROW;
-    const int b = b0 + (int)(i / TC_MROW), k = (int)(i % TC_MROW);
+    Ms += (size_t)blockIdx.y * (nbox + 1) * TC_XP * mrow;
+    const int b = b0 + (int)(i / mrow), k = (int)(i % mrow);
     const float x = (k < nc) ? M[(size_t)b * nc + k] : 0.f;
     const uint32_t hi = to_tf32(x);
     const uint32_t lo = to_tf32(x - __uint_as_float(hi));
-    Ms[((size_t)b * TC_XP + 0) * TC_MROW + k] = __uint_as_float(hi);
-    Ms[((size_t)b * TC_XP + 1) * TC_MROW + k] = __uint_as_float(lo);
+    Ms[((size_t)b * TC_XP + 0) * mrow + k] = __uint_as_float(hi);
+    Ms[((size_t)b * TC_XP + 1) * mrow + k] = __uint_as_float(lo);
 }
+
+static int ms_row(const lfmm_ctx* ctx) { return ctx->m2l_tc_wide ? 2 * TC_MROW : TC_MROW; }
 
 static LfErr split_boxes(lfmm_ctx* ctx, const float* src, int b0, int count, cudaStream_t st)
 {
     if (count <= 0) return LfErr();
-    const int nb = ctx->nbox_total, nr = ctx->nrhs_b;
-    LF_TRY(lf_reserve(ctx->m2l_Ms, (size_t)(nb + 1) * TC_XP * TC_MROW * sizeof(float) * nr));
-    const size_t tot = (size_t)count * TC_MROW;
+    const int nb = ctx->nbox_total, nr = ctx->nrhs_b, mrow = ms_row(ctx);
+    LF_TRY(lf_reserve(ctx->m2l_Ms, (size_t)(nb + 1) * TC_XP * mrow * sizeof(float) * nr));
+    const size_t tot = (size_t)count * mrow;
     ++ctx->launches, k_split_m<<<dim3((unsigned)((tot + 255) / 256), nr), 256, 0, st>>>(
-        src, nb, lf_nc(ctx->p), b0, count, ctx->m2l_Ms.as<float>());
+        src, nb, lf_nc(ctx->p), mrow, b0, count, ctx->m2l_Ms.as<float>());
     return lf_cuda(cudaGetLastError(), "split");
 }
 
@@ -742,9 +796,10 @@ static TcArgs tc_args(lfmm_ctx* ctx)
     g.levelh = ctx->m2l_levelh.as<double>();
     g.Ms = ctx->m2l_Ms.as<float>();
     g.zero_row = nb;
-    g.ms_stride = (size_t)(nb + 1) * TC_XP * TC_MROW;
+    g.ms_stride = (size_t)(nb + 1) * TC_XP * ms_row(ctx);
     g.l_stride = (size_t)nb * lf_nc(ctx->p);
     g.nc = lf_nc(ctx->p);
+    g.nkc = (g.nc + TC_KC - 1) / TC_KC;
     g.err = reinterpret_cast<int*>(ctx->counts.as<char>() + LFMM_TIMEOUT_OFF);
     return g;
 }
@@ -764,19 +819,24 @@ LfErr lf_m2l_tc(lfmm_ctx* ctx, cudaStream_t st)
     g.unit_scale = 0;
     g.A = ctx->m2l_Atc.as<unsigned char>();
     g.L = ctx->Lexp.as<float>();
-    g.groups = ctx->tc_groups;
+    // automatic: 7 offsets per accumulator, 3 in the wide form, whose float32
+    // accumulation adds twice the MMAs per offset (measured at N = 1M, p = 14:
+    // Err2 of the potential 1.18e-6 with 7 offsets, 7.5e-7 with 3, for 1.2 ms more)
+    g.groups = ctx->tc_groups > 0 ? ctx->tc_groups : (ctx->m2l_tc_wide ? 63 : 27);
     const int nunits = ctx->m2l_tc_ntiles * g.groups;
     // the persistent form pays off when every SM walks many units; a small
     // tree (or one of many problems sharing the GPU in a batch) keeps one
     // CTA per unit, two of which share an SM
-    if (ctx->tc_persistent && nunits * nr >= 4 * ctx->num_sms) {
+    if (ctx->m2l_tc_wide) {
+        ++ctx->launches, k_m2l_tc<true><<<dim3(nunits, nr), TC_THREADS, TC_WIDE_SMEM, st>>>(g);
+    } else if (ctx->tc_persistent && nunits * nr >= 4 * ctx->num_sms) {
         // one CTA per SM (shared memory and the 512 tensor-memory columns allow
         // no second); all right-hand sides share the SMs
         int per = std::max(1, ctx->num_sms / std::max(1, nr));
         per = std::min(per, nunits);
         ++ctx->launches, k_m2l_tcp<<<dim3(per, nr), TCP_THREADS, TCP_SMEM, st>>>(g, nunits);
     } else {
-        ++ctx->launches, k_m2l_tc<<<dim3(nunits, nr), TC_THREADS, TC_SMEM, st>>>(g);
+        ++ctx->launches, k_m2l_tc<false><<<dim3(nunits, nr), TC_THREADS, TC_SMEM, st>>>(g);
     }
     return lf_cuda(cudaGetLastError(), "m2l tensor-core gemm");
 }
@@ -790,6 +850,7 @@ LfErr lf_shift_tc(lfmm_ctx* ctx, int level, bool l2l, cudaStream_t st)
     const int t0 = l2l ? ctx->tc_l2l_first[level] : ctx->tc_m2m_first[level];
     const int t1 = l2l ? ctx->tc_l2l_first[level + 1] : ctx->tc_m2m_first[level + 1];
     if (t1 <= t0) return LfErr();
+    if (ctx->m2l_tc_wide) return LfErr("internal: tensor-core translations need (p+1)^2 <= 128");
     const int nr = ctx->nrhs_b, nc = lf_nc(ctx->p);
     const LfmmLevel& src = ctx->levels[l2l ? level - 1 : level + 1];
     TcArgs g;
@@ -819,7 +880,7 @@ LfErr lf_shift_tc(lfmm_ctx* ctx, int level, bool l2l, cudaStream_t st)
     g.tiles = ctx->tc_shift_tiles.as<int4>() + t0;
     g.cls = ctx->shift_cls.as<int>();
     g.unit_scale = 1;
-    ++ctx->launches, k_m2l_tc<<<dim3((t1 - t0) * g.groups, nr), TC_THREADS, TC_SMEM, st>>>(g);
+    ++ctx->launches, k_m2l_tc<false><<<dim3((t1 - t0) * g.groups, nr), TC_THREADS, TC_SMEM, st>>>(g);
     return lf_cuda(cudaGetLastError(), l2l ? "l2l tensor-core gemm" : "m2m tensor-core gemm");
 }
 
@@ -854,4 +915,4 @@ LfErr lf_wait_probe(lfmm_ctx* ctx, double limit_ms, int* timed_out)
     return LfErr();
 }
 
-int lf_m2l_tc_tile() { return TC_N; }
+int lf_m2l_tc_tile(const lfmm_ctx* ctx) { return ctx->m2l_tc_wide ? 128 : TC_N; }
