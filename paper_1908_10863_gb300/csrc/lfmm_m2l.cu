@@ -281,6 +281,31 @@ __global__ void k_class_keys(ClassLevels lv, int nsort, const uint32_t* __restri
     atomicAdd(&counts[level * 8 + c], 1);
 }
 
+// Free M2L tiles of levels 2 .. depth: the targets of a level are sorted by
+// (octant class, Morton index) and cut into tiles of `tn` per class; the
+// tiles go out with the classes interleaved (tile k of class 0, of class 1,
+// ..., then tile k + 1), so that tiles running at the same time cover one
+// region of the level and share its source multipoles in L2 (class after
+// class, every class streams the whole level's multipoles).
+static void m2l_tiles_interleaved(const int* hcnt, int depth, int tn, std::vector<int4>& out)
+{
+    out.clear();
+    int start = 0;
+    for (int l = 1; l <= depth; ++l) {
+        int first[8], n[8], most = 0;
+        for (int c = 0; c < 8; ++c) {
+            n[c] = hcnt[16 + l * 8 + c];
+            first[c] = start;
+            start += n[c];
+            most = std::max(most, n[c]);
+        }
+        if (l < 2) continue;
+        for (int s = 0; s < most; s += tn)
+            for (int c = 0; c < 8; ++c)
+                if (s < n[c]) out.push_back(make_int4(l, c, first[c] + s, std::min(tn, n[c] - s)));
+    }
+}
+
 LfErr lf_prepare_m2l(lfmm_ctx* ctx, cudaStream_t st)
 {
     ctx->m2l_ntiles = 0;
@@ -337,13 +362,11 @@ LfErr lf_prepare_m2l(lfmm_ctx* ctx, cudaStream_t st)
         l2l_first[l] = (int)l2l_tiles.size();
         for (int c = 0; c < 8; ++c) {
             int n = hcnt[16 + l * 8 + c];
-            for (int s = 0; s < n; s += G_TB) {
-                if (l >= 2) tiles.push_back(make_int4(l, c, start + s, std::min(G_TB, n - s)));
-                l2l_tiles.push_back(make_int4(l, c, start + s, std::min(G_TB, n - s)));
-            }
+            for (int s = 0; s < n; s += G_TB) l2l_tiles.push_back(make_int4(l, c, start + s, std::min(G_TB, n - s)));
             start += n;
         }
     }
+    m2l_tiles_interleaved(hcnt, depth, G_TB, tiles);
     l2l_first[depth + 1] = (int)l2l_tiles.size();
     // M2M tiles: parents of levels 0 .. depth-1 in box order
     std::vector<int4>& m2m_tiles = ctx->m2m_tiles_h;
@@ -376,14 +399,7 @@ LfErr lf_prepare_m2l(lfmm_ctx* ctx, cudaStream_t st)
     ctx->m2l_tc_ntiles = 0;
     if (ctx->m2l_tc_ok) {
         const int TN = lf_m2l_tc_tile(ctx);
-        int st0 = 0;
-        for (int l = 1; l <= depth; ++l)
-            for (int c = 0; c < 8; ++c) {
-                int n = hcnt[16 + l * 8 + c];
-                if (l >= 2)
-                    for (int s = 0; s < n; s += TN) tct.push_back(make_int4(l, c, st0 + s, std::min(TN, n - s)));
-                st0 += n;
-            }
+        m2l_tiles_interleaved(hcnt, depth, TN, tct);
         ctx->m2l_tc_ntiles = (int)tct.size();
         // translations: M2M tiles of parents (levels 0 .. depth-1, box order),
         // L2L tiles of children grouped by octant (levels 1 .. depth)
