@@ -525,36 +525,133 @@ __device__ __noinline__ int pf_fill(const P2PArgs& a, const float4* __restrict__
     return fill;
 }
 
-// pairs of one target with staged sources [u0, u1), compensated every 32
-template <bool SELF>
-__device__ __forceinline__ void pf_pairs(const float4* S, int u0, int u1, float xi, float yi, float zi,
-                                         P2PAcc<float, 1>& A)
+// pairs of this lane's R targets with staged sources [u0, u1), compensated
+// every 32 sources; each staged source is read once for all R targets
+template <bool SELF, int R>
+__device__ __forceinline__ void pf_pairs(const float4* S, int u0, int u1, const float* xi, const float* yi,
+                                         const float* zi, P2PAcc<float, R>& A)
 {
     for (int c0 = u0; c0 < u1; c0 += 32) {
         const int c1 = min(c0 + 32, u1);
-        float P = 0.f, Ex = 0.f, Ey = 0.f, Ez = 0.f;
-#pragma unroll 8
+        P2PPart<float, R> part;
+#pragma unroll
+        for (int r = 0; r < R; ++r) part.P[r].s = part.Ex[r].s = part.Ey[r].s = part.Ez[r].s = 0.f;
+#pragma unroll 2
         for (int u = c0; u < c1; ++u) {
             const float4 v = S[u];
-            const float dx = xi - v.x, dy = yi - v.y, dz = zi - v.z;
-            const float r2 = dx * dx + dy * dy + dz * dz;
-            float ir = rsqrtf(r2);
-            if (SELF) ir = (r2 > 0.f) ? ir : 0.f;  // the target itself: no term
-            const float qi = v.w * ir;
-            const float q3 = qi * ir * ir;
-            P += qi;
-            Ex += q3 * dx;
-            Ey += q3 * dy;
-            Ez += q3 * dz;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const float dx = xi[r] - v.x, dy = yi[r] - v.y, dz = zi[r] - v.z;
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                float ir = rsqrtf(r2);
+                if (SELF) ir = (r2 > 0.f) ? ir : 0.f;  // the target itself: no term
+                const float qi = v.w * ir;
+                const float q3 = qi * ir * ir;
+                part.P[r].s += qi;
+                part.Ex[r].s += q3 * dx;
+                part.Ey[r].s += q3 * dy;
+                part.Ez[r].s += q3 * dz;
+            }
         }
-        A.P[0].add(P);
-        A.Ex[0].add(Ex);
-        A.Ey[0].add(Ey);
-        A.Ez[0].add(Ez);
+        p2p_flush<float, R>(part, A);
     }
 }
 
-__global__ void __launch_bounds__(32 * PF_WARPS, 6) k_p2p_free_staged(P2PArgs a, const float4* __restrict__ rel,
+// One pass over targets base + ti + G r (r < R) of the leaf [tb, te): the
+// lane's slice of the staged near list (restaged in rounds when it did not
+// fit), the slices of a target slot summed by shuffles, stored by slice 0.
+template <int R>
+__device__ __forceinline__ void pf_pass(const P2PArgs& a, const float4* __restrict__ rel, const float* __restrict__ q,
+                                        float4* S, int t, int4 gt, int tb, int te, int eb, int nmine, int part0,
+                                        int base, int lg, int lane, bool once, bool first, PfCursor start,
+                                        PfCursor& cur, int& fill, int& nself, bool& more)
+{
+    const int G = 32 >> lg;
+    const int ti = lane & (G - 1), slice = lane >> (5 - lg);
+    float xi[R], yi[R], zi[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int i = base + ti + G * r;
+        xi[r] = yi[r] = zi[r] = 0.f;
+        if (i < te) {
+            const float4 v = rel[i];
+            xi[r] = v.x;
+            yi[r] = v.y;
+            zi[r] = v.z;
+        }
+    }
+    P2PAcc<float, R> A;
+    if (!once && !first) {  // stage the first round again
+        cur = start;
+        __syncwarp();
+        fill = pf_fill(a, rel, q, S, t, gt, tb, te, eb, nmine, part0, cur, nself, more, lane);
+        __syncwarp();
+    }
+    for (;;) {
+        // this lane's contiguous share of the own-box part and of the rest
+        const int a0 = (slice * nself) >> lg, a1 = ((slice + 1) * nself) >> lg;
+        const int nr = fill - nself;
+        const int b0 = nself + ((slice * nr) >> lg), b1 = nself + (((slice + 1) * nr) >> lg);
+        pf_pairs<true, R>(S, a0, a1, xi, yi, zi, A);
+        pf_pairs<false, R>(S, b0, b1, xi, yi, zi, A);
+        if (once || !more) break;
+        __syncwarp();
+        fill = pf_fill(a, rel, q, S, t, gt, tb, te, eb, nmine, part0, cur, nself, more, lane);
+        __syncwarp();
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        // the slices of one target slot meet (every lane takes part in the shuffles)
+        float v0 = A.P[r].s - A.P[r].c, v1 = A.Ex[r].s - A.Ex[r].c;
+        float v2 = A.Ey[r].s - A.Ey[r].c, v3 = A.Ez[r].s - A.Ez[r].c;
+        for (int off = G; off < 32; off <<= 1) {
+            v0 += __shfl_xor_sync(0xffffffffu, v0, off);
+            v1 += __shfl_xor_sync(0xffffffffu, v1, off);
+            v2 += __shfl_xor_sync(0xffffffffu, v2, off);
+            v3 += __shfl_xor_sync(0xffffffffu, v3, off);
+        }
+        const int i = base + ti + G * r;
+        if (slice == 0 && i < te) {
+            if (a.split > 1) {
+                atomicAdd(a.phi + i, (double)v0);
+                atomicAdd(a.fld + 3 * (size_t)i + 0, (double)v1);
+                atomicAdd(a.fld + 3 * (size_t)i + 1, (double)v2);
+                atomicAdd(a.fld + 3 * (size_t)i + 2, (double)v3);
+            } else {
+                a.phi[i] = (double)v0;
+                a.fld[3 * (size_t)i + 0] = (double)v1;
+                a.fld[3 * (size_t)i + 1] = (double)v2;
+                a.fld[3 * (size_t)i + 2] = (double)v3;
+            }
+        }
+    }
+}
+
+// Lanes as G = 32 / 2^lg target slots times 2^lg source slices, each lane
+// holding R <= PF_R targets: per staged source a lane spends one shared load
+// and R pair evaluations, so the choice minimises (1 load + R pairs) / 2^lg
+// over the layouts that cover the leaf's nt targets in one pass (about 3 and
+// 15 issue slots; leaves of more than 32 PF_R charges take passes of 32 PF_R).
+#define PF_R 3
+__device__ __forceinline__ void pf_layout(int nt, int& lg, int& R)
+{
+    lg = 0;
+    R = PF_R;
+    if (nt > 32 * PF_R) return;
+    int best = 1 << 30;
+    for (int l = 0; l <= 5; ++l) {
+        const int g = 32 >> l, r = (nt + g - 1) / g;
+        if (r > PF_R) continue;
+        const int cost = (3 + 15 * r) << (5 - l);
+        if (cost < best) {
+            best = cost;
+            lg = l;
+            R = r;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(32 * PF_WARPS, 4) k_p2p_free_staged(P2PArgs a, const float4* __restrict__ rel,
                                                                     int nleaf)
 {
     __shared__ float4 sp[PF_WARPS][PF_CAP];
@@ -569,10 +666,9 @@ __global__ void __launch_bounds__(32 * PF_WARPS, 6) k_p2p_free_staged(P2PArgs a,
     const int tb = a.pbeg[t], te = a.pend[t];
     const int eb = a.nbeg[t], ee = a.nend[t];
     const int nmine = (ee - eb > part0) ? (ee - eb - part0 + a.split - 1) / a.split : 0;
-    const int nt = te - tb;
-    const int lg = nt <= 8 ? 2 : (nt <= 16 ? 1 : 0);  // log2 of the lanes per target (warp-uniform)
-    const int T = 32 >> lg;                          // targets per pass
-    const int ti = lane & (T - 1), slice = lane >> (5 - lg);
+    int lg, R;  // warp-uniform
+    pf_layout(te - tb, lg, R);
+    const int per = (32 >> lg) * R;  // targets per pass
     const PfCursor start{part0 == 0 ? -1 : 0, 0};
     // the first round stages everything when the list fits: later passes reuse it
     PfCursor cur = start;
@@ -581,54 +677,21 @@ __global__ void __launch_bounds__(32 * PF_WARPS, 6) k_p2p_free_staged(P2PArgs a,
     int fill = pf_fill(a, rel, q, S, t, gt, tb, te, eb, nmine, part0, cur, nself, more, lane);
     const bool once = !more;
     __syncwarp();
-    for (int base = tb; base < te; base += T) {
-        const int i = base + ti;
-        const bool valid = i < te;
-        float xi = 0.f, yi = 0.f, zi = 0.f;
-        if (valid) {
-            const float4 r = rel[i];
-            xi = r.x;
-            yi = r.y;
-            zi = r.z;
-        }
-        P2PAcc<float, 1> A;
-        if (!once && base != tb) {  // stage the first round again
-            cur = start;
-            __syncwarp();
-            fill = pf_fill(a, rel, q, S, t, gt, tb, te, eb, nmine, part0, cur, nself, more, lane);
-            __syncwarp();
-        }
-        for (;;) {
-            if (valid) {
-                // this lane's contiguous share of the own-box part and of the rest
-                const int a0 = (slice * nself) >> lg, a1 = ((slice + 1) * nself) >> lg;
-                const int nr = fill - nself;
-                const int b0 = nself + ((slice * nr) >> lg), b1 = nself + (((slice + 1) * nr) >> lg);
-                pf_pairs<true>(S, a0, a1, xi, yi, zi, A);
-                pf_pairs<false>(S, b0, b1, xi, yi, zi, A);
-            }
-            if (once || !more) break;
-            __syncwarp();
-            fill = pf_fill(a, rel, q, S, t, gt, tb, te, eb, nmine, part0, cur, nself, more, lane);
-            __syncwarp();
-        }
-        if (lg > 0) {
-            // the lanes of one target meet (every lane takes part in the shuffles)
-            float v0 = A.P[0].s - A.P[0].c, v1 = A.Ex[0].s - A.Ex[0].c;
-            float v2 = A.Ey[0].s - A.Ey[0].c, v3 = A.Ez[0].s - A.Ez[0].c;
-            for (int off = T; off < 32; off <<= 1) {
-                v0 += __shfl_xor_sync(0xffffffffu, v0, off);
-                v1 += __shfl_xor_sync(0xffffffffu, v1, off);
-                v2 += __shfl_xor_sync(0xffffffffu, v2, off);
-                v3 += __shfl_xor_sync(0xffffffffu, v3, off);
-            }
-            A.P[0].s = v0;
-            A.Ex[0].s = v1;
-            A.Ey[0].s = v2;
-            A.Ez[0].s = v3;
-            A.P[0].c = A.Ex[0].c = A.Ey[0].c = A.Ez[0].c = 0.f;
-        }
-        if (valid && slice == 0) p2p_store<float, 1>(a, i, A);
+    for (int base = tb; base < te; base += per) {
+        const bool first = base == tb;
+#define PF_PASS(RR) \
+    pf_pass<RR>(a, rel, q, S, t, gt, tb, te, eb, nmine, part0, base, lg, lane, once, first, start, cur, fill, nself, more)
+        if (R == 1) PF_PASS(1);
+#if PF_R >= 2
+        else if (R == 2) PF_PASS(2);
+#endif
+#if PF_R >= 3
+        else if (R == 3) PF_PASS(3);
+#endif
+#if PF_R >= 4
+        else PF_PASS(4);
+#endif
+#undef PF_PASS
     }
 }
 

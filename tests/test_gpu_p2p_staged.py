@@ -13,9 +13,9 @@ from paper_1908_10863_gb300.lfmm import OPT_P2P_SPLIT, OPT_P2P_STAGED
 pytestmark = pytest.mark.gpu
 
 
-def _both(w, p=8, split=0):
+def _both(w, p=8, split=0, leaf_cap=40):
     out = []
-    with LayeredFMM(w.d, w.eps, p, precision=1) as f:
+    with LayeredFMM(w.d, w.eps, p, precision=1, leaf_cap=leaf_cap) as f:
         if split:
             f.set_option(OPT_P2P_SPLIT, split)
         f.build(w.xyz, w.layer)
@@ -52,6 +52,21 @@ def test_staged_matches_per_box_staging(case):
     e, eE = oracle.err2(p0, p1), oracle.err2(E0, E1)
     print("%s: staged vs per-box Err2 phi %.2e field %.2e (leaves %d, mean %.1f per leaf)"
           % (case, e, eE, st["leaves"], w.n / st["leaves"]))
+    assert e < 3e-7 and eE < 3e-7
+
+
+@pytest.mark.parametrize("cap", [6, 16, 64, 160])
+def test_staged_leaf_sizes(cap):
+    # the lanes of a warp are laid out per leaf as target slots x source
+    # slices with up to four targets per lane; leaf capacities from 6 to 160
+    # give leaves of a few charges (many slices) up to more than 128 (several
+    # passes over the targets)
+    w = workloads.config2(1 << 18)
+    ((p0, E0), (p1, E1)), st = _both(w, leaf_cap=cap)
+    assert st["p2p_reaction"] == 0
+    e, eE = oracle.err2(p0, p1), oracle.err2(E0, E1)
+    print("leaf cap %d (mean %.1f per leaf): staged vs per-box Err2 phi %.2e field %.2e"
+          % (cap, w.n / st["leaves"], e, eE))
     assert e < 3e-7 and eE < 3e-7
 
 
