@@ -145,6 +145,8 @@ struct lfmm_ctx {
     DevBuf m2r_keys, m2r_order, m2r_tgt, m2r_kstart, m2r_kval, m2r_tables, m2r_levelh, m2r_batches;
     DevBuf m2r_tdesc, m2r_ktab;  // table descriptors (component, level, rho^2, oz); table of each key
     std::vector<int4> m2r_tdesc_h, m2r_batches_h;  // host staging of asynchronous uploads
+    std::vector<int> m2r_slot_h;                   // reaction table lookup: slot per (rho^2, oz)
+    std::vector<uint32_t> m2r_stamp_h;             // and the generation that filled it
     std::vector<int> m2r_ktab_h;
     double m2r_levelh_h[16] = {0};
     int m2r_nkeys = 0, m2r_nbatch = 0, m2r_keyed_from = 0, m2r_ntab = 0;

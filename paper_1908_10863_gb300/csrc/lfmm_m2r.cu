@@ -16,7 +16,6 @@
 #include <math.h>
 
 #include <algorithm>
-#include <map>
 #include <vector>
 
 #include "lfmm_ctx.h"
@@ -225,18 +224,31 @@ LfErr lf_prepare_m2r(lfmm_ctx* ctx, cudaStream_t st)
     tdesc.clear();
     ktab.assign(nk, 0);
     {
-        std::map<uint64_t, int> seen;
+        // keys arrive sorted by (component, level, offset): within one
+        // (component, level) run a table is identified by (rho^2, oz), looked
+        // up in a direct-indexed slot array (a generation stamp instead of
+        // clearing it per run); tables are numbered in order of first use
+        constexpr int NR2 = 2 * R_OR * R_OR + 1;
+        std::vector<int>& slot = ctx->m2r_slot_h;
+        std::vector<uint32_t>& stamp = ctx->m2r_stamp_h;
+        slot.assign((size_t)NR2 * R_OW, 0);
+        stamp.assign((size_t)NR2 * R_OW, 0u);
+        uint32_t gen = 0, run = ~0u;
         for (int64_t k = 0; k < nk; ++k) {
             int c, l, ox, oy, oz;
             rkey_decode(kv[k], c, l, ox, oy, oz);
+            if ((kv[k] >> 12) != run) {
+                run = kv[k] >> 12;
+                ++gen;
+            }
             const int r2 = ox * ox + oy * oy;
-            const uint64_t tk = ((uint64_t)c << 40) | ((uint64_t)l << 32) | ((uint64_t)r2 << 8) | (uint64_t)(oz + 128);
-            auto it = seen.find(tk);
-            if (it == seen.end()) {
-                it = seen.emplace(tk, (int)tdesc.size()).first;
+            const size_t i = (size_t)r2 * R_OW + (oz + R_OR);
+            if (stamp[i] != gen) {
+                stamp[i] = gen;
+                slot[i] = (int)tdesc.size();
                 tdesc.push_back(make_int4(c, l, r2, oz));
             }
-            ktab[k] = it->second;
+            ktab[k] = slot[i];
         }
     }
     const int ntab = (int)tdesc.size();
