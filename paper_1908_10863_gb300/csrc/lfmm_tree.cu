@@ -334,85 +334,178 @@ __global__ void k_gather_sorted(const double* __restrict__ xyz, const uint32_t* 
 // ---------------------------------------------------------------------------
 // Boxes.
 // ---------------------------------------------------------------------------
-__global__ void k_flags_particles(const uint32_t* __restrict__ keys, int64_t n, int shift, int* __restrict__ f)
+
+// All levels' boxes from the sorted particle keys in four launches.  A box of
+// level l is a run of equal key prefixes key >> 3 (fine - l); the particle
+// that starts a box of level l starts one at every finer level too, so one
+// number per particle, lev(i) (the coarsest level at which particle i starts
+// a box; > depth when it starts none), gives every level's run starts.  Box
+// ids: level l holds off[l] .. off[l] + nb[l] - 1 (finest level first), in
+// order of their first particles.
+#define BX_T 256                  // threads per block
+#define BX_E 8                    // consecutive particles per thread
+#define BX_TILE (BX_T * BX_E)
+#define BX_LV 17                  // levels 0 .. 16
+struct BoxLevels {
+    int depth, fine;
+    int off[BX_LV], nb[BX_LV];
+    double h[BX_LV];
+};
+
+__device__ __forceinline__ int box_lev(const uint32_t* __restrict__ keys, int64_t i, int fine, int depth)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    f[i] = (i == 0 || (keys[i] >> shift) != (keys[i - 1] >> shift)) ? 1 : 0;
+    if (i == 0) return 0;
+    const uint32_t x = keys[i] ^ keys[i - 1];
+    if (x == 0u) return depth + 1;
+    const int hb = 31 - __clz((int)x);
+    const int l = max(0, fine - hb / 3);
+    return l > depth ? depth + 1 : l;
 }
 
-__global__ void k_leaf_boxes(const uint32_t* __restrict__ keys, int64_t n, int shift, const int* __restrict__ f,
-                             const int* __restrict__ idx, int off, uint32_t* __restrict__ bkey,
-                             int* __restrict__ pbeg, int* __restrict__ cbeg, int* __restrict__ cend)
+// block-wide exclusive scan of one value per thread (BX_T threads); *total gets the sum
+__device__ __forceinline__ int box_scan(int v, int* s_w, int& total)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || !f[i]) return;
-    int b = off + idx[i];
-    bkey[b] = keys[i] >> shift;
-    pbeg[b] = (int)i;
-    cbeg[b] = -1;
-    cend[b] = -1;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[w] = x;
+    __syncthreads();
+    int base = 0;
+    total = 0;
+#pragma unroll
+    for (int k = 0; k < BX_T / 32; ++k) {
+        const int t = s_w[k];
+        if (k < w) base += t;
+        total += t;
+    }
+    __syncthreads();
+    return base + x - v;
 }
 
-__global__ void k_flags_boxes(const uint32_t* __restrict__ bkey, int off, int nb, int* __restrict__ f)
+// per tile of BX_TILE particles, the number of boxes of each level starting in it
+__global__ void __launch_bounds__(BX_T) k_box_tile_counts(const uint32_t* __restrict__ keys, int64_t n, int fine,
+                                                          int depth, int* __restrict__ tcnt)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nb) return;
-    f[i] = (i == 0 || (bkey[off + i] >> 3) != (bkey[off + i - 1] >> 3)) ? 1 : 0;
+    __shared__ int s_c[BX_LV];
+    if (threadIdx.x < BX_LV) s_c[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t i0 = (int64_t)blockIdx.x * BX_TILE + (int64_t)threadIdx.x * BX_E;
+    int lev[BX_E];
+#pragma unroll
+    for (int e = 0; e < BX_E; ++e) lev[e] = (i0 + e < n) ? box_lev(keys, i0 + e, fine, depth) : depth + 1;
+    for (int l = 0; l <= depth; ++l) {
+        int c = 0;
+#pragma unroll
+        for (int e = 0; e < BX_E; ++e) c += lev[e] <= l;
+        c = __reduce_add_sync(0xffffffffu, c);
+        if ((threadIdx.x & 31) == 0 && c) atomicAdd(&s_c[l], c);
+    }
+    __syncthreads();
+    if (threadIdx.x <= depth) tcnt[(size_t)blockIdx.x * BX_LV + threadIdx.x] = s_c[threadIdx.x];
 }
 
-__global__ void k_parent_boxes(const int* __restrict__ f, const int* __restrict__ idx, int coff, int nb, int poff,
-                               uint32_t* __restrict__ bkey, int* __restrict__ pbeg, int* __restrict__ parent,
-                               int* __restrict__ cbeg)
+// exclusive scan over the tiles, per level (one block)
+__global__ void __launch_bounds__(BX_T) k_box_tile_scan(int* __restrict__ tcnt, int ntile, int depth)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nb) return;
-    int c = coff + i;
-    // idx is the exclusive scan of the first-child flags: the parent of a
-    // non-first child is the last flagged run before it
-    int p = poff + idx[i] + f[i] - 1;
-    parent[c] = p;
-    if (f[i]) {
-        bkey[p] = bkey[c] >> 3;
-        pbeg[p] = pbeg[c];
-        cbeg[p] = c;
+    __shared__ int s_w[BX_T / 32];
+    for (int l = 0; l <= depth; ++l) {
+        int carry = 0;
+        for (int t0 = 0; t0 < ntile; t0 += BX_T) {
+            const int t = t0 + (int)threadIdx.x;
+            const int v = (t < ntile) ? tcnt[(size_t)t * BX_LV + l] : 0;
+            int total;
+            const int ex = box_scan(v, s_w, total);
+            if (t < ntile) tcnt[(size_t)t * BX_LV + l] = carry + ex;
+            carry += total;
+        }
     }
 }
 
-__global__ void k_level_ends(int off, int nb, int64_t n, int child_end, const int* __restrict__ pbeg,
-                             int* __restrict__ pend, const int* __restrict__ cbeg, int* __restrict__ cend,
-                             int is_leaf)
+// every box's key, first particle, parent and first child
+__global__ void __launch_bounds__(BX_T) k_box_write(const uint32_t* __restrict__ keys, int64_t n, BoxLevels L,
+                                                    const int* __restrict__ toff, uint32_t* __restrict__ bkey,
+                                                    int* __restrict__ pbeg, int* __restrict__ parent,
+                                                    int* __restrict__ cbeg)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nb) return;
-    int b = off + i;
-    pend[b] = (i + 1 < nb) ? pbeg[b + 1] : (int)n;
-    if (!is_leaf) cend[b] = (i + 1 < nb) ? cbeg[b + 1] : child_end;
+    __shared__ int s_w[BX_T / 32];
+    const int depth = L.depth, fine = L.fine;
+    const int64_t i0 = (int64_t)blockIdx.x * BX_TILE + (int64_t)threadIdx.x * BX_E;
+    int lev[BX_E];
+    int mn = depth + 1;
+#pragma unroll
+    for (int e = 0; e < BX_E; ++e) {
+        lev[e] = (i0 + e < n) ? box_lev(keys, i0 + e, fine, depth) : depth + 1;
+        mn = min(mn, lev[e]);
+    }
+    // base[l]: boxes of level l that start before this thread's particles
+    int base[BX_LV];
+    for (int l = 0; l <= depth; ++l) {
+        int c = 0;
+#pragma unroll
+        for (int e = 0; e < BX_E; ++e) c += lev[e] <= l;
+        int total;
+        base[l] = toff[(size_t)blockIdx.x * BX_LV + l] + box_scan(c, s_w, total);
+    }
+    if (mn > depth) return;  // no box starts here (after the block-wide scans)
+#pragma unroll
+    for (int e = 0; e < BX_E; ++e) {
+        const int le = lev[e];
+        if (le > depth) continue;
+        // inc[l] = boxes of level l starting at or before particle i0 + e: the
+        // counts of levels >= le include this particle
+        const uint32_t key = keys[i0 + e];
+        for (int l = le; l <= depth; ++l) {
+            int inc_l = base[l];
+            for (int f = 0; f <= e; ++f) inc_l += lev[f] <= l;
+            const int b = L.off[l] + inc_l - 1;
+            bkey[b] = key >> (3 * (fine - l));
+            pbeg[b] = (int)(i0 + e);
+            if (l > 0) {
+                int inc_p = base[l - 1];
+                for (int f = 0; f <= e; ++f) inc_p += lev[f] <= l - 1;
+                parent[b] = L.off[l - 1] + inc_p - 1;
+            }
+            if (l < depth) {  // the first child starts at the same particle
+                int inc_c = base[l + 1];
+                for (int f = 0; f <= e; ++f) inc_c += lev[f] <= l + 1;
+                cbeg[b] = L.off[l + 1] + inc_c - 1;
+            }
+        }
+    }
 }
 
-// Every level in one launch: box b belongs to level l when off[l] <= b <
-// off[l] + nb[l] (finest level first in the box ids).
-struct CenterLevels {
-    int depth;
-    int off[17];
-    double h[17];
-};
-
-__global__ void k_centers(const uint32_t* __restrict__ bkey, int nbox, CenterLevels lv, double ox, double oy,
-                          double oz, LfD4* __restrict__ cen, int4* __restrict__ grid)
+// per box: particle and child ranges' ends, the roots' parents, leaves'
+// child ranges, centres and grid cells
+__global__ void k_box_finish(int nbox, int64_t n, BoxLevels L, double ox, double oy, double oz,
+                             const uint32_t* __restrict__ bkey, const int* __restrict__ pbeg, int* __restrict__ pend,
+                             int* __restrict__ cbeg, int* __restrict__ cend, int* __restrict__ parent,
+                             LfD4* __restrict__ cen, int4* __restrict__ grid)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nbox) return;
-    int level = lv.depth;
-    while (level > 0 && b >= lv.off[level - 1]) --level;
-    const double h = lv.h[level];
-    const int off = lv.off[level], i = b - off;
-    uint32_t k = bkey[off + i];
-    uint32_t layer = k >> (3 * level);
-    uint32_t mort = (level > 0) ? (k & ((1u << (3 * level)) - 1u)) : 0u;
-    uint32_t ix = lf_compact3(mort), iy = lf_compact3(mort >> 1), iz = lf_compact3(mort >> 2);
-    cen[off + i] = LfD4{ox + (ix + 0.5) * h, oy + (iy + 0.5) * h, oz + (iz + 0.5) * h, (double)layer};
-    grid[off + i] = make_int4((int)ix, (int)iy, (int)iz, (int)layer);
+    int level = L.depth;
+    while (level > 0 && b >= L.off[level - 1]) --level;
+    const int i = b - L.off[level];
+    const bool last = i + 1 == L.nb[level];
+    pend[b] = last ? (int)n : pbeg[b + 1];
+    if (level == L.depth) {
+        cbeg[b] = -1;
+        cend[b] = -1;
+    } else {
+        cend[b] = last ? L.off[level + 1] + L.nb[level + 1] : cbeg[b + 1];
+    }
+    if (level == 0) parent[b] = -1;
+    const double h = L.h[level];
+    const uint32_t k = bkey[b];
+    const uint32_t layer = k >> (3 * level);
+    const uint32_t mort = (level > 0) ? (k & ((1u << (3 * level)) - 1u)) : 0u;
+    const uint32_t ix = lf_compact3(mort), iy = lf_compact3(mort >> 1), iz = lf_compact3(mort >> 2);
+    cen[b] = LfD4{ox + (ix + 0.5) * h, oy + (iy + 0.5) * h, oz + (iz + 0.5) * h, (double)layer};
+    grid[b] = make_int4((int)ix, (int)iy, (int)iz, (int)layer);
 }
 
 // ---------------------------------------------------------------------------
@@ -639,6 +732,9 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
     // ---- bounds ----
     const int nbb = 256;
     LF_TRY(lf_reserve(ctx->counts, 65536));  // [0,16K) bounds partials, 16K level counts, 20K stats
+    // the bounded-wait counter reads zero until an evaluation's waits run out
+    // (the buffer may reuse memory that held anything)
+    LF_CHECK(cudaMemsetAsync(ctx->counts.as<char>() + LFMM_TIMEOUT_OFF, 0, sizeof(int), st));
     double* part = ctx->counts.as<double>();
     ++ctx->launches, k_bounds<<<nbb, 256, 0, st>>>(xyz, n, part);
     LF_TRY(lf_cuda(cudaGetLastError(), "bounds"));
@@ -831,56 +927,30 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
     LF_TRY(lf_reserve(ctx->box_cend, nb * 4));
     LF_TRY(lf_reserve(ctx->box_center, nb * sizeof(LfD4)));
     LF_TRY(lf_reserve(ctx->box_grid, nb * sizeof(int4)));
-    LF_TRY(lf_reserve(ctx->flags, (size_t)n * 4));
-    LF_TRY(lf_reserve(ctx->scan_tmp, 64));
-    DevBuf& idxb = ctx->keys_tmp;  // reuse as scan output
-    LF_TRY(lf_reserve(idxb, (size_t)n * 4));
     uint32_t* bkey = ctx->box_key.as<uint32_t>();
     int *pbeg = ctx->box_pbeg.as<int>(), *pend = ctx->box_pend.as<int>(), *par = ctx->box_parent.as<int>();
     int *cbeg = ctx->box_cbeg.as<int>(), *cend = ctx->box_cend.as<int>();
-    int* fl = ctx->flags.as<int>();
-    int* ix = idxb.as<int>();
-
-    // leaf level
     {
-        const LfmmLevel& lv = ctx->levels[depth];
-        int sh = 3 * (fine - depth);
-        ++ctx->launches, k_flags_particles<<<lf_blocks(n, 256), 256, 0, st>>>(keys, n, sh, fl);
-        // the box counts per level are known (k_level_counts): no read-back
-        LF_TRY(lf_scan_i32(ctx, fl, ix, n, nullptr, st));
-        ++ctx->launches, k_leaf_boxes<<<lf_blocks(n, 256), 256, 0, st>>>(keys, n, sh, fl, ix, lv.off, bkey, pbeg, cbeg, cend);
-        ++ctx->launches, k_level_ends<<<lf_blocks(lv.nbox, 256), 256, 0, st>>>(lv.off, lv.nbox, n, 0, pbeg, pend, cbeg, cend, 1);
-        LF_TRY(lf_cuda(cudaGetLastError(), "leaf boxes"));
-    }
-    for (int l = depth - 1; l >= 0; --l) {
-        const LfmmLevel& ch = ctx->levels[l + 1];
-        const LfmmLevel& lv = ctx->levels[l];
-        ++ctx->launches, k_flags_boxes<<<lf_blocks(ch.nbox, 256), 256, 0, st>>>(bkey, ch.off, ch.nbox, fl);
-        LF_TRY(lf_scan_i32(ctx, fl, ix, ch.nbox, nullptr, st));
-        ++ctx->launches, k_parent_boxes<<<lf_blocks(ch.nbox, 256), 256, 0, st>>>(fl, ix, ch.off, ch.nbox, lv.off, bkey, pbeg, par,
-                                                                   cbeg);
-        ++ctx->launches, k_level_ends<<<lf_blocks(lv.nbox, 256), 256, 0, st>>>(lv.off, lv.nbox, n, ch.off + ch.nbox, pbeg, pend, cbeg,
-                                                                cend, 0);
-        LF_TRY(lf_cuda(cudaGetLastError(), "parent boxes"));
-    }
-    {
-        // roots have no parent
-        const LfmmLevel& r = ctx->levels[0];
-        std::vector<int> mone(r.nbox, -1);
-        LF_CHECK(cudaMemcpyAsync(par + r.off, mone.data(), sizeof(int) * r.nbox, cudaMemcpyHostToDevice, st));
-    }
-    {
-        CenterLevels cl;
-        cl.depth = depth;
-        for (int l = 0; l <= depth; ++l) {
-            cl.off[l] = ctx->levels[l].off;
-            cl.h[l] = ctx->levels[l].h;
+        if (depth >= BX_LV) return "internal: tree deeper than 16 levels";
+        BoxLevels bl;
+        bl.depth = depth;
+        bl.fine = fine;
+        for (int l = 0; l < BX_LV; ++l) {
+            bl.off[l] = (l <= depth) ? ctx->levels[l].off : 0;
+            bl.nb[l] = (l <= depth) ? ctx->levels[l].nbox : 0;
+            bl.h[l] = (l <= depth) ? ctx->levels[l].h : 0.0;
         }
-        ++ctx->launches, k_centers<<<lf_blocks(tot, 256), 256, 0, st>>>(bkey, tot, cl, ctx->origin[0], ctx->origin[1],
-                                                                        ctx->origin[2], ctx->box_center.as<LfD4>(),
-                                                                        ctx->box_grid.as<int4>());
+        const int ntile = (int)((n + BX_TILE - 1) / BX_TILE);
+        LF_TRY(lf_reserve(ctx->flags, (size_t)ntile * BX_LV * sizeof(int) + 64));
+        int* tcnt = ctx->flags.as<int>();
+        ++ctx->launches, k_box_tile_counts<<<ntile, BX_T, 0, st>>>(keys, n, fine, depth, tcnt);
+        ++ctx->launches, k_box_tile_scan<<<1, BX_T, 0, st>>>(tcnt, ntile, depth);
+        ++ctx->launches, k_box_write<<<ntile, BX_T, 0, st>>>(keys, n, bl, tcnt, bkey, pbeg, par, cbeg);
+        ++ctx->launches, k_box_finish<<<lf_blocks(tot, 256), 256, 0, st>>>(
+            tot, n, bl, ctx->origin[0], ctx->origin[1], ctx->origin[2], bkey, pbeg, pend, cbeg, cend, par,
+            ctx->box_center.as<LfD4>(), ctx->box_grid.as<int4>());
     }
-    LF_TRY(lf_cuda(cudaGetLastError(), "centers"));
+    LF_TRY(lf_cuda(cudaGetLastError(), "boxes"));
     {
         // per (component, level) constants of the admissibility test
         // host staging owned by the context: the copy needs no synchronisation
