@@ -716,7 +716,7 @@ lfmm_status lfmm_create(const double* d, int L, const double* eps, int p, lfmm_c
     if (e.empty()) e = lf_setup_m2l_ops(ctx);
     // the setup tables travel by pageable copies on the legacy stream, which
     // the context's non-blocking streams do not wait for
-    if (e.empty()) e = lf_cuda(cudaMallocHost(&ctx->host_pin, 4096), "pinned host buffer");
+    if (e.empty()) e = lf_cuda(cudaMallocHost(&ctx->host_pin, LFMM_PIN_BYTES), "pinned host buffer");
     if (e.empty()) e = lf_cuda(cudaDeviceSynchronize(), "setup copies");
     if (!e.empty()) {
         lfmm_status s = status_of(e);
@@ -1010,6 +1010,13 @@ void lfmm_destroy(lfmm_ctx* ctx)
 lfmm_status lfmm_get_stats(const lfmm_ctx* ctx, int64_t* out, int nout)
 {
     if (!ctx || !out || nout < 1) return LFMM_EINVAL;
+    if (ctx->p2p_stats_stale && nout > LFMM_STAT_P2P_FREE) {
+        // the pair counts are a statistic, computed from the near lists on request
+        lfmm_ctx* mc = const_cast<lfmm_ctx*>(ctx);
+        cudaStreamSynchronize(ctx->s_near);
+        const LfErr e = lf_p2p_pair_stats(mc);
+        if (!e.empty()) return fail(mc, e);
+    }
     for (int i = 0; i < nout && i < LFMM_STAT_COUNT; ++i) out[i] = ctx->stats[i];
     if (nout > LFMM_STAT_LAUNCHES) out[LFMM_STAT_LAUNCHES] = ctx->launches;
     if (nout > LFMM_STAT_TIMEOUTS && ctx->counts.ptr) {

@@ -263,7 +263,7 @@ static lfmm_status apply_setting(lfmm_batch* b, const BatchSetting& s)
         lfmm_ctx* c = b->ctx[i];
         lfmm_status st = lfmm_set_option(c, LFMM_OPT_TENSOR_CORES, c->n >= s.tc_min ? 1.0 : 0.0);
         if (st == LFMM_OK) st = lfmm_set_option(c, LFMM_OPT_P2P_SPLIT, (double)s.split);
-        const bool tab = s.tables && c->stats[LFMM_STAT_P2P_REACTION] > 0;
+        const bool tab = s.tables && c->near_reaction_entries > 0;
         if (st == LFMM_OK) st = lfmm_set_option(c, LFMM_OPT_NEAR_TABLES, tab ? 1.0 : 0.0);
         if (st != LFMM_OK) return bfail(b, "problem " + std::to_string(i) + ": " + c->err, st);
     }

@@ -145,7 +145,11 @@ struct lfmm_ctx {
     DevBuf m2r_keys, m2r_order, m2r_tgt, m2r_kstart, m2r_kval, m2r_tables, m2r_levelh, m2r_batches;
     DevBuf m2r_tdesc, m2r_ktab;  // table descriptors (component, level, rho^2, oz); table of each key
     std::vector<int4> m2r_tdesc_h, m2r_batches_h;  // host staging of asynchronous uploads
+    int64_t near_reaction_entries = 0;  // leaf-level near entries of reaction components (last build)
+    int p2p_stats_stale = 0;            // the particle-pair statistics wait for lf_p2p_pair_stats
     std::vector<int> m2r_slot_h;                   // reaction table lookup: slot per (rho^2, oz)
+    std::vector<int> m2r_kstart_h;                 // key starts and values read back (when the
+    std::vector<uint32_t> m2r_kval_h;              // pinned buffer is too small for them)
     std::vector<uint32_t> m2r_stamp_h;             // and the generation that filled it
     std::vector<int> m2r_ktab_h;
     double m2r_levelh_h[16] = {0};
@@ -185,6 +189,23 @@ struct lfmm_ctx {
 // ---- allocation helpers (lfmm_api.cu) ----
 LfErr lf_reserve(DevBuf& b, size_t bytes);
 LfErr lf_cuda(cudaError_t e, const char* what);
+// The context's pinned host buffer, in regions for the build's read-backs:
+// copies into pinned memory are queued without waiting, so each build phase
+// synchronises once for all of its read-backs.
+#define LFMM_PIN_BYTES (256 * 1024)
+#define LFMM_PIN_ERR 0          // input check flags (4 ints)
+#define LFMM_PIN_LEVELS 256     // boxes per level (16 ints)
+#define LFMM_PIN_SCAN 512       // a scan's last input and output (2 ints)
+#define LFMM_PIN_LIST 1024      // list statistics, overflow, counters, per-level snapshots (< 1 KB)
+#define LFMM_PIN_M2L 2048       // free M2L class counts (144 ints)
+#define LFMM_PIN_ROOT 2688      // root box keys (up to 128)
+#define LFMM_PIN_BOUNDS 4096    // bounding-box partials (256 blocks x 6 doubles)
+#define LFMM_PIN_M2R 16384      // reaction M2L key starts and values (the rest)
+template <typename T>
+inline T* lf_pin(const lfmm_ctx* ctx, size_t off)
+{
+    return reinterpret_cast<T*>(static_cast<char*>(ctx->host_pin) + off);
+}
 // device-to-host copy ordered after the work queued on st, complete on return
 inline cudaError_t lf_d2h(void* dst, const void* src, size_t bytes, cudaStream_t st)
 {
@@ -194,6 +215,7 @@ inline cudaError_t lf_d2h(void* dst, const void* src, size_t bytes, cudaStream_t
 
 // ---- tree construction (lfmm_tree.cu) ----
 LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz_dev, const int32_t* layer_dev, int64_t n, cudaStream_t st);
+LfErr lf_p2p_pair_stats(lfmm_ctx* ctx);
 
 // ---- free-space M2L GEMM (lfmm_m2l.cu) ----
 LfErr lf_setup_m2l_ops(lfmm_ctx* ctx);

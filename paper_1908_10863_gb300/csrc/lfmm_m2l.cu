@@ -348,8 +348,10 @@ LfErr lf_prepare_m2l(lfmm_ctx* ctx, cudaStream_t st)
         LF_TRY(lf_radix_sort(ctx, ctx->m2l_keys.as<uint32_t>(), ctx->m2l_sorted.as<uint32_t>(), nsort, st, 3, 1));
     else
         LF_TRY(lf_radix_sort(ctx, ctx->m2l_keys.as<uint32_t>(), ctx->m2l_sorted.as<uint32_t>(), nsort, st));
-    int hcnt[16 + 16 * 8];
-    LF_CHECK(cudaMemcpyAsync(hcnt, err, sizeof(hcnt), cudaMemcpyDeviceToHost, st));
+    static_assert(LFMM_PIN_M2L + (16 + 16 * 8) * sizeof(int) <= LFMM_PIN_ROOT, "pinned regions");
+    const int* hcnt = lf_pin<int>(ctx, LFMM_PIN_M2L);
+    LF_CHECK(cudaMemcpyAsync(lf_pin<int>(ctx, LFMM_PIN_M2L), err, (16 + 16 * 8) * sizeof(int), cudaMemcpyDeviceToHost,
+                             st));
     LF_CHECK(cudaStreamSynchronize(st));
     if (hcnt[0] != 0) return "internal: free M2L entry outside its offset class";
     std::vector<int4>& tiles = ctx->m2l_tiles_h;

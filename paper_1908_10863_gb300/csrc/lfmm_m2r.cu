@@ -209,14 +209,24 @@ LfErr lf_prepare_m2r(lfmm_ctx* ctx, cudaStream_t st)
     ++ctx->launches, k_key_starts<<<lf_blocks(ne, 256), 256, 0, st>>>(keys, ne, fl, ix, ctx->m2r_kstart.as<int>(),
                                                                        ctx->m2r_kval.as<uint32_t>());
     LF_TRY(lf_cuda(cudaGetLastError(), "m2r key starts"));
-    std::vector<int> kstart(nk + 1);
-    std::vector<uint32_t> kv(nk);
-    int hbad = 0;
-    LF_CHECK(cudaMemcpyAsync(kstart.data(), ctx->m2r_kstart.ptr, sizeof(int) * nk, cudaMemcpyDeviceToHost, st));
-    LF_CHECK(cudaMemcpyAsync(kv.data(), ctx->m2r_kval.ptr, sizeof(uint32_t) * nk, cudaMemcpyDeviceToHost, st));
-    LF_CHECK(cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, st));
+    // key starts, key values and the error flag come back into the pinned
+    // buffer when they fit (one synchronisation), else into host vectors
+    const size_t pin_need = sizeof(int) * (2 * (size_t)nk + 2);
+    const bool pinned = LFMM_PIN_M2R + pin_need <= LFMM_PIN_BYTES;
+    std::vector<int>& kst_h = ctx->m2r_kstart_h;
+    std::vector<uint32_t>& kv_h = ctx->m2r_kval_h;
+    if (!pinned) {
+        kst_h.resize(nk + 1);
+        kv_h.resize(nk);
+    }
+    int* kstart = pinned ? lf_pin<int>(ctx, LFMM_PIN_M2R) : kst_h.data();
+    uint32_t* kv = pinned ? lf_pin<uint32_t>(ctx, LFMM_PIN_M2R + sizeof(int) * (nk + 1)) : kv_h.data();
+    int* hbad = pinned ? lf_pin<int>(ctx, LFMM_PIN_M2R + sizeof(int) * (2 * (size_t)nk + 1)) : lf_pin<int>(ctx, LFMM_PIN_SCAN);
+    LF_CHECK(cudaMemcpyAsync(kstart, ctx->m2r_kstart.ptr, sizeof(int) * nk, cudaMemcpyDeviceToHost, st));
+    LF_CHECK(cudaMemcpyAsync(kv, ctx->m2r_kval.ptr, sizeof(uint32_t) * nk, cudaMemcpyDeviceToHost, st));
+    LF_CHECK(cudaMemcpyAsync(hbad, bad, 4, cudaMemcpyDeviceToHost, st));
     LF_CHECK(cudaStreamSynchronize(st));
-    if (hbad) return "internal: reaction M2L pair with a non-integer or too distant offset on an aligned level";
+    if (*hbad) return "internal: reaction M2L pair with a non-integer or too distant offset on an aligned level";
     kstart[nk] = ne;
     // tables, one per distinct (component, level, rho^2, oz)
     std::vector<int4>& tdesc = ctx->m2r_tdesc_h;

@@ -933,14 +933,14 @@ LfErr lf_near_field(lfmm_ctx* ctx, cudaStream_t st)
     // per right-hand side.  The quadrature kernels take batches of up to 4
     // (float32: more registers per thread cost more than the shared pair
     // geometry saves) or 8 (FP64).
-    const bool net = a.sv.ready != 0 && ctx->stats[LFMM_STAT_P2P_REACTION] > 0;
+    const bool net = a.sv.ready != 0 && ctx->near_reaction_entries > 0;
     // Few leaves (small problems) leave most SMs idle with one warp or block
     // per leaf: share each near list between `split` of them.  A set value
     // (ctx->p2p_split, e.g. from the tuner) wins over this occupancy rule.
     // media of four or five layers need the solved densities only for reaction pairs
     // of the near lists (counted at every build); without any, the kernels of
     // thinner media compute the free-space pairs alone and are exact
-    const bool general = ctx->L >= 3 && ctx->stats[LFMM_STAT_P2P_REACTION] > 0;
+    const bool general = ctx->L >= 3 && ctx->near_reaction_entries > 0;
     const bool warp_kernel = !net && !general && ctx->precision;
     int split = ctx->p2p_split;
     if (split <= 0) {
@@ -975,7 +975,7 @@ LfErr lf_near_field(lfmm_ctx* ctx, cudaStream_t st)
         } else if (ctx->precision) {
             const int g = lf_blocks((int64_t)leaf.nbox * split, PW_WARPS), T = 32 * PW_WARPS;
             const float4* rel = ctx->pos_rel.as<float4>();
-            if (a.nr == 1 && a.grid && ctx->stats[LFMM_STAT_P2P_REACTION] == 0 && ctx->p2p_staged)
+            if (a.nr == 1 && a.grid && ctx->near_reaction_entries == 0 && ctx->p2p_staged)
                 ++ctx->launches, k_p2p_free_staged<<<lf_blocks((int64_t)leaf.nbox * split, PF_WARPS), 32 * PF_WARPS, 0,
                                                      st>>>(a, rel, leaf.nbox);
             else if (a.nr == 1)

@@ -120,12 +120,13 @@ LfErr lf_scan_i32(lfmm_ctx* ctx, const int* in, int* out, int64_t n, int64_t* to
         need += m + 1;
     }
     LF_TRY(lf_reserve(ctx->scan_tmp, (size_t)(need + 16) * sizeof(int)));
-    // the last input is copied before the scan is enqueued, so in-place scans work
-    int last[2] = {0, 0};
-    if (total) LF_CHECK(cudaMemcpyAsync(&last[0], in + n - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    // the last input is copied before the scan is enqueued, so in-place scans
+    // work (into pinned memory: neither copy waits, one synchronisation)
+    int* last = lf_pin<int>(ctx, LFMM_PIN_SCAN);
+    if (total) LF_CHECK(cudaMemcpyAsync(last, in + n - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
     LF_TRY(scan_rec(ctx, in, out, n, ctx->scan_tmp.as<int>(), st));
     if (total) {
-        LF_CHECK(cudaMemcpyAsync(&last[1], out + n - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+        LF_CHECK(cudaMemcpyAsync(last + 1, out + n - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
         LF_CHECK(cudaStreamSynchronize(st));
         *total = (int64_t)last[1] + last[0];
     }
@@ -263,7 +264,7 @@ struct KeyParams {
     int fine;  // fine grid level of the keys (lf_fine_level)
     double d[LFMM_MAXL];
     double org[3];
-    double hfine;
+    double hfine, ihfine;  // fine cell size and its reciprocal
     int iz_lo[LFMM_MAXL + 1], iz_hi[LFMM_MAXL + 1];
 };
 
@@ -289,10 +290,14 @@ __global__ void k_make_keys(const double* __restrict__ xyz, const int32_t* __res
         atomicOr(&err[0], 1);
         l = 0;
     }
+    // cells by a product with the reciprocal (the FP64 divide is costly): a
+    // point within rounding of a cell face may take the cell beside it, which
+    // only moves it by that rounding outside its box; across an interface the
+    // per-layer clamp of iz decides
     const int top = (1 << kp.fine) - 1;
-    int ix = (int)floor((x - kp.org[0]) / kp.hfine);
-    int iy = (int)floor((y - kp.org[1]) / kp.hfine);
-    int iz = (int)floor((z - kp.org[2]) / kp.hfine);
+    int ix = (int)floor((x - kp.org[0]) * kp.ihfine);
+    int iy = (int)floor((y - kp.org[1]) * kp.ihfine);
+    int iz = (int)floor((z - kp.org[2]) * kp.ihfine);
     ix = min(max(ix, 0), top);
     iy = min(max(iy, 0), top);
     iz = min(max(iz, kp.iz_lo[l]), kp.iz_hi[l]);
@@ -569,23 +574,75 @@ struct ListOut {
     int *nbeg, *nend, *mbeg, *mend, *rbeg, *rend;
 };
 
+// Candidates of the near entries [e0, e0 + 32) of a parent list (ending at
+// ee), in slots q = lane + 32 m (m < 8): entry e0 + q / 8, child q mod 8 --
+// the order of taking them 4 entries at a time.  Each lane loads one entry and
+// its child range, and then the eight child cells of its slots, so a chunk
+// costs three rounds of dependent loads rather than three per 4 entries.
+// kind: 0 free M2L, 1 reaction M2L, 2 near, -1 no candidate.
+__device__ __forceinline__ void list_chunk(const LfListMedium& med, const ListOut& o, int level, int e0, int ee,
+                                           int4 gt, const int* __restrict__ cbeg, const int* __restrict__ cend,
+                                           const int4* __restrict__ grid, int lane, int kind[8], uint32_t v[8],
+                                           int sc[8], int4 gs[8])
+{
+    const int e = e0 + lane;
+    uint32_t ent = 0;
+    int cb = 0, ce = 0;
+    if (e < ee) {
+        ent = o.near_ent[e];
+        const int s = (int)(ent & LFMM_ENT_MASK);
+        cb = cbeg[s];
+        ce = cend[s];
+    }
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        const int src = 4 * m + (lane >> 3);  // lane holding the slot's entry
+        const uint32_t en = __shfl_sync(0xffffffffu, ent, src);
+        const int b = __shfl_sync(0xffffffffu, cb, src), bend = __shfl_sync(0xffffffffu, ce, src);
+        const int ch = b + (lane & 7);
+        sc[m] = (e0 + src < ee && ch < bend) ? ch : -1;
+        v[m] = (en & ~LFMM_ENT_MASK) | (uint32_t)max(sc[m], 0);
+        if (sc[m] >= 0) gs[m] = grid[sc[m]];
+    }
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        kind[m] = -1;
+        if (sc[m] >= 0) {
+            const int c = (int)(v[m] >> LFMM_ENT_SHIFT);
+            const LfmmComp& cp = med.comps[c];
+            kind[m] = lf_admissible(cp, med.lc[c * 16 + level], med.sep, gt, gs[m]) ? (cp.is_free ? 0 : 1) : 2;
+        }
+    }
+}
+
 // One warp per target box.  The candidates (children of the parent's near
 // entries) are taken 32 at a time as 4 entries x 8 child slots.  A first pass
-// counts the admissible ones per category; lane 0 then takes that many
-// positions in each array; a second pass writes them in candidate order
-// through a ballot prefix, so each box's lists are deterministic (the boxes'
-// segments are placed in whatever order the warps reach the counters).
-// With `slots`, the second pass also records each free M2L source at its
-// position in the target's octant-class offset list (slots[t][189],
-// inv[class][343]: position or -1).
-__global__ void k_list_level(LfListMedium med, int level_off, int nb, int level, const int* __restrict__ parent,
-                             const int* __restrict__ cbeg, const int* __restrict__ cend,
-                             const int4* __restrict__ grid, ListOut o, unsigned long long* __restrict__ stat,
-                             const uint32_t* __restrict__ bkey, const int* __restrict__ inv, int* __restrict__ slots,
-                             int* __restrict__ slot_err)
+// classifies them (every candidate costs dependent loads: entry, child
+// range, child cell) and keeps the accepted ones in candidate order in a
+// shared-memory stash of LST_CAP entries per warp; lane 0 then takes
+// positions in each array for the counted entries, and the second pass
+// copies the stash out through a ballot prefix per category, so each box's
+// lists are deterministic (the boxes' segments are placed in whatever order
+// the warps reach the counters).  A box with more accepted candidates than
+// the stash holds classifies them again in the second pass.  With `slots`,
+// the first pass also records each free M2L source at its position in the
+// target's octant-class offset list (slots[t][189], inv[class][343]:
+// position or -1).
+#define LST_WARPS 4
+#define LST_CAP 1024
+__global__ void __launch_bounds__(32 * LST_WARPS) k_list_level(LfListMedium med, int level_off, int nb, int level,
+                                                               const int* __restrict__ parent,
+                                                               const int* __restrict__ cbeg, const int* __restrict__ cend,
+                                                               const int4* __restrict__ grid, ListOut o,
+                                                               unsigned long long* __restrict__ stat,
+                                                               const uint32_t* __restrict__ bkey,
+                                                               const int* __restrict__ inv, int* __restrict__ slots,
+                                                               int* __restrict__ slot_err, int leaf)
 {
-    const int lane = threadIdx.x & 31;
-    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    __shared__ uint32_t s_v[LST_WARPS][LST_CAP];
+    __shared__ unsigned char s_k[LST_WARPS][LST_CAP];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int i = blockIdx.x * LST_WARPS + w;
     if (i >= nb) return;  // whole warp
     const int t = level_off + i;
     const int pt = parent[t];
@@ -594,62 +651,88 @@ __global__ void k_list_level(LfListMedium med, int level_off, int nb, int level,
     const int cls = slots ? (int)(bkey[t] & 7u) : 0;
     const int eb = o.nbeg[pt], ee = o.nend[pt];
     int wf = 0, wr = 0, wn = 0;
+    int nst = 0;  // accepted candidates (stashed while nst <= LST_CAP)
     for (int pass = 0; pass < 2; ++pass) {
         int nf = 0, nr = 0, nn = 0;  // warp-uniform running counts
-        for (int e0 = eb; e0 < ee; e0 += 4) {
-            const int e = e0 + (lane >> 3), k = lane & 7;
-            int kind = -1;  // 0 free M2L, 1 reaction M2L, 2 near
-            uint32_t v = 0;
-            int sc = -1;
-            if (e < ee) {
-                const uint32_t ent = o.near_ent[e];
-                const int c = (int)(ent >> LFMM_ENT_SHIFT);
-                const int s = (int)(ent & LFMM_ENT_MASK);
-                const int ch = cbeg[s] + k;
-                if (ch < cend[s]) {
-                    sc = ch;
-                    const LfmmComp& cp = med.comps[c];
-                    v = ((uint32_t)c << LFMM_ENT_SHIFT) | (uint32_t)sc;
-                    if (lf_admissible(cp, med.lc[c * 16 + level], med.sep, gt, grid[sc]))
-                        kind = cp.is_free ? 0 : 1;
-                    else
-                        kind = 2;
-                }
-            }
-            const unsigned bf = __ballot_sync(0xffffffffu, kind == 0);
-            const unsigned br = __ballot_sync(0xffffffffu, kind == 1);
-            const unsigned bn = __ballot_sync(0xffffffffu, kind == 2);
-            if (pass == 1) {
-                if (kind == 0) {
+        int nrn = 0;                 // leaf level: near entries of reaction components
+        if (pass == 1 && nst <= LST_CAP) {
+            // copy the stash out, in candidate order within each category
+            for (int j0 = 0; j0 < nst; j0 += 32) {
+                const int j = j0 + lane;
+                const int kind = (j < nst) ? (int)s_k[w][j] : -1;
+                const uint32_t v = (j < nst) ? s_v[w][j] : 0u;
+                const unsigned bf = __ballot_sync(0xffffffffu, kind == 0);
+                const unsigned br = __ballot_sync(0xffffffffu, kind == 1);
+                const unsigned bn = __ballot_sync(0xffffffffu, kind == 2);
+                if (kind == 0)
                     o.m2l_ent[wf + nf + __popc(bf & lt_mask)] = v;
-                    if (slots) {
-                        const int4 gs = grid[sc];
-                        const int ox = gt.x - gs.x, oy = gt.y - gs.y, oz = gt.z - gs.z;
-                        int loc = -1;
-                        if (ox >= -3 && ox <= 3 && oy >= -3 && oy <= 3 && oz >= -3 && oz <= 3)
-                            loc = inv[cls * 343 + (ox + 3) * 49 + (oy + 3) * 7 + (oz + 3)];
-                        if (loc < 0)
-                            atomicAdd(slot_err, 1);
-                        else
-                            slots[(size_t)t * 189 + loc] = sc;
-                    }
-                } else if (kind == 1) {
+                else if (kind == 1)
                     o.m2r_ent[wr + nr + __popc(br & lt_mask)] = v;
-                } else if (kind == 2) {
+                else if (kind == 2)
                     o.near_ent[wn + nn + __popc(bn & lt_mask)] = v;
+                if (leaf) nrn += __popc(__ballot_sync(0xffffffffu, kind == 2 && !med.comps[v >> LFMM_ENT_SHIFT].is_free));
+                nf += __popc(bf);
+                nr += __popc(br);
+                nn += __popc(bn);
+            }
+        } else {
+            for (int e0 = eb; e0 < ee; e0 += 32) {
+                int kinds[8], scs[8];
+                uint32_t vs[8];
+                int4 gss[8];
+                list_chunk(med, o, level, e0, ee, gt, cbeg, cend, grid, lane, kinds, vs, scs, gss);
+#pragma unroll
+                for (int m = 0; m < 8; ++m) {
+                    const int kind = kinds[m];
+                    const uint32_t v = vs[m];
+                    const unsigned bf = __ballot_sync(0xffffffffu, kind == 0);
+                    const unsigned br = __ballot_sync(0xffffffffu, kind == 1);
+                    const unsigned bn = __ballot_sync(0xffffffffu, kind == 2);
+                    if (pass == 0) {
+                        const unsigned ba = bf | br | bn;
+                        const int pos = nst + __popc(ba & lt_mask);
+                        if (kind >= 0 && pos < LST_CAP) {
+                            s_v[w][pos] = v;
+                            s_k[w][pos] = (unsigned char)kind;
+                        }
+                        nst += __popc(ba);
+                        if (kind == 0 && slots) {
+                            const int4 gs = gss[m];
+                            const int ox = gt.x - gs.x, oy = gt.y - gs.y, oz = gt.z - gs.z;
+                            int loc = -1;
+                            if (ox >= -3 && ox <= 3 && oy >= -3 && oy <= 3 && oz >= -3 && oz <= 3)
+                                loc = inv[cls * 343 + (ox + 3) * 49 + (oy + 3) * 7 + (oz + 3)];
+                            if (loc < 0)
+                                atomicAdd(slot_err, 1);
+                            else
+                                slots[(size_t)t * 189 + loc] = scs[m];
+                        }
+                    } else {
+                        if (kind == 0)
+                            o.m2l_ent[wf + nf + __popc(bf & lt_mask)] = v;
+                        else if (kind == 1)
+                            o.m2r_ent[wr + nr + __popc(br & lt_mask)] = v;
+                        else if (kind == 2)
+                            o.near_ent[wn + nn + __popc(bn & lt_mask)] = v;
+                        if (leaf)
+                            nrn += __popc(__ballot_sync(0xffffffffu,
+                                                        kind == 2 && !med.comps[v >> LFMM_ENT_SHIFT].is_free));
+                    }
+                    nf += __popc(bf);
+                    nr += __popc(br);
+                    nn += __popc(bn);
                 }
             }
-            nf += __popc(bf);
-            nr += __popc(br);
-            nn += __popc(bn);
         }
         if (pass == 1) {
             if (lane == 0 && stat) {
                 if (nf) atomicAdd(&stat[0], (unsigned long long)nf);
                 if (nr) atomicAdd(&stat[1], (unsigned long long)nr);
+                if (nrn) atomicAdd(&stat[4], (unsigned long long)nrn);
             }
             break;
         }
+        __syncwarp();  // the stash is complete before the second pass reads it
         // take the positions, and publish the ranges (empty where an array is full)
         int ok = 0;
         if (lane == 0) {
@@ -703,6 +786,31 @@ __global__ void k_p2p_stats(const LfmmComp* __restrict__ comps, int level_off, i
     }
 }
 
+// The particle-pair counts of the last build's leaf-level near lists (free
+// and reaction components), computed on request: the build only needs to
+// know whether any reaction entry is near.
+LfErr lf_p2p_pair_stats(lfmm_ctx* ctx)
+{
+    if (!ctx->p2p_stats_stale || !ctx->built) return LfErr();
+    cudaStream_t st = ctx->s_main;
+    const LfmmLevel& lf = ctx->levels[ctx->depth];
+    const int nb = ctx->nbox_total;
+    unsigned long long* stat = reinterpret_cast<unsigned long long*>(ctx->counts.as<char>() + 20480);
+    LF_CHECK(cudaMemsetAsync(stat + 2, 0, 2 * sizeof(unsigned long long), st));
+    if (lf.nbox > 0)
+        ++ctx->launches, k_p2p_stats<<<lf_blocks(lf.nbox, 8), 256, 0, st>>>(
+            ctx->comp_dev.as<LfmmComp>(), lf.off, lf.nbox, ctx->near_off.as<int>(), ctx->near_off.as<int>() + nb,
+            ctx->near_ent.as<uint32_t>(), ctx->box_pbeg.as<int>(), ctx->box_pend.as<int>(), stat);
+    LF_TRY(lf_cuda(cudaGetLastError(), "p2p stats"));
+    unsigned long long* h = lf_pin<unsigned long long>(ctx, LFMM_PIN_LIST);
+    LF_CHECK(cudaMemcpyAsync(h, stat + 2, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    LF_CHECK(cudaStreamSynchronize(st));
+    ctx->stats[LFMM_STAT_P2P_FREE] = (int64_t)h[0];
+    ctx->stats[LFMM_STAT_P2P_REACTION] = (int64_t)h[1];
+    ctx->p2p_stats_stale = 0;
+    return LfErr();
+}
+
 // grow a buffer keeping its first `keep` bytes
 static LfErr grow_keep(DevBuf& b, size_t bytes, size_t keep, cudaStream_t st)
 {
@@ -738,8 +846,10 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
     double* part = ctx->counts.as<double>();
     ++ctx->launches, k_bounds<<<nbb, 256, 0, st>>>(xyz, n, part);
     LF_TRY(lf_cuda(cudaGetLastError(), "bounds"));
-    std::vector<double> hp(nbb * 6);
-    LF_CHECK(cudaMemcpyAsync(hp.data(), part, sizeof(double) * 6 * nbb, cudaMemcpyDeviceToHost, st));
+    static_assert(LFMM_PIN_BOUNDS + 256 * 6 * sizeof(double) <= LFMM_PIN_M2R, "pinned regions");
+    const double* hp = lf_pin<double>(ctx, LFMM_PIN_BOUNDS);
+    LF_CHECK(cudaMemcpyAsync(lf_pin<double>(ctx, LFMM_PIN_BOUNDS), part, sizeof(double) * 6 * nbb,
+                             cudaMemcpyDeviceToHost, st));
     LF_CHECK(cudaStreamSynchronize(st));
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     for (int b = 0; b < nbb; ++b)
@@ -820,6 +930,7 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
     for (int j = 0; j < LFMM_MAXL; ++j) kp.d[j] = (j < ctx->L) ? ctx->d[j] : 0.0;
     for (int k = 0; k < 3; ++k) kp.org[k] = ctx->origin[k];
     kp.hfine = H / (double)(1 << fine);
+    kp.ihfine = 1.0 / kp.hfine;
     const int top = (1 << fine) - 1;
     // fine cells a layer's points may take: interfaces on cell planes (L == 1 or
     // an alignment unit) bound them exactly; otherwise the straddling cells count
@@ -854,7 +965,7 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
     // the flags come back (into pinned memory, without waiting) with the level
     // counts: a rejected point gets a clamped, valid key, so the sort and the
     // counts below stay in bounds
-    int* herr = reinterpret_cast<int*>(ctx->host_pin);
+    int* herr = lf_pin<int>(ctx, LFMM_PIN_ERR);
     LF_CHECK(cudaMemcpyAsync(herr, ctx->err_flag.ptr, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
     LF_TRY(lf_radix_sort(ctx, keys, vals, n, st));
 
@@ -872,8 +983,8 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
     LF_CHECK(cudaMemsetAsync(cnt, 0, sizeof(int) * 16, st));
     ++ctx->launches, k_level_counts<<<lf_blocks(n, 256), 256, 0, st>>>(keys, n, fine, cnt);
     LF_TRY(lf_cuda(cudaGetLastError(), "level counts"));
-    int hc[16];
-    LF_CHECK(cudaMemcpyAsync(hc, cnt, sizeof(int) * 16, cudaMemcpyDeviceToHost, st));
+    const int* hc = lf_pin<int>(ctx, LFMM_PIN_LEVELS);
+    LF_CHECK(cudaMemcpyAsync(lf_pin<int>(ctx, LFMM_PIN_LEVELS), cnt, sizeof(int) * 16, cudaMemcpyDeviceToHost, st));
     LF_CHECK(cudaStreamSynchronize(st));
     if (herr[0] & 2) {
         char buf[160];
@@ -1002,8 +1113,10 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
     int64_t near_used = 0;
     {
         const LfmmLevel& r = ctx->levels[0];
-        std::vector<uint32_t> rk(r.nbox);
-        LF_CHECK(cudaMemcpyAsync(rk.data(), bkey + r.off, 4 * r.nbox, cudaMemcpyDeviceToHost, st));
+        if (r.nbox > 128) return "internal: more than 128 root boxes";
+        const uint32_t* rk = lf_pin<uint32_t>(ctx, LFMM_PIN_ROOT);
+        LF_CHECK(cudaMemcpyAsync(lf_pin<uint32_t>(ctx, LFMM_PIN_ROOT), bkey + r.off, 4 * r.nbox, cudaMemcpyDeviceToHost,
+                                 st));
         LF_CHECK(cudaStreamSynchronize(st));
         int root_of[LFMM_MAXL + 1];
         for (int l = 0; l <= LFMM_MAXL; ++l) root_of[l] = -1;
@@ -1057,8 +1170,12 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
     // with the measured totals when an array overflows (first builds)
     for (int k = 0; k < 3; ++k)
         if (ctx->list_cap[k] == 0) ctx->list_cap[k] = (int64_t)nb * (k == 0 ? 64 : (k == 1 ? 189 : 16)) + nroot + 1024;
-    unsigned long long hs[8];
-    std::vector<unsigned> hsnap(3 * (size_t)(depth + 1));
+    // read-backs of the list phase, in the pinned buffer
+    unsigned long long* hs = lf_pin<unsigned long long>(ctx, LFMM_PIN_LIST);       // 8 statistics
+    int* hovp = lf_pin<int>(ctx, LFMM_PIN_LIST + 64);                              // overflow flag
+    unsigned* hused = lf_pin<unsigned>(ctx, LFMM_PIN_LIST + 80);                   // 3 counters
+    unsigned* hsnap = lf_pin<unsigned>(ctx, LFMM_PIN_LIST + 128);                  // 3 (depth + 1)
+    static_assert(LFMM_PIN_LIST + 128 + 3 * 17 * sizeof(unsigned) <= LFMM_PIN_M2L, "pinned regions");
     for (int attempt = 0;; ++attempt) {
         if (ctx->list_cap[0] > 0x7fffffffLL || ctx->list_cap[1] > 0x7fffffffLL || ctx->list_cap[2] > 0x7fffffffLL)
             return "interaction lists too long";
@@ -1090,26 +1207,19 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
         for (int l = 1; l <= depth; ++l) {
             const LfmmLevel& lv = ctx->levels[l];
             if (lv.nbox > 0)
-                ++ctx->launches, k_list_level<<<lf_blocks(lv.nbox, 4), 128, 0, st>>>(
+                ++ctx->launches, k_list_level<<<lf_blocks(lv.nbox, LST_WARPS), 32 * LST_WARPS, 0, st>>>(
                     med, lv.off, lv.nbox, l, par, cbeg, cend, ctx->box_grid.as<int4>(), o, stat,
                     ctx->box_key.as<uint32_t>(), ctx->m2l_inv.as<int>(),
-                    (want_slots && l >= 2) ? ctx->m2l_slots.as<int>() : nullptr, slot_err);
+                    (want_slots && l >= 2) ? ctx->m2l_slots.as<int>() : nullptr, slot_err, l == depth ? 1 : 0);
             LF_CHECK(cudaMemcpyAsync(snap + 3 * l, used, 3 * sizeof(unsigned), cudaMemcpyDeviceToDevice, st));
         }
         LF_TRY(lf_cuda(cudaGetLastError(), "lists"));
-        const LfmmLevel& lf = ctx->levels[depth];
-        ++ctx->launches, k_p2p_stats<<<lf_blocks(lf.nbox, 8), 256, 0, st>>>(ctx->comp_dev.as<LfmmComp>(), lf.off,
-                                                                          lf.nbox, nbeg, nend, o.near_ent, pbeg,
-                                                                          pend, stat);
-        LF_TRY(lf_cuda(cudaGetLastError(), "p2p stats"));
-        int hov = 0;
-        unsigned hused[3];
-        LF_CHECK(cudaMemcpyAsync(hs, stat, sizeof(hs), cudaMemcpyDeviceToHost, st));
-        LF_CHECK(cudaMemcpyAsync(&hov, overflow, sizeof(int), cudaMemcpyDeviceToHost, st));
-        LF_CHECK(cudaMemcpyAsync(hused, used, sizeof(hused), cudaMemcpyDeviceToHost, st));
-        LF_CHECK(cudaMemcpyAsync(hsnap.data(), snap, sizeof(unsigned) * hsnap.size(), cudaMemcpyDeviceToHost, st));
+        LF_CHECK(cudaMemcpyAsync(hs, stat, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+        LF_CHECK(cudaMemcpyAsync(hovp, overflow, sizeof(int), cudaMemcpyDeviceToHost, st));
+        LF_CHECK(cudaMemcpyAsync(hused, used, 3 * sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        LF_CHECK(cudaMemcpyAsync(hsnap, snap, sizeof(unsigned) * 3 * (size_t)(depth + 1), cudaMemcpyDeviceToHost, st));
         LF_CHECK(cudaStreamSynchronize(st));
-        if (!hov) break;
+        if (!*hovp) break;
         if (attempt >= 8) return "internal: interaction lists keep overflowing";
         // the counters kept counting past the capacities, but boxes below a
         // full array found no candidates: grow to at least the counted totals
@@ -1139,8 +1249,12 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
     ctx->stats[LFMM_STAT_LEAVES] = ctx->levels[depth].nbox;
     ctx->stats[LFMM_STAT_M2L_FREE] = (int64_t)hs[0];
     ctx->stats[LFMM_STAT_M2L_REACTION] = (int64_t)hs[1];
-    ctx->stats[LFMM_STAT_P2P_FREE] = (int64_t)hs[2];
-    ctx->stats[LFMM_STAT_P2P_REACTION] = (int64_t)hs[3];
+    // particle-pair counts only on request (lf_p2p_pair_stats); the near field
+    // needs to know whether any leaf's near list holds a reaction entry
+    ctx->near_reaction_entries = (int64_t)hs[4];
+    ctx->p2p_stats_stale = 1;
+    ctx->stats[LFMM_STAT_P2P_FREE] = 0;
+    ctx->stats[LFMM_STAT_P2P_REACTION] = 0;
     ctx->stats[LFMM_STAT_COMPONENTS] = ctx->ncomp;
     ctx->stats[LFMM_STAT_M2M_EDGES] = tot - ctx->levels[0].nbox;
     ctx->n = n;
