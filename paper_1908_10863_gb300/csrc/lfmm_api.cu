@@ -816,10 +816,10 @@ lfmm_status lf_build_dev(lfmm_ctx* ctx, int64_t n, const double* xyz_dev, const 
     ctx->built = false;
     prof_reset(ctx);
     int ph = lf_prof_start(ctx, LFMM_TIME_BUILD, ctx->s_main);
-    LfErr e = lf_build_tree(ctx, xyz_dev, layer_dev, n, ctx->s_main);
-    if (e.empty()) e = lf_near_prepare(ctx, ctx->s_main);
+    LfErr e = lf_build_tree(ctx, xyz_dev, layer_dev, n, ctx->s_main);  // (and the near field's positions)
     lf_prof_stop(ctx, ph, ctx->s_main);
     if (!e.empty()) {
+        cudaStreamSynchronize(ctx->s_near);
         cudaStreamSynchronize(ctx->s_main);
         return fail(ctx, e);
     }
@@ -983,7 +983,7 @@ void lfmm_destroy(lfmm_ctx* ctx)
     if (ctx->s_near) cudaStreamSynchronize(ctx->s_near);
     DevBuf* bufs[] = {&ctx->gl_t_m2l, &ctx->gl_w_m2l, &ctx->gl_t_near, &ctx->gl_w_near, &ctx->free_T64, &ctx->free_T32,
                       &ctx->oct_U64, &ctx->oct_U32, &ctx->comp_dev, &ctx->perm, &ctx->xs, &ctx->ys, &ctx->zs,
-                      &ctx->keys, &ctx->keys_tmp, &ctx->vals_tmp, &ctx->scan_tmp, &ctx->hist, &ctx->xyz_in,
+                      &ctx->keys, &ctx->keys_tmp, &ctx->vals_tmp, &ctx->scan_tmp, &ctx->hist, &ctx->keys_tmp2, &ctx->vals_tmp2, &ctx->scan_tmp2, &ctx->hist2, &ctx->xyz_in,
                       &ctx->layer_in, &ctx->err_flag, &ctx->counts, &ctx->box_key, &ctx->box_pbeg, &ctx->box_pend,
                       &ctx->box_parent, &ctx->box_cbeg, &ctx->box_cend, &ctx->box_center, &ctx->box_grid, &ctx->pos_rel, &ctx->leaf_of, &ctx->near_tab, &ctx->level_consts, &ctx->flags, &ctx->idx,
                       &ctx->near_off, &ctx->near_ent, &ctx->m2l_off, &ctx->m2l_ent, &ctx->m2r_off, &ctx->m2r_ent,

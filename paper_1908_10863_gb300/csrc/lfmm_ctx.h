@@ -88,6 +88,7 @@ struct lfmm_ctx {
     DevBuf perm;          // int32 [n]: sorted index -> caller index
     DevBuf xs, ys, zs;    // double [n]
     DevBuf keys, keys_tmp, vals_tmp, scan_tmp, hist;
+    DevBuf keys_tmp2, vals_tmp2, scan_tmp2, hist2;  // the same scratch for the build's second stream
     DevBuf xyz_in, layer_in;  // staging of host inputs
     DevBuf err_flag;          // int [4]
     DevBuf counts;            // misc small counters
@@ -136,8 +137,6 @@ struct lfmm_ctx {
     DevBuf near_tab;            // remainder tables of the near-field reaction kernels
     int near_tab_ready = 0, use_near_tab = 0;
     double near_tab_err = -1.0;  // largest relative deviation from the quadrature at the check points
-    std::vector<uint32_t> root_ent_h;
-    std::vector<int> root_beg_h, root_end_h, root_zero_h;
     double m2l_levelh_h[16] = {0};
     int m2l_tc_ok = 0, m2l_tc_ntiles = 0, use_tc = 1, tc_groups = 0;  // tc_groups 0: automatic
     int m2l_tc_wide = 0;  // tensor-core free M2L in its wide form ((p+1)^2 > 128): no tensor-core M2M / L2L
@@ -145,6 +144,7 @@ struct lfmm_ctx {
     DevBuf m2r_keys, m2r_order, m2r_tgt, m2r_kstart, m2r_kval, m2r_tables, m2r_levelh, m2r_batches;
     DevBuf m2r_tdesc, m2r_ktab;  // table descriptors (component, level, rho^2, oz); table of each key
     std::vector<int4> m2r_tdesc_h, m2r_batches_h;  // host staging of asynchronous uploads
+    int m2r_pending_ne = 0;             // reaction M2L entries whose key grouping awaits lf_prepare_m2r_finish
     int64_t near_reaction_entries = 0;  // leaf-level near entries of reaction components (last build)
     int p2p_stats_stale = 0;            // the particle-pair statistics wait for lf_p2p_pair_stats
     std::vector<int> m2r_slot_h;                   // reaction table lookup: slot per (rho^2, oz)
@@ -200,6 +200,7 @@ LfErr lf_cuda(cudaError_t e, const char* what);
 #define LFMM_PIN_M2L 2048       // free M2L class counts (144 ints)
 #define LFMM_PIN_ROOT 2688      // root box keys (up to 128)
 #define LFMM_PIN_BOUNDS 4096    // bounding-box partials (256 blocks x 6 doubles)
+#define LFMM_PIN_UP 4096        // later in the build: root lists and list counters to upload (12 KB)
 #define LFMM_PIN_M2R 16384      // reaction M2L key starts and values (the rest)
 template <typename T>
 inline T* lf_pin(const lfmm_ctx* ctx, size_t off)
@@ -222,13 +223,15 @@ LfErr lf_setup_m2l_ops(lfmm_ctx* ctx);
 LfErr lf_prepare_m2l(lfmm_ctx* ctx, cudaStream_t st);
 LfErr lf_m2l_gemm(lfmm_ctx* ctx, cudaStream_t st);
 // ---- reaction M2L by geometry key (lfmm_m2r.cu) ----
-LfErr lf_prepare_m2r(lfmm_ctx* ctx, cudaStream_t st);
+LfErr lf_prepare_m2r(lfmm_ctx* ctx, cudaStream_t st);         // enqueue (no synchronisation)
+LfErr lf_prepare_m2r_finish(lfmm_ctx* ctx, cudaStream_t st);  // synchronise st, host part
 LfErr lf_m2r_apply(lfmm_ctx* ctx, cudaStream_t st);
 LfErr lf_m2r_ops(lfmm_ctx* ctx, cudaStream_t st);
 LfErr lf_m2r_device(lfmm_ctx* ctx, cudaStream_t st);
 // stable LSD radix sort of uint32 (key, value) pairs (lfmm_tree.cu); uses keys_tmp, vals_tmp, hist
+// (set 1: keys_tmp2, vals_tmp2, hist2)
 LfErr lf_radix_sort(lfmm_ctx* ctx, uint32_t* keys, uint32_t* vals, int64_t n, cudaStream_t st, int first_pass = 0,
-                    int npass = 4);
+                    int npass = 4, int set = 0);
 
 // ---- evaluation (lfmm_fmm.cu, lfmm_near.cu) ----
 LfErr lf_evaluate_sorted(lfmm_ctx* ctx, int nrhs, const double* q_dev, double* phi_dev, double* field_dev,
@@ -277,7 +280,8 @@ LfErr lf_reaction_kernel_dev(lfmm_ctx* ctx, int comp, int npts, const double* rh
 int lf_find_comp(const lfmm_ctx* ctx, int l, int lp, int a, int b);
 
 // exclusive scan of int32 (lfmm_tree.cu); returns the total through *total (host) if non-null
-LfErr lf_scan_i32(lfmm_ctx* ctx, const int* in, int* out, int64_t n, int64_t* total, cudaStream_t st);
+// set: scratch buffers 0 (the build's main stream) or 1 (its second stream)
+LfErr lf_scan_i32(lfmm_ctx* ctx, const int* in, int* out, int64_t n, int64_t* total, cudaStream_t st, int set = 0);
 
 // profile helpers: lf_prof_start returns a handle for lf_prof_stop (or -1 when off)
 int lf_prof_start(lfmm_ctx* ctx, int slot, cudaStream_t st);

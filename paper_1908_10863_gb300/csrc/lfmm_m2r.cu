@@ -150,6 +150,7 @@ LfErr lf_prepare_m2r(lfmm_ctx* ctx, cudaStream_t st)
     ctx->stats[LFMM_STAT_REACTION_KEYS] = 0;
     ctx->stats[LFMM_STAT_REACTION_TABLES] = 0;
     ctx->m2r_keyed_from = ctx->depth + 1;
+    ctx->m2r_pending_ne = 0;
     // the keyed GEMM holds a whole operator in shared memory (p <= 10) or
     // stages it in chunks (p <= 15)
     if (ctx->m2l_rm == 0 || ctx->m2l_rm > 16 || ctx->m2r_total == 0) return LfErr();
@@ -196,19 +197,38 @@ LfErr lf_prepare_m2r(lfmm_ctx* ctx, cudaStream_t st)
     LF_TRY(lf_cuda(cudaGetLastError(), "m2r keys"));
     // vals hold absolute entry indices (e), keys sorted ascending
     // keys use bits 0..21 (component << 16 | level << 12 | offset): three digits
-    LF_TRY(lf_radix_sort(ctx, keys, vals, ne, st, 0, 3));
+    LF_TRY(lf_radix_sort(ctx, keys, vals, ne, st, 0, 3, 1));
     LF_TRY(lf_reserve(ctx->flags, (size_t)ne * 4 + 16));
     LF_TRY(lf_reserve(ctx->idx, (size_t)ne * 4 + 16));
     int* fl = ctx->flags.as<int>();
     int* ix = ctx->idx.as<int>();
     ++ctx->launches, k_key_flags<<<lf_blocks(ne, 256), 256, 0, st>>>(keys, ne, fl);
-    int64_t nk = 0;
-    LF_TRY(lf_scan_i32(ctx, fl, ix, ne, &nk, st));
-    LF_TRY(lf_reserve(ctx->m2r_kstart, (size_t)(nk + 1) * 4));
-    LF_TRY(lf_reserve(ctx->m2r_kval, (size_t)(nk + 1) * 4));
+    // the key count comes back with the last flag and scan value (pinned, no
+    // wait here): the key arrays are sized for one key per entry
+    int* klast = lf_pin<int>(ctx, LFMM_PIN_SCAN + 8);
+    LF_CHECK(cudaMemcpyAsync(klast, fl + ne - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LF_TRY(lf_scan_i32(ctx, fl, ix, ne, nullptr, st, 1));
+    LF_CHECK(cudaMemcpyAsync(klast + 1, ix + ne - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LF_TRY(lf_reserve(ctx->m2r_kstart, (size_t)(ne + 1) * 4));
+    LF_TRY(lf_reserve(ctx->m2r_kval, (size_t)(ne + 1) * 4));
     ++ctx->launches, k_key_starts<<<lf_blocks(ne, 256), 256, 0, st>>>(keys, ne, fl, ix, ctx->m2r_kstart.as<int>(),
                                                                        ctx->m2r_kval.as<uint32_t>());
     LF_TRY(lf_cuda(cudaGetLastError(), "m2r key starts"));
+    ctx->m2r_pending_ne = ne;  // the rest (key count, tables, batches) in lf_prepare_m2r_finish
+    return LfErr();
+}
+
+// After lf_prepare_m2r: wait for its device part on st, read the keys back
+// and set up the tables and batches.
+LfErr lf_prepare_m2r_finish(lfmm_ctx* ctx, cudaStream_t st)
+{
+    const int ne = ctx->m2r_pending_ne;
+    if (ne <= 0) return LfErr();
+    ctx->m2r_pending_ne = 0;
+    LF_CHECK(cudaStreamSynchronize(st));
+    const int* klast = lf_pin<int>(ctx, LFMM_PIN_SCAN + 8);
+    const int64_t nk = (int64_t)klast[0] + klast[1];
+    int* bad = reinterpret_cast<int*>(ctx->counts.as<char>() + 32768);
     // key starts, key values and the error flag come back into the pinned
     // buffer when they fit (one synchronisation), else into host vectors
     const size_t pin_need = sizeof(int) * (2 * (size_t)nk + 2);
@@ -221,7 +241,8 @@ LfErr lf_prepare_m2r(lfmm_ctx* ctx, cudaStream_t st)
     }
     int* kstart = pinned ? lf_pin<int>(ctx, LFMM_PIN_M2R) : kst_h.data();
     uint32_t* kv = pinned ? lf_pin<uint32_t>(ctx, LFMM_PIN_M2R + sizeof(int) * (nk + 1)) : kv_h.data();
-    int* hbad = pinned ? lf_pin<int>(ctx, LFMM_PIN_M2R + sizeof(int) * (2 * (size_t)nk + 1)) : lf_pin<int>(ctx, LFMM_PIN_SCAN);
+    int* hbad = pinned ? lf_pin<int>(ctx, LFMM_PIN_M2R + sizeof(int) * (2 * (size_t)nk + 1))
+                       : lf_pin<int>(ctx, LFMM_PIN_SCAN + 16);
     LF_CHECK(cudaMemcpyAsync(kstart, ctx->m2r_kstart.ptr, sizeof(int) * nk, cudaMemcpyDeviceToHost, st));
     LF_CHECK(cudaMemcpyAsync(kv, ctx->m2r_kval.ptr, sizeof(uint32_t) * nk, cudaMemcpyDeviceToHost, st));
     LF_CHECK(cudaMemcpyAsync(hbad, bad, 4, cudaMemcpyDeviceToHost, st));

@@ -108,23 +108,24 @@ static LfErr scan_rec(lfmm_ctx* ctx, const int* in, int* out, int64_t n, int* tm
     return lf_cuda(cudaGetLastError(), "scan add");
 }
 
-LfErr lf_scan_i32(lfmm_ctx* ctx, const int* in, int* out, int64_t n, int64_t* total, cudaStream_t st)
+LfErr lf_scan_i32(lfmm_ctx* ctx, const int* in, int* out, int64_t n, int64_t* total, cudaStream_t st, int set)
 {
     if (n <= 0) {
         if (total) *total = 0;
         return LfErr();
     }
+    DevBuf& tmp = set ? ctx->scan_tmp2 : ctx->scan_tmp;
     int64_t need = 0, m = n;
     while (m > 1) {
         m = (m + SCAN_TILE - 1) / SCAN_TILE;
         need += m + 1;
     }
-    LF_TRY(lf_reserve(ctx->scan_tmp, (size_t)(need + 16) * sizeof(int)));
+    LF_TRY(lf_reserve(tmp, (size_t)(need + 16) * sizeof(int)));
     // the last input is copied before the scan is enqueued, so in-place scans
     // work (into pinned memory: neither copy waits, one synchronisation)
-    int* last = lf_pin<int>(ctx, LFMM_PIN_SCAN);
+    int* last = lf_pin<int>(ctx, LFMM_PIN_SCAN + 8 * set);
     if (total) LF_CHECK(cudaMemcpyAsync(last, in + n - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
-    LF_TRY(scan_rec(ctx, in, out, n, ctx->scan_tmp.as<int>(), st));
+    LF_TRY(scan_rec(ctx, in, out, n, tmp.as<int>(), st));
     if (total) {
         LF_CHECK(cudaMemcpyAsync(last + 1, out + n - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
         LF_CHECK(cudaStreamSynchronize(st));
@@ -203,19 +204,22 @@ __global__ void k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t
 // Sorts by the key bits [8 first_pass, 8 (first_pass + npass)); the other
 // bits are ignored (stable within equal digits).
 LfErr lf_radix_sort(lfmm_ctx* ctx, uint32_t* keys, uint32_t* vals, int64_t n, cudaStream_t st, int first_pass,
-                    int npass)
+                    int npass, int set)
 {
     int nb = lf_blocks(n, RS_TILE);
-    LF_TRY(lf_reserve(ctx->keys_tmp, (size_t)n * 4));
-    LF_TRY(lf_reserve(ctx->vals_tmp, (size_t)n * 4));
-    LF_TRY(lf_reserve(ctx->hist, (size_t)256 * nb * 4));
-    uint32_t *ka = keys, *va = vals, *kb = ctx->keys_tmp.as<uint32_t>(), *vb = ctx->vals_tmp.as<uint32_t>();
-    int* h = ctx->hist.as<int>();
+    DevBuf& kt = set ? ctx->keys_tmp2 : ctx->keys_tmp;
+    DevBuf& vt = set ? ctx->vals_tmp2 : ctx->vals_tmp;
+    DevBuf& ht = set ? ctx->hist2 : ctx->hist;
+    LF_TRY(lf_reserve(kt, (size_t)n * 4));
+    LF_TRY(lf_reserve(vt, (size_t)n * 4));
+    LF_TRY(lf_reserve(ht, (size_t)256 * nb * 4));
+    uint32_t *ka = keys, *va = vals, *kb = kt.as<uint32_t>(), *vb = vt.as<uint32_t>();
+    int* h = ht.as<int>();
     for (int pass = first_pass; pass < first_pass + npass; ++pass) {
         int shift = 8 * pass;
         ++ctx->launches, k_radix_hist<<<nb, RS_T, 0, st>>>(ka, n, shift, h, nb);
         LF_TRY(lf_cuda(cudaGetLastError(), "radix hist"));
-        LF_TRY(lf_scan_i32(ctx, h, h, (int64_t)256 * nb, nullptr, st));
+        LF_TRY(lf_scan_i32(ctx, h, h, (int64_t)256 * nb, nullptr, st, set));
         ++ctx->launches, k_radix_scatter<<<nb, RS_T, 0, st>>>(ka, va, kb, vb, n, shift, h, nb);
         LF_TRY(lf_cuda(cudaGetLastError(), "radix scatter"));
         std::swap(ka, kb);
@@ -652,6 +656,10 @@ __global__ void __launch_bounds__(32 * LST_WARPS) k_list_level(LfListMedium med,
     const int eb = o.nbeg[pt], ee = o.nend[pt];
     int wf = 0, wr = 0, wn = 0;
     int nst = 0;  // accepted candidates (stashed while nst <= LST_CAP)
+    if (slots) {
+        for (int j = lane; j < 189; j += 32) slots[(size_t)t * 189 + j] = -1;
+        __syncwarp();
+    }
     for (int pass = 0; pass < 2; ++pass) {
         int nf = 0, nr = 0, nn = 0;  // warp-uniform running counts
         int nrn = 0;                 // leaf level: near entries of reaction components
@@ -1122,37 +1130,39 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
         for (int l = 0; l <= LFMM_MAXL; ++l) root_of[l] = -1;
         for (int i = 0; i < r.nbox; ++i) root_of[rk[i]] = r.off + i;
         for (int l = 0; l <= LFMM_MAXL; ++l) ctx->nlayer_used[l] = root_of[l] >= 0;
-        // host staging owned by the context: the copies need no synchronisation
-        std::vector<uint32_t>& ent = ctx->root_ent_h;
-        std::vector<int>& hb = ctx->root_beg_h;
-        std::vector<int>& he = ctx->root_end_h;
-        std::vector<int>& zero = ctx->root_zero_h;
-        ent.clear();
-        hb.assign(r.nbox, 0);
-        he.assign(r.nbox, 0);
-        zero.assign(r.nbox, 0);
+        // staged in the pinned buffer (the bounds region, read long before):
+        // the copies are queued without waiting, and the buffer is not
+        // written again before the build's final synchronisation
+        constexpr int MAXE = 2048;  // root entries: roots x components
+        uint32_t* ent = lf_pin<uint32_t>(ctx, LFMM_PIN_UP);
+        int* hb = lf_pin<int>(ctx, LFMM_PIN_UP + 4 * MAXE);
+        int* he = hb + 128;
+        int* zero = he + 128;
+        static_assert(4 * MAXE + 3 * 128 * 4 + 8 * 16 <= LFMM_PIN_M2R - LFMM_PIN_UP, "pinned regions");
+        int ne = 0;
         for (int i = 0; i < r.nbox; ++i) {
             int tl = (int)rk[i];
-            hb[i] = (int)ent.size();
+            hb[i] = ne;
+            zero[i] = 0;
             for (int c = 0; c < ctx->ncomp; ++c) {
                 const LfmmComp& cp = ctx->comp[c];
                 if (cp.l != tl) continue;
                 int src = root_of[cp.lp];
                 if (src < 0) continue;
-                ent.push_back(((uint32_t)c << LFMM_ENT_SHIFT) | (uint32_t)src);
+                if (ne >= MAXE) return "internal: too many root list entries";
+                ent[ne++] = ((uint32_t)c << LFMM_ENT_SHIFT) | (uint32_t)src;
             }
-            he[i] = (int)ent.size();
+            he[i] = ne;
         }
-        LF_TRY(grow_keep(ctx->near_ent, std::max<size_t>(ent.size(), 1) * 4, 0, st));
-        if (!ent.empty())
-            LF_CHECK(cudaMemcpyAsync(ctx->near_ent.ptr, ent.data(), ent.size() * 4, cudaMemcpyHostToDevice, st));
-        LF_CHECK(cudaMemcpyAsync(nbeg + r.off, hb.data(), 4 * r.nbox, cudaMemcpyHostToDevice, st));
-        LF_CHECK(cudaMemcpyAsync(nend + r.off, he.data(), 4 * r.nbox, cudaMemcpyHostToDevice, st));
-        LF_CHECK(cudaMemcpyAsync(mbeg + r.off, zero.data(), 4 * r.nbox, cudaMemcpyHostToDevice, st));
-        LF_CHECK(cudaMemcpyAsync(mend + r.off, zero.data(), 4 * r.nbox, cudaMemcpyHostToDevice, st));
-        LF_CHECK(cudaMemcpyAsync(rbeg + r.off, zero.data(), 4 * r.nbox, cudaMemcpyHostToDevice, st));
-        LF_CHECK(cudaMemcpyAsync(rend + r.off, zero.data(), 4 * r.nbox, cudaMemcpyHostToDevice, st));
-        near_used = (int64_t)ent.size();
+        LF_TRY(grow_keep(ctx->near_ent, std::max<size_t>((size_t)ne, 1) * 4, 0, st));
+        if (ne > 0) LF_CHECK(cudaMemcpyAsync(ctx->near_ent.ptr, ent, (size_t)ne * 4, cudaMemcpyHostToDevice, st));
+        LF_CHECK(cudaMemcpyAsync(nbeg + r.off, hb, 4 * r.nbox, cudaMemcpyHostToDevice, st));
+        LF_CHECK(cudaMemcpyAsync(nend + r.off, he, 4 * r.nbox, cudaMemcpyHostToDevice, st));
+        LF_CHECK(cudaMemcpyAsync(mbeg + r.off, zero, 4 * r.nbox, cudaMemcpyHostToDevice, st));
+        LF_CHECK(cudaMemcpyAsync(mend + r.off, zero, 4 * r.nbox, cudaMemcpyHostToDevice, st));
+        LF_CHECK(cudaMemcpyAsync(rbeg + r.off, zero, 4 * r.nbox, cudaMemcpyHostToDevice, st));
+        LF_CHECK(cudaMemcpyAsync(rend + r.off, zero, 4 * r.nbox, cudaMemcpyHostToDevice, st));
+        near_used = ne;
         ctx->levels[0].near_base = 0;
         ctx->levels[0].near_count = near_used;
     }
@@ -1183,11 +1193,14 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
         LF_TRY(grow_keep(ctx->near_ent, (size_t)ctx->list_cap[0] * 4 + 16, (size_t)nroot * 4, st));
         LF_TRY(lf_reserve(ctx->m2l_ent, (size_t)ctx->list_cap[1] * 4 + 16));
         LF_TRY(lf_reserve(ctx->m2r_ent, (size_t)ctx->list_cap[2] * 4 + 16));
-        const unsigned init[4] = {(unsigned)nroot, 0u, 0u, 0u};
-        LF_CHECK(cudaMemcpyAsync(used, init, sizeof(init), cudaMemcpyHostToDevice, st));
+        // one pinned slot per attempt (an attempt's upload may still be queued)
+        unsigned* init = lf_pin<unsigned>(ctx, LFMM_PIN_UP + 4 * 2048 + 3 * 128 * 4 + 16 * (attempt % 8));
+        init[0] = (unsigned)nroot;
+        init[1] = init[2] = init[3] = 0u;
+        LF_CHECK(cudaMemcpyAsync(used, init, 4 * sizeof(unsigned), cudaMemcpyHostToDevice, st));
         LF_CHECK(cudaMemsetAsync(stat, 0, 8 * 8, st));
         LF_CHECK(cudaMemsetAsync(slot_err, 0, sizeof(int), st));
-        if (want_slots) LF_CHECK(cudaMemsetAsync(ctx->m2l_slots.ptr, 0xff, (size_t)nb * 189 * sizeof(int), st));
+        // (the list kernel clears each box's slots of levels >= 2 before filling them)
         ListOut o;
         o.near_ent = ctx->near_ent.as<uint32_t>();
         o.m2l_ent = ctx->m2l_ent.as<uint32_t>();
@@ -1259,6 +1272,17 @@ LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz, const int32_t* layer, int6
     ctx->stats[LFMM_STAT_M2M_EDGES] = tot - ctx->levels[0].nbox;
     ctx->n = n;
     ctx->stats[LFMM_STAT_REACTION_KEYS] = 0;
+    // the reaction M2L keys and the near field's relative positions go on the
+    // second stream, beside the free M2L classes and slots on this one (their
+    // scratch buffers and pinned read-back regions are disjoint)
+    cudaStream_t s2 = ctx->s_near;
+    LF_CHECK(cudaEventRecord(ctx->ev_fork, st));
+    LF_CHECK(cudaStreamWaitEvent(s2, ctx->ev_fork, 0));
+    LF_TRY(lf_prepare_m2r(ctx, s2));
+    LF_TRY(lf_near_prepare(ctx, s2));
     LF_TRY(lf_prepare_m2l(ctx, st));
-    return lf_prepare_m2r(ctx, st);
+    LF_TRY(lf_prepare_m2r_finish(ctx, s2));
+    LF_CHECK(cudaEventRecord(ctx->ev_join, s2));
+    LF_CHECK(cudaStreamWaitEvent(st, ctx->ev_join, 0));
+    return LfErr();
 }
