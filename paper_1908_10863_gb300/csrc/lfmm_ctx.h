@@ -145,6 +145,9 @@ struct lfmm_ctx {
     DevBuf m2r_tdesc, m2r_ktab;  // table descriptors (component, level, rho^2, oz); table of each key
     std::vector<int4> m2r_tdesc_h, m2r_batches_h;  // host staging of asynchronous uploads
     int m2r_pending_ne = 0;             // reaction M2L entries whose key grouping awaits lf_prepare_m2r_finish
+    int m2r_la = 0;                     // first level with reaction M2L entries (keyed from there if in range)
+    int m2r_kfirst = 0;                 // first key of the keyed levels among the sorted keys
+    DevBuf m2r_zfrac, m2r_zbase;        // per (component, level): image offset fraction and integer base
     int64_t near_reaction_entries = 0;  // leaf-level near entries of reaction components (last build)
     int p2p_stats_stale = 0;            // the particle-pair statistics wait for lf_p2p_pair_stats
     std::vector<int> m2r_slot_h;                   // reaction table lookup: slot per (rho^2, oz)

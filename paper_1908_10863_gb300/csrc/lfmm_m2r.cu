@@ -38,29 +38,34 @@ static inline int lf_blocks(int64_t n, int t) { return (int)((n + t - 1) / t); }
 #define KEY_NONE 0xffffffffu
 
 
-// key = comp (7 bits) | level (4 bits) | offset index (12 bits, offsets in [-7, 7]^3)
+// key = level (4 bits) | comp (7 bits) | offset index (12 bits, offsets in
+// [-7, 7]^3): sorted keys group a level's keys together, so the keys of the
+// levels left to the per-pair kernel are a prefix
 #define R_OR 7
 #define R_OW (2 * R_OR + 1)
 __host__ __device__ __forceinline__ uint32_t rkey(int c, int l, int ox, int oy, int oz)
 {
-    return ((uint32_t)c << 16) | ((uint32_t)l << 12) | (uint32_t)(((ox + R_OR) * R_OW + (oy + R_OR)) * R_OW + (oz + R_OR));
+    return ((uint32_t)l << 19) | ((uint32_t)c << 12) | (uint32_t)(((ox + R_OR) * R_OW + (oy + R_OR)) * R_OW + (oz + R_OR));
 }
 __host__ __device__ __forceinline__ void rkey_decode(uint32_t key, int& c, int& l, int& ox, int& oy, int& oz)
 {
-    c = (int)(key >> 16);
-    l = (int)((key >> 12) & 15u);
+    c = (int)((key >> 12) & 127u);
+    l = (int)(key >> 19);
     int oi = (int)(key & 4095u);
     ox = oi / (R_OW * R_OW) - R_OR;
     oy = (oi / R_OW) % R_OW - R_OR;
     oz = oi % R_OW - R_OR;
 }
 
-// Keys of the reaction M2L entries of one aligned level, from the boxes' grid
-// cells: lateral offsets are exact integers; the vertical offset of the
-// source's polarization image, (iz_t + 1/2) - s (iz_s + 1/2) - K, is an integer
-// on aligned levels (checked).
+// Keys of the reaction M2L entries of one level, from the boxes' grid cells.
+// Lateral offsets are exact integers.  The vertical offset of the source's
+// polarization image, in box units, (iz_t + 1/2) - s (iz_s + 1/2) - K, is
+// n + f with the integer n = iz_t - s iz_s + base and the fraction f fixed per
+// (component, level) (0 on levels where the interfaces are grid planes); the
+// key holds n, the table is taken at n + f.  An entry outside the key's
+// offset range counts in bad[level] (its level then stays per pair).
 __global__ void k_m2r_keys(const LfmmComp* __restrict__ comps, int off, int nb, const int4* __restrict__ grid,
-                           const float4* __restrict__ lc,
+                           const int* __restrict__ zbase,
                            const int* __restrict__ rbeg, const int* __restrict__ rend,
                            const uint32_t* __restrict__ rent, int level, uint32_t* __restrict__ keys,
                            uint32_t* __restrict__ vals, int* __restrict__ tgt, int* __restrict__ bad)
@@ -76,12 +81,10 @@ __global__ void k_m2r_keys(const LfmmComp* __restrict__ comps, int off, int nb, 
         int s = (int)(v & LFMM_ENT_MASK);
         const LfmmComp& cp = comps[c];
         const int4 gs = grid[s];
-        const float4 k = lc[c * 16 + level];
-        const float vz = ((float)gt.z + 0.5f) - (float)cp.s * ((float)gs.z + 0.5f) - k.x;
-        const int ox = gt.x - gs.x, oy = gt.y - gs.y, oz = (int)lrintf(vz);
-        bool ok = fabsf(vz - (float)oz) < 1e-3f && ox >= -R_OR && ox <= R_OR && oy >= -R_OR && oy <= R_OR &&
-                  oz >= -R_OR && oz <= R_OR;
-        if (!ok) atomicAdd(bad, 1);
+        const int sz = cp.s > 0.0 ? 1 : -1;
+        const int ox = gt.x - gs.x, oy = gt.y - gs.y, oz = gt.z - sz * gs.z + zbase[c * 16 + level];
+        const bool ok = ox >= -R_OR && ox <= R_OR && oy >= -R_OR && oy <= R_OR && oz >= -R_OR && oz <= R_OR;
+        if (!ok) atomicAdd(bad + level, 1);
         keys[e] = ok ? rkey(c, level, ox, oy, oz) : KEY_NONE;
         vals[e] = (uint32_t)e;
         tgt[e] = t;
@@ -110,7 +113,7 @@ __global__ void k_key_starts(const uint32_t* __restrict__ keys, int n, const int
 // when the operator is assembled.
 template <bool GEN>
 __global__ void k_m2r_tables(const LfmmComp* __restrict__ comps, const int4* __restrict__ tdesc, int ntab,
-                             const double* __restrict__ levelh, int P,
+                             const double* __restrict__ levelh, const double* __restrict__ zfrac, int P,
                              const double* __restrict__ gt, const double* __restrict__ gw, int Q,
                              double* __restrict__ tables)
 {
@@ -124,7 +127,8 @@ __global__ void k_m2r_tables(const LfmmComp* __restrict__ comps, const int4* __r
     const int c = d.x, l = d.y, oz = d.w;
     const LfmmComp cp = comps[c];
     const double rho = sqrt((double)d.z);
-    const double zz = (cp.a == 1) ? (double)oz : (double)(-oz);
+    const double vz = (double)oz + zfrac[c * 16 + l];  // image offset n + f in box units
+    const double zz = (cp.a == 1) ? vz : -vz;
     for (int j = threadIdx.x; j < TT; j += blockDim.x) sT[j] = 0.0;
     __syncthreads();
     lf_sommerfeld_table_block<GEN>(cp, rho, zz, levelh[l], 2 * P, sT, TS, Q, gt, gw, sJ, sA);
@@ -154,21 +158,42 @@ LfErr lf_prepare_m2r(lfmm_ctx* ctx, cudaStream_t st)
     // the keyed GEMM holds a whole operator in shared memory (p <= 10) or
     // stages it in chunks (p <= 15)
     if (ctx->m2l_rm == 0 || ctx->m2l_rm > 16 || ctx->m2r_total == 0) return LfErr();
-    // first level whose grid planes contain the interfaces
+    // every level with reaction entries is keyed; a level some of whose
+    // entries fall outside the key's offset range stays per pair (found at
+    // lf_prepare_m2r_finish)
     int la = ctx->depth + 1;
-    for (int l = 0; l <= ctx->depth; ++l) {
-        const double h = ctx->levels[l].h;
-        bool ok = true;
-        for (int i = 0; i < ctx->L; ++i) {
-            double r = (ctx->d[i] - ctx->origin[2]) / h;
-            if (fabs(r - llround(r)) > 1e-9 * std::max(1.0, fabs(r))) ok = false;
-        }
-        if (ok) {
+    for (int l = 0; l <= ctx->depth; ++l)
+        if (ctx->levels[l].m2r_count > 0) {
             la = l;
             break;
         }
+    if (la > ctx->depth) return LfErr();
+    ctx->m2r_la = la;
+    // per (component, level): the image's vertical offset in box units is
+    // iz_t - s iz_s + g with g = (1 - s)/2 - K, K = (o + (s - 1) z0)/h; split
+    // as an integer base (for the keys) and a fraction in [0, 1) (for the tables)
+    {
+        static_assert(LFMM_PIN_M2R + LFMM_MAXCOMP * 16 * (sizeof(double) + sizeof(int)) <= LFMM_PIN_BYTES,
+                      "pinned regions");
+        double* zf = lf_pin<double>(ctx, LFMM_PIN_M2R);
+        int* zb = lf_pin<int>(ctx, LFMM_PIN_M2R + LFMM_MAXCOMP * 16 * sizeof(double));
+        for (int c = 0; c < LFMM_MAXCOMP; ++c)
+            for (int l = 0; l < 16; ++l) {
+                double g = 0.0;
+                if (c < ctx->ncomp && l <= ctx->depth) {
+                    const LfmmComp& cp = ctx->comp[c];
+                    const double K = (cp.o + (cp.s - 1.0) * ctx->origin[2]) / ctx->levels[l].h;
+                    g = 0.5 * (1.0 - cp.s) - K;
+                }
+                const double b = std::floor(g + 1e-9);
+                zb[c * 16 + l] = (int)b;
+                zf[c * 16 + l] = std::max(0.0, g - b);
+            }
+        LF_TRY(lf_reserve(ctx->m2r_zfrac, LFMM_MAXCOMP * 16 * sizeof(double)));
+        LF_TRY(lf_reserve(ctx->m2r_zbase, LFMM_MAXCOMP * 16 * sizeof(int)));
+        LF_CHECK(cudaMemcpyAsync(ctx->m2r_zfrac.ptr, zf, LFMM_MAXCOMP * 16 * sizeof(double), cudaMemcpyHostToDevice, st));
+        LF_CHECK(cudaMemcpyAsync(ctx->m2r_zbase.ptr, zb, LFMM_MAXCOMP * 16 * sizeof(int), cudaMemcpyHostToDevice, st));
     }
-    ctx->m2r_keyed_from = la;
     int64_t first = -1, last = -1;
     for (int l = la; l <= ctx->depth; ++l) {
         const LfmmLevel& lv = ctx->levels[l];
@@ -181,22 +206,22 @@ LfErr lf_prepare_m2r(lfmm_ctx* ctx, cudaStream_t st)
     LF_TRY(lf_reserve(ctx->m2r_keys, (size_t)ne * 4 + 16));
     LF_TRY(lf_reserve(ctx->m2r_order, (size_t)ne * 4 + 16));
     LF_TRY(lf_reserve(ctx->m2r_tgt, (size_t)ctx->m2r_total * 4 + 16));
-    int* bad = reinterpret_cast<int*>(ctx->counts.as<char>() + 32768);
-    LF_CHECK(cudaMemsetAsync(bad, 0, 16, st));
-    // entries of aligned levels are contiguous: index them relative to `first`
+    int* bad = reinterpret_cast<int*>(ctx->counts.as<char>() + 32768);  // [16 levels]
+    LF_CHECK(cudaMemsetAsync(bad, 0, 16 * sizeof(int), st));
+    // entries of levels la .. depth are contiguous: index them relative to `first`
     uint32_t* keys = ctx->m2r_keys.as<uint32_t>();
     uint32_t* vals = ctx->m2r_order.as<uint32_t>();
     for (int l = la; l <= ctx->depth; ++l) {
         const LfmmLevel& lv = ctx->levels[l];
         if (lv.nbox == 0 || lv.m2r_count == 0) continue;
         ++ctx->launches, k_m2r_keys<<<lf_blocks(lv.nbox, 4), 128, 0, st>>>(
-            ctx->comp_dev.as<LfmmComp>(), lv.off, lv.nbox, ctx->box_grid.as<int4>(), ctx->level_consts.as<float4>(), ctx->m2r_off.as<int>(),
+            ctx->comp_dev.as<LfmmComp>(), lv.off, lv.nbox, ctx->box_grid.as<int4>(), ctx->m2r_zbase.as<int>(), ctx->m2r_off.as<int>(),
             ctx->m2r_off.as<int>() + ctx->nbox_total, ctx->m2r_ent.as<uint32_t>(), l, keys - first, vals - first,
             ctx->m2r_tgt.as<int>(), bad);
     }
     LF_TRY(lf_cuda(cudaGetLastError(), "m2r keys"));
     // vals hold absolute entry indices (e), keys sorted ascending
-    // keys use bits 0..21 (component << 16 | level << 12 | offset): three digits
+    // keys use bits 0..22 (level << 19 | component << 12 | offset): three digits
     LF_TRY(lf_radix_sort(ctx, keys, vals, ne, st, 0, 3, 1));
     LF_TRY(lf_reserve(ctx->flags, (size_t)ne * 4 + 16));
     LF_TRY(lf_reserve(ctx->idx, (size_t)ne * 4 + 16));
@@ -229,9 +254,10 @@ LfErr lf_prepare_m2r_finish(lfmm_ctx* ctx, cudaStream_t st)
     const int* klast = lf_pin<int>(ctx, LFMM_PIN_SCAN + 8);
     const int64_t nk = (int64_t)klast[0] + klast[1];
     int* bad = reinterpret_cast<int*>(ctx->counts.as<char>() + 32768);
-    // key starts, key values and the error flag come back into the pinned
-    // buffer when they fit (one synchronisation), else into host vectors
-    const size_t pin_need = sizeof(int) * (2 * (size_t)nk + 2);
+    // key starts, key values and the per-level range counts come back into
+    // the pinned buffer when they fit (one synchronisation), else into host
+    // vectors (the pinned region's staged uploads are complete by now)
+    const size_t pin_need = sizeof(int) * (2 * (size_t)nk + 17);
     const bool pinned = LFMM_PIN_M2R + pin_need <= LFMM_PIN_BYTES;
     std::vector<int>& kst_h = ctx->m2r_kstart_h;
     std::vector<uint32_t>& kv_h = ctx->m2r_kval_h;
@@ -245,15 +271,28 @@ LfErr lf_prepare_m2r_finish(lfmm_ctx* ctx, cudaStream_t st)
                        : lf_pin<int>(ctx, LFMM_PIN_SCAN + 16);
     LF_CHECK(cudaMemcpyAsync(kstart, ctx->m2r_kstart.ptr, sizeof(int) * nk, cudaMemcpyDeviceToHost, st));
     LF_CHECK(cudaMemcpyAsync(kv, ctx->m2r_kval.ptr, sizeof(uint32_t) * nk, cudaMemcpyDeviceToHost, st));
-    LF_CHECK(cudaMemcpyAsync(hbad, bad, 4, cudaMemcpyDeviceToHost, st));
+    LF_CHECK(cudaMemcpyAsync(hbad, bad, 16 * sizeof(int), cudaMemcpyDeviceToHost, st));
     LF_CHECK(cudaStreamSynchronize(st));
-    if (*hbad) return "internal: reaction M2L pair with a non-integer or too distant offset on an aligned level";
     kstart[nk] = ne;
+    // levels from keyed_from on are keyed: below it, a level with an entry
+    // outside the key range (and every coarser one) stays per pair.  Their
+    // keys (sorted by level first) are a prefix, and the out-of-range ones
+    // (KEY_NONE) the suffix
+    int keyed_from = ctx->m2r_la;
+    for (int l = ctx->m2r_la; l <= ctx->depth && l < 16; ++l)
+        if (hbad[l] > 0) keyed_from = l + 1;
+    ctx->m2r_keyed_from = keyed_from;
+    int64_t k0 = 0, k1 = nk;
+    while (k0 < nk && (int)(kv[k0] >> 19) < keyed_from) ++k0;  // (KEY_NONE >> 19 exceeds every level)
+    while (k1 > k0 && kv[k1 - 1] == KEY_NONE) --k1;
+    const int64_t nku = k1 - k0;
+    ctx->m2r_kfirst = (int)k0;
+    if (nku <= 0) return LfErr();
     // tables, one per distinct (component, level, rho^2, oz)
     std::vector<int4>& tdesc = ctx->m2r_tdesc_h;
     std::vector<int>& ktab = ctx->m2r_ktab_h;
     tdesc.clear();
-    ktab.assign(nk, 0);
+    ktab.assign(nku, 0);
     {
         // keys arrive sorted by (component, level, offset): within one
         // (component, level) run a table is identified by (rho^2, oz), looked
@@ -265,7 +304,7 @@ LfErr lf_prepare_m2r_finish(lfmm_ctx* ctx, cudaStream_t st)
         slot.assign((size_t)NR2 * R_OW, 0);
         stamp.assign((size_t)NR2 * R_OW, 0u);
         uint32_t gen = 0, run = ~0u;
-        for (int64_t k = 0; k < nk; ++k) {
+        for (int64_t k = k0; k < k1; ++k) {
             int c, l, ox, oy, oz;
             rkey_decode(kv[k], c, l, ox, oy, oz);
             if ((kv[k] >> 12) != run) {
@@ -279,16 +318,16 @@ LfErr lf_prepare_m2r_finish(lfmm_ctx* ctx, cudaStream_t st)
                 slot[i] = (int)tdesc.size();
                 tdesc.push_back(make_int4(c, l, r2, oz));
             }
-            ktab[k] = slot[i];
+            ktab[k - k0] = slot[i];
         }
     }
     const int ntab = (int)tdesc.size();
     const int P = ctx->p, TS = 2 * P + 1, TT = TS * TS, Q = ctx->gl_q_m2l;
     LF_TRY(lf_reserve(ctx->m2r_tables, (size_t)ntab * TT * 8 + 16));
     LF_TRY(lf_reserve(ctx->m2r_tdesc, (size_t)ntab * sizeof(int4) + 16));
-    LF_TRY(lf_reserve(ctx->m2r_ktab, (size_t)nk * sizeof(int) + 16));
+    LF_TRY(lf_reserve(ctx->m2r_ktab, (size_t)nku * sizeof(int) + 16));
     LF_CHECK(cudaMemcpyAsync(ctx->m2r_tdesc.ptr, tdesc.data(), ntab * sizeof(int4), cudaMemcpyHostToDevice, st));
-    LF_CHECK(cudaMemcpyAsync(ctx->m2r_ktab.ptr, ktab.data(), nk * sizeof(int), cudaMemcpyHostToDevice, st));
+    LF_CHECK(cudaMemcpyAsync(ctx->m2r_ktab.ptr, ktab.data(), nku * sizeof(int), cudaMemcpyHostToDevice, st));
     double* hl = ctx->m2r_levelh_h;
     for (int l = 0; l < 16; ++l) hl[l] = (l <= ctx->depth) ? ctx->levels[l].h : 0.0;
     LF_TRY(lf_reserve(ctx->m2r_levelh, sizeof(double) * 16));
@@ -299,16 +338,16 @@ LfErr lf_prepare_m2r_finish(lfmm_ctx* ctx, cudaStream_t st)
     // batches of R_TB pairs of one key
     std::vector<int4>& batches = ctx->m2r_batches_h;
     batches.clear();
-    for (int k = 0; k < nk; ++k)
+    for (int64_t k = k0; k < k1; ++k)
         for (int s = kstart[k]; s < kstart[k + 1]; s += R_TB)
-            batches.push_back(make_int4(k, s, std::min(R_TB, kstart[k + 1] - s), 0));
-    ctx->m2r_nkeys = (int)nk;
+            batches.push_back(make_int4((int)(k - k0), s, std::min(R_TB, kstart[k + 1] - s), 0));
+    ctx->m2r_nkeys = (int)nku;
     ctx->m2r_nbatch = (int)batches.size();
     LF_TRY(lf_reserve(ctx->m2r_batches, batches.size() * sizeof(int4) + 16));
     LF_CHECK(cudaMemcpyAsync(ctx->m2r_batches.ptr, batches.data(), batches.size() * sizeof(int4),
                              cudaMemcpyHostToDevice, st));
     // (the host staging vectors live in the context; the build synchronises at its end)
-    ctx->stats[LFMM_STAT_REACTION_KEYS] = nk;
+    ctx->stats[LFMM_STAT_REACTION_KEYS] = nku;
     ctx->stats[LFMM_STAT_REACTION_TABLES] = ntab;
     // the tables and operators themselves are device work of the first
     // evaluation after this build (lf_m2r_device), beside its upward pass
@@ -332,7 +371,8 @@ LfErr lf_m2r_device(lfmm_ctx* ctx, cudaStream_t st)
     auto tabk = (ctx->L >= 3) ? k_m2r_tables<true> : k_m2r_tables<false>;
     LF_CHECK(cudaFuncSetAttribute(tabk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     ++ctx->launches, tabk<<<ntab, 128, sm, st>>>(ctx->comp_dev.as<LfmmComp>(), ctx->m2r_tdesc.as<int4>(), ntab,
-                                                 ctx->m2r_levelh.as<double>(), P, ctx->gl_t_m2l.as<double>(),
+                                                 ctx->m2r_levelh.as<double>(), ctx->m2r_zfrac.as<double>(), P,
+                                                 ctx->gl_t_m2l.as<double>(),
                                                  ctx->gl_w_m2l.as<double>(), Q, ctx->m2r_tables.as<double>());
     LF_TRY(lf_cuda(cudaGetLastError(), "m2r tables"));
     LF_TRY(lf_m2r_ops(ctx, st));
@@ -686,7 +726,7 @@ static LfErr m2r_build_ops(lfmm_ctx* ctx, cudaStream_t st)
     ROpArgs g;
     g.p = ctx->p;
     g.nc = lf_nc(ctx->p);
-    g.kval = ctx->m2r_kval.as<uint32_t>();
+    g.kval = ctx->m2r_kval.as<uint32_t>() + ctx->m2r_kfirst;
     g.tables = ctx->m2r_tables.as<double>();
     g.ktab = ctx->m2r_ktab.as<int>();
     g.comps = ctx->comp_dev.as<LfmmComp>();
@@ -708,7 +748,7 @@ static LfErr m2r_apply_rp(lfmm_ctx* ctx, cudaStream_t st)
     g.p = ctx->p;
     g.nc = lf_nc(ctx->p);
     g.batches = ctx->m2r_batches.as<int4>();
-    g.kval = ctx->m2r_kval.as<uint32_t>();
+    g.kval = ctx->m2r_kval.as<uint32_t>() + ctx->m2r_kfirst;
     g.ops = ctx->m2r_ops.ptr;
     g.order = ctx->m2r_order.as<uint32_t>();
     g.ent = ctx->m2r_ent.as<uint32_t>();
@@ -732,7 +772,7 @@ static LfErr m2r_apply_kc(lfmm_ctx* ctx, cudaStream_t st)
     g.p = ctx->p;
     g.nc = lf_nc(ctx->p);
     g.batches = ctx->m2r_batches.as<int4>();
-    g.kval = ctx->m2r_kval.as<uint32_t>();
+    g.kval = ctx->m2r_kval.as<uint32_t>() + ctx->m2r_kfirst;
     g.ops = ctx->m2r_ops.ptr;
     g.order = ctx->m2r_order.as<uint32_t>();
     g.ent = ctx->m2r_ent.as<uint32_t>();
