@@ -80,6 +80,9 @@ def test_fmm_matches_oracle(aligned, precision, tol):
         st = f.stats()
         phi, E = f.evaluate(w.q)
     assert st["m2l_reaction"] > 0 and st["p2p_reaction"] > 0
+    # the reaction M2L is keyed on aligned and unaligned grids alike (the
+    # image's vertical offset: an integer key part and a per-level fraction)
+    assert st["reaction_keys"] > 0
     t = workloads.subsample(w.n, 96)
     ref, refE = oracle.direct(w.d, w.eps, w.xyz, w.layer, w.q, targets=t, mode=oracle.MODE_QUAD)
     e_phi, e_fld = oracle.err2(ref, phi[t]), oracle.err2(refE, E[t])
