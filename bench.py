@@ -499,10 +499,10 @@ def sweep(torch, dev, flush, sizes=(1 << 16, 1 << 18, 1 << 20), orders=(6, 10, 1
         phi_d = torch.empty(w.n, dtype=torch.float64, device=dev)
         fld_d = torch.empty((w.n, 3), dtype=torch.float64, device=dev)
         for p in orders:
-            # float32 with the free M2L on the tensor cores (the default), FP64,
-            # and for the wide tensor-core form ((p+1)^2 > 128) also float32
-            # with the free M2L on the CUDA cores
-            forms = [(1, 1), (0, 0)] + ([(1, 0)] if (p + 1) ** 2 > 128 else [])
+            # float32 and FP64 with the automatic free M2L engine (tensor cores
+            # where (p+1)^2 <= 128), and for wider expansions also float32 with
+            # the wide tensor-core form asked for
+            forms = [(1, 2), (0, 2)] + ([(1, 1)] if (p + 1) ** 2 > 128 else [])
             for prec, tc in forms:
                 with LayeredFMM(w.d, w.eps, p, precision=prec) as f:
                     f.set_option(OPT_TENSOR_CORES, tc)
@@ -511,7 +511,7 @@ def sweep(torch, dev, flush, sizes=(1 << 16, 1 << 18, 1 << 20), orders=(6, 10, 1
                     st = f.stats()
                 ms = sum(times) / len(times)
                 phi, E = phi_d.cpu().numpy(), fld_d.cpu().numpy()
-                form = ("fp32" if tc else "fp32 (CUDA-core M2L)") if prec else "fp64"
+                form = ("fp32" if tc == 2 else "fp32 (wide tensor-core M2L)") if prec else "fp64"
                 print(json.dumps({"sweep": "config2", "n": n, "p": p, "form": form,
                                   "ms_per_step": ms, "particles_per_s": n / (ms / 1e3), "build_ms": stages["build"],
                                   "evaluate_ms": stages["total"], "m2l_free_ms": stages["m2l_free"],

@@ -57,11 +57,12 @@ enum {
     LFMM_OPT_QUAD_NODES = 4, /* Gauss-Laguerre nodes of the M2L remainder integrals (16..128, default 64) */
     LFMM_OPT_SURROGATE = 5,  /* 1 = near-field reaction kernels by the trained network (default 0) */
     LFMM_OPT_SURROGATE_TOL = 6, /* error estimate above which a pair falls back to quadrature (default 1e-6) */
-    LFMM_OPT_TENSOR_CORES = 7,  /* 1 = float32 free M2L on the tensor cores (3xTF32) (default); 0 = on
-                                   the CUDA cores.  For 128 < (p+1)^2 (11 <= p <= 14) the tensor cores run
-                                   the wide form: Err2 of the potential ~8e-7 at p = 14 against ~4e-7 for
-                                   the compensated CUDA-core sums, in a sixth of the time.  Where
-                                   (p+1)^2 <= 128 they also take the L2L into the leaves. */
+    LFMM_OPT_TENSOR_CORES = 7,  /* float32 free M2L engine: 2 = automatic (default): tensor cores (3xTF32)
+                                   where (p+1)^2 <= 128, the compensated CUDA-core sums above; 1 = tensor
+                                   cores at every order (for 11 <= p <= 14 the wide form: Err2 of the
+                                   potential ~8e-7 at p = 14 against ~4e-7 on the CUDA cores, in a sixth
+                                   of the time); 0 = CUDA cores.  Where (p+1)^2 <= 128 the tensor cores
+                                   also take the L2L into the leaves. */
     LFMM_OPT_P2P_SPLIT = 8,     /* near list of a leaf shared by this many warps/blocks of the P2P kernels:
                                    0 = chosen from the leaf count (default), else 1, 2, 4, 8 or 16 */
     LFMM_OPT_TC_GROUPS = 9,     /* tensor-core free M2L: CTAs per tile of targets (256, or 128 in the wide
@@ -164,7 +165,8 @@ void lfmm_destroy(lfmm_ctx* ctx);
  * (CUDA events on the context's stream); the paper tunes nothing at run time,
  * this is a library facility.  Coordinate search, in this order:
  *   1. leaf capacity (tree depth) in {10, 20, 40, 80, 160};
- *   2. float32 form with (p+1)^2 <= 128: free M2L on tensor cores or CUDA cores;
+ *   2. float32 form: free M2L on the other engine (CUDA cores where the
+ *      tensor cores run, tensor cores at any order where not);
  *   3. near-list split of the P2P kernels in {automatic, 1, 2, 4, 8, 16}.
  * Each setting is timed as the median of `reps` (>= 1) evaluations of one
  * charge vector (mode 0) or builds plus evaluations (mode 1), after one

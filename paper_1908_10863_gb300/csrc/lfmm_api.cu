@@ -764,7 +764,8 @@ static lfmm_status set_option(lfmm_ctx* ctx, int opt, double v)
         ctx->use_surr = (v != 0.0);
         return LFMM_OK;
     case LFMM_OPT_TENSOR_CORES:
-        ctx->use_tc = (v != 0.0);
+        if (v != 0.0 && v != 1.0 && v != 2.0) return fail(ctx, "EINVAL: tensor-core option must be 0, 1 or 2");
+        ctx->use_tc = (int)v;
         return LFMM_OK;
     case LFMM_OPT_SERIAL_NEAR:
         if (v != 0.0 && v != 1.0) return fail(ctx, "EINVAL: serial near-field option must be 0 or 1");

@@ -138,7 +138,8 @@ struct lfmm_ctx {
     int near_tab_ready = 0, use_near_tab = 0;
     double near_tab_err = -1.0;  // largest relative deviation from the quadrature at the check points
     double m2l_levelh_h[16] = {0};
-    int m2l_tc_ok = 0, m2l_tc_ntiles = 0, use_tc = 1, tc_groups = 0;  // tc_groups 0: automatic
+    // use_tc: 2 automatic (tensor cores where (p+1)^2 <= 128), 1 at every order, 0 never
+    int m2l_tc_ok = 0, m2l_tc_ntiles = 0, use_tc = 2, tc_groups = 0;  // tc_groups 0: automatic
     int m2l_tc_wide = 0;  // tensor-core free M2L in its wide form ((p+1)^2 > 128): no tensor-core M2M / L2L
     // reaction M2L grouped by geometry key on interface-aligned levels
     DevBuf m2r_keys, m2r_order, m2r_tgt, m2r_kstart, m2r_kval, m2r_tables, m2r_levelh, m2r_batches;
@@ -220,6 +221,13 @@ inline cudaError_t lf_d2h(void* dst, const void* src, size_t bytes, cudaStream_t
 // ---- tree construction (lfmm_tree.cu) ----
 LfErr lf_build_tree(lfmm_ctx* ctx, const double* xyz_dev, const int32_t* layer_dev, int64_t n, cudaStream_t st);
 LfErr lf_p2p_pair_stats(lfmm_ctx* ctx);
+// whether the float32 free M2L runs on the tensor cores: the automatic setting
+// keeps the compensated CUDA-core sums for the wide form ((p+1)^2 > 128),
+// where they are the more accurate choice
+inline bool lf_tc_on(const lfmm_ctx* ctx)
+{
+    return ctx->m2l_tc_ok && (ctx->use_tc == 1 || (ctx->use_tc == 2 && !ctx->m2l_tc_wide));
+}
 
 // ---- free-space M2L GEMM (lfmm_m2l.cu) ----
 LfErr lf_setup_m2l_ops(lfmm_ctx* ctx);

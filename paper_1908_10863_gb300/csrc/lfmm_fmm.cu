@@ -584,7 +584,7 @@ static LfErr far_field(lfmm_ctx* ctx, cudaStream_t st)
     const bool gemm = ctx->m2l_ntiles > 0;
     if (gemm) {
         ph = lf_prof_start(ctx, LFMM_TIME_M2L_FREE, st);
-        if (sizeof(R) == 4 && ctx->use_tc && ctx->m2l_tc_ok && ctx->m2l_tc_ntiles > 0)
+        if (sizeof(R) == 4 && lf_tc_on(ctx) && ctx->m2l_tc_ntiles > 0)
             LF_TRY(lf_m2l_tc(ctx, st));
         else
             LF_TRY(lf_m2l_gemm(ctx, st));

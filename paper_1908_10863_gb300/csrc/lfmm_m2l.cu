@@ -677,7 +677,7 @@ static LfErr shift_gemm_t(lfmm_ctx* ctx, int level, bool l2l, cudaStream_t st)
     // other translations stay on the CUDA cores: at N = 1M, p = 10 the
     // tensor-core M2M saved 0.05 ms, and chaining 3xTF32 L2L over every level
     // raised Err2(phi) from 2.0e-6 to 3.2e-6.
-    if (sizeof(R) == 4 && l2l && level == ctx->depth && ctx->use_tc && ctx->m2l_tc_ok && !ctx->m2l_tc_wide)
+    if (sizeof(R) == 4 && l2l && level == ctx->depth && lf_tc_on(ctx) && !ctx->m2l_tc_wide)
         return lf_shift_tc(ctx, level, l2l, st);
     GemmArgs g;
     g.p = ctx->p;

@@ -161,7 +161,11 @@ extern "C" lfmm_status lfmm_autotune(lfmm_ctx* ctx, int64_t n, const double* xyz
     // 2. free M2L engine
     if (st == LFMM_OK && ctx->precision == 1 && ctx->m2l_tc_ok) {
         Setting s = best;
-        s.tc = !best.tc;
+        // the other engine: off where the tensor cores run, on (at any order) where not
+        const int saved = ctx->use_tc;
+        ctx->use_tc = best.tc;
+        s.tc = lf_tc_on(ctx) ? 0 : 1;
+        ctx->use_tc = saved;
         st = consider(s);
     }
     // 3. near-list split (the automatic rule included)

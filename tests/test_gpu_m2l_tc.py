@@ -89,6 +89,7 @@ def test_wide_tensor_core_m2l_several_right_hand_sides():
     rng = np.random.default_rng(5)
     Q = np.stack([w.q, rng.standard_normal(w.n)])
     with LayeredFMM(w.d, w.eps, 13, precision=1) as f:
+        f.set_option(OPT_TENSOR_CORES, 1)  # the wide form is on request
         f.build(w.xyz, w.layer)
         phi2, _ = f.evaluate(Q)
         one = [f.evaluate(Q[i])[0] for i in range(2)]
@@ -113,6 +114,10 @@ def test_offset_groups_option():
         for bad in (-1, 2, 10, 190):
             with pytest.raises(LfmmError) as ei:
                 f.set_option(OPT_TC_GROUPS, bad)
+            assert ei.value.status == EINVAL
+        for bad in (-1, 3, 0.5):  # the engine: 0, 1 or 2
+            with pytest.raises(LfmmError) as ei:
+                f.set_option(OPT_TENSOR_CORES, bad)
             assert ei.value.status == EINVAL
     e = oracle.err2(ref, phi)
     print("groups 9 vs 27: Err2 %.2e" % e)
