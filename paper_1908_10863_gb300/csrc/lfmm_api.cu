@@ -503,6 +503,21 @@ static LfErr setup_components(lfmm_ctx* ctx)
                             }
                         }
                         for (int k = 0; k < 3; ++k) c.den[k] = den[k];
+                        // the remainder's series in x: rem(x)/den(x) = sum a_n x^n, by
+                        // exact division (den[0] = 1)
+                        {
+                            double t[5];
+                            for (int k = 0; k < 5; ++k) t[k] = c.has_rem ? c.rem[k] : 0.0;
+                            for (int n = 0; n < LFMM_IMG_N; ++n) {
+                                const double a = t[0];
+                                c.img[n] = a;
+                                t[0] = t[1] - a * den[1];
+                                t[1] = t[2] - a * den[2];
+                                t[2] = t[3];
+                                t[3] = t[4];
+                                t[4] = 0.0;
+                            }
+                        }
                         // a real zero of den(x) close to x = 1 (k slightly negative) makes the
                         // remainder nearly singular at k = 0: use the composite rule
                         for (int k = 0; k <= 300; ++k) {

@@ -76,6 +76,11 @@ struct LfmmSurrView {  // what the near-field kernel needs
 
 // One FMM component: free space (a = b = 0) or a reaction component
 // (l, lp, a, b).  Plain data, copied to constant memory.
+// terms of the remainder's image series a near-field pair may take (far pairs)
+#define LFMM_IMG_N 32
+// a pair takes images when rho exceeds this many times its remainder depth
+#define LFMM_IMG_RATIO 4
+
 struct LfmmComp {
     int l, lp, a, b;
     int is_free;
@@ -89,6 +94,7 @@ struct LfmmComp {
     double zeta_r;   // remainder ~ exp(-k zeta_r)
     double rem[5];   // remainder numerator / x^{zeta_r / D}
     double den[3];   // den[0] = 1
+    double img[LFMM_IMG_N];  // series of rem(x) / den(x) in powers of x (the remainder's images)
     // more than two interfaces: sigma(k) has no single x; it is evaluated by
     // solving the interface problem of the medium at each k
     int nif;                         // interfaces of the medium
@@ -624,15 +630,44 @@ __device__ __forceinline__ void lf_reaction_pair(const LfmmComp& c, R rho, R h, 
         }
     }
     R Z = h + (R)c.zeta_r;
-    R iZ = R(1) / Z;
     R D = (R)c.D;
+    // Far pairs (rho > LFMM_IMG_RATIO Z) of a rational remainder rem(x)/den(x),
+    // x = e^{-k D}: its series sum a_n x^n splits off M + 1 terms, each an
+    // image at depth Z + n D integrated in closed form, and leaves
+    // x^{M+1} t(x)/den(x) (t by exact division, t <- (t - a_n den)/x), whose
+    // quadrature sees the depth Z + (M + 1) D: the Gauss-Laguerre rule in k Z
+    // cannot follow J0(k rho) once rho is many times Z.
+    R t[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) t[i] = (R)c.rem[i];
+    if ((!GEN || c.nif <= 2) && D > R(0) && rho > (R)LFMM_IMG_RATIO * Z) {
+        int M = (int)ceil((double)((rho * (R)(1.0 / LFMM_IMG_RATIO) - Z) / D)) - 1;
+        M = M < 0 ? 0 : (M > LFMM_IMG_N - 1 ? LFMM_IMG_N - 1 : M);
+        for (int n = 0; n <= M; ++n) {
+            const R a = (R)c.img[n];
+            const R Hn = Z + (R)n * D;
+            const R rr = F::Rsqrt(rho * rho + Hn * Hn);
+            const R rr3 = rr * rr * rr;
+            k00 += a * rr;
+            k10 += a * Hn * rr3;
+            k11 += a * rho * rr3;
+            // t <- (t - a den) / x (t[0] - a den[0] = 0 by the choice of a)
+            t[0] = t[1] - a * (R)c.den[1];
+            t[1] = t[2] - a * (R)c.den[2];
+            t[2] = t[3];
+            t[3] = t[4];
+            t[4] = R(0);
+        }
+        Z += (R)(M + 1) * D;
+    }
+    R iZ = R(1) / Z;
     for (int q = 0; q < Q; ++q) {
         R kap = (R)gl_t[q] * iZ;
         R w;
         if (!GEN || c.nif <= 2) {
             R x = F::Exp(-D * kap);
-            R num = (R)c.rem[4];
-            for (int i = 3; i >= 0; --i) num = num * x + (R)c.rem[i];
+            R num = t[4];
+            for (int i = 3; i >= 0; --i) num = num * x + t[i];
             R den = ((R)c.den[2] * x + (R)c.den[1]) * x + (R)c.den[0];
             R rt = num / den;
             w = (R)gl_w[q] * iZ * rt;

@@ -206,6 +206,27 @@ def four_layers_near_interface(n: int = 3000, delta: float = 0.02, hmin: float =
                     layer, q)
 
 
+def slab(n: int = 4000, half_width: float = 50.0, seed: int | None = None, eps=EPS_CONFIG,
+         margin: float = 0.01) -> Workload:
+    """A flat, wide layout (interconnect-like): x over [-half_width, half_width],
+    y over [-0.1, 0.1], z over [-2.5, 1.0] across the three layers of config 2,
+    every charge at least `margin` from an interface.  Most reaction pairs are
+    then laterally far (rho up to 2 half_width) and shallow, so they stay in
+    the near field."""
+    rng = np.random.Generator(np.random.PCG64(SEED_BASE + 11 if seed is None else seed))
+    d0, d1 = D_CONFIG
+    x = rng.uniform(-half_width, half_width, n)
+    y = rng.uniform(-0.1, 0.1, n)
+    z = rng.uniform(-2.5, 1.0, n)
+    for di in (d0, d1):  # keep the margin: push charges off the interfaces
+        close = np.abs(z - di) < margin
+        z[close] = di + np.where(z[close] >= di, margin, -margin)
+    layer = np.where(z > d0, 0, np.where(z > d1, 1, 2)).astype(np.int32)
+    q = rng.uniform(-1.0, 1.0, size=n)
+    return Workload("slab_n%d_w%g" % (n, half_width), np.array(D_CONFIG), np.array(eps, dtype=np.float64),
+                    np.column_stack([x, y, z]), layer, q)
+
+
 def subsample(n: int, count: int, seed: int = SEED_BASE + 3) -> np.ndarray:
     """The first ``count`` indices of a seeded permutation of range(n)."""
     rng = np.random.Generator(np.random.PCG64(seed))

@@ -299,3 +299,23 @@ def test_keyed_reaction_m2l_high_order_against_oracle(p, tol):
     e = oracle.err2(ref, phi[t])
     print("config2 20k p=%d FP64 keyed reaction M2L: Err2 phi %.2e field %.2e" % (p, e, oracle.err2(refE, E[t])))
     assert e < tol
+
+
+@pytest.mark.parametrize("half_width", [10.0, 50.0])
+@pytest.mark.parametrize("precision,tol_phi,tol_fld", [(0, 2e-5, 5e-6), (1, 5e-5, 1e-4)])
+def test_flat_wide_layout_against_oracle(half_width, precision, tol_phi, tol_fld):
+    # Reaction pairs up to 100 apart laterally but shallow (rho >> depth) stay
+    # in the near field; their remainder splits into images and a quadrature
+    # at a deeper depth.  With the Gauss-Laguerre rule alone the potential was
+    # off by Err2 2e-4 (half width 10) and 9e-3 (half width 50).
+    w = workloads.slab(4000, half_width)
+    with LayeredFMM(w.d, w.eps, 10, precision=precision) as f:
+        f.build(w.xyz, w.layer)
+        phi, E = f.evaluate(w.q)
+        st = f.stats()
+    assert st["p2p_reaction"] > 0 and st["timeouts"] == 0
+    ref, refE = oracle.direct(w.d, w.eps, w.xyz, w.layer, w.q, mode=oracle.MODE_IMAGES)
+    e, ef = oracle.err2(ref, phi), oracle.err2(refE, E)
+    print("slab half width %g precision %d: Err2 phi %.2e field %.2e (p2p_reaction %d)"
+          % (half_width, precision, e, ef, st["p2p_reaction"]))
+    assert e < tol_phi and ef < tol_fld
