@@ -738,6 +738,28 @@ def main():
                                  "SM clock sampled in the timed region; algorithmic flops = 20 per near pair "
                                  "(potential and field); duration = CUDA events around the near field run alone "
                                  "(not beside the far field), after the timed steps"}
+    # the other stages: counted work (the library's statistics) over their
+    # CUDA-event times inside the timed steps, against the float32 CUDA-core
+    # peak (the near field runs beside them, so these are lower bounds)
+    sm_mhz = (clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0)
+    pk32 = fp32_peak_tflops(sm_mhz)
+    sms = forms_out[headline]["stage_ms"]
+    nc, nre = (args.p + 1) ** 2, (args.p + 1) * (args.p + 2) // 2
+    edge = 8 * nc * nre  # flops per parent-child edge (dense complex shift) and per M2L pair
+    work = [("p2m", "k_p2m", st["n"], 20 * nc, "charge"),
+            ("m2m", "k_m2l_gemm (M2M)", st["m2m_edges"], edge, "parent-child edge"),
+            ("m2l_reaction", "k_m2r_gemm (keyed reaction M2L)", st["m2l_reaction"], edge, "reaction box pair"),
+            ("l2l", "k_m2l_gemm / k_m2l_tc (L2L)", st["m2m_edges"], edge, "parent-child edge"),
+            ("l2p", "k_l2p", st["n"], 20 * nc, "charge")]
+    stage_roofs = []
+    for stage, kern, units, fpu, unit in work:
+        ms_s = sms.get(stage)
+        if not ms_s or not units:
+            continue
+        ach = units * fpu / (ms_s / 1e3) / 1e12
+        stage_roofs.append({"stage": stage, "kernel": kern, "units": int(units), "unit": unit,
+                            "flops_per_unit": fpu, "ms": ms_s, "achieved_tflops": ach, "peak_tflops": pk32,
+                            "frac": ach / pk32})
     line = {
         "metric": METRIC,
         "value": value,
@@ -760,6 +782,7 @@ def main():
         "forms": forms_out,
         "roofline": roof,
         "roofline_near_field": roof_p2p,
+        "roofline_stages": stage_roofs,
         "cpu_baseline": {"value": len(t) / dt, "unit": "particles/s", "cores": threads, "kind": "oracle",
                          "sample": "%d targets (seeded subsample) x all %d sources, exact three-layer image "
                                    "series, %.1f s" % (len(t), w.n, dt)},
