@@ -50,6 +50,7 @@
 #include <vector>
 
 #include "lfmm_ctx.h"
+#include "lfmm_tc.cuh"
 
 #define LF_CHECK(call)                                    \
     do {                                                  \
@@ -64,11 +65,7 @@
 
 #define TC_N 256                     // targets per tile (MMA N)
 #define TC_M 128                     // output coefficients (MMA M)
-#ifndef TC_KC
-#define TC_KC 16                     // K elements per stage (64-byte rows)
-#endif
 #define TC_NKC (128 / TC_KC)         // K chunks (K = 128)
-#define TC_ROWB (TC_KC * 4)          // bytes per row of a stage tile
 #define TC_RCH (TC_ROWB / 16)        // 16-byte chunks per row
 #define TC_NOFF 189                  // offsets per octant class
 #define TC_NALL 343
@@ -97,131 +94,6 @@
 #define TC_TMEM_COLS 256
 #define TC_WIDE_STAGES 4             // wide form: one CTA per SM
 #define TC_WIDE_SMEM (TC_WIDE_STAGES * TC_STAGE_BYTES + 1024)
-#define TC_SPIN_CYCLES (1ll << 31)   // ~1 s at 2 GHz
-
-// ---------------------------------------------------------------------------
-// PTX helpers
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
-{
-    asm volatile(
-        "{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
-        : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t bytes)
-{
-    asm volatile(
-        "{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
-        "r"(bytes)
-        : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// bounded wait: false after `limit` cycles
-__device__ __forceinline__ bool mbar_wait_for(uint64_t* bar, uint32_t parity, long long limit)
-{
-    if (mbar_try(bar, parity)) return true;
-    const long long t0 = clock64();
-    while (!mbar_try(bar, parity))
-        if (clock64() - t0 > limit) return false;
-    return true;
-}
-// the pipeline's waits: false after ~1 s
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) { return mbar_wait_for(bar, parity, TC_SPIN_CYCLES); }
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ uint32_t to_tf32(float x)
-{
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups 512 B apart
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
-    d |= (uint64_t)1 << 16;                   // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)((8 * TC_ROWB) >> 4) << 32;  // stride byte offset: 8 rows
-    d |= (uint64_t)1 << 46;                   // descriptor version
-    d |= (uint64_t)(TC_ROWB == 64 ? 4 : 6) << 61;  // 64-byte or 32-byte swizzle
-    return d;
-}
-// instruction descriptor: D float32, A and B TF32, both K-major, M x N
-__host__ __device__ constexpr uint32_t tc_idesc(int M, int N)
-{
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc)
-{
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
-        : "memory");
-}
-__device__ __forceinline__ void tc_commit(uint64_t* bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-__device__ __forceinline__ void tc_ld32(uint32_t taddr, float v[32])
-{
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
-        "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// byte offset of element (row, k) of a swizzled K-major tile with TC_ROWB-byte
-// rows: the 16-byte chunk index is XORed with the address bits just above the
-// swizzle span -- 64-byte swizzle: chunk (bits 4-5) ^ bits 7-8 = (row / 2) mod 4;
-// 32-byte swizzle: chunk (bit 4) ^ bit 7 = (row / 4) mod 2
-__host__ __device__ __forceinline__ uint32_t swz(int row, int k)
-{
-    const uint32_t c = (uint32_t)(k >> 2);
-    const uint32_t x = (TC_ROWB == 64) ? (uint32_t)((row >> 1) & 3) : (uint32_t)((row >> 2) & 1);
-    return (uint32_t)row * TC_ROWB + ((c ^ x) << 4) + (uint32_t)(k & 3) * 4u;
-}
 
 struct TcArgs {
     const int4* tiles;      // level, class, start, count

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "lfmm_ctx.h"
+#include "lfmm_tc.cuh"
 
 #define LF_CHECK(call)                                    \
     do {                                                  \
@@ -718,6 +719,292 @@ __global__ void __launch_bounds__(R_T) k_m2r_gemm_kc(RGemmArgs g)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core form (float32, (p+1)^2 <= 128): one CTA per batch of up to
+// R_TB pairs of one key.  The key's operator is never stored: the CTA forms
+// it in shared memory from the key's Sommerfeld table and the lateral phases
+// (the same entries as k_m2r_ops), directly as two TF32 pieces a1 + a2 in the
+// 64-byte-swizzled K-major layout of the MMA's A operand (M = 128 output
+// coefficients, K = the input coefficients in chunks of 16).  The batch's
+// source multipoles (B operand: N = the batch rounded up to 16 columns) are
+// loaded into registers up front and split the same way.  K runs in rounds
+// of RT_KQ chunks through two 48 KB buffers: while the tensor cores take one
+// round (3xTF32: a1 x1 + a1 x2 + a2 x1, issued by one thread into one
+// accumulator of 64 tensor-memory columns), the threads form the next.  With
+// 97 KB of shared memory the kernel shares its SMs with the near field that
+// runs beside it.  The eight warps then read the accumulator back (warp w:
+// lanes 32 (w mod 4) .., columns 32 (w / 4) ..), scale it by 1/h and add it
+// into the targets' local expansions.  Several right-hand sides repeat the
+// rounds per vector.  Every wait is bounded: on a timeout the CTA counts it
+// in err and skips its read-backs.
+// ---------------------------------------------------------------------------
+#define RT_THREADS 256
+#define RT_TS 21                        // table side 2p + 1 for p <= 10
+#define RT_WS 41                        // 4p + 1: orders -2p .. 2p
+#define RT_KQ 2                         // K chunks per round
+#define RT_A_CHUNK (128 * TC_ROWB)      // one K chunk of one operator piece: 128 rows x 64 B
+#define RT_X_CHUNK (R_TB * TC_ROWB)     // one K chunk of one multipole piece: 64 rows x 64 B
+#define RT_A_ROUND (RT_KQ * RT_A_CHUNK)
+#define RT_X_ROUND (RT_KQ * RT_X_CHUNK)
+#define RT_BUF (2 * RT_A_ROUND + 2 * RT_X_ROUND)  // a1, a2, x1, x2 of one round
+#define RT_SMEM (2 * RT_BUF + 512)
+#define RT_TMEM_COLS 64
+
+struct RTcArgs {
+    int p, nc, nkc;         // order, coefficients, K chunks of 16 that hold them
+    const int4* batches;    // key, first sorted entry, count
+    const uint32_t* kval;
+    const double* tables;   // [table][TS][TS]
+    const int* ktab;        // table of each key
+    const LfmmComp* comps;
+    const float* phase;     // [225 lateral offsets][cos | sin][RT_TS] (k_m2r_phase)
+    const uint32_t* order;  // sorted entry indices
+    const uint32_t* ent;    // m2r entries (component | source box)
+    const int* tgt;         // target box per entry
+    const double* levelh;
+    const float* M;
+    float* L;
+    size_t stride;          // expansions per right-hand side, in floats
+    int nr;
+    int* err;               // [0]: timeouts
+};
+
+// e^{i m phi} of every lateral key offset (ox, oy) in [-7, 7]^2, m <= 2p:
+// FP64 sincos rounded to float32, [offset][cos | sin][RT_TS]
+__global__ void k_m2r_phase(int p, float* out)
+{
+    const int b = blockIdx.x, m = threadIdx.x;
+    if (m > 2 * p) return;
+    const int ox = b / R_OW - R_OR, oy = b % R_OW - R_OR;
+    const double phi = (ox == 0 && oy == 0) ? 0.0 : atan2((double)oy, (double)ox);
+    double sn, cs;
+    sincos(m * phi, &sn, &cs);
+    out[(size_t)b * 2 * RT_TS + m] = (float)cs;
+    out[(size_t)b * 2 * RT_TS + RT_TS + m] = (float)sn;
+}
+
+__global__ void __launch_bounds__(RT_THREADS, 2) k_m2r_tc(RTcArgs g)
+{
+    extern __shared__ unsigned char smem_raw[];
+    // 512-byte alignment: the period of the 64-byte swizzle
+    unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 511) &
+                                                         ~(uintptr_t)511);
+    // W(N, mu) = T(N, |mu|) e^{i mu phi} for mu in [-2p, 2p], extended to
+    // negative orders by W(N, -mu) = (-1)^mu conj W(N, mu); real parts, then
+    // imaginary parts, each [N][mu + 2p] with rows of 4p + 1
+    __shared__ float sW[2 * RT_TS * RT_WS];
+    __shared__ float sPh[2 * RT_TS];
+    __shared__ int2 s_off[2][128];   // per output parity aim and input: offsets of the two W terms
+    __shared__ float2 s_cf[2][128];  // their signs (0: no second term, or no such input)
+    __shared__ int s_roff[128];      // per output coefficient (k, l): k (4p + 1) + l + 2p
+    __shared__ float s_sk[128];      // (-1)^k, 0 past the last coefficient
+    __shared__ unsigned char s_aim[128];
+    __shared__ int s_src[R_TB], s_tgt[R_TB];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort;
+    __shared__ float s_ih;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int p = g.p, nc = g.nc, nkc = g.nkc, TS = 2 * p + 1, WS = 4 * p + 1, TSZ = TS * WS;
+    const int4 b = g.batches[blockIdx.x];
+    const int kidx = b.x, start = b.y, cnt = b.z;
+    if (cnt <= 0 || cnt > R_TB) return;
+    const int N = (cnt + 15) & ~15;  // MMA columns
+    const int nq = (nkc + RT_KQ - 1) / RT_KQ;
+    int c, lev, ox, oy, oz;
+    rkey_decode(g.kval[kidx], c, lev, ox, oy, oz);
+    const bool refl = g.comps[c].refl != 0;
+
+    if (tid < 128) {
+        // output coefficient tid as a row, input coefficient tid as a column
+        int n = 0, m = 0, im = 0;
+        const bool in = tid < nc;
+        if (in) lf_decode(p, tid, n, m, im);
+        s_roff[tid] = in ? n * WS + m + 2 * p : 0;
+        s_sk[tid] = in ? ((n & 1) ? -1.f : 1.f) : 0.f;
+        s_aim[tid] = (unsigned char)im;
+        // the multipole's reflection sign (-1)^{n+m} for s = -1 maps
+        const float rs = (refl && ((n + m) & 1)) ? -1.f : 1.f;
+        const float sg = (m & 1) ? -1.f : 1.f;  // (-1)^m of the second term
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const int t = (a ^ im) * TSZ;  // real parts where the parities agree, else imaginary
+            s_off[a][tid] = in ? make_int2(t + n * WS + m, t + n * WS - m) : make_int2(0, 0);
+            // (re,re): W1 + sg W2; (re out, im in): -W1 + sg W2; (im, re): W1 + sg W2; (im, im): W1 - sg W2
+            const float c1 = (a == 0 && im == 1) ? -1.f : 1.f;
+            const float c2 = m > 0 ? ((a == 1 && im == 1) ? -sg : sg) : 0.f;
+            s_cf[a][tid] = in ? make_float2(rs * c1, rs * c2) : make_float2(0.f, 0.f);
+        }
+    }
+    if (tid < R_TB) {
+        if (tid < cnt) {
+            const uint32_t e = g.order[start + tid];
+            s_src[tid] = (int)(g.ent[e] & LFMM_ENT_MASK);
+            s_tgt[tid] = g.tgt[e];
+        } else {
+            s_src[tid] = -1;
+            s_tgt[tid] = -1;
+        }
+    }
+    if (tid >= 128 && tid < 128 + 2 * RT_TS)
+        sPh[tid - 128] = g.phase[(size_t)((ox + R_OR) * R_OW + (oy + R_OR)) * 2 * RT_TS + (tid - 128)];
+    if (tid == 192) s_ih = (float)(1.0 / g.levelh[lev]);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(RT_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    {
+        const double* Tk = g.tables + (size_t)g.ktab[kidx] * TS * TS;
+        for (int j = tid; j < TSZ; j += RT_THREADS) {
+            const int Nn = j / WS, mu = j - Nn * WS - 2 * p, a = mu < 0 ? -mu : mu;
+            const float t = (float)Tk[Nn * TS + a];
+            float wr = t * sPh[a], wi = t * sPh[RT_TS + a];
+            if (mu < 0) {
+                if (a & 1) wr = -wr; else wi = -wi;
+            }
+            sW[j] = wr;
+            sW[TSZ + j] = wi;
+        }
+    }
+    const float ih = s_ih;
+    // gather unit of every K chunk: column xj (rows >= N are not read), 16-byte
+    // quarter xq; a warp covers 8 columns = 512 contiguous bytes of a chunk.
+    // Operator units: rows xj and xj + 64, quarter xq.
+    const int xj = tid >> 2, xq = tid & 3;
+    const uint32_t idesc = tc_idesc(128, N);
+    bool ok = true;
+    for (int r = 0; r < g.nr && ok; ++r) {
+        float xv[8][4];
+        {
+            const float* M = g.M + (size_t)r * g.stride;
+            const int s = (xj < N) ? s_src[xj] : -1;
+#pragma unroll
+            for (int kc = 0; kc < 8; ++kc)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int k = kc * 16 + 4 * xq + e;
+                    xv[kc][e] = (kc < nkc && s >= 0 && k < nc) ? M[(size_t)s * nc + k] : 0.f;
+                }
+        }
+        if (r == 0) __syncthreads();  // W is in shared memory
+#pragma unroll
+        for (int i = 0; i < 8 / RT_KQ; ++i) {
+            if (i >= nq) break;
+            const int gr = r * nq + i, buf = gr & 1;  // round counter over the vectors
+            if (gr >= 2 && !mbar_wait(&bar[buf], (uint32_t)(((gr - 2) >> 1) & 1))) s_abort = 1;
+            unsigned char* sb = sm + (size_t)buf * RT_BUF;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int row = xj + 64 * h;
+                const float* W = sW + s_roff[row];
+                const float sk = s_sk[row];
+                const int a = s_aim[row];
+#pragma unroll
+                for (int kl = 0; kl < RT_KQ; ++kl) {
+                    const int kc = i * RT_KQ + kl;
+                    if (kc >= nkc) break;
+                    float hi[4], lo[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int kin = kc * 16 + 4 * xq + e;
+                        const int2 o = s_off[a][kin];
+                        const float2 cf = s_cf[a][kin];
+                        const float v = sk * fmaf(cf.x, W[o.x], cf.y * W[o.y]);
+                        hi[e] = __uint_as_float(to_tf32(v));
+                        lo[e] = __uint_as_float(to_tf32(v - hi[e]));
+                    }
+                    const uint32_t off = (uint32_t)kl * RT_A_CHUNK + swz(row, 4 * xq);
+                    *reinterpret_cast<float4*>(sb + off) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+                    *reinterpret_cast<float4*>(sb + RT_A_ROUND + off) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+                }
+            }
+            if (xj < N) {
+#pragma unroll
+                for (int kl = 0; kl < RT_KQ; ++kl) {
+                    const int kc = i * RT_KQ + kl;
+                    if (kc >= nkc) break;
+                    float hi[4], lo[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        hi[e] = __uint_as_float(to_tf32(xv[kc][e]));
+                        lo[e] = __uint_as_float(to_tf32(xv[kc][e] - hi[e]));
+                    }
+                    const uint32_t off = 2 * RT_A_ROUND + (uint32_t)kl * RT_X_CHUNK + swz(xj, 4 * xq);
+                    *reinterpret_cast<float4*>(sb + off) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+                    *reinterpret_cast<float4*>(sb + RT_X_ROUND + off) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+                }
+            }
+            fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            if (*(volatile int*)&s_abort) break;  // block-uniform after the barrier
+            if (tid == 0) {
+                tc_fence_after();
+                const uint32_t a0 = smem_u32(sb), x0 = a0 + 2 * RT_A_ROUND;
+#pragma unroll
+                for (int prod = 0; prod < 3; ++prod) {
+                    const uint32_t a = a0 + (prod == 2 ? RT_A_ROUND : 0), x = x0 + (prod == 1 ? RT_X_ROUND : 0);
+#pragma unroll
+                    for (int kl = 0; kl < RT_KQ; ++kl) {
+                        if (i * RT_KQ + kl >= nkc) break;
+#pragma unroll
+                        for (int ks = 0; ks < 2; ++ks)
+                            tc_mma(tmem, smem_desc(a + kl * RT_A_CHUNK + 32 * ks),
+                                   smem_desc(x + kl * RT_X_CHUNK + 32 * ks), idesc,
+                                   (i | prod | kl | ks) != 0 ? 1u : 0u);
+                    }
+                }
+                tc_commit(&bar[buf]);
+            }
+            __syncwarp();
+        }
+        // the last round's commit covers every MMA before it
+        bool got = false;
+        if (!*(volatile int*)&s_abort) {
+            const int gl = r * nq + nq - 1;
+            got = mbar_wait(&bar[gl & 1], (uint32_t)((gl >> 1) & 1));
+        }
+        ok = __syncthreads_and(got) != 0;  // block-uniform
+        tc_fence_after();
+        if (ok) {
+            const int q4 = warp & 3, half = warp >> 2;
+            if (half * 32 < N) {
+                float v[32];
+                tc_ld32(tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(half * 32), v);
+                const int row = 32 * q4 + lane;
+                if (row < nc) {
+                    float* L = g.L + (size_t)r * g.stride;
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        const int j = half * 32 + i;
+                        if (j < cnt) atomicAdd(L + (size_t)s_tgt[j] * nc + row, v[i] * ih);
+                    }
+                }
+            }
+        } else if (tid == 0) {
+            atomicAdd(g.err, 1);
+        }
+        tc_fence_before();
+        __syncthreads();  // the accumulator is free again
+        tc_fence_after();
+    }
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(RT_TMEM_COLS)
+                     : "memory");
+}
+
 template <typename R, int RP>
 static LfErr m2r_build_ops(lfmm_ctx* ctx, cudaStream_t st)
 {
@@ -788,9 +1075,47 @@ static LfErr m2r_apply_kc(lfmm_ctx* ctx, cudaStream_t st)
     return lf_cuda(cudaGetLastError(), "m2r gemm (operator chunks)");
 }
 
+// the float32 form with (p+1)^2 <= 128 applies the keys on the tensor cores
+// whenever the free M2L does (tensor-core option)
+static bool m2r_tc_on(const lfmm_ctx* ctx) { return ctx->precision == 1 && ctx->p <= 10 && lf_tc_on(ctx); }
+
+static LfErr m2r_apply_tc(lfmm_ctx* ctx, cudaStream_t st)
+{
+    RTcArgs g;
+    g.p = ctx->p;
+    g.nc = lf_nc(ctx->p);
+    g.nkc = (g.nc + 15) / 16;
+    g.batches = ctx->m2r_batches.as<int4>();
+    g.kval = ctx->m2r_kval.as<uint32_t>() + ctx->m2r_kfirst;
+    g.tables = ctx->m2r_tables.as<double>();
+    g.ktab = ctx->m2r_ktab.as<int>();
+    g.comps = ctx->comp_dev.as<LfmmComp>();
+    g.order = ctx->m2r_order.as<uint32_t>();
+    g.ent = ctx->m2r_ent.as<uint32_t>();
+    g.tgt = ctx->m2r_tgt.as<int>();
+    g.levelh = ctx->m2r_levelh.as<double>();
+    g.M = ctx->Mexp.as<float>();
+    g.L = ctx->Lexp.as<float>();
+    g.stride = (size_t)ctx->nbox_total * g.nc;
+    g.nr = ctx->nrhs_b;
+    g.err = reinterpret_cast<int*>(ctx->counts.as<char>() + LFMM_TIMEOUT_OFF);
+    if (ctx->m2r_phase_p != ctx->p) {
+        // once per context (the first evaluation; a captured batch graph never sees it)
+        LF_TRY(lf_reserve(ctx->m2r_phase, (size_t)R_OW * R_OW * 2 * RT_TS * sizeof(float)));
+        ++ctx->launches, k_m2r_phase<<<R_OW * R_OW, 32, 0, st>>>(ctx->p, ctx->m2r_phase.as<float>());
+        LF_TRY(lf_cuda(cudaGetLastError(), "m2r phases"));
+        ctx->m2r_phase_p = ctx->p;
+    }
+    g.phase = ctx->m2r_phase.as<float>();
+    LF_CHECK(cudaFuncSetAttribute(k_m2r_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, RT_SMEM));
+    ++ctx->launches, k_m2r_tc<<<ctx->m2r_nbatch, RT_THREADS, RT_SMEM, st>>>(g);
+    return lf_cuda(cudaGetLastError(), "m2r tensor-core GEMM");
+}
+
 template <typename R>
 static LfErr m2r_apply_t(lfmm_ctx* ctx, cudaStream_t st)
 {
+    if (sizeof(R) == 4 && m2r_tc_on(ctx)) return m2r_apply_tc(ctx, st);
     switch (ctx->m2l_rm) {
     case 2: return m2r_apply_rp<R, 32>(ctx, st);
     case 4: return m2r_apply_rp<R, 64>(ctx, st);
@@ -804,7 +1129,9 @@ static LfErr m2r_apply_t(lfmm_ctx* ctx, cudaStream_t st)
 // assemble the operators of the keys for the current precision (build time)
 LfErr lf_m2r_ops(lfmm_ctx* ctx, cudaStream_t st)
 {
-    if (ctx->m2r_nbatch == 0) return LfErr();
+    // the tensor-core form assembles each operator where it is applied; the
+    // CUDA-core GEMM builds them on first use if the option changes later
+    if (ctx->m2r_nbatch == 0 || m2r_tc_on(ctx)) return LfErr();
     switch (ctx->m2l_rm) {
     case 2: return ctx->precision ? m2r_build_ops<float, 32>(ctx, st) : m2r_build_ops<double, 32>(ctx, st);
     case 4: return ctx->precision ? m2r_build_ops<float, 64>(ctx, st) : m2r_build_ops<double, 64>(ctx, st);
