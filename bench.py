@@ -739,27 +739,34 @@ def main():
                                  "(potential and field); duration = CUDA events around the near field run alone "
                                  "(not beside the far field), after the timed steps"}
     # the other stages: counted work (the library's statistics) over their
-    # CUDA-event times inside the timed steps, against the float32 CUDA-core
-    # peak (the near field runs beside them, so these are lower bounds)
+    # CUDA-event times inside the timed steps, against the peak of the units
+    # each runs on (the near field runs beside them, so these are lower bounds)
     sm_mhz = (clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0)
     pk32 = fp32_peak_tflops(sm_mhz)
     sms = forms_out[headline]["stage_ms"]
     nc, nre = (args.p + 1) ** 2, (args.p + 1) * (args.p + 2) // 2
     edge = 8 * nc * nre  # flops per parent-child edge (dense complex shift) and per M2L pair
-    work = [("p2m", "k_p2m", st["n"], 20 * nc, "charge"),
-            ("m2m", "k_m2l_gemm (M2M)", st["m2m_edges"], edge, "parent-child edge"),
-            ("m2l_reaction", "k_m2r_gemm (keyed reaction M2L)", st["m2l_reaction"], edge, "reaction box pair"),
-            ("l2l", "k_m2l_gemm / k_m2l_tc (L2L)", st["m2m_edges"], edge, "parent-child edge"),
-            ("l2p", "k_l2p", st["n"], 20 * nc, "charge")]
+    # the float32 form at (p+1)^2 <= 128 applies the reaction keys on the tensor
+    # cores (k_m2r_tc, 3xTF32): its peak is the dense TF32 rate
+    r_tc = results[headline].get("prec", 1) == 1 and (args.p + 1) ** 2 <= 128
+    pk_tf32 = tf32_peak_tflops()[0]
+    work = [("p2m", "k_p2m", st["n"], 20 * nc, "charge", pk32),
+            ("m2m", "k_m2l_gemm (M2M)", st["m2m_edges"], edge, "parent-child edge", pk32),
+            ("m2l_reaction", "k_m2r_tc (keyed reaction M2L, tcgen05 3xTF32)" if r_tc
+             else "k_m2r_gemm (keyed reaction M2L)", st["m2l_reaction"], edge, "reaction box pair",
+             pk_tf32 if r_tc else pk32),
+            ("l2l", "k_m2l_gemm / k_m2l_tc (L2L)", st["m2m_edges"], edge, "parent-child edge", pk32),
+            ("l2p", "k_l2p", st["n"], 20 * nc, "charge", pk32)]
     stage_roofs = []
-    for stage, kern, units, fpu, unit in work:
+    for stage, kern, units, fpu, unit, pk in work:
         ms_s = sms.get(stage)
         if not ms_s or not units:
             continue
         ach = units * fpu / (ms_s / 1e3) / 1e12
         stage_roofs.append({"stage": stage, "kernel": kern, "units": int(units), "unit": unit,
-                            "flops_per_unit": fpu, "ms": ms_s, "achieved_tflops": ach, "peak_tflops": pk32,
-                            "frac": ach / pk32})
+                            "flops_per_unit": fpu, "ms": ms_s, "achieved_tflops": ach, "peak_tflops": pk,
+                            "peak": "dense TF32 tensor" if pk is pk_tf32 else "FP32 CUDA core",
+                            "frac": ach / pk})
     line = {
         "metric": METRIC,
         "value": value,

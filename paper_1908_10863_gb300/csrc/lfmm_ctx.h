@@ -161,6 +161,8 @@ struct lfmm_ctx {
     DevBuf m2r_ops;         // assembled operator per key, [nkeys][RP][RP] in the precision below
     DevBuf m2r_phase;       // float32 e^{i m phi} of the 225 lateral key offsets, m <= 2p (tensor-core form)
     int m2r_phase_p = -1;   // order the phase table holds
+    DevBuf m2r_pairs;       // int2 (source box, target box) per sorted reaction entry
+    int m2r_nent = 0;       // sorted reaction entries
     int m2r_ops_prec = -1;  // 0 FP64, 1 FP32, -1 not assembled for this build
     int m2r_dev_pending = 0;  // 1: the keys' tables and operators are still to be computed (first evaluation)
     cudaEvent_t ev_m2r = nullptr;  // recorded after them on the stream that computed them

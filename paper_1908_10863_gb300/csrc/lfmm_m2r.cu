@@ -156,6 +156,7 @@ LfErr lf_prepare_m2r(lfmm_ctx* ctx, cudaStream_t st)
     ctx->stats[LFMM_STAT_REACTION_TABLES] = 0;
     ctx->m2r_keyed_from = ctx->depth + 1;
     ctx->m2r_pending_ne = 0;
+    ctx->m2r_nent = 0;
     // the keyed GEMM holds a whole operator in shared memory (p <= 10) or
     // stages it in chunks (p <= 15)
     if (ctx->m2l_rm == 0 || ctx->m2l_rm > 16 || ctx->m2r_total == 0) return LfErr();
@@ -249,6 +250,7 @@ LfErr lf_prepare_m2r(lfmm_ctx* ctx, cudaStream_t st)
 LfErr lf_prepare_m2r_finish(lfmm_ctx* ctx, cudaStream_t st)
 {
     const int ne = ctx->m2r_pending_ne;
+    ctx->m2r_nent = ne;
     if (ne <= 0) return LfErr();
     ctx->m2r_pending_ne = 0;
     LF_CHECK(cudaStreamSynchronize(st));
@@ -336,12 +338,13 @@ LfErr lf_prepare_m2r_finish(lfmm_ctx* ctx, cudaStream_t st)
     (void)P;
     (void)Q;
     ctx->m2r_ntab = ntab;
-    // batches of R_TB pairs of one key
+    // batches of R_TB pairs of one key: key index, first sorted entry, count | key << 8, table
     std::vector<int4>& batches = ctx->m2r_batches_h;
     batches.clear();
     for (int64_t k = k0; k < k1; ++k)
         for (int s = kstart[k]; s < kstart[k + 1]; s += R_TB)
-            batches.push_back(make_int4((int)(k - k0), s, std::min(R_TB, kstart[k + 1] - s), 0));
+            batches.push_back(make_int4((int)(k - k0), s, std::min(R_TB, kstart[k + 1] - s) | (int)(kv[k] << 8),
+                                        ktab[k - k0]));
     ctx->m2r_nkeys = (int)nku;
     ctx->m2r_nbatch = (int)batches.size();
     LF_TRY(lf_reserve(ctx->m2r_batches, batches.size() * sizeof(int4) + 16));
@@ -360,6 +363,16 @@ LfErr lf_prepare_m2r_finish(lfmm_ctx* ctx, cudaStream_t st)
 // current precision, enqueued on `st` (the first evaluation after a build
 // runs this on the near-field stream, so it overlaps the far field's upward
 // pass and free M2L; the reaction M2L waits for it).
+// (source box, target box) of every reaction M2L entry in key order
+__global__ void k_m2r_pairs(const uint32_t* __restrict__ order, const uint32_t* __restrict__ ent,
+                            const int* __restrict__ tgt, int ne, int2* __restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ne) return;
+    const uint32_t e = order[i];
+    out[i] = make_int2((int)(ent[e] & LFMM_ENT_MASK), tgt[e]);
+}
+
 LfErr lf_m2r_device(lfmm_ctx* ctx, cudaStream_t st)
 {
     if (ctx->m2r_nbatch == 0 || ctx->m2r_ntab == 0) {
@@ -376,6 +389,13 @@ LfErr lf_m2r_device(lfmm_ctx* ctx, cudaStream_t st)
                                                  ctx->gl_t_m2l.as<double>(),
                                                  ctx->gl_w_m2l.as<double>(), Q, ctx->m2r_tables.as<double>());
     LF_TRY(lf_cuda(cudaGetLastError(), "m2r tables"));
+    if (ctx->m2r_nent > 0) {
+        LF_TRY(lf_reserve(ctx->m2r_pairs, (size_t)ctx->m2r_nent * sizeof(int2) + 16));
+        ++ctx->launches, k_m2r_pairs<<<lf_blocks(ctx->m2r_nent, 256), 256, 0, st>>>(
+            ctx->m2r_order.as<uint32_t>(), ctx->m2r_ent.as<uint32_t>(), ctx->m2r_tgt.as<int>(), ctx->m2r_nent,
+            ctx->m2r_pairs.as<int2>());
+        LF_TRY(lf_cuda(cudaGetLastError(), "m2r pairs"));
+    }
     LF_TRY(lf_m2r_ops(ctx, st));
     ctx->m2r_dev_pending = 0;  // only once both are enqueued
     return LfErr();
@@ -535,7 +555,7 @@ __global__ void __launch_bounds__(R_T) k_m2r_gemm(RGemmArgs g)
     __shared__ int s_src[R_TB], s_tgt[R_TB];
     const int tid = threadIdx.x;
     const int4 b = g.batches[blockIdx.x];
-    const int kidx = b.x, start = b.y, cnt = b.z;
+    const int kidx = b.x, start = b.y, cnt = b.z & 255;
     int c, lev, ox, oy, oz;
     rkey_decode(g.kval[kidx], c, lev, ox, oy, oz);
     // the key's operator: a contiguous copy in 16-byte pieces
@@ -666,7 +686,7 @@ __global__ void __launch_bounds__(R_T) k_m2r_gemm_kc(RGemmArgs g)
     __shared__ int s_src[R_TB], s_tgt[R_TB];
     const int tid = threadIdx.x;
     const int4 b = g.batches[blockIdx.x];
-    const int kidx = b.x, start = b.y, cnt = b.z;
+    const int kidx = b.x, start = b.y, cnt = b.z & 255;
     int c, lev, ox, oy, oz;
     rkey_decode(g.kval[kidx], c, lev, ox, oy, oz);
     const R* A = reinterpret_cast<const R*>(g.ops) + (size_t)kidx * KP * RP;
@@ -728,11 +748,16 @@ __global__ void __launch_bounds__(R_T) k_m2r_gemm_kc(RGemmArgs g)
 // coefficients, K = the input coefficients in chunks of 16).  The batch's
 // source multipoles (B operand: N = the batch rounded up to 16 columns) are
 // loaded into registers up front and split the same way.  K runs in rounds
-// of RT_KQ chunks through two 48 KB buffers: while the tensor cores take one
-// round (3xTF32: a1 x1 + a1 x2 + a2 x1, issued by one thread into one
-// accumulator of 64 tensor-memory columns), the threads form the next.  With
-// 97 KB of shared memory the kernel shares its SMs with the near field that
-// runs beside it.  The eight warps then read the accumulator back (warp w:
+// of RT_KQ chunks through two buffers: while the tensor cores take one round
+// (3xTF32: a1 x1 + a1 x2 + a2 x1, issued by one thread into one accumulator
+// of 64 tensor-memory columns), the threads form the next.  The operator
+// entries come from a table of the reaction coefficient extended to negative
+// orders, so each is two shared-memory loads and a fused multiply-add with
+// signs and offsets precomputed per output row and input coefficient.  Each
+// batch carries its key and table index, so one dependent load reaches the
+// table, the phases and the batch's (source, target) pairs.  With 61 KB of
+// shared memory the kernel shares its SMs with the near field that runs
+// beside it.  The eight warps then read the accumulator back (warp w:
 // lanes 32 (w mod 4) .., columns 32 (w / 4) ..), scale it by 1/h and add it
 // into the targets' local expansions.  Several right-hand sides repeat the
 // rounds per vector.  Every wait is bounded: on a timeout the CTA counts it
@@ -741,7 +766,15 @@ __global__ void __launch_bounds__(R_T) k_m2r_gemm_kc(RGemmArgs g)
 #define RT_THREADS 256
 #define RT_TS 21                        // table side 2p + 1 for p <= 10
 #define RT_WS 41                        // 4p + 1: orders -2p .. 2p
-#define RT_KQ 2                         // K chunks per round
+// one K chunk per round and three CTAs per SM (61 KB of shared memory, 64
+// registers each) measured 0.26 ms at N = 1M, p = 10, against 0.31 ms for
+// rounds of two chunks at two CTAs per SM
+#ifndef RT_KQ
+#define RT_KQ 1                         // K chunks per round
+#endif
+#ifndef RT_MINB
+#define RT_MINB 3                       // resident CTAs per SM
+#endif
 #define RT_A_CHUNK (128 * TC_ROWB)      // one K chunk of one operator piece: 128 rows x 64 B
 #define RT_X_CHUNK (R_TB * TC_ROWB)     // one K chunk of one multipole piece: 64 rows x 64 B
 #define RT_A_ROUND (RT_KQ * RT_A_CHUNK)
@@ -752,15 +785,11 @@ __global__ void __launch_bounds__(R_T) k_m2r_gemm_kc(RGemmArgs g)
 
 struct RTcArgs {
     int p, nc, nkc;         // order, coefficients, K chunks of 16 that hold them
-    const int4* batches;    // key, first sorted entry, count
-    const uint32_t* kval;
+    const int4* batches;    // key index, first sorted entry, count | key << 8, table
     const double* tables;   // [table][TS][TS]
-    const int* ktab;        // table of each key
     const LfmmComp* comps;
     const float* phase;     // [225 lateral offsets][cos | sin][RT_TS] (k_m2r_phase)
-    const uint32_t* order;  // sorted entry indices
-    const uint32_t* ent;    // m2r entries (component | source box)
-    const int* tgt;         // target box per entry
+    const int2* pairs;      // (source box, target box) per sorted entry (k_m2r_pairs)
     const double* levelh;
     const float* M;
     float* L;
@@ -783,7 +812,7 @@ __global__ void k_m2r_phase(int p, float* out)
     out[(size_t)b * 2 * RT_TS + RT_TS + m] = (float)sn;
 }
 
-__global__ void __launch_bounds__(RT_THREADS, 2) k_m2r_tc(RTcArgs g)
+__global__ void __launch_bounds__(RT_THREADS, RT_MINB) k_m2r_tc(RTcArgs g)
 {
     extern __shared__ unsigned char smem_raw[];
     // 512-byte alignment: the period of the 64-byte swizzle
@@ -807,12 +836,13 @@ __global__ void __launch_bounds__(RT_THREADS, 2) k_m2r_tc(RTcArgs g)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int p = g.p, nc = g.nc, nkc = g.nkc, TS = 2 * p + 1, WS = 4 * p + 1, TSZ = TS * WS;
     const int4 b = g.batches[blockIdx.x];
-    const int kidx = b.x, start = b.y, cnt = b.z;
+    // the batch carries its key and table: one dependent load to everything else
+    const int start = b.y, cnt = b.z & 255, tab = b.w;
     if (cnt <= 0 || cnt > R_TB) return;
     const int N = (cnt + 15) & ~15;  // MMA columns
     const int nq = (nkc + RT_KQ - 1) / RT_KQ;
     int c, lev, ox, oy, oz;
-    rkey_decode(g.kval[kidx], c, lev, ox, oy, oz);
+    rkey_decode((uint32_t)b.z >> 8, c, lev, ox, oy, oz);
     const bool refl = g.comps[c].refl != 0;
 
     if (tid < 128) {
@@ -837,14 +867,9 @@ __global__ void __launch_bounds__(RT_THREADS, 2) k_m2r_tc(RTcArgs g)
         }
     }
     if (tid < R_TB) {
-        if (tid < cnt) {
-            const uint32_t e = g.order[start + tid];
-            s_src[tid] = (int)(g.ent[e] & LFMM_ENT_MASK);
-            s_tgt[tid] = g.tgt[e];
-        } else {
-            s_src[tid] = -1;
-            s_tgt[tid] = -1;
-        }
+        const int2 pr = (tid < cnt) ? g.pairs[start + tid] : make_int2(-1, -1);
+        s_src[tid] = pr.x;
+        s_tgt[tid] = pr.y;
     }
     if (tid >= 128 && tid < 128 + 2 * RT_TS)
         sPh[tid - 128] = g.phase[(size_t)((ox + R_OR) * R_OW + (oy + R_OR)) * 2 * RT_TS + (tid - 128)];
@@ -866,7 +891,7 @@ __global__ void __launch_bounds__(RT_THREADS, 2) k_m2r_tc(RTcArgs g)
     tc_fence_after();
     const uint32_t tmem = s_tmem;
     {
-        const double* Tk = g.tables + (size_t)g.ktab[kidx] * TS * TS;
+        const double* Tk = g.tables + (size_t)tab * TS * TS;
         for (int j = tid; j < TSZ; j += RT_THREADS) {
             const int Nn = j / WS, mu = j - Nn * WS - 2 * p, a = mu < 0 ? -mu : mu;
             const float t = (float)Tk[Nn * TS + a];
@@ -1086,13 +1111,9 @@ static LfErr m2r_apply_tc(lfmm_ctx* ctx, cudaStream_t st)
     g.nc = lf_nc(ctx->p);
     g.nkc = (g.nc + 15) / 16;
     g.batches = ctx->m2r_batches.as<int4>();
-    g.kval = ctx->m2r_kval.as<uint32_t>() + ctx->m2r_kfirst;
     g.tables = ctx->m2r_tables.as<double>();
-    g.ktab = ctx->m2r_ktab.as<int>();
     g.comps = ctx->comp_dev.as<LfmmComp>();
-    g.order = ctx->m2r_order.as<uint32_t>();
-    g.ent = ctx->m2r_ent.as<uint32_t>();
-    g.tgt = ctx->m2r_tgt.as<int>();
+    g.pairs = ctx->m2r_pairs.as<int2>();
     g.levelh = ctx->m2r_levelh.as<double>();
     g.M = ctx->Mexp.as<float>();
     g.L = ctx->Lexp.as<float>();
