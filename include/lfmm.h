@@ -62,7 +62,9 @@ enum {
                                    cores at every order (for 11 <= p <= 14 the wide form: Err2 of the
                                    potential ~8e-7 at p = 14 against ~4e-7 on the CUDA cores, in a sixth
                                    of the time); 0 = CUDA cores.  Where (p+1)^2 <= 128 the tensor cores
-                                   also take the L2L into the leaves. */
+                                   also take the L2L into the leaves and the keyed reaction M2L (each
+                                   key's operator formed in shared memory from its Sommerfeld table,
+                                   eqs. metoleimage1, coefintable); 0 puts both on the CUDA cores. */
     LFMM_OPT_P2P_SPLIT = 8,     /* near list of a leaf shared by this many warps/blocks of the P2P kernels:
                                    0 = chosen from the leaf count (default), else 1, 2, 4, 8 or 16 */
     LFMM_OPT_TC_GROUPS = 9,     /* tensor-core free M2L: CTAs per tile of targets (256, or 128 in the wide
