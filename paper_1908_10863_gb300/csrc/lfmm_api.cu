@@ -1001,7 +1001,7 @@ void lfmm_destroy(lfmm_ctx* ctx)
                       &ctx->oct_U64, &ctx->oct_U32, &ctx->comp_dev, &ctx->perm, &ctx->xs, &ctx->ys, &ctx->zs,
                       &ctx->keys, &ctx->keys_tmp, &ctx->vals_tmp, &ctx->scan_tmp, &ctx->hist, &ctx->keys_tmp2, &ctx->vals_tmp2, &ctx->scan_tmp2, &ctx->hist2, &ctx->xyz_in,
                       &ctx->layer_in, &ctx->err_flag, &ctx->counts, &ctx->box_key, &ctx->box_pbeg, &ctx->box_pend,
-                      &ctx->box_parent, &ctx->box_cbeg, &ctx->box_cend, &ctx->box_center, &ctx->box_grid, &ctx->pos_rel, &ctx->leaf_of, &ctx->near_tab, &ctx->level_consts, &ctx->flags, &ctx->idx,
+                      &ctx->box_parent, &ctx->box_cbeg, &ctx->box_cend, &ctx->box_center, &ctx->box_grid, &ctx->pos_rel, &ctx->leaf_of, &ctx->near_tab, &ctx->near_tab4, &ctx->level_consts, &ctx->flags, &ctx->idx,
                       &ctx->near_off, &ctx->near_ent, &ctx->m2l_off, &ctx->m2l_ent, &ctx->m2r_off, &ctx->m2r_ent,
                       &ctx->q_sorted, &ctx->Mexp, &ctx->Lexp, &ctx->phi_far, &ctx->phi_near, &ctx->fld_far,
                       &ctx->fld_near, &ctx->q_stage, &ctx->phi_stage, &ctx->fld_stage, &ctx->m2l_A64, &ctx->m2l_A32,

@@ -135,6 +135,7 @@ struct lfmm_ctx {
     std::vector<float4> p2p_consts_h;
     void* host_pin = nullptr;  // small pinned host buffer for readbacks that must not wait
     DevBuf near_tab;            // remainder tables of the near-field reaction kernels
+    DevBuf near_tab4;           // their float32 copy, one float4 per grid point (float32 kernels)
     int near_tab_ready = 0, use_near_tab = 0;
     double near_tab_err = -1.0;  // largest relative deviation from the quadrature at the check points
     double m2l_levelh_h[16] = {0};

@@ -605,10 +605,49 @@ __device__ __forceinline__ bool lf_nt_remainder(const double* __restrict__ ctab,
     return true;
 }
 
+// the same from the float32 copy of the table, one float4 {T00, T10, T11, 0}
+// per grid point ([w][s]): 16 loads of 16 bytes per pair instead of 48 of 8
+template <typename R>
+__device__ __forceinline__ bool lf_nt_remainder4(const float4* __restrict__ ctab, const LfmmComp& c, R rho, R h,
+                                                 R& r00, R& r10, R& r11)
+{
+    const R Z = h + (R)c.zeta_r;
+    const R iZ = R(1) / Z;
+    const R fs = rho * iZ * R((LF_NT_NS - 1) / LF_NT_SMAX);
+    if (!(fs <= R(LF_NT_NS - 1))) return false;
+    const R fw = (R)c.zeta_r * iZ * R(LF_NT_NW - 1);
+    int is = (int)fs - 1, iw = (int)fw - 1;
+    is = is < 0 ? 0 : (is > LF_NT_NS - 4 ? LF_NT_NS - 4 : is);
+    iw = iw < 0 ? 0 : (iw > LF_NT_NW - 4 ? LF_NT_NW - 4 : iw);
+    R ws[4], ww[4];
+    lf_lagrange4<R>(fs - (R)is, ws);
+    lf_lagrange4<R>(fw - (R)iw, ww);
+    R a0 = R(0), a1 = R(0), a2 = R(0);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const float4* row = ctab + (size_t)(iw + b) * LF_NT_NS + is;
+        R s0 = R(0), s1 = R(0), s2 = R(0);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const float4 v = __ldg(row + a);
+            s0 += ws[a] * (R)v.x;
+            s1 += ws[a] * (R)v.y;
+            s2 += ws[a] * (R)v.z;
+        }
+        a0 += ww[b] * s0;
+        a1 += ww[b] * s1;
+        a2 += ww[b] * s2;
+    }
+    r00 = a0 * iZ;
+    r10 = a1 * iZ * iZ;
+    r11 = a2 * iZ * iZ;
+    return true;
+}
+
 template <typename R, bool GEN = false>
 __device__ __forceinline__ void lf_reaction_pair(const LfmmComp& c, R rho, R h, int Q, const double* gl_t,
                                                  const double* gl_w, R& k00, R& k10, R& k11,
-                                                 const double* ctab = nullptr)
+                                                 const double* ctab = nullptr, const float4* ctab4 = nullptr)
 {
     typedef LfMath<R> F;
     R H = h + (R)c.zeta;
@@ -620,7 +659,15 @@ __device__ __forceinline__ void lf_reaction_pair(const LfmmComp& c, R rho, R h, 
     k10 = C * H * ir3;
     k11 = C * rho * ir3;
     if (!c.has_rem) return;
-    if (ctab) {
+    if (ctab4) {
+        R r00, r10, r11;
+        if (lf_nt_remainder4<R>(ctab4, c, rho, h, r00, r10, r11)) {
+            k00 += r00;
+            k10 += r10;
+            k11 += r11;
+            return;
+        }
+    } else if (ctab) {
         R r00, r10, r11;
         if (lf_nt_remainder<R>(ctab, c, rho, h, r00, r10, r11)) {
             k00 += r00;

@@ -58,6 +58,7 @@ struct P2PArgs {
     const double* gl_t;     // near-field quadrature rule (Qn nodes and weights)
     const double* gl_w;
     const double* ntab;  // remainder tables [component][LF_NT_PER], or null: the quadrature
+    const float4* ntab4;  // their float32 copy [component][w][s] {T00, T10, T11, 0} for the float32 kernels
     LfmmSurrView sv;  // learned near-field kernels (sv.ready = 0: quadrature only)
     // float32 warp kernel on a leaf level whose polarization images are grid
     // cells: box grid cells and per component (s, K, is_free) in leaf units,
@@ -68,6 +69,7 @@ struct P2PArgs {
     float hleaf;
 };
 #define LF_CTAB(a, c) ((a).ntab ? (a).ntab + (size_t)(c) * LF_NT_PER : nullptr)
+#define LF_CTAB4(a, c) ((a).ntab4 ? (a).ntab4 + (size_t)(c) * LF_NT_NS * LF_NT_NW : nullptr)
 
 #define P2P_T 128
 
@@ -128,13 +130,13 @@ __device__ __forceinline__ void p2p_free_add(R dx, R dy, R dz, const R* qs, int 
 template <typename R, int RB, bool GEN = false, typename S>
 __device__ __forceinline__ void p2p_reaction_add(const LfmmComp& cp, R dx, R dy, R dz, const R* qs, int qsk, int nr,
                                                  int Qn, const double* gl_t, const double* gl_w, P2PAccT<S, RB>& A,
-                                                 const double* ctab)
+                                                 const double* ctab, const float4* ctab4 = nullptr)
 {
     typedef LfMath<R> F;
     R h = (cp.a == 1) ? dz : -dz;
     R rho = F::Sqrt(dx * dx + dy * dy);
     R k00, k10, k11;
-    lf_reaction_pair<R, GEN>(cp, rho, h, Qn, gl_t, gl_w, k00, k10, k11, ctab);
+    lf_reaction_pair<R, GEN>(cp, rho, h, Qn, gl_t, gl_w, k00, k10, k11, ctab, ctab4);
     const R k10s = (cp.a == 1) ? k10 : -k10;
     const R g = rho > R(0) ? k11 / rho : R(0);
 #pragma unroll
@@ -220,7 +222,8 @@ __global__ void __launch_bounds__(P2P_T) k_p2p(P2PArgs a)
                 } else {
                     for (int u = 0; u < cnt; ++u)
                         p2p_reaction_add<R, RB, GEN>(cp, xi - sx[u], yi - sy[u], zi - sz[u], &sq[0][u], P2P_T,
-                                                     a.nr, a.Qn, a.gl_t, a.gl_w, A, LF_CTAB(a, c));
+                                                     a.nr, a.Qn, a.gl_t, a.gl_w, A, LF_CTAB(a, c),
+                                                     sizeof(R) == 4 ? LF_CTAB4(a, c) : nullptr);
                 }
             }
         }
@@ -353,7 +356,7 @@ __global__ void __launch_bounds__(32 * PW_WARPS) k_p2p_warp(P2PArgs a, const flo
                         for (int u = u0; u < u1; ++u) {
                             const float4 v = sp[w][u];
                             p2p_reaction_add<float, 1>(cp, xi - v.x, yi - v.y, zi - v.z, &sp[w][u].w, 0, 1, a.Qn,
-                                                       a.gl_t, a.gl_w, part, LF_CTAB(a, c));
+                                                       a.gl_t, a.gl_w, part, LF_CTAB(a, c), LF_CTAB4(a, c));
                         }
                     }
                     continue;
@@ -365,7 +368,8 @@ __global__ void __launch_bounds__(32 * PW_WARPS) k_p2p_warp(P2PArgs a, const flo
                 } else {
                     for (int u = u0; u < u1; ++u)
                         p2p_reaction_add<float, RB>(cp, xi - sx[w][u], yi - sy[w][u], zi - sz[w][u], &sq[w][0][u],
-                                                    32, a.nr, a.Qn, a.gl_t, a.gl_w, part, LF_CTAB(a, c));
+                                                    32, a.nr, a.Qn, a.gl_t, a.gl_w, part, LF_CTAB(a, c),
+                                                    LF_CTAB4(a, c));
                 }
             }
             p2p_flush<float, RB>(part, A);
@@ -914,6 +918,7 @@ LfErr lf_near_field(lfmm_ctx* ctx, cudaStream_t st)
     a.gl_t = ctx->gl_t_near.as<double>();
     a.gl_w = ctx->gl_w_near.as<double>();
     a.ntab = (ctx->use_near_tab && ctx->near_tab_ready) ? ctx->near_tab.as<double>() : nullptr;
+    a.ntab4 = (ctx->use_near_tab && ctx->near_tab_ready) ? ctx->near_tab4.as<float4>() : nullptr;
     a.grid = nullptr;
     a.pcon = nullptr;
     a.hleaf = (float)leaf.h;
@@ -1028,6 +1033,18 @@ __global__ void k_near_tables(const LfmmComp* __restrict__ comps, int ncomp, int
     t[2 * per] = out[2];
 }
 
+// the float32 copy of the tables: one float4 {T00, T10, T11, 0} per grid point
+__global__ void k_near_tab4(const double* __restrict__ tab, int ncomp, float4* __restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t per = (int64_t)LF_NT_NS * LF_NT_NW;
+    if (i >= per * ncomp) return;
+    const int c = (int)(i / per);
+    const int64_t r = i - (int64_t)c * per;
+    const double* t = tab + (size_t)c * LF_NT_PER + r;
+    out[i] = make_float4((float)t[0], (float)t[per], (float)t[2 * per], 0.f);
+}
+
 // err[i]: largest deviation of the three interpolated kernels from the
 // quadrature, relative to |I_00| (field kernels times the distance R)
 template <bool GEN>
@@ -1060,6 +1077,10 @@ LfErr lf_near_tables(lfmm_ctx* ctx, double* max_err)
             ctx->comp_dev.as<LfmmComp>(), nc, Q, ctx->gl_t_m2l.as<double>(), ctx->gl_w_m2l.as<double>(),
             ctx->near_tab.as<double>());
         LF_TRY(lf_cuda(cudaGetLastError(), "near tables"));
+        LF_TRY(lf_reserve(ctx->near_tab4, sizeof(float4) * (size_t)LF_NT_NS * LF_NT_NW * nc));
+        ++ctx->launches, k_near_tab4<<<lf_blocks(tot, 256), 256, 0, st>>>(ctx->near_tab.as<double>(), nc,
+                                                                          ctx->near_tab4.as<float4>());
+        LF_TRY(lf_cuda(cudaGetLastError(), "near tables (float32 copy)"));
     }
     // seeded check points: per reaction component, s uniform over the table,
     // depth sum h log-uniform in [1e-4, 3]
