@@ -71,8 +71,12 @@ enum {
                                    form), each summing 189/groups offsets in its tensor-memory accumulator
                                    before a float atomic add; a divisor of 189, or 0 = automatic (default:
                                    27, i.e. 7 offsets per accumulation; 63 in the wide form) */
-    LFMM_OPT_NEAR_TABLES = 10,  /* 1 = near-field reaction kernels with their remainder from pre-computed
-                                   tables (built on first use, see lfmm_near_tables); 0 = quadrature (default) */
+    LFMM_OPT_NEAR_TABLES = 10,  /* near-field reaction kernels: 2 = automatic (default): the float32 form
+                                   takes the remainder from pre-computed tables (deviation from the
+                                   quadrature ~2e-8, see lfmm_near_tables) once a build's near lists hold
+                                   reaction pairs, building them at the end of that build (once per
+                                   context), the FP64 form keeps the quadrature; 1 = tables in both forms
+                                   (built on first use); 0 = quadrature */
     LFMM_OPT_TC_PERSISTENT = 11, /* tensor-core free M2L: 1 = one persistent CTA per SM walking the
                                    (tile, offset group) units with a double-buffered accumulator, for
                                    launches of at least 4 units per SM; 0 = one CTA per unit, two CTAs per

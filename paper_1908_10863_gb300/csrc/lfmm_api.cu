@@ -645,6 +645,8 @@ int lf_find_comp(const lfmm_ctx* ctx, int l, int lp, int a, int b)
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
+static LfErr auto_near_tables(lfmm_ctx* ctx);  // below, beside the build
+
 extern "C" {
 
 lfmm_status lfmm_gauss_laguerre(int Q, double* nodes, double* weights)
@@ -756,11 +758,13 @@ lfmm_status lfmm_set_option(lfmm_ctx* ctx, int opt, double v)
 static lfmm_status set_option(lfmm_ctx* ctx, int opt, double v)
 {
     switch (opt) {
-    case LFMM_OPT_PRECISION:
+    case LFMM_OPT_PRECISION: {
         if (v != 0.0 && v != 1.0) return fail(ctx, "EINVAL: precision must be 0 or 1");
         if (v == 1.0 && ctx->p > 14) return fail(ctx, "EINVAL: the FP32 form supports p <= 14");
         ctx->precision = (int)v;
-        return LFMM_OK;
+        const LfErr e = auto_near_tables(ctx);
+        return e.empty() ? LFMM_OK : fail(ctx, e);
+    }
     case LFMM_OPT_LEAF_CAP:
         if (!(v >= 1.0 && v <= 100000.0)) return fail(ctx, "EINVAL: leaf capacity out of range");
         ctx->leaf_cap = (int)v;
@@ -794,14 +798,16 @@ static lfmm_status set_option(lfmm_ctx* ctx, int opt, double v)
         if (v != 0.0 && v != 1.0) return fail(ctx, "EINVAL: persistent tensor-core option must be 0 or 1");
         ctx->tc_persistent = (v != 0.0);
         return LFMM_OK;
-    case LFMM_OPT_NEAR_TABLES:
-        if (v != 0.0 && v != 1.0) return fail(ctx, "EINVAL: near tables option must be 0 or 1");
+    case LFMM_OPT_NEAR_TABLES: {
+        if (v != 0.0 && v != 1.0 && v != 2.0) return fail(ctx, "EINVAL: near tables option must be 0, 1 or 2");
         if (v == 1.0 && !ctx->near_tab_ready) {
             const LfErr e = lf_near_tables(ctx, nullptr);
             if (!e.empty()) return fail(ctx, e);
         }
-        ctx->use_near_tab = (v != 0.0);
-        return LFMM_OK;
+        ctx->use_near_tab = (int)v;
+        const LfErr e = auto_near_tables(ctx);
+        return e.empty() ? LFMM_OK : fail(ctx, e);
+    }
     case LFMM_OPT_TC_GROUPS: {
         const int k = (int)v;
         if ((double)k != v || k < 0 || (k > 0 && 189 % k != 0))
@@ -827,6 +833,18 @@ static lfmm_status set_option(lfmm_ctx* ctx, int opt, double v)
 
 }  // extern "C"
 
+// Automatic near tables (the default): the float32 form takes the pre-computed
+// remainder tables once a built tree's near lists hold reaction pairs (their
+// deviation from the quadrature, ~2e-8, is far below float32 rounding); the
+// tables are built here once per context, outside any evaluation.
+static LfErr auto_near_tables(lfmm_ctx* ctx)
+{
+    if (ctx->use_near_tab != 2 || ctx->precision != 1 || !ctx->built || ctx->near_reaction_entries == 0 ||
+        ctx->near_tab_ready)
+        return LfErr();
+    return lf_near_tables(ctx, nullptr);
+}
+
 lfmm_status lf_build_dev(lfmm_ctx* ctx, int64_t n, const double* xyz_dev, const int32_t* layer_dev)
 {
     ctx->built = false;
@@ -845,6 +863,8 @@ lfmm_status lf_build_dev(lfmm_ctx* ctx, int64_t n, const double* xyz_dev, const 
     prof_reset(ctx);
     ctx->built = true;
     ++ctx->serial;
+    e = auto_near_tables(ctx);
+    if (!e.empty()) return fail(ctx, e);
     return LFMM_OK;
 }
 

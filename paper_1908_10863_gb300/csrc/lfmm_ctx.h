@@ -136,7 +136,8 @@ struct lfmm_ctx {
     void* host_pin = nullptr;  // small pinned host buffer for readbacks that must not wait
     DevBuf near_tab;            // remainder tables of the near-field reaction kernels
     DevBuf near_tab4;           // their float32 copy, one float4 per grid point (float32 kernels)
-    int near_tab_ready = 0, use_near_tab = 0;
+    int near_tab_ready = 0;
+    int use_near_tab = 2;       // 0 quadrature, 1 tables, 2 tables in the float32 form (default)
     double near_tab_err = -1.0;  // largest relative deviation from the quadrature at the check points
     double m2l_levelh_h[16] = {0};
     // use_tc: 2 automatic (tensor cores where (p+1)^2 <= 128), 1 at every order, 0 never

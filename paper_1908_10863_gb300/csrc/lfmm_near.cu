@@ -917,8 +917,9 @@ LfErr lf_near_field(lfmm_ctx* ctx, cudaStream_t st)
     a.comps = ctx->comp_dev.as<LfmmComp>();
     a.gl_t = ctx->gl_t_near.as<double>();
     a.gl_w = ctx->gl_w_near.as<double>();
-    a.ntab = (ctx->use_near_tab && ctx->near_tab_ready) ? ctx->near_tab.as<double>() : nullptr;
-    a.ntab4 = (ctx->use_near_tab && ctx->near_tab_ready) ? ctx->near_tab4.as<float4>() : nullptr;
+    const bool tab_on = ctx->near_tab_ready && (ctx->use_near_tab == 1 || (ctx->use_near_tab == 2 && ctx->precision == 1));
+    a.ntab = tab_on ? ctx->near_tab.as<double>() : nullptr;
+    a.ntab4 = tab_on ? ctx->near_tab4.as<float4>() : nullptr;
     a.grid = nullptr;
     a.pcon = nullptr;
     a.hleaf = (float)leaf.h;

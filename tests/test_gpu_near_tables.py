@@ -26,13 +26,14 @@ def test_fmm_with_tables_matches_quadrature_and_oracle(precision, tol):
     with LayeredFMM(w.d, w.eps, 10, precision=precision) as f:
         f.build(w.xyz, w.layer)
         assert f.stats()["p2p_reaction"] > 0
+        f.set_option(OPT_NEAR_TABLES, 0)
         phi0, E0 = f.evaluate(w.q)
         f.set_option(OPT_NEAR_TABLES, 1)
         phi1, E1 = f.evaluate(w.q)
         f.set_option(OPT_NEAR_TABLES, 0)
         phi2, _ = f.evaluate(w.q)
         with pytest.raises(LfmmError):
-            f.set_option(OPT_NEAR_TABLES, 2)
+            f.set_option(OPT_NEAR_TABLES, 3)
     d_phi, d_fld = oracle.err2(phi0, phi1), oracle.err2(E0, E1)
     print("precision %d: tables vs quadrature Err2 phi %.2e field %.2e" % (precision, d_phi, d_fld))
     assert d_phi < tol and d_fld < 10 * tol
@@ -60,3 +61,26 @@ def test_tables_gain_in_near_field(precision):
     print("precision %d: near field %.3f ms by quadrature, %.3f ms with tables (%.2fx); Err2 %.2e"
           % (precision, res[0][0], res[1][0], res[0][0] / res[1][0], oracle.err2(res[0][1], res[1][1])))
     assert oracle.err2(res[0][1], res[1][1]) < (1e-8 if precision == 0 else 1e-6)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_default_near_tables_automatic(precision):
+    # the default (2) takes the tables in the float32 form once the near lists
+    # hold reaction pairs and keeps the quadrature in the FP64 form
+    w = workloads.near_interface(12000)
+    with LayeredFMM(w.d, w.eps, 10, precision=precision) as f:
+        f.build(w.xyz, w.layer)
+        assert f.stats()["p2p_reaction"] > 0
+        phi_d, _ = f.evaluate(w.q)
+        f.set_option(OPT_NEAR_TABLES, 0)
+        phi_q, _ = f.evaluate(w.q)
+        f.set_option(OPT_NEAR_TABLES, 1)
+        phi_t, _ = f.evaluate(w.q)
+        f.set_option(OPT_NEAR_TABLES, 2)
+        phi_a, _ = f.evaluate(w.q)
+    if precision == 0:
+        # tables and quadrature differ by ~2e-11 here: the default is the quadrature
+        assert oracle.err2(phi_q, phi_d) < 1e-14 and oracle.err2(phi_q, phi_a) < 1e-14
+        assert oracle.err2(phi_t, phi_d) > 1e-13
+    else:
+        assert oracle.err2(phi_t, phi_d) < 1e-6 and oracle.err2(phi_t, phi_a) < 1e-6
