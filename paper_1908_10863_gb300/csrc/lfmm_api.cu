@@ -1030,7 +1030,7 @@ void lfmm_destroy(lfmm_ctx* ctx)
                       &ctx->m2r_tgt, &ctx->m2r_ops, &ctx->m2r_phase, &ctx->m2r_pairs, &ctx->m2r_kstart, &ctx->m2r_kval, &ctx->m2r_tables, &ctx->m2r_levelh, &ctx->m2r_zfrac, &ctx->m2r_zbase,
                       &ctx->m2r_batches, &ctx->m2r_tdesc, &ctx->m2r_ktab, &ctx->surr_theta, &ctx->surr_grad, &ctx->surr_m1,
                       &ctx->surr_m2, &ctx->surr_w, &ctx->surr_b, &ctx->surr_meta, &ctx->surr_err, &ctx->surr_comps,
-                      &ctx->surr_xoff, &ctx->surr_counters, &ctx->m2l_Atc, &ctx->m2m_Atc, &ctx->l2l_Atc, &ctx->tc_shift_tiles, &ctx->m2l_tc_tiles, &ctx->m2l_Ms, &ctx->m2m_A64, &ctx->m2m_A32,
+                      &ctx->surr_xoff, &ctx->surr_counters, &ctx->m2l_Atc, &ctx->m2m_Atc, &ctx->l2l_Atc, &ctx->tc_shift_tiles, &ctx->m2l_tc_tiles, &ctx->tc_mseg, &ctx->m2l_Ms, &ctx->m2m_A64, &ctx->m2m_A32,
                       &ctx->l2l_A64, &ctx->l2l_A32, &ctx->shift_cls, &ctx->m2m_slots, &ctx->shift_tiles};
     for (DevBuf* b : bufs) lf_free(*b);
     for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);

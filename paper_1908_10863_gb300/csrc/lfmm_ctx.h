@@ -123,6 +123,7 @@ struct lfmm_ctx {
     int m2l_rm = 0, m2l_rp = 0, m2l_ntiles = 0;
     // tensor-core free M2L (float32 form, (p+1)^2 <= 128)
     DevBuf m2l_Atc, m2l_tc_tiles, m2l_Ms;
+    DevBuf tc_mseg;  // runs of the merged tensor-core tiles, [merged tile][LFMM_TC_MSEG] int4 (level, start, count, 0)
     DevBuf m2m_Atc, l2l_Atc, tc_shift_tiles;        // tensor-core M2M / L2L operators and tiles
     std::vector<int> tc_m2m_first, tc_l2l_first;    // first tensor-core translation tile of each level
     std::vector<int4> tc_shift_h;
@@ -130,7 +131,7 @@ struct lfmm_ctx {
     DevBuf m2m_A64, m2m_A32, l2l_A64, l2l_A32, shift_cls, m2m_slots, shift_tiles;
     std::vector<int> m2m_first, l2l_first;  // first tile of each level
     int l2l_tile_base = 0, shift_ready = 0;
-    std::vector<int4> m2l_tiles_h, l2l_tiles_h, m2m_tiles_h, tc_tiles_h;  // host staging of asynchronous uploads
+    std::vector<int4> m2l_tiles_h, l2l_tiles_h, m2m_tiles_h, tc_tiles_h, tc_mseg_h;  // host staging of asynchronous uploads
     std::vector<float4> level_consts_h;
     std::vector<float4> p2p_consts_h;
     void* host_pin = nullptr;  // small pinned host buffer for readbacks that must not wait
@@ -279,6 +280,7 @@ LfErr lf_shift_gemm(lfmm_ctx* ctx, int level, bool l2l, cudaStream_t st);
 // ---- tensor-core free M2L (lfmm_m2l_tc.cu) ----
 // byte offset in ctx->counts of the int counting device waits that ran out
 #define LFMM_TIMEOUT_OFF 40960
+#define LFMM_TC_MSEG 16  // runs per merged tensor-core M2L tile (one leftover run per level and class)
 LfErr lf_setup_m2l_tc(lfmm_ctx* ctx, const double* A64, const double* M2M64, const double* L2L64, int KP, int RP);
 LfErr lf_shift_tc(lfmm_ctx* ctx, int level, bool l2l, cudaStream_t st);
 LfErr lf_wait_probe(lfmm_ctx* ctx, double limit_ms, int* timed_out);

@@ -306,6 +306,65 @@ static void m2l_tiles_interleaved(const int* hcnt, int depth, int tn, std::vecto
     }
 }
 
+// Tensor-core tiles: the full tiles of every (level, class) run, in the
+// order of m2l_tiles_interleaved; the leftover of each run (fewer than tn
+// targets: every run of a small level) joins the leftovers of its class on
+// the other levels in merged tiles of up to tn targets and LFMM_TC_MSEG runs
+// (tile.x = -1 - its index in segs, tile.z = its runs), after the full tiles.
+// A tile streams the operators of its 189 offsets whatever its fill, so a
+// small tree's coarse levels no longer pay that once per level and class.
+static void m2l_tc_tiles(const int* hcnt, int depth, int tn, std::vector<int4>& out, std::vector<int4>& segs)
+{
+    out.clear();
+    segs.clear();
+    std::vector<int4> left[8];  // (level, start, count, 0)
+    int start = 0;
+    for (int l = 1; l <= depth; ++l) {
+        int first[8], n[8], most = 0;
+        for (int c = 0; c < 8; ++c) {
+            n[c] = hcnt[16 + l * 8 + c];
+            first[c] = start;
+            start += n[c];
+            most = std::max(most, n[c]);
+        }
+        if (l < 2) continue;
+        for (int s = 0; s < most; s += tn)
+            for (int c = 0; c < 8; ++c) {
+                if (s + tn <= n[c])
+                    out.push_back(make_int4(l, c, first[c] + s, tn));
+                else if (s < n[c])
+                    left[c].push_back(make_int4(l, first[c] + s, n[c] - s, 0));
+            }
+    }
+    for (int c = 0; c < 8; ++c) {
+        std::vector<int4> cur;
+        int fill = 0;
+        auto flush = [&]() {
+            if (cur.empty()) return;
+            if (cur.size() == 1) {
+                out.push_back(make_int4(cur[0].x, c, cur[0].y, cur[0].z));
+            } else {
+                const int m = (int)(segs.size() / LFMM_TC_MSEG);
+                segs.insert(segs.end(), cur.begin(), cur.end());
+                segs.resize((size_t)(m + 1) * LFMM_TC_MSEG, make_int4(0, 0, 0, 0));
+                out.push_back(make_int4(-1 - m, c, (int)cur.size(), fill));
+            }
+            cur.clear();
+            fill = 0;
+        };
+        for (int4 r : left[c])
+            while (r.z > 0) {
+                if (fill == tn || (int)cur.size() == LFMM_TC_MSEG) flush();
+                const int take = std::min(r.z, tn - fill);
+                cur.push_back(make_int4(r.x, r.y, take, 0));
+                fill += take;
+                r.y += take;
+                r.z -= take;
+            }
+        flush();
+    }
+}
+
 LfErr lf_prepare_m2l(lfmm_ctx* ctx, cudaStream_t st)
 {
     ctx->m2l_ntiles = 0;
@@ -401,7 +460,7 @@ LfErr lf_prepare_m2l(lfmm_ctx* ctx, cudaStream_t st)
     ctx->m2l_tc_ntiles = 0;
     if (ctx->m2l_tc_ok) {
         const int TN = lf_m2l_tc_tile(ctx);
-        m2l_tiles_interleaved(hcnt, depth, TN, tct);
+        m2l_tc_tiles(hcnt, depth, TN, tct, ctx->tc_mseg_h);
         ctx->m2l_tc_ntiles = (int)tct.size();
         // translations: M2M tiles of parents (levels 0 .. depth-1, box order),
         // L2L tiles of children grouped by octant (levels 1 .. depth)
@@ -437,6 +496,11 @@ LfErr lf_prepare_m2l(lfmm_ctx* ctx, cudaStream_t st)
             LF_CHECK(cudaMemcpyAsync(ctx->m2l_tc_tiles.ptr, tct.data(), tct.size() * sizeof(int4),
                                      cudaMemcpyHostToDevice, st));
         }
+        const std::vector<int4>& segs = ctx->tc_mseg_h;
+        LF_TRY(lf_reserve(ctx->tc_mseg, segs.size() * sizeof(int4) + 16));
+        if (!segs.empty())
+            LF_CHECK(cudaMemcpyAsync(ctx->tc_mseg.ptr, segs.data(), segs.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                                     st));
     }
     double* hl = ctx->m2l_levelh_h;
     for (int l = 0; l < 16; ++l) hl[l] = (l <= depth) ? ctx->levels[l].h : 0.0;

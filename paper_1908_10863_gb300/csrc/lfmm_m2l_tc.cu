@@ -94,6 +94,7 @@
 #define TC_TMEM_COLS 256
 #define TC_WIDE_STAGES 4             // wide form: one CTA per SM
 #define TC_WIDE_SMEM (TC_WIDE_STAGES * TC_STAGE_BYTES + 1024)
+#define TC_MSEG LFMM_TC_MSEG
 
 struct TcArgs {
     const int4* tiles;      // level, class, start, count
@@ -103,6 +104,7 @@ struct TcArgs {
     int noff;               // offsets per class: 189 (M2L), 8 (M2M: children), 1 (L2L: parent)
     int unit_scale;         // 1: add D as it is (M2M, L2L); 0: add D / h_level (M2L)
     const double* levelh;   // box size per level
+    const int4* mseg;       // merged tiles' runs [merged tile][TC_MSEG]: (level, start, count, 0)
     const unsigned char* A; // [343][4 chunks][2 pieces x 16 KB], pre-swizzled
     const float* Ms;        // split multipoles [box + 1][2 pieces][128] (last box: zeros)
     int zero_row;           // index of the zero box of Ms
@@ -114,6 +116,32 @@ struct TcArgs {
     int groups;             // CTAs per tile (offset groups; divides noff)
     int* err;               // [0]: timeouts
 };
+
+// Target t of a tile (a box id, or -1 past the tile's count) and its output
+// scale (1 for M2M and L2L, 1/h of the target's level for M2L).  A tile with
+// level < 0 is a merged tile: the leftover runs (fewer targets than a tile)
+// of one octant class on several levels, listed at mseg[-1 - level] with
+// tile.z runs; its columns take the runs in order, each with its level's
+// scale (the operators depend only on the class and the offset).
+__device__ __forceinline__ int tc_tile_target(const TcArgs& g, const int4& tile, int t, float& ih)
+{
+    ih = 0.f;
+    if (t >= tile.w) return -1;
+    if (tile.x >= 0) {
+        ih = g.unit_scale ? 1.f : 1.f / (float)g.levelh[tile.x];
+        return g.sorted ? g.sorted[tile.z + t] : tile.z + t;
+    }
+    const int4* sg = g.mseg + (size_t)(-1 - tile.x) * TC_MSEG;
+    for (int k = 0; k < tile.z; ++k) {
+        const int4 r = sg[k];
+        if (t < r.z) {
+            ih = g.unit_scale ? 1.f : 1.f / (float)g.levelh[r.x];
+            return g.sorted[r.y + t];
+        }
+        t -= r.z;
+    }
+    return -1;
+}
 
 // WIDE: expansions with 128 < (p+1)^2 <= 256 (p <= 15): the output rows are
 // two 128-row halves (two MMAs per K step), K runs over 16 chunks, and a tile
@@ -144,18 +172,23 @@ __global__ void __launch_bounds__(TC_THREADS, WIDE ? 1 : TC_MINB) k_m2l_tc(TcArg
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
     __shared__ int s_tb[TC_N];
+    __shared__ float s_ih[TC_N];  // output scale of each target column
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int item = blockIdx.x;
     const int4 tile = g.tiles[item / g.groups];
     const int grp = item % g.groups;
     const int goff = g.noff / g.groups;
-    const int level = tile.x, cl = tile.y, start = tile.z, cnt = tile.w;
+    const int cl = tile.y, cnt = tile.w;
     const int nc = g.nc;
     const int nkc = g.nkc;  // K chunks that hold coefficients (the rest are zero)
     const int nstage = goff * nkc;
 
-    if (tid < TN) s_tb[tid] = (tid < cnt) ? (g.sorted ? g.sorted[start + tid] : start + tid) : -1;
+    if (tid < TN) {
+        float ih;
+        s_tb[tid] = tc_tile_target(g, tile, tid, ih);
+        s_ih[tid] = ih;
+    }
     if (tid == 0) {
         for (int s = 0; s < NST; ++s) {
             mbar_init(&full_bar[s], TC_PROD_WARPS + 1);  // one arrival per producer warp + the bulk copy's
@@ -255,7 +288,6 @@ __global__ void __launch_bounds__(TC_THREADS, WIDE ? 1 : TC_MINB) k_m2l_tc(TcArg
             // narrow: half = target half of the 256 columns; wide: half = the
             // 128-row half of the outputs, whose accumulator starts at column half * TN
             const int row = (WIDE ? 128 * half : 0) + 32 * q + lane;
-            const float ih = g.unit_scale ? 1.f : (float)(1.0 / g.levelh[level]);
 #pragma unroll 1
             for (int ch = 0; ch < 4; ++ch) {
                 const int col0 = (WIDE ? 0 : half * 128) + ch * 32;  // first target of the chunk
@@ -272,7 +304,7 @@ __global__ void __launch_bounds__(TC_THREADS, WIDE ? 1 : TC_MINB) k_m2l_tc(TcArg
 #pragma unroll
                     for (int i = 0; i < 32; ++i) {
                         const int j = col0 + i;
-                        if (j < cnt) atomicAdd(g.L + (size_t)blockIdx.y * g.l_stride + (size_t)s_tb[j] * nc + row, v[i] * ih);
+                        if (j < cnt) atomicAdd(g.L + (size_t)blockIdx.y * g.l_stride + (size_t)s_tb[j] * nc + row, v[i] * s_ih[j]);
                     }
                 }
             }
@@ -402,8 +434,9 @@ __global__ void __launch_bounds__(TCP_THREADS, 1) k_m2l_tcp(TcArgs g, int nunits
         for (int u = blockIdx.x; u < nunits && !stop; u += gridDim.x) {
             const int4 tile = g.tiles[u / g.groups];
             const int grp = u % g.groups;
-            const int cl = tile.y, start = tile.z, cnt = tile.w;
-            const int my_tb = (row < cnt) ? (g.sorted ? g.sorted[start + row] : start + row) : -1;
+            const int cl = tile.y;
+            float ih_unused;
+            const int my_tb = tc_tile_target(g, tile, row, ih_unused);
             const int rot = (u / g.groups) % goff;
             int my_src = -1;
             // the source at the next offset is loaded one offset ahead
@@ -520,7 +553,7 @@ __global__ void __launch_bounds__(TCP_THREADS, 1) k_m2l_tcp(TcArgs g, int nunits
         for (int u = blockIdx.x; u < nunits; u += gridDim.x, ++ul) {
             const int b = ul & 1;
             const int4 tile = g.tiles[u / g.groups];
-            const int level = tile.x, start = tile.z, cnt = tile.w;
+            const int cnt = tile.w;
             const bool ok = mbar_wait(&accf_bar[b], (ul >> 1) & 1);
             tc_fence_after();
             if (!ok || *(volatile int*)&s_abort) {
@@ -528,7 +561,6 @@ __global__ void __launch_bounds__(TCP_THREADS, 1) k_m2l_tcp(TcArgs g, int nunits
                 atomicExch(&s_abort, 1);
                 break;
             }
-            const float ih = g.unit_scale ? 1.f : (float)(1.0 / g.levelh[level]);
             float* Lb = g.L + (size_t)blockIdx.y * g.l_stride;
 #pragma unroll 1
             for (int ch = 0; ch < TC_N / 32; ++ch) {
@@ -536,12 +568,14 @@ __global__ void __launch_bounds__(TCP_THREADS, 1) k_m2l_tcp(TcArgs g, int nunits
                 if (col0 >= cnt) break;  // warp-uniform
                 // target box of column col0 + lane, handed to every lane by shuffles
                 const int jl = col0 + lane;
-                const int tbl = (jl < cnt) ? (g.sorted ? g.sorted[start + jl] : start + jl) : -1;
+                float ihl;
+                const int tbl = tc_tile_target(g, tile, jl, ihl);
                 float v[32];
                 tc_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * TC_N + col0), v);
 #pragma unroll
                 for (int i = 0; i < 32; ++i) {
                     const int tb = __shfl_sync(0xffffffffu, tbl, i);
+                    const float ih = __shfl_sync(0xffffffffu, ihl, i);
                     if (r < nc && tb >= 0) atomicAdd(Lb + (size_t)tb * nc + r, v[i] * ih);
                 }
             }
@@ -666,6 +700,7 @@ static TcArgs tc_args(lfmm_ctx* ctx)
     const int nb = ctx->nbox_total;
     TcArgs g;
     g.levelh = ctx->m2l_levelh.as<double>();
+    g.mseg = ctx->tc_mseg.as<int4>();
     g.Ms = ctx->m2l_Ms.as<float>();
     g.zero_row = nb;
     g.ms_stride = (size_t)(nb + 1) * TC_XP * ms_row(ctx);
