@@ -54,9 +54,9 @@ def fp32_peak_tflops(sm_mhz):
 # times the nominal TF32/BF16 ratio (1.1 / 2.25 PFLOP/s); fallback 1.9 PF bf16.
 TF32_PER_BF16 = 1.1 / 2.25
 # DRAM bytes (read + write) of one k_m2l_tc launch per free-space M2L pair,
-# from an ncu capture of the bench's own workload (N=1,048,576, p=10: 251.4 MB
-# read + 33.5 MB written for 10,905,072 pairs), scaled to the bench's pair count.
-TC_DRAM_BYTES_PER_PAIR = (251.352832e6 + 33.462528e6) / 10905072
+# from an ncu capture of the bench's own workload (N=1,048,576, p=10: 245.1 MB
+# read + 33.3 MB written for 10,905,072 pairs), scaled to the bench's pair count.
+TC_DRAM_BYTES_PER_PAIR = (245.149952e6 + 33.294592e6) / 10905072
 
 
 def tf32_peak_tflops():
