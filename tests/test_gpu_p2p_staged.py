@@ -91,7 +91,7 @@ def test_staged_clustered_against_oracle():
     # box staged in pieces).  Pair distances of ~1e-4 against float32 offsets
     # of ~1e-2 from the leaf centre limit the float32 form there (both kernels
     # measured Err2(phi) 9.1e-5, field 8.0e-4 on these targets): each kernel is
-    # judged against the oracle, and the staged one must be as accurate as
+    # compared with the oracle, and the staged one must be as accurate as
     # the per-box one.
     import os
     w = _clustered()
