@@ -146,7 +146,9 @@ lfmm_status lfmm_evaluate_device(lfmm_ctx* ctx, int nrhs, const double* q_dev, d
  * tables if needed (once per context) and writes the largest deviation of the
  * interpolated kernels from the quadrature at 2048 seeded points per
  * component, relative to |I_00| (field kernels times the distance), to
- * *max_rel_err (may be NULL).  Does not switch them on (LFMM_OPT_NEAR_TABLES). */
+ * *max_rel_err (may be NULL).  Does not change LFMM_OPT_NEAR_TABLES: with its
+ * automatic default the float32 form uses built tables wherever the near
+ * lists hold reaction pairs; the float32 kernels read a float32 copy. */
 lfmm_status lfmm_near_tables(lfmm_ctx* ctx, double* max_rel_err);
 
 /* Self-check of failure detection (the paper has no counterpart).  Every
@@ -245,8 +247,10 @@ lfmm_status lfmm_batch_info(lfmm_batch* b, int64_t* out, int nout);
  *   1. tensor-core free M2L (float32 form) for every member, for none, or for
  *      the members of at least 20,000 / 60,000 charges;
  *   2. near-list split of the P2P kernels: automatic, 1, 2, 4, 8;
- *   3. near-field reaction kernels from the pre-computed tables (members
- *      whose near lists hold reaction pairs; see lfmm_near_tables).
+ *   3. near-field reaction kernels by quadrature (0) or from the pre-computed
+ *      tables (1; members whose near lists hold reaction pairs; see
+ *      lfmm_near_tables).  The members' automatic default already takes the
+ *      tables in the float32 form.
  * A member tuned alone picks the settings that fill the GPU with its own
  * work; in a batch the members fill it together, which is what this times.
  * Afterwards every member holds the winner.  Needs use_graph = 1.
