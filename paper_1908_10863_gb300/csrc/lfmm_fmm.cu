@@ -101,7 +101,7 @@ template <typename R>
 __global__ void __launch_bounds__(128) k_p2m(int64_t n, int p, const int* __restrict__ leaf_of,
                                              const LfD4* __restrict__ cen, const double* __restrict__ xs,
                                              const double* __restrict__ ys, const double* __restrict__ zs,
-                                             const R* __restrict__ q, double h, R* __restrict__ M, int nrhs,
+                                             const R* __restrict__ q, double ih, R* __restrict__ M, int nrhs,
                                              int64_t qstride, size_t mstride)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -120,8 +120,7 @@ __global__ void __launch_bounds__(128) k_p2m(int64_t n, int p, const int* __rest
     const bool head = valid && (lane == 0 || bprev != b);
     R x = 0, y = 0, z = 0;
     if (valid) {
-        const LfD4 c = cen[b];
-        const double ih = 1.0 / h;
+        const LfD4 c = cen[b];  // ih = 1 / h of the leaf level, divided once on the host
         x = (R)((xs[i] - c.x) * ih);
         y = (R)((ys[i] - c.y) * ih);
         z = (R)((zs[i] - c.z) * ih);
@@ -428,15 +427,14 @@ __global__ void k_m2l(M2LArgs a)
 template <typename R>
 __global__ void __launch_bounds__(128) k_l2p(int64_t n, int p, const int* __restrict__ leaf_of,
                                              const LfD4* __restrict__ cen, const double* __restrict__ xs,
-                                             const double* __restrict__ ys, const double* __restrict__ zs, double h,
+                                             const double* __restrict__ ys, const double* __restrict__ zs, double ih,
                                              const R* __restrict__ L, double* __restrict__ phi,
                                              double* __restrict__ fld, int nrhs, size_t lstride, int64_t ostride)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int b = leaf_of[i];
-    const LfD4 c = cen[b];
-    const double ih = 1.0 / h;
+    const LfD4 c = cen[b];  // ih = 1 / h of the leaf level, divided once on the host
     const R x = (R)((xs[i] - c.x) * ih), y = (R)((ys[i] - c.y) * ih), z = (R)((zs[i] - c.z) * ih);
     const int nc = lf_nc(p);
     for (int r = 0; r < nrhs; ++r) {
@@ -549,7 +547,7 @@ static LfErr far_field(lfmm_ctx* ctx, cudaStream_t st)
                                    nr, st));
         ++ctx->launches, k_p2m<R><<<lf_blocks(ctx->n, 128), 128, 0, st>>>(
             ctx->n, p, ctx->leaf_of.as<int>(), cen, ctx->xs.as<double>(), ctx->ys.as<double>(),
-            ctx->zs.as<double>(), ctx->q_sorted.as<R>(), leaf.h, M, nr, ctx->n, ms);
+            ctx->zs.as<double>(), ctx->q_sorted.as<R>(), 1.0 / leaf.h, M, nr, ctx->n, ms);
         LF_TRY(lf_cuda(cudaGetLastError(), "p2m"));
     }
     lf_prof_stop(ctx, ph, st);
@@ -660,7 +658,8 @@ static LfErr far_field(lfmm_ctx* ctx, cudaStream_t st)
     {
         ++ctx->launches, k_l2p<R><<<lf_blocks(ctx->n, 128), 128, 0, st>>>(
             ctx->n, p, ctx->leaf_of.as<int>(), cen, ctx->xs.as<double>(), ctx->ys.as<double>(),
-            ctx->zs.as<double>(), leaf.h, L, ctx->phi_far.as<double>(), ctx->fld_far.as<double>(), nr, ms, ctx->n);
+            ctx->zs.as<double>(), 1.0 / leaf.h, L, ctx->phi_far.as<double>(), ctx->fld_far.as<double>(), nr, ms,
+            ctx->n);
         LF_TRY(lf_cuda(cudaGetLastError(), "l2p"));
     }
     lf_prof_stop(ctx, ph, st);
